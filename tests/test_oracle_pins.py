@@ -1,0 +1,577 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle (oracle/qnsch_ref.c) against a statement that is not
+the oracle's own formula:
+  * the discrete energy identity of Thm. 6.2 (Sec. 6.1) for arbitrary states;
+  * the pointwise discrete continuity equation behind Thm. 6.1 and exact
+    conservation of sum(rho) and sum(rho c) after a converged step;
+  * second-order consistency of every residual family with the continuous
+    equations of Sec. 3-4 (closed forms from sympy);
+  * Newton's method with a direct solve of each linearised system (tiny grids)
+    against the multigrid fixed point;
+  * local Jacobians of the smoothers against differences of the residual;
+  * conflict-freeness of the colourings against the measured stencil;
+  * special cases (constant state at rest, x-independence, rho1 = rho2,
+    mirror symmetry) and the limit of eta(rho1, rho2) at rho1 = rho2.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.ref import RefSolver
+from paper_1703_06606_gb300 import workloads as W
+
+
+def rho_fn(c, r1, r2):
+    return r1 * r2 / ((r2 - r1) * c + r1)
+
+
+def make(m1, m2, px, **kw):
+    base = dict(Lx=1.0, periodic_x=px, levels=0, rho1=1.0, rho2=3.0, eta1=1.0, eta2=2.5,
+                Re=50.0, We=5.0, Pe=20.0, Cn=0.05, Fr=0.8)
+    base.update(kw)
+    return RefSolver(m1, m2, **base)
+
+
+def set_random(s, seed_n, seed_x, amp=None):
+    fn = W.random_state(s.m1, s.m2, s.periodic_x, seed=seed_n)
+    s.set_fields(fn)
+    s.begin_step(2e-3)
+    fx = W.random_state(s.m1, s.m2, s.periodic_x, seed=seed_x, scale=amp)
+    s.set_iterate(fx)
+    return fn, s.get_iterate()
+
+
+def u_cols(s):
+    return slice(1, s.m1 + 1) if s.periodic_x else slice(1, s.m1)
+
+
+# ---------------------------------------------------------------------------
+# energy identity (Thm. 6.2) for arbitrary states
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("px", [False, True])
+@pytest.mark.parametrize("seed", [1, 2])
+def test_energy_identity_arbitrary_state(px, seed):
+    """h^2 [dt(u,N_u) + dt(v,N_v) + dt/M (mu,N_c) + dt/M (p,N_p) - 1/M (c-c^n, N_mu)
+    + dt/Fr (y, -alpha rho^n N_c + rho^n N_p)] = E(x) - E^n + D(x): the test
+    functions of the proof of Thm. 6.2 make every term of the scheme telescope."""
+    s = make(16, 12, px)
+    dt = 2e-3
+    fn = W.random_state(16, 12, px, seed=seed)
+    s.set_fields(fn)
+    s.begin_step(dt)
+    fx = W.random_state(16, 12, px, seed=seed + 100)
+    s.set_iterate(fx)
+    x = s.get_iterate()
+    r, _ = s.residual()
+    N = {k: -v for k, v in r.items()}
+    P = s.params()
+    h, M, alpha, Fr_inv = P["h"], P["M"], P["alpha"], P["Fr_inv"]
+    rhon = rho_fn(s.get_fields()["c"], 1.0, 3.0)
+    y = ((np.arange(1, 13) - 0.5) * h)[:, None]
+    cols = u_cols(s)
+    terms = [dt * np.sum(x["u"][:, cols] * N["u"][:, cols]),
+             dt * np.sum(x["v"][1:-1, :] * N["v"][1:-1, :]),
+             dt / M * np.sum(x["mu"] * N["c"]),
+             dt / M * np.sum(x["p"] * N["p"]),
+             -1.0 / M * np.sum((x["c"] - fn["c"]) * N["mu"]),
+             dt * Fr_inv * np.sum(y * (-alpha * rhon * N["c"] + rhon * N["p"]))]
+    lhs = h * h * sum(terms)
+    rhs = s.iterate_energy() - s.energy() + s.iterate_dissipation()
+    scale = h * h * sum(abs(t) for t in terms)
+    assert abs(lhs - rhs) <= 1e-12 * scale, (lhs, rhs, scale)
+    assert s.iterate_dissipation() > 0
+
+
+def test_energy_identity_detects_planted_sign_error():
+    """The identity is sensitive: flipping the sign of one term family breaks it."""
+    s = make(16, 12, True)
+    dt = 2e-3
+    fn = W.random_state(16, 12, True, seed=5)
+    s.set_fields(fn)
+    s.begin_step(dt)
+    s.set_iterate(W.random_state(16, 12, True, seed=6))
+    x = s.get_iterate()
+    r, _ = s.residual()
+    P = s.params()
+    h, M = P["h"], P["M"]
+    cols = u_cols(s)
+    a = dt * np.sum(x["u"][:, cols] * -r["u"][:, cols])
+    b = dt * np.sum(x["v"][1:-1, :] * -r["v"][1:-1, :])
+    c = dt / M * np.sum(x["mu"] * -r["c"]) + dt / M * np.sum(x["p"] * -r["p"])
+    d = -1.0 / M * np.sum((x["c"] - fn["c"]) * -r["mu"])
+    rhon = rho_fn(fn["c"], 1.0, 3.0)
+    y = ((np.arange(1, 13) - 0.5) * h)[:, None]
+    g = dt * P["Fr_inv"] * np.sum(y * (-P["alpha"] * rhon * -r["c"] + rhon * -r["p"]))
+    rhs = s.iterate_energy() - s.energy() + s.iterate_dissipation()
+    good = h * h * (a + b + c + d + g)
+    bad = h * h * (a + b + c - d + g)
+    assert abs(good - rhs) < 1e-10 * abs(rhs) + 1e-14
+    assert abs(bad - rhs) > 1e-3 * abs(rhs)
+
+
+# ---------------------------------------------------------------------------
+# mass: pointwise continuity (proof of Thm. 6.1) and conservation
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("px", [False, True])
+def test_pointwise_continuity_identity(px):
+    """-alpha rho^n N_c + rho^n N_p = (rho - rho^n)/dt + d_x(A_x rho^n u) + d_y(A_y rho^n v)
+    at every cell, for any state (App. A.4 with the secant r of (def-r))."""
+    s = make(16, 12, px)
+    dt = 2e-3
+    fn = W.random_state(16, 12, px, seed=11)
+    s.set_fields(fn)
+    s.begin_step(dt)
+    s.set_iterate(W.random_state(16, 12, px, seed=12))
+    x = s.get_iterate()
+    r, _ = s.residual()
+    P = s.params()
+    h, alpha = P["h"], P["alpha"]
+    rn = rho_fn(fn["c"], 1.0, 3.0)
+    rho = rho_fn(x["c"], 1.0, 3.0)
+    lhs = -alpha * rn * -r["c"] + rn * -r["p"]
+    # A_x rho^n at x-edges i = 0..m1 (Neumann or periodic ghosts of rho^n)
+    if px:
+        rpad = np.concatenate([rn[:, -1:], rn, rn[:, :1]], axis=1)
+    else:
+        rpad = np.concatenate([rn[:, :1], rn, rn[:, -1:]], axis=1)
+    Axr = 0.5 * (rpad[:, :-1] + rpad[:, 1:])            # (m2, m1+1)
+    fx = Axr * x["u"]
+    rpy = np.concatenate([rn[:1, :], rn, rn[-1:, :]], axis=0)
+    Ayr = 0.5 * (rpy[:-1, :] + rpy[1:, :])              # (m2+1, m1)
+    fy = Ayr * x["v"]
+    rhs = (rho - rn) / dt + (fx[:, 1:] - fx[:, :-1]) / h + (fy[1:, :] - fy[:-1, :]) / h
+    assert np.max(np.abs(lhs - rhs)) <= 1e-11 * np.max(np.abs(rhs))
+
+
+@pytest.mark.parametrize("px", [False, True])
+def test_mass_conserved_after_step(px):
+    P = W.small_case(32, 32, px)
+    s = RefSolver(**P.create_kwargs(), tol=1e-11)
+    s.set_fields(P.fields())
+    m0 = s.mass()
+    e0 = s.energy()
+    for _ in range(2):
+        n, res = s.step(P.dt)
+        assert res <= 1e-11
+    m1 = s.mass()
+    assert abs(m1[0] - m0[0]) <= 1e-13 * m0[0]
+    assert abs(m1[1] - m0[1]) <= 1e-12 * m0[1]
+    assert s.energy() < e0
+
+
+# ---------------------------------------------------------------------------
+# second-order consistency with the continuous equations (sympy closed forms)
+# ---------------------------------------------------------------------------
+
+def _continuous_residuals(prm, dt):
+    sp = pytest.importorskip("sympy")
+    x, y = sp.symbols("x y", real=True)
+    pi = sp.pi
+    c = sp.Rational(1, 2) + sp.Rational(1, 4) * sp.cos(2 * pi * x) * sp.cos(pi * y)
+    cn = (sp.Rational(1, 2) + sp.Rational(1, 5) * sp.sin(2 * pi * x) * sp.cos(pi * y)
+          + sp.Rational(1, 10) * sp.cos(2 * pi * y))
+    mu = sp.Rational(3, 10) * sp.cos(2 * pi * x + sp.Rational(1, 2)) * sp.cos(pi * y)
+    p = sp.Rational(1, 5) * sp.sin(2 * pi * x) * sp.cos(2 * pi * y)
+    u = sp.Rational(3, 10) * sp.cos(2 * pi * x) * sp.sin(pi * y)
+    un = sp.Rational(1, 5) * sp.sin(2 * pi * x) * sp.sin(2 * pi * y) + sp.Rational(1, 10) * sp.sin(pi * y)
+    v = sp.Rational(1, 4) * sp.sin(2 * pi * x) * sp.sin(pi * y)
+    vn = sp.Rational(1, 5) * sp.cos(2 * pi * x) * sp.sin(2 * pi * y)
+    r1, r2, m1_, m2_ = prm["rho1"], prm["rho2"], prm["eta1"], prm["eta2"]
+    alpha, K, Lam, M = prm["alpha"], prm["K"], prm["Lam"], prm["M"]
+    Re, Pe, Fr_inv, eps = prm["Re"], prm["Pe"], prm["Fr_inv"], prm["eps_m"]
+    rho = lambda q: r1 * r2 / ((r2 - r1) * q + r1)
+    visc = lambda q: m1_ * m2_ / ((m2_ - m1_) * q + m1_)
+    F = lambda q: q ** 2 * (q - 1) ** 2 / 4
+    g = lambda a, b: (a * (a - 1) + b * (b - 1)) * (a + b - 1) / 4
+    rs = lambda a, b: -alpha * rho(a) * rho(b)
+    m = sp.sqrt(cn ** 2 * (1 - cn) ** 2 + eps)
+    dx = lambda f: sp.diff(f, x)
+    dy = lambda f: sp.diff(f, y)
+    div_k_grad = lambda k, f: dx(k * dx(f)) + dy(k * dy(f))
+    rn, rc = rho(cn), rho(c)
+    rh = (rc + rn) / 2
+    ch = (c + cn) / 2
+    G = lambda f: dx(f) ** 2 + dy(f) ** 2
+    # (mm-phase-1), (mm-chem-1), (mm-mass2-1), (mm-mom-1) with the frozen data of Sec. 6.1
+    Nc = rc * (c - cn) / dt + rn * (u * dx(cn) + v * dy(cn)) - div_k_grad(m, mu) / Pe \
+        - alpha / Pe * div_k_grad(m, p)
+    Nmu = rc * mu - K * (rh * g(c, cn) + (F(c) + F(cn)) / 2 * rs(c, cn)) \
+        - Lam / 4 * (G(c) + G(cn)) * rs(c, cn) + Lam * div_k_grad(rh, ch)
+    Np = dx(u) + dy(v) - alpha / Pe * div_k_grad(m, mu) - alpha ** 2 / Pe * div_k_grad(m, p)
+    vis = visc(cn)
+    divu = dx(u) + dy(v)
+    divrun = dx(rn * un) + dy(rn * vn)
+    Nu = rn * (u - un) / dt + rn * (un * dx(u) + vn * dy(u)) + (rc - rn) * u / (2 * dt) \
+        + divrun * u / 2 + dx(p) / M - rn * mu * dx(cn) / M - div_k_grad(vis, u) / Re \
+        - dx(vis * divu) / (3 * Re)
+    Nv = rn * (v - vn) / dt + rn * (un * dx(v) + vn * dy(v)) + (rc - rn) * v / (2 * dt) \
+        + divrun * v / 2 + dy(p) / M - rn * mu * dy(cn) / M - div_k_grad(vis, v) / Re \
+        - dy(vis * divu) / (3 * Re) + Fr_inv * rn
+    fields = dict(c=c, cn=cn, mu=mu, p=p, u=u, un=un, v=v, vn=vn)
+    fl = {k: sp.lambdify((x, y), f, "numpy") for k, f in fields.items()}
+    Nl = {k: sp.lambdify((x, y), f, "numpy") for k, f in
+          dict(c=Nc, mu=Nmu, p=Np, u=Nu, v=Nv).items()}
+    return fl, Nl
+
+
+def _grid_values(fl, m, h):
+    xc = (np.arange(1, m + 1) - 0.5) * h
+    xe = np.arange(0, m + 1) * h
+    Xc, Yc = np.meshgrid(xc, xc)
+    Xu, Yu = np.meshgrid(xe, xc)
+    Xv, Yv = np.meshgrid(xc, xe)
+    ev = lambda f, X, Y: np.broadcast_to(f(X, Y), X.shape).astype(float)
+    return dict(cell=(Xc, Yc), u=(Xu, Yu), v=(Xv, Yv), ev=ev)
+
+
+@pytest.mark.slow
+def test_second_order_consistency_with_continuous_equations():
+    """Every residual family approximates the continuous operator of Sec. 4.1 at
+    its own grid location with error O(h^2); a dropped term, wrong sign or
+    transposed operand gives an O(1) error instead."""
+    dt = 1e-2
+    kw = dict(rho1=1.0, rho2=3.0, eta1=1.0, eta2=2.5, Re=50.0, We=5.0, Pe=20.0, Cn=0.05, Fr=0.8)
+    errs = []
+    fl = Nl = None
+    for m in (16, 32, 64):
+        s = RefSolver(m, m, Lx=1.0, periodic_x=True, levels=1, **kw)
+        prm = dict(s.params(), **kw)
+        prm["Re"], prm["Pe"] = kw["Re"], kw["Pe"]
+        if fl is None:
+            fl, Nl = _continuous_residuals(prm, dt)
+        h = 1.0 / m
+        G = _grid_values(fl, m, h)
+        ev = G["ev"]
+        nfield = dict(c=ev(fl["cn"], *G["cell"]), mu=np.zeros((m, m)), p=np.zeros((m, m)),
+                      u=ev(fl["un"], *G["u"]), v=ev(fl["vn"], *G["v"]))
+        s.set_fields(nfield)
+        s.begin_step(dt)
+        s.set_iterate(dict(c=ev(fl["c"], *G["cell"]), mu=ev(fl["mu"], *G["cell"]),
+                           p=ev(fl["p"], *G["cell"]), u=ev(fl["u"], *G["u"]),
+                           v=ev(fl["v"], *G["v"])))
+        r, _ = s.residual()
+        e = {}
+        for k, loc in (("c", "cell"), ("mu", "cell"), ("p", "cell"), ("u", "u"), ("v", "v")):
+            exact = ev(Nl[k], *G[loc])
+            d = -r[k] - exact
+            if k == "u":
+                d = d[:, 1:]
+            if k == "v":
+                d = d[1:-1, :]
+            e[k] = np.max(np.abs(d)) / max(1.0, np.max(np.abs(exact)))
+        errs.append(e)
+    for k in errs[0]:
+        r1 = errs[0][k] / errs[1][k]
+        r2 = errs[1][k] / errs[2][k]
+        assert r2 > 3.3 and r1 > 3.0, (k, [e[k] for e in errs])
+        assert errs[2][k] < 5e-3, (k, errs[2][k])
+
+
+# ---------------------------------------------------------------------------
+# multigrid fixed point vs Newton with a direct solve (tiny grids)
+# ---------------------------------------------------------------------------
+
+def _pack(s, f):
+    cols = u_cols(s)
+    return np.concatenate([f["c"].ravel(), f["mu"].ravel(), f["p"].ravel(),
+                           f["u"][:, cols].ravel(), f["v"][1:-1, :].ravel()])
+
+
+def _unpack(s, z, like):
+    m1, m2 = s.m1, s.m2
+    n = m1 * m2
+    f = {k: v.copy() for k, v in like.items()}
+    f["c"] = z[:n].reshape(m2, m1)
+    f["mu"] = z[n:2 * n].reshape(m2, m1)
+    f["p"] = z[2 * n:3 * n].reshape(m2, m1)
+    cols = u_cols(s)
+    nu = f["u"][:, cols].size
+    f["u"][:, cols] = z[3 * n:3 * n + nu].reshape(m2, -1)
+    if s.periodic_x:
+        f["u"][:, 0] = f["u"][:, -1]
+    f["v"][1:-1, :] = z[3 * n + nu:].reshape(m2 - 1, m1)
+    return f
+
+
+def _newton(s, x0):
+    like = x0
+    z = _pack(s, x0)
+    n = s.m1 * s.m2
+
+    def F(zz):
+        s.set_iterate(_unpack(s, zz, like))
+        r, _ = s.residual()
+        return -_pack(s, r)
+
+    for it in range(30):
+        Fz = F(z)
+        if np.max(np.abs(Fz)) < 1e-12:
+            break
+        J = np.zeros((z.size, z.size))
+        for k in range(z.size):
+            dz = 1e-6 * max(1.0, abs(z[k]))
+            zp = z.copy(); zp[k] += dz
+            zm = z.copy(); zm[k] -= dz
+            J[:, k] = (F(zp) - F(zm)) / (2 * dz)
+        gauge = np.zeros(z.size)
+        gauge[2 * n:3 * n] = 1.0
+        A = np.vstack([J, gauge])
+        b = np.concatenate([-Fz, [-np.sum(z[2 * n:3 * n])]])
+        dz = np.linalg.lstsq(A, b, rcond=None)[0]
+        z = z + dz
+    return _unpack(s, z, like), np.max(np.abs(F(z)))
+
+
+@pytest.mark.parametrize("m1,m2,px", [(8, 8, False), (8, 8, True), (8, 12, False)])
+def test_multigrid_fixed_point_equals_newton_direct_solve(m1, m2, px):
+    P = W.small_case(m1, m2, px)
+    P.Cn, P.Pe = 0.1, 10.0
+    s = RefSolver(**P.create_kwargs(), tol=1e-13, maxcyc=200)
+    f0 = P.fields()
+    s.set_fields(f0)
+    n, res = s.step(P.dt)
+    xm = s.get_fields()
+    s.set_fields(f0)
+    s.begin_step(P.dt)
+    xn, fres = _newton(s, s.get_iterate())
+    assert fres < 1e-11
+    xn["p"] -= xn["p"].mean()
+    for k in xm:
+        scale = max(np.max(np.abs(xm[k])), 1e-8)
+        assert np.max(np.abs(xm[k] - xn[k])) <= 1e-10 * max(scale, 1.0), k
+
+
+# ---------------------------------------------------------------------------
+# local Jacobians of the smoothers
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("px", [False, True])
+def test_ch_local_jacobian_matches_central_differences(px):
+    s = make(12, 10, px)
+    set_random(s, 21, 22)
+    base = s.get_iterate()
+    for (i, j) in [(1, 1), (5, 4), (12, 10), (1, 10), (7, 1)]:
+        J, R = s.ch_jacobian(i, j)
+        Jfd = np.zeros((2, 2))
+        for col, key in enumerate(("c", "mu")):
+            for sgn in (+1, -1):
+                f = {k: v.copy() for k, v in base.items()}
+                eps = 1e-6
+                f[key][j - 1, i - 1] += sgn * eps
+                s.set_iterate(f)
+                _, Rs = s.ch_jacobian(i, j)
+                Jfd[:, col] += sgn * Rs / (2 * eps)
+        s.set_iterate(base)
+        assert np.allclose(J, Jfd, rtol=1e-6, atol=1e-6 * np.max(np.abs(J))), (i, j, J, Jfd)
+
+
+@pytest.mark.parametrize("px", [False, True])
+def test_vanka_jacobian_equals_exact_differences(px):
+    """The NS block is affine in (u, v, p) for fixed (c, mu): unit differences of
+    the residual give its Jacobian exactly (up to rounding)."""
+    s = make(12, 10, px)
+    set_random(s, 31, 32)
+    base = s.get_iterate()
+    m1 = s.m1
+    for (i, j) in [(1, 1), (6, 5), (12, 10), (1, 10), (12, 1), (4, 7)]:
+        J, R, act = s.vanka_jacobian(i, j)
+        Jd = np.zeros((5, 5))
+        slots = [("u", (j - 1, i - 1 if i > 1 else (m1 if px else 0))), ("u", (j - 1, i)),
+                 ("v", (j - 1, i - 1)), ("v", (j, i - 1)), ("p", (j - 1, i - 1))]
+        for col, (key, idx) in enumerate(slots):
+            if not act[col]:
+                continue
+            f = {k: v.copy() for k, v in base.items()}
+            f[key][idx] += 1.0
+            if key == "u" and px and idx[1] == m1:
+                f[key][idx[0], 0] = f[key][idx]
+            s.set_iterate(f)
+            _, R2, _ = s.vanka_jacobian(i, j)
+            Jd[:, col] = R2 - R
+        s.set_iterate(base)
+        a = act
+        assert np.allclose(J[np.ix_(a, a)], Jd[np.ix_(a, a)], rtol=1e-9,
+                           atol=1e-9 * np.max(np.abs(J))), (i, j)
+
+
+def test_vanka_local_solve_matches_numpy():
+    s = make(12, 10, False)
+    set_random(s, 41, 42)
+    for (i, j) in [(3, 3), (1, 1), (12, 10)]:
+        J, R, act = s.vanka_jacobian(i, j)
+        d = np.linalg.solve(J, R)
+        assert np.all(np.isfinite(d))
+    # one Vanka sweep of a colour removes the local residuals of its cells exactly
+    s.smooth_vanka(0)
+    K = s.ncolours_vanka
+    for (i, j) in [(i, j) for j in range(1, 11) for i in range(1, 13)]:
+        col = (2 * i + j) % K if s.periodic_x else (i + 2 * j) % K
+        if col == 0:
+            _, R, act = s.vanka_jacobian(i, j)
+            assert np.max(np.abs(R[act])) < 1e-9 * (1 + np.max(np.abs(R)))
+
+
+# ---------------------------------------------------------------------------
+# colourings: no two cells of one colour touch each other's equations
+# ---------------------------------------------------------------------------
+
+def _stencil(s, base):
+    """unknown (key, index) -> set of residual locations it changes (measured)."""
+    r0, _ = s.residual()
+    out = {}
+    keys = [("c", (j, i)) for j in range(s.m2) for i in range(s.m1)]
+    keys += [("mu", (j, i)) for j in range(s.m2) for i in range(s.m1)]
+    keys += [("p", (j, i)) for j in range(s.m2) for i in range(s.m1)]
+    cols = range(1, s.m1 + 1) if s.periodic_x else range(1, s.m1)
+    keys += [("u", (j, i)) for j in range(s.m2) for i in cols]
+    keys += [("v", (j, i)) for j in range(1, s.m2) for i in range(s.m1)]
+    for key, idx in keys:
+        f = {k: v.copy() for k, v in base.items()}
+        f[key][idx] += 1e-3
+        if key == "u" and s.periodic_x and idx[1] == s.m1:
+            f["u"][idx[0], 0] = f["u"][idx]
+        s.set_iterate(f)
+        r, _ = s.residual()
+        hit = set()
+        for k in r:
+            d = np.argwhere(np.abs(r[k] - r0[k]) > 0)
+            for q in d:
+                q = tuple(int(t) for t in q)
+                if k == "u" and s.periodic_x and q[1] == 0:
+                    q = (q[0], s.m1)
+                hit.add((k, q))
+        out[(key, idx)] = hit
+    s.set_iterate(base)
+    return out
+
+
+@pytest.mark.parametrize("m1,m2,px", [(8, 6, True), (4, 6, True), (7, 6, False)])
+def test_colourings_are_conflict_free(m1, m2, px):
+    s = make(m1, m2, px)
+    base = set_random(s, 51, 52)[1]
+    st = _stencil(s, base)
+    K = s.ncolours_vanka
+
+    def vanka_block(i, j):  # 1-based cell -> owned unknowns / equations
+        w = i - 1 if i > 1 else (m1 if px else None)
+        own = []
+        if w is not None and (px or w >= 1):
+            own.append(("u", (j - 1, w)))
+        if px or i < m1:
+            own.append(("u", (j - 1, i)))
+        if j > 1:
+            own.append(("v", (j - 1, i - 1)))
+        if j < m2:
+            own.append(("v", (j, i - 1)))
+        own.append(("p", (j - 1, i - 1)))
+        return [o for o in own if o in st]
+
+    def ch_block(i, j):
+        return [("c", (j - 1, i - 1)), ("mu", (j - 1, i - 1))]
+
+    colour_v = (lambda i, j: (2 * i + j) % K) if px else (lambda i, j: (i + 2 * j) % K)
+    for blocks, colour in ((vanka_block, colour_v), (ch_block, lambda i, j: (i + j) % 2)):
+        cells = [(i, j) for j in range(1, m2 + 1) for i in range(1, m1 + 1)]
+        for a in cells:
+            for b in cells:
+                if a == b or colour(*a) != colour(*b):
+                    continue
+                ua = blocks(*a)
+                eqb = {(k if k != "c" else "c", idx) for k, idx in blocks(*b)}
+                # equations of b live where b's unknowns live
+                for unk in ua:
+                    assert not (st[unk] & eqb), ("conflict", a, b, unk)
+                    assert unk not in blocks(*b)
+
+
+# ---------------------------------------------------------------------------
+# special cases
+# ---------------------------------------------------------------------------
+
+def test_constant_state_at_rest_stays_put():
+    s = RefSolver(16, 16, periodic_x=False, rho1=1.0, rho2=4.0, eta1=1.0, eta2=3.0, Re=10.0,
+                  We=1.0, Pe=10.0, Cn=0.05, Fr=math.inf, tol=1e-12)
+    f = dict(c=np.full((16, 16), 0.3), mu=np.zeros((16, 16)), p=np.zeros((16, 16)),
+             u=np.zeros((16, 17)), v=np.zeros((17, 16)))
+    s.set_fields(f)
+    s.step(1e-3)
+    g = s.get_fields()
+    assert np.max(np.abs(g["c"] - 0.3)) < 1e-14
+    assert np.max(np.abs(g["u"])) < 1e-13 and np.max(np.abs(g["v"])) < 1e-13
+    assert np.ptp(g["mu"]) < 1e-12 and np.max(np.abs(g["p"])) < 1e-12
+
+
+def test_x_independent_data_stays_x_independent():
+    P = W.small_case(16, 16, True)
+    P.init_args = dict(y0=0.5, H0=0.0)
+    s = RefSolver(**P.create_kwargs(), tol=1e-12)
+    s.set_fields(P.fields())
+    s.step(P.dt)
+    g = s.get_fields()
+    for k in ("c", "mu", "p", "v"):
+        assert np.max(np.ptp(g[k], axis=1)) < 1e-11, k
+    assert np.max(np.abs(g["u"])) < 1e-11
+
+
+def test_equal_densities_make_velocity_discretely_divergence_free():
+    """rho1 = rho2 gives alpha = 0, so (pm-num-mass) reduces to div_d u = 0."""
+    P = W.capillary_64()
+    P.m1 = P.m2 = 32
+    P.Cn, P.Pe = 0.04, 25.0
+    s = RefSolver(**P.create_kwargs(), tol=1e-12)
+    f = P.fields()
+    s.set_fields(f)
+    s.step(P.dt)
+    g = s.get_fields()
+    h = 1.0 / 32
+    div = (g["u"][:, 1:] - g["u"][:, :-1]) / h + (g["v"][1:, :] - g["v"][:-1, :]) / h
+    assert np.max(np.abs(div)) < 1e-10
+    assert s.params()["alpha"] == 0.0
+
+
+def test_mirror_symmetry_of_centred_drop():
+    P = W.rising_drop_256x512()
+    P.m1, P.m2, P.Cn, P.Pe = 16, 32, 0.06, 1 / 0.06
+    P.init_args = dict(x0=0.5, y0=0.5, R=0.25)
+    s = RefSolver(**P.create_kwargs(), tol=1e-13, maxcyc=100)
+    s.set_fields(P.fields())
+    s.step(P.dt)
+    g = s.get_fields()
+    assert np.max(np.abs(g["c"] - g["c"][:, ::-1])) < 1e-10
+    assert np.max(np.abs(g["u"] + g["u"][:, ::-1])) < 1e-10
+    assert np.max(np.abs(g["v"] - g["v"][:, ::-1])) < 1e-10
+
+
+def test_eta_limit_and_continuity():
+    """eta(rho1, rho2) of Sec. 8.1 tends to 3/(2 sqrt 2 rho1) as rho2 -> rho1; the
+    series branch used near the limit joins the direct formula continuously, and
+    far from the limit eta matches a high-precision evaluation of the formula."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+
+    def eta_mp(r1, r2):
+        r1, r2 = mp.mpf(r1), mp.mpf(r2)
+        return (r2 - r1) ** 3 / (2 * mp.sqrt(2) * r1 * r2 * (r2 ** 2 - r1 ** 2 - 2 * r1 * r2 * mp.log(r2 / r1)))
+
+    for r1 in (1.0, 0.3):
+        s = RefSolver(8, 8, rho1=r1, rho2=r1)
+        assert abs(s.params()["eta"] - 3 / (2 * math.sqrt(2) * r1)) < 1e-14 / r1
+        for q in (1e-4, 1e-2, 0.0999, 0.1001, 0.5, 9.0, -0.5):
+            r2 = r1 * (1 + q)
+            e = RefSolver(8, 8, rho1=r1, rho2=r2).params()["eta"]
+            assert abs(e - float(eta_mp(r1, r2))) < 1e-10 * e, (r1, q)
+
+
+def test_vcycle_contracts():
+    """Soft target (the paper prints no contraction factor): < 0.35 per cycle."""
+    for P in (W.small_case(32, 32, True), W.small_case(32, 64, False)):
+        s = RefSolver(**P.create_kwargs())
+        s.set_fields(P.fields())
+        s.begin_step(P.dt)
+        hist = [max(s.vcycle()[:5]) for _ in range(6)]
+        rates = [hist[k + 1] / hist[k] for k in range(1, 5)]
+        assert max(rates) < 0.35, hist
