@@ -1,0 +1,318 @@
+"""Benchmark: cell-updates per second of the implicit primitive q-NSCH time step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One "step" is one implicit time step of the primitive method (Sec. 6.1 of
+arXiv:1703.06606): freeze the level-n data on every multigrid level, run FAS
+V-cycles (Sec. 7.1) until the largest scaled residual norm is <= 1e-9, commit.
+Workload: the rising droplet, 256 x 512 cells on [0,1] x [0,2], walls all round,
+drop radius 0.25 at (0.5, 0.5), rho and viscosity ratio 10 (light drop),
+Re = 35, We = 10, Fr = 1, Cn = 0.01, dt = 2e-4, FP64 (synthetic initial state,
+no dataset).  value = cells x K / (device time of the K timed steps), inputs
+resident in HBM; L2 is flushed (256 MiB write) between timed steps.
+
+With N > 1 (torchrun) each rank runs an independent replica of the workload on
+its own GPU (a single instance does not shard); value sums the cells of all
+ranks over the slowest rank's time.
+
+--impl reference times the FP64 CPU oracle (serial C, host cores) on the same
+workload and prints the same JSON line with "impl": "reference".
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1703_06606_gb300 import workloads  # noqa: E402
+
+METRIC = ("cell-updates/s per time step at residual 1e-9 (FP64 plain vs batched mixed) "
+          "+ p99 latency")
+UNIT = "cell-updates/s"
+
+
+def field_bytes(P):
+    m1, m2 = P.m1, P.m2
+    return 8 * (3 * m1 * m2 + (m1 + 1) * m2 + m1 * (m2 + 1))
+
+
+def config_of(P, levels, precision="fp64"):
+    return {"workload": P.name, "grid": "%dx%d" % (P.m1, P.m2), "levels": levels,
+            "dt": P.dt, "tol": P.tol, "precision": precision,
+            "smoother": "CH 2x2 red-black + Vanka 5x5 (5 colours)",
+            "nu1_nu2_nucoarse": [2, 2, 20],
+            "l2": "flushed between timed steps (256 MiB write)",
+            "parallelism": "replicas"}
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# the CPU oracle (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+def oracle_rate(P, steps, budget_s):
+    """Time the FP64 oracle (serial, as it stands) on the workload: up to `steps`
+    implicit steps from the initial state, stopping once `budget_s` is spent."""
+    from oracle.ref import RefSolver
+    r = RefSolver(**P.create_kwargs(), tol=P.tol)
+    r.set_fields(P.fields())
+    times, cycles = [], []
+    t_all = time.perf_counter()
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        n, _ = r.step(P.dt)
+        times.append(time.perf_counter() - t0)
+        cycles.append(n)
+        if time.perf_counter() - t_all > budget_s:
+            break
+    return times, cycles
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1703_06606_gb300 import qnsch
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    if rank == 0:
+        qnsch.lib()  # build once
+    if world > 1:
+        dist.barrier()
+    qnsch.lib()
+
+    P = workloads.rising_drop_256x512()
+    stream = torch.cuda.current_stream(dev)
+    s = qnsch.Solver(**P.create_kwargs(), tol=P.tol, stream=stream)
+    levels = s.levels
+    f0 = P.fields()
+    dev_fields = {k: torch.tensor(v, device=dev, dtype=torch.float64) for k, v in f0.items()}
+    s.set_fields_device(dev_fields)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    for _ in range(args.warmup):
+        s.step(P.dt)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, device time per step (CUDA events on our stream)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    cyc = []
+    s.profile(True)
+    l0 = qnsch.kernel_launches()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            evs[k][0].record(stream)
+            n, res = s.step(P.dt)
+            evs[k][1].record(stream)
+            cyc.append(n)
+        torch.cuda.synchronize()
+    launches = qnsch.kernel_launches() - l0
+    prof_n, prof_ms = s.profile_read()
+    s.profile(False)
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_s = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+        dist.barrier()
+
+    # ---- end to end through the public API with host buffers (pinned)
+    host_in = {k: torch.empty(v.shape, dtype=torch.float64, pin_memory=True).numpy()
+               for k, v in f0.items()}
+    cur = s.get_fields()
+    for k in host_in:
+        host_in[k][...] = cur[k]
+    e2e_ms = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.set_fields(host_in)
+        n, res = s.step(P.dt)
+        out = s.get_fields()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        for q in host_in:
+            host_in[q][...] = out[q]
+    e2e_total = sum(e2e_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    cells = P.cells
+    value = world * cells * args.steps / total_s
+    e2e_value = world * cells * args.steps / e2e_total
+    # dominant kernel: the FP64 Vanka smoother on the finest level, colour sweep
+    # = m1*m2/5 cell visits; algorithmic FP64 operations per visit from the kernel
+    visits = cells / 5.0
+    flops_per_visit = VANKA_FP64_FLOPS_PER_VISIT
+    avg_ms = prof_ms / max(prof_n, 1)
+    achieved = visits * flops_per_visit / (avg_ms * 1e-3) / 1e12
+    peak = FP64_PEAK_TFLOPS
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_of(P, levels),
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
+                       "p99": float(np.percentile(step_ms, 99))},
+        "vcycles_per_step": float(np.mean(cyc)),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": field_bytes(P),
+                "d2h_bytes_per_step": field_bytes(P)},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "k_vanka<double> finest level",
+                     "launches_timed": prof_n, "avg_launch_us": avg_ms * 1e3,
+                     "peak_source": "measured FP64 FMA throughput (profiles/fp64_fp32_peak_probe.md)"},
+        "clocks": clk.summary(),
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        times, cycles = oracle_rate(P, steps=3, budget_s=args.cpu_budget)
+        line["cpu_baseline"] = {
+            "value": cells * len(times) / sum(times), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "first %d time step(s) of the rising-droplet 256x512 workload from its "
+                      "initial state, serial FP64 oracle (%s V-cycles), %.1f s"
+                      % (len(times), "/".join(map(str, cycles)), sum(times))}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# algorithmic FP64 operations per Vanka cell visit (add/sub/mul/div = 1, fused
+# multiply-add = 2), counted from the formulas of k_vanka; see the design doc
+VANKA_FP64_FLOPS_PER_VISIT = 960.0
+# measured FP64 FMA throughput of one GB300 (dependent-chain-free DFMA loop)
+FP64_PEAK_TFLOPS = 1.193
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    P = workloads.rising_drop_256x512()
+    per_step_budget = 150.0 / max(args.steps + args.warmup, 1)
+    # warm-up: one short untimed oracle call on a small case
+    from oracle.ref import RefSolver
+    w = workloads.small_case(32, 32, False)
+    r = RefSolver(**w.create_kwargs())
+    r.set_fields(w.fields())
+    for _ in range(min(args.warmup, 3)):
+        r.step(w.dt)
+    times, cycles = oracle_rate(P, steps=args.steps, budget_s=max(per_step_budget * args.steps, 20.0))
+    value = P.cells * len(times) / sum(times)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": len(times),
+        "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_of(P, 8), "impl": "reference",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "first %d time step(s) of the workload from its initial "
+                                   "state (%s V-cycles)" % (len(times),
+                                                            "/".join(map(str, cycles)))},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,157 @@
+/*
+ * qnsch.h -- C ABI of the GB300 library for one implicit time step of the
+ * primitive method for the quasi-incompressible Navier-Stokes-Cahn-Hilliard
+ * system of Guo, Lin, Lowengrub & Wise (arXiv:1703.06606).
+ *
+ * Problem (Sec. 6.1): given (c^n, mu^n, p^n, u^n, v^n) on an m1 x m2 staggered
+ * MAC grid (Sec. 5, App. A) with spacing h = Lx/m1, find the level n+1 fields
+ * solving the fully discrete primitive scheme, equations (pm-num-mx),
+ * (pm-num-mass), (pm-num-phase) and (pm-num-chem).  mu is the paper's mu-bar_c
+ * and p its p-bar.  The nonlinear system is solved by FAS multigrid V-cycles
+ * (Sec. 7.1) until the largest of the five scaled residual norms
+ * (h^2 sum r^2)^{1/2} is at most `tol`.
+ *
+ * Boundaries: y is bounded by no-slip walls (u = v = 0, Neumann data for c, mu, p;
+ * App. A.6).  x is either periodic or bounded by the same walls.
+ *
+ * Host array layouts (row-major, x fastest, no ghost cells; all FP64):
+ *   c, mu, p : m2 rows x m1 columns        (cell (i,j), i = 1..m1, j = 1..m2)
+ *   u        : m2 rows x (m1+1) columns    (u_{i+1/2,j}, i = 0..m1)
+ *   v        : (m2+1) rows x m1 columns    (v_{i,j+1/2}, j = 0..m2)
+ * Wall entries (columns 0 and m1 of u with walls in x, rows 0 and m2 of v) are
+ * ignored on input and returned as 0.  With periodic x, u_{1/2} and u_{m1+1/2}
+ * are one unknown: inputs take column m1, outputs write both columns.
+ *
+ * Ownership: the handle owns all device memory it allocates, until
+ * qnsch_destroy.  Arrays passed in are copied; the library keeps no pointer to
+ * caller memory.  Device memory comes from the allocator set by
+ * qnsch_set_allocator (cudaMalloc/cudaFree by default).  All work is issued on
+ * the stream set by qnsch_set_stream (default: the legacy default stream) and
+ * every call returns only after that work has completed, unless stated.
+ *
+ * Every call returns an int status: 0 on success, a negative QNSCH_E* code on
+ * failure.  On failure no output is written and, unless stated, the handle is
+ * unchanged.
+ */
+#ifndef QNSCH_H
+#define QNSCH_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QNSCH_OK 0
+#define QNSCH_EINVAL (-1)   /* bad argument or option */
+#define QNSCH_ENODEV (-2)   /* no CUDA device */
+#define QNSCH_ENOMEM (-3)   /* allocation failed */
+#define QNSCH_ENOTCONV (-4) /* maxcyc V-cycles without reaching tol; step not committed */
+#define QNSCH_ENAN (-5)     /* non-finite residual; step not committed */
+#define QNSCH_ESTATE (-8)   /* call not valid in the current state (e.g. vcycle outside a step) */
+#define QNSCH_ECUDA (-9)    /* a CUDA call failed */
+
+typedef struct qnsch_s qnsch_t;
+
+typedef struct {
+  int m1, m2;      /* cells in x and y; m1, m2 >= 2; periodic x needs m1 % 4 == 0 */
+  double Lx;       /* domain width; h = Lx / m1, height Ly = m2 h */
+  int periodic_x;  /* 1: periodic in x; 0: no-slip walls in x */
+  int periodic_y;  /* must be 0: y is always bounded by walls */
+  int levels;      /* multigrid levels; 0 = deepest the grid allows */
+} qnsch_grid;
+
+/* Device allocator used for every later allocation (process-wide).
+   alloc(bytes, ctx) returns device memory or NULL; free(ptr, ctx) releases it.
+   Passing NULL for both restores cudaMalloc/cudaFree. */
+int qnsch_set_allocator(void* (*alloc)(size_t bytes, void* ctx),
+                        void (*free_fn)(void* ptr, void* ctx), void* ctx);
+
+/* Create a solver for one instance (Sec. 6.1 statement of the problem).
+   rho1, rho2: densities of the fluids at c = 1 and c = 0 (Sec. 2.1);
+   eta1, eta2: their viscosities (the paper's mu_1, mu_2);
+   Re, We, Pe: Reynolds, Weber, Peclet numbers (Sec. 2.2); Cn: interface
+   parameter epsilon; Fr: Froude number, INFINITY (or <= 0) for no gravity.
+   Derived (Sec. 8): M = Cn, eta = eta(rho1, rho2) of Sec. 8.1, mobility
+   regularisation eps = Cn; each can be overridden with qnsch_set_option.
+   Returns QNSCH_ENODEV without a CUDA device. */
+int qnsch_create(const qnsch_grid* grid, double rho1, double rho2, double eta1, double eta2,
+                 double Re, double We, double Pe, double Cn, double Fr, qnsch_t** out);
+int qnsch_destroy(qnsch_t* h);
+
+/* Options (key: default): "nu1": 2, "nu2": 2 (pre/post smoothing steps),
+   "nu_coarse": 20 (smoothing steps on the coarsest level), "tol": 1e-9,
+   "maxcyc": 50, "omega_vanka": 1, "M": Cn, "eta_st": eta(rho1, rho2),
+   "eps_mob": Cn.  Unknown keys give QNSCH_EINVAL. */
+int qnsch_set_option(qnsch_t* h, const char* key, double value);
+int qnsch_get_option(const qnsch_t* h, const char* key, double* value);
+int qnsch_set_stream(qnsch_t* h, void* cuda_stream);
+int qnsch_levels(const qnsch_t* h);          /* number of levels, or < 0 */
+int qnsch_ncolours_vanka(const qnsch_t* h);  /* 5 (walls in x) or 8 (periodic x) */
+
+/* Committed state (time level n): host arrays in the layouts above. */
+int qnsch_set_fields(qnsch_t* h, const double* c, const double* mu, const double* u,
+                     const double* v, const double* p);
+int qnsch_get_fields(const qnsch_t* h, double* c, double* mu, double* u, double* v, double* p);
+/* Same, with device pointers in the same (dense, ghost-free) layouts. */
+int qnsch_set_fields_device(qnsch_t* h, const double* c, const double* mu, const double* u,
+                            const double* v, const double* p);
+int qnsch_get_fields_device(const qnsch_t* h, double* c, double* mu, double* u, double* v,
+                            double* p);
+
+/* One time step: qnsch_begin_step, then V-cycles until the largest scaled
+   residual norm is <= tol, then qnsch_commit_step.  Writes the number of
+   V-cycles and the final norm (either pointer may be NULL).  Returns
+   QNSCH_ENOTCONV or QNSCH_ENAN, leaving the state at level n, when the
+   iteration does not converge. */
+int qnsch_step(qnsch_t* h, double dt, int* n_vcycles, double* final_residual);
+/* Freeze level-n data on every level (restrict c^n, u^n, v^n; derive rho^n,
+   m(c^n), mu(c^n), G(c^n)) and start the iterate at the level-n fields. */
+int qnsch_begin_step(qnsch_t* h, double dt);
+/* One outer FAS V-cycle on the pending step, followed by removal of the mean of
+   p; writes [scaled l2 norms of r_c, r_mu, r_p, r_u, r_v, then their max norms]
+   after the cycle (NULL allowed). */
+int qnsch_vcycle(qnsch_t* h, double* residual_norms10);
+/* Accept the iterate as level n+1. */
+int qnsch_commit_step(qnsch_t* h);
+
+/* Mass of the committed state (Thm. 6.1): h^2 sum rho(c), h^2 sum rho(c) c. */
+int qnsch_mass(const qnsch_t* h, double* mass_rho, double* mass_rhoc);
+/* Discrete energy E_h of the committed state (Thm. 6.2, norms of App. A.7), and
+   the dissipation of the last committed step (0 before the first step). */
+int qnsch_energy(const qnsch_t* h, double* E, double* last_dissipation);
+
+/* Inspection of a pending step (valid between begin_step and commit_step). */
+int qnsch_set_iterate(qnsch_t* h, const double* c, const double* mu, const double* u,
+                      const double* v, const double* p);
+int qnsch_get_iterate(const qnsch_t* h, double* c, double* mu, double* u, double* v, double* p);
+/* r = f - N(x) on the finest level (f = 0 there) into host arrays (NULL skips a
+   family) and the ten norms of qnsch_vcycle. */
+int qnsch_residual(qnsch_t* h, double* rc, double* rmu, double* rp, double* ru, double* rv,
+                   double* norms10);
+/* Smoother pieces on the finest level (Sec. 7.1): one colour of the CH
+   nonlinear Gauss-Seidel (colour 0: (i+j) even), one colour of the Vanka
+   smoother ((i+2j) mod 5 with walls in x, (2i+j) mod 8 with periodic x), or
+   `sweeps` full smoothing steps (CH red, CH black, Vanka colours 0..K-1). */
+int qnsch_smooth_ch(qnsch_t* h, int colour);
+int qnsch_smooth_vanka(qnsch_t* h, int colour);
+int qnsch_smooth(qnsch_t* h, int sweeps);
+/* Energy and dissipation of the pending iterate against the frozen data. */
+int qnsch_iterate_energy(const qnsch_t* h, double* E, double* D);
+
+/* Measurement hooks (no counterpart in the paper).  qnsch_profile(h, 1) starts
+   bracketing every launch of the Vanka smoother on the finest level with a pair
+   of CUDA events on the handle's stream (at most 4096 launches between reads)
+   and resets the totals; qnsch_profile(h, 0) stops.  qnsch_profile_read
+   synchronises the stream and returns the number of timed launches and their
+   summed device time in milliseconds. */
+int qnsch_profile(qnsch_t* h, int enable);
+int qnsch_profile_read(qnsch_t* h, long long* launches, double* total_ms);
+/* Number of CUDA kernels this library has issued since it was loaded
+   (process-wide, counted on the host at launch). */
+int qnsch_kernel_launches(long long* n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

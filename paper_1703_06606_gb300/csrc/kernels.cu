@@ -1,0 +1,885 @@
+// kernels.cu -- CUDA kernels (sm_103a) for one implicit step of the primitive
+// q-NSCH scheme of arXiv:1703.06606: residual with fused norms (Sec. 6.1),
+// CH 2x2 Newton Gauss-Seidel and 5x5 Vanka smoothers (Sec. 7.1), FAS
+// transfers, frozen-data setup, ghost filling (App. A.6), and FP64 reductions
+// for the norms, the mean of p, mass (Thm. 6.1) and energy (Thm. 6.2).
+#include <cuda_runtime.h>
+
+#include "kernels.h"
+#include "qnsch_dev.cuh"
+
+namespace qn {
+
+constexpr int BX = 32, BY = 8, NT = BX * BY;
+
+static inline dim3 grid2(int nx, int ny) { return dim3((nx + BX - 1) / BX, (ny + BY - 1) / BY); }
+
+// number of kernels issued by this library since load (host-side count)
+static long long g_launches = 0;
+long long launches_issued() { return g_launches; }
+
+// --------------------------------------------------------------------------
+// block reduction helpers (fixed order: deterministic for a fixed launch shape)
+// --------------------------------------------------------------------------
+template <int NV>
+__device__ __forceinline__ void block_sum_store(double (&val)[NV], double* part, int nmax_first) {
+  // first `nmax_first` values are reduced with max, the rest with sum
+  __shared__ double sh[NT / 32][NV];
+  int lane = (threadIdx.y * BX + threadIdx.x) & 31, warp = (threadIdx.y * BX + threadIdx.x) >> 5;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    double x = val[q];
+    for (int o = 16; o > 0; o >>= 1) {
+      double y = __shfl_down_sync(0xffffffffu, x, o);
+      x = (q < nmax_first) ? fmax(x, y) : x + y;
+    }
+    if (lane == 0) sh[warp][q] = x;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double x = lane < NT / 32 ? sh[lane][q] : (q < nmax_first ? 0.0 : 0.0);
+      for (int o = 16; o > 0; o >>= 1) {
+        double y = __shfl_down_sync(0xffffffffu, x, o);
+        x = (q < nmax_first) ? fmax(x, y) : x + y;
+      }
+      if (lane == 0) part[(blockIdx.y * gridDim.x + blockIdx.x) * NV + q] = x;
+    }
+  }
+}
+
+// Sum (or max) nparts rows of NV partials in a fixed order; one block of 256.
+__global__ void k_finalize(const double* part, int nparts, int nv, int nmax_first, double scale_sum,
+                           double* out) {
+  __shared__ double sh[256];
+  for (int q = 0; q < nv; ++q) {
+    bool mx = q < nmax_first;
+    double acc = 0.0;
+    for (int p = threadIdx.x; p < nparts; p += 256) {
+      double x = part[p * nv + q];
+      acc = mx ? fmax(acc, x) : acc + x;
+    }
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+      if (threadIdx.x < s) sh[threadIdx.x] = mx ? fmax(sh[threadIdx.x], sh[threadIdx.x + s])
+                                                 : sh[threadIdx.x] + sh[threadIdx.x + s];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[q] = mx ? sh[0] : sh[0] * scale_sum;
+    __syncthreads();
+  }
+}
+
+// --------------------------------------------------------------------------
+// residual r = f - N(x) (mode 0, optional norms) or f += N(x) (mode 1)
+// thread (i,j): cell families at (i,j), u-edge (i,j) and v-edge (i,j)
+// --------------------------------------------------------------------------
+template <typename T, int MODE>
+__global__ void k_residual(Prm<T> P, Lv<T> L, double* part) {
+  int i = blockIdx.x * BX + threadIdx.x + 1;
+  int j = blockIdx.y * BY + threadIdx.y + 1;
+  double val[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};  // max x5 then sum of squares x5
+  if (i <= L.m1 && j <= L.m2) {
+    int k = L.at(i, j);
+    T nc = op_c(P, L, k), nm = op_mu(P, L, k), np = op_p(P, L, k);
+    bool hu = i <= L.uhi(), hv = j < L.m2;
+    T nu = hu ? op_u(P, L, k) : T(0);
+    T nv = hv ? op_v(P, L, k) : T(0);
+    if (MODE == 0) {
+      T r[5] = {L.fc[k] - nc, L.fmu[k] - nm, L.fp[k] - np, hu ? L.fu[k] - nu : T(0),
+                hv ? L.fv[k] - nv : T(0)};
+      L.rc[k] = r[0];
+      L.rmu[k] = r[1];
+      L.rp[k] = r[2];
+      if (hu) L.ru[k] = r[3];
+      if (hv) L.rv[k] = r[4];
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        double a = (double)r[q];
+        val[q] = fabs(a);
+        val[5 + q] = a * a;
+      }
+    } else {
+      L.fc[k] += nc;
+      L.fmu[k] += nm;
+      L.fp[k] += np;
+      if (hu) L.fu[k] += nu;
+      if (hv) L.fv[k] += nv;
+    }
+  }
+  if (MODE == 0 && part) block_sum_store<10>(val, part, 5);
+}
+
+// --------------------------------------------------------------------------
+// CH step 1 of Sec. 7.1: Newton step on the 2x2 system (N_c, N_mu) in (c, mu)
+// of each cell with (i + j) % 2 == colour; neighbours frozen.  Faces on
+// Neumann walls do not contribute (their ghost follows the cell).
+// --------------------------------------------------------------------------
+template <typename T>
+__global__ void k_ch(Prm<T> P, Lv<T> L, int colour) {
+  int j = blockIdx.y * BY + threadIdx.y + 1;
+  if (j > L.m2) return;
+  int i0 = ((colour - j) & 1) ? 1 : 2;
+  int i = i0 + 2 * (blockIdx.x * BX + threadIdx.x);
+  if (i > L.m1) return;
+  const int W = L.pitch;
+  int k = L.at(i, j);
+  T Rc = op_c(P, L, k) - L.fc[k];
+  T Rm = op_mu(P, L, k) - L.fmu[k];
+  const T *c = L.c, *cn = L.cn, *rn = L.rhon, *mob = L.mobn;
+  T ck = c[k], cnk = cn[k], mk = L.mu[k];
+  T rho = rho_of(P, ck), drho = -P.alpha * rho * rho;
+  T rnk = rn[k];
+  T rh = T(0.5) * (rho + rnk);
+  T chk = ck + cnk;  // 2 c^{n+1/2}
+  T r = -P.alpha * rho * rnk, dr = -P.alpha * drho * rnk;
+  bool wall[4] = {!L.px && i == L.m1, !L.px && i == 1, j == L.m2, j == 1};
+  const int off[4] = {1, -1, W, -W};
+  T sm = 0, dG = 0, dd = 0;
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    if (wall[f]) continue;
+    int q = k + off[f];
+    sm += mob[k] + mob[q];
+    dG += ck - c[q];
+    T rq = T(0.5) * (rho_of(P, c[q]) + rn[q]);
+    dd += T(0.5) * drho * ((c[q] + cn[q]) - chk) - (rh + rq);
+  }
+  // sm = 2 sum A m; dG = h^2 dG/dc; dd = 4 h^2 d(div)/dc
+  T J11 = (rho + drho * (ck - cnk)) * P.idt;
+  T J12 = T(0.5) * sm * P.iPe * L.ih2;
+  T Gs = G_h2(c, k, W) * L.ih2 + L.Gn[k];
+  T dbulk = T(0.5) * drho * gsec(ck, cnk) + rh * gsec_da(ck, cnk) + T(0.5) * fdw(ck) * r +
+            T(0.5) * (Fdw(ck) + Fdw(cnk)) * dr;
+  T dgrad = T(0.25) * P.Lam * (dG * L.ih2 * r + Gs * dr);
+  T J21 = drho * mk - P.K * dbulk - dgrad + P.Lam * T(0.25) * L.ih2 * dd;
+  T J22 = rho;
+  T idet = T(1) / (J11 * J22 - J12 * J21);
+  T dc = (J22 * Rc - J12 * Rm) * idet;
+  T dm = (J11 * Rm - J21 * Rc) * idet;
+  store_cell(L, L.c, i, j, ck - dc);
+  store_cell(L, L.mu, i, j, mk - dm);
+}
+
+// --------------------------------------------------------------------------
+// Vanka step 2 of Sec. 7.1: exact solve of the 5x5 block of cell (i,j):
+// unknowns (u_W, u_E, v_S, v_N, p), equations (N_u W, N_u E, N_v S, N_v N, N_p).
+// Colours: (i + 2j) % 5 (walls in x) or (2i + j) % 8 (periodic x).
+// --------------------------------------------------------------------------
+// Gaussian elimination with partial pivoting on a 5x5 system held in registers.
+// Pivoting by compare-and-swap with compile-time row indices: after the inner
+// loop row k holds the largest |A[r][k]| of rows k..4 (the argmax row).
+template <typename T>
+__device__ __forceinline__ void solve5(T (&A)[5][5], T (&b)[5]) {
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+#pragma unroll
+    for (int r = k + 1; r < 5; ++r) {
+      if (fabs(A[r][k]) > fabs(A[k][k])) {
+#pragma unroll
+        for (int c = k; c < 5; ++c) {
+          T t = A[k][c];
+          A[k][c] = A[r][c];
+          A[r][c] = t;
+        }
+        T t = b[k];
+        b[k] = b[r];
+        b[r] = t;
+      }
+    }
+    T inv = T(1) / A[k][k];
+#pragma unroll
+    for (int r = k + 1; r < 5; ++r) {
+      T l = A[r][k] * inv;
+#pragma unroll
+      for (int c = k + 1; c < 5; ++c) A[r][c] -= l * A[k][c];
+      b[r] -= l * b[k];
+    }
+    A[k][k] = inv;
+  }
+#pragma unroll
+  for (int k = 4; k >= 0; --k) {
+    T s = b[k];
+#pragma unroll
+    for (int c = k + 1; c < 5; ++c) s -= A[k][c] * b[c];
+    b[k] = s * A[k][k];
+  }
+}
+
+template <typename T>
+__global__ void k_vanka(Prm<T> P, Lv<T> L, int colour, T omega) {
+  int j = blockIdx.y * BY + threadIdx.y + 1;
+  if (j > L.m2) return;
+  int i0, stride;
+  if (L.px) {
+    int d = (colour - j) & 7;
+    if (d & 1) return;  // no cell of this colour in row j
+    i0 = d >> 1;
+    if (i0 == 0) i0 = 4;
+    stride = 4;
+  } else {
+    i0 = ((colour - 2 * j) % 5 + 5) % 5;
+    if (i0 == 0) i0 = 5;
+    stride = 5;
+  }
+  int i = i0 + stride * (blockIdx.x * BX + threadIdx.x);
+  if (i > L.m1) return;
+  const int W = L.pitch;
+  const T ih = L.ih, ih2 = L.ih2;
+  const T *rn = L.rhon, *vis = L.visn, *un = L.un, *vn = L.vn;
+  int k = L.at(i, j);
+  int eW = (L.px && i == 1) ? L.m1 : i - 1;
+  int kW = L.at(eW, j);
+  bool act[5] = {L.px || i > 1, L.px || i < L.m1, j > 1, j < L.m2, true};
+  T A[5][5], b[5];
+#pragma unroll
+  for (int r = 0; r < 5; ++r)
+#pragma unroll
+    for (int c = 0; c < 5; ++c) A[r][c] = T(0);
+  const T third = T(1.0 / 3.0);
+  // x-edge rows: q = 0 (west edge, index kW), q = 1 (east edge, index k)
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    int ke = q == 0 ? kW : k;
+    T rl = rn[ke], rr = rn[ke + 1];
+    T axl = T(0.5) * (un[ke] + un[ke - 1]), axr = T(0.5) * (un[ke + 1] + un[ke]);
+    T Arn = T(0.5) * (rl + rr);
+    T Ar = T(0.5) * (rho_of(P, L.c[ke]) + rho_of(P, L.c[ke + 1]));
+    T Art = T(0.25) * (rl + rr + rn[ke + W] + rn[ke + 1 + W]);
+    T Arb = T(0.25) * (rl + rr + rn[ke - W] + rn[ke + 1 - W]);
+    T Avt = T(0.25) * (vis[ke] + vis[ke + 1] + vis[ke + W] + vis[ke + 1 + W]);
+    T Avb = T(0.25) * (vis[ke] + vis[ke + 1] + vis[ke - W] + vis[ke + 1 - W]);
+    T At = T(0.5) * (vn[ke + 1] + vn[ke]), Ab = T(0.5) * (vn[ke + 1 - W] + vn[ke - W]);
+    T gt = (j == L.m2) ? T(2) : T(1), gb = (j == 1) ? T(2) : T(1);
+    T vl = vis[ke], vr = vis[ke + 1];
+    A[q][q] = Arn * P.idt + T(0.5) * (Ar - Arn) * P.idt +
+              T(0.5) * ih * (-rr * axr + rl * axl - Art * At * gt + Arb * Ab * gb) +
+              T(0.5) * ih * ((rr * axr - rl * axl) + (Art * At - Arb * Ab)) +
+              P.iRe * ih2 * ((vr + vl) * (T(1) + third) + gt * Avt + gb * Avb);
+  }
+  {
+    T rc = rn[k], vc = vis[k];
+    T axc = T(0.5) * (un[k] + un[k - 1]);
+    T v3 = vc * P.iRe * ih2 * third;
+    A[0][1] = T(0.5) * rc * axc * ih - vc * P.iRe * ih2 - v3;
+    A[1][0] = -T(0.5) * rc * axc * ih - vc * P.iRe * ih2 - v3;
+    A[0][2] = v3;
+    A[0][3] = -v3;
+    A[1][2] = -v3;
+    A[1][3] = v3;
+    A[0][4] = ih * P.iM;
+    A[1][4] = -ih * P.iM;
+  }
+  // y-edge rows: q = 2 (south edge, index k - W), q = 3 (north edge, index k)
+#pragma unroll
+  for (int q = 2; q < 4; ++q) {
+    int ke = q == 2 ? k - W : k;
+    T rb = rn[ke], rt = rn[ke + W];
+    T ayb = T(0.5) * (vn[ke] + vn[ke - W]), ayt = T(0.5) * (vn[ke + W] + vn[ke]);
+    T Arn = T(0.5) * (rb + rt);
+    T Ar = T(0.5) * (rho_of(P, L.c[ke]) + rho_of(P, L.c[ke + W]));
+    T Are = T(0.25) * (rb + rt + rn[ke + 1] + rn[ke + 1 + W]);
+    T Arw = T(0.25) * (rb + rt + rn[ke - 1] + rn[ke - 1 + W]);
+    T Ave = T(0.25) * (vis[ke] + vis[ke + W] + vis[ke + 1] + vis[ke + 1 + W]);
+    T Avw = T(0.25) * (vis[ke] + vis[ke + W] + vis[ke - 1] + vis[ke - 1 + W]);
+    T Ae = T(0.5) * (un[ke + W] + un[ke]), Aw = T(0.5) * (un[ke - 1 + W] + un[ke - 1]);
+    T ge = (!L.px && i == L.m1) ? T(2) : T(1), gw = (!L.px && i == 1) ? T(2) : T(1);
+    T vb = vis[ke], vt = vis[ke + W];
+    A[q][q] = Arn * P.idt + T(0.5) * (Ar - Arn) * P.idt +
+              T(0.5) * ih * (-Are * Ae * ge + Arw * Aw * gw - rt * ayt + rb * ayb) +
+              T(0.5) * ih * ((Are * Ae - Arw * Aw) + (rt * ayt - rb * ayb)) +
+              P.iRe * ih2 * (ge * Ave + gw * Avw + (vt + vb) * (T(1) + third));
+  }
+  {
+    T rc = rn[k], vc = vis[k];
+    T ayc = T(0.5) * (vn[k] + vn[k - W]);
+    T v3 = vc * P.iRe * ih2 * third;
+    A[2][3] = T(0.5) * rc * ayc * ih - vc * P.iRe * ih2 - v3;
+    A[3][2] = -T(0.5) * rc * ayc * ih - vc * P.iRe * ih2 - v3;
+    A[2][0] = v3;
+    A[2][1] = -v3;
+    A[3][0] = -v3;
+    A[3][1] = v3;
+    A[2][4] = ih * P.iM;
+    A[3][4] = -ih * P.iM;
+  }
+  {
+    const T* mob = L.mobn;
+    bool wall[4] = {!L.px && i == L.m1, !L.px && i == 1, j == L.m2, j == 1};
+    const int off[4] = {1, -1, W, -W};
+    T sm = 0;
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+      if (!wall[f]) sm += mob[k] + mob[k + off[f]];
+    A[4][0] = -ih;
+    A[4][1] = ih;
+    A[4][2] = -ih;
+    A[4][3] = ih;
+    A[4][4] = T(0.5) * P.alpha * P.alpha * P.iPe * sm * ih2;
+  }
+  b[0] = act[0] ? op_u(P, L, kW) - L.fu[kW] : T(0);
+  b[1] = act[1] ? op_u(P, L, k) - L.fu[k] : T(0);
+  b[2] = act[2] ? op_v(P, L, k - W) - L.fv[k - W] : T(0);
+  b[3] = act[3] ? op_v(P, L, k) - L.fv[k] : T(0);
+  b[4] = op_p(P, L, k) - L.fp[k];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (!act[q]) {
+#pragma unroll
+      for (int c = 0; c < 5; ++c) { A[q][c] = T(0); A[c][q] = T(0); }
+      A[q][q] = T(1);
+    }
+  solve5(A, b);
+  if (act[0]) store_u(L, eW, j, L.u[kW] - omega * b[0]);
+  if (act[1]) store_u(L, i, j, L.u[k] - omega * b[1]);
+  if (act[2]) store_v(L, i, j - 1, L.v[k - W] - omega * b[2]);
+  if (act[3]) store_v(L, i, j, L.v[k] - omega * b[3]);
+  store_cell(L, L.p, i, j, L.p[k] - omega * b[4]);
+}
+
+// --------------------------------------------------------------------------
+// ghost filling (App. A.6): every ghost entry computed from interior entries
+// --------------------------------------------------------------------------
+__device__ __forceinline__ int xsrc_cell(int I, int m1, int px) {
+  if (I == 0) return px ? m1 : 1;
+  if (I == m1 + 1) return px ? 1 : m1;
+  return I;
+}
+
+// band: I = -1..m1+1 on rows J in {-1, 0, 1?}... we enumerate a 4-wide frame
+__device__ __forceinline__ bool frame_pos(int t, int m1, int m2, int& I, int& J) {
+  int NX = m1 + 3, NY = m2 + 3;
+  if (t < 4 * NX) {
+    int r = t / NX;
+    I = t % NX - 1;
+    J = r < 2 ? r - 1 : m2 + r - 2;  // rows -1, 0, m2, m2+1
+    return true;
+  }
+  t -= 4 * NX;
+  if (t < 4 * NY) {
+    int cidx = t / NY;
+    J = t % NY - 1;
+    I = cidx < 2 ? cidx - 1 : m1 + cidx - 2;  // columns -1, 0, m1, m1+1
+    return true;
+  }
+  return false;
+}
+
+template <typename T>
+__device__ __forceinline__ void fill_cell_ghost(const Lv<T>& L, T* a, int I, int J) {
+  if (I < 0 || J < 0) return;
+  bool gx = (I == 0 || I == L.m1 + 1), gy = (J == 0 || J == L.m2 + 1);
+  if (!gx && !gy) return;
+  int si = xsrc_cell(I, L.m1, L.px);
+  int sj = J == 0 ? 1 : (J == L.m2 + 1 ? L.m2 : J);
+  a[L.at(I, J)] = a[L.at(si, sj)];
+}
+
+template <typename T>
+__device__ __forceinline__ T u_interior_or_zero(const Lv<T>& L, const T* a, int I, int J) {
+  // value of u(I, J) for J in 1..m2 after applying the x rule
+  if (L.px) {
+    int s = I;
+    if (I == 0) s = L.m1;
+    else if (I == -1) s = L.m1 - 1;
+    else if (I == L.m1 + 1) s = 1;
+    return a[L.at(s, J)];
+  }
+  if (I <= 0 || I >= L.m1) return T(0);
+  return a[L.at(I, J)];
+}
+
+template <typename T>
+__device__ __forceinline__ void fill_u_ghost(const Lv<T>& L, T* a, int I, int J) {
+  if (J < 0) return;
+  bool xg = L.px ? (I == 0 || I == -1 || I == L.m1 + 1) : (I <= 0 || I >= L.m1);
+  bool yg = (J == 0 || J == L.m2 + 1);
+  if (!xg && !yg) return;
+  if (yg) {
+    int sj = J == 0 ? 1 : L.m2;
+    a[L.at(I, J)] = -u_interior_or_zero(L, a, I, sj);
+  } else {
+    a[L.at(I, J)] = u_interior_or_zero(L, a, I, J);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T v_interior_or_zero(const Lv<T>& L, const T* a, int I, int J) {
+  // value of v(I, J) for I in 1..m1 after applying the y (wall) rule
+  if (J <= 0 || J >= L.m2) return T(0);
+  return a[L.at(I, J)];
+}
+
+template <typename T>
+__device__ __forceinline__ void fill_v_ghost(const Lv<T>& L, T* a, int I, int J) {
+  if (I < 0) return;
+  bool xg = (I == 0 || I == L.m1 + 1);
+  bool yg = (J <= 0 || J >= L.m2);
+  if (!xg && !yg) return;
+  if (xg) {
+    int si = xsrc_cell(I, L.m1, L.px);
+    T s = v_interior_or_zero(L, a, si, J);
+    a[L.at(I, J)] = L.px ? s : -s;
+  } else {
+    a[L.at(I, J)] = T(0);
+  }
+}
+
+template <typename T>
+__global__ void k_bc_unknowns(Lv<T> L) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int I, J;
+  if (!frame_pos(t, L.m1, L.m2, I, J)) return;
+  fill_cell_ghost(L, L.c, I, J);
+  fill_cell_ghost(L, L.mu, I, J);
+  fill_cell_ghost(L, L.p, I, J);
+  fill_u_ghost(L, L.u, I, J);
+  fill_v_ghost(L, L.v, I, J);
+}
+
+template <typename T>
+__global__ void k_bc_frozen(Lv<T> L) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int I, J;
+  if (!frame_pos(t, L.m1, L.m2, I, J)) return;
+  fill_cell_ghost(L, L.cn, I, J);
+  fill_u_ghost(L, L.un, I, J);
+  fill_v_ghost(L, L.vn, I, J);
+}
+
+// rho(c^n), m(c^n), mu(c^n) on the whole ghosted cell range; G(c^n) inside
+template <typename T>
+__global__ void k_frozen_derived(Prm<T> P, Lv<T> L) {
+  int i = blockIdx.x * BX + threadIdx.x;
+  int j = blockIdx.y * BY + threadIdx.y;
+  if (i > L.m1 + 1 || j > L.m2 + 1) return;
+  int k = L.at(i, j);
+  T c = L.cn[k];
+  L.rhon[k] = rho_of(P, c);
+  L.mobn[k] = mob_of(P, c);
+  L.visn[k] = visc_of(P, c);
+  if (i >= 1 && i <= L.m1 && j >= 1 && j <= L.m2) L.Gn[k] = G_h2(L.cn, k, L.pitch) * L.ih2;
+}
+
+// --------------------------------------------------------------------------
+// FAS transfers
+// --------------------------------------------------------------------------
+// coarse iterate = R x_h (cells: 4-mean; edges: mean of the 2 coincident fine edges),
+// and a copy kept for the correction
+template <typename T>
+__global__ void k_restrict_state(Lv<T> F, Lv<T> C) {
+  int I = blockIdx.x * BX + threadIdx.x;
+  int J = blockIdx.y * BY + threadIdx.y;
+  if (I > C.m1 || J > C.m2) return;
+  int kc = C.at(I, J);
+  if (I >= 1 && J >= 1) {
+    int kf = F.at(2 * I - 1, 2 * J - 1), W = F.pitch;
+    T a = T(0.25) * (F.c[kf] + F.c[kf + 1] + F.c[kf + W] + F.c[kf + W + 1]);
+    T b = T(0.25) * (F.mu[kf] + F.mu[kf + 1] + F.mu[kf + W] + F.mu[kf + W + 1]);
+    T d = T(0.25) * (F.p[kf] + F.p[kf + 1] + F.p[kf + W] + F.p[kf + W + 1]);
+    C.c[kc] = a; C.sc[kc] = a;
+    C.mu[kc] = b; C.smu[kc] = b;
+    C.p[kc] = d; C.sp[kc] = d;
+  }
+  if (J >= 1) {  // u edge (I, J), I = 0..M1
+    int kf = F.at(2 * I, 2 * J - 1);
+    T a = T(0.5) * (F.u[kf] + F.u[kf + F.pitch]);
+    C.u[kc] = a; C.su[kc] = a;
+  }
+  if (I >= 1) {  // v edge (I, J), J = 0..M2
+    int kf = F.at(2 * I - 1, 2 * J);
+    T a = T(0.5) * (F.v[kf] + F.v[kf + 1]);
+    C.v[kc] = a; C.sv[kc] = a;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T ru_at(const Lv<T>& F, int i, int j) {
+  if (F.px) {
+    if (i > F.m1) i -= F.m1;
+    if (i < 1) i += F.m1;
+  } else if (i <= 0 || i >= F.m1) {
+    return T(0);
+  }
+  return F.ru[F.at(i, j)];
+}
+template <typename T>
+__device__ __forceinline__ T rv_at(const Lv<T>& F, int i, int j) {
+  if (j <= 0 || j >= F.m2) return T(0);
+  return F.rv[F.at(i, j)];
+}
+
+// coarse right-hand side f_H = R r_h (cells: 4-mean; edges: full weighting),
+// to which k_residual<MODE 1> then adds N_H(R x_h)
+template <typename T>
+__global__ void k_restrict_res(Lv<T> F, Lv<T> C) {
+  int I = blockIdx.x * BX + threadIdx.x + 1;
+  int J = blockIdx.y * BY + threadIdx.y + 1;
+  if (I > C.m1 || J > C.m2) return;
+  int kc = C.at(I, J);
+  int kf = F.at(2 * I - 1, 2 * J - 1), W = F.pitch;
+  C.fc[kc] = T(0.25) * (F.rc[kf] + F.rc[kf + 1] + F.rc[kf + W] + F.rc[kf + W + 1]);
+  C.fmu[kc] = T(0.25) * (F.rmu[kf] + F.rmu[kf + 1] + F.rmu[kf + W] + F.rmu[kf + W + 1]);
+  C.fp[kc] = T(0.25) * (F.rp[kf] + F.rp[kf + 1] + F.rp[kf + W] + F.rp[kf + W + 1]);
+  if (I <= C.uhi()) {
+    T s = T(0);
+#pragma unroll
+    for (int jj = 0; jj < 2; ++jj) {
+      int jf = 2 * J - 1 + jj;
+      s += T(0.25) * ru_at(F, 2 * I - 1, jf) + T(0.5) * ru_at(F, 2 * I, jf) +
+           T(0.25) * ru_at(F, 2 * I + 1, jf);
+    }
+    C.fu[kc] = T(0.5) * s;
+  }
+  if (J < C.m2) {
+    T s = T(0);
+#pragma unroll
+    for (int ii = 0; ii < 2; ++ii) {
+      int ifn = 2 * I - 1 + ii;
+      s += T(0.25) * rv_at(F, ifn, 2 * J - 1) + T(0.5) * rv_at(F, ifn, 2 * J) +
+           T(0.25) * rv_at(F, ifn, 2 * J + 1);
+    }
+    C.fv[kc] = T(0.5) * s;
+  }
+}
+
+template <typename T>
+__global__ void k_restrict_frozen(Lv<T> F, Lv<T> C) {
+  int I = blockIdx.x * BX + threadIdx.x;
+  int J = blockIdx.y * BY + threadIdx.y;
+  if (I > C.m1 || J > C.m2) return;
+  int kc = C.at(I, J);
+  if (I >= 1 && J >= 1) {
+    int kf = F.at(2 * I - 1, 2 * J - 1), W = F.pitch;
+    C.cn[kc] = T(0.25) * (F.cn[kf] + F.cn[kf + 1] + F.cn[kf + W] + F.cn[kf + W + 1]);
+  }
+  if (J >= 1) {
+    int kf = F.at(2 * I, 2 * J - 1);
+    C.un[kc] = T(0.5) * (F.un[kf] + F.un[kf + F.pitch]);
+  }
+  if (I >= 1) {
+    int kf = F.at(2 * I - 1, 2 * J);
+    C.vn[kc] = T(0.5) * (F.vn[kf] + F.vn[kf + 1]);
+  }
+}
+
+// x_h += P(x_H - saved_H): cells piecewise constant; edges coincident or linear
+// in the normal direction, constant in the tangential direction
+template <typename T>
+__global__ void k_prolong(Lv<T> F, Lv<T> C) {
+  int i = blockIdx.x * BX + threadIdx.x + 1;
+  int j = blockIdx.y * BY + threadIdx.y + 1;
+  if (i > F.m1 || j > F.m2) return;
+  int k = F.at(i, j);
+  int I = (i + 1) >> 1, J = (j + 1) >> 1;
+  int kc = C.at(I, J);
+  F.c[k] += C.c[kc] - C.sc[kc];
+  F.mu[k] += C.mu[kc] - C.smu[kc];
+  F.p[k] += C.p[kc] - C.sp[kc];
+  if (i <= F.uhi()) {
+    T e;
+    if ((i & 1) == 0) {
+      int q = C.at(i >> 1, J);
+      e = C.u[q] - C.su[q];
+    } else {
+      int q0 = C.at((i - 1) >> 1, J), q1 = C.at((i + 1) >> 1, J);
+      e = T(0.5) * ((C.u[q0] - C.su[q0]) + (C.u[q1] - C.su[q1]));
+    }
+    F.u[k] += e;
+  }
+  if (j < F.m2) {
+    T e;
+    if ((j & 1) == 0) {
+      int q = C.at(I, j >> 1);
+      e = C.v[q] - C.sv[q];
+    } else {
+      int q0 = C.at(I, (j - 1) >> 1), q1 = C.at(I, (j + 1) >> 1);
+      e = T(0.5) * ((C.v[q0] - C.sv[q0]) + (C.v[q1] - C.sv[q1]));
+    }
+    F.v[k] += e;
+  }
+}
+
+// --------------------------------------------------------------------------
+// reductions
+// --------------------------------------------------------------------------
+template <typename T>
+__global__ void k_sum_p(Lv<T> L, double* part) {
+  int i = blockIdx.x * BX + threadIdx.x + 1;
+  int j = blockIdx.y * BY + threadIdx.y + 1;
+  double val[1] = {0.0};
+  if (i <= L.m1 && j <= L.m2) val[0] = (double)L.p[L.at(i, j)];
+  block_sum_store<1>(val, part, 0);
+}
+
+template <typename T>
+__global__ void k_sub_mean_p(Lv<T> L, const double* sum, double inv_n) {
+  int i = blockIdx.x * BX + threadIdx.x;
+  int j = blockIdx.y * BY + threadIdx.y;
+  if (i > L.m1 + 1 || j > L.m2 + 1) return;
+  L.p[L.at(i, j)] -= (T)(sum[0] * inv_n);
+}
+
+// mass: sum rho(c), sum rho(c) c over the cells (Thm. 6.1)
+template <typename T>
+__global__ void k_mass(Prm<T> P, Lv<T> L, const T* c, double* part) {
+  int i = blockIdx.x * BX + threadIdx.x + 1;
+  int j = blockIdx.y * BY + threadIdx.y + 1;
+  double val[2] = {0.0, 0.0};
+  if (i <= L.m1 && j <= L.m2) {
+    double cc = (double)c[L.at(i, j)];
+    double r = 1.0 / ((double)P.ia * cc + (double)P.ib);
+    val[0] = r;
+    val[1] = r * cc;
+  }
+  block_sum_store<2>(val, part, 0);
+}
+
+// energy E_h (Thm. 6.2): per cell rho [a_x(u^2) + a_y(v^2)]/2 + (eps eta/(2We)) rho G(c)
+// + (eta/(eps We)) rho F(c) + rho y / Fr; weights passed in w[0..2]
+template <typename T>
+__global__ void k_energy(Prm<T> P, Lv<T> L, const T* c, const T* u, const T* v, double w_grad,
+                         double w_bulk, double w_pot, double* part) {
+  int i = blockIdx.x * BX + threadIdx.x + 1;
+  int j = blockIdx.y * BY + threadIdx.y + 1;
+  double val[1] = {0.0};
+  if (i <= L.m1 && j <= L.m2) {
+    const int W = L.pitch;
+    int k = L.at(i, j);
+    double cc = (double)c[k];
+    double r = 1.0 / ((double)P.ia * cc + (double)P.ib);
+    double u0 = u[k], u1 = u[k - 1], v0 = v[k], v1 = v[k - W];
+    double kin = 0.25 * (u0 * u0 + u1 * u1 + v0 * v0 + v1 * v1);
+    double de = (double)c[k + 1] - cc, dw = cc - (double)c[k - 1];
+    double dn = (double)c[k + W] - cc, ds = cc - (double)c[k - W];
+    double G = 0.5 * (de * de + dw * dw + dn * dn + ds * ds) / ((double)L.h * (double)L.h);
+    double F = 0.25 * cc * cc * (cc - 1.0) * (cc - 1.0);
+    double y = (j - 0.5) * (double)L.h;
+    val[0] = r * (kin + w_grad * G + w_bulk * F + w_pot * y);
+  }
+  block_sum_store<1>(val, part, 0);
+}
+
+// dissipation of Thm. 6.2 as sums of squares for the iterate against frozen data;
+// thread (i,j) with i = 0..m1, j = 0..m2 handles vertex (i+1/2, j+1/2) and, for
+// i, j >= 1, cell (i,j) and its east / north faces.  w: [dt/Re, dt/(3Re), dt/(M Pe)]
+template <typename T>
+__global__ void k_dissipation(Prm<T> P, Lv<T> L, double w_visc, double w_div, double w_ch,
+                              double* part) {
+  int i = blockIdx.x * BX + threadIdx.x;
+  int j = blockIdx.y * BY + threadIdx.y;
+  double val[1] = {0.0};
+  if (i <= L.m1 && j <= L.m2) {
+    const int W = L.pitch;
+    const double ih = 1.0 / (double)L.h;
+    int k = L.at(i, j);
+    double acc = 0.0;
+    if (i >= 1 && j >= 1) {
+      double rn = L.rhon[k], mv = L.visn[k];
+      double du0 = (double)L.u[k] - L.un[k], du1 = (double)L.u[k - 1] - L.un[k - 1];
+      double dv0 = (double)L.v[k] - L.vn[k], dv1 = (double)L.v[k - W] - L.vn[k - W];
+      acc += 0.5 * rn * 0.5 * (du0 * du0 + du1 * du1 + dv0 * dv0 + dv1 * dv1);
+      double dxu = ((double)L.u[k] - L.u[k - 1]) * ih, dyv = ((double)L.v[k] - L.v[k - W]) * ih;
+      acc += w_visc * mv * (dxu * dxu + dyv * dyv) + w_div * mv * (dxu + dyv) * (dxu + dyv);
+      double alpha = (double)P.alpha;
+      double mc = (double)L.mu[k] + alpha * (double)L.p[k];
+      if (L.px || i < L.m1) {
+        double me = (double)L.mu[k + 1] + alpha * (double)L.p[k + 1];
+        acc += w_ch * 0.5 * ((double)L.mobn[k] + L.mobn[k + 1]) * (me - mc) * (me - mc) * ih * ih;
+      }
+      if (j < L.m2) {
+        double mn = (double)L.mu[k + W] + alpha * (double)L.p[k + W];
+        acc += w_ch * 0.5 * ((double)L.mobn[k] + L.mobn[k + W]) * (mn - mc) * (mn - mc) * ih * ih;
+      }
+    }
+    if (!L.px || i >= 1) {
+      double Av = 0.25 * ((double)L.visn[k] + L.visn[k + 1] + L.visn[k + W] + L.visn[k + W + 1]);
+      double Dyu = ((double)L.u[k + W] - L.u[k]) * ih;
+      double Dxv = ((double)L.v[k + 1] - L.v[k]) * ih;
+      double wy = (j == 0 || j == L.m2) ? 0.5 : 1.0;
+      double wx = (!L.px && (i == 0 || i == L.m1)) ? 0.5 : 1.0;
+      acc += w_visc * Av * (wy * Dyu * Dyu + wx * Dxv * Dxv);
+    }
+    val[0] = acc;
+  }
+  block_sum_store<1>(val, part, 0);
+}
+
+// --------------------------------------------------------------------------
+// host layout <-> padded layout
+// --------------------------------------------------------------------------
+// kind 0: cell (m2 x m1), 1: u (m2 x (m1+1)), 2: v ((m2+1) x m1)
+template <typename T>
+__global__ void k_pack_in(Lv<T> L, T* dst, const double* src, int kind) {
+  int a = blockIdx.x * BX + threadIdx.x;
+  int b = blockIdx.y * BY + threadIdx.y;
+  int nx = kind == 1 ? L.m1 + 1 : L.m1, ny = kind == 2 ? L.m2 + 1 : L.m2;
+  if (a >= nx || b >= ny) return;
+  int I = kind == 1 ? a : a + 1, J = kind == 2 ? b : b + 1;
+  dst[L.at(I, J)] = (T)src[(size_t)b * nx + a];
+}
+template <typename T>
+__global__ void k_pack_out(Lv<T> L, double* dst, const T* src, int kind) {
+  int a = blockIdx.x * BX + threadIdx.x;
+  int b = blockIdx.y * BY + threadIdx.y;
+  int nx = kind == 1 ? L.m1 + 1 : L.m1, ny = kind == 2 ? L.m2 + 1 : L.m2;
+  if (a >= nx || b >= ny) return;
+  int I = kind == 1 ? a : a + 1, J = kind == 2 ? b : b + 1;
+  dst[(size_t)b * nx + a] = (double)src[L.at(I, J)];
+}
+
+// ==========================================================================
+// launchers
+// ==========================================================================
+static int frame_threads(int m1, int m2) { return 4 * (m1 + 3) + 4 * (m2 + 3); }
+
+template <typename T>
+int nparts_cells(const Lv<T>& L) {
+  dim3 g = grid2(L.m1, L.m2);
+  return g.x * g.y;
+}
+
+template <typename T>
+void launch_residual(const Prm<T>& P, const Lv<T>& L, double* part, cudaStream_t s) {
+  k_residual<T, 0><<<grid2(L.m1, L.m2), dim3(BX, BY), 0, s>>>(P, L, part);
+  ++g_launches;
+}
+template <typename T>
+void launch_add_op(const Prm<T>& P, const Lv<T>& L, cudaStream_t s) {
+  k_residual<T, 1><<<grid2(L.m1, L.m2), dim3(BX, BY), 0, s>>>(P, L, nullptr);
+  ++g_launches;
+}
+template <typename T>
+void launch_ch(const Prm<T>& P, const Lv<T>& L, int colour, cudaStream_t s) {
+  k_ch<T><<<grid2((L.m1 + 1) / 2, L.m2), dim3(BX, BY), 0, s>>>(P, L, colour);
+  ++g_launches;
+}
+template <typename T>
+void launch_vanka(const Prm<T>& P, const Lv<T>& L, int colour, T omega, cudaStream_t s) {
+  int stride = L.px ? 4 : 5;
+  k_vanka<T><<<grid2((L.m1 + stride - 1) / stride, L.m2), dim3(BX, BY), 0, s>>>(P, L, colour, omega);
+  ++g_launches;
+}
+template <typename T>
+void launch_bc_unknowns(const Lv<T>& L, cudaStream_t s) {
+  int n = frame_threads(L.m1, L.m2);
+  k_bc_unknowns<T><<<(n + 255) / 256, 256, 0, s>>>(L);
+  ++g_launches;
+}
+template <typename T>
+void launch_frozen(const Prm<T>& P, const Lv<T>& L, cudaStream_t s) {
+  int n = frame_threads(L.m1, L.m2);
+  k_bc_frozen<T><<<(n + 255) / 256, 256, 0, s>>>(L);
+  ++g_launches;
+  k_frozen_derived<T><<<grid2(L.m1 + 2, L.m2 + 2), dim3(BX, BY), 0, s>>>(P, L);
+  ++g_launches;
+}
+template <typename T>
+void launch_restrict_state(const Lv<T>& F, const Lv<T>& C, cudaStream_t s) {
+  k_restrict_state<T><<<grid2(C.m1 + 1, C.m2 + 1), dim3(BX, BY), 0, s>>>(F, C);
+  ++g_launches;
+}
+template <typename T>
+void launch_restrict_res(const Lv<T>& F, const Lv<T>& C, cudaStream_t s) {
+  k_restrict_res<T><<<grid2(C.m1, C.m2), dim3(BX, BY), 0, s>>>(F, C);
+  ++g_launches;
+}
+template <typename T>
+void launch_restrict_frozen(const Lv<T>& F, const Lv<T>& C, cudaStream_t s) {
+  k_restrict_frozen<T><<<grid2(C.m1 + 1, C.m2 + 1), dim3(BX, BY), 0, s>>>(F, C);
+  ++g_launches;
+}
+template <typename T>
+void launch_prolong(const Lv<T>& F, const Lv<T>& C, cudaStream_t s) {
+  k_prolong<T><<<grid2(F.m1, F.m2), dim3(BX, BY), 0, s>>>(F, C);
+  ++g_launches;
+}
+template <typename T>
+void launch_gauge(const Lv<T>& L, double* part, double* scal, cudaStream_t s) {
+  k_sum_p<T><<<grid2(L.m1, L.m2), dim3(BX, BY), 0, s>>>(L, part);
+  ++g_launches;
+  k_finalize<<<1, 256, 0, s>>>(part, nparts_cells(L), 1, 0, 1.0, scal);
+  ++g_launches;
+  k_sub_mean_p<T><<<grid2(L.m1 + 2, L.m2 + 2), dim3(BX, BY), 0, s>>>(L, scal,
+                                                                     1.0 / ((double)L.m1 * L.m2));
+  ++g_launches;
+}
+template <typename T>
+void launch_norms_finalize(const Lv<T>& L, double* part, double* out10, cudaStream_t s) {
+  // part rows are [max x5, sum of squares x5]; out10 = [l2 x5, max x5] after the
+  // host applies sqrt(h^2 *) to the sums; here: out[0..4] = max, out[5..9] = h^2 sum
+  k_finalize<<<1, 256, 0, s>>>(part, nparts_cells(L), 10, 5, (double)L.h * (double)L.h, out10);
+  ++g_launches;
+}
+template <typename T>
+void launch_mass(const Prm<T>& P, const Lv<T>& L, const T* c, double* part, double* out2,
+                 cudaStream_t s) {
+  k_mass<T><<<grid2(L.m1, L.m2), dim3(BX, BY), 0, s>>>(P, L, c, part);
+  ++g_launches;
+  k_finalize<<<1, 256, 0, s>>>(part, nparts_cells(L), 2, 0, (double)L.h * (double)L.h, out2);
+  ++g_launches;
+}
+template <typename T>
+void launch_energy(const Prm<T>& P, const Lv<T>& L, const T* c, const T* u, const T* v,
+                   double w_grad, double w_bulk, double w_pot, double* part, double* out1,
+                   cudaStream_t s) {
+  k_energy<T><<<grid2(L.m1, L.m2), dim3(BX, BY), 0, s>>>(P, L, c, u, v, w_grad, w_bulk, w_pot,
+                                                          part);
+  ++g_launches;
+  k_finalize<<<1, 256, 0, s>>>(part, nparts_cells(L), 1, 0, (double)L.h * (double)L.h, out1);
+  ++g_launches;
+}
+template <typename T>
+void launch_dissipation(const Prm<T>& P, const Lv<T>& L, double w_visc, double w_div,
+                        double w_ch, double* part, double* out1, cudaStream_t s) {
+  dim3 g = grid2(L.m1 + 1, L.m2 + 1);
+  k_dissipation<T><<<g, dim3(BX, BY), 0, s>>>(P, L, w_visc, w_div, w_ch, part);
+  ++g_launches;
+  k_finalize<<<1, 256, 0, s>>>(part, g.x * g.y, 1, 0, (double)L.h * (double)L.h, out1);
+  ++g_launches;
+}
+template <typename T>
+void launch_pack_in(const Lv<T>& L, T* dst, const double* src, int kind, cudaStream_t s) {
+  int nx = kind == 1 ? L.m1 + 1 : L.m1, ny = kind == 2 ? L.m2 + 1 : L.m2;
+  k_pack_in<T><<<grid2(nx, ny), dim3(BX, BY), 0, s>>>(L, dst, src, kind);
+  ++g_launches;
+}
+template <typename T>
+void launch_pack_out(const Lv<T>& L, double* dst, const T* src, int kind, cudaStream_t s) {
+  int nx = kind == 1 ? L.m1 + 1 : L.m1, ny = kind == 2 ? L.m2 + 1 : L.m2;
+  k_pack_out<T><<<grid2(nx, ny), dim3(BX, BY), 0, s>>>(L, dst, src, kind);
+  ++g_launches;
+}
+
+int partial_rows_needed(int m1, int m2) {
+  dim3 g = grid2(m1 + 1, m2 + 1);
+  return g.x * g.y;
+}
+
+#define QN_INSTANTIATE(T)                                                                        \
+  template void launch_residual<T>(const Prm<T>&, const Lv<T>&, double*, cudaStream_t);          \
+  template void launch_add_op<T>(const Prm<T>&, const Lv<T>&, cudaStream_t);                     \
+  template void launch_ch<T>(const Prm<T>&, const Lv<T>&, int, cudaStream_t);                    \
+  template void launch_vanka<T>(const Prm<T>&, const Lv<T>&, int, T, cudaStream_t);              \
+  template void launch_bc_unknowns<T>(const Lv<T>&, cudaStream_t);                               \
+  template void launch_frozen<T>(const Prm<T>&, const Lv<T>&, cudaStream_t);                     \
+  template void launch_restrict_state<T>(const Lv<T>&, const Lv<T>&, cudaStream_t);              \
+  template void launch_restrict_res<T>(const Lv<T>&, const Lv<T>&, cudaStream_t);                \
+  template void launch_restrict_frozen<T>(const Lv<T>&, const Lv<T>&, cudaStream_t);             \
+  template void launch_prolong<T>(const Lv<T>&, const Lv<T>&, cudaStream_t);                     \
+  template void launch_gauge<T>(const Lv<T>&, double*, double*, cudaStream_t);                   \
+  template void launch_norms_finalize<T>(const Lv<T>&, double*, double*, cudaStream_t);          \
+  template void launch_mass<T>(const Prm<T>&, const Lv<T>&, const T*, double*, double*,          \
+                               cudaStream_t);                                                    \
+  template void launch_energy<T>(const Prm<T>&, const Lv<T>&, const T*, const T*, const T*,      \
+                                 double, double, double, double*, double*, cudaStream_t);        \
+  template void launch_dissipation<T>(const Prm<T>&, const Lv<T>&, double, double, double,       \
+                                      double*, double*, cudaStream_t);                           \
+  template void launch_pack_in<T>(const Lv<T>&, T*, const double*, int, cudaStream_t);           \
+  template void launch_pack_out<T>(const Lv<T>&, double*, const T*, int, cudaStream_t);
+
+QN_INSTANTIATE(double)
+
+}  // namespace qn

@@ -1,0 +1,38 @@
+// kernels.h -- host-side launchers of the CUDA kernels in kernels.cu.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "qnsch_dev.cuh"
+
+namespace qn {
+
+template <typename T> void launch_residual(const Prm<T>& P, const Lv<T>& L, double* part, cudaStream_t s);
+template <typename T> void launch_add_op(const Prm<T>& P, const Lv<T>& L, cudaStream_t s);
+template <typename T> void launch_ch(const Prm<T>& P, const Lv<T>& L, int colour, cudaStream_t s);
+template <typename T> void launch_vanka(const Prm<T>& P, const Lv<T>& L, int colour, T omega, cudaStream_t s);
+template <typename T> void launch_bc_unknowns(const Lv<T>& L, cudaStream_t s);
+template <typename T> void launch_frozen(const Prm<T>& P, const Lv<T>& L, cudaStream_t s);
+template <typename T> void launch_restrict_state(const Lv<T>& F, const Lv<T>& C, cudaStream_t s);
+template <typename T> void launch_restrict_res(const Lv<T>& F, const Lv<T>& C, cudaStream_t s);
+template <typename T> void launch_restrict_frozen(const Lv<T>& F, const Lv<T>& C, cudaStream_t s);
+template <typename T> void launch_prolong(const Lv<T>& F, const Lv<T>& C, cudaStream_t s);
+template <typename T> void launch_gauge(const Lv<T>& L, double* part, double* scal, cudaStream_t s);
+template <typename T> void launch_norms_finalize(const Lv<T>& L, double* part, double* out10, cudaStream_t s);
+template <typename T>
+void launch_mass(const Prm<T>& P, const Lv<T>& L, const T* c, double* part, double* out2, cudaStream_t s);
+template <typename T>
+void launch_energy(const Prm<T>& P, const Lv<T>& L, const T* c, const T* u, const T* v, double w_grad,
+                   double w_bulk, double w_pot, double* part, double* out1, cudaStream_t s);
+template <typename T>
+void launch_dissipation(const Prm<T>& P, const Lv<T>& L, double w_visc, double w_div, double w_ch,
+                        double* part, double* out1, cudaStream_t s);
+template <typename T> void launch_pack_in(const Lv<T>& L, T* dst, const double* src, int kind, cudaStream_t s);
+template <typename T> void launch_pack_out(const Lv<T>& L, double* dst, const T* src, int kind, cudaStream_t s);
+
+// kernels issued by this library since it was loaded
+long long launches_issued();
+
+// rows of block partials any reduction on an m1 x m2 level may write
+int partial_rows_needed(int m1, int m2);
+
+}  // namespace qn

@@ -1,0 +1,256 @@
+// qnsch_dev.cuh -- device data structures and the discrete operator of the
+// primitive method (Guo, Lin, Lowengrub & Wise, arXiv:1703.06606, Sec. 6.1) on
+// the staggered grid of Sec. 5 / App. A, for sm_103a.
+//
+// Layout: every array of a level lives in one padded 2-D index space with one
+// ghost layer: entry (I, J), I = -1..m1+1, J = -1..m2+1, at origin[J*pitch + I];
+// pitch is a multiple of 32 elements so that rows start 256-byte aligned.
+//   cell (i,j)        -> (i, j)       i, j = 0..m1+1 / 0..m2+1 (with ghosts)
+//   u_{i+1/2, j}      -> (i, j)       i = -1..m1+1
+//   v_{i, j+1/2}      -> (i, j)       j = -1..m2+1
+// A thread working at cell (i,j) therefore reads cell, u and v arrays at the same
+// offset plus small constant displacements.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace qn {
+
+template <typename T>
+struct Prm {
+  T ia, ib;        // rho(c) = 1 / (ia c + ib): ia = alpha = (rho2-rho1)/(rho1 rho2), ib = 1/rho2
+  T va, vb;        // viscosity mu(c) = 1 / (va c + vb)
+  T alpha;         // (rho2 - rho1) / (rho1 rho2), Sec. 2.1
+  T K, Lam;        // M eta/(eps We) and eps eta M/We, coefficients of (pm-num-chem)
+  T iM, iRe, iPe;  // 1/M, 1/Re, 1/Pe
+  T Fr_inv;        // 1/Fr (0: no gravity)
+  T eps_m;         // mobility regularisation, m(c) = sqrt(c^2 (1-c)^2 + eps_m)
+  T idt;           // 1/dt
+};
+
+template <typename T>
+struct Lv {
+  int m1, m2, px, pitch;
+  T h, ih, ih2;
+  T *c, *mu, *p, *u, *v;       // iterate
+  T *fc, *fmu, *fp, *fu, *fv;  // FAS right-hand side
+  T *rc, *rmu, *rp, *ru, *rv;  // residual f - N(x)
+  T *sc, *smu, *sp, *su, *sv;  // restricted iterate kept for the correction
+  T *cn, *un, *vn;             // frozen level-n data
+  T *rhon, *mobn, *visn, *Gn;  // rho(c^n), m(c^n), mu(c^n), G(c^n)
+  __device__ __forceinline__ int at(int i, int j) const { return j * pitch + i; }
+  // x-edge unknowns: walls exclude i = 0 and i = m1; periodic keeps i = m1 (= edge 0)
+  __device__ __forceinline__ int uhi() const { return px ? m1 : m1 - 1; }
+};
+
+// ---------------------------------------------------------------------------
+// constitutive functions (Sec. 2.1) and secants (Sec. 4.1)
+// ---------------------------------------------------------------------------
+template <typename T> __device__ __forceinline__ T rho_of(const Prm<T>& P, T c) {
+  return T(1) / (P.ia * c + P.ib);
+}
+template <typename T> __device__ __forceinline__ T visc_of(const Prm<T>& P, T c) {
+  return T(1) / (P.va * c + P.vb);
+}
+template <typename T> __device__ __forceinline__ T mob_of(const Prm<T>& P, T c) {
+  T w = c * (T(1) - c);
+  return sqrt(w * w + P.eps_m);
+}
+template <typename T> __device__ __forceinline__ T Fdw(T c) {
+  T w = c * (c - T(1));
+  return T(0.25) * w * w;
+}
+template <typename T> __device__ __forceinline__ T fdw(T c) { return c * (c - T(1)) * (c - T(0.5)); }
+// g(a,b) with F(a) - F(b) = g(a,b) (a - b)
+template <typename T> __device__ __forceinline__ T gsec(T a, T b) {
+  return T(0.25) * (a * (a - T(1)) + b * (b - T(1))) * (a + b - T(1));
+}
+template <typename T> __device__ __forceinline__ T gsec_da(T a, T b) {
+  return T(0.25) * ((T(2) * a - T(1)) * (a + b - T(1)) + a * (a - T(1)) + b * (b - T(1)));
+}
+
+// ---------------------------------------------------------------------------
+// pieces of the discrete operator N(x) (Sec. 6.1)
+// ---------------------------------------------------------------------------
+
+// G(c) = a_x((D_x c)^2) + a_y((D_y c)^2) at cell k (times h^2)
+template <typename T>
+__device__ __forceinline__ T G_h2(const T* c, int k, int pitch) {
+  T cc = c[k];
+  T de = c[k + 1] - cc, dw = cc - c[k - 1], dn = c[k + pitch] - cc, ds = cc - c[k - pitch];
+  return T(0.5) * (de * de + dw * dw + dn * dn + ds * ds);
+}
+
+// h^2 grad_d.(A kap grad_D phi) at cell k
+template <typename T>
+__device__ __forceinline__ T lap_h2(const T* kap, const T* phi, int k, int pitch) {
+  T kc = kap[k], pc = phi[k];
+  return T(0.5) * ((kap[k + 1] + kc) * (phi[k + 1] - pc) - (kc + kap[k - 1]) * (pc - phi[k - 1]) +
+                   (kap[k + pitch] + kc) * (phi[k + pitch] - pc) -
+                   (kc + kap[k - pitch]) * (pc - phi[k - pitch]));
+}
+
+// (pm-num-phase) with the advection (e1e2) of App. A.4
+template <typename T>
+__device__ __forceinline__ T op_c(const Prm<T>& P, const Lv<T>& L, int k) {
+  const int W = L.pitch;
+  const T* cn = L.cn;
+  const T* rn = L.rhon;
+  T c = L.c[k], cnk = cn[k];
+  T adv = T(0.5) * L.ih *
+          (rn[k + 1] * (cn[k + 1] - cnk) * L.u[k] + rn[k - 1] * (cnk - cn[k - 1]) * L.u[k - 1] +
+           rn[k + W] * (cn[k + W] - cnk) * L.v[k] + rn[k - W] * (cnk - cn[k - W]) * L.v[k - W]);
+  T diff = lap_h2(L.mobn, L.mu, k, W) + P.alpha * lap_h2(L.mobn, L.p, k, W);
+  return rho_of(P, c) * (c - cnk) * P.idt + adv - P.iPe * L.ih2 * diff;
+}
+
+// (pm-num-chem) with the time-averaged gradient term (pointwise G)
+template <typename T>
+__device__ __forceinline__ T op_mu(const Prm<T>& P, const Lv<T>& L, int k) {
+  const int W = L.pitch;
+  const T* c = L.c;
+  const T* cn = L.cn;
+  const T* rn = L.rhon;
+  T ck = c[k], cnk = cn[k];
+  T rho = rho_of(P, ck), rnk = rn[k];
+  T rh = T(0.5) * (rho + rnk);
+  T r = -P.alpha * rho * rnk;
+  T bulk = rh * gsec(ck, cnk) + T(0.5) * (Fdw(ck) + Fdw(cnk)) * r;
+  T grad = T(0.25) * P.Lam * (G_h2(c, k, W) * L.ih2 + L.Gn[k]) * r;
+  // grad_d.(A rho^{n+1/2} grad_D c^{n+1/2})
+  T chk = ck + cnk;
+  T div = T(0);
+  const int off[4] = {1, -1, W, -W};
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    int q = k + off[f];
+    T rq = T(0.5) * (rho_of(P, c[q]) + rn[q]);
+    div += (rh + rq) * ((c[q] + cn[q]) - chk);
+  }
+  div *= T(0.25) * L.ih2;  // 1/2 (face average) * 1/2 (c^{n+1/2}) / h^2
+  return rho * L.mu[k] - P.K * bulk - grad + P.Lam * div;
+}
+
+// (pm-num-mass)
+template <typename T>
+__device__ __forceinline__ T op_p(const Prm<T>& P, const Lv<T>& L, int k) {
+  const int W = L.pitch;
+  T dv = (L.u[k] - L.u[k - 1] + L.v[k] - L.v[k - W]) * L.ih;
+  T diff = lap_h2(L.mobn, L.mu, k, W) + P.alpha * lap_h2(L.mobn, L.p, k, W);
+  return dv - P.alpha * P.iPe * L.ih2 * diff;
+}
+
+// x row of (pm-num-mx) at edge u_{i+1/2,j} (array index k = at(i,j)); cells k (left), k+1 (right),
+// vertices k (top, (i+1/2, j+1/2)) and k-W (bottom); (e1e1-1), (e1e1-2) and (e1e1)
+template <typename T>
+__device__ __forceinline__ T op_u(const Prm<T>& P, const Lv<T>& L, int k) {
+  const int W = L.pitch;
+  const T *u = L.u, *un = L.un, *vn = L.vn, *rn = L.rhon, *vis = L.visn;
+  T ue = u[k];
+  T rl = rn[k], rr = rn[k + 1];
+  T Arn = T(0.5) * (rl + rr);
+  T Ar = T(0.5) * (rho_of(P, L.c[k]) + rho_of(P, L.c[k + 1]));
+  T axl = T(0.5) * (un[k] + un[k - 1]), axr = T(0.5) * (un[k + 1] + un[k]);
+  T dxl = (ue - u[k - 1]) * L.ih, dxr = (u[k + 1] - ue) * L.ih;
+  T dvl = dxl + (L.v[k] - L.v[k - W]) * L.ih;
+  T dvr = dxr + (L.v[k + 1] - L.v[k + 1 - W]) * L.ih;
+  T Art = T(0.25) * (rl + rr + rn[k + W] + rn[k + 1 + W]);
+  T Arb = T(0.25) * (rl + rr + rn[k - W] + rn[k + 1 - W]);
+  T Avt = T(0.25) * (vis[k] + vis[k + 1] + vis[k + W] + vis[k + 1 + W]);
+  T Avb = T(0.25) * (vis[k] + vis[k + 1] + vis[k - W] + vis[k + 1 - W]);
+  T At = T(0.5) * (vn[k + 1] + vn[k]), Ab = T(0.5) * (vn[k + 1 - W] + vn[k - W]);
+  T Dt = (u[k + W] - ue) * L.ih, Db = (ue - u[k - W]) * L.ih;
+  T qt = Art * At, qb = Arb * Ab;   // vertex mass fluxes
+  T sr = rr * axr, sl = rl * axl;   // cell mass fluxes
+  T conv = T(0.5) * (sr * dxr + sl * dxl + qt * Dt + qb * Db);
+  T divc = T(0.5) * ((sr - sl) + (qt - qb)) * L.ih * ue;
+  T time = Arn * (ue - un[k]) * P.idt + T(0.5) * (Ar - Arn) * P.idt * ue;
+  T press = (L.p[k + 1] - L.p[k]) * L.ih * P.iM;
+  T st = -T(0.5) * (rr * L.mu[k] + rl * L.mu[k + 1]) * (L.cn[k + 1] - L.cn[k]) * L.ih * P.iM;
+  T vl = vis[k], vr = vis[k + 1];
+  T visc = -P.iRe * L.ih * ((vr * dxr - vl * dxl) + (Avt * Dt - Avb * Db) +
+                            (vr * dvr - vl * dvl) * T(1.0 / 3.0));
+  return time + conv + divc + press + st + visc;
+}
+
+// y row of (pm-num-mx) at edge v_{i,j+1/2} (index k = at(i,j)); cells k (bottom), k+W (top),
+// vertices k (east, (i+1/2, j+1/2)) and k-1 (west); plus gravity (1/Fr) A_y rho^n
+template <typename T>
+__device__ __forceinline__ T op_v(const Prm<T>& P, const Lv<T>& L, int k) {
+  const int W = L.pitch;
+  const T *v = L.v, *vn = L.vn, *un = L.un, *rn = L.rhon, *vis = L.visn;
+  T ve = v[k];
+  T rb = rn[k], rt = rn[k + W];
+  T Arn = T(0.5) * (rb + rt);
+  T Ar = T(0.5) * (rho_of(P, L.c[k]) + rho_of(P, L.c[k + W]));
+  T ayb = T(0.5) * (vn[k] + vn[k - W]), ayt = T(0.5) * (vn[k + W] + vn[k]);
+  T dyb = (ve - v[k - W]) * L.ih, dyt = (v[k + W] - ve) * L.ih;
+  T dvb = dyb + (L.u[k] - L.u[k - 1]) * L.ih;
+  T dvt = dyt + (L.u[k + W] - L.u[k + W - 1]) * L.ih;
+  T Are = T(0.25) * (rb + rt + rn[k + 1] + rn[k + 1 + W]);
+  T Arw = T(0.25) * (rb + rt + rn[k - 1] + rn[k - 1 + W]);
+  T Ave = T(0.25) * (vis[k] + vis[k + W] + vis[k + 1] + vis[k + 1 + W]);
+  T Avw = T(0.25) * (vis[k] + vis[k + W] + vis[k - 1] + vis[k - 1 + W]);
+  T Ae = T(0.5) * (un[k + W] + un[k]), Aw = T(0.5) * (un[k - 1 + W] + un[k - 1]);
+  T De = (v[k + 1] - ve) * L.ih, Dw = (ve - v[k - 1]) * L.ih;
+  T qe = Are * Ae, qw = Arw * Aw;
+  T st_ = rt * ayt, sb = rb * ayb;
+  T conv = T(0.5) * (qe * De + qw * Dw + st_ * dyt + sb * dyb);
+  T divc = T(0.5) * ((qe - qw) + (st_ - sb)) * L.ih * ve;
+  T time = Arn * (ve - vn[k]) * P.idt + T(0.5) * (Ar - Arn) * P.idt * ve;
+  T press = (L.p[k + W] - L.p[k]) * L.ih * P.iM;
+  T st = -T(0.5) * (rt * L.mu[k] + rb * L.mu[k + W]) * (L.cn[k + W] - L.cn[k]) * L.ih * P.iM;
+  T vb = vis[k], vt = vis[k + W];
+  T visc = -P.iRe * L.ih * ((Ave * De - Avw * Dw) + (vt * dyt - vb * dyb) +
+                            (vt * dvt - vb * dvb) * T(1.0 / 3.0));
+  return time + conv + divc + press + st + visc + P.Fr_inv * Arn;
+}
+
+// ---------------------------------------------------------------------------
+// stores that keep ghost copies consistent (App. A.6 boundary conditions)
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void store_cell(const Lv<T>& L, T* a, int i, int j, T x) {
+  const int W = L.pitch;
+  int k = j * W + i;
+  a[k] = x;
+  if (i == 1) a[k + (L.px ? L.m1 : -1)] = x;       // ghost (m1+1, j) or (0, j)
+  if (i == L.m1) a[k + (L.px ? -L.m1 : 1)] = x;    // ghost (0, j) or (m1+1, j)
+  if (j == 1) a[k - W] = x;
+  if (j == L.m2) a[k + W] = x;
+}
+
+template <typename T>
+__device__ __forceinline__ void store_u(const Lv<T>& L, int e, int j, T x) {
+  const int W = L.pitch;
+  T* u = L.u;
+  int cols[3] = {e, e, e};
+  int n = 1;
+  if (L.px) {
+    if (e == L.m1) cols[n++] = 0;
+    if (e == L.m1 - 1) cols[n++] = -1;
+    if (e == 1) cols[n++] = L.m1 + 1;
+  }
+  for (int q = 0; q < n; ++q) {
+    int k = j * W + cols[q];
+    u[k] = x;
+    if (j == 1) u[k - W] = -x;
+    if (j == L.m2) u[k + W] = -x;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void store_v(const Lv<T>& L, int i, int e, T x) {
+  const int W = L.pitch;
+  T* v = L.v;
+  int k = e * W + i;
+  v[k] = x;
+  if (L.px) {
+    if (i == L.m1) v[k - L.m1] = x;
+    if (i == 1) v[k + L.m1] = x;
+  } else {
+    if (i == 1) v[k - 1] = -x;
+    if (i == L.m1) v[k + 1] = -x;
+  }
+}
+
+}  // namespace qn

@@ -1,0 +1,750 @@
+// solver.cu -- host driver and C ABI (include/qnsch.h) of the GB300 q-NSCH solver:
+// level hierarchy in device memory, one implicit time step of the primitive
+// method (Sec. 6.1) solved by FAS V-cycles (Sec. 7.1), reductions for mass and
+// energy (Thms. 6.1, 6.2).  Every step of the numerical path runs in the CUDA
+// kernels of kernels.cu; this file only allocates, sequences and copies.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "qnsch.h"
+
+using qn::Lv;
+using qn::Prm;
+
+namespace {
+
+void* (*g_alloc)(size_t, void*) = nullptr;
+void (*g_free)(void*, void*) = nullptr;
+void* g_ctx = nullptr;
+
+void* dev_alloc(size_t bytes) {
+  if (g_alloc) return g_alloc(bytes, g_ctx);
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+void dev_free(void* p) {
+  if (!p) return;
+  if (g_free) g_free(p, g_ctx);
+  else cudaFree(p);
+}
+
+constexpr int NFIELD = 27;  // arrays per level (see Lv)
+
+// surface-tension ratio eta(rho1, rho2) of Sec. 8.1; near rho1 = rho2 the
+// formula is 0/0 and the Taylor series of x^2 - 1 - 2x ln x in q = x - 1 is used
+double eta_st(double r1, double r2) {
+  double q = r2 / r1 - 1.0;
+  if (std::fabs(q) < 0.1) {
+    double S = 0.0, qn = 1.0;
+    for (int n = 0; n < 24; ++n) {
+      S += 2.0 * ((n & 1) ? -1.0 : 1.0) * qn / ((n + 2.0) * (n + 3.0));
+      qn *= q;
+    }
+    return 1.0 / (2.0 * std::sqrt(2.0) * r1 * (1.0 + q) * S);
+  }
+  double d = r2 - r1;
+  return d * d * d /
+         (2.0 * std::sqrt(2.0) * r1 * r2 * (r2 * r2 - r1 * r1 - 2.0 * r1 * r2 * std::log(r2 / r1)));
+}
+
+int max_levels(int m1, int m2, int px) {
+  int n = 1;
+  int cmin = px ? 4 : 2;
+  while (m1 % 2 == 0 && m2 % 2 == 0 && m1 / 2 >= cmin && m2 / 2 >= cmin &&
+         (!px || (m1 / 2) % 4 == 0)) {
+    m1 /= 2;
+    m2 /= 2;
+    ++n;
+  }
+  return n;
+}
+
+}  // namespace
+
+struct qnsch_s {
+  // physical parameters as given
+  double rho1, rho2, mu1, mu2, Re, We, Pe, Cn, Fr_inv;
+  double M, eta, eps_m;
+  // options
+  int nu1 = 2, nu2 = 2, nuc = 20, maxcyc = 50;
+  double tol = 1e-9, omega = 1.0;
+  // grid
+  int m1, m2, px, nlev, kcol;
+  double h;
+  std::vector<Lv<double>> L;
+  std::vector<void*> blocks;
+  size_t level_elems0 = 0;
+  // committed state, same padded layout as level 0
+  double *sc = nullptr, *smu = nullptr, *sp = nullptr, *su = nullptr, *sv = nullptr;
+  // scratch: block partials and small results
+  double* part = nullptr;
+  double* scal = nullptr;  // [0..9] norms, [16] p sum, [20..21] mass, [24] energy, [25] diss
+  double* hbuf = nullptr;  // pinned host mirror of scal
+  double* stage = nullptr;  // device staging buffer for host-array I/O (one field)
+  cudaStream_t stream = nullptr;
+  int pending = 0;
+  // optional CUDA-event timing of the finest-level Vanka launches
+  int prof = 0;
+  std::vector<cudaEvent_t> ev;
+  int ev_used = 0;
+  long long prof_launches = 0;
+  double prof_ms = 0.0;
+  double dt = 0.0;
+  double last_diss = 0.0;
+};
+
+namespace {
+
+Prm<double> make_prm(const qnsch_s* s) {
+  Prm<double> P;
+  double alpha = (s->rho2 - s->rho1) / (s->rho1 * s->rho2);
+  P.ia = alpha;
+  P.ib = 1.0 / s->rho2;
+  P.va = (s->mu2 - s->mu1) / (s->mu1 * s->mu2);
+  P.vb = 1.0 / s->mu2;
+  P.alpha = alpha;
+  P.K = s->M * s->eta / (s->Cn * s->We);
+  P.Lam = s->Cn * s->eta * s->M / s->We;
+  P.iM = 1.0 / s->M;
+  P.iRe = 1.0 / s->Re;
+  P.iPe = 1.0 / s->Pe;
+  P.Fr_inv = s->Fr_inv;
+  P.eps_m = s->eps_m;
+  P.idt = s->dt > 0 ? 1.0 / s->dt : 0.0;
+  return P;
+}
+
+int cuda_status() {
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? QNSCH_OK : QNSCH_ECUDA;
+}
+
+int sync(const qnsch_s* s) {
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return QNSCH_ECUDA;
+  }
+  return cuda_status();
+}
+
+size_t padded_elems(int m1, int m2, int* pitch) {
+  int p = ((m1 + 3) + 31) / 32 * 32;
+  *pitch = p;
+  return (size_t)p * (size_t)(m2 + 3);
+}
+
+void free_all(qnsch_s* s) {
+  for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
+  s->ev.clear();
+  for (void* b : s->blocks) dev_free(b);
+  s->blocks.clear();
+  if (s->hbuf) cudaFreeHost(s->hbuf);
+  s->hbuf = nullptr;
+}
+
+int alloc_all(qnsch_s* s) {
+  int a = s->m1, b = s->m2;
+  double h = s->h;
+  s->L.resize(s->nlev);
+  for (int l = 0; l < s->nlev; ++l) {
+    Lv<double>& L = s->L[l];
+    int pitch;
+    size_t n = padded_elems(a, b, &pitch);
+    if (l == 0) s->level_elems0 = n;
+    double* base = (double*)dev_alloc(n * NFIELD * sizeof(double));
+    if (!base) return QNSCH_ENOMEM;
+    s->blocks.push_back(base);
+    if (cudaMemsetAsync(base, 0, n * NFIELD * sizeof(double), s->stream) != cudaSuccess)
+      return QNSCH_ECUDA;
+    L.m1 = a;
+    L.m2 = b;
+    L.px = s->px;
+    L.pitch = pitch;
+    L.h = h;
+    L.ih = 1.0 / h;
+    L.ih2 = 1.0 / (h * h);
+    double** f[NFIELD] = {&L.c,  &L.mu, &L.p,  &L.u,  &L.v,  &L.fc, &L.fmu, &L.fp,  &L.fu,
+                          &L.fv, &L.rc, &L.rmu, &L.rp, &L.ru, &L.rv, &L.sc,  &L.smu, &L.sp,
+                          &L.su, &L.sv, &L.cn, &L.un, &L.vn, &L.rhon, &L.mobn, &L.visn, &L.Gn};
+    for (int q = 0; q < NFIELD; ++q) *f[q] = base + (size_t)q * n + pitch + 1;  // origin (0,0)
+    a /= 2;
+    b /= 2;
+    h *= 2.0;
+  }
+  size_t n0 = s->level_elems0;
+  double* st = (double*)dev_alloc(n0 * 5 * sizeof(double));
+  if (!st) return QNSCH_ENOMEM;
+  s->blocks.push_back(st);
+  cudaMemsetAsync(st, 0, n0 * 5 * sizeof(double), s->stream);
+  int pitch0 = s->L[0].pitch;
+  s->sc = st + 0 * n0 + pitch0 + 1;
+  s->smu = st + 1 * n0 + pitch0 + 1;
+  s->sp = st + 2 * n0 + pitch0 + 1;
+  s->su = st + 3 * n0 + pitch0 + 1;
+  s->sv = st + 4 * n0 + pitch0 + 1;
+  int rows = qn::partial_rows_needed(s->m1, s->m2);
+  s->part = (double*)dev_alloc((size_t)rows * 10 * sizeof(double));
+  if (!s->part) return QNSCH_ENOMEM;
+  s->blocks.push_back(s->part);
+  size_t nstage = (size_t)(s->m1 + 1) * (s->m2 + 1);
+  s->stage = (double*)dev_alloc(nstage * sizeof(double));
+  if (!s->stage) return QNSCH_ENOMEM;
+  s->blocks.push_back(s->stage);
+  s->scal = (double*)dev_alloc(32 * sizeof(double));
+  if (!s->scal) return QNSCH_ENOMEM;
+  s->blocks.push_back(s->scal);
+  if (cudaMallocHost(&s->hbuf, 32 * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return QNSCH_ENOMEM;
+  }
+  return sync(s);
+}
+
+// a level view whose iterate arrays are the committed state (for packing/energy)
+Lv<double> state_view(const qnsch_s* s) {
+  Lv<double> V = s->L[0];
+  V.c = s->sc;
+  V.mu = s->smu;
+  V.p = s->sp;
+  V.u = s->su;
+  V.v = s->sv;
+  return V;
+}
+
+constexpr int MAX_PROF_EVENTS = 8192;
+
+void smooth(qnsch_s* s, const Prm<double>& P, int l) {
+  const Lv<double>& L = s->L[l];
+  qn::launch_ch(P, L, 0, s->stream);
+  qn::launch_ch(P, L, 1, s->stream);
+  for (int c = 0; c < s->kcol; ++c) {
+    bool rec = s->prof && l == 0 && s->ev_used + 2 <= MAX_PROF_EVENTS;
+    if (rec) {
+      while ((int)s->ev.size() < s->ev_used + 2) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) { rec = false; break; }
+        s->ev.push_back(e);
+      }
+    }
+    if (rec) cudaEventRecord(s->ev[s->ev_used], s->stream);
+    qn::launch_vanka(P, L, c, s->omega, s->stream);
+    if (rec) {
+      cudaEventRecord(s->ev[s->ev_used + 1], s->stream);
+      s->ev_used += 2;
+    }
+  }
+}
+
+// fold the recorded event pairs into the totals (stream must be idle)
+void prof_collect(qnsch_s* s) {
+  for (int q = 0; q + 1 < s->ev_used; q += 2) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, s->ev[q], s->ev[q + 1]) == cudaSuccess) {
+      s->prof_ms += ms;
+      s->prof_launches += 1;
+    }
+  }
+  cudaGetLastError();
+  s->ev_used = 0;
+}
+
+void vcycle(qnsch_s* s, const Prm<double>& P, int l) {
+  if (l == s->nlev - 1) {
+    for (int k = 0; k < s->nuc; ++k) smooth(s, P, l);
+    return;
+  }
+  for (int k = 0; k < s->nu1; ++k) smooth(s, P, l);
+  const Lv<double>& F = s->L[l];
+  const Lv<double>& C = s->L[l + 1];
+  qn::launch_residual(P, F, (double*)nullptr, s->stream);
+  qn::launch_restrict_state(F, C, s->stream);
+  qn::launch_bc_unknowns(C, s->stream);
+  qn::launch_restrict_res(F, C, s->stream);
+  qn::launch_add_op(P, C, s->stream);
+  vcycle(s, P, l + 1);
+  qn::launch_prolong(F, C, s->stream);
+  qn::launch_bc_unknowns(F, s->stream);
+  for (int k = 0; k < s->nu2; ++k) smooth(s, P, l);
+}
+
+// finest residual + norms; result left in s->hbuf[0..9] as [l2 x5, max x5]
+int residual_norms(qnsch_s* s, const Prm<double>& P, double* norms10) {
+  const Lv<double>& F = s->L[0];
+  qn::launch_residual(P, F, s->part, s->stream);
+  qn::launch_norms_finalize(F, s->part, s->scal, s->stream);
+  cudaMemcpyAsync(s->hbuf, s->scal, 10 * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+  int rc = sync(s);
+  if (rc) return rc;
+  for (int q = 0; q < 5; ++q) {
+    norms10[q] = std::sqrt(s->hbuf[5 + q]);
+    norms10[5 + q] = s->hbuf[q];
+  }
+  return QNSCH_OK;
+}
+
+double maxfam(const double* n10) {
+  double m = 0.0;
+  for (int q = 0; q < 5; ++q) {
+    if (!(n10[q] == n10[q])) return NAN;
+    m = n10[q] > m ? n10[q] : m;
+  }
+  return m;
+}
+
+int copy_fields_in(qnsch_s* s, double* const dst[5], const double* const src[5], bool host) {
+  Lv<double> V = s->L[0];
+  const int kinds[5] = {0, 0, 1, 2, 0};  // c, mu, u, v, p
+  size_t nel[3] = {(size_t)s->m1 * s->m2, (size_t)(s->m1 + 1) * s->m2,
+                   (size_t)s->m1 * (s->m2 + 1)};
+  double* tmp = host ? s->stage : nullptr;
+  for (int q = 0; q < 5; ++q) {
+    const double* sp = src[q];
+    if (host) {
+      if (cudaMemcpyAsync(tmp, src[q], nel[kinds[q]] * sizeof(double), cudaMemcpyHostToDevice,
+                          s->stream) != cudaSuccess)
+        return QNSCH_ECUDA;
+      sp = tmp;
+    }
+    qn::launch_pack_in(V, dst[q], sp, kinds[q], s->stream);
+    if (host) {
+      int rc = sync(s);  // the staging buffer is reused by the next field
+      if (rc) return rc;
+    }
+  }
+  Lv<double> W = V;
+  W.c = dst[0];
+  W.mu = dst[1];
+  W.u = dst[2];
+  W.v = dst[3];
+  W.p = dst[4];
+  qn::launch_bc_unknowns(W, s->stream);
+  return sync(s);
+}
+
+int copy_fields_out(const qnsch_s* s, double* const src[5], double* const dst[5], bool host) {
+  const Lv<double>& V = s->L[0];
+  const int kinds[5] = {0, 0, 1, 2, 0};
+  size_t nel[3] = {(size_t)s->m1 * s->m2, (size_t)(s->m1 + 1) * s->m2,
+                   (size_t)s->m1 * (s->m2 + 1)};
+  double* tmp = host ? s->stage : nullptr;
+  for (int q = 0; q < 5; ++q) {
+    if (!dst[q]) continue;
+    double* dp = host ? tmp : dst[q];
+    qn::launch_pack_out(V, dp, src[q], kinds[q], s->stream);
+    if (host) {
+      cudaMemcpyAsync(dst[q], tmp, nel[kinds[q]] * sizeof(double), cudaMemcpyDeviceToHost,
+                      s->stream);
+      int rc = sync(s);
+      if (rc) return rc;
+    }
+  }
+  return sync(s);
+}
+
+int begin(qnsch_s* s, double dt) {
+  s->dt = dt;
+  Prm<double> P = make_prm(s);
+  Lv<double>& F = s->L[0];
+  size_t bytes = s->level_elems0 * sizeof(double);
+  double* src[5] = {s->sc, s->smu, s->sp, s->su, s->sv};
+  double* dst[5] = {F.c, F.mu, F.p, F.u, F.v};
+  int pitch = F.pitch;
+  for (int q = 0; q < 5; ++q)
+    cudaMemcpyAsync(dst[q] - pitch - 1, src[q] - pitch - 1, bytes, cudaMemcpyDeviceToDevice,
+                    s->stream);
+  cudaMemcpyAsync(F.cn - pitch - 1, s->sc - pitch - 1, bytes, cudaMemcpyDeviceToDevice, s->stream);
+  cudaMemcpyAsync(F.un - pitch - 1, s->su - pitch - 1, bytes, cudaMemcpyDeviceToDevice, s->stream);
+  cudaMemcpyAsync(F.vn - pitch - 1, s->sv - pitch - 1, bytes, cudaMemcpyDeviceToDevice, s->stream);
+  qn::launch_frozen(P, F, s->stream);
+  for (int l = 1; l < s->nlev; ++l) {
+    qn::launch_restrict_frozen(s->L[l - 1], s->L[l], s->stream);
+    qn::launch_frozen(P, s->L[l], s->stream);
+  }
+  s->pending = 1;
+  return cuda_status();
+}
+
+int one_cycle(qnsch_s* s, double* norms10) {
+  Prm<double> P = make_prm(s);
+  vcycle(s, P, 0);
+  qn::launch_gauge(s->L[0], s->part, s->scal + 16, s->stream);
+  int rc = residual_norms(s, P, norms10);
+  if (s->prof) prof_collect(s);
+  return rc;
+}
+
+int commit(qnsch_s* s) {
+  Prm<double> P = make_prm(s);
+  const Lv<double>& F = s->L[0];
+  // dissipation of this step (Thm. 6.2), then accept the iterate
+  double w_visc = s->dt / s->Re, w_div = s->dt / (3.0 * s->Re), w_ch = s->dt / (s->M * s->Pe);
+  qn::launch_dissipation(P, F, w_visc, w_div, w_ch, s->part, s->scal + 25, s->stream);
+  size_t bytes = s->level_elems0 * sizeof(double);
+  int pitch = F.pitch;
+  double* src[5] = {F.c, F.mu, F.p, F.u, F.v};
+  double* dst[5] = {s->sc, s->smu, s->sp, s->su, s->sv};
+  for (int q = 0; q < 5; ++q)
+    cudaMemcpyAsync(dst[q] - pitch - 1, src[q] - pitch - 1, bytes, cudaMemcpyDeviceToDevice,
+                    s->stream);
+  cudaMemcpyAsync(s->hbuf + 25, s->scal + 25, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+  int rc = sync(s);
+  if (rc) return rc;
+  s->last_diss = s->hbuf[25];
+  s->pending = 0;
+  return QNSCH_OK;
+}
+
+}  // namespace
+
+// ============================================================================
+// C ABI
+// ============================================================================
+extern "C" {
+
+int qnsch_set_allocator(void* (*alloc)(size_t, void*), void (*free_fn)(void*, void*), void* ctx) {
+  if ((alloc == nullptr) != (free_fn == nullptr)) return QNSCH_EINVAL;
+  g_alloc = alloc;
+  g_free = free_fn;
+  g_ctx = ctx;
+  return QNSCH_OK;
+}
+
+int qnsch_create(const qnsch_grid* grid, double rho1, double rho2, double eta1, double eta2,
+                 double Re, double We, double Pe, double Cn, double Fr, qnsch_t** out) {
+  if (!grid || !out) return QNSCH_EINVAL;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return QNSCH_ENODEV;
+  }
+  if (grid->m1 < 2 || grid->m2 < 2 || !(grid->Lx > 0) || grid->periodic_y) return QNSCH_EINVAL;
+  if (grid->periodic_x && grid->m1 % 4 != 0) return QNSCH_EINVAL;
+  if (!(rho1 > 0) || !(rho2 > 0) || !(eta1 > 0) || !(eta2 > 0) || !(Re > 0) || !(We > 0) ||
+      !(Pe > 0) || !(Cn > 0))
+    return QNSCH_EINVAL;
+  int lmax = max_levels(grid->m1, grid->m2, grid->periodic_x);
+  int lev = grid->levels <= 0 ? lmax : grid->levels;
+  if (lev > lmax) return QNSCH_EINVAL;
+  qnsch_s* s = new (std::nothrow) qnsch_s();
+  if (!s) return QNSCH_ENOMEM;
+  s->rho1 = rho1;
+  s->rho2 = rho2;
+  s->mu1 = eta1;
+  s->mu2 = eta2;
+  s->Re = Re;
+  s->We = We;
+  s->Pe = Pe;
+  s->Cn = Cn;
+  s->Fr_inv = (std::isinf(Fr) || Fr <= 0) ? 0.0 : 1.0 / Fr;
+  s->M = Cn;
+  s->eps_m = Cn;
+  s->eta = eta_st(rho1, rho2);
+  s->m1 = grid->m1;
+  s->m2 = grid->m2;
+  s->px = grid->periodic_x ? 1 : 0;
+  s->kcol = s->px ? 8 : 5;
+  s->nlev = lev;
+  s->h = grid->Lx / grid->m1;
+  int rc = alloc_all(s);
+  if (rc) {
+    free_all(s);
+    delete s;
+    return rc;
+  }
+  *out = s;
+  return QNSCH_OK;
+}
+
+int qnsch_destroy(qnsch_t* s) {
+  if (!s) return QNSCH_EINVAL;
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  else cudaDeviceSynchronize();
+  free_all(s);
+  delete s;
+  return QNSCH_OK;
+}
+
+int qnsch_set_option(qnsch_t* s, const char* key, double value) {
+  if (!s || !key) return QNSCH_EINVAL;
+  std::string k(key);
+  if (k == "nu1") s->nu1 = (int)value;
+  else if (k == "nu2") s->nu2 = (int)value;
+  else if (k == "nu_coarse") s->nuc = (int)value;
+  else if (k == "maxcyc") s->maxcyc = (int)value;
+  else if (k == "tol") s->tol = value;
+  else if (k == "omega_vanka") s->omega = value;
+  else if (k == "M") s->M = value;
+  else if (k == "eta_st") s->eta = value;
+  else if (k == "eps_mob") s->eps_m = value;
+  else return QNSCH_EINVAL;
+  return QNSCH_OK;
+}
+
+int qnsch_get_option(const qnsch_t* s, const char* key, double* value) {
+  if (!s || !key || !value) return QNSCH_EINVAL;
+  std::string k(key);
+  if (k == "nu1") *value = s->nu1;
+  else if (k == "nu2") *value = s->nu2;
+  else if (k == "nu_coarse") *value = s->nuc;
+  else if (k == "maxcyc") *value = s->maxcyc;
+  else if (k == "tol") *value = s->tol;
+  else if (k == "omega_vanka") *value = s->omega;
+  else if (k == "M") *value = s->M;
+  else if (k == "eta_st") *value = s->eta;
+  else if (k == "eps_mob") *value = s->eps_m;
+  else return QNSCH_EINVAL;
+  return QNSCH_OK;
+}
+
+int qnsch_set_stream(qnsch_t* s, void* stream) {
+  if (!s) return QNSCH_EINVAL;
+  s->stream = (cudaStream_t)stream;
+  return QNSCH_OK;
+}
+
+int qnsch_profile(qnsch_t* s, int enable) {
+  if (!s) return QNSCH_EINVAL;
+  if (s->ev_used) {
+    cudaStreamSynchronize(s->stream);
+    prof_collect(s);
+  }
+  s->prof = enable ? 1 : 0;
+  s->prof_launches = 0;
+  s->prof_ms = 0.0;
+  return QNSCH_OK;
+}
+
+int qnsch_profile_read(qnsch_t* s, long long* launches, double* total_ms) {
+  if (!s || !launches || !total_ms) return QNSCH_EINVAL;
+  if (s->ev_used) {
+    int rc = sync(s);
+    if (rc) return rc;
+    prof_collect(s);
+  }
+  *launches = s->prof_launches;
+  *total_ms = s->prof_ms;
+  return QNSCH_OK;
+}
+
+int qnsch_kernel_launches(long long* n) {
+  if (!n) return QNSCH_EINVAL;
+  *n = qn::launches_issued();
+  return QNSCH_OK;
+}
+
+int qnsch_levels(const qnsch_t* s) { return s ? s->nlev : QNSCH_EINVAL; }
+int qnsch_ncolours_vanka(const qnsch_t* s) { return s ? s->kcol : QNSCH_EINVAL; }
+
+int qnsch_set_fields(qnsch_t* s, const double* c, const double* mu, const double* u,
+                     const double* v, const double* p) {
+  if (!s || !c || !mu || !u || !v || !p) return QNSCH_EINVAL;
+  if (s->pending) return QNSCH_ESTATE;
+  double* dst[5] = {s->sc, s->smu, s->su, s->sv, s->sp};
+  const double* src[5] = {c, mu, u, v, p};
+  return copy_fields_in(s, dst, src, true);
+}
+
+int qnsch_set_fields_device(qnsch_t* s, const double* c, const double* mu, const double* u,
+                            const double* v, const double* p) {
+  if (!s || !c || !mu || !u || !v || !p) return QNSCH_EINVAL;
+  if (s->pending) return QNSCH_ESTATE;
+  double* dst[5] = {s->sc, s->smu, s->su, s->sv, s->sp};
+  const double* src[5] = {c, mu, u, v, p};
+  return copy_fields_in(s, dst, src, false);
+}
+
+int qnsch_get_fields(const qnsch_t* s, double* c, double* mu, double* u, double* v, double* p) {
+  if (!s) return QNSCH_EINVAL;
+  double* src[5] = {s->sc, s->smu, s->su, s->sv, s->sp};
+  double* dst[5] = {c, mu, u, v, p};
+  return copy_fields_out(s, src, dst, true);
+}
+
+int qnsch_get_fields_device(const qnsch_t* s, double* c, double* mu, double* u, double* v,
+                            double* p) {
+  if (!s) return QNSCH_EINVAL;
+  double* src[5] = {s->sc, s->smu, s->su, s->sv, s->sp};
+  double* dst[5] = {c, mu, u, v, p};
+  return copy_fields_out(s, src, dst, false);
+}
+
+int qnsch_begin_step(qnsch_t* s, double dt) {
+  if (!s || !(dt > 0)) return QNSCH_EINVAL;
+  int rc = begin(s, dt);
+  if (rc) return rc;
+  return sync(s);
+}
+
+int qnsch_vcycle(qnsch_t* s, double* norms10) {
+  if (!s) return QNSCH_EINVAL;
+  if (!s->pending) return QNSCH_ESTATE;
+  double n[10];
+  int rc = one_cycle(s, n);
+  if (rc) return rc;
+  if (norms10) std::memcpy(norms10, n, sizeof(n));
+  return QNSCH_OK;
+}
+
+int qnsch_commit_step(qnsch_t* s) {
+  if (!s) return QNSCH_EINVAL;
+  if (!s->pending) return QNSCH_ESTATE;
+  return commit(s);
+}
+
+int qnsch_step(qnsch_t* s, double dt, int* n_vcycles, double* final_residual) {
+  if (!s || !(dt > 0)) return QNSCH_EINVAL;
+  if (s->pending) return QNSCH_ESTATE;
+  int rc = begin(s, dt);
+  if (rc) return rc;
+  Prm<double> P = make_prm(s);
+  double n[10];
+  rc = residual_norms(s, P, n);
+  if (rc) return rc;
+  int k = 0;
+  double r = maxfam(n);
+  while (r == r && r > s->tol && k < s->maxcyc) {
+    rc = one_cycle(s, n);
+    if (rc) return rc;
+    r = maxfam(n);
+    ++k;
+  }
+  if (n_vcycles) *n_vcycles = k;
+  if (final_residual) *final_residual = r;
+  if (!(r == r)) {
+    s->pending = 0;
+    return QNSCH_ENAN;
+  }
+  if (r > s->tol) {
+    s->pending = 0;
+    return QNSCH_ENOTCONV;
+  }
+  return commit(s);
+}
+
+int qnsch_mass(const qnsch_t* s, double* mass_rho, double* mass_rhoc) {
+  if (!s || !mass_rho || !mass_rhoc) return QNSCH_EINVAL;
+  qnsch_s* m = const_cast<qnsch_s*>(s);
+  Prm<double> P = make_prm(s);
+  qn::launch_mass(P, s->L[0], (const double*)s->sc, s->part, s->scal + 20, s->stream);
+  cudaMemcpyAsync(m->hbuf + 20, s->scal + 20, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                  s->stream);
+  int rc = sync(s);
+  if (rc) return rc;
+  *mass_rho = m->hbuf[20];
+  *mass_rhoc = m->hbuf[21];
+  return QNSCH_OK;
+}
+
+static int energy_of(const qnsch_s* s, const double* c, const double* u, const double* v,
+                     double* E) {
+  qnsch_s* m = const_cast<qnsch_s*>(s);
+  Prm<double> P = make_prm(s);
+  double w_grad = s->Cn * s->eta / s->We;          // (eps eta / (2 We)) / (1/2)
+  double w_bulk = s->eta / (s->Cn * s->We);
+  double w_pot = s->Fr_inv;
+  // k_energy sums rho [ (a_x u^2 + a_y v^2)/2 + w_grad G / 2 + w_bulk F + w_pot y ]:
+  qn::launch_energy(P, s->L[0], c, u, v, 0.5 * w_grad, w_bulk, w_pot, s->part, s->scal + 24,
+                    s->stream);
+  cudaMemcpyAsync(m->hbuf + 24, s->scal + 24, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+  int rc = sync(s);
+  if (rc) return rc;
+  *E = m->hbuf[24];
+  return QNSCH_OK;
+}
+
+int qnsch_energy(const qnsch_t* s, double* E, double* last_dissipation) {
+  if (!s || !E) return QNSCH_EINVAL;
+  int rc = energy_of(s, s->sc, s->su, s->sv, E);
+  if (rc) return rc;
+  if (last_dissipation) *last_dissipation = s->last_diss;
+  return QNSCH_OK;
+}
+
+int qnsch_iterate_energy(const qnsch_t* s, double* E, double* D) {
+  if (!s || !E) return QNSCH_EINVAL;
+  if (!s->pending) return QNSCH_ESTATE;
+  const Lv<double>& F = s->L[0];
+  int rc = energy_of(s, F.c, F.u, F.v, E);
+  if (rc) return rc;
+  if (D) {
+    qnsch_s* m = const_cast<qnsch_s*>(s);
+    Prm<double> P = make_prm(s);
+    double w_visc = s->dt / s->Re, w_div = s->dt / (3.0 * s->Re), w_ch = s->dt / (s->M * s->Pe);
+    qn::launch_dissipation(P, F, w_visc, w_div, w_ch, s->part, s->scal + 25, s->stream);
+    cudaMemcpyAsync(m->hbuf + 25, s->scal + 25, sizeof(double), cudaMemcpyDeviceToHost,
+                    s->stream);
+    rc = sync(s);
+    if (rc) return rc;
+    *D = m->hbuf[25];
+  }
+  return QNSCH_OK;
+}
+
+int qnsch_set_iterate(qnsch_t* s, const double* c, const double* mu, const double* u,
+                      const double* v, const double* p) {
+  if (!s || !c || !mu || !u || !v || !p) return QNSCH_EINVAL;
+  if (!s->pending) return QNSCH_ESTATE;
+  const Lv<double>& F = s->L[0];
+  double* dst[5] = {F.c, F.mu, F.u, F.v, F.p};
+  const double* src[5] = {c, mu, u, v, p};
+  return copy_fields_in(s, dst, src, true);
+}
+
+int qnsch_get_iterate(const qnsch_t* s, double* c, double* mu, double* u, double* v, double* p) {
+  if (!s) return QNSCH_EINVAL;
+  if (!s->pending) return QNSCH_ESTATE;
+  const Lv<double>& F = s->L[0];
+  double* src[5] = {F.c, F.mu, F.u, F.v, F.p};
+  double* dst[5] = {c, mu, u, v, p};
+  return copy_fields_out(s, src, dst, true);
+}
+
+int qnsch_residual(qnsch_t* s, double* rc_, double* rmu, double* rp, double* ru, double* rv,
+                   double* norms10) {
+  if (!s) return QNSCH_EINVAL;
+  if (!s->pending) return QNSCH_ESTATE;
+  Prm<double> P = make_prm(s);
+  double n[10];
+  int rc = residual_norms(s, P, n);
+  if (rc) return rc;
+  if (norms10) std::memcpy(norms10, n, sizeof(n));
+  const Lv<double>& F = s->L[0];
+  double* src[5] = {F.rc, F.rmu, F.ru, F.rv, F.rp};
+  double* dst[5] = {rc_, rmu, ru, rv, rp};
+  return copy_fields_out(s, src, dst, true);
+}
+
+int qnsch_smooth_ch(qnsch_t* s, int colour) {
+  if (!s || colour < 0 || colour > 1) return QNSCH_EINVAL;
+  if (!s->pending) return QNSCH_ESTATE;
+  qn::launch_ch(make_prm(s), s->L[0], colour, s->stream);
+  return sync(s);
+}
+
+int qnsch_smooth_vanka(qnsch_t* s, int colour) {
+  if (!s || colour < 0 || colour >= s->kcol) return QNSCH_EINVAL;
+  if (!s->pending) return QNSCH_ESTATE;
+  qn::launch_vanka(make_prm(s), s->L[0], colour, s->omega, s->stream);
+  return sync(s);
+}
+
+int qnsch_smooth(qnsch_t* s, int sweeps) {
+  if (!s || sweeps < 0) return QNSCH_EINVAL;
+  if (!s->pending) return QNSCH_ESTATE;
+  Prm<double> P = make_prm(s);
+  for (int k = 0; k < sweeps; ++k) smooth(s, P, 0);
+  return sync(s);
+}
+
+}  // extern "C"

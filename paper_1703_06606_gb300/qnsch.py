@@ -1,0 +1,264 @@
+"""Thin ctypes binding of libqnsch.so (include/qnsch.h): argument marshalling only.
+
+Every numerical step runs in the CUDA kernels of the library.  There is no CPU
+fallback: if the library cannot be loaded, or no GPU is present, calls raise.
+
+Array layouts (numpy / torch, C order, float64, no ghost cells):
+    c, mu, p : (m2, m1); u : (m2, m1 + 1); v : (m2 + 1, m1)
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_D = ctypes.POINTER(ctypes.c_double)
+_VP = ctypes.c_void_p
+
+STATUS = {0: "OK", -1: "EINVAL", -2: "ENODEV", -3: "ENOMEM", -4: "ENOTCONV", -5: "ENAN",
+          -8: "ESTATE", -9: "ECUDA"}
+
+
+class QnschError(RuntimeError):
+    def __init__(self, what, code):
+        super().__init__("%s failed: QNSCH_%s (%d)" % (what, STATUS.get(code, "?"), code))
+        self.code = code
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("m1", ctypes.c_int), ("m2", ctypes.c_int), ("Lx", ctypes.c_double),
+                ("periodic_x", ctypes.c_int), ("periodic_y", ctypes.c_int),
+                ("levels", ctypes.c_int)]
+
+
+_lib = None
+
+
+def lib():
+    """Load (building first if stale) the in-tree libqnsch.so."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path) or _build.is_stale():
+            path = _build.build()
+        L = ctypes.CDLL(path)
+        i, d, p = ctypes.c_int, ctypes.c_double, _D
+        L.qnsch_create.argtypes = [ctypes.POINTER(_Grid), d, d, d, d, d, d, d, d, d,
+                                   ctypes.POINTER(_VP)]
+        L.qnsch_destroy.argtypes = [_VP]
+        L.qnsch_set_option.argtypes = [_VP, ctypes.c_char_p, d]
+        L.qnsch_get_option.argtypes = [_VP, ctypes.c_char_p, p]
+        L.qnsch_set_stream.argtypes = [_VP, _VP]
+        L.qnsch_levels.argtypes = [_VP]
+        L.qnsch_ncolours_vanka.argtypes = [_VP]
+        for name in ("set_fields", "get_fields", "set_fields_device", "get_fields_device",
+                     "set_iterate", "get_iterate"):
+            getattr(L, "qnsch_" + name).argtypes = [_VP, _VP, _VP, _VP, _VP, _VP]
+        L.qnsch_step.argtypes = [_VP, d, ctypes.POINTER(i), p]
+        L.qnsch_begin_step.argtypes = [_VP, d]
+        L.qnsch_vcycle.argtypes = [_VP, p]
+        L.qnsch_commit_step.argtypes = [_VP]
+        L.qnsch_mass.argtypes = [_VP, p, p]
+        L.qnsch_energy.argtypes = [_VP, p, p]
+        L.qnsch_iterate_energy.argtypes = [_VP, p, p]
+        L.qnsch_residual.argtypes = [_VP, _VP, _VP, _VP, _VP, _VP, p]
+        L.qnsch_smooth_ch.argtypes = [_VP, i]
+        L.qnsch_smooth_vanka.argtypes = [_VP, i]
+        L.qnsch_smooth.argtypes = [_VP, i]
+        L.qnsch_set_allocator.argtypes = [_VP, _VP, _VP]
+        L.qnsch_profile.argtypes = [_VP, i]
+        L.qnsch_profile_read.argtypes = [_VP, ctypes.POINTER(ctypes.c_longlong), p]
+        L.qnsch_kernel_launches.argtypes = [ctypes.POINTER(ctypes.c_longlong)]
+        _lib = L
+    return _lib
+
+
+def kernel_launches():
+    """Kernels issued by libqnsch.so in this process (host-side count)."""
+    n = ctypes.c_longlong()
+    _check(lib().qnsch_kernel_launches(ctypes.byref(n)), "qnsch_kernel_launches")
+    return n.value
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise QnschError(what, rc)
+
+
+def _np_ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+class Solver:
+    """One q-NSCH instance on the GPU (the handle of qnsch_create)."""
+
+    FIELDS = ("c", "mu", "u", "v", "p")  # argument order of the C calls
+
+    def __init__(self, m1, m2, Lx=1.0, periodic_x=False, levels=0, rho1=1.0, rho2=1.0,
+                 eta1=1.0, eta2=1.0, Re=100.0, We=10.0, Pe=100.0, Cn=0.01, Fr=math.inf,
+                 stream=None, **options):
+        self.m1, self.m2 = int(m1), int(m2)
+        self.periodic_x = bool(periodic_x)
+        self.h = Lx / m1
+        g = _Grid(self.m1, self.m2, float(Lx), int(periodic_x), 0, int(levels))
+        h = _VP()
+        _check(lib().qnsch_create(ctypes.byref(g), rho1, rho2, eta1, eta2, Re, We, Pe, Cn, Fr,
+                                  ctypes.byref(h)), "qnsch_create")
+        self._h = h
+        if stream is not None:
+            self.set_stream(stream)
+        for k, v in options.items():
+            self.set_option(k, v)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().qnsch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- configuration ----
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, an int handle, or None for the default stream."""
+        handle = getattr(stream, "cuda_stream", stream)
+        _check(lib().qnsch_set_stream(self._h, handle or None), "qnsch_set_stream")
+
+    def set_option(self, key, value):
+        _check(lib().qnsch_set_option(self._h, key.encode(), float(value)), "set_option " + key)
+
+    def get_option(self, key):
+        out = ctypes.c_double()
+        _check(lib().qnsch_get_option(self._h, key.encode(), ctypes.byref(out)), "get_option")
+        return out.value
+
+    @property
+    def levels(self):
+        return lib().qnsch_levels(self._h)
+
+    @property
+    def ncolours_vanka(self):
+        return lib().qnsch_ncolours_vanka(self._h)
+
+    def shapes(self):
+        m1, m2 = self.m1, self.m2
+        return dict(c=(m2, m1), mu=(m2, m1), p=(m2, m1), u=(m2, m1 + 1), v=(m2 + 1, m1))
+
+    def zeros(self):
+        return {k: np.zeros(s) for k, s in self.shapes().items()}
+
+    def _host_in(self, f):
+        out = {}
+        for k, s in self.shapes().items():
+            a = np.ascontiguousarray(f[k], dtype=np.float64)
+            if a.shape != s:
+                raise ValueError("%s has shape %s, expected %s" % (k, a.shape, s))
+            out[k] = a
+        return out
+
+    def _host_call(self, fn, f, what):
+        a = self._host_in(f)
+        _check(fn(self._h, *[_np_ptr(a[k]) for k in self.FIELDS]), what)
+
+    def _host_get(self, fn, what):
+        a = self.zeros()
+        _check(fn(self._h, *[_np_ptr(a[k]) for k in self.FIELDS]), what)
+        return a
+
+    # ---- fields ----
+    def set_fields(self, f):
+        self._host_call(lib().qnsch_set_fields, f, "qnsch_set_fields")
+
+    def get_fields(self):
+        return self._host_get(lib().qnsch_get_fields, "qnsch_get_fields")
+
+    def set_fields_device(self, t):
+        """t: dict of contiguous float64 CUDA tensors in the host layouts."""
+        ptrs = []
+        for k in self.FIELDS:
+            x = t[k]
+            if tuple(x.shape) != self.shapes()[k] or not x.is_contiguous() or not x.is_cuda:
+                raise ValueError("field %s: need a contiguous CUDA tensor of shape %s"
+                                 % (k, self.shapes()[k]))
+            ptrs.append(x.data_ptr())
+        _check(lib().qnsch_set_fields_device(self._h, *ptrs), "qnsch_set_fields_device")
+
+    def get_fields_device(self, t):
+        ptrs = [t[k].data_ptr() for k in self.FIELDS]
+        _check(lib().qnsch_get_fields_device(self._h, *ptrs), "qnsch_get_fields_device")
+
+    def set_iterate(self, f):
+        self._host_call(lib().qnsch_set_iterate, f, "qnsch_set_iterate")
+
+    def get_iterate(self):
+        return self._host_get(lib().qnsch_get_iterate, "qnsch_get_iterate")
+
+    # ---- stepping ----
+    def step(self, dt):
+        n = ctypes.c_int()
+        r = ctypes.c_double()
+        _check(lib().qnsch_step(self._h, float(dt), ctypes.byref(n), ctypes.byref(r)),
+               "qnsch_step")
+        return n.value, r.value
+
+    def begin_step(self, dt):
+        _check(lib().qnsch_begin_step(self._h, float(dt)), "qnsch_begin_step")
+
+    def vcycle(self):
+        out = np.zeros(10)
+        _check(lib().qnsch_vcycle(self._h, out.ctypes.data_as(_D)), "qnsch_vcycle")
+        return out
+
+    def commit_step(self):
+        _check(lib().qnsch_commit_step(self._h), "qnsch_commit_step")
+
+    def residual(self):
+        r = self.zeros()
+        n = np.zeros(10)
+        _check(lib().qnsch_residual(self._h, _np_ptr(r["c"]), _np_ptr(r["mu"]), _np_ptr(r["p"]),
+                                    _np_ptr(r["u"]), _np_ptr(r["v"]), n.ctypes.data_as(_D)),
+               "qnsch_residual")
+        return r, n
+
+    def smooth_ch(self, colour):
+        _check(lib().qnsch_smooth_ch(self._h, int(colour)), "qnsch_smooth_ch")
+
+    def smooth_vanka(self, colour):
+        _check(lib().qnsch_smooth_vanka(self._h, int(colour)), "qnsch_smooth_vanka")
+
+    def smooth(self, sweeps=1):
+        _check(lib().qnsch_smooth(self._h, int(sweeps)), "qnsch_smooth")
+
+    # ---- measurement ----
+    def profile(self, enable=True):
+        _check(lib().qnsch_profile(self._h, int(bool(enable))), "qnsch_profile")
+
+    def profile_read(self):
+        n, ms = ctypes.c_longlong(), ctypes.c_double()
+        _check(lib().qnsch_profile_read(self._h, ctypes.byref(n), ctypes.byref(ms)),
+               "qnsch_profile_read")
+        return n.value, ms.value
+
+    # ---- diagnostics ----
+    def mass(self):
+        a, b = ctypes.c_double(), ctypes.c_double()
+        _check(lib().qnsch_mass(self._h, ctypes.byref(a), ctypes.byref(b)), "qnsch_mass")
+        return a.value, b.value
+
+    def energy(self):
+        e, d = ctypes.c_double(), ctypes.c_double()
+        _check(lib().qnsch_energy(self._h, ctypes.byref(e), ctypes.byref(d)), "qnsch_energy")
+        return e.value, d.value
+
+    def iterate_energy(self):
+        e, d = ctypes.c_double(), ctypes.c_double()
+        _check(lib().qnsch_iterate_energy(self._h, ctypes.byref(e), ctypes.byref(d)),
+               "qnsch_iterate_energy")
+        return e.value, d.value

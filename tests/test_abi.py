@@ -1,0 +1,40 @@
+"""The C ABI library builds, loads and exports every symbol include/qnsch.h
+declares (no compute calls: this runs without a GPU); without a device,
+qnsch_create reports QNSCH_ENODEV instead of falling back to the CPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1703_06606_gb300 import build as qbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "qnsch.h")).read()
+    return sorted(set(re.findall(r"^int\s+(qnsch_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_header_declares_the_paper_calls():
+    names = declared_symbols()
+    for must in ("qnsch_create", "qnsch_step", "qnsch_vcycle", "qnsch_mass", "qnsch_energy",
+                 "qnsch_begin_step", "qnsch_commit_step", "qnsch_destroy"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ctypes.CDLL(qbuild.build())
+    missing = [n for n in declared_symbols() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_create_without_device_reports_enodev():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_1703_06606_gb300 import qnsch
+    with pytest.raises(qnsch.QnschError) as e:
+        qnsch.Solver(16, 16)
+    assert e.value.code == -2

@@ -1,0 +1,208 @@
+"""Parity of the CUDA path (libqnsch.so, through its C ABI) with the FP64 oracle.
+
+Element-by-element comparisons on the same seeded inputs: the residual of every
+family, single colour sweeps of both smoothers, a full smoothing step, one
+V-cycle, and full time steps; conservation and energy checks on the GPU
+results; edge cases (smallest grids, ragged sizes, periodic seams) and error
+statuses.  FP64 tolerances: per-kernel results to 1e-11 relative (rounding
+order and FMA contraction differ between the two builds), converged steps to
+1e-10 relative in max norm per field.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.ref import RefSolver
+from paper_1703_06606_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qn():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1703_06606_gb300 import qnsch
+    return qnsch
+
+
+KW = dict(Lx=1.0, levels=0, rho1=1.0, rho2=3.0, eta1=1.0, eta2=2.5, Re=50.0, We=5.0, Pe=20.0,
+          Cn=0.05, Fr=0.8)
+
+
+def pair(qn, m1, m2, px, **over):
+    kw = dict(KW, **over)
+    return qn.Solver(m1, m2, periodic_x=px, **kw), RefSolver(m1, m2, periodic_x=px, **kw)
+
+
+def relerr(a, b):
+    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+
+
+def load_random(g, r, px, seed=7, dt=2e-3):
+    fn = W.random_state(g.m1, g.m2, px, seed=seed)
+    fx = W.random_state(g.m1, g.m2, px, seed=seed + 1)
+    for s in (g, r):
+        s.set_fields(fn)
+        s.begin_step(dt)
+        s.set_iterate(fx)
+    return fn, fx
+
+
+def same_fields(fg, fr, tol, keys=("c", "mu", "p", "u", "v")):
+    for k in keys:
+        e = relerr(fg[k], fr[k])
+        assert e <= tol, (k, e)
+
+
+SIZES = [(16, 12, False), (16, 12, True), (37, 29, False), (40, 24, True), (2, 2, False),
+         (4, 6, True), (70, 45, False)]
+
+
+@pytest.mark.parametrize("m1,m2,px", SIZES)
+def test_residual_parity(qn, m1, m2, px):
+    g, r = pair(qn, m1, m2, px)
+    load_random(g, r, px)
+    rg, ng = g.residual()
+    rr, nr = r.residual()
+    for k in rg:
+        sl = (slice(None), slice(1, m1 + (1 if px else 0))) if k == "u" else (
+            (slice(1, m2), slice(None)) if k == "v" else (slice(None), slice(None)))
+        assert relerr(rg[k][sl], rr[k][sl]) <= 1e-11, k
+    assert np.allclose(ng, nr, rtol=1e-11, atol=0)
+
+
+@pytest.mark.parametrize("m1,m2,px", SIZES)
+def test_ch_sweep_parity(qn, m1, m2, px):
+    g, r = pair(qn, m1, m2, px)
+    load_random(g, r, px, seed=17)
+    for colour in (0, 1):
+        g.smooth_ch(colour)
+        r.smooth_ch(colour)
+        same_fields(g.get_iterate(), r.get_iterate(), 1e-11)
+
+
+@pytest.mark.parametrize("m1,m2,px", SIZES)
+def test_vanka_sweep_parity(qn, m1, m2, px):
+    g, r = pair(qn, m1, m2, px)
+    load_random(g, r, px, seed=27)
+    for colour in range(g.ncolours_vanka):
+        g.smooth_vanka(colour)
+        r.smooth_vanka(colour)
+        same_fields(g.get_iterate(), r.get_iterate(), 1e-11)
+
+
+@pytest.mark.parametrize("m1,m2,px", [(32, 24, False), (32, 24, True)])
+def test_smoothing_and_vcycle_parity(qn, m1, m2, px):
+    g, r = pair(qn, m1, m2, px)
+    load_random(g, r, px, seed=37)
+    g.smooth(2)
+    r.smooth(2)
+    same_fields(g.get_iterate(), r.get_iterate(), 1e-10)
+    ng = g.vcycle()
+    nr = r.vcycle()
+    same_fields(g.get_iterate(), r.get_iterate(), 1e-9)
+    assert np.allclose(ng, nr, rtol=1e-6)
+
+
+def _step_both(qn, P, steps=1, **opt):
+    g = qn.Solver(**P.create_kwargs(), tol=P.tol, **opt)
+    r = RefSolver(**P.create_kwargs(), tol=P.tol, **opt)
+    f = P.fields()
+    g.set_fields(f)
+    r.set_fields(f)
+    hist = []
+    for _ in range(steps):
+        ng, resg = g.step(P.dt)
+        nr, resr = r.step(P.dt)
+        hist.append((ng, nr, resg, resr))
+    return g, r, hist
+
+
+@pytest.mark.parametrize("px", [False, True])
+def test_full_step_parity_small(qn, px):
+    P = W.small_case(32, 48, px)
+    g, r, hist = _step_both(qn, P, steps=2)
+    for ng, nr, resg, resr in hist:
+        assert ng == nr and resg <= P.tol and resr <= P.tol
+    fg, fr = g.get_fields(), r.get_fields()
+    same_fields(fg, fr, 1e-10)
+    mg, mr = g.mass(), r.mass()
+    assert abs(mg[0] - mr[0]) <= 1e-13 * mr[0] and abs(mg[1] - mr[1]) <= 1e-13 * mr[1]
+    eg, dg = g.energy()
+    assert abs(eg - r.energy()) <= 1e-12 * abs(r.energy()) and dg > 0
+
+
+def test_capillary_wave_64_parity(qn):
+    P = W.capillary_64()
+    P.steps = 3
+    g, r, hist = _step_both(qn, P, steps=P.steps)
+    same_fields(g.get_fields(), r.get_fields(), 1e-10)
+    m0 = r.mass()
+
+
+def test_rising_drop_full_size_one_step(qn):
+    """The benchmark workload (256x512, 8 levels, tol 1e-9), one step, every field."""
+    P = W.rising_drop_256x512()
+    g, r, hist = _step_both(qn, P, steps=1)
+    (ng, nr, resg, resr), = hist
+    assert ng == nr
+    same_fields(g.get_fields(), r.get_fields(), 1e-10)
+
+
+def test_conservation_and_energy_on_gpu(qn):
+    P = W.small_case(64, 64, False, rho_ratio=10.0)
+    g = qn.Solver(**P.create_kwargs(), tol=1e-11)
+    g.set_fields(P.fields())
+    m0 = g.mass()
+    e0, _ = g.energy()
+    prev = e0
+    for _ in range(3):
+        g.step(P.dt)
+        e, d = g.energy()
+        assert e < prev and d > 0
+        prev = e
+    m1 = g.mass()
+    assert abs(m1[0] - m0[0]) <= 1e-12 * m0[0]
+    assert abs(m1[1] - m0[1]) <= 1e-12 * m0[1]
+
+
+def test_device_field_io_roundtrip(qn):
+    import torch
+    P = W.small_case(24, 16, True)
+    g = qn.Solver(**P.create_kwargs())
+    f = W.random_state(24, 16, True, seed=3)
+    t = {k: torch.tensor(v, device="cuda", dtype=torch.float64) for k, v in f.items()}
+    g.set_fields_device(t)
+    back = g.get_fields()
+    for k in f:
+        assert np.array_equal(back[k], f[k]), k
+    out = {k: torch.empty_like(v) for k, v in t.items()}
+    g.get_fields_device(out)
+    for k in f:
+        assert np.array_equal(out[k].cpu().numpy(), f[k]), k
+
+
+def test_error_statuses(qn):
+    with pytest.raises(qn.QnschError) as e:
+        qn.Solver(6, 8, periodic_x=True)  # periodic x needs m1 % 4 == 0
+    assert e.value.code == -1
+    with pytest.raises(qn.QnschError):
+        qn.Solver(16, 16, levels=9)
+    g = qn.Solver(16, 16)
+    with pytest.raises(qn.QnschError) as e:
+        g.vcycle()  # no pending step
+    assert e.value.code == -8
+    with pytest.raises(qn.QnschError) as e:
+        g.set_option("no_such_option", 1.0)
+    assert e.value.code == -1
+    P = W.small_case(16, 16, False)
+    g = qn.Solver(**P.create_kwargs(), tol=1e-14, maxcyc=1)
+    f = P.fields()
+    g.set_fields(f)
+    with pytest.raises(qn.QnschError) as e:
+        g.step(P.dt)
+    assert e.value.code == -4
+    assert np.array_equal(g.get_fields()["c"], f["c"])  # not committed
