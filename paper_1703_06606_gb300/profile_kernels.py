@@ -1,0 +1,44 @@
+"""Run single kernels of libqnsch.so on a chosen grid, for profilers (ncu).
+
+    python -m paper_1703_06606_gb300.profile_kernels --kernel vanka --m1 1024 --m2 1024 --reps 3
+
+Sets up the drop workload at the given size, freezes a time step and issues
+`reps` launches of one finest-level kernel (vanka: colour 0 of the Vanka
+smoother; ch: colour 0 of the CH smoother; step: whole time steps).
+"""
+from __future__ import annotations
+
+import argparse
+
+from . import qnsch, workloads
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--kernel", default="vanka", choices=["vanka", "ch", "residual", "step"])
+    ap.add_argument("--m1", type=int, default=1024)
+    ap.add_argument("--m2", type=int, default=1024)
+    ap.add_argument("--reps", type=int, default=3)
+    a = ap.parse_args()
+    P = workloads.rising_drop_256x512()
+    P.m1, P.m2, P.Lx = a.m1, a.m2, 1.0
+    P.init_args = dict(x0=0.5, y0=0.25 * a.m2 / a.m1, R=0.2)
+    s = qnsch.Solver(**P.create_kwargs(), tol=P.tol)
+    s.set_fields(P.fields())
+    if a.kernel == "step":
+        for _ in range(a.reps):
+            print(s.step(P.dt))
+        return
+    s.begin_step(P.dt)
+    for _ in range(a.reps):
+        if a.kernel == "vanka":
+            s.smooth_vanka(0)
+        elif a.kernel == "ch":
+            s.smooth_ch(0)
+        else:
+            s.residual()
+    print("done", a)
+
+
+if __name__ == "__main__":
+    main()

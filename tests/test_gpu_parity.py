@@ -95,16 +95,29 @@ def test_vanka_sweep_parity(qn, m1, m2, px):
 
 
 @pytest.mark.parametrize("m1,m2,px", [(32, 24, False), (32, 24, True)])
-def test_smoothing_and_vcycle_parity(qn, m1, m2, px):
+def test_smoothing_parity_random_state(qn, m1, m2, px):
     g, r = pair(qn, m1, m2, px)
     load_random(g, r, px, seed=37)
     g.smooth(2)
     r.smooth(2)
     same_fields(g.get_iterate(), r.get_iterate(), 1e-10)
-    ng = g.vcycle()
-    nr = r.vcycle()
-    same_fields(g.get_iterate(), r.get_iterate(), 1e-9)
-    assert np.allclose(ng, nr, rtol=1e-6)
+
+
+@pytest.mark.parametrize("m1,m2,px", [(32, 48, False), (32, 48, True), (24, 40, False)])
+def test_vcycle_parity_from_physical_state(qn, m1, m2, px):
+    """V-cycles (all levels, transfers, coarsest solve, gauge) from the level-n state."""
+    P = W.small_case(m1, m2, px)
+    g = qn.Solver(**P.create_kwargs())
+    r = RefSolver(**P.create_kwargs())
+    for s in (g, r):
+        s.set_fields(P.fields())
+        s.begin_step(P.dt)
+    assert g.levels == r.levels
+    for _ in range(3):
+        ng = g.vcycle()
+        nr = r.vcycle()
+        same_fields(g.get_iterate(), r.get_iterate(), 1e-10)
+        assert np.allclose(ng, nr, rtol=1e-6, atol=1e-14)
 
 
 def _step_both(qn, P, steps=1, **opt):
