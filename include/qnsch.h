@@ -151,6 +151,34 @@ int qnsch_profile_read(qnsch_t* h, long long* launches, double* total_ms);
    (process-wide, counted on the host at launch). */
 int qnsch_kernel_launches(long long* n);
 
+/* Mass reduction that allocates nothing (the paper has no counterpart: this is
+   an interface for callers, not a step of the method).  It is meant for code
+   that cannot allocate device memory when it needs the result: work issued
+   while a stream is being captured into a CUDA graph, code running inside an
+   allocator or memory-pool callback, and programs whose device memory is fully
+   reserved up front by another framework.  It creates no handle and calls no
+   cudaMalloc, cudaFree or allocating library routine.
+
+   c: device pointer to the m2 x m1 cell array (layout above); h: cell size;
+   rho1, rho2: the densities of qnsch_create; out2: device pointer to two
+   doubles that receive h^2 sum rho(c) and h^2 sum rho(c) c (Thm. 6.1
+   quantities, as qnsch_mass returns for a handle's state).  Work is queued on
+   `stream` (NULL: legacy default stream) and the call returns without waiting:
+   synchronise the stream before reading out2.
+
+   Limit: m1 * m2 <= QNSCH_NOALLOC_MAX_CELLS, else QNSCH_EINVAL.  Its scratch is
+   one file-scope device array of 64 KiB (QNSCH_NOALLOC_MAX_CELLS / 2048 pairs
+   of doubles) that every GPU loading the library holds until the process
+   exits.  All calls share that array, so calls whose work overlaps on the GPU
+   (other streams, other host threads) race and must be serialised by the
+   caller; each call writes every entry it reads, so no clearing is needed.
+   The first call on a device looks up the array's device address
+   (cudaGetSymbolAddress) with that device current: make that first call
+   before starting any stream capture. */
+#define QNSCH_NOALLOC_MAX_CELLS 8388608
+int qnsch_mass_noalloc(const double* c, int m1, int m2, double h, double rho1, double rho2,
+                       double* out2, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -73,6 +73,7 @@ def lib():
         L.qnsch_profile.argtypes = [_VP, i]
         L.qnsch_profile_read.argtypes = [_VP, ctypes.POINTER(ctypes.c_longlong), p]
         L.qnsch_kernel_launches.argtypes = [ctypes.POINTER(ctypes.c_longlong)]
+        L.qnsch_mass_noalloc.argtypes = [_VP, i, i, d, d, d, _VP, _VP]
         _lib = L
     return _lib
 
@@ -82,6 +83,21 @@ def kernel_launches():
     n = ctypes.c_longlong()
     _check(lib().qnsch_kernel_launches(ctypes.byref(n)), "qnsch_kernel_launches")
     return n.value
+
+
+def mass_noalloc(c, h, rho1, rho2, out2, stream=None):
+    """qnsch_mass_noalloc: h^2 sum rho(c), h^2 sum rho(c) c of a caller-owned CUDA
+    float64 tensor c (m2, m1) into the caller-owned CUDA float64 tensor out2 (2,),
+    queued on `stream` (torch stream or handle) without allocating anything.  The
+    caller synchronises before reading out2."""
+    if not (c.is_cuda and c.is_contiguous() and c.dim() == 2 and out2.is_cuda and
+            out2.numel() >= 2):
+        raise ValueError("need a contiguous 2-D CUDA tensor c and a CUDA tensor out2 of 2")
+    handle = getattr(stream, "cuda_stream", stream)
+    m2, m1 = c.shape
+    _check(lib().qnsch_mass_noalloc(c.data_ptr(), int(m1), int(m2), float(h), float(rho1),
+                                    float(rho2), out2.data_ptr(), handle or None),
+           "qnsch_mass_noalloc")
 
 
 def _check(rc, what):
