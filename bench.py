@@ -50,7 +50,7 @@ def config_of(P, levels, precision="fp64"):
     return {"workload": P.name, "grid": "%dx%d" % (P.m1, P.m2), "levels": levels,
             "dt": P.dt, "tol": P.tol, "precision": precision,
             "smoother": "CH 2x2 red-black + Vanka 5x5 (5 colours)",
-            "nu1_nu2_nucoarse": [2, 2, 20],
+            "nu1_nu2_nucoarse": [2, 2, 4],
             "l2": "flushed between timed steps (256 MiB write)",
             "parallelism": "replicas"}
 
@@ -243,7 +243,7 @@ def run_ours(args, rank, world, local_rank):
                 "d2h_bytes_per_step": field_bytes(P)},
         "gpu_launches": int(launches),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": VANKA_FP64_TRAFFIC_BYTES,
                      "kernel": "k_vanka<double> finest level",
                      "launches_timed": prof_n, "avg_launch_us": avg_ms * 1e3,
                      "peak_source": "measured FP64 FMA throughput (profiles/fp64_fp32_peak_probe.md)"},
@@ -264,6 +264,10 @@ def run_ours(args, rank, world, local_rank):
 # algorithmic FP64 operations per Vanka cell visit (add/sub/mul/div = 1, fused
 # multiply-add = 2), counted from the formulas of k_vanka; see the design doc
 VANKA_FP64_FLOPS_PER_VISIT = 960.0
+# dram__bytes_read.sum + dram__bytes_write.sum of one finest-level k_vanka<double> launch at
+# 256x512 (ncu, profiles/k_vanka_fp64_drop_1024x1024.md and the design doc); None once the kernel
+# changes after the capture
+VANKA_FP64_TRAFFIC_BYTES = 15.6e6
 # measured FP64 FMA throughput of one GB300 (dependent-chain-free DFMA loop)
 FP64_PEAK_TFLOPS = 1.193
 

@@ -80,7 +80,7 @@ int qnsch_create(const qnsch_grid* grid, double rho1, double rho2, double eta1, 
 int qnsch_destroy(qnsch_t* h);
 
 /* Options (key: default): "nu1": 2, "nu2": 2 (pre/post smoothing steps),
-   "nu_coarse": 20 (smoothing steps on the coarsest level), "tol": 1e-9,
+   "nu_coarse": 4 (smoothing steps on the coarsest level), "tol": 1e-9,
    "maxcyc": 50, "omega_vanka": 1, "M": Cn, "eta_st": eta(rho1, rho2),
    "eps_mob": Cn.  Unknown keys give QNSCH_EINVAL. */
 int qnsch_set_option(qnsch_t* h, const char* key, double value);

@@ -1176,7 +1176,7 @@ int qnsch_ref_create(int m1, int m2, double Lx, int periodic_x, int levels, doub
   derive_params(&s->P);
   s->nu1 = 2;
   s->nu2 = 2;
-  s->nuc = 20;
+  s->nuc = 4;
   s->maxcyc = 50;
   s->tol = 1e-9;
   s->omega = 1.0;

@@ -77,7 +77,7 @@ struct qnsch_s {
   double rho1, rho2, mu1, mu2, Re, We, Pe, Cn, Fr_inv;
   double M, eta, eps_m;
   // options
-  int nu1 = 2, nu2 = 2, nuc = 20, maxcyc = 50;
+  int nu1 = 2, nu2 = 2, nuc = 4, maxcyc = 50;
   double tol = 1e-9, omega = 1.0;
   // grid
   int m1, m2, px, nlev, kcol;
