@@ -82,7 +82,17 @@ int qnsch_destroy(qnsch_t* h);
 /* Options (key: default): "nu1": 2, "nu2": 2 (pre/post smoothing steps),
    "nu_coarse": 4 (smoothing steps on the coarsest level), "tol": 1e-9,
    "maxcyc": 50, "omega_vanka": 1, "M": Cn, "eta_st": eta(rho1, rho2),
-   "eps_mob": Cn.  Unknown keys give QNSCH_EINVAL. */
+   "eps_mob": Cn, "precision": 0.  Unknown keys give QNSCH_EINVAL.
+   precision 0: FAS V-cycles in FP64 on the scheme itself.
+   precision 1: mixed.  Each outer cycle forms the FP64 residual r = -N(x),
+     runs one FAS V-cycle in FP32 on the error equation N(x + e) - N(x) = r
+     (smoothing, transfers and coarse levels in FP32; every nonlinear
+     difference written with the secant identities of Sec. 4.1, so nothing
+     cancels in FP32), adds e to x in FP64 and removes the mean of p in FP64.
+     Convergence is still judged on the FP64 residual, so the step meets the
+     same tol.
+   precision 2: as 1 with an FP64 error cycle (a check of the error form).
+   "precision" cannot change between qnsch_begin_step and qnsch_commit_step. */
 int qnsch_set_option(qnsch_t* h, const char* key, double value);
 int qnsch_get_option(const qnsch_t* h, const char* key, double* value);
 int qnsch_set_stream(qnsch_t* h, void* cuda_stream);

@@ -76,17 +76,17 @@ __global__ void k_finalize(const double* part, int nparts, int nv, int nmax_firs
 // residual r = f - N(x) (mode 0, optional norms) or f += N(x) (mode 1)
 // thread (i,j): cell families at (i,j), u-edge (i,j) and v-edge (i,j)
 // --------------------------------------------------------------------------
-template <typename T, int MODE>
+template <typename T, int MODE, class Form>
 __global__ void k_residual(Prm<T> P, Lv<T> L, double* part) {
   int i = blockIdx.x * BX + threadIdx.x + 1;
   int j = blockIdx.y * BY + threadIdx.y + 1;
   double val[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};  // max x5 then sum of squares x5
   if (i <= L.m1 && j <= L.m2) {
     int k = L.at(i, j);
-    T nc = op_c(P, L, k), nm = op_mu(P, L, k), np = op_p(P, L, k);
+    T nc = Form::Nc(P, L, k), nm = Form::Nmu(P, L, k), np = Form::Np(P, L, k);
     bool hu = i <= L.uhi(), hv = j < L.m2;
-    T nu = hu ? op_u(P, L, k) : T(0);
-    T nv = hv ? op_v(P, L, k) : T(0);
+    T nu = hu ? Form::Nu(P, L, k) : T(0);
+    T nv = hv ? Form::Nv(P, L, k) : T(0);
     if (MODE == 0) {
       T r[5] = {L.fc[k] - nc, L.fmu[k] - nm, L.fp[k] - np, hu ? L.fu[k] - nu : T(0),
                 hv ? L.fv[k] - nv : T(0)};
@@ -117,7 +117,7 @@ __global__ void k_residual(Prm<T> P, Lv<T> L, double* part) {
 // of each cell with (i + j) % 2 == colour; neighbours frozen.  Faces on
 // Neumann walls do not contribute (their ghost follows the cell).
 // --------------------------------------------------------------------------
-template <typename T>
+template <typename T, class Form>
 __global__ void k_ch(Prm<T> P, Lv<T> L, int colour) {
   int j = blockIdx.y * BY + threadIdx.y + 1;
   if (j > L.m2) return;
@@ -126,10 +126,11 @@ __global__ void k_ch(Prm<T> P, Lv<T> L, int colour) {
   if (i > L.m1) return;
   const int W = L.pitch;
   int k = L.at(i, j);
-  T Rc = op_c(P, L, k) - L.fc[k];
-  T Rm = op_mu(P, L, k) - L.fmu[k];
-  const T *c = L.c, *cn = L.cn, *rn = L.rhon, *mob = L.mobn;
-  T ck = c[k], cnk = cn[k], mk = L.mu[k];
+  T Rc = Form::Nc(P, L, k) - L.fc[k];
+  T Rm = Form::Nmu(P, L, k) - L.fmu[k];
+  const T *cn = L.cn, *rn = L.rhon, *mob = L.mobn;
+  // full values c, mu at which the local Jacobian is evaluated
+  T ck = Form::val_c(L, k), cnk = cn[k], mk = Form::val_mu(L, k);
   T rho = rho_of(P, ck), drho = -P.alpha * rho * rho;
   T rnk = rn[k];
   T rh = T(0.5) * (rho + rnk);
@@ -137,20 +138,23 @@ __global__ void k_ch(Prm<T> P, Lv<T> L, int colour) {
   T r = -P.alpha * rho * rnk, dr = -P.alpha * drho * rnk;
   bool wall[4] = {!L.px && i == L.m1, !L.px && i == 1, j == L.m2, j == 1};
   const int off[4] = {1, -1, W, -W};
-  T sm = 0, dG = 0, dd = 0;
+  T sm = 0, dG = 0, dd = 0, G2 = 0;
 #pragma unroll
   for (int f = 0; f < 4; ++f) {
-    if (wall[f]) continue;
     int q = k + off[f];
+    T cq = Form::val_c(L, q);
+    T d = cq - ck;
+    G2 += d * d;
+    if (wall[f]) continue;
     sm += mob[k] + mob[q];
-    dG += ck - c[q];
-    T rq = T(0.5) * (rho_of(P, c[q]) + rn[q]);
-    dd += T(0.5) * drho * ((c[q] + cn[q]) - chk) - (rh + rq);
+    dG -= d;
+    T rq = T(0.5) * (rho_of(P, cq) + rn[q]);
+    dd += T(0.5) * drho * ((cq + cn[q]) - chk) - (rh + rq);
   }
-  // sm = 2 sum A m; dG = h^2 dG/dc; dd = 4 h^2 d(div)/dc
+  // sm = 2 sum A m; dG = h^2 dG/dc; dd = 4 h^2 d(div)/dc; G2 = 2 h^2 G(c)
   T J11 = (rho + drho * (ck - cnk)) * P.idt;
   T J12 = T(0.5) * sm * P.iPe * L.ih2;
-  T Gs = G_h2(c, k, W) * L.ih2 + L.Gn[k];
+  T Gs = T(0.5) * G2 * L.ih2 + L.Gn[k];
   T dbulk = T(0.5) * drho * gsec(ck, cnk) + rh * gsec_da(ck, cnk) + T(0.5) * fdw(ck) * r +
             T(0.5) * (Fdw(ck) + Fdw(cnk)) * dr;
   T dgrad = T(0.25) * P.Lam * (dG * L.ih2 * r + Gs * dr);
@@ -159,8 +163,8 @@ __global__ void k_ch(Prm<T> P, Lv<T> L, int colour) {
   T idet = T(1) / (J11 * J22 - J12 * J21);
   T dc = (J22 * Rc - J12 * Rm) * idet;
   T dm = (J11 * Rm - J21 * Rc) * idet;
-  store_cell(L, L.c, i, j, ck - dc);
-  store_cell(L, L.mu, i, j, mk - dm);
+  store_cell(L, L.c, i, j, L.c[k] - dc);
+  store_cell(L, L.mu, i, j, L.mu[k] - dm);
 }
 
 // --------------------------------------------------------------------------
@@ -208,7 +212,7 @@ __device__ __forceinline__ void solve5(T (&A)[5][5], T (&b)[5]) {
   }
 }
 
-template <typename T>
+template <typename T, class Form>
 __global__ void k_vanka(Prm<T> P, Lv<T> L, int colour, T omega) {
   int j = blockIdx.y * BY + threadIdx.y + 1;
   if (j > L.m2) return;
@@ -246,7 +250,7 @@ __global__ void k_vanka(Prm<T> P, Lv<T> L, int colour, T omega) {
     T rl = rn[ke], rr = rn[ke + 1];
     T axl = T(0.5) * (un[ke] + un[ke - 1]), axr = T(0.5) * (un[ke + 1] + un[ke]);
     T Arn = T(0.5) * (rl + rr);
-    T Ar = T(0.5) * (rho_of(P, L.c[ke]) + rho_of(P, L.c[ke + 1]));
+    T Ar = T(0.5) * (rho_of(P, Form::val_c(L, ke)) + rho_of(P, Form::val_c(L, ke + 1)));
     T Art = T(0.25) * (rl + rr + rn[ke + W] + rn[ke + 1 + W]);
     T Arb = T(0.25) * (rl + rr + rn[ke - W] + rn[ke + 1 - W]);
     T Avt = T(0.25) * (vis[ke] + vis[ke + 1] + vis[ke + W] + vis[ke + 1 + W]);
@@ -279,7 +283,7 @@ __global__ void k_vanka(Prm<T> P, Lv<T> L, int colour, T omega) {
     T rb = rn[ke], rt = rn[ke + W];
     T ayb = T(0.5) * (vn[ke] + vn[ke - W]), ayt = T(0.5) * (vn[ke + W] + vn[ke]);
     T Arn = T(0.5) * (rb + rt);
-    T Ar = T(0.5) * (rho_of(P, L.c[ke]) + rho_of(P, L.c[ke + W]));
+    T Ar = T(0.5) * (rho_of(P, Form::val_c(L, ke)) + rho_of(P, Form::val_c(L, ke + W)));
     T Are = T(0.25) * (rb + rt + rn[ke + 1] + rn[ke + 1 + W]);
     T Arw = T(0.25) * (rb + rt + rn[ke - 1] + rn[ke - 1 + W]);
     T Ave = T(0.25) * (vis[ke] + vis[ke + W] + vis[ke + 1] + vis[ke + 1 + W]);
@@ -319,11 +323,11 @@ __global__ void k_vanka(Prm<T> P, Lv<T> L, int colour, T omega) {
     A[4][3] = ih;
     A[4][4] = T(0.5) * P.alpha * P.alpha * P.iPe * sm * ih2;
   }
-  b[0] = act[0] ? op_u(P, L, kW) - L.fu[kW] : T(0);
-  b[1] = act[1] ? op_u(P, L, k) - L.fu[k] : T(0);
-  b[2] = act[2] ? op_v(P, L, k - W) - L.fv[k - W] : T(0);
-  b[3] = act[3] ? op_v(P, L, k) - L.fv[k] : T(0);
-  b[4] = op_p(P, L, k) - L.fp[k];
+  b[0] = act[0] ? Form::Nu(P, L, kW) - L.fu[kW] : T(0);
+  b[1] = act[1] ? Form::Nu(P, L, k) - L.fu[k] : T(0);
+  b[2] = act[2] ? Form::Nv(P, L, k - W) - L.fv[k - W] : T(0);
+  b[3] = act[3] ? Form::Nv(P, L, k) - L.fv[k] : T(0);
+  b[4] = Form::Np(P, L, k) - L.fp[k];
 #pragma unroll
   for (int q = 0; q < 4; ++q)
     if (!act[q]) {
@@ -603,6 +607,96 @@ __global__ void k_prolong(Lv<T> F, Lv<T> C) {
 }
 
 // --------------------------------------------------------------------------
+// defect correction (mixed precision): FP64 level <-> error-equation level
+// --------------------------------------------------------------------------
+// error-equation frozen data = rounded FP64 frozen data (whole padded arrays)
+template <typename T>
+__global__ void k_cast_frozen(Lv<double> D, Lv<T> E, long long n, int off) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  long long q = t - off;  // origin-relative index
+  E.cn[q] = (T)D.cn[q];
+  E.un[q] = (T)D.un[q];
+  E.vn[q] = (T)D.vn[q];
+  E.rhon[q] = (T)D.rhon[q];
+  E.mobn[q] = (T)D.mobn[q];
+  E.visn[q] = (T)D.visn[q];
+  E.Gn[q] = (T)D.Gn[q];
+}
+
+// base X = x (rounded), X.c - c^n formed in FP64, right-hand side = FP64 residual
+// (rounded), correction e = 0
+template <typename T>
+__global__ void k_start_correction(Lv<double> D, Lv<T> E, long long n, int off) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  long long q = t - off;
+  E.Bc[q] = (T)D.c[q];
+  E.Bmu[q] = (T)D.mu[q];
+  E.Bu[q] = (T)D.u[q];
+  E.Bv[q] = (T)D.v[q];
+  E.Bdc[q] = (T)(D.c[q] - D.cn[q]);
+  E.fc[q] = (T)D.rc[q];
+  E.fmu[q] = (T)D.rmu[q];
+  E.fp[q] = (T)D.rp[q];
+  E.fu[q] = (T)D.ru[q];
+  E.fv[q] = (T)D.rv[q];
+  E.c[q] = T(0);
+  E.mu[q] = T(0);
+  E.p[q] = T(0);
+  E.u[q] = T(0);
+  E.v[q] = T(0);
+}
+
+// x += e on the whole padded arrays (ghost rules are linear, so ghosts stay valid)
+template <typename T>
+__global__ void k_apply_correction(Lv<double> D, Lv<T> E, long long n, int off) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  long long q = t - off;
+  D.c[q] += (double)E.c[q];
+  D.mu[q] += (double)E.mu[q];
+  D.p[q] += (double)E.p[q];
+  D.u[q] += (double)E.u[q];
+  D.v[q] += (double)E.v[q];
+}
+
+// coarse base X_H = R X_h (cells: 4-mean; edges: 2 coincident fine edges)
+template <typename T>
+__global__ void k_restrict_base(Lv<T> F, Lv<T> C) {
+  int I = blockIdx.x * BX + threadIdx.x;
+  int J = blockIdx.y * BY + threadIdx.y;
+  if (I > C.m1 || J > C.m2) return;
+  int kc = C.at(I, J);
+  if (I >= 1 && J >= 1) {
+    int kf = F.at(2 * I - 1, 2 * J - 1), W = F.pitch;
+    C.Bc[kc] = T(0.25) * (F.Bc[kf] + F.Bc[kf + 1] + F.Bc[kf + W] + F.Bc[kf + W + 1]);
+    C.Bmu[kc] = T(0.25) * (F.Bmu[kf] + F.Bmu[kf + 1] + F.Bmu[kf + W] + F.Bmu[kf + W + 1]);
+    C.Bdc[kc] = T(0.25) * (F.Bdc[kf] + F.Bdc[kf + 1] + F.Bdc[kf + W] + F.Bdc[kf + W + 1]);
+  }
+  if (J >= 1) {
+    int kf = F.at(2 * I, 2 * J - 1);
+    C.Bu[kc] = T(0.5) * (F.Bu[kf] + F.Bu[kf + F.pitch]);
+  }
+  if (I >= 1) {
+    int kf = F.at(2 * I - 1, 2 * J);
+    C.Bv[kc] = T(0.5) * (F.Bv[kf] + F.Bv[kf + 1]);
+  }
+}
+
+template <typename T>
+__global__ void k_bc_base(Lv<T> L) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int I, J;
+  if (!frame_pos(t, L.m1, L.m2, I, J)) return;
+  fill_cell_ghost(L, L.Bc, I, J);
+  fill_cell_ghost(L, L.Bmu, I, J);
+  fill_cell_ghost(L, L.Bdc, I, J);
+  fill_u_ghost(L, L.Bu, I, J);
+  fill_v_ghost(L, L.Bv, I, J);
+}
+
+// --------------------------------------------------------------------------
 // reductions
 // --------------------------------------------------------------------------
 template <typename T>
@@ -741,25 +835,56 @@ int nparts_cells(const Lv<T>& L) {
   return g.x * g.y;
 }
 
-template <typename T>
+template <typename T, class Form>
 void launch_residual(const Prm<T>& P, const Lv<T>& L, double* part, cudaStream_t s) {
-  k_residual<T, 0><<<grid2(L.m1, L.m2), dim3(BX, BY), 0, s>>>(P, L, part);
+  k_residual<T, 0, Form><<<grid2(L.m1, L.m2), dim3(BX, BY), 0, s>>>(P, L, part);
   ++g_launches;
 }
-template <typename T>
+template <typename T, class Form>
 void launch_add_op(const Prm<T>& P, const Lv<T>& L, cudaStream_t s) {
-  k_residual<T, 1><<<grid2(L.m1, L.m2), dim3(BX, BY), 0, s>>>(P, L, nullptr);
+  k_residual<T, 1, Form><<<grid2(L.m1, L.m2), dim3(BX, BY), 0, s>>>(P, L, nullptr);
   ++g_launches;
 }
-template <typename T>
+template <typename T, class Form>
 void launch_ch(const Prm<T>& P, const Lv<T>& L, int colour, cudaStream_t s) {
-  k_ch<T><<<grid2((L.m1 + 1) / 2, L.m2), dim3(BX, BY), 0, s>>>(P, L, colour);
+  k_ch<T, Form><<<grid2((L.m1 + 1) / 2, L.m2), dim3(BX, BY), 0, s>>>(P, L, colour);
   ++g_launches;
 }
-template <typename T>
+template <typename T, class Form>
 void launch_vanka(const Prm<T>& P, const Lv<T>& L, int colour, T omega, cudaStream_t s) {
   int stride = L.px ? 4 : 5;
-  k_vanka<T><<<grid2((L.m1 + stride - 1) / stride, L.m2), dim3(BX, BY), 0, s>>>(P, L, colour, omega);
+  k_vanka<T, Form><<<grid2((L.m1 + stride - 1) / stride, L.m2), dim3(BX, BY), 0, s>>>(P, L, colour,
+                                                                                       omega);
+  ++g_launches;
+}
+static long long padded_n(int m1, int m2) {
+  long long pitch = ((m1 + 3) + 31) / 32 * 32;
+  return pitch * (m2 + 3);
+}
+template <typename T>
+void launch_cast_frozen(const Lv<double>& D, const Lv<T>& E, cudaStream_t s) {
+  long long n = padded_n(D.m1, D.m2);
+  k_cast_frozen<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(D, E, n, D.pitch + 1);
+  ++g_launches;
+}
+template <typename T>
+void launch_start_correction(const Lv<double>& D, const Lv<T>& E, cudaStream_t s) {
+  long long n = padded_n(D.m1, D.m2);
+  k_start_correction<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(D, E, n, D.pitch + 1);
+  ++g_launches;
+}
+template <typename T>
+void launch_apply_correction(const Lv<double>& D, const Lv<T>& E, cudaStream_t s) {
+  long long n = padded_n(D.m1, D.m2);
+  k_apply_correction<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(D, E, n, D.pitch + 1);
+  ++g_launches;
+}
+template <typename T>
+void launch_restrict_base(const Lv<T>& F, const Lv<T>& C, cudaStream_t s) {
+  k_restrict_base<T><<<grid2(C.m1 + 1, C.m2 + 1), dim3(BX, BY), 0, s>>>(F, C);
+  ++g_launches;
+  int n = frame_threads(C.m1, C.m2);
+  k_bc_base<T><<<(n + 255) / 256, 256, 0, s>>>(C);
   ++g_launches;
 }
 template <typename T>
@@ -858,11 +983,17 @@ int partial_rows_needed(int m1, int m2) {
   return g.x * g.y;
 }
 
+#define QN_INSTANTIATE_FORM(T, F)                                                                \
+  template void launch_residual<T, F>(const Prm<T>&, const Lv<T>&, double*, cudaStream_t);       \
+  template void launch_add_op<T, F>(const Prm<T>&, const Lv<T>&, cudaStream_t);                  \
+  template void launch_ch<T, F>(const Prm<T>&, const Lv<T>&, int, cudaStream_t);                 \
+  template void launch_vanka<T, F>(const Prm<T>&, const Lv<T>&, int, T, cudaStream_t);
+
 #define QN_INSTANTIATE(T)                                                                        \
-  template void launch_residual<T>(const Prm<T>&, const Lv<T>&, double*, cudaStream_t);          \
-  template void launch_add_op<T>(const Prm<T>&, const Lv<T>&, cudaStream_t);                     \
-  template void launch_ch<T>(const Prm<T>&, const Lv<T>&, int, cudaStream_t);                    \
-  template void launch_vanka<T>(const Prm<T>&, const Lv<T>&, int, T, cudaStream_t);              \
+  template void launch_cast_frozen<T>(const Lv<double>&, const Lv<T>&, cudaStream_t);            \
+  template void launch_start_correction<T>(const Lv<double>&, const Lv<T>&, cudaStream_t);       \
+  template void launch_apply_correction<T>(const Lv<double>&, const Lv<T>&, cudaStream_t);       \
+  template void launch_restrict_base<T>(const Lv<T>&, const Lv<T>&, cudaStream_t);               \
   template void launch_bc_unknowns<T>(const Lv<T>&, cudaStream_t);                               \
   template void launch_frozen<T>(const Prm<T>&, const Lv<T>&, cudaStream_t);                     \
   template void launch_restrict_state<T>(const Lv<T>&, const Lv<T>&, cudaStream_t);              \
@@ -881,5 +1012,9 @@ int partial_rows_needed(int m1, int m2) {
   template void launch_pack_out<T>(const Lv<T>&, double*, const T*, int, cudaStream_t);
 
 QN_INSTANTIATE(double)
+QN_INSTANTIATE(float)
+QN_INSTANTIATE_FORM(double, FullForm)
+QN_INSTANTIATE_FORM(double, ErrForm)
+QN_INSTANTIATE_FORM(float, ErrForm)
 
 }  // namespace qn

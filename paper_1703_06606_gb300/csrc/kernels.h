@@ -6,10 +6,18 @@
 
 namespace qn {
 
-template <typename T> void launch_residual(const Prm<T>& P, const Lv<T>& L, double* part, cudaStream_t s);
-template <typename T> void launch_add_op(const Prm<T>& P, const Lv<T>& L, cudaStream_t s);
-template <typename T> void launch_ch(const Prm<T>& P, const Lv<T>& L, int colour, cudaStream_t s);
-template <typename T> void launch_vanka(const Prm<T>& P, const Lv<T>& L, int colour, T omega, cudaStream_t s);
+// Form: FullForm (the iterate is x) or ErrForm (the iterate is a correction e to
+// a base X; the operator is N(X + e) - N(X))
+template <typename T, class Form> void launch_residual(const Prm<T>& P, const Lv<T>& L, double* part, cudaStream_t s);
+template <typename T, class Form> void launch_add_op(const Prm<T>& P, const Lv<T>& L, cudaStream_t s);
+template <typename T, class Form> void launch_ch(const Prm<T>& P, const Lv<T>& L, int colour, cudaStream_t s);
+template <typename T, class Form>
+void launch_vanka(const Prm<T>& P, const Lv<T>& L, int colour, T omega, cudaStream_t s);
+// defect correction: E (error-equation level) from the FP64 level D
+template <typename T> void launch_cast_frozen(const Lv<double>& D, const Lv<T>& E, cudaStream_t s);
+template <typename T> void launch_start_correction(const Lv<double>& D, const Lv<T>& E, cudaStream_t s);
+template <typename T> void launch_apply_correction(const Lv<double>& D, const Lv<T>& E, cudaStream_t s);
+template <typename T> void launch_restrict_base(const Lv<T>& F, const Lv<T>& C, cudaStream_t s);
 template <typename T> void launch_bc_unknowns(const Lv<T>& L, cudaStream_t s);
 template <typename T> void launch_frozen(const Prm<T>& P, const Lv<T>& L, cudaStream_t s);
 template <typename T> void launch_restrict_state(const Lv<T>& F, const Lv<T>& C, cudaStream_t s);

@@ -37,6 +37,9 @@ struct Lv {
   T *sc, *smu, *sp, *su, *sv;  // restricted iterate kept for the correction
   T *cn, *un, *vn;             // frozen level-n data
   T *rhon, *mobn, *visn, *Gn;  // rho(c^n), m(c^n), mu(c^n), G(c^n)
+  // error-equation (defect-correction) levels only: base state X the iterate
+  // e is a correction to, and X.c - c^n formed in FP64 before rounding
+  T *Bc = nullptr, *Bmu = nullptr, *Bu = nullptr, *Bv = nullptr, *Bdc = nullptr;
   __device__ __forceinline__ int at(int i, int j) const { return j * pitch + i; }
   // x-edge unknowns: walls exclude i = 0 and i = m1; periodic keeps i = m1 (= edge 0)
   __device__ __forceinline__ int uhi() const { return px ? m1 : m1 - 1; }
@@ -252,5 +255,172 @@ __device__ __forceinline__ void store_v(const Lv<T>& L, int i, int e, T x) {
     if (i == L.m1) v[k + 1] = -x;
   }
 }
+
+// ---------------------------------------------------------------------------
+// error equation for defect correction: N_e(e) = N(X + e) - N(X) for the
+// iterate e stored in c, mu, p, u, v of the level and the base X in Bc, Bmu, Bu,
+// Bv.  Every nonlinear difference is written with the secant identities of
+// Sec. 4.1 (rho(a) - rho(b) = r(a,b)(a-b), F(a) - F(b) = g(a,b)(a-b)) and the
+// algebraic factorisations below, so that no term is a difference of two
+// nearly equal numbers: in FP32 the result keeps the relative accuracy of e.
+// ---------------------------------------------------------------------------
+
+// r(a,b) = -alpha rho(a) rho(b)
+template <typename T> __device__ __forceinline__ T rsec_(const Prm<T>& P, T ra, T rb) {
+  return -P.alpha * ra * rb;
+}
+// g(a+e, b) - g(a, b) = e/4 [a(a-1) + b(b-1) + (2a - 1 + e)(a + b - 1 + e)]
+template <typename T> __device__ __forceinline__ T dgsec(T a, T b, T e) {
+  return T(0.25) * e * (a * (a - T(1)) + b * (b - T(1)) + (T(2) * a - T(1) + e) * (a + b - T(1) + e));
+}
+
+template <typename T>
+__device__ __forceinline__ T opd_c(const Prm<T>& P, const Lv<T>& L, int k) {
+  const int W = L.pitch;
+  const T* cn = L.cn;
+  const T* rn = L.rhon;
+  T e = L.c[k], C = L.Bc[k];
+  T rp = rho_of(P, C + e), rC = rho_of(P, C);
+  T cnk = cn[k];
+  T adv = T(0.5) * L.ih *
+          (rn[k + 1] * (cn[k + 1] - cnk) * L.u[k] + rn[k - 1] * (cnk - cn[k - 1]) * L.u[k - 1] +
+           rn[k + W] * (cn[k + W] - cnk) * L.v[k] + rn[k - W] * (cnk - cn[k - W]) * L.v[k - W]);
+  T diff = lap_h2(L.mobn, L.mu, k, W) + P.alpha * lap_h2(L.mobn, L.p, k, W);
+  return e * (rp + rsec_(P, rp, rC) * L.Bdc[k]) * P.idt + adv - P.iPe * L.ih2 * diff;
+}
+
+template <typename T>
+__device__ __forceinline__ T opd_mu(const Prm<T>& P, const Lv<T>& L, int k) {
+  const int W = L.pitch;
+  const T *e = L.c, *B = L.Bc, *cn = L.cn, *rn = L.rhon;
+  T ek = e[k], Ck = B[k], cnk = cn[k], rnk = rn[k];
+  T cp = Ck + ek;
+  T rp = rho_of(P, cp), rC = rho_of(P, Ck);
+  T dr = rsec_(P, rp, rC) * ek;             // rho(c') - rho(C)
+  T rhp = T(0.5) * (rp + rnk);              // rho^{n+1/2} at c'
+  T r_new = rsec_(P, rp, rnk);              // r(c', c^n)
+  T d_r = -P.alpha * rnk * dr;              // r(c', c^n) - r(C, c^n)
+  T dF = gsec(cp, Ck) * ek;                 // F(c') - F(C)
+  T dbulk = rhp * dgsec(Ck, cnk, ek) + T(0.5) * dr * gsec(Ck, cnk) + T(0.5) * dF * r_new +
+            T(0.5) * (Fdw(Ck) + Fdw(cnk)) * d_r;
+  // G(c') - G(C) and G(C), both times h^2
+  const int off[4] = {1, -1, W, -W};
+  T dG = T(0), GC = T(0), ddiv = T(0);
+  T chP = Ck + cnk;  // 2 c^{n+1/2} at C
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    int q = k + off[f];
+    T dC = B[q] - Ck, de = e[q] - ek;
+    dG += de * (T(2) * dC + de);
+    GC += dC * dC;
+    T rq = rho_of(P, B[q] + e[q]), rCq = rho_of(P, B[q]);
+    T rhq = T(0.5) * (rq + rn[q]);
+    T drq = rsec_(P, rq, rCq) * e[q];
+    // div(A rho_h(c') grad(e/2)) + div(A d rho_h grad c^{n+1/2}(C)), per face
+    ddiv += (rhp + rhq) * de + T(0.5) * (dr + drq) * ((B[q] + cn[q]) - chP);
+  }
+  dG *= T(0.5);
+  GC *= T(0.5);
+  T dgrad = T(0.25) * P.Lam * (dG * L.ih2 * r_new + (GC * L.ih2 + L.Gn[k]) * d_r);
+  ddiv *= T(0.25) * L.ih2;
+  return rp * L.mu[k] + dr * L.Bmu[k] - P.K * dbulk - dgrad + P.Lam * ddiv;
+}
+
+template <typename T>
+__device__ __forceinline__ T opd_p(const Prm<T>& P, const Lv<T>& L, int k) { return op_p(P, L, k); }
+
+// x row: the terms of op_u that are linear in (u, v, p, mu), applied to e, plus
+// 1/2 (A_x rho(c') - A_x rho^n) e_u/dt + 1/2 A_x(rho(c') - rho(C)) U/dt
+template <typename T>
+__device__ __forceinline__ T opd_u(const Prm<T>& P, const Lv<T>& L, int k) {
+  const int W = L.pitch;
+  const T *u = L.u, *un = L.un, *vn = L.vn, *rn = L.rhon, *vis = L.visn;
+  T ue = u[k];
+  T rl = rn[k], rr = rn[k + 1];
+  T Arn = T(0.5) * (rl + rr);
+  T cl = L.Bc[k] + L.c[k], cr = L.Bc[k + 1] + L.c[k + 1];
+  T rpl = rho_of(P, cl), rpr = rho_of(P, cr);
+  T Arp = T(0.5) * (rpl + rpr);
+  T dAr = T(0.5) * (rsec_(P, rpl, rho_of(P, L.Bc[k])) * L.c[k] +
+                    rsec_(P, rpr, rho_of(P, L.Bc[k + 1])) * L.c[k + 1]);
+  T axl = T(0.5) * (un[k] + un[k - 1]), axr = T(0.5) * (un[k + 1] + un[k]);
+  T dxl = (ue - u[k - 1]) * L.ih, dxr = (u[k + 1] - ue) * L.ih;
+  T dvl = dxl + (L.v[k] - L.v[k - W]) * L.ih;
+  T dvr = dxr + (L.v[k + 1] - L.v[k + 1 - W]) * L.ih;
+  T Art = T(0.25) * (rl + rr + rn[k + W] + rn[k + 1 + W]);
+  T Arb = T(0.25) * (rl + rr + rn[k - W] + rn[k + 1 - W]);
+  T Avt = T(0.25) * (vis[k] + vis[k + 1] + vis[k + W] + vis[k + 1 + W]);
+  T Avb = T(0.25) * (vis[k] + vis[k + 1] + vis[k - W] + vis[k + 1 - W]);
+  T At = T(0.5) * (vn[k + 1] + vn[k]), Ab = T(0.5) * (vn[k + 1 - W] + vn[k - W]);
+  T Dt = (u[k + W] - ue) * L.ih, Db = (ue - u[k - W]) * L.ih;
+  T qt = Art * At, qb = Arb * Ab;
+  T sr = rr * axr, sl = rl * axl;
+  T conv = T(0.5) * (sr * dxr + sl * dxl + qt * Dt + qb * Db);
+  T divc = T(0.5) * ((sr - sl) + (qt - qb)) * L.ih * ue;
+  T time = Arn * ue * P.idt + T(0.5) * (Arp - Arn) * P.idt * ue + T(0.5) * dAr * P.idt * L.Bu[k];
+  T press = (L.p[k + 1] - L.p[k]) * L.ih * P.iM;
+  T st = -T(0.5) * (rr * L.mu[k] + rl * L.mu[k + 1]) * (L.cn[k + 1] - L.cn[k]) * L.ih * P.iM;
+  T vl = vis[k], vr = vis[k + 1];
+  T visc = -P.iRe * L.ih * ((vr * dxr - vl * dxl) + (Avt * Dt - Avb * Db) +
+                            (vr * dvr - vl * dvl) * T(1.0 / 3.0));
+  return time + conv + divc + press + st + visc;
+}
+
+template <typename T>
+__device__ __forceinline__ T opd_v(const Prm<T>& P, const Lv<T>& L, int k) {
+  const int W = L.pitch;
+  const T *v = L.v, *vn = L.vn, *un = L.un, *rn = L.rhon, *vis = L.visn;
+  T ve = v[k];
+  T rb = rn[k], rt = rn[k + W];
+  T Arn = T(0.5) * (rb + rt);
+  T cb = L.Bc[k] + L.c[k], ct = L.Bc[k + W] + L.c[k + W];
+  T rpb = rho_of(P, cb), rpt = rho_of(P, ct);
+  T Arp = T(0.5) * (rpb + rpt);
+  T dAr = T(0.5) * (rsec_(P, rpb, rho_of(P, L.Bc[k])) * L.c[k] +
+                    rsec_(P, rpt, rho_of(P, L.Bc[k + W])) * L.c[k + W]);
+  T ayb = T(0.5) * (vn[k] + vn[k - W]), ayt = T(0.5) * (vn[k + W] + vn[k]);
+  T dyb = (ve - v[k - W]) * L.ih, dyt = (v[k + W] - ve) * L.ih;
+  T dvb = dyb + (L.u[k] - L.u[k - 1]) * L.ih;
+  T dvt = dyt + (L.u[k + W] - L.u[k + W - 1]) * L.ih;
+  T Are = T(0.25) * (rb + rt + rn[k + 1] + rn[k + 1 + W]);
+  T Arw = T(0.25) * (rb + rt + rn[k - 1] + rn[k - 1 + W]);
+  T Ave = T(0.25) * (vis[k] + vis[k + W] + vis[k + 1] + vis[k + 1 + W]);
+  T Avw = T(0.25) * (vis[k] + vis[k + W] + vis[k - 1] + vis[k - 1 + W]);
+  T Ae = T(0.5) * (un[k + W] + un[k]), Aw = T(0.5) * (un[k - 1 + W] + un[k - 1]);
+  T De = (v[k + 1] - ve) * L.ih, Dw = (ve - v[k - 1]) * L.ih;
+  T qe = Are * Ae, qw = Arw * Aw;
+  T st_ = rt * ayt, sb = rb * ayb;
+  T conv = T(0.5) * (qe * De + qw * Dw + st_ * dyt + sb * dyb);
+  T divc = T(0.5) * ((qe - qw) + (st_ - sb)) * L.ih * ve;
+  T time = Arn * ve * P.idt + T(0.5) * (Arp - Arn) * P.idt * ve + T(0.5) * dAr * P.idt * L.Bv[k];
+  T press = (L.p[k + W] - L.p[k]) * L.ih * P.iM;
+  T st = -T(0.5) * (rt * L.mu[k] + rb * L.mu[k + W]) * (L.cn[k + W] - L.cn[k]) * L.ih * P.iM;
+  T vb = vis[k], vt = vis[k + W];
+  T visc = -P.iRe * L.ih * ((Ave * De - Avw * Dw) + (vt * dyt - vb * dyb) +
+                            (vt * dvt - vb * dvb) * T(1.0 / 3.0));
+  return time + conv + divc + press + st + visc;
+}
+
+// Two forms of the iterate: Full (x itself, Sec. 6.1) and Err (correction e to
+// the base X of a defect-correction cycle).  val_c / val_mu return the full
+// value c, mu that the local Jacobians of the smoothers are evaluated at.
+struct FullForm {
+  template <typename T> static __device__ __forceinline__ T val_c(const Lv<T>& L, int k) { return L.c[k]; }
+  template <typename T> static __device__ __forceinline__ T val_mu(const Lv<T>& L, int k) { return L.mu[k]; }
+  template <typename T> static __device__ __forceinline__ T Nc(const Prm<T>& P, const Lv<T>& L, int k) { return op_c(P, L, k); }
+  template <typename T> static __device__ __forceinline__ T Nmu(const Prm<T>& P, const Lv<T>& L, int k) { return op_mu(P, L, k); }
+  template <typename T> static __device__ __forceinline__ T Np(const Prm<T>& P, const Lv<T>& L, int k) { return op_p(P, L, k); }
+  template <typename T> static __device__ __forceinline__ T Nu(const Prm<T>& P, const Lv<T>& L, int k) { return op_u(P, L, k); }
+  template <typename T> static __device__ __forceinline__ T Nv(const Prm<T>& P, const Lv<T>& L, int k) { return op_v(P, L, k); }
+};
+struct ErrForm {
+  template <typename T> static __device__ __forceinline__ T val_c(const Lv<T>& L, int k) { return L.Bc[k] + L.c[k]; }
+  template <typename T> static __device__ __forceinline__ T val_mu(const Lv<T>& L, int k) { return L.Bmu[k] + L.mu[k]; }
+  template <typename T> static __device__ __forceinline__ T Nc(const Prm<T>& P, const Lv<T>& L, int k) { return opd_c(P, L, k); }
+  template <typename T> static __device__ __forceinline__ T Nmu(const Prm<T>& P, const Lv<T>& L, int k) { return opd_mu(P, L, k); }
+  template <typename T> static __device__ __forceinline__ T Np(const Prm<T>& P, const Lv<T>& L, int k) { return opd_p(P, L, k); }
+  template <typename T> static __device__ __forceinline__ T Nu(const Prm<T>& P, const Lv<T>& L, int k) { return opd_u(P, L, k); }
+  template <typename T> static __device__ __forceinline__ T Nv(const Prm<T>& P, const Lv<T>& L, int k) { return opd_v(P, L, k); }
+};
 
 }  // namespace qn

@@ -15,6 +15,8 @@
 #include "kernels.h"
 #include "qnsch.h"
 
+using qn::ErrForm;
+using qn::FullForm;
 using qn::Lv;
 using qn::Prm;
 
@@ -79,10 +81,15 @@ struct qnsch_s {
   // options
   int nu1 = 2, nu2 = 2, nuc = 4, maxcyc = 50;
   double tol = 1e-9, omega = 1.0;
+  // 0: FP64 FAS on the scheme itself; 1: FP64 defect correction around FP32 FAS
+  // cycles on the error equation; 2: the same with FP64 error cycles
+  int precision = 0;
   // grid
   int m1, m2, px, nlev, kcol;
   double h;
   std::vector<Lv<double>> L;
+  std::vector<Lv<float>> Ef;   // error-equation levels, FP32 (precision 1)
+  std::vector<Lv<double>> Ed;  // error-equation levels, FP64 (precision 2)
   std::vector<void*> blocks;
   size_t level_elems0 = 0;
   // committed state, same padded layout as level 0
@@ -211,23 +218,64 @@ int alloc_all(qnsch_s* s) {
   return sync(s);
 }
 
-// a level view whose iterate arrays are the committed state (for packing/energy)
-Lv<double> state_view(const qnsch_s* s) {
-  Lv<double> V = s->L[0];
-  V.c = s->sc;
-  V.mu = s->smu;
-  V.p = s->sp;
-  V.u = s->su;
-  V.v = s->sv;
-  return V;
+constexpr int NFIELD_ERR = NFIELD + 5;  // + base Bc, Bmu, Bu, Bv, Bdc
+
+template <typename T>
+int alloc_err_levels(qnsch_s* s, std::vector<Lv<T>>& E) {
+  if (!E.empty()) return QNSCH_OK;
+  std::vector<Lv<T>> out(s->nlev);
+  for (int l = 0; l < s->nlev; ++l) {
+    const Lv<double>& D = s->L[l];
+    Lv<T>& L = out[l];
+    size_t n = (size_t)D.pitch * (size_t)(D.m2 + 3);
+    T* base = (T*)dev_alloc(n * NFIELD_ERR * sizeof(T));
+    if (!base) return QNSCH_ENOMEM;
+    s->blocks.push_back(base);
+    if (cudaMemsetAsync(base, 0, n * NFIELD_ERR * sizeof(T), s->stream) != cudaSuccess)
+      return QNSCH_ECUDA;
+    L.m1 = D.m1;
+    L.m2 = D.m2;
+    L.px = D.px;
+    L.pitch = D.pitch;
+    L.h = (T)D.h;
+    L.ih = (T)D.ih;
+    L.ih2 = (T)D.ih2;
+    T** f[NFIELD_ERR] = {&L.c,  &L.mu, &L.p,  &L.u,  &L.v,    &L.fc,   &L.fmu,  &L.fp,
+                         &L.fu, &L.fv, &L.rc, &L.rmu, &L.rp,  &L.ru,   &L.rv,   &L.sc,
+                         &L.smu, &L.sp, &L.su, &L.sv, &L.cn,  &L.un,   &L.vn,   &L.rhon,
+                         &L.mobn, &L.visn, &L.Gn, &L.Bc, &L.Bmu, &L.Bu, &L.Bv, &L.Bdc};
+    for (int q = 0; q < NFIELD_ERR; ++q) *f[q] = base + (size_t)q * n + D.pitch + 1;
+  }
+  E.swap(out);
+  return QNSCH_OK;
+}
+
+template <typename T>
+Prm<T> cast_prm(const Prm<double>& P) {
+  Prm<T> Q;
+  Q.ia = (T)P.ia;
+  Q.ib = (T)P.ib;
+  Q.va = (T)P.va;
+  Q.vb = (T)P.vb;
+  Q.alpha = (T)P.alpha;
+  Q.K = (T)P.K;
+  Q.Lam = (T)P.Lam;
+  Q.iM = (T)P.iM;
+  Q.iRe = (T)P.iRe;
+  Q.iPe = (T)P.iPe;
+  Q.Fr_inv = (T)P.Fr_inv;
+  Q.eps_m = (T)P.eps_m;
+  Q.idt = (T)P.idt;
+  return Q;
 }
 
 constexpr int MAX_PROF_EVENTS = 8192;
 
-void smooth(qnsch_s* s, const Prm<double>& P, int l) {
-  const Lv<double>& L = s->L[l];
-  qn::launch_ch(P, L, 0, s->stream);
-  qn::launch_ch(P, L, 1, s->stream);
+template <typename T, class Form>
+void smooth(qnsch_s* s, const std::vector<Lv<T>>& Ls, const Prm<T>& P, int l) {
+  const Lv<T>& L = Ls[l];
+  qn::launch_ch<T, Form>(P, L, 0, s->stream);
+  qn::launch_ch<T, Form>(P, L, 1, s->stream);
   for (int c = 0; c < s->kcol; ++c) {
     bool rec = s->prof && l == 0 && s->ev_used + 2 <= MAX_PROF_EVENTS;
     if (rec) {
@@ -238,12 +286,33 @@ void smooth(qnsch_s* s, const Prm<double>& P, int l) {
       }
     }
     if (rec) cudaEventRecord(s->ev[s->ev_used], s->stream);
-    qn::launch_vanka(P, L, c, s->omega, s->stream);
+    qn::launch_vanka<T, Form>(P, L, c, (T)s->omega, s->stream);
     if (rec) {
       cudaEventRecord(s->ev[s->ev_used + 1], s->stream);
       s->ev_used += 2;
     }
   }
+}
+
+// FAS V-cycle (Sec. 7.1) from level l on the level set Ls
+template <typename T, class Form>
+void vcycle(qnsch_s* s, const std::vector<Lv<T>>& Ls, const Prm<T>& P, int l) {
+  if (l == s->nlev - 1) {
+    for (int k = 0; k < s->nuc; ++k) smooth<T, Form>(s, Ls, P, l);
+    return;
+  }
+  for (int k = 0; k < s->nu1; ++k) smooth<T, Form>(s, Ls, P, l);
+  const Lv<T>& F = Ls[l];
+  const Lv<T>& C = Ls[l + 1];
+  qn::launch_residual<T, Form>(P, F, (double*)nullptr, s->stream);
+  qn::launch_restrict_state(F, C, s->stream);
+  qn::launch_bc_unknowns(C, s->stream);
+  qn::launch_restrict_res(F, C, s->stream);
+  qn::launch_add_op<T, Form>(P, C, s->stream);
+  vcycle<T, Form>(s, Ls, P, l + 1);
+  qn::launch_prolong(F, C, s->stream);
+  qn::launch_bc_unknowns(F, s->stream);
+  for (int k = 0; k < s->nu2; ++k) smooth<T, Form>(s, Ls, P, l);
 }
 
 // fold the recorded event pairs into the totals (stream must be idle)
@@ -259,29 +328,10 @@ void prof_collect(qnsch_s* s) {
   s->ev_used = 0;
 }
 
-void vcycle(qnsch_s* s, const Prm<double>& P, int l) {
-  if (l == s->nlev - 1) {
-    for (int k = 0; k < s->nuc; ++k) smooth(s, P, l);
-    return;
-  }
-  for (int k = 0; k < s->nu1; ++k) smooth(s, P, l);
-  const Lv<double>& F = s->L[l];
-  const Lv<double>& C = s->L[l + 1];
-  qn::launch_residual(P, F, (double*)nullptr, s->stream);
-  qn::launch_restrict_state(F, C, s->stream);
-  qn::launch_bc_unknowns(C, s->stream);
-  qn::launch_restrict_res(F, C, s->stream);
-  qn::launch_add_op(P, C, s->stream);
-  vcycle(s, P, l + 1);
-  qn::launch_prolong(F, C, s->stream);
-  qn::launch_bc_unknowns(F, s->stream);
-  for (int k = 0; k < s->nu2; ++k) smooth(s, P, l);
-}
-
 // finest residual + norms; result left in s->hbuf[0..9] as [l2 x5, max x5]
 int residual_norms(qnsch_s* s, const Prm<double>& P, double* norms10) {
   const Lv<double>& F = s->L[0];
-  qn::launch_residual(P, F, s->part, s->stream);
+  qn::launch_residual<double, FullForm>(P, F, s->part, s->stream);
   qn::launch_norms_finalize(F, s->part, s->scal, s->stream);
   cudaMemcpyAsync(s->hbuf, s->scal, 10 * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
   int rc = sync(s);
@@ -371,13 +421,42 @@ int begin(qnsch_s* s, double dt) {
     qn::launch_restrict_frozen(s->L[l - 1], s->L[l], s->stream);
     qn::launch_frozen(P, s->L[l], s->stream);
   }
+  if (s->precision == 1) {
+    int rc = alloc_err_levels(s, s->Ef);
+    if (rc) return rc;
+    for (int l = 0; l < s->nlev; ++l) qn::launch_cast_frozen(s->L[l], s->Ef[l], s->stream);
+  } else if (s->precision == 2) {
+    int rc = alloc_err_levels(s, s->Ed);
+    if (rc) return rc;
+    for (int l = 0; l < s->nlev; ++l) qn::launch_cast_frozen(s->L[l], s->Ed[l], s->stream);
+  }
   s->pending = 1;
   return cuda_status();
 }
 
+// one defect-correction cycle: e solves N(x + e) - N(x) = r(x) approximately by
+// one FAS V-cycle on the error equation in precision T; then x += e.  Requires
+// the FP64 residual of x in level 0's residual arrays.
+template <typename T>
+void correction_cycle(qnsch_s* s, std::vector<Lv<T>>& E) {
+  Prm<double> P64 = make_prm(s);
+  Prm<T> P = cast_prm<T>(P64);
+  qn::launch_start_correction(s->L[0], E[0], s->stream);
+  for (int l = 1; l < s->nlev; ++l) qn::launch_restrict_base(E[l - 1], E[l], s->stream);
+  vcycle<T, ErrForm>(s, E, P, 0);
+  qn::launch_apply_correction(s->L[0], E[0], s->stream);
+}
+
 int one_cycle(qnsch_s* s, double* norms10) {
   Prm<double> P = make_prm(s);
-  vcycle(s, P, 0);
+  if (s->precision == 0) {
+    vcycle<double, FullForm>(s, s->L, P, 0);
+  } else {
+    // the residual arrays must hold r(x) of the current iterate
+    qn::launch_residual<double, FullForm>(P, s->L[0], (double*)nullptr, s->stream);
+    if (s->precision == 1) correction_cycle<float>(s, s->Ef);
+    else correction_cycle<double>(s, s->Ed);
+  }
   qn::launch_gauge(s->L[0], s->part, s->scal + 16, s->stream);
   int rc = residual_norms(s, P, norms10);
   if (s->prof) prof_collect(s);
@@ -487,7 +566,12 @@ int qnsch_set_option(qnsch_t* s, const char* key, double value) {
   else if (k == "M") s->M = value;
   else if (k == "eta_st") s->eta = value;
   else if (k == "eps_mob") s->eps_m = value;
-  else return QNSCH_EINVAL;
+  else if (k == "precision") {
+    int p = (int)value;
+    if (p < 0 || p > 2 || (double)p != value) return QNSCH_EINVAL;
+    if (s->pending) return QNSCH_ESTATE;
+    s->precision = p;
+  } else return QNSCH_EINVAL;
   return QNSCH_OK;
 }
 
@@ -503,6 +587,7 @@ int qnsch_get_option(const qnsch_t* s, const char* key, double* value) {
   else if (k == "M") *value = s->M;
   else if (k == "eta_st") *value = s->eta;
   else if (k == "eps_mob") *value = s->eps_m;
+  else if (k == "precision") *value = s->precision;
   else return QNSCH_EINVAL;
   return QNSCH_OK;
 }
@@ -728,14 +813,14 @@ int qnsch_residual(qnsch_t* s, double* rc_, double* rmu, double* rp, double* ru,
 int qnsch_smooth_ch(qnsch_t* s, int colour) {
   if (!s || colour < 0 || colour > 1) return QNSCH_EINVAL;
   if (!s->pending) return QNSCH_ESTATE;
-  qn::launch_ch(make_prm(s), s->L[0], colour, s->stream);
+  qn::launch_ch<double, FullForm>(make_prm(s), s->L[0], colour, s->stream);
   return sync(s);
 }
 
 int qnsch_smooth_vanka(qnsch_t* s, int colour) {
   if (!s || colour < 0 || colour >= s->kcol) return QNSCH_EINVAL;
   if (!s->pending) return QNSCH_ESTATE;
-  qn::launch_vanka(make_prm(s), s->L[0], colour, s->omega, s->stream);
+  qn::launch_vanka<double, FullForm>(make_prm(s), s->L[0], colour, s->omega, s->stream);
   return sync(s);
 }
 
@@ -743,7 +828,7 @@ int qnsch_smooth(qnsch_t* s, int sweeps) {
   if (!s || sweeps < 0) return QNSCH_EINVAL;
   if (!s->pending) return QNSCH_ESTATE;
   Prm<double> P = make_prm(s);
-  for (int k = 0; k < sweeps; ++k) smooth(s, P, 0);
+  for (int k = 0; k < sweeps; ++k) smooth<double, FullForm>(s, s->L, P, 0);
   return sync(s);
 }
 

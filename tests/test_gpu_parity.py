@@ -219,3 +219,49 @@ def test_error_statuses(qn):
         g.step(P.dt)
     assert e.value.code == -4
     assert np.array_equal(g.get_fields()["c"], f["c"])  # not committed
+
+
+# ---------------------------------------------------------------------------
+# defect correction on the error equation (precision 2: FP64, 1: FP32 inner)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("m1,m2,px", [(32, 48, False), (32, 48, True)])
+def test_error_form_fp64_cycles_match_oracle(qn, m1, m2, px):
+    """FAS on N(x+e) - N(x) = r(x) followed by x += e is the same algorithm as FAS
+    on N(x) = 0 (the coarse problems differ only by the constant N_H(R x)), so in
+    FP64 its iterates must match the oracle's direct V-cycles."""
+    P = W.small_case(m1, m2, px)
+    g = qn.Solver(**P.create_kwargs(), precision=2)
+    r = RefSolver(**P.create_kwargs())
+    for s in (g, r):
+        s.set_fields(P.fields())
+        s.begin_step(P.dt)
+    for _ in range(3):
+        ng = g.vcycle()
+        nr = r.vcycle()
+        same_fields(g.get_iterate(), r.get_iterate(), 1e-9)
+        assert np.allclose(ng, nr, rtol=1e-5, atol=1e-14)
+
+
+@pytest.mark.parametrize("case", ["small_walls", "small_periodic", "drop_256x512"])
+def test_mixed_precision_step_meets_fp64_tolerance(qn, case):
+    """Precision 1: the FP64 residual meets tol, the fields agree with the FP64
+    oracle's converged step, and mass is conserved to FP64 accuracy."""
+    if case == "drop_256x512":
+        P = W.rising_drop_256x512()
+    else:
+        P = W.small_case(32, 48, case.endswith("periodic"))
+    g = qn.Solver(**P.create_kwargs(), tol=P.tol, precision=1)
+    r = RefSolver(**P.create_kwargs(), tol=P.tol)
+    f = P.fields()
+    g.set_fields(f)
+    r.set_fields(f)
+    m0 = g.mass()
+    ng, resg = g.step(P.dt)
+    nr, resr = r.step(P.dt)
+    assert resg <= P.tol and ng <= nr + 6
+    fg, fr = g.get_fields(), r.get_fields()
+    errs = {k: relerr(fg[k], fr[k]) for k in fg}
+    assert max(errs.values()) <= 1e-7, errs
+    m1 = g.mass()
+    assert abs(m1[0] - m0[0]) <= 1e-12 * m0[0] and abs(m1[1] - m0[1]) <= 1e-12 * m0[1]
