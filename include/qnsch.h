@@ -26,8 +26,12 @@
  * qnsch_destroy.  Arrays passed in are copied; the library keeps no pointer to
  * caller memory.  Device memory comes from the allocator set by
  * qnsch_set_allocator (cudaMalloc/cudaFree by default).  All work is issued on
- * the stream set by qnsch_set_stream (default: the legacy default stream) and
- * every call returns only after that work has completed, unless stated.
+ * the stream set by qnsch_set_stream; without one, on a private stream of the
+ * handle that the device-array calls order after the caller's earlier work on
+ * the legacy default stream.  Every call returns only after its work has
+ * completed, unless stated.  Each outer V-cycle is captured once as a CUDA
+ * graph and replayed (option "graphs", default 1; recaptured when dt or an
+ * option changes).
  *
  * Every call returns an int status: 0 on success, a negative QNSCH_E* code on
  * failure.  On failure no output is written and, unless stated, the handle is
@@ -82,7 +86,17 @@ int qnsch_destroy(qnsch_t* h);
 /* Options (key: default): "nu1": 2, "nu2": 2 (pre/post smoothing steps),
    "nu_coarse": 4 (smoothing steps on the coarsest level), "tol": 1e-9,
    "maxcyc": 50, "omega_vanka": 1, "M": Cn, "eta_st": eta(rho1, rho2),
-   "eps_mob": Cn, "precision": 0.  Unknown keys give QNSCH_EINVAL.
+   "eps_mob": Cn, "precision": 0, "graphs": 1, "fuse_cells": 512,
+   "fuse_cells32": 2048, "coupled": 0.  Unknown keys give QNSCH_EINVAL.
+   coupled: 0 smooths with the paper's separate sweeps (CH 2x2 red-black, then
+   the Vanka 5x5 colours, Sec. 7.1); 1 replaces them by one sweep over the
+   Vanka colours of a coupled 7x7 Newton block in (c, mu, u_W, u_E, v_S, v_N, p).
+   Same fixed point; the coupled block keeps converging on fine grids where the
+   separate sweeps stall (the CH/NS coupling through (alpha/Pe) div(m grad(mu +
+   alpha p)) grows like 1/h^2).
+   fuse_cells / fuse_cells32: the V-cycle on every FP64 / FP32 level with at
+   most this many cells runs in one thread block, one launch for all of them
+   (same arithmetic and order as the per-level launches; 0 disables).
    precision 0: FAS V-cycles in FP64 on the scheme itself.
    precision 1: mixed.  Each outer cycle forms the FP64 residual r = -N(x),
      runs one FAS V-cycle in FP32 on the error equation N(x + e) - N(x) = r

@@ -76,39 +76,45 @@ __global__ void k_finalize(const double* part, int nparts, int nv, int nmax_firs
 // residual r = f - N(x) (mode 0, optional norms) or f += N(x) (mode 1)
 // thread (i,j): cell families at (i,j), u-edge (i,j) and v-edge (i,j)
 // --------------------------------------------------------------------------
+// r = f - N(x) (MODE 0; val receives |r| and r^2 per family) or f += N(x) (MODE 1)
+// at thread (i,j): cell families at (i,j), u-edge (i,j) and v-edge (i,j)
+template <typename T, int MODE, class Form>
+__device__ __forceinline__ void residual_cell(const Prm<T>& P, const Lv<T>& L, int i, int j,
+                                              double (&val)[10]) {
+  int k = L.at(i, j);
+  T nc = Form::Nc(P, L, k), nm = Form::Nmu(P, L, k), np = Form::Np(P, L, k);
+  bool hu = i <= L.uhi(), hv = j < L.m2;
+  T nu = hu ? Form::Nu(P, L, k) : T(0);
+  T nv = hv ? Form::Nv(P, L, k) : T(0);
+  if (MODE == 0) {
+    T r[5] = {L.fc[k] - nc, L.fmu[k] - nm, L.fp[k] - np, hu ? L.fu[k] - nu : T(0),
+              hv ? L.fv[k] - nv : T(0)};
+    L.rc[k] = r[0];
+    L.rmu[k] = r[1];
+    L.rp[k] = r[2];
+    if (hu) L.ru[k] = r[3];
+    if (hv) L.rv[k] = r[4];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      double a = (double)r[q];
+      val[q] = fabs(a);
+      val[5 + q] = a * a;
+    }
+  } else {
+    L.fc[k] += nc;
+    L.fmu[k] += nm;
+    L.fp[k] += np;
+    if (hu) L.fu[k] += nu;
+    if (hv) L.fv[k] += nv;
+  }
+}
+
 template <typename T, int MODE, class Form>
 __global__ void k_residual(Prm<T> P, Lv<T> L, double* part) {
   int i = blockIdx.x * BX + threadIdx.x + 1;
   int j = blockIdx.y * BY + threadIdx.y + 1;
   double val[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};  // max x5 then sum of squares x5
-  if (i <= L.m1 && j <= L.m2) {
-    int k = L.at(i, j);
-    T nc = Form::Nc(P, L, k), nm = Form::Nmu(P, L, k), np = Form::Np(P, L, k);
-    bool hu = i <= L.uhi(), hv = j < L.m2;
-    T nu = hu ? Form::Nu(P, L, k) : T(0);
-    T nv = hv ? Form::Nv(P, L, k) : T(0);
-    if (MODE == 0) {
-      T r[5] = {L.fc[k] - nc, L.fmu[k] - nm, L.fp[k] - np, hu ? L.fu[k] - nu : T(0),
-                hv ? L.fv[k] - nv : T(0)};
-      L.rc[k] = r[0];
-      L.rmu[k] = r[1];
-      L.rp[k] = r[2];
-      if (hu) L.ru[k] = r[3];
-      if (hv) L.rv[k] = r[4];
-#pragma unroll
-      for (int q = 0; q < 5; ++q) {
-        double a = (double)r[q];
-        val[q] = fabs(a);
-        val[5 + q] = a * a;
-      }
-    } else {
-      L.fc[k] += nc;
-      L.fmu[k] += nm;
-      L.fp[k] += np;
-      if (hu) L.fu[k] += nu;
-      if (hv) L.fv[k] += nv;
-    }
-  }
+  if (i <= L.m1 && j <= L.m2) residual_cell<T, MODE, Form>(P, L, i, j, val);
   if (MODE == 0 && part) block_sum_store<10>(val, part, 5);
 }
 
@@ -117,13 +123,11 @@ __global__ void k_residual(Prm<T> P, Lv<T> L, double* part) {
 // of each cell with (i + j) % 2 == colour; neighbours frozen.  Faces on
 // Neumann walls do not contribute (their ghost follows the cell).
 // --------------------------------------------------------------------------
+// The 2x2 CH system of cell (i,j): residuals R = N - f of (N_c, N_mu) and their
+// Jacobian J in (c, mu), neighbours frozen, at the full values c, mu
 template <typename T, class Form>
-__global__ void k_ch(Prm<T> P, Lv<T> L, int colour) {
-  int j = blockIdx.y * BY + threadIdx.y + 1;
-  if (j > L.m2) return;
-  int i0 = ((colour - j) & 1) ? 1 : 2;
-  int i = i0 + 2 * (blockIdx.x * BX + threadIdx.x);
-  if (i > L.m1) return;
+__device__ __forceinline__ void ch_system(const Prm<T>& P, const Lv<T>& L, int i, int j,
+                                          T (&J)[2][2], T (&R)[2]) {
   const int W = L.pitch;
   int k = L.at(i, j);
   T Rc = Form::Nc(P, L, k) - L.fc[k];
@@ -160,11 +164,34 @@ __global__ void k_ch(Prm<T> P, Lv<T> L, int colour) {
   T dgrad = T(0.25) * P.Lam * (dG * L.ih2 * r + Gs * dr);
   T J21 = drho * mk - P.K * dbulk - dgrad + P.Lam * T(0.25) * L.ih2 * dd;
   T J22 = rho;
-  T idet = T(1) / (J11 * J22 - J12 * J21);
-  T dc = (J22 * Rc - J12 * Rm) * idet;
-  T dm = (J11 * Rm - J21 * Rc) * idet;
+  J[0][0] = J11;
+  J[0][1] = J12;
+  J[1][0] = J21;
+  J[1][1] = J22;
+  R[0] = Rc;
+  R[1] = Rm;
+}
+
+template <typename T, class Form>
+__device__ __forceinline__ void ch_cell(const Prm<T>& P, const Lv<T>& L, int i, int j) {
+  T J[2][2], R[2];
+  ch_system<T, Form>(P, L, i, j, J, R);
+  T idet = T(1) / (J[0][0] * J[1][1] - J[0][1] * J[1][0]);
+  T dc = (J[1][1] * R[0] - J[0][1] * R[1]) * idet;
+  T dm = (J[0][0] * R[1] - J[1][0] * R[0]) * idet;
+  int k = L.at(i, j);
   store_cell(L, L.c, i, j, L.c[k] - dc);
   store_cell(L, L.mu, i, j, L.mu[k] - dm);
+}
+
+template <typename T, class Form>
+__global__ void k_ch(Prm<T> P, Lv<T> L, int colour) {
+  int j = blockIdx.y * BY + threadIdx.y + 1;
+  if (j > L.m2) return;
+  int i0 = ((colour - j) & 1) ? 1 : 2;
+  int i = i0 + 2 * (blockIdx.x * BX + threadIdx.x);
+  if (i > L.m1) return;
+  ch_cell<T, Form>(P, L, i, j);
 }
 
 // --------------------------------------------------------------------------
@@ -212,32 +239,23 @@ __device__ __forceinline__ void solve5(T (&A)[5][5], T (&b)[5]) {
   }
 }
 
+// The 5x5 Vanka system of cell (i,j): A = Jacobian of (N_u W, N_u E, N_v S,
+// N_v N, N_p) in (u_W, u_E, v_S, v_N, p), b = residuals N - f; rows and
+// columns of wall edges (act = false) replaced by the identity
 template <typename T, class Form>
-__global__ void k_vanka(Prm<T> P, Lv<T> L, int colour, T omega) {
-  int j = blockIdx.y * BY + threadIdx.y + 1;
-  if (j > L.m2) return;
-  int i0, stride;
-  if (L.px) {
-    int d = (colour - j) & 7;
-    if (d & 1) return;  // no cell of this colour in row j
-    i0 = d >> 1;
-    if (i0 == 0) i0 = 4;
-    stride = 4;
-  } else {
-    i0 = ((colour - 2 * j) % 5 + 5) % 5;
-    if (i0 == 0) i0 = 5;
-    stride = 5;
-  }
-  int i = i0 + stride * (blockIdx.x * BX + threadIdx.x);
-  if (i > L.m1) return;
+__device__ __forceinline__ void vanka_system(const Prm<T>& P, const Lv<T>& L, int i, int j,
+                                             T (&A)[5][5], T (&b)[5], bool (&act)[5]) {
   const int W = L.pitch;
   const T ih = L.ih, ih2 = L.ih2;
   const T *rn = L.rhon, *vis = L.visn, *un = L.un, *vn = L.vn;
   int k = L.at(i, j);
   int eW = (L.px && i == 1) ? L.m1 : i - 1;
   int kW = L.at(eW, j);
-  bool act[5] = {L.px || i > 1, L.px || i < L.m1, j > 1, j < L.m2, true};
-  T A[5][5], b[5];
+  act[0] = L.px || i > 1;
+  act[1] = L.px || i < L.m1;
+  act[2] = j > 1;
+  act[3] = j < L.m2;
+  act[4] = true;
 #pragma unroll
   for (int r = 0; r < 5; ++r)
 #pragma unroll
@@ -335,12 +353,193 @@ __global__ void k_vanka(Prm<T> P, Lv<T> L, int colour, T omega) {
       for (int c = 0; c < 5; ++c) { A[q][c] = T(0); A[c][q] = T(0); }
       A[q][q] = T(1);
     }
+}
+
+template <typename T, class Form>
+__device__ __forceinline__ void vanka_cell(const Prm<T>& P, const Lv<T>& L, int i, int j, T omega) {
+  T A[5][5], b[5];
+  bool act[5];
+  vanka_system<T, Form>(P, L, i, j, A, b, act);
   solve5(A, b);
+  const int W = L.pitch;
+  int k = L.at(i, j);
+  int eW = (L.px && i == 1) ? L.m1 : i - 1;
+  int kW = L.at(eW, j);
   if (act[0]) store_u(L, eW, j, L.u[kW] - omega * b[0]);
   if (act[1]) store_u(L, i, j, L.u[k] - omega * b[1]);
   if (act[2]) store_v(L, i, j - 1, L.v[k - W] - omega * b[2]);
   if (act[3]) store_v(L, i, j, L.v[k] - omega * b[3]);
   store_cell(L, L.p, i, j, L.p[k] - omega * b[4]);
+}
+
+// Gaussian elimination with partial pivoting (compare-and-swap) on a 7x7 system
+template <typename T>
+__device__ __forceinline__ void solve7(T (&A)[7][7], T (&b)[7]) {
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+#pragma unroll
+    for (int r = k + 1; r < 7; ++r) {
+      if (fabs(A[r][k]) > fabs(A[k][k])) {
+#pragma unroll
+        for (int c = k; c < 7; ++c) {
+          T t = A[k][c];
+          A[k][c] = A[r][c];
+          A[r][c] = t;
+        }
+        T t = b[k];
+        b[k] = b[r];
+        b[r] = t;
+      }
+    }
+    T inv = T(1) / A[k][k];
+#pragma unroll
+    for (int r = k + 1; r < 7; ++r) {
+      T l = A[r][k] * inv;
+#pragma unroll
+      for (int c = k + 1; c < 7; ++c) A[r][c] -= l * A[k][c];
+      b[r] -= l * b[k];
+    }
+    A[k][k] = inv;
+  }
+#pragma unroll
+  for (int k = 6; k >= 0; --k) {
+    T t = b[k];
+#pragma unroll
+    for (int c = k + 1; c < 7; ++c) t -= A[k][c] * b[c];
+    b[k] = t * A[k][k];
+  }
+}
+
+// Coupled block (an option; the paper's smoother keeps the two blocks
+// separate): one Newton step on the 7x7 system of (N_c, N_mu, N_u W, N_u E,
+// N_v S, N_v N, N_p) in (c, mu, u_W, u_E, v_S, v_N, p).  It adds to the 2x2 CH
+// and 5x5 Vanka blocks the couplings the separate smoothers treat explicitly:
+// the CH advection (e1e2) and (alpha/Pe) grad.(A m grad p) in N_c, the
+// (alpha/Pe) grad.(A m grad mu) term of N_p, and the rho(c) and surface-tension
+// (e1e1) terms of the momentum rows.
+template <typename T, class Form>
+__device__ __forceinline__ void coupled_cell(const Prm<T>& P, const Lv<T>& L, int i, int j, T omega) {
+  T A5[5][5], b5[5], J2[2][2], R2[2];
+  bool act[5];
+  vanka_system<T, Form>(P, L, i, j, A5, b5, act);
+  ch_system<T, Form>(P, L, i, j, J2, R2);
+  T A[7][7], b[7];
+#pragma unroll
+  for (int r = 0; r < 7; ++r)
+#pragma unroll
+    for (int c = 0; c < 7; ++c) A[r][c] = T(0);
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+    b[2 + r] = b5[r];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) A[2 + r][2 + c] = A5[r][c];
+  }
+  A[0][0] = J2[0][0];
+  A[0][1] = J2[0][1];
+  A[1][0] = J2[1][0];
+  A[1][1] = J2[1][1];
+  b[0] = R2[0];
+  b[1] = R2[1];
+  const int W = L.pitch;
+  int k = L.at(i, j);
+  int eW = (L.px && i == 1) ? L.m1 : i - 1;
+  int kW = L.at(eW, j);
+  const T *rn = L.rhon, *cn = L.cn, *mob = L.mobn;
+  bool wall[4] = {!L.px && i == L.m1, !L.px && i == 1, j == L.m2, j == 1};
+  const int off[4] = {1, -1, W, -W};
+  T sm = T(0);
+#pragma unroll
+  for (int f = 0; f < 4; ++f)
+    if (!wall[f]) sm += mob[k] + mob[k + off[f]];
+  T cfull = Form::val_c(L, k);
+  T rho = rho_of(P, cfull), drho = -P.alpha * rho * rho;
+  // rho^n D c^n / 2 at the four faces of the cell, as in (e1e2) and (e1e1)
+  T gW = T(0.5) * rn[k - 1] * (cn[k] - cn[k - 1]) * L.ih;
+  T gE = T(0.5) * rn[k + 1] * (cn[k + 1] - cn[k]) * L.ih;
+  T gS = T(0.5) * rn[k - W] * (cn[k] - cn[k - W]) * L.ih;
+  T gN = T(0.5) * rn[k + W] * (cn[k + W] - cn[k]) * L.ih;
+  T diffc = T(0.5) * P.alpha * P.iPe * sm * L.ih2;
+  A[0][2] = gW;
+  A[0][3] = gE;
+  A[0][4] = gS;
+  A[0][5] = gN;
+  A[0][6] = diffc;
+  T half_idt = T(0.25) * drho * P.idt;  // d/dc of (A rho(c) - A rho^n) x / (2 dt), per edge
+  A[2][0] = half_idt * Form::val_u(L, kW);
+  A[3][0] = half_idt * Form::val_u(L, k);
+  A[4][0] = half_idt * Form::val_v(L, k - W);
+  A[5][0] = half_idt * Form::val_v(L, k);
+  A[2][1] = -gW * P.iM;
+  A[3][1] = -gE * P.iM;
+  A[4][1] = -gS * P.iM;
+  A[5][1] = -gN * P.iM;
+  A[6][1] = diffc;
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (!act[q]) {
+#pragma unroll
+      for (int c = 0; c < 7; ++c) {
+        A[2 + q][c] = T(0);
+        A[c][2 + q] = T(0);
+      }
+      A[2 + q][2 + q] = T(1);
+    }
+  solve7(A, b);
+  store_cell(L, L.c, i, j, L.c[k] - omega * b[0]);
+  store_cell(L, L.mu, i, j, L.mu[k] - omega * b[1]);
+  if (act[0]) store_u(L, eW, j, L.u[kW] - omega * b[2]);
+  if (act[1]) store_u(L, i, j, L.u[k] - omega * b[3]);
+  if (act[2]) store_v(L, i, j - 1, L.v[k - W] - omega * b[4]);
+  if (act[3]) store_v(L, i, j, L.v[k] - omega * b[5]);
+  store_cell(L, L.p, i, j, L.p[k] - omega * b[6]);
+}
+
+// Vanka colour of cell (i,j): (i + 2j) mod 5 with walls in x, (2i + j) mod 8 periodic
+template <typename T>
+__device__ __forceinline__ int vanka_colour(const Lv<T>& L, int i, int j) {
+  return L.px ? (2 * i + j) & 7 : (i + 2 * j) % 5;
+}
+
+template <typename T, class Form>
+__global__ void k_vanka(Prm<T> P, Lv<T> L, int colour, T omega) {
+  int j = blockIdx.y * BY + threadIdx.y + 1;
+  if (j > L.m2) return;
+  int i0, stride;
+  if (L.px) {
+    int d = (colour - j) & 7;
+    if (d & 1) return;  // no cell of this colour in row j
+    i0 = d >> 1;
+    if (i0 == 0) i0 = 4;
+    stride = 4;
+  } else {
+    i0 = ((colour - 2 * j) % 5 + 5) % 5;
+    if (i0 == 0) i0 = 5;
+    stride = 5;
+  }
+  int i = i0 + stride * (blockIdx.x * BX + threadIdx.x);
+  if (i > L.m1) return;
+  vanka_cell<T, Form>(P, L, i, j, omega);
+}
+
+template <typename T, class Form>
+__global__ void __launch_bounds__(BX * BY) k_coupled(Prm<T> P, Lv<T> L, int colour, T omega) {
+  int j = blockIdx.y * BY + threadIdx.y + 1;
+  if (j > L.m2) return;
+  int i0, stride;
+  if (L.px) {
+    int d = (colour - j) & 7;
+    if (d & 1) return;
+    i0 = d >> 1;
+    if (i0 == 0) i0 = 4;
+    stride = 4;
+  } else {
+    i0 = ((colour - 2 * j) % 5 + 5) % 5;
+    if (i0 == 0) i0 = 5;
+    stride = 5;
+  }
+  int i = i0 + stride * (blockIdx.x * BX + threadIdx.x);
+  if (i > L.m1) return;
+  coupled_cell<T, Form>(P, L, i, j, omega);
 }
 
 // --------------------------------------------------------------------------
@@ -473,10 +672,7 @@ __global__ void k_frozen_derived(Prm<T> P, Lv<T> L) {
 // coarse iterate = R x_h (cells: 4-mean; edges: mean of the 2 coincident fine edges),
 // and a copy kept for the correction
 template <typename T>
-__global__ void k_restrict_state(Lv<T> F, Lv<T> C) {
-  int I = blockIdx.x * BX + threadIdx.x;
-  int J = blockIdx.y * BY + threadIdx.y;
-  if (I > C.m1 || J > C.m2) return;
+__device__ __forceinline__ void restrict_state_cell(const Lv<T>& F, const Lv<T>& C, int I, int J) {
   int kc = C.at(I, J);
   if (I >= 1 && J >= 1) {
     int kf = F.at(2 * I - 1, 2 * J - 1), W = F.pitch;
@@ -499,6 +695,16 @@ __global__ void k_restrict_state(Lv<T> F, Lv<T> C) {
   }
 }
 
+// coarse iterate = R x_h (cells: 4-mean; edges: mean of the 2 coincident fine edges),
+// and a copy kept for the correction
+template <typename T>
+__global__ void k_restrict_state(Lv<T> F, Lv<T> C) {
+  int I = blockIdx.x * BX + threadIdx.x;
+  int J = blockIdx.y * BY + threadIdx.y;
+  if (I > C.m1 || J > C.m2) return;
+  restrict_state_cell(F, C, I, J);
+}
+
 template <typename T>
 __device__ __forceinline__ T ru_at(const Lv<T>& F, int i, int j) {
   if (F.px) {
@@ -518,10 +724,7 @@ __device__ __forceinline__ T rv_at(const Lv<T>& F, int i, int j) {
 // coarse right-hand side f_H = R r_h (cells: 4-mean; edges: full weighting),
 // to which k_residual<MODE 1> then adds N_H(R x_h)
 template <typename T>
-__global__ void k_restrict_res(Lv<T> F, Lv<T> C) {
-  int I = blockIdx.x * BX + threadIdx.x + 1;
-  int J = blockIdx.y * BY + threadIdx.y + 1;
-  if (I > C.m1 || J > C.m2) return;
+__device__ __forceinline__ void restrict_res_cell(const Lv<T>& F, const Lv<T>& C, int I, int J) {
   int kc = C.at(I, J);
   int kf = F.at(2 * I - 1, 2 * J - 1), W = F.pitch;
   C.fc[kc] = T(0.25) * (F.rc[kf] + F.rc[kf + 1] + F.rc[kf + W] + F.rc[kf + W + 1]);
@@ -550,6 +753,14 @@ __global__ void k_restrict_res(Lv<T> F, Lv<T> C) {
 }
 
 template <typename T>
+__global__ void k_restrict_res(Lv<T> F, Lv<T> C) {
+  int I = blockIdx.x * BX + threadIdx.x + 1;
+  int J = blockIdx.y * BY + threadIdx.y + 1;
+  if (I > C.m1 || J > C.m2) return;
+  restrict_res_cell(F, C, I, J);
+}
+
+template <typename T>
 __global__ void k_restrict_frozen(Lv<T> F, Lv<T> C) {
   int I = blockIdx.x * BX + threadIdx.x;
   int J = blockIdx.y * BY + threadIdx.y;
@@ -572,10 +783,7 @@ __global__ void k_restrict_frozen(Lv<T> F, Lv<T> C) {
 // x_h += P(x_H - saved_H): cells piecewise constant; edges coincident or linear
 // in the normal direction, constant in the tangential direction
 template <typename T>
-__global__ void k_prolong(Lv<T> F, Lv<T> C) {
-  int i = blockIdx.x * BX + threadIdx.x + 1;
-  int j = blockIdx.y * BY + threadIdx.y + 1;
-  if (i > F.m1 || j > F.m2) return;
+__device__ __forceinline__ void prolong_cell(const Lv<T>& F, const Lv<T>& C, int i, int j) {
   int k = F.at(i, j);
   int I = (i + 1) >> 1, J = (j + 1) >> 1;
   int kc = C.at(I, J);
@@ -603,6 +811,106 @@ __global__ void k_prolong(Lv<T> F, Lv<T> C) {
       e = T(0.5) * ((C.v[q0] - C.sv[q0]) + (C.v[q1] - C.sv[q1]));
     }
     F.v[k] += e;
+  }
+}
+
+template <typename T>
+__global__ void k_prolong(Lv<T> F, Lv<T> C) {
+  int i = blockIdx.x * BX + threadIdx.x + 1;
+  int j = blockIdx.y * BY + threadIdx.y + 1;
+  if (i > F.m1 || j > F.m2) return;
+  prolong_cell(F, C, i, j);
+}
+
+// --------------------------------------------------------------------------
+// the coarse end of a V-cycle in one thread block: levels small enough for one
+// SM run their smoothing colours, residuals, transfers and ghost fills as
+// block-stride loops separated by __syncthreads(), one launch instead of
+// dozens.  Per-cell work is the same device code as the grid kernels above,
+// in the same colour order, so the results are the same.
+// --------------------------------------------------------------------------
+template <typename T>
+struct CoarseLevels {
+  Lv<T> L[QN_MAX_FUSED_LEVELS];
+  int n;
+};
+
+template <typename T>
+__device__ __forceinline__ void bc_unknowns_block(const Lv<T>& L) {
+  int n = 4 * (L.m1 + 3) + 4 * (L.m2 + 3);
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    int I, J;
+    if (!frame_pos(t, L.m1, L.m2, I, J)) continue;
+    fill_cell_ghost(L, L.c, I, J);
+    fill_cell_ghost(L, L.mu, I, J);
+    fill_cell_ghost(L, L.p, I, J);
+    fill_u_ghost(L, L.u, I, J);
+    fill_v_ghost(L, L.v, I, J);
+  }
+  __syncthreads();
+}
+
+template <typename T, class Form>
+__device__ void smooth_block(const Prm<T>& P, const Lv<T>& L, int kcol, T omega, int coupled) {
+  int n = L.m1 * L.m2;
+  if (coupled) {
+    for (int col = 0; col < kcol; ++col) {
+      for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        int i = t % L.m1 + 1, j = t / L.m1 + 1;
+        if (vanka_colour(L, i, j) == col) coupled_cell<T, Form>(P, L, i, j, omega);
+      }
+      __syncthreads();
+    }
+    return;
+  }
+  for (int col = 0; col < 2; ++col) {
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+      int i = t % L.m1 + 1, j = t / L.m1 + 1;
+      if (((i + j) & 1) == col) ch_cell<T, Form>(P, L, i, j);
+    }
+    __syncthreads();
+  }
+  for (int col = 0; col < kcol; ++col) {
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+      int i = t % L.m1 + 1, j = t / L.m1 + 1;
+      if (vanka_colour(L, i, j) == col) vanka_cell<T, Form>(P, L, i, j, omega);
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T, class Form, int NT>
+__global__ void __launch_bounds__(NT) k_coarse_vcycle(Prm<T> P, CoarseLevels<T> C, int nu1, int nu2,
+                                                      int nuc, int kcol, T omega, int coupled) {
+  const int n = C.n;
+  double dummy[10];
+  for (int l = 0; l < n - 1; ++l) {
+    const Lv<T>& F = C.L[l];
+    const Lv<T>& G = C.L[l + 1];
+    for (int s = 0; s < nu1; ++s) smooth_block<T, Form>(P, F, kcol, omega, coupled);
+    for (int t = threadIdx.x; t < F.m1 * F.m2; t += NT)
+      residual_cell<T, 0, Form>(P, F, t % F.m1 + 1, t / F.m1 + 1, dummy);
+    __syncthreads();
+    for (int t = threadIdx.x; t < (G.m1 + 1) * (G.m2 + 1); t += NT)
+      restrict_state_cell(F, G, t % (G.m1 + 1), t / (G.m1 + 1));
+    __syncthreads();
+    bc_unknowns_block(G);
+    for (int t = threadIdx.x; t < G.m1 * G.m2; t += NT)
+      restrict_res_cell(F, G, t % G.m1 + 1, t / G.m1 + 1);
+    __syncthreads();
+    for (int t = threadIdx.x; t < G.m1 * G.m2; t += NT)
+      residual_cell<T, 1, Form>(P, G, t % G.m1 + 1, t / G.m1 + 1, dummy);
+    __syncthreads();
+  }
+  for (int s = 0; s < nuc; ++s) smooth_block<T, Form>(P, C.L[n - 1], kcol, omega, coupled);
+  for (int l = n - 2; l >= 0; --l) {
+    const Lv<T>& F = C.L[l];
+    const Lv<T>& G = C.L[l + 1];
+    for (int t = threadIdx.x; t < F.m1 * F.m2; t += NT)
+      prolong_cell(F, G, t % F.m1 + 1, t / F.m1 + 1);
+    __syncthreads();
+    bc_unknowns_block(F);
+    for (int s = 0; s < nu2; ++s) smooth_block<T, Form>(P, F, kcol, omega, coupled);
   }
 }
 
@@ -857,6 +1165,25 @@ void launch_vanka(const Prm<T>& P, const Lv<T>& L, int colour, T omega, cudaStre
                                                                                        omega);
   ++g_launches;
 }
+template <typename T, class Form>
+void launch_coarse_vcycle(const Prm<T>& P, const Lv<T>* levels, int n, int nu1, int nu2, int nuc,
+                          int kcol, T omega, int coupled, cudaStream_t s) {
+  CoarseLevels<T> C;
+  C.n = n;
+  for (int l = 0; l < n; ++l) C.L[l] = levels[l];
+  constexpr int NT = sizeof(T) == 8 ? 256 : 512;
+  k_coarse_vcycle<T, Form, NT><<<1, NT, 0, s>>>(P, C, nu1, nu2, nuc, kcol, omega, coupled);
+  ++g_launches;
+}
+
+template <typename T, class Form>
+void launch_coupled(const Prm<T>& P, const Lv<T>& L, int colour, T omega, cudaStream_t s) {
+  int stride = L.px ? 4 : 5;
+  k_coupled<T, Form><<<grid2((L.m1 + stride - 1) / stride, L.m2), dim3(BX, BY), 0, s>>>(P, L, colour,
+                                                                                         omega);
+  ++g_launches;
+}
+
 static long long padded_n(int m1, int m2) {
   long long pitch = ((m1 + 3) + 31) / 32 * 32;
   return pitch * (m2 + 3);
@@ -984,6 +1311,9 @@ int partial_rows_needed(int m1, int m2) {
 }
 
 #define QN_INSTANTIATE_FORM(T, F)                                                                \
+  template void launch_coarse_vcycle<T, F>(const Prm<T>&, const Lv<T>*, int, int, int, int, int,  \
+                                           T, int, cudaStream_t);                                \
+  template void launch_coupled<T, F>(const Prm<T>&, const Lv<T>&, int, T, cudaStream_t);          \
   template void launch_residual<T, F>(const Prm<T>&, const Lv<T>&, double*, cudaStream_t);       \
   template void launch_add_op<T, F>(const Prm<T>&, const Lv<T>&, cudaStream_t);                  \
   template void launch_ch<T, F>(const Prm<T>&, const Lv<T>&, int, cudaStream_t);                 \

@@ -6,6 +6,9 @@
 
 namespace qn {
 
+// most levels one fused coarse-level V-cycle launch can hold
+#define QN_MAX_FUSED_LEVELS 10
+
 // Form: FullForm (the iterate is x) or ErrForm (the iterate is a correction e to
 // a base X; the operator is N(X + e) - N(X))
 template <typename T, class Form> void launch_residual(const Prm<T>& P, const Lv<T>& L, double* part, cudaStream_t s);
@@ -13,6 +16,13 @@ template <typename T, class Form> void launch_add_op(const Prm<T>& P, const Lv<T
 template <typename T, class Form> void launch_ch(const Prm<T>& P, const Lv<T>& L, int colour, cudaStream_t s);
 template <typename T, class Form>
 void launch_vanka(const Prm<T>& P, const Lv<T>& L, int colour, T omega, cudaStream_t s);
+// the V-cycle on levels[0..n-1] (levels[0] is its finest) in one thread block
+template <typename T, class Form>
+void launch_coarse_vcycle(const Prm<T>& P, const Lv<T>* levels, int n, int nu1, int nu2, int nuc,
+                          int kcol, T omega, int coupled, cudaStream_t s);
+// one colour of the coupled 7x7 smoother (option "coupled")
+template <typename T, class Form>
+void launch_coupled(const Prm<T>& P, const Lv<T>& L, int colour, T omega, cudaStream_t s);
 // defect correction: E (error-equation level) from the FP64 level D
 template <typename T> void launch_cast_frozen(const Lv<double>& D, const Lv<T>& E, cudaStream_t s);
 template <typename T> void launch_start_correction(const Lv<double>& D, const Lv<T>& E, cudaStream_t s);

@@ -406,6 +406,8 @@ __device__ __forceinline__ T opd_v(const Prm<T>& P, const Lv<T>& L, int k) {
 // value c, mu that the local Jacobians of the smoothers are evaluated at.
 struct FullForm {
   template <typename T> static __device__ __forceinline__ T val_c(const Lv<T>& L, int k) { return L.c[k]; }
+  template <typename T> static __device__ __forceinline__ T val_u(const Lv<T>& L, int k) { return L.u[k]; }
+  template <typename T> static __device__ __forceinline__ T val_v(const Lv<T>& L, int k) { return L.v[k]; }
   template <typename T> static __device__ __forceinline__ T val_mu(const Lv<T>& L, int k) { return L.mu[k]; }
   template <typename T> static __device__ __forceinline__ T Nc(const Prm<T>& P, const Lv<T>& L, int k) { return op_c(P, L, k); }
   template <typename T> static __device__ __forceinline__ T Nmu(const Prm<T>& P, const Lv<T>& L, int k) { return op_mu(P, L, k); }
@@ -415,6 +417,8 @@ struct FullForm {
 };
 struct ErrForm {
   template <typename T> static __device__ __forceinline__ T val_c(const Lv<T>& L, int k) { return L.Bc[k] + L.c[k]; }
+  template <typename T> static __device__ __forceinline__ T val_u(const Lv<T>& L, int k) { return L.Bu[k] + L.u[k]; }
+  template <typename T> static __device__ __forceinline__ T val_v(const Lv<T>& L, int k) { return L.Bv[k] + L.v[k]; }
   template <typename T> static __device__ __forceinline__ T val_mu(const Lv<T>& L, int k) { return L.Bmu[k] + L.mu[k]; }
   template <typename T> static __device__ __forceinline__ T Nc(const Prm<T>& P, const Lv<T>& L, int k) { return opd_c(P, L, k); }
   template <typename T> static __device__ __forceinline__ T Nmu(const Prm<T>& P, const Lv<T>& L, int k) { return opd_mu(P, L, k); }

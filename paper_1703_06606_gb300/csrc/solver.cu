@@ -22,6 +22,11 @@ using qn::Prm;
 
 namespace {
 
+// kernels queued into captured graphs (not executed at capture time) and
+// kernels executed by graph replays, for qnsch_kernel_launches
+long long g_captured = 0;
+long long g_replayed = 0;
+
 void* (*g_alloc)(size_t, void*) = nullptr;
 void (*g_free)(void*, void*) = nullptr;
 void* g_ctx = nullptr;
@@ -84,6 +89,11 @@ struct qnsch_s {
   // 0: FP64 FAS on the scheme itself; 1: FP64 defect correction around FP32 FAS
   // cycles on the error equation; 2: the same with FP64 error cycles
   int precision = 0;
+  // levels with at most this many cells run as one fused single-block V-cycle
+  // (0: never); separate thresholds for FP64 and FP32 levels
+  int fuse64 = 512, fuse32 = 2048;
+  // 0: the paper's separate CH and Vanka sweeps; 1: the coupled 7x7 block
+  int coupled = 0;
   // grid
   int m1, m2, px, nlev, kcol;
   double h;
@@ -99,8 +109,21 @@ struct qnsch_s {
   double* scal = nullptr;  // [0..9] norms, [16] p sum, [20..21] mass, [24] energy, [25] diss
   double* hbuf = nullptr;  // pinned host mirror of scal
   double* stage = nullptr;  // device staging buffer for host-array I/O (one field)
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;       // work stream: the user's, else own_stream
+  cudaStream_t user_stream = nullptr;  // set by qnsch_set_stream (NULL: legacy default stream)
+  cudaStream_t own_stream = nullptr;   // non-blocking stream used when user_stream is NULL
+  cudaEvent_t ev_entry = nullptr;      // orders own_stream after the legacy stream at entry
   int pending = 0;
+  // one outer cycle captured as a CUDA graph and replayed (option "graphs")
+  int use_graphs = 1;
+  unsigned opt_version = 0;
+  cudaGraphExec_t gexec = nullptr;
+  double g_dt = -1.0;
+  int g_precision = -1, g_prof = -1, g_ev_used = 0;
+  unsigned g_opt = ~0u;
+  long long g_nodes = 0;  // kernels in the captured graph
+  // the FP64 residual arrays of level 0 hold r(x) of the current iterate
+  int res_valid = 0;
   // optional CUDA-event timing of the finest-level Vanka launches
   int prof = 0;
   std::vector<cudaEvent_t> ev;
@@ -152,8 +175,14 @@ size_t padded_elems(int m1, int m2, int* pitch) {
 }
 
 void free_all(qnsch_s* s) {
+  if (s->gexec) cudaGraphExecDestroy(s->gexec);
+  s->gexec = nullptr;
   for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
   s->ev.clear();
+  if (s->ev_entry) cudaEventDestroy(s->ev_entry);
+  s->ev_entry = nullptr;
+  if (s->own_stream) cudaStreamDestroy(s->own_stream);
+  s->own_stream = nullptr;
   for (void* b : s->blocks) dev_free(b);
   s->blocks.clear();
   if (s->hbuf) cudaFreeHost(s->hbuf);
@@ -161,6 +190,12 @@ void free_all(qnsch_s* s) {
 }
 
 int alloc_all(qnsch_s* s) {
+  if (cudaStreamCreateWithFlags(&s->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->ev_entry, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    return QNSCH_ECUDA;
+  }
+  s->stream = s->own_stream;
   int a = s->m1, b = s->m2;
   double h = s->h;
   s->L.resize(s->nlev);
@@ -274,8 +309,10 @@ constexpr int MAX_PROF_EVENTS = 8192;
 template <typename T, class Form>
 void smooth(qnsch_s* s, const std::vector<Lv<T>>& Ls, const Prm<T>& P, int l) {
   const Lv<T>& L = Ls[l];
-  qn::launch_ch<T, Form>(P, L, 0, s->stream);
-  qn::launch_ch<T, Form>(P, L, 1, s->stream);
+  if (!s->coupled) {
+    qn::launch_ch<T, Form>(P, L, 0, s->stream);
+    qn::launch_ch<T, Form>(P, L, 1, s->stream);
+  }
   for (int c = 0; c < s->kcol; ++c) {
     bool rec = s->prof && l == 0 && s->ev_used + 2 <= MAX_PROF_EVENTS;
     if (rec) {
@@ -286,7 +323,8 @@ void smooth(qnsch_s* s, const std::vector<Lv<T>>& Ls, const Prm<T>& P, int l) {
       }
     }
     if (rec) cudaEventRecord(s->ev[s->ev_used], s->stream);
-    qn::launch_vanka<T, Form>(P, L, c, (T)s->omega, s->stream);
+    if (s->coupled) qn::launch_coupled<T, Form>(P, L, c, (T)s->omega, s->stream);
+    else qn::launch_vanka<T, Form>(P, L, c, (T)s->omega, s->stream);
     if (rec) {
       cudaEventRecord(s->ev[s->ev_used + 1], s->stream);
       s->ev_used += 2;
@@ -294,9 +332,23 @@ void smooth(qnsch_s* s, const std::vector<Lv<T>>& Ls, const Prm<T>& P, int l) {
   }
 }
 
+// first level of Ls whose V-cycle runs fused in one thread block
+template <typename T>
+int fused_from(const qnsch_s* s, const std::vector<Lv<T>>& Ls) {
+  long long thr = sizeof(T) == 8 ? s->fuse64 : s->fuse32;
+  for (int l = 0; l < s->nlev; ++l)
+    if ((long long)Ls[l].m1 * Ls[l].m2 <= thr && s->nlev - l <= QN_MAX_FUSED_LEVELS) return l;
+  return s->nlev;
+}
+
 // FAS V-cycle (Sec. 7.1) from level l on the level set Ls
 template <typename T, class Form>
 void vcycle(qnsch_s* s, const std::vector<Lv<T>>& Ls, const Prm<T>& P, int l) {
+  if (l >= fused_from(s, Ls)) {
+    qn::launch_coarse_vcycle<T, Form>(P, &Ls[l], s->nlev - l, s->nu1, s->nu2, s->nuc, s->kcol,
+                                      (T)s->omega, s->coupled, s->stream);
+    return;
+  }
   if (l == s->nlev - 1) {
     for (int k = 0; k < s->nuc; ++k) smooth<T, Form>(s, Ls, P, l);
     return;
@@ -328,12 +380,25 @@ void prof_collect(qnsch_s* s) {
   s->ev_used = 0;
 }
 
-// finest residual + norms; result left in s->hbuf[0..9] as [l2 x5, max x5]
-int residual_norms(qnsch_s* s, const Prm<double>& P, double* norms10) {
+// Work queued by a call runs on s->stream.  When the caller gave no stream,
+// that is a private non-blocking stream, ordered here after everything the
+// caller queued on the legacy default stream before the call.
+void enter(qnsch_s* s) {
+  if (!s->user_stream) {
+    cudaEventRecord(s->ev_entry, 0);
+    cudaStreamWaitEvent(s->stream, s->ev_entry, 0);
+  }
+}
+
+// queue the finest FP64 residual, its norms and their copy to s->hbuf[0..9]
+void enqueue_norms(qnsch_s* s, const Prm<double>& P) {
   const Lv<double>& F = s->L[0];
   qn::launch_residual<double, FullForm>(P, F, s->part, s->stream);
   qn::launch_norms_finalize(F, s->part, s->scal, s->stream);
   cudaMemcpyAsync(s->hbuf, s->scal, 10 * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+}
+
+int read_norms(qnsch_s* s, double* norms10) {
   int rc = sync(s);
   if (rc) return rc;
   for (int q = 0; q < 5; ++q) {
@@ -341,6 +406,13 @@ int residual_norms(qnsch_s* s, const Prm<double>& P, double* norms10) {
     norms10[5 + q] = s->hbuf[q];
   }
   return QNSCH_OK;
+}
+
+// finest residual + norms as [l2 x5, max x5]
+int residual_norms(qnsch_s* s, const Prm<double>& P, double* norms10) {
+  enqueue_norms(s, P);
+  s->res_valid = 1;
+  return read_norms(s, norms10);
 }
 
 double maxfam(const double* n10) {
@@ -404,6 +476,7 @@ int copy_fields_out(const qnsch_s* s, double* const src[5], double* const dst[5]
 
 int begin(qnsch_s* s, double dt) {
   s->dt = dt;
+  s->res_valid = 0;
   Prm<double> P = make_prm(s);
   Lv<double>& F = s->L[0];
   size_t bytes = s->level_elems0 * sizeof(double);
@@ -447,18 +520,89 @@ void correction_cycle(qnsch_s* s, std::vector<Lv<T>>& E) {
   qn::launch_apply_correction(s->L[0], E[0], s->stream);
 }
 
-int one_cycle(qnsch_s* s, double* norms10) {
-  Prm<double> P = make_prm(s);
+// all work of one outer cycle: V-cycle (or defect-correction cycle), gauge,
+// FP64 residual with norms and their copy to the host
+void cycle_body(qnsch_s* s, const Prm<double>& P) {
   if (s->precision == 0) {
     vcycle<double, FullForm>(s, s->L, P, 0);
   } else {
-    // the residual arrays must hold r(x) of the current iterate
-    qn::launch_residual<double, FullForm>(P, s->L[0], (double*)nullptr, s->stream);
+    // the residual arrays hold r(x) of the current iterate (see one_cycle)
     if (s->precision == 1) correction_cycle<float>(s, s->Ef);
     else correction_cycle<double>(s, s->Ed);
   }
   qn::launch_gauge(s->L[0], s->part, s->scal + 16, s->stream);
-  int rc = residual_norms(s, P, norms10);
+  enqueue_norms(s, P);
+}
+
+void drop_graph(qnsch_s* s) {
+  if (s->gexec) cudaGraphExecDestroy(s->gexec);
+  s->gexec = nullptr;
+}
+
+// capture cycle_body once per (dt, precision, profiling, options) and replay it
+int cycle_graph(qnsch_s* s, const Prm<double>& P) {
+  bool fresh = s->gexec && s->g_dt == s->dt && s->g_precision == s->precision &&
+               s->g_prof == s->prof && s->g_opt == s->opt_version;
+  if (!fresh) {
+    drop_graph(s);
+    s->ev_used = 0;
+    if (s->prof) {  // create the timing events before capture begins
+      int pairs = s->kcol * (s->nlev == 1 ? s->nuc : s->nu1 + s->nu2);
+      while ((int)s->ev.size() < 2 * pairs && (int)s->ev.size() < MAX_PROF_EVENTS) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+          cudaGetLastError();
+          break;
+        }
+        s->ev.push_back(e);
+      }
+    }
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      return QNSCH_ECUDA;
+    }
+    long long before = qn::launches_issued();
+    cycle_body(s, P);
+    s->g_nodes = qn::launches_issued() - before;
+    g_captured += s->g_nodes;
+    cudaError_t e1 = cudaStreamEndCapture(s->stream, &g);
+    cudaError_t e2 = e1 == cudaSuccess ? cudaGraphInstantiate(&s->gexec, g, 0) : e1;
+    if (g) cudaGraphDestroy(g);
+    if (e2 != cudaSuccess) {
+      cudaGetLastError();
+      s->gexec = nullptr;
+      s->ev_used = 0;
+      return QNSCH_ECUDA;
+    }
+    s->g_dt = s->dt;
+    s->g_precision = s->precision;
+    s->g_prof = s->prof;
+    s->g_opt = s->opt_version;
+    s->g_ev_used = s->ev_used;  // event pairs recorded by every replay
+    s->ev_used = 0;
+  }
+  if (cudaGraphLaunch(s->gexec, s->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return QNSCH_ECUDA;
+  }
+  g_replayed += s->g_nodes;
+  s->ev_used = s->g_ev_used;
+  return QNSCH_OK;
+}
+
+int one_cycle(qnsch_s* s, double* norms10) {
+  Prm<double> P = make_prm(s);
+  if (s->precision != 0 && !s->res_valid)
+    qn::launch_residual<double, FullForm>(P, s->L[0], (double*)nullptr, s->stream);
+  bool graphed = false;
+  if (s->use_graphs) {
+    graphed = cycle_graph(s, P) == QNSCH_OK;
+    if (!graphed) s->use_graphs = 0;  // capture unavailable: run the launches directly
+  }
+  if (!graphed) cycle_body(s, P);
+  s->res_valid = 1;  // cycle_body ends with the residual of the new iterate
+  int rc = read_norms(s, norms10);
   if (s->prof) prof_collect(s);
   return rc;
 }
@@ -557,6 +701,7 @@ int qnsch_destroy(qnsch_t* s) {
 int qnsch_set_option(qnsch_t* s, const char* key, double value) {
   if (!s || !key) return QNSCH_EINVAL;
   std::string k(key);
+  ++s->opt_version;
   if (k == "nu1") s->nu1 = (int)value;
   else if (k == "nu2") s->nu2 = (int)value;
   else if (k == "nu_coarse") s->nuc = (int)value;
@@ -566,6 +711,10 @@ int qnsch_set_option(qnsch_t* s, const char* key, double value) {
   else if (k == "M") s->M = value;
   else if (k == "eta_st") s->eta = value;
   else if (k == "eps_mob") s->eps_m = value;
+  else if (k == "graphs") s->use_graphs = value != 0.0;
+  else if (k == "fuse_cells") s->fuse64 = (int)value;
+  else if (k == "coupled") s->coupled = value != 0.0;
+  else if (k == "fuse_cells32") s->fuse32 = (int)value;
   else if (k == "precision") {
     int p = (int)value;
     if (p < 0 || p > 2 || (double)p != value) return QNSCH_EINVAL;
@@ -588,13 +737,19 @@ int qnsch_get_option(const qnsch_t* s, const char* key, double* value) {
   else if (k == "eta_st") *value = s->eta;
   else if (k == "eps_mob") *value = s->eps_m;
   else if (k == "precision") *value = s->precision;
+  else if (k == "graphs") *value = s->use_graphs;
+  else if (k == "fuse_cells") *value = s->fuse64;
+  else if (k == "coupled") *value = s->coupled;
+  else if (k == "fuse_cells32") *value = s->fuse32;
   else return QNSCH_EINVAL;
   return QNSCH_OK;
 }
 
 int qnsch_set_stream(qnsch_t* s, void* stream) {
   if (!s) return QNSCH_EINVAL;
-  s->stream = (cudaStream_t)stream;
+  if (sync(s)) return QNSCH_ECUDA;
+  s->user_stream = (cudaStream_t)stream;
+  s->stream = s->user_stream ? s->user_stream : s->own_stream;
   return QNSCH_OK;
 }
 
@@ -624,7 +779,7 @@ int qnsch_profile_read(qnsch_t* s, long long* launches, double* total_ms) {
 
 int qnsch_kernel_launches(long long* n) {
   if (!n) return QNSCH_EINVAL;
-  *n = qn::launches_issued();
+  *n = qn::launches_issued() - g_captured + g_replayed;
   return QNSCH_OK;
 }
 
@@ -646,6 +801,7 @@ int qnsch_set_fields_device(qnsch_t* s, const double* c, const double* mu, const
   if (s->pending) return QNSCH_ESTATE;
   double* dst[5] = {s->sc, s->smu, s->su, s->sv, s->sp};
   const double* src[5] = {c, mu, u, v, p};
+  enter(s);
   return copy_fields_in(s, dst, src, false);
 }
 
@@ -661,6 +817,7 @@ int qnsch_get_fields_device(const qnsch_t* s, double* c, double* mu, double* u, 
   if (!s) return QNSCH_EINVAL;
   double* src[5] = {s->sc, s->smu, s->su, s->sv, s->sp};
   double* dst[5] = {c, mu, u, v, p};
+  enter(const_cast<qnsch_s*>(s));
   return copy_fields_out(s, src, dst, false);
 }
 
@@ -778,6 +935,7 @@ int qnsch_iterate_energy(const qnsch_t* s, double* E, double* D) {
 
 int qnsch_set_iterate(qnsch_t* s, const double* c, const double* mu, const double* u,
                       const double* v, const double* p) {
+  if (s) s->res_valid = 0;
   if (!s || !c || !mu || !u || !v || !p) return QNSCH_EINVAL;
   if (!s->pending) return QNSCH_ESTATE;
   const Lv<double>& F = s->L[0];
@@ -811,6 +969,7 @@ int qnsch_residual(qnsch_t* s, double* rc_, double* rmu, double* rp, double* ru,
 }
 
 int qnsch_smooth_ch(qnsch_t* s, int colour) {
+  if (s) s->res_valid = 0;
   if (!s || colour < 0 || colour > 1) return QNSCH_EINVAL;
   if (!s->pending) return QNSCH_ESTATE;
   qn::launch_ch<double, FullForm>(make_prm(s), s->L[0], colour, s->stream);
@@ -818,6 +977,7 @@ int qnsch_smooth_ch(qnsch_t* s, int colour) {
 }
 
 int qnsch_smooth_vanka(qnsch_t* s, int colour) {
+  if (s) s->res_valid = 0;
   if (!s || colour < 0 || colour >= s->kcol) return QNSCH_EINVAL;
   if (!s->pending) return QNSCH_ESTATE;
   qn::launch_vanka<double, FullForm>(make_prm(s), s->L[0], colour, s->omega, s->stream);
@@ -825,6 +985,7 @@ int qnsch_smooth_vanka(qnsch_t* s, int colour) {
 }
 
 int qnsch_smooth(qnsch_t* s, int sweeps) {
+  if (s) s->res_valid = 0;
   if (!s || sweeps < 0) return QNSCH_EINVAL;
   if (!s->pending) return QNSCH_ESTATE;
   Prm<double> P = make_prm(s);

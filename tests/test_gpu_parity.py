@@ -265,3 +265,76 @@ def test_mixed_precision_step_meets_fp64_tolerance(qn, case):
     assert max(errs.values()) <= 1e-7, errs
     m1 = g.mass()
     assert abs(m1[0] - m0[0]) <= 1e-12 * m0[0] and abs(m1[1] - m0[1]) <= 1e-12 * m0[1]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_fused_coarse_levels_match_per_level_launches(qn, precision):
+    """The single-block V-cycle of the small levels runs the same per-cell code in
+    the same colour order as the per-level launches: the iterates agree to rounding."""
+    P = W.small_case(64, 96, False)
+    f = P.fields()
+    out = []
+    for fuse in (0, 10 ** 6):
+        g = qn.Solver(**P.create_kwargs(), precision=precision, fuse_cells=fuse,
+                      fuse_cells32=fuse)
+        g.set_fields(f)
+        g.begin_step(P.dt)
+        for _ in range(2):
+            g.vcycle()
+        out.append(g.get_iterate())
+    same_fields(out[0], out[1], 1e-12 if precision == 0 else 1e-5)
+
+
+# ---------------------------------------------------------------------------
+# coupled 7x7 smoother (option)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("m1,m2,px", [(16, 12, False), (16, 12, True), (37, 29, False)])
+def test_coupled_sweep_parity(qn, m1, m2, px):
+    g, r = pair(qn, m1, m2, px)
+    g.set_option("coupled", 1)
+    r.set_option("coupled", 1)
+    load_random(g, r, px, seed=47)
+    g.smooth(1)
+    r.smooth(1)
+    same_fields(g.get_iterate(), r.get_iterate(), 1e-10)
+
+
+@pytest.mark.parametrize("precision", [0, 2])
+def test_coupled_vcycle_parity(qn, precision):
+    P = W.small_case(64, 96, False)
+    g = qn.Solver(**P.create_kwargs(), coupled=1, precision=precision)
+    r = RefSolver(**P.create_kwargs(), coupled=1)
+    for s in (g, r):
+        s.set_fields(P.fields())
+        s.begin_step(P.dt)
+    for _ in range(3):
+        g.vcycle()
+        r.vcycle()
+        same_fields(g.get_iterate(), r.get_iterate(), 1e-9)
+
+
+def test_coupled_full_step_rising_drop(qn):
+    P = W.rising_drop_256x512()
+    g, r, hist = _step_both(qn, P, steps=1, coupled=1)
+    (ng, nr, resg, resr), = hist
+    assert ng == nr and resg <= P.tol
+    same_fields(g.get_fields(), r.get_fields(), 1e-10)
+
+
+def test_coupled_mixed_step_512(qn):
+    """Fine grid where the separate sweeps stall: the coupled block converges in
+    both the FP64 oracle and the mixed GPU path, to the same fields."""
+    P = W.rising_drop_256x512()
+    P.m1, P.m2 = 512, 512
+    P.init_args = dict(x0=0.5, y0=0.3, R=0.2)
+    g = qn.Solver(**P.create_kwargs(), tol=P.tol, coupled=1, precision=1)
+    r = RefSolver(**P.create_kwargs(), tol=P.tol, coupled=1)
+    f = P.fields()
+    g.set_fields(f)
+    r.set_fields(f)
+    ng, resg = g.step(P.dt)
+    nr, resr = r.step(P.dt)
+    assert resg <= P.tol and ng <= nr + 4
+    errs = {k: relerr(v, r.get_fields()[k]) for k, v in g.get_fields().items()}
+    assert max(errs.values()) <= 1e-7, errs
