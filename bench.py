@@ -316,11 +316,11 @@ def run_ours(args, rank, world, local_rank):
 
 # algorithmic FP64 operations per Vanka cell visit (add/sub/mul/div = 1, fused
 # multiply-add = 2), counted from the formulas of k_vanka; see the design doc
-VANKA_FP64_FLOPS_PER_VISIT = 960.0
+VANKA_FP64_FLOPS_PER_VISIT = 620.0
 # dram__bytes_read.sum + dram__bytes_write.sum of one finest-level k_vanka<double> launch at
 # 256x512 (ncu, profiles/k_vanka_fp64_drop_1024x1024.md and the design doc); None once the kernel
 # changes after the capture
-VANKA_FP64_TRAFFIC_BYTES = 15.6e6
+VANKA_FP64_TRAFFIC_BYTES = 26.47e6
 # measured FP64 FMA throughput of one GB300 (dependent-chain-free DFMA loop)
 FP64_PEAK_TFLOPS = 1.193
 

@@ -247,7 +247,7 @@ __device__ __forceinline__ void vanka_system(const Prm<T>& P, const Lv<T>& L, in
                                              T (&A)[5][5], T (&b)[5], bool (&act)[5]) {
   const int W = L.pitch;
   const T ih = L.ih, ih2 = L.ih2;
-  const T *rn = L.rhon, *vis = L.visn, *un = L.un, *vn = L.vn;
+  const T* vis = L.visn;
   int k = L.at(i, j);
   int eW = (L.px && i == 1) ? L.m1 : i - 1;
   int kW = L.at(eW, j);
@@ -265,28 +265,20 @@ __device__ __forceinline__ void vanka_system(const Prm<T>& P, const Lv<T>& L, in
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
     int ke = q == 0 ? kW : k;
-    T rl = rn[ke], rr = rn[ke + 1];
-    T axl = T(0.5) * (un[ke] + un[ke - 1]), axr = T(0.5) * (un[ke + 1] + un[ke]);
-    T Arn = T(0.5) * (rl + rr);
+    T Arn = L.Aru[ke];
     T Ar = T(0.5) * (rho_of(P, Form::val_c(L, ke)) + rho_of(P, Form::val_c(L, ke + 1)));
-    T Art = T(0.25) * (rl + rr + rn[ke + W] + rn[ke + 1 + W]);
-    T Arb = T(0.25) * (rl + rr + rn[ke - W] + rn[ke + 1 - W]);
-    T Avt = T(0.25) * (vis[ke] + vis[ke + 1] + vis[ke + W] + vis[ke + 1 + W]);
-    T Avb = T(0.25) * (vis[ke] + vis[ke + 1] + vis[ke - W] + vis[ke + 1 - W]);
-    T At = T(0.5) * (vn[ke + 1] + vn[ke]), Ab = T(0.5) * (vn[ke + 1 - W] + vn[ke - W]);
     T gt = (j == L.m2) ? T(2) : T(1), gb = (j == 1) ? T(2) : T(1);
-    T vl = vis[ke], vr = vis[ke + 1];
     A[q][q] = Arn * P.idt + T(0.5) * (Ar - Arn) * P.idt +
-              T(0.5) * ih * (-rr * axr + rl * axl - Art * At * gt + Arb * Ab * gb) +
-              T(0.5) * ih * ((rr * axr - rl * axl) + (Art * At - Arb * Ab)) +
-              P.iRe * ih2 * ((vr + vl) * (T(1) + third) + gt * Avt + gb * Avb);
+              T(0.5) * ih * (-L.Sx[ke + 1] + L.Sx[ke] - L.Qx[ke] * gt + L.Qx[ke - W] * gb) +
+              L.Dvu[ke] +
+              P.iRe * ih2 * ((vis[ke + 1] + vis[ke]) * (T(1) + third) + gt * L.Av[ke] +
+                             gb * L.Av[ke - W]);
   }
   {
-    T rc = rn[k], vc = vis[k];
-    T axc = T(0.5) * (un[k] + un[k - 1]);
+    T vc = vis[k];
     T v3 = vc * P.iRe * ih2 * third;
-    A[0][1] = T(0.5) * rc * axc * ih - vc * P.iRe * ih2 - v3;
-    A[1][0] = -T(0.5) * rc * axc * ih - vc * P.iRe * ih2 - v3;
+    A[0][1] = T(0.5) * L.Sx[k] * ih - vc * P.iRe * ih2 - v3;
+    A[1][0] = -T(0.5) * L.Sx[k] * ih - vc * P.iRe * ih2 - v3;
     A[0][2] = v3;
     A[0][3] = -v3;
     A[1][2] = -v3;
@@ -298,28 +290,20 @@ __device__ __forceinline__ void vanka_system(const Prm<T>& P, const Lv<T>& L, in
 #pragma unroll
   for (int q = 2; q < 4; ++q) {
     int ke = q == 2 ? k - W : k;
-    T rb = rn[ke], rt = rn[ke + W];
-    T ayb = T(0.5) * (vn[ke] + vn[ke - W]), ayt = T(0.5) * (vn[ke + W] + vn[ke]);
-    T Arn = T(0.5) * (rb + rt);
+    T Arn = L.Arv[ke];
     T Ar = T(0.5) * (rho_of(P, Form::val_c(L, ke)) + rho_of(P, Form::val_c(L, ke + W)));
-    T Are = T(0.25) * (rb + rt + rn[ke + 1] + rn[ke + 1 + W]);
-    T Arw = T(0.25) * (rb + rt + rn[ke - 1] + rn[ke - 1 + W]);
-    T Ave = T(0.25) * (vis[ke] + vis[ke + W] + vis[ke + 1] + vis[ke + 1 + W]);
-    T Avw = T(0.25) * (vis[ke] + vis[ke + W] + vis[ke - 1] + vis[ke - 1 + W]);
-    T Ae = T(0.5) * (un[ke + W] + un[ke]), Aw = T(0.5) * (un[ke - 1 + W] + un[ke - 1]);
     T ge = (!L.px && i == L.m1) ? T(2) : T(1), gw = (!L.px && i == 1) ? T(2) : T(1);
-    T vb = vis[ke], vt = vis[ke + W];
     A[q][q] = Arn * P.idt + T(0.5) * (Ar - Arn) * P.idt +
-              T(0.5) * ih * (-Are * Ae * ge + Arw * Aw * gw - rt * ayt + rb * ayb) +
-              T(0.5) * ih * ((Are * Ae - Arw * Aw) + (rt * ayt - rb * ayb)) +
-              P.iRe * ih2 * (ge * Ave + gw * Avw + (vt + vb) * (T(1) + third));
+              T(0.5) * ih * (-L.Qy[ke] * ge + L.Qy[ke - 1] * gw - L.Sy[ke + W] + L.Sy[ke]) +
+              L.Dvv[ke] +
+              P.iRe * ih2 * (ge * L.Av[ke] + gw * L.Av[ke - 1] +
+                             (vis[ke + W] + vis[ke]) * (T(1) + third));
   }
   {
-    T rc = rn[k], vc = vis[k];
-    T ayc = T(0.5) * (vn[k] + vn[k - W]);
+    T vc = vis[k];
     T v3 = vc * P.iRe * ih2 * third;
-    A[2][3] = T(0.5) * rc * ayc * ih - vc * P.iRe * ih2 - v3;
-    A[3][2] = -T(0.5) * rc * ayc * ih - vc * P.iRe * ih2 - v3;
+    A[2][3] = T(0.5) * L.Sy[k] * ih - vc * P.iRe * ih2 - v3;
+    A[3][2] = -T(0.5) * L.Sy[k] * ih - vc * P.iRe * ih2 - v3;
     A[2][0] = v3;
     A[2][1] = -v3;
     A[3][0] = -v3;
@@ -444,7 +428,7 @@ __device__ __forceinline__ void coupled_cell(const Prm<T>& P, const Lv<T>& L, in
   int k = L.at(i, j);
   int eW = (L.px && i == 1) ? L.m1 : i - 1;
   int kW = L.at(eW, j);
-  const T *rn = L.rhon, *cn = L.cn, *mob = L.mobn;
+  const T *rn = L.rhon, *mob = L.mobn;
   bool wall[4] = {!L.px && i == L.m1, !L.px && i == 1, j == L.m2, j == 1};
   const int off[4] = {1, -1, W, -W};
   T sm = T(0);
@@ -454,10 +438,10 @@ __device__ __forceinline__ void coupled_cell(const Prm<T>& P, const Lv<T>& L, in
   T cfull = Form::val_c(L, k);
   T rho = rho_of(P, cfull), drho = -P.alpha * rho * rho;
   // rho^n D c^n / 2 at the four faces of the cell, as in (e1e2) and (e1e1)
-  T gW = T(0.5) * rn[k - 1] * (cn[k] - cn[k - 1]) * L.ih;
-  T gE = T(0.5) * rn[k + 1] * (cn[k + 1] - cn[k]) * L.ih;
-  T gS = T(0.5) * rn[k - W] * (cn[k] - cn[k - W]) * L.ih;
-  T gN = T(0.5) * rn[k + W] * (cn[k + W] - cn[k]) * L.ih;
+  T gW = rn[k - 1] * L.Tx[k - 1];
+  T gE = rn[k + 1] * L.Tx[k];
+  T gS = rn[k - W] * L.Ty[k - W];
+  T gN = rn[k + W] * L.Ty[k];
   T diffc = T(0.5) * P.alpha * P.iPe * sm * L.ih2;
   A[0][2] = gW;
   A[0][3] = gE;
@@ -664,6 +648,41 @@ __global__ void k_frozen_derived(Prm<T> P, Lv<T> L) {
   L.mobn[k] = mob_of(P, c);
   L.visn[k] = visc_of(P, c);
   if (i >= 1 && i <= L.m1 && j >= 1 && j <= L.m2) L.Gn[k] = G_h2(L.cn, k, L.pitch) * L.ih2;
+}
+
+// frozen coefficients of (pm-num-mx): cells and vertices (needs rho^n, mu(c^n), ghosts)
+template <typename T>
+__global__ void k_frozen_coef1(Lv<T> L) {
+  int i = blockIdx.x * BX + threadIdx.x;
+  int j = blockIdx.y * BY + threadIdx.y;
+  if (i > L.m1 + 1 || j > L.m2 + 1) return;
+  const int W = L.pitch;
+  int k = L.at(i, j);
+  const T *rn = L.rhon, *vis = L.visn, *un = L.un, *vn = L.vn, *cn = L.cn;
+  L.Sx[k] = rn[k] * T(0.5) * (un[k] + un[k - 1]);   // cell (i,j)
+  L.Sy[k] = rn[k] * T(0.5) * (vn[k] + vn[k - W]);
+  if (i <= L.m1 && j <= L.m2) {  // vertex (i+1/2, j+1/2), edges (i+1/2, j), (i, j+1/2)
+    T Ar = T(0.25) * (rn[k] + rn[k + 1] + rn[k + W] + rn[k + 1 + W]);
+    L.Qx[k] = Ar * T(0.5) * (vn[k + 1] + vn[k]);
+    L.Qy[k] = Ar * T(0.5) * (un[k + W] + un[k]);
+    L.Av[k] = T(0.25) * (vis[k] + vis[k + 1] + vis[k + W] + vis[k + 1 + W]);
+    L.Aru[k] = T(0.5) * (rn[k] + rn[k + 1]);
+    L.Arv[k] = T(0.5) * (rn[k] + rn[k + W]);
+    L.Tx[k] = T(0.5) * (cn[k + 1] - cn[k]) * L.ih;
+    L.Ty[k] = T(0.5) * (cn[k + W] - cn[k]) * L.ih;
+  }
+}
+
+// divergence corrections of (e1e1-2) on edges (needs k_frozen_coef1)
+template <typename T>
+__global__ void k_frozen_coef2(Lv<T> L) {
+  int i = blockIdx.x * BX + threadIdx.x;
+  int j = blockIdx.y * BY + threadIdx.y;
+  if (i > L.m1 || j > L.m2) return;
+  const int W = L.pitch;
+  int k = L.at(i, j);
+  if (j >= 1) L.Dvu[k] = T(0.5) * ((L.Sx[k + 1] - L.Sx[k]) + (L.Qx[k] - L.Qx[k - W])) * L.ih;
+  if (i >= 1) L.Dvv[k] = T(0.5) * ((L.Qy[k] - L.Qy[k - 1]) + (L.Sy[k + W] - L.Sy[k])) * L.ih;
 }
 
 // --------------------------------------------------------------------------
@@ -930,6 +949,17 @@ __global__ void k_cast_frozen(Lv<double> D, Lv<T> E, long long n, int off) {
   E.mobn[q] = (T)D.mobn[q];
   E.visn[q] = (T)D.visn[q];
   E.Gn[q] = (T)D.Gn[q];
+  E.Aru[q] = (T)D.Aru[q];
+  E.Arv[q] = (T)D.Arv[q];
+  E.Sx[q] = (T)D.Sx[q];
+  E.Sy[q] = (T)D.Sy[q];
+  E.Qx[q] = (T)D.Qx[q];
+  E.Qy[q] = (T)D.Qy[q];
+  E.Av[q] = (T)D.Av[q];
+  E.Tx[q] = (T)D.Tx[q];
+  E.Ty[q] = (T)D.Ty[q];
+  E.Dvu[q] = (T)D.Dvu[q];
+  E.Dvv[q] = (T)D.Dvv[q];
 }
 
 // base X = x (rounded), X.c - c^n formed in FP64, right-hand side = FP64 residual
@@ -1226,6 +1256,10 @@ void launch_frozen(const Prm<T>& P, const Lv<T>& L, cudaStream_t s) {
   k_bc_frozen<T><<<(n + 255) / 256, 256, 0, s>>>(L);
   ++g_launches;
   k_frozen_derived<T><<<grid2(L.m1 + 2, L.m2 + 2), dim3(BX, BY), 0, s>>>(P, L);
+  ++g_launches;
+  k_frozen_coef1<T><<<grid2(L.m1 + 2, L.m2 + 2), dim3(BX, BY), 0, s>>>(L);
+  ++g_launches;
+  k_frozen_coef2<T><<<grid2(L.m1 + 1, L.m2 + 1), dim3(BX, BY), 0, s>>>(L);
   ++g_launches;
 }
 template <typename T>

@@ -37,6 +37,13 @@ struct Lv {
   T *sc, *smu, *sp, *su, *sv;  // restricted iterate kept for the correction
   T *cn, *un, *vn;             // frozen level-n data
   T *rhon, *mobn, *visn, *Gn;  // rho(c^n), m(c^n), mu(c^n), G(c^n)
+  // coefficients of (pm-num-mx) that depend on frozen data only, built once
+  // per step: A_x rho^n, A_y rho^n (edges); rho^n a_x u^n, rho^n a_y v^n
+  // (cells); Acal rho^n Acal_x v^n, Acal rho^n Acal_y u^n, Acal mu(c^n)
+  // (vertices (i+1/2, j+1/2) at (i,j)); D_x c^n / 2, D_y c^n / 2 (edges);
+  // the divergence corrections 1/2[D_x(rho a_x u) + Dfrak_y(..)] (x-edges)
+  // and 1/2[Dfrak_x(..) + D_y(rho a_y v)] (y-edges) of (e1e1-2)
+  T *Aru, *Arv, *Sx, *Sy, *Qx, *Qy, *Av, *Tx, *Ty, *Dvu, *Dvv;
   // error-equation (defect-correction) levels only: base state X the iterate
   // e is a correction to, and X.c - c^n formed in FP64 before rounding
   T *Bc = nullptr, *Bmu = nullptr, *Bu = nullptr, *Bv = nullptr, *Bdc = nullptr;
@@ -99,9 +106,8 @@ __device__ __forceinline__ T op_c(const Prm<T>& P, const Lv<T>& L, int k) {
   const T* cn = L.cn;
   const T* rn = L.rhon;
   T c = L.c[k], cnk = cn[k];
-  T adv = T(0.5) * L.ih *
-          (rn[k + 1] * (cn[k + 1] - cnk) * L.u[k] + rn[k - 1] * (cnk - cn[k - 1]) * L.u[k - 1] +
-           rn[k + W] * (cn[k + W] - cnk) * L.v[k] + rn[k - W] * (cnk - cn[k - W]) * L.v[k - W]);
+  T adv = rn[k + 1] * L.Tx[k] * L.u[k] + rn[k - 1] * L.Tx[k - 1] * L.u[k - 1] +
+          rn[k + W] * L.Ty[k] * L.v[k] + rn[k - W] * L.Ty[k - W] * L.v[k - W];
   T diff = lap_h2(L.mobn, L.mu, k, W) + P.alpha * lap_h2(L.mobn, L.p, k, W);
   return rho_of(P, c) * (c - cnk) * P.idt + adv - P.iPe * L.ih2 * diff;
 }
@@ -147,32 +153,22 @@ __device__ __forceinline__ T op_p(const Prm<T>& P, const Lv<T>& L, int k) {
 template <typename T>
 __device__ __forceinline__ T op_u(const Prm<T>& P, const Lv<T>& L, int k) {
   const int W = L.pitch;
-  const T *u = L.u, *un = L.un, *vn = L.vn, *rn = L.rhon, *vis = L.visn;
+  const T *u = L.u, *vis = L.visn, *rn = L.rhon;
   T ue = u[k];
-  T rl = rn[k], rr = rn[k + 1];
-  T Arn = T(0.5) * (rl + rr);
   T Ar = T(0.5) * (rho_of(P, L.c[k]) + rho_of(P, L.c[k + 1]));
-  T axl = T(0.5) * (un[k] + un[k - 1]), axr = T(0.5) * (un[k + 1] + un[k]);
   T dxl = (ue - u[k - 1]) * L.ih, dxr = (u[k + 1] - ue) * L.ih;
   T dvl = dxl + (L.v[k] - L.v[k - W]) * L.ih;
   T dvr = dxr + (L.v[k + 1] - L.v[k + 1 - W]) * L.ih;
-  T Art = T(0.25) * (rl + rr + rn[k + W] + rn[k + 1 + W]);
-  T Arb = T(0.25) * (rl + rr + rn[k - W] + rn[k + 1 - W]);
-  T Avt = T(0.25) * (vis[k] + vis[k + 1] + vis[k + W] + vis[k + 1 + W]);
-  T Avb = T(0.25) * (vis[k] + vis[k + 1] + vis[k - W] + vis[k + 1 - W]);
-  T At = T(0.5) * (vn[k + 1] + vn[k]), Ab = T(0.5) * (vn[k + 1 - W] + vn[k - W]);
   T Dt = (u[k + W] - ue) * L.ih, Db = (ue - u[k - W]) * L.ih;
-  T qt = Art * At, qb = Arb * Ab;   // vertex mass fluxes
-  T sr = rr * axr, sl = rl * axl;   // cell mass fluxes
-  T conv = T(0.5) * (sr * dxr + sl * dxl + qt * Dt + qb * Db);
-  T divc = T(0.5) * ((sr - sl) + (qt - qb)) * L.ih * ue;
-  T time = Arn * (ue - un[k]) * P.idt + T(0.5) * (Ar - Arn) * P.idt * ue;
+  T Arn = L.Aru[k];
+  T conv = T(0.5) * (L.Sx[k + 1] * dxr + L.Sx[k] * dxl + L.Qx[k] * Dt + L.Qx[k - W] * Db);
+  T time = Arn * (ue - L.un[k]) * P.idt + T(0.5) * (Ar - Arn) * P.idt * ue + L.Dvu[k] * ue;
   T press = (L.p[k + 1] - L.p[k]) * L.ih * P.iM;
-  T st = -T(0.5) * (rr * L.mu[k] + rl * L.mu[k + 1]) * (L.cn[k + 1] - L.cn[k]) * L.ih * P.iM;
+  T st = -(rn[k + 1] * L.mu[k] + rn[k] * L.mu[k + 1]) * L.Tx[k] * P.iM;
   T vl = vis[k], vr = vis[k + 1];
-  T visc = -P.iRe * L.ih * ((vr * dxr - vl * dxl) + (Avt * Dt - Avb * Db) +
+  T visc = -P.iRe * L.ih * ((vr * dxr - vl * dxl) + (L.Av[k] * Dt - L.Av[k - W] * Db) +
                             (vr * dvr - vl * dvl) * T(1.0 / 3.0));
-  return time + conv + divc + press + st + visc;
+  return time + conv + press + st + visc;
 }
 
 // y row of (pm-num-mx) at edge v_{i,j+1/2} (index k = at(i,j)); cells k (bottom), k+W (top),
@@ -180,32 +176,22 @@ __device__ __forceinline__ T op_u(const Prm<T>& P, const Lv<T>& L, int k) {
 template <typename T>
 __device__ __forceinline__ T op_v(const Prm<T>& P, const Lv<T>& L, int k) {
   const int W = L.pitch;
-  const T *v = L.v, *vn = L.vn, *un = L.un, *rn = L.rhon, *vis = L.visn;
+  const T *v = L.v, *vis = L.visn, *rn = L.rhon;
   T ve = v[k];
-  T rb = rn[k], rt = rn[k + W];
-  T Arn = T(0.5) * (rb + rt);
   T Ar = T(0.5) * (rho_of(P, L.c[k]) + rho_of(P, L.c[k + W]));
-  T ayb = T(0.5) * (vn[k] + vn[k - W]), ayt = T(0.5) * (vn[k + W] + vn[k]);
   T dyb = (ve - v[k - W]) * L.ih, dyt = (v[k + W] - ve) * L.ih;
   T dvb = dyb + (L.u[k] - L.u[k - 1]) * L.ih;
   T dvt = dyt + (L.u[k + W] - L.u[k + W - 1]) * L.ih;
-  T Are = T(0.25) * (rb + rt + rn[k + 1] + rn[k + 1 + W]);
-  T Arw = T(0.25) * (rb + rt + rn[k - 1] + rn[k - 1 + W]);
-  T Ave = T(0.25) * (vis[k] + vis[k + W] + vis[k + 1] + vis[k + 1 + W]);
-  T Avw = T(0.25) * (vis[k] + vis[k + W] + vis[k - 1] + vis[k - 1 + W]);
-  T Ae = T(0.5) * (un[k + W] + un[k]), Aw = T(0.5) * (un[k - 1 + W] + un[k - 1]);
   T De = (v[k + 1] - ve) * L.ih, Dw = (ve - v[k - 1]) * L.ih;
-  T qe = Are * Ae, qw = Arw * Aw;
-  T st_ = rt * ayt, sb = rb * ayb;
-  T conv = T(0.5) * (qe * De + qw * Dw + st_ * dyt + sb * dyb);
-  T divc = T(0.5) * ((qe - qw) + (st_ - sb)) * L.ih * ve;
-  T time = Arn * (ve - vn[k]) * P.idt + T(0.5) * (Ar - Arn) * P.idt * ve;
+  T Arn = L.Arv[k];
+  T conv = T(0.5) * (L.Qy[k] * De + L.Qy[k - 1] * Dw + L.Sy[k + W] * dyt + L.Sy[k] * dyb);
+  T time = Arn * (ve - L.vn[k]) * P.idt + T(0.5) * (Ar - Arn) * P.idt * ve + L.Dvv[k] * ve;
   T press = (L.p[k + W] - L.p[k]) * L.ih * P.iM;
-  T st = -T(0.5) * (rt * L.mu[k] + rb * L.mu[k + W]) * (L.cn[k + W] - L.cn[k]) * L.ih * P.iM;
+  T st = -(rn[k + W] * L.mu[k] + rn[k] * L.mu[k + W]) * L.Ty[k] * P.iM;
   T vb = vis[k], vt = vis[k + W];
-  T visc = -P.iRe * L.ih * ((Ave * De - Avw * Dw) + (vt * dyt - vb * dyb) +
+  T visc = -P.iRe * L.ih * ((L.Av[k] * De - L.Av[k - 1] * Dw) + (vt * dyt - vb * dyb) +
                             (vt * dvt - vb * dvb) * T(1.0 / 3.0));
-  return time + conv + divc + press + st + visc + P.Fr_inv * Arn;
+  return time + conv + press + st + visc + P.Fr_inv * Arn;
 }
 
 // ---------------------------------------------------------------------------
@@ -281,10 +267,9 @@ __device__ __forceinline__ T opd_c(const Prm<T>& P, const Lv<T>& L, int k) {
   const T* rn = L.rhon;
   T e = L.c[k], C = L.Bc[k];
   T rp = rho_of(P, C + e), rC = rho_of(P, C);
-  T cnk = cn[k];
-  T adv = T(0.5) * L.ih *
-          (rn[k + 1] * (cn[k + 1] - cnk) * L.u[k] + rn[k - 1] * (cnk - cn[k - 1]) * L.u[k - 1] +
-           rn[k + W] * (cn[k + W] - cnk) * L.v[k] + rn[k - W] * (cnk - cn[k - W]) * L.v[k - W]);
+  (void)cn;
+  T adv = rn[k + 1] * L.Tx[k] * L.u[k] + rn[k - 1] * L.Tx[k - 1] * L.u[k - 1] +
+          rn[k + W] * L.Ty[k] * L.v[k] + rn[k - W] * L.Ty[k - W] * L.v[k - W];
   T diff = lap_h2(L.mobn, L.mu, k, W) + P.alpha * lap_h2(L.mobn, L.p, k, W);
   return e * (rp + rsec_(P, rp, rC) * L.Bdc[k]) * P.idt + adv - P.iPe * L.ih2 * diff;
 }
@@ -334,71 +319,53 @@ __device__ __forceinline__ T opd_p(const Prm<T>& P, const Lv<T>& L, int k) { ret
 template <typename T>
 __device__ __forceinline__ T opd_u(const Prm<T>& P, const Lv<T>& L, int k) {
   const int W = L.pitch;
-  const T *u = L.u, *un = L.un, *vn = L.vn, *rn = L.rhon, *vis = L.visn;
+  const T *u = L.u, *vis = L.visn, *rn = L.rhon;
   T ue = u[k];
-  T rl = rn[k], rr = rn[k + 1];
-  T Arn = T(0.5) * (rl + rr);
   T cl = L.Bc[k] + L.c[k], cr = L.Bc[k + 1] + L.c[k + 1];
   T rpl = rho_of(P, cl), rpr = rho_of(P, cr);
   T Arp = T(0.5) * (rpl + rpr);
   T dAr = T(0.5) * (rsec_(P, rpl, rho_of(P, L.Bc[k])) * L.c[k] +
                     rsec_(P, rpr, rho_of(P, L.Bc[k + 1])) * L.c[k + 1]);
-  T axl = T(0.5) * (un[k] + un[k - 1]), axr = T(0.5) * (un[k + 1] + un[k]);
   T dxl = (ue - u[k - 1]) * L.ih, dxr = (u[k + 1] - ue) * L.ih;
   T dvl = dxl + (L.v[k] - L.v[k - W]) * L.ih;
   T dvr = dxr + (L.v[k + 1] - L.v[k + 1 - W]) * L.ih;
-  T Art = T(0.25) * (rl + rr + rn[k + W] + rn[k + 1 + W]);
-  T Arb = T(0.25) * (rl + rr + rn[k - W] + rn[k + 1 - W]);
-  T Avt = T(0.25) * (vis[k] + vis[k + 1] + vis[k + W] + vis[k + 1 + W]);
-  T Avb = T(0.25) * (vis[k] + vis[k + 1] + vis[k - W] + vis[k + 1 - W]);
-  T At = T(0.5) * (vn[k + 1] + vn[k]), Ab = T(0.5) * (vn[k + 1 - W] + vn[k - W]);
   T Dt = (u[k + W] - ue) * L.ih, Db = (ue - u[k - W]) * L.ih;
-  T qt = Art * At, qb = Arb * Ab;
-  T sr = rr * axr, sl = rl * axl;
-  T conv = T(0.5) * (sr * dxr + sl * dxl + qt * Dt + qb * Db);
-  T divc = T(0.5) * ((sr - sl) + (qt - qb)) * L.ih * ue;
-  T time = Arn * ue * P.idt + T(0.5) * (Arp - Arn) * P.idt * ue + T(0.5) * dAr * P.idt * L.Bu[k];
+  T Arn = L.Aru[k];
+  T conv = T(0.5) * (L.Sx[k + 1] * dxr + L.Sx[k] * dxl + L.Qx[k] * Dt + L.Qx[k - W] * Db);
+  T time = Arn * ue * P.idt + T(0.5) * (Arp - Arn) * P.idt * ue + T(0.5) * dAr * P.idt * L.Bu[k] +
+           L.Dvu[k] * ue;
   T press = (L.p[k + 1] - L.p[k]) * L.ih * P.iM;
-  T st = -T(0.5) * (rr * L.mu[k] + rl * L.mu[k + 1]) * (L.cn[k + 1] - L.cn[k]) * L.ih * P.iM;
+  T st = -(rn[k + 1] * L.mu[k] + rn[k] * L.mu[k + 1]) * L.Tx[k] * P.iM;
   T vl = vis[k], vr = vis[k + 1];
-  T visc = -P.iRe * L.ih * ((vr * dxr - vl * dxl) + (Avt * Dt - Avb * Db) +
+  T visc = -P.iRe * L.ih * ((vr * dxr - vl * dxl) + (L.Av[k] * Dt - L.Av[k - W] * Db) +
                             (vr * dvr - vl * dvl) * T(1.0 / 3.0));
-  return time + conv + divc + press + st + visc;
+  return time + conv + press + st + visc;
 }
 
 template <typename T>
 __device__ __forceinline__ T opd_v(const Prm<T>& P, const Lv<T>& L, int k) {
   const int W = L.pitch;
-  const T *v = L.v, *vn = L.vn, *un = L.un, *rn = L.rhon, *vis = L.visn;
+  const T *v = L.v, *vis = L.visn, *rn = L.rhon;
   T ve = v[k];
-  T rb = rn[k], rt = rn[k + W];
-  T Arn = T(0.5) * (rb + rt);
   T cb = L.Bc[k] + L.c[k], ct = L.Bc[k + W] + L.c[k + W];
   T rpb = rho_of(P, cb), rpt = rho_of(P, ct);
   T Arp = T(0.5) * (rpb + rpt);
   T dAr = T(0.5) * (rsec_(P, rpb, rho_of(P, L.Bc[k])) * L.c[k] +
                     rsec_(P, rpt, rho_of(P, L.Bc[k + W])) * L.c[k + W]);
-  T ayb = T(0.5) * (vn[k] + vn[k - W]), ayt = T(0.5) * (vn[k + W] + vn[k]);
   T dyb = (ve - v[k - W]) * L.ih, dyt = (v[k + W] - ve) * L.ih;
   T dvb = dyb + (L.u[k] - L.u[k - 1]) * L.ih;
   T dvt = dyt + (L.u[k + W] - L.u[k + W - 1]) * L.ih;
-  T Are = T(0.25) * (rb + rt + rn[k + 1] + rn[k + 1 + W]);
-  T Arw = T(0.25) * (rb + rt + rn[k - 1] + rn[k - 1 + W]);
-  T Ave = T(0.25) * (vis[k] + vis[k + W] + vis[k + 1] + vis[k + 1 + W]);
-  T Avw = T(0.25) * (vis[k] + vis[k + W] + vis[k - 1] + vis[k - 1 + W]);
-  T Ae = T(0.5) * (un[k + W] + un[k]), Aw = T(0.5) * (un[k - 1 + W] + un[k - 1]);
   T De = (v[k + 1] - ve) * L.ih, Dw = (ve - v[k - 1]) * L.ih;
-  T qe = Are * Ae, qw = Arw * Aw;
-  T st_ = rt * ayt, sb = rb * ayb;
-  T conv = T(0.5) * (qe * De + qw * Dw + st_ * dyt + sb * dyb);
-  T divc = T(0.5) * ((qe - qw) + (st_ - sb)) * L.ih * ve;
-  T time = Arn * ve * P.idt + T(0.5) * (Arp - Arn) * P.idt * ve + T(0.5) * dAr * P.idt * L.Bv[k];
+  T Arn = L.Arv[k];
+  T conv = T(0.5) * (L.Qy[k] * De + L.Qy[k - 1] * Dw + L.Sy[k + W] * dyt + L.Sy[k] * dyb);
+  T time = Arn * ve * P.idt + T(0.5) * (Arp - Arn) * P.idt * ve + T(0.5) * dAr * P.idt * L.Bv[k] +
+           L.Dvv[k] * ve;
   T press = (L.p[k + W] - L.p[k]) * L.ih * P.iM;
-  T st = -T(0.5) * (rt * L.mu[k] + rb * L.mu[k + W]) * (L.cn[k + W] - L.cn[k]) * L.ih * P.iM;
+  T st = -(rn[k + W] * L.mu[k] + rn[k] * L.mu[k + W]) * L.Ty[k] * P.iM;
   T vb = vis[k], vt = vis[k + W];
-  T visc = -P.iRe * L.ih * ((Ave * De - Avw * Dw) + (vt * dyt - vb * dyb) +
+  T visc = -P.iRe * L.ih * ((L.Av[k] * De - L.Av[k - 1] * Dw) + (vt * dyt - vb * dyb) +
                             (vt * dvt - vb * dvb) * T(1.0 / 3.0));
-  return time + conv + divc + press + st + visc;
+  return time + conv + press + st + visc;
 }
 
 // Two forms of the iterate: Full (x itself, Sec. 6.1) and Err (correction e to

@@ -46,7 +46,7 @@ void dev_free(void* p) {
   else cudaFree(p);
 }
 
-constexpr int NFIELD = 27;  // arrays per level (see Lv)
+constexpr int NFIELD = 38;  // arrays per level (see Lv)
 
 // surface-tension ratio eta(rho1, rho2) of Sec. 8.1; near rho1 = rho2 the
 // formula is 0/0 and the Taylor series of x^2 - 1 - 2x ln x in q = x - 1 is used
@@ -216,9 +216,11 @@ int alloc_all(qnsch_s* s) {
     L.h = h;
     L.ih = 1.0 / h;
     L.ih2 = 1.0 / (h * h);
-    double** f[NFIELD] = {&L.c,  &L.mu, &L.p,  &L.u,  &L.v,  &L.fc, &L.fmu, &L.fp,  &L.fu,
-                          &L.fv, &L.rc, &L.rmu, &L.rp, &L.ru, &L.rv, &L.sc,  &L.smu, &L.sp,
-                          &L.su, &L.sv, &L.cn, &L.un, &L.vn, &L.rhon, &L.mobn, &L.visn, &L.Gn};
+    double** f[NFIELD] = {&L.c,  &L.mu,  &L.p,    &L.u,    &L.v,    &L.fc, &L.fmu, &L.fp,
+                          &L.fu, &L.fv,  &L.rc,   &L.rmu,  &L.rp,   &L.ru, &L.rv,  &L.sc,
+                          &L.smu, &L.sp, &L.su,   &L.sv,   &L.cn,   &L.un, &L.vn,  &L.rhon,
+                          &L.mobn, &L.visn, &L.Gn, &L.Aru, &L.Arv,  &L.Sx, &L.Sy,  &L.Qx,
+                          &L.Qy, &L.Av,  &L.Tx,   &L.Ty,   &L.Dvu,  &L.Dvv};
     for (int q = 0; q < NFIELD; ++q) *f[q] = base + (size_t)q * n + pitch + 1;  // origin (0,0)
     a /= 2;
     b /= 2;
@@ -275,10 +277,12 @@ int alloc_err_levels(qnsch_s* s, std::vector<Lv<T>>& E) {
     L.h = (T)D.h;
     L.ih = (T)D.ih;
     L.ih2 = (T)D.ih2;
-    T** f[NFIELD_ERR] = {&L.c,  &L.mu, &L.p,  &L.u,  &L.v,    &L.fc,   &L.fmu,  &L.fp,
-                         &L.fu, &L.fv, &L.rc, &L.rmu, &L.rp,  &L.ru,   &L.rv,   &L.sc,
-                         &L.smu, &L.sp, &L.su, &L.sv, &L.cn,  &L.un,   &L.vn,   &L.rhon,
-                         &L.mobn, &L.visn, &L.Gn, &L.Bc, &L.Bmu, &L.Bu, &L.Bv, &L.Bdc};
+    T** f[NFIELD_ERR] = {&L.c,   &L.mu,  &L.p,   &L.u,   &L.v,    &L.fc,  &L.fmu, &L.fp,
+                         &L.fu,  &L.fv,  &L.rc,  &L.rmu, &L.rp,   &L.ru,  &L.rv,  &L.sc,
+                         &L.smu, &L.sp,  &L.su,  &L.sv,  &L.cn,   &L.un,  &L.vn,  &L.rhon,
+                         &L.mobn, &L.visn, &L.Gn, &L.Aru, &L.Arv, &L.Sx,  &L.Sy,  &L.Qx,
+                         &L.Qy,  &L.Av,  &L.Tx,  &L.Ty,  &L.Dvu,  &L.Dvv, &L.Bc,  &L.Bmu,
+                         &L.Bu,  &L.Bv,  &L.Bdc};
     for (int q = 0; q < NFIELD_ERR; ++q) *f[q] = base + (size_t)q * n + D.pitch + 1;
   }
   E.swap(out);
