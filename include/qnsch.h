@@ -82,6 +82,9 @@ int qnsch_set_allocator(void* (*alloc)(size_t bytes, void* ctx),
 int qnsch_create(const qnsch_grid* grid, double rho1, double rho2, double eta1, double eta2,
                  double Re, double We, double Pe, double Cn, double Fr, qnsch_t** out);
 int qnsch_destroy(qnsch_t* h);
+/* Device bytes a handle for `grid` holds once created and stepped with the
+   given "precision" option (0, 1 or 2), computed without allocating. */
+int qnsch_footprint(const qnsch_grid* grid, int precision, size_t* bytes);
 
 /* Options (key: default): "nu1": 2, "nu2": 2 (pre/post smoothing steps),
    "nu_coarse": 4 (smoothing steps on the coarsest level), "tol": 1e-9,
@@ -174,6 +177,25 @@ int qnsch_profile_read(qnsch_t* h, long long* launches, double* total_ms);
 /* Number of CUDA kernels this library has issued since it was loaded
    (process-wide, counted on the host at launch). */
 int qnsch_kernel_launches(long long* n);
+
+/* Batches of independent instances (no counterpart in the paper; the way a
+   GPU runs many small problems at once).  A batch refers to n existing
+   handles, each with its own stream (handles created without qnsch_set_stream
+   each have a private one; two handles sharing a stream are rejected).
+   qnsch_batch_step advances every instance by one step of size dt[a]: it
+   queues every instance's outer cycles, one cycle per instance per round, so
+   the instances' kernels run concurrently on the GPU, and stops each instance
+   at its own tolerance.  Every instance goes through exactly the arithmetic of
+   qnsch_step on that handle, so its result does not depend on the batch.
+   status[a] receives that instance's qnsch_step status (0, QNSCH_ENOTCONV,
+   QNSCH_ENAN, ...), n_vcycles[a] (may be NULL) its V-cycle count.  The call
+   returns QNSCH_OK unless its arguments are invalid.  The batch does not own
+   the handles; destroy it before them. */
+typedef struct qnsch_batch_s qnsch_batch_t;
+int qnsch_batch_create(int n, qnsch_t* const* insts, qnsch_batch_t** out);
+int qnsch_batch_step(qnsch_batch_t* b, const double* dt, int* status, int* n_vcycles);
+int qnsch_batch_size(const qnsch_batch_t* b);
+int qnsch_batch_destroy(qnsch_batch_t* b);
 
 /* Mass reduction that allocates nothing (the paper has no counterpart: this is
    an interface for callers, not a step of the method).  It is meant for code

@@ -595,7 +595,9 @@ int cycle_graph(qnsch_s* s, const Prm<double>& P) {
   return QNSCH_OK;
 }
 
-int one_cycle(qnsch_s* s, double* norms10) {
+// queue one outer cycle (as a graph replay when possible); finish_cycle waits
+// for it and reads the norms
+void launch_cycle(qnsch_s* s) {
   Prm<double> P = make_prm(s);
   if (s->precision != 0 && !s->res_valid)
     qn::launch_residual<double, FullForm>(P, s->L[0], (double*)nullptr, s->stream);
@@ -606,15 +608,24 @@ int one_cycle(qnsch_s* s, double* norms10) {
   }
   if (!graphed) cycle_body(s, P);
   s->res_valid = 1;  // cycle_body ends with the residual of the new iterate
+}
+
+int finish_cycle(qnsch_s* s, double* norms10) {
   int rc = read_norms(s, norms10);
   if (s->prof) prof_collect(s);
   return rc;
 }
 
-int commit(qnsch_s* s) {
+int one_cycle(qnsch_s* s, double* norms10) {
+  launch_cycle(s);
+  return finish_cycle(s, norms10);
+}
+
+// queue the dissipation of the step (Thm. 6.2) and the copy of the iterate into
+// the committed state; finish_commit waits and records
+void launch_commit(qnsch_s* s) {
   Prm<double> P = make_prm(s);
   const Lv<double>& F = s->L[0];
-  // dissipation of this step (Thm. 6.2), then accept the iterate
   double w_visc = s->dt / s->Re, w_div = s->dt / (3.0 * s->Re), w_ch = s->dt / (s->M * s->Pe);
   qn::launch_dissipation(P, F, w_visc, w_div, w_ch, s->part, s->scal + 25, s->stream);
   size_t bytes = s->level_elems0 * sizeof(double);
@@ -625,11 +636,19 @@ int commit(qnsch_s* s) {
     cudaMemcpyAsync(dst[q] - pitch - 1, src[q] - pitch - 1, bytes, cudaMemcpyDeviceToDevice,
                     s->stream);
   cudaMemcpyAsync(s->hbuf + 25, s->scal + 25, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+}
+
+int finish_commit(qnsch_s* s) {
   int rc = sync(s);
   if (rc) return rc;
   s->last_diss = s->hbuf[25];
   s->pending = 0;
   return QNSCH_OK;
+}
+
+int commit(qnsch_s* s) {
+  launch_commit(s);
+  return finish_commit(s);
 }
 
 }  // namespace
@@ -690,6 +709,34 @@ int qnsch_create(const qnsch_grid* grid, double rho1, double rho2, double eta1, 
     return rc;
   }
   *out = s;
+  return QNSCH_OK;
+}
+
+int qnsch_footprint(const qnsch_grid* grid, int precision, size_t* bytes) {
+  if (!grid || !bytes || grid->m1 < 2 || grid->m2 < 2 || grid->periodic_y) return QNSCH_EINVAL;
+  if (grid->periodic_x && grid->m1 % 4 != 0) return QNSCH_EINVAL;
+  if (precision < 0 || precision > 2) return QNSCH_EINVAL;
+  int lmax = max_levels(grid->m1, grid->m2, grid->periodic_x);
+  int lev = grid->levels <= 0 ? lmax : grid->levels;
+  if (lev > lmax) return QNSCH_EINVAL;
+  size_t total = 0;
+  int a = grid->m1, b = grid->m2;
+  size_t elem_err = precision == 1 ? sizeof(float) : sizeof(double);
+  size_t n0 = 0;
+  for (int l = 0; l < lev; ++l) {
+    int pitch;
+    size_t n = padded_elems(a, b, &pitch);
+    if (l == 0) n0 = n;
+    total += n * NFIELD * sizeof(double);
+    if (precision) total += n * NFIELD_ERR * elem_err;
+    a /= 2;
+    b /= 2;
+  }
+  total += n0 * 5 * sizeof(double);                                           // committed state
+  total += (size_t)qn::partial_rows_needed(grid->m1, grid->m2) * 10 * sizeof(double);
+  total += (size_t)(grid->m1 + 1) * (grid->m2 + 1) * sizeof(double);         // staging
+  total += 32 * sizeof(double);
+  *bytes = total;
   return QNSCH_OK;
 }
 
@@ -986,6 +1033,108 @@ int qnsch_smooth_vanka(qnsch_t* s, int colour) {
   if (!s->pending) return QNSCH_ESTATE;
   qn::launch_vanka<double, FullForm>(make_prm(s), s->L[0], colour, s->omega, s->stream);
   return sync(s);
+}
+
+// ----------------------------------------------------------------------------
+// batches of independent instances
+// ----------------------------------------------------------------------------
+struct qnsch_batch_s {
+  std::vector<qnsch_s*> inst;
+};
+
+int qnsch_batch_create(int n, qnsch_t* const* insts, qnsch_batch_t** out) {
+  if (n <= 0 || !insts || !out) return QNSCH_EINVAL;
+  for (int a = 0; a < n; ++a) {
+    if (!insts[a]) return QNSCH_EINVAL;
+    for (int b = 0; b < a; ++b)
+      if (insts[a] == insts[b] || (insts[a]->stream == insts[b]->stream)) return QNSCH_EINVAL;
+  }
+  qnsch_batch_s* B = new (std::nothrow) qnsch_batch_s();
+  if (!B) return QNSCH_ENOMEM;
+  B->inst.assign(insts, insts + n);
+  *out = B;
+  return QNSCH_OK;
+}
+
+int qnsch_batch_destroy(qnsch_batch_t* B) {
+  if (!B) return QNSCH_EINVAL;
+  delete B;
+  return QNSCH_OK;
+}
+
+int qnsch_batch_size(const qnsch_batch_t* B) { return B ? (int)B->inst.size() : QNSCH_EINVAL; }
+
+int qnsch_batch_step(qnsch_batch_t* B, const double* dt, int* status, int* n_vcycles) {
+  if (!B || !dt || !status) return QNSCH_EINVAL;
+  const int n = (int)B->inst.size();
+  for (int a = 0; a < n; ++a)
+    if (!(dt[a] > 0) || B->inst[a]->pending) return QNSCH_EINVAL;
+  std::vector<int> live(n, 1), cyc(n, 0);
+  std::vector<double> res(n, 0.0);
+  double nrm[10];
+  for (int a = 0; a < n; ++a) {
+    qnsch_s* s = B->inst[a];
+    status[a] = begin(s, dt[a]);
+    if (status[a]) {
+      live[a] = 0;
+      continue;
+    }
+    enqueue_norms(s, make_prm(s));
+    s->res_valid = 1;
+  }
+  for (int a = 0; a < n; ++a) {
+    if (!live[a]) continue;
+    status[a] = read_norms(B->inst[a], nrm);
+    res[a] = maxfam(nrm);
+    if (status[a]) live[a] = 0;
+  }
+  // outer cycles: queue one cycle on every unfinished instance, then collect
+  std::vector<char> queued(n, 0);
+  for (;;) {
+    int any = 0;
+    for (int a = 0; a < n; ++a) {
+      qnsch_s* s = B->inst[a];
+      queued[a] = live[a] && res[a] == res[a] && res[a] > s->tol && cyc[a] < s->maxcyc;
+      if (!queued[a]) continue;
+      launch_cycle(s);
+      ++cyc[a];
+      any = 1;
+    }
+    if (!any) break;
+    for (int a = 0; a < n; ++a) {
+      if (!queued[a]) continue;
+      qnsch_s* s = B->inst[a];
+      int rc = finish_cycle(s, nrm);
+      if (rc) {
+        status[a] = rc;
+        live[a] = 0;
+        continue;
+      }
+      res[a] = maxfam(nrm);
+    }
+  }
+  for (int a = 0; a < n; ++a) {
+    qnsch_s* s = B->inst[a];
+    if (n_vcycles) n_vcycles[a] = cyc[a];
+    if (!live[a]) {
+      s->pending = 0;
+      continue;
+    }
+    if (!(res[a] == res[a])) {
+      status[a] = QNSCH_ENAN;
+      s->pending = 0;
+    } else if (res[a] > s->tol) {
+      status[a] = QNSCH_ENOTCONV;
+      s->pending = 0;
+    } else {
+      launch_commit(s);
+    }
+  }
+  for (int a = 0; a < n; ++a) {
+    qnsch_s* s = B->inst[a];
+    if (live[a] && s->pending) status[a] = finish_commit(s);
+  }
+  return QNSCH_OK;
 }
 
 int qnsch_smooth(qnsch_t* s, int sweeps) {

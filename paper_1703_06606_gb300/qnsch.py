@@ -74,6 +74,11 @@ def lib():
         L.qnsch_profile_read.argtypes = [_VP, ctypes.POINTER(ctypes.c_longlong), p]
         L.qnsch_kernel_launches.argtypes = [ctypes.POINTER(ctypes.c_longlong)]
         L.qnsch_mass_noalloc.argtypes = [_VP, i, i, d, d, d, _VP, _VP]
+        L.qnsch_batch_create.argtypes = [i, ctypes.POINTER(_VP), ctypes.POINTER(_VP)]
+        L.qnsch_batch_step.argtypes = [_VP, p, ctypes.POINTER(i), ctypes.POINTER(i)]
+        L.qnsch_batch_size.argtypes = [_VP]
+        L.qnsch_batch_destroy.argtypes = [_VP]
+        L.qnsch_footprint.argtypes = [ctypes.POINTER(_Grid), i, ctypes.POINTER(ctypes.c_size_t)]
         _lib = L
     return _lib
 
@@ -278,3 +283,44 @@ class Solver:
         _check(lib().qnsch_iterate_energy(self._h, ctypes.byref(e), ctypes.byref(d)),
                "qnsch_iterate_energy")
         return e.value, d.value
+
+
+def footprint(m1, m2, periodic_x=False, levels=0, precision=0, Lx=1.0):
+    """Device bytes of one handle (qnsch_footprint), computed without allocating."""
+    g = _Grid(int(m1), int(m2), float(Lx), int(periodic_x), 0, int(levels))
+    out = ctypes.c_size_t()
+    _check(lib().qnsch_footprint(ctypes.byref(g), int(precision), ctypes.byref(out)),
+           "qnsch_footprint")
+    return out.value
+
+
+class Batch:
+    """qnsch_batch_*: step several Solver instances together (their kernels run
+    concurrently on the GPU); each instance keeps its own tolerance and result."""
+
+    def __init__(self, solvers):
+        self.solvers = list(solvers)
+        arr = (_VP * len(self.solvers))(*[sv._h.value for sv in self.solvers])
+        h = _VP()
+        _check(lib().qnsch_batch_create(len(self.solvers), arr, ctypes.byref(h)),
+               "qnsch_batch_create")
+        self._h = h
+
+    def step(self, dt):
+        n = len(self.solvers)
+        dts = np.ascontiguousarray(np.broadcast_to(np.asarray(dt, dtype=np.float64), (n,)))
+        st = (ctypes.c_int * n)()
+        cy = (ctypes.c_int * n)()
+        _check(lib().qnsch_batch_step(self._h, dts.ctypes.data_as(_D), st, cy), "qnsch_batch_step")
+        return list(st), list(cy)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().qnsch_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
