@@ -58,7 +58,7 @@ extern "C" {
 typedef struct qnsch_s qnsch_t;
 
 typedef struct {
-  int m1, m2;      /* cells in x and y; m1, m2 >= 2; periodic x needs m1 % 4 == 0 */
+  int m1, m2;      /* cells in x and y; m1, m2 >= 2; periodic x needs m1 even, >= 4 */
   double Lx;       /* domain width; h = Lx / m1, height Ly = m2 h */
   int periodic_x;  /* 1: periodic in x; 0: no-slip walls in x */
   int periodic_y;  /* must be 0: y is always bounded by walls */
@@ -114,7 +114,7 @@ int qnsch_set_option(qnsch_t* h, const char* key, double value);
 int qnsch_get_option(const qnsch_t* h, const char* key, double* value);
 int qnsch_set_stream(qnsch_t* h, void* cuda_stream);
 int qnsch_levels(const qnsch_t* h);          /* number of levels, or < 0 */
-int qnsch_ncolours_vanka(const qnsch_t* h);  /* 5 (walls in x) or 8 (periodic x) */
+int qnsch_ncolours_vanka(const qnsch_t* h);  /* Vanka colours on the finest level */
 
 /* Committed state (time level n): host arrays in the layouts above. */
 int qnsch_set_fields(qnsch_t* h, const double* c, const double* mu, const double* u,
@@ -158,7 +158,8 @@ int qnsch_residual(qnsch_t* h, double* rc, double* rmu, double* rp, double* ru, 
                    double* norms10);
 /* Smoother pieces on the finest level (Sec. 7.1): one colour of the CH
    nonlinear Gauss-Seidel (colour 0: (i+j) even), one colour of the Vanka
-   smoother ((i+2j) mod 5 with walls in x, (2i+j) mod 8 with periodic x), or
+   smoother ((i+2j) mod 5 with walls in x; with periodic x (2i+j) mod 8 when
+   m1 = 0 mod 4, else (i+2j) mod K, K the smallest divisor >= 5 of m1), or
    `sweeps` full smoothing steps (CH red, CH black, Vanka colours 0..K-1). */
 int qnsch_smooth_ch(qnsch_t* h, int colour);
 int qnsch_smooth_vanka(qnsch_t* h, int colour);

@@ -30,9 +30,10 @@
  *       limit 3/(2 sqrt(2) rho1) is used (series for |rho2/rho1 - 1| < 0.1).
  *   R6 periodic edge data wrap with period m1 (u_{m1+1/2} = u_{1/2}).
  *   R7 smoother order: CH red-black, (i+j) mod 2; Vanka colours (i+2j) mod 5
- *       (walls in x) or (2i+j) mod 8 (periodic x, m1 a multiple of 4): any two
- *       cells whose 5x5 Vanka blocks couple are at L1 distance <= 2 and get
- *       distinct colours, also across the periodic seam.
+ *       (walls in x), (2i+j) mod 8 (periodic x, m1 a multiple of 4) or
+ *       (i+2j) mod K, K the smallest divisor >= 5 of m1 (other even periodic
+ *       m1): any two cells whose 5x5 Vanka blocks couple are at L1 distance
+ *       <= 2 and get distinct colours, also across the periodic seam.
  *   R8 transfers: cell data restricted by the 4-cell mean and prolongated
  *       piecewise constant; edge iterates restricted by the mean of the two
  *       coincident fine edges, edge residuals by full weighting (the transpose
@@ -125,6 +126,7 @@ static void derive_params(ref_params* P) {
 
 typedef struct {
   int m1, m2, px;
+  int kcol; /* number of Vanka colours on this level (reading R7) */
   double h;
   double *c, *mu, *p, *u, *v;       /* current iterate x */
   double *fc, *fmu, *fp, *fu, *fv;  /* FAS right-hand side f */
@@ -678,8 +680,22 @@ static void solve_dense(int n, double* A, double* b) {
   }
 }
 
+/* Vanka colours (reading R7): walls in x: (i+2j) mod 5; periodic x with
+   m1 = 0 mod 4: (2i+j) mod 8; other (even) periodic m1: (i+2j) mod K with K the
+   smallest divisor of m1 that is >= 5.  The offsets of coupled blocks give
+   i+2j differences in {+-1..+-4} and 2i+j differences in {+-1, +-2, +-3, +-4}
+   with 2(i+m1)+j = 2i+j mod 8 when 4 | m1, so no two coupled cells share a
+   colour, also across the periodic seam. */
+static int colours_of(int m1, int px) {
+  if (!px) return 5;
+  if (m1 % 4 == 0) return 8;
+  for (int K = 5; K <= m1; ++K)
+    if (m1 % K == 0) return K;
+  return m1;
+}
 static int vanka_colour(const ref_level* L, int kcol, int i, int j) {
-  return L->px ? (2 * i + j) % kcol : (i + 2 * j) % kcol;
+  if (L->px && L->m1 % 4 == 0) return (2 * i + j) % 8;
+  return (i + 2 * j) % kcol;
 }
 
 /* CH step 1 of Sec. 7.1 at cell (i,j): one Newton step on the 2x2 local system */
@@ -805,12 +821,12 @@ static void smooth_coupled(const ref_params* P, ref_level* L, double dt, int kco
    colours 0..K-1.  Coupled option: the 7x7 block over the K Vanka colours. */
 static void smooth(const ref_solver* s, ref_level* L) {
   if (s->coupled) {
-    for (int col = 0; col < s->kcol; ++col) smooth_coupled(&s->P, L, s->dt, s->kcol, col, s->omega);
+    for (int col = 0; col < L->kcol; ++col) smooth_coupled(&s->P, L, s->dt, L->kcol, col, s->omega);
     return;
   }
   smooth_ch(&s->P, L, s->dt, 0);
   smooth_ch(&s->P, L, s->dt, 1);
-  for (int col = 0; col < s->kcol; ++col) smooth_vanka(&s->P, L, s->dt, s->kcol, col, s->omega);
+  for (int col = 0; col < L->kcol; ++col) smooth_vanka(&s->P, L, s->dt, L->kcol, col, s->omega);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -1114,6 +1130,7 @@ static int level_alloc(ref_level* L, int m1, int m2, int px, double h) {
   L->m1 = m1;
   L->m2 = m2;
   L->px = px;
+  L->kcol = colours_of(m1, px);
   L->h = h;
   size_t nc = ncell(L), nu = nu_(L), nv = nv_(L);
   double** cells[] = {&L->c, &L->mu, &L->p, &L->fc, &L->fmu, &L->fp, &L->rc, &L->rmu, &L->rp,
@@ -1140,8 +1157,10 @@ static void level_free(ref_level* L) {
    stays a multiple of 4 and >= 4 (periodic x, for the colouring of R7) */
 static int max_levels(int m1, int m2, int px) {
   int n = 1;
-  int cmin = px ? 4 : 2;
-  while (m1 % 2 == 0 && m2 % 2 == 0 && m1 / 2 >= cmin && m2 / 2 >= cmin && (!px || (m1 / 2) % 4 == 0)) {
+  /* walls: down to 2 cells; periodic x: the coarse m1 stays even (red-black
+     across the seam) and >= 4 */
+  while (m1 % 2 == 0 && m2 % 2 == 0 && m2 / 2 >= 2 &&
+         (px ? (m1 / 2 >= 4 && (m1 / 2) % 2 == 0) : m1 / 2 >= 2)) {
     m1 /= 2;
     m2 /= 2;
     ++n;
@@ -1155,7 +1174,7 @@ int qnsch_ref_create(int m1, int m2, double Lx, int periodic_x, int levels, doub
   if (!out || m1 < 2 || m2 < 2 || !(Lx > 0) || !(rho1 > 0) || !(rho2 > 0) || !(eta1 > 0) ||
       !(eta2 > 0) || !(Re > 0) || !(We > 0) || !(Pe > 0) || !(Cn > 0))
     return REF_EINVAL;
-  if (periodic_x && m1 % 4 != 0) return REF_EINVAL;
+  if (periodic_x && (m1 % 2 != 0 || m1 < 4)) return REF_EINVAL;
   int lmax = max_levels(m1, m2, periodic_x);
   if (levels <= 0) levels = lmax;
   if (levels > lmax) return REF_EINVAL;
@@ -1180,7 +1199,7 @@ int qnsch_ref_create(int m1, int m2, double Lx, int periodic_x, int levels, doub
   s->maxcyc = 50;
   s->tol = 1e-9;
   s->omega = 1.0;
-  s->kcol = periodic_x ? 8 : 5;
+  s->kcol = colours_of(m1, periodic_x);
   s->nlev = levels;
   s->lev = (ref_level*)calloc((size_t)levels, sizeof(ref_level));
   double h = Lx / m1;

@@ -478,10 +478,30 @@ __device__ __forceinline__ void coupled_cell(const Prm<T>& P, const Lv<T>& L, in
   store_cell(L, L.p, i, j, L.p[k] - omega * b[6]);
 }
 
-// Vanka colour of cell (i,j): (i + 2j) mod 5 with walls in x, (2i + j) mod 8 periodic
+// Vanka colour of cell (i,j): (2i + j) mod 8 (periodic x, m1 = 0 mod 4) or
+// (i + 2j) mod kcol (kcol = 5 with walls, the smallest divisor >= 5 of m1 otherwise)
 template <typename T>
 __device__ __forceinline__ int vanka_colour(const Lv<T>& L, int i, int j) {
-  return L.px ? (2 * i + j) & 7 : (i + 2 * j) % 5;
+  return L.c8 ? (2 * i + j) & 7 : (i + 2 * j) % L.kcol;
+}
+
+// first cell i0 >= 1 of colour `colour` in row j and the stride between cells
+// of that colour in the row; false if the row has none
+template <typename T>
+__device__ __forceinline__ bool colour_row(const Lv<T>& L, int colour, int j, int& i0, int& stride) {
+  if (L.c8) {
+    int d = (colour - j) & 7;
+    if (d & 1) return false;
+    i0 = d >> 1;
+    if (i0 == 0) i0 = 4;
+    stride = 4;
+  } else {
+    int K = L.kcol;
+    i0 = ((colour - 2 * j) % K + K) % K;
+    if (i0 == 0) i0 = K;
+    stride = K;
+  }
+  return true;
 }
 
 template <typename T, class Form>
@@ -489,17 +509,7 @@ __global__ void k_vanka(Prm<T> P, Lv<T> L, int colour, T omega) {
   int j = blockIdx.y * BY + threadIdx.y + 1;
   if (j > L.m2) return;
   int i0, stride;
-  if (L.px) {
-    int d = (colour - j) & 7;
-    if (d & 1) return;  // no cell of this colour in row j
-    i0 = d >> 1;
-    if (i0 == 0) i0 = 4;
-    stride = 4;
-  } else {
-    i0 = ((colour - 2 * j) % 5 + 5) % 5;
-    if (i0 == 0) i0 = 5;
-    stride = 5;
-  }
+  if (!colour_row(L, colour, j, i0, stride)) return;
   int i = i0 + stride * (blockIdx.x * BX + threadIdx.x);
   if (i > L.m1) return;
   vanka_cell<T, Form>(P, L, i, j, omega);
@@ -510,17 +520,7 @@ __global__ void __launch_bounds__(BX * BY) k_coupled(Prm<T> P, Lv<T> L, int colo
   int j = blockIdx.y * BY + threadIdx.y + 1;
   if (j > L.m2) return;
   int i0, stride;
-  if (L.px) {
-    int d = (colour - j) & 7;
-    if (d & 1) return;
-    i0 = d >> 1;
-    if (i0 == 0) i0 = 4;
-    stride = 4;
-  } else {
-    i0 = ((colour - 2 * j) % 5 + 5) % 5;
-    if (i0 == 0) i0 = 5;
-    stride = 5;
-  }
+  if (!colour_row(L, colour, j, i0, stride)) return;
   int i = i0 + stride * (blockIdx.x * BX + threadIdx.x);
   if (i > L.m1) return;
   coupled_cell<T, Form>(P, L, i, j, omega);
@@ -870,8 +870,9 @@ __device__ __forceinline__ void bc_unknowns_block(const Lv<T>& L) {
 }
 
 template <typename T, class Form>
-__device__ void smooth_block(const Prm<T>& P, const Lv<T>& L, int kcol, T omega, int coupled) {
+__device__ void smooth_block(const Prm<T>& P, const Lv<T>& L, T omega, int coupled) {
   int n = L.m1 * L.m2;
+  const int kcol = L.kcol;
   if (coupled) {
     for (int col = 0; col < kcol; ++col) {
       for (int t = threadIdx.x; t < n; t += blockDim.x) {
@@ -906,7 +907,7 @@ __global__ void __launch_bounds__(NT) k_coarse_vcycle(Prm<T> P, CoarseLevels<T> 
   for (int l = 0; l < n - 1; ++l) {
     const Lv<T>& F = C.L[l];
     const Lv<T>& G = C.L[l + 1];
-    for (int s = 0; s < nu1; ++s) smooth_block<T, Form>(P, F, kcol, omega, coupled);
+    for (int s = 0; s < nu1; ++s) smooth_block<T, Form>(P, F, omega, coupled);
     for (int t = threadIdx.x; t < F.m1 * F.m2; t += NT)
       residual_cell<T, 0, Form>(P, F, t % F.m1 + 1, t / F.m1 + 1, dummy);
     __syncthreads();
@@ -921,7 +922,7 @@ __global__ void __launch_bounds__(NT) k_coarse_vcycle(Prm<T> P, CoarseLevels<T> 
       residual_cell<T, 1, Form>(P, G, t % G.m1 + 1, t / G.m1 + 1, dummy);
     __syncthreads();
   }
-  for (int s = 0; s < nuc; ++s) smooth_block<T, Form>(P, C.L[n - 1], kcol, omega, coupled);
+  for (int s = 0; s < nuc; ++s) smooth_block<T, Form>(P, C.L[n - 1], omega, coupled);
   for (int l = n - 2; l >= 0; --l) {
     const Lv<T>& F = C.L[l];
     const Lv<T>& G = C.L[l + 1];
@@ -929,7 +930,7 @@ __global__ void __launch_bounds__(NT) k_coarse_vcycle(Prm<T> P, CoarseLevels<T> 
       prolong_cell(F, G, t % F.m1 + 1, t / F.m1 + 1);
     __syncthreads();
     bc_unknowns_block(F);
-    for (int s = 0; s < nu2; ++s) smooth_block<T, Form>(P, F, kcol, omega, coupled);
+    for (int s = 0; s < nu2; ++s) smooth_block<T, Form>(P, F, omega, coupled);
   }
 }
 
@@ -1190,7 +1191,7 @@ void launch_ch(const Prm<T>& P, const Lv<T>& L, int colour, cudaStream_t s) {
 }
 template <typename T, class Form>
 void launch_vanka(const Prm<T>& P, const Lv<T>& L, int colour, T omega, cudaStream_t s) {
-  int stride = L.px ? 4 : 5;
+  int stride = L.c8 ? 4 : L.kcol;
   k_vanka<T, Form><<<grid2((L.m1 + stride - 1) / stride, L.m2), dim3(BX, BY), 0, s>>>(P, L, colour,
                                                                                        omega);
   ++g_launches;
@@ -1208,7 +1209,7 @@ void launch_coarse_vcycle(const Prm<T>& P, const Lv<T>* levels, int n, int nu1, 
 
 template <typename T, class Form>
 void launch_coupled(const Prm<T>& P, const Lv<T>& L, int colour, T omega, cudaStream_t s) {
-  int stride = L.px ? 4 : 5;
+  int stride = L.c8 ? 4 : L.kcol;
   k_coupled<T, Form><<<grid2((L.m1 + stride - 1) / stride, L.m2), dim3(BX, BY), 0, s>>>(P, L, colour,
                                                                                          omega);
   ++g_launches;

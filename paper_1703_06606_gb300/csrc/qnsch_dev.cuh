@@ -30,6 +30,9 @@ struct Prm {
 template <typename T>
 struct Lv {
   int m1, m2, px, pitch;
+  // Vanka colours of this level: kcol colours, (2i+j) mod 8 when c8 is set
+  // (periodic x with m1 = 0 mod 4), else (i+2j) mod kcol
+  int kcol, c8;
   T h, ih, ih2;
   T *c, *mu, *p, *u, *v;       // iterate
   T *fc, *fmu, *fp, *fu, *fv;  // FAS right-hand side

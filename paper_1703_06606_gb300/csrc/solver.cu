@@ -65,11 +65,22 @@ double eta_st(double r1, double r2) {
          (2.0 * std::sqrt(2.0) * r1 * r2 * (r2 * r2 - r1 * r1 - 2.0 * r1 * r2 * std::log(r2 / r1)));
 }
 
+// Vanka colours of a level: 5 (walls in x), 8 for (2i+j) mod 8 (periodic x,
+// m1 = 0 mod 4), else the smallest divisor >= 5 of m1 for (i+2j) mod K
+int colours_of(int m1, int px) {
+  if (!px) return 5;
+  if (m1 % 4 == 0) return 8;
+  for (int K = 5; K <= m1; ++K)
+    if (m1 % K == 0) return K;
+  return m1;
+}
+
+// coarsen by 2 while both sizes are even: walls down to 2 cells; periodic x
+// keeps the coarse m1 even (red-black across the seam) and >= 4
 int max_levels(int m1, int m2, int px) {
   int n = 1;
-  int cmin = px ? 4 : 2;
-  while (m1 % 2 == 0 && m2 % 2 == 0 && m1 / 2 >= cmin && m2 / 2 >= cmin &&
-         (!px || (m1 / 2) % 4 == 0)) {
+  while (m1 % 2 == 0 && m2 % 2 == 0 && m2 / 2 >= 2 &&
+         (px ? (m1 / 2 >= 4 && (m1 / 2) % 2 == 0) : m1 / 2 >= 2)) {
     m1 /= 2;
     m2 /= 2;
     ++n;
@@ -212,6 +223,8 @@ int alloc_all(qnsch_s* s) {
     L.m1 = a;
     L.m2 = b;
     L.px = s->px;
+    L.kcol = colours_of(a, s->px);
+    L.c8 = s->px && a % 4 == 0;
     L.pitch = pitch;
     L.h = h;
     L.ih = 1.0 / h;
@@ -273,6 +286,8 @@ int alloc_err_levels(qnsch_s* s, std::vector<Lv<T>>& E) {
     L.m1 = D.m1;
     L.m2 = D.m2;
     L.px = D.px;
+    L.kcol = D.kcol;
+    L.c8 = D.c8;
     L.pitch = D.pitch;
     L.h = (T)D.h;
     L.ih = (T)D.ih;
@@ -317,7 +332,7 @@ void smooth(qnsch_s* s, const std::vector<Lv<T>>& Ls, const Prm<T>& P, int l) {
     qn::launch_ch<T, Form>(P, L, 0, s->stream);
     qn::launch_ch<T, Form>(P, L, 1, s->stream);
   }
-  for (int c = 0; c < s->kcol; ++c) {
+  for (int c = 0; c < L.kcol; ++c) {
     bool rec = s->prof && l == 0 && s->ev_used + 2 <= MAX_PROF_EVENTS;
     if (rec) {
       while ((int)s->ev.size() < s->ev_used + 2) {
@@ -551,7 +566,7 @@ int cycle_graph(qnsch_s* s, const Prm<double>& P) {
     drop_graph(s);
     s->ev_used = 0;
     if (s->prof) {  // create the timing events before capture begins
-      int pairs = s->kcol * (s->nlev == 1 ? s->nuc : s->nu1 + s->nu2);
+      int pairs = s->L[0].kcol * (s->nlev == 1 ? s->nuc : s->nu1 + s->nu2);
       while ((int)s->ev.size() < 2 * pairs && (int)s->ev.size() < MAX_PROF_EVENTS) {
         cudaEvent_t e;
         if (cudaEventCreate(&e) != cudaSuccess) {
@@ -675,7 +690,7 @@ int qnsch_create(const qnsch_grid* grid, double rho1, double rho2, double eta1, 
     return QNSCH_ENODEV;
   }
   if (grid->m1 < 2 || grid->m2 < 2 || !(grid->Lx > 0) || grid->periodic_y) return QNSCH_EINVAL;
-  if (grid->periodic_x && grid->m1 % 4 != 0) return QNSCH_EINVAL;
+  if (grid->periodic_x && (grid->m1 % 2 != 0 || grid->m1 < 4)) return QNSCH_EINVAL;
   if (!(rho1 > 0) || !(rho2 > 0) || !(eta1 > 0) || !(eta2 > 0) || !(Re > 0) || !(We > 0) ||
       !(Pe > 0) || !(Cn > 0))
     return QNSCH_EINVAL;
@@ -699,7 +714,7 @@ int qnsch_create(const qnsch_grid* grid, double rho1, double rho2, double eta1, 
   s->m1 = grid->m1;
   s->m2 = grid->m2;
   s->px = grid->periodic_x ? 1 : 0;
-  s->kcol = s->px ? 8 : 5;
+  s->kcol = colours_of(grid->m1, s->px);
   s->nlev = lev;
   s->h = grid->Lx / grid->m1;
   int rc = alloc_all(s);
@@ -714,7 +729,7 @@ int qnsch_create(const qnsch_grid* grid, double rho1, double rho2, double eta1, 
 
 int qnsch_footprint(const qnsch_grid* grid, int precision, size_t* bytes) {
   if (!grid || !bytes || grid->m1 < 2 || grid->m2 < 2 || grid->periodic_y) return QNSCH_EINVAL;
-  if (grid->periodic_x && grid->m1 % 4 != 0) return QNSCH_EINVAL;
+  if (grid->periodic_x && (grid->m1 % 2 != 0 || grid->m1 < 4)) return QNSCH_EINVAL;
   if (precision < 0 || precision > 2) return QNSCH_EINVAL;
   int lmax = max_levels(grid->m1, grid->m2, grid->periodic_x);
   int lev = grid->levels <= 0 ? lmax : grid->levels;

@@ -58,7 +58,7 @@ def same_fields(fg, fr, tol, keys=("c", "mu", "p", "u", "v")):
 
 
 SIZES = [(16, 12, False), (16, 12, True), (37, 29, False), (40, 24, True), (2, 2, False),
-         (4, 6, True), (70, 45, False)]
+         (4, 6, True), (70, 45, False), (10, 8, True), (14, 6, True)]
 
 
 @pytest.mark.parametrize("m1,m2,px", SIZES)
@@ -103,7 +103,8 @@ def test_smoothing_parity_random_state(qn, m1, m2, px):
     same_fields(g.get_iterate(), r.get_iterate(), 1e-10)
 
 
-@pytest.mark.parametrize("m1,m2,px", [(32, 48, False), (32, 48, True), (24, 40, False)])
+@pytest.mark.parametrize("m1,m2,px", [(32, 48, False), (32, 48, True), (24, 40, False),
+                                     (40, 40, True), (56, 56, True)])
 def test_vcycle_parity_from_physical_state(qn, m1, m2, px):
     """V-cycles (all levels, transfers, coarsest solve, gauge) from the level-n state."""
     P = W.small_case(m1, m2, px)
@@ -200,7 +201,7 @@ def test_device_field_io_roundtrip(qn):
 
 def test_error_statuses(qn):
     with pytest.raises(qn.QnschError) as e:
-        qn.Solver(6, 8, periodic_x=True)  # periodic x needs m1 % 4 == 0
+        qn.Solver(7, 8, periodic_x=True)  # periodic x needs an even m1
     assert e.value.code == -1
     with pytest.raises(qn.QnschError):
         qn.Solver(16, 16, levels=9)
