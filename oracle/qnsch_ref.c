@@ -930,10 +930,25 @@ static void prolong_correct(ref_level* F, const ref_level* C) {
 /* FAS V-cycle (Sec. 7.1; standard FAS)                                     */
 /* ------------------------------------------------------------------------ */
 
+/* Sweeps on the coarsest grid.  A fixed handful of sweeps only solves the
+   coarsest problem when it is a few cells across; the pressure and chemical
+   potential modes there converge at a rate set by the grid's longest side n,
+   so a coarsest grid that could not coarsen further (periodic width 4 under a
+   tall domain, or an odd periodic width) gets nu_coarse * ceil(n/4)^2 sweeps
+   (Sec. 7.1 leaves the coarsest solve open). */
+static int coarse_sweeps(const ref_solver* s) {
+  const ref_level* C = &s->lev[s->nlev - 1];
+  int n = C->m1 > C->m2 ? C->m1 : C->m2;
+  int q = (n + 3) / 4;
+  if (q < 1) q = 1;
+  return s->nuc * q * q;
+}
+
 static void vcycle(ref_solver* s, int l) {
   ref_level* L = &s->lev[l];
   if (l == s->nlev - 1) {
-    for (int k = 0; k < s->nuc; ++k) smooth(s, L);
+    int nc = coarse_sweeps(s);
+    for (int k = 0; k < nc; ++k) smooth(s, L);
     return;
   }
   for (int k = 0; k < s->nu1; ++k) smooth(s, L);

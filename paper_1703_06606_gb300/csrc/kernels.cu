@@ -5,6 +5,8 @@
 // for the norms, the mean of p, mass (Thm. 6.1) and energy (Thm. 6.2).
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "kernels.h"
 #include "qnsch_dev.cuh"
 
@@ -82,10 +84,26 @@ template <typename T, int MODE, class Form>
 __device__ __forceinline__ void residual_cell(const Prm<T>& P, const Lv<T>& L, int i, int j,
                                               double (&val)[10]) {
   int k = L.at(i, j);
-  T nc = Form::Nc(P, L, k), nm = Form::Nmu(P, L, k), np = Form::Np(P, L, k);
   bool hu = i <= L.uhi(), hv = j < L.m2;
-  T nu = hu ? Form::Nu(P, L, k) : T(0);
-  T nv = hv ? Form::Nv(P, L, k) : T(0);
+  T nc, nm, np, nu, nv;
+  if constexpr (std::is_same<Form, FullForm>::value) {
+    // rho(c) of the cell and its neighbours, shared by the five rows
+    const int W = L.pitch;
+    T rk = rho_of(P, L.c[k]);
+    const T rq[4] = {rho_of(P, L.c[k + 1]), rho_of(P, L.c[k - 1]), rho_of(P, L.c[k + W]),
+                     rho_of(P, L.c[k - W])};
+    nc = op_c(P, L, k, rk);
+    nm = op_mu(P, L, k, rk, rq);
+    np = op_p(P, L, k);
+    nu = hu ? op_u(P, L, k, T(0.5) * (rk + rq[0])) : T(0);
+    nv = hv ? op_v(P, L, k, T(0.5) * (rk + rq[2])) : T(0);
+  } else {
+    nc = Form::Nc(P, L, k);
+    nm = Form::Nmu(P, L, k);
+    np = Form::Np(P, L, k);
+    nu = hu ? Form::Nu(P, L, k) : T(0);
+    nv = hv ? Form::Nv(P, L, k) : T(0);
+  }
   if (MODE == 0) {
     T r[5] = {L.fc[k] - nc, L.fmu[k] - nm, L.fp[k] - np, hu ? L.fu[k] - nu : T(0),
               hv ? L.fv[k] - nv : T(0)};
@@ -130,18 +148,29 @@ __device__ __forceinline__ void ch_system(const Prm<T>& P, const Lv<T>& L, int i
                                           T (&J)[2][2], T (&R)[2]) {
   const int W = L.pitch;
   int k = L.at(i, j);
-  T Rc = Form::Nc(P, L, k) - L.fc[k];
-  T Rm = Form::Nmu(P, L, k) - L.fmu[k];
+  const int off[4] = {1, -1, W, -W};
+  // rho(c) of the cell and its four neighbours, shared by N_c, N_mu and J
+  T rho, rq4[4];
+  rho = rho_of(P, Form::val_c(L, k));
+#pragma unroll
+  for (int f = 0; f < 4; ++f) rq4[f] = rho_of(P, Form::val_c(L, k + off[f]));
+  T Rc, Rm;
+  if constexpr (std::is_same<Form, FullForm>::value) {
+    Rc = op_c(P, L, k, rho) - L.fc[k];
+    Rm = op_mu(P, L, k, rho, rq4) - L.fmu[k];
+  } else {
+    Rc = Form::Nc(P, L, k) - L.fc[k];
+    Rm = Form::Nmu(P, L, k) - L.fmu[k];
+  }
   const T *cn = L.cn, *rn = L.rhon, *mob = L.mobn;
   // full values c, mu at which the local Jacobian is evaluated
   T ck = Form::val_c(L, k), cnk = cn[k], mk = Form::val_mu(L, k);
-  T rho = rho_of(P, ck), drho = -P.alpha * rho * rho;
+  T drho = -P.alpha * rho * rho;
   T rnk = rn[k];
   T rh = T(0.5) * (rho + rnk);
   T chk = ck + cnk;  // 2 c^{n+1/2}
   T r = -P.alpha * rho * rnk, dr = -P.alpha * drho * rnk;
   bool wall[4] = {!L.px && i == L.m1, !L.px && i == 1, j == L.m2, j == 1};
-  const int off[4] = {1, -1, W, -W};
   T sm = 0, dG = 0, dd = 0, G2 = 0;
 #pragma unroll
   for (int f = 0; f < 4; ++f) {
@@ -152,7 +181,7 @@ __device__ __forceinline__ void ch_system(const Prm<T>& P, const Lv<T>& L, int i
     if (wall[f]) continue;
     sm += mob[k] + mob[q];
     dG -= d;
-    T rq = T(0.5) * (rho_of(P, cq) + rn[q]);
+    T rq = T(0.5) * (rq4[f] + rn[q]);
     dd += T(0.5) * drho * ((cq + cn[q]) - chk) - (rh + rq);
   }
   // sm = 2 sum A m; dG = h^2 dG/dc; dd = 4 h^2 d(div)/dc; G2 = 2 h^2 G(c)
@@ -184,12 +213,14 @@ __device__ __forceinline__ void ch_cell(const Prm<T>& P, const Lv<T>& L, int i, 
   store_cell(L, L.mu, i, j, L.mu[k] - dm);
 }
 
+// cells of CH colour `colour` ((i + j) % 2), packed: slot t -> row t / mpr + 1
 template <typename T, class Form>
-__global__ void k_ch(Prm<T> P, Lv<T> L, int colour) {
-  int j = blockIdx.y * BY + threadIdx.y + 1;
-  if (j > L.m2) return;
-  int i0 = ((colour - j) & 1) ? 1 : 2;
-  int i = i0 + 2 * (blockIdx.x * BX + threadIdx.x);
+__global__ void __launch_bounds__(64) k_ch(Prm<T> P, Lv<T> L, int colour) {
+  int mpr = (L.m1 + 1) / 2;
+  int t = blockIdx.x * 64 + threadIdx.x;
+  if (t >= mpr * L.m2) return;
+  int j = t / mpr + 1;
+  int i = (((colour - j) & 1) ? 1 : 2) + 2 * (t % mpr);
   if (i > L.m1) return;
   ch_cell<T, Form>(P, L, i, j);
 }
@@ -261,12 +292,22 @@ __device__ __forceinline__ void vanka_system(const Prm<T>& P, const Lv<T>& L, in
 #pragma unroll
     for (int c = 0; c < 5; ++c) A[r][c] = T(0);
   const T third = T(1.0 / 3.0);
+  // density averages on the four edges from rho(c) of the cell and its four
+  // neighbours (c at kW + 1 is c at k, exactly: ghosts are copies)
+  T Arq[4];
+  {
+    T rk = rho_of(P, Form::val_c(L, k));
+    Arq[0] = T(0.5) * (rho_of(P, Form::val_c(L, kW)) + rk);
+    Arq[1] = T(0.5) * (rk + rho_of(P, Form::val_c(L, k + 1)));
+    Arq[2] = T(0.5) * (rho_of(P, Form::val_c(L, k - W)) + rk);
+    Arq[3] = T(0.5) * (rk + rho_of(P, Form::val_c(L, k + W)));
+  }
   // x-edge rows: q = 0 (west edge, index kW), q = 1 (east edge, index k)
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
     int ke = q == 0 ? kW : k;
     T Arn = L.Aru[ke];
-    T Ar = T(0.5) * (rho_of(P, Form::val_c(L, ke)) + rho_of(P, Form::val_c(L, ke + 1)));
+    T Ar = Arq[q];
     T gt = (j == L.m2) ? T(2) : T(1), gb = (j == 1) ? T(2) : T(1);
     A[q][q] = Arn * P.idt + T(0.5) * (Ar - Arn) * P.idt +
               T(0.5) * ih * (-L.Sx[ke + 1] + L.Sx[ke] - L.Qx[ke] * gt + L.Qx[ke - W] * gb) +
@@ -291,7 +332,7 @@ __device__ __forceinline__ void vanka_system(const Prm<T>& P, const Lv<T>& L, in
   for (int q = 2; q < 4; ++q) {
     int ke = q == 2 ? k - W : k;
     T Arn = L.Arv[ke];
-    T Ar = T(0.5) * (rho_of(P, Form::val_c(L, ke)) + rho_of(P, Form::val_c(L, ke + W)));
+    T Ar = Arq[q];
     T ge = (!L.px && i == L.m1) ? T(2) : T(1), gw = (!L.px && i == 1) ? T(2) : T(1);
     A[q][q] = Arn * P.idt + T(0.5) * (Ar - Arn) * P.idt +
               T(0.5) * ih * (-L.Qy[ke] * ge + L.Qy[ke - 1] * gw - L.Sy[ke + W] + L.Sy[ke]) +
@@ -325,10 +366,17 @@ __device__ __forceinline__ void vanka_system(const Prm<T>& P, const Lv<T>& L, in
     A[4][3] = ih;
     A[4][4] = T(0.5) * P.alpha * P.alpha * P.iPe * sm * ih2;
   }
-  b[0] = act[0] ? Form::Nu(P, L, kW) - L.fu[kW] : T(0);
-  b[1] = act[1] ? Form::Nu(P, L, k) - L.fu[k] : T(0);
-  b[2] = act[2] ? Form::Nv(P, L, k - W) - L.fv[k - W] : T(0);
-  b[3] = act[3] ? Form::Nv(P, L, k) - L.fv[k] : T(0);
+  if constexpr (std::is_same<Form, FullForm>::value) {
+    b[0] = act[0] ? op_u(P, L, kW, Arq[0]) - L.fu[kW] : T(0);
+    b[1] = act[1] ? op_u(P, L, k, Arq[1]) - L.fu[k] : T(0);
+    b[2] = act[2] ? op_v(P, L, k - W, Arq[2]) - L.fv[k - W] : T(0);
+    b[3] = act[3] ? op_v(P, L, k, Arq[3]) - L.fv[k] : T(0);
+  } else {
+    b[0] = act[0] ? Form::Nu(P, L, kW) - L.fu[kW] : T(0);
+    b[1] = act[1] ? Form::Nu(P, L, k) - L.fu[k] : T(0);
+    b[2] = act[2] ? Form::Nv(P, L, k - W) - L.fv[k - W] : T(0);
+    b[3] = act[3] ? Form::Nv(P, L, k) - L.fv[k] : T(0);
+  }
   b[4] = Form::Np(P, L, k) - L.fp[k];
 #pragma unroll
   for (int q = 0; q < 4; ++q)
@@ -504,25 +552,58 @@ __device__ __forceinline__ bool colour_row(const Lv<T>& L, int colour, int j, in
   return true;
 }
 
-template <typename T, class Form>
-__global__ void k_vanka(Prm<T> P, Lv<T> L, int colour, T omega) {
-  int j = blockIdx.y * BY + threadIdx.y + 1;
-  if (j > L.m2) return;
+// slots of Vanka colour `col`: slot t -> row j0 + rstep * (t / mpr), t % mpr-th
+// cell of that row's colour
+struct ColourSlots {
+  int j0, rstep, mpr, n;
+};
+
+template <typename T>
+__host__ __device__ __forceinline__ ColourSlots vanka_slots(const Lv<T>& L, int col) {
+  ColourSlots cs;
+  if (L.c8) {
+    cs.j0 = ((col - 1) & 1) ? 2 : 1;  // rows with (col - j) even
+    cs.rstep = 2;
+    cs.mpr = (L.m1 + 3) / 4;
+  } else {
+    cs.j0 = 1;
+    cs.rstep = 1;
+    cs.mpr = (L.m1 + L.kcol - 1) / L.kcol;
+  }
+  cs.n = cs.j0 > L.m2 ? 0 : ((L.m2 - cs.j0) / cs.rstep + 1) * cs.mpr;
+  return cs;
+}
+
+template <typename T>
+__device__ __forceinline__ bool vanka_slot_cell(const Lv<T>& L, int col, const ColourSlots& cs, int t,
+                                                int& i, int& j) {
+  j = cs.j0 + cs.rstep * (t / cs.mpr);
   int i0, stride;
-  if (!colour_row(L, colour, j, i0, stride)) return;
-  int i = i0 + stride * (blockIdx.x * BX + threadIdx.x);
-  if (i > L.m1) return;
+  if (!colour_row(L, col, j, i0, stride)) return false;
+  i = i0 + stride * (t % cs.mpr);
+  return i <= L.m1;
+}
+
+// per-level smoother launches: one thread per cell of the colour, packed into
+// 64-thread blocks so that a level's warps spread over many SMs (on the FP64
+// pipe a warp costs the same with 1 or 32 lanes busy)
+constexpr int SNT = 64;
+
+template <typename T, class Form>
+__global__ void __launch_bounds__(SNT) k_vanka(Prm<T> P, Lv<T> L, int colour, T omega) {
+  ColourSlots cs = vanka_slots(L, colour);
+  int t = blockIdx.x * SNT + threadIdx.x;
+  int i, j;
+  if (t >= cs.n || !vanka_slot_cell(L, colour, cs, t, i, j)) return;
   vanka_cell<T, Form>(P, L, i, j, omega);
 }
 
 template <typename T, class Form>
-__global__ void __launch_bounds__(BX * BY) k_coupled(Prm<T> P, Lv<T> L, int colour, T omega) {
-  int j = blockIdx.y * BY + threadIdx.y + 1;
-  if (j > L.m2) return;
-  int i0, stride;
-  if (!colour_row(L, colour, j, i0, stride)) return;
-  int i = i0 + stride * (blockIdx.x * BX + threadIdx.x);
-  if (i > L.m1) return;
+__global__ void __launch_bounds__(SNT) k_coupled(Prm<T> P, Lv<T> L, int colour, T omega) {
+  ColourSlots cs = vanka_slots(L, colour);
+  int t = blockIdx.x * SNT + threadIdx.x;
+  int i, j;
+  if (t >= cs.n || !vanka_slot_cell(L, colour, cs, t, i, j)) return;
   coupled_cell<T, Form>(P, L, i, j, omega);
 }
 
@@ -869,31 +950,204 @@ __device__ __forceinline__ void bc_unknowns_block(const Lv<T>& L) {
   __syncthreads();
 }
 
+// --------------------------------------------------------------------------
+// single-block smoothing of the coarse levels.  An FP64 warp instruction
+// holds the SM sub-partition's FP64 pipe for about 64 cycles however many of
+// its lanes are active, so a colour step on a small level costs (warp
+// instructions per visit) x (warps per sub-partition): threads are packed onto
+// the cells of the colour, and on the smallest levels four lanes share one
+// Vanka block (one edge row each).
+// --------------------------------------------------------------------------
+// Momentum row of the full-form operator in one direction: d = 0 is the x row
+// (op_u, unknown u), d = 1 the y row (op_v, unknown v).  Both directions run
+// the same instructions on different arrays and strides (s along the edge
+// normal, t across it).
+template <typename T>
+struct MomRow {
+  const T *a, *b, *S, *Q, *Tf, *Arn, *Dv, *an, *f;
+  int s, t;
+  T grav;
+};
+
+template <typename T>
+__device__ __forceinline__ MomRow<T> mom_row(const Prm<T>& P, const Lv<T>& L, int d) {
+  MomRow<T> R;
+  R.a = d ? L.v : L.u;
+  R.b = d ? L.u : L.v;
+  R.S = d ? L.Sy : L.Sx;
+  R.Q = d ? L.Qy : L.Qx;
+  R.Tf = d ? L.Ty : L.Tx;
+  R.Arn = d ? L.Arv : L.Aru;
+  R.Dv = d ? L.Dvv : L.Dvu;
+  R.an = d ? L.vn : L.un;
+  R.f = d ? L.fv : L.fu;
+  R.s = d ? L.pitch : 1;
+  R.t = d ? 1 : L.pitch;
+  R.grav = d ? P.Fr_inv : T(0);
+  return R;
+}
+
+// N - f of the momentum row at edge index k (op_u / op_v with the density
+// average Ar of the edge passed in)
+template <typename T>
+__device__ __forceinline__ T mom_residual(const Prm<T>& P, const Lv<T>& L, const MomRow<T>& R, int k,
+                                          T Ar) {
+  const int s = R.s, t = R.t;
+  const T *a = R.a, *b = R.b, *vis = L.visn, *rn = L.rhon;
+  T ae = a[k];
+  T dl = (ae - a[k - s]) * L.ih, dr = (a[k + s] - ae) * L.ih;
+  T dvl = dl + (b[k] - b[k - t]) * L.ih;
+  T dvr = dr + (b[k + s] - b[k + s - t]) * L.ih;
+  T Dp = (a[k + t] - ae) * L.ih, Dm = (ae - a[k - t]) * L.ih;
+  T Arn = R.Arn[k];
+  T conv = T(0.5) * (R.S[k + s] * dr + R.S[k] * dl + R.Q[k] * Dp + R.Q[k - t] * Dm);
+  T time = Arn * (ae - R.an[k]) * P.idt + T(0.5) * (Ar - Arn) * P.idt * ae + R.Dv[k] * ae;
+  T press = (L.p[k + s] - L.p[k]) * L.ih * P.iM;
+  T st = -(rn[k + s] * L.mu[k] + rn[k] * L.mu[k + s]) * R.Tf[k] * P.iM;
+  T vl = vis[k], vr = vis[k + s];
+  T visc = -P.iRe * L.ih * ((vr * dr - vl * dl) + (L.Av[k] * Dp - L.Av[k - t] * Dm) +
+                            (vr * dvr - vl * dvl) * T(1.0 / 3.0));
+  return time + conv + press + st + visc + R.grav * Arn - R.f[k];
+}
+
+// Vanka block of cell (i,j) by a team of four lanes (lane & 3 = q): lane q
+// builds row q (diagonal entry and residual of edge q: W, E, S, N); the rows
+// are gathered by shuffles and every lane of the team solves the 5x5 system;
+// lane q writes edge q and lane 0 the pressure.  All 32 lanes of the warp
+// call this (ok = false: a spare team, which computes on cell (1,1) and
+// stores nothing).
+template <typename T>
+__device__ __forceinline__ void vanka_team(const Prm<T>& P, const Lv<T>& L, int i, int j, bool ok,
+                                           T omega) {
+  const unsigned FULL = 0xffffffffu;
+  const int W = L.pitch;
+  const int lane = threadIdx.x & 31, q = lane & 3, d = q >> 1, lead = lane & ~3;
+  const T ih = L.ih, ih2 = L.ih2, third = T(1.0 / 3.0);
+  int k = L.at(i, j);
+  int eW = (L.px && i == 1) ? L.m1 : i - 1;
+  int kW = L.at(eW, j);
+  bool a0 = L.px || i > 1, a1 = L.px || i < L.m1, a2 = j > 1, a3 = j < L.m2;
+  bool mine = q == 0 ? a0 : q == 1 ? a1 : q == 2 ? a2 : a3;
+  int ke = q == 0 ? kW : (q == 2 ? k - W : k);
+  MomRow<T> R = mom_row(P, L, d);
+  T Ar = T(0.5) * (rho_of(P, L.c[ke]) + rho_of(P, L.c[ke + R.s]));
+  T gp = d ? ((!L.px && i == L.m1) ? T(2) : T(1)) : ((j == L.m2) ? T(2) : T(1));
+  T gm = d ? ((!L.px && i == 1) ? T(2) : T(1)) : ((j == 1) ? T(2) : T(1));
+  const T* vis = L.visn;
+  T Arn = R.Arn[ke];
+  T dq = Arn * P.idt + T(0.5) * (Ar - Arn) * P.idt +
+         T(0.5) * ih * (-R.S[ke + R.s] + R.S[ke] - R.Q[ke] * gp + R.Q[ke - R.t] * gm) + R.Dv[ke] +
+         P.iRe * ih2 * ((vis[ke + R.s] + vis[ke]) * (T(1) + third) + gp * L.Av[ke] +
+                        gm * L.Av[ke - R.t]);
+  T bq = T(0);
+  if (mine) bq = mom_residual(P, L, R, ke, Ar);
+  T A[5][5], b[5];
+#pragma unroll
+  for (int r = 0; r < 5; ++r)
+#pragma unroll
+    for (int c = 0; c < 5; ++c) A[r][c] = T(0);
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    A[r][r] = __shfl_sync(FULL, dq, lead + r);
+    b[r] = __shfl_sync(FULL, bq, lead + r);
+  }
+  T vc = vis[k];
+  T v3 = vc * P.iRe * ih2 * third;
+  A[0][1] = T(0.5) * L.Sx[k] * ih - vc * P.iRe * ih2 - v3;
+  A[1][0] = -T(0.5) * L.Sx[k] * ih - vc * P.iRe * ih2 - v3;
+  A[0][2] = v3;
+  A[0][3] = -v3;
+  A[1][2] = -v3;
+  A[1][3] = v3;
+  A[0][4] = ih * P.iM;
+  A[1][4] = -ih * P.iM;
+  A[2][3] = T(0.5) * L.Sy[k] * ih - vc * P.iRe * ih2 - v3;
+  A[3][2] = -T(0.5) * L.Sy[k] * ih - vc * P.iRe * ih2 - v3;
+  A[2][0] = v3;
+  A[2][1] = -v3;
+  A[3][0] = -v3;
+  A[3][1] = v3;
+  A[2][4] = ih * P.iM;
+  A[3][4] = -ih * P.iM;
+  {
+    const T* mob = L.mobn;
+    T sm = T(0);
+    if (L.px || i < L.m1) sm += mob[k] + mob[k + 1];
+    if (L.px || i > 1) sm += mob[k] + mob[k - 1];
+    if (j < L.m2) sm += mob[k] + mob[k + W];
+    if (j > 1) sm += mob[k] + mob[k - W];
+    A[4][0] = -ih;
+    A[4][1] = ih;
+    A[4][2] = -ih;
+    A[4][3] = ih;
+    A[4][4] = T(0.5) * P.alpha * P.alpha * P.iPe * sm * ih2;
+  }
+  b[4] = op_p(P, L, k) - L.fp[k];
+  const bool act[4] = {a0, a1, a2, a3};
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+    if (!act[r]) {
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        A[r][c] = T(0);
+        A[c][r] = T(0);
+      }
+      A[r][r] = T(1);
+    }
+  solve5(A, b);
+  if (!ok) return;
+  T x = q == 0 ? b[0] : q == 1 ? b[1] : q == 2 ? b[2] : b[3];
+  if (mine) {
+    if (q == 0) store_u(L, eW, j, L.u[kW] - omega * x);
+    else if (q == 1) store_u(L, i, j, L.u[k] - omega * x);
+    else if (q == 2) store_v(L, i, j - 1, L.v[k - W] - omega * x);
+    else store_v(L, i, j, L.v[k] - omega * x);
+  }
+  if (q == 0) store_cell(L, L.p, i, j, L.p[k] - omega * b[4]);
+}
+
+// teams of four lanes while the colour fits in four warps (one per sub-partition)
+constexpr int QN_TEAM_MAX_SLOTS = 32;
+
 template <typename T, class Form>
 __device__ void smooth_block(const Prm<T>& P, const Lv<T>& L, T omega, int coupled) {
-  int n = L.m1 * L.m2;
   const int kcol = L.kcol;
   if (coupled) {
     for (int col = 0; col < kcol; ++col) {
-      for (int t = threadIdx.x; t < n; t += blockDim.x) {
-        int i = t % L.m1 + 1, j = t / L.m1 + 1;
-        if (vanka_colour(L, i, j) == col) coupled_cell<T, Form>(P, L, i, j, omega);
+      ColourSlots cs = vanka_slots(L, col);
+      for (int t = threadIdx.x; t < cs.n; t += blockDim.x) {
+        int i, j;
+        if (vanka_slot_cell(L, col, cs, t, i, j)) coupled_cell<T, Form>(P, L, i, j, omega);
       }
       __syncthreads();
     }
     return;
   }
+  const int mpr = (L.m1 + 1) / 2;
   for (int col = 0; col < 2; ++col) {
-    for (int t = threadIdx.x; t < n; t += blockDim.x) {
-      int i = t % L.m1 + 1, j = t / L.m1 + 1;
-      if (((i + j) & 1) == col) ch_cell<T, Form>(P, L, i, j);
+    for (int t = threadIdx.x; t < mpr * L.m2; t += blockDim.x) {
+      int j = t / mpr + 1;
+      int i = (((col - j) & 1) ? 1 : 2) + 2 * (t % mpr);
+      if (i <= L.m1) ch_cell<T, Form>(P, L, i, j);
     }
     __syncthreads();
   }
+  constexpr bool team_ok = std::is_same<Form, FullForm>::value && sizeof(T) == 8;
   for (int col = 0; col < kcol; ++col) {
-    for (int t = threadIdx.x; t < n; t += blockDim.x) {
-      int i = t % L.m1 + 1, j = t / L.m1 + 1;
-      if (vanka_colour(L, i, j) == col) vanka_cell<T, Form>(P, L, i, j, omega);
+    ColourSlots cs = vanka_slots(L, col);
+    if (team_ok && cs.n <= QN_TEAM_MAX_SLOTS) {
+      int t = threadIdx.x;
+      if ((t & ~31) < 4 * cs.n) {  // warp-uniform: the warp holds at least one team
+        int i = 1, j = 1;
+        bool ok = (t >> 2) < cs.n && vanka_slot_cell(L, col, cs, t >> 2, i, j);
+        if (!ok) i = j = 1;
+        vanka_team<T>(P, L, i, j, ok, omega);
+      }
+    } else {
+      for (int t = threadIdx.x; t < cs.n; t += blockDim.x) {
+        int i, j;
+        if (vanka_slot_cell(L, col, cs, t, i, j)) vanka_cell<T, Form>(P, L, i, j, omega);
+      }
     }
     __syncthreads();
   }
@@ -1186,14 +1440,16 @@ void launch_add_op(const Prm<T>& P, const Lv<T>& L, cudaStream_t s) {
 }
 template <typename T, class Form>
 void launch_ch(const Prm<T>& P, const Lv<T>& L, int colour, cudaStream_t s) {
-  k_ch<T, Form><<<grid2((L.m1 + 1) / 2, L.m2), dim3(BX, BY), 0, s>>>(P, L, colour);
+  int n = (L.m1 + 1) / 2 * L.m2;
+  if (n <= 0) return;
+  k_ch<T, Form><<<(n + 63) / 64, 64, 0, s>>>(P, L, colour);
   ++g_launches;
 }
 template <typename T, class Form>
 void launch_vanka(const Prm<T>& P, const Lv<T>& L, int colour, T omega, cudaStream_t s) {
-  int stride = L.c8 ? 4 : L.kcol;
-  k_vanka<T, Form><<<grid2((L.m1 + stride - 1) / stride, L.m2), dim3(BX, BY), 0, s>>>(P, L, colour,
-                                                                                       omega);
+  int n = vanka_slots(L, colour).n;
+  if (n <= 0) return;
+  k_vanka<T, Form><<<(n + SNT - 1) / SNT, SNT, 0, s>>>(P, L, colour, omega);
   ++g_launches;
 }
 template <typename T, class Form>
@@ -1209,9 +1465,9 @@ void launch_coarse_vcycle(const Prm<T>& P, const Lv<T>* levels, int n, int nu1, 
 
 template <typename T, class Form>
 void launch_coupled(const Prm<T>& P, const Lv<T>& L, int colour, T omega, cudaStream_t s) {
-  int stride = L.c8 ? 4 : L.kcol;
-  k_coupled<T, Form><<<grid2((L.m1 + stride - 1) / stride, L.m2), dim3(BX, BY), 0, s>>>(P, L, colour,
-                                                                                         omega);
+  int n = vanka_slots(L, colour).n;
+  if (n <= 0) return;
+  k_coupled<T, Form><<<(n + SNT - 1) / SNT, SNT, 0, s>>>(P, L, colour, omega);
   ++g_launches;
 }
 

@@ -103,8 +103,10 @@ __device__ __forceinline__ T lap_h2(const T* kap, const T* phi, int k, int pitch
 }
 
 // (pm-num-phase) with the advection (e1e2) of App. A.4
+// (the overloads taking densities let a caller that already holds rho(c) of
+// the cell and its neighbours skip the divisions; the values are the same)
 template <typename T>
-__device__ __forceinline__ T op_c(const Prm<T>& P, const Lv<T>& L, int k) {
+__device__ __forceinline__ T op_c(const Prm<T>& P, const Lv<T>& L, int k, T rho) {
   const int W = L.pitch;
   const T* cn = L.cn;
   const T* rn = L.rhon;
@@ -112,18 +114,23 @@ __device__ __forceinline__ T op_c(const Prm<T>& P, const Lv<T>& L, int k) {
   T adv = rn[k + 1] * L.Tx[k] * L.u[k] + rn[k - 1] * L.Tx[k - 1] * L.u[k - 1] +
           rn[k + W] * L.Ty[k] * L.v[k] + rn[k - W] * L.Ty[k - W] * L.v[k - W];
   T diff = lap_h2(L.mobn, L.mu, k, W) + P.alpha * lap_h2(L.mobn, L.p, k, W);
-  return rho_of(P, c) * (c - cnk) * P.idt + adv - P.iPe * L.ih2 * diff;
+  return rho * (c - cnk) * P.idt + adv - P.iPe * L.ih2 * diff;
+}
+template <typename T>
+__device__ __forceinline__ T op_c(const Prm<T>& P, const Lv<T>& L, int k) {
+  return op_c(P, L, k, rho_of(P, L.c[k]));
 }
 
 // (pm-num-chem) with the time-averaged gradient term (pointwise G)
+// rq[f]: rho(c) of the neighbours k + 1, k - 1, k + W, k - W
 template <typename T>
-__device__ __forceinline__ T op_mu(const Prm<T>& P, const Lv<T>& L, int k) {
+__device__ __forceinline__ T op_mu(const Prm<T>& P, const Lv<T>& L, int k, T rho, const T (&rq)[4]) {
   const int W = L.pitch;
   const T* c = L.c;
   const T* cn = L.cn;
   const T* rn = L.rhon;
   T ck = c[k], cnk = cn[k];
-  T rho = rho_of(P, ck), rnk = rn[k];
+  T rnk = rn[k];
   T rh = T(0.5) * (rho + rnk);
   T r = -P.alpha * rho * rnk;
   T bulk = rh * gsec(ck, cnk) + T(0.5) * (Fdw(ck) + Fdw(cnk)) * r;
@@ -135,11 +142,18 @@ __device__ __forceinline__ T op_mu(const Prm<T>& P, const Lv<T>& L, int k) {
 #pragma unroll
   for (int f = 0; f < 4; ++f) {
     int q = k + off[f];
-    T rq = T(0.5) * (rho_of(P, c[q]) + rn[q]);
-    div += (rh + rq) * ((c[q] + cn[q]) - chk);
+    T rf = T(0.5) * (rq[f] + rn[q]);
+    div += (rh + rf) * ((c[q] + cn[q]) - chk);
   }
   div *= T(0.25) * L.ih2;  // 1/2 (face average) * 1/2 (c^{n+1/2}) / h^2
   return rho * L.mu[k] - P.K * bulk - grad + P.Lam * div;
+}
+template <typename T>
+__device__ __forceinline__ T op_mu(const Prm<T>& P, const Lv<T>& L, int k) {
+  const int W = L.pitch;
+  const T rq[4] = {rho_of(P, L.c[k + 1]), rho_of(P, L.c[k - 1]), rho_of(P, L.c[k + W]),
+                   rho_of(P, L.c[k - W])};
+  return op_mu(P, L, k, rho_of(P, L.c[k]), rq);
 }
 
 // (pm-num-mass)
@@ -153,12 +167,12 @@ __device__ __forceinline__ T op_p(const Prm<T>& P, const Lv<T>& L, int k) {
 
 // x row of (pm-num-mx) at edge u_{i+1/2,j} (array index k = at(i,j)); cells k (left), k+1 (right),
 // vertices k (top, (i+1/2, j+1/2)) and k-W (bottom); (e1e1-1), (e1e1-2) and (e1e1)
+// (Ar = (rho(c_k) + rho(c_{k+1})) / 2, the density average on the edge)
 template <typename T>
-__device__ __forceinline__ T op_u(const Prm<T>& P, const Lv<T>& L, int k) {
+__device__ __forceinline__ T op_u(const Prm<T>& P, const Lv<T>& L, int k, T Ar) {
   const int W = L.pitch;
   const T *u = L.u, *vis = L.visn, *rn = L.rhon;
   T ue = u[k];
-  T Ar = T(0.5) * (rho_of(P, L.c[k]) + rho_of(P, L.c[k + 1]));
   T dxl = (ue - u[k - 1]) * L.ih, dxr = (u[k + 1] - ue) * L.ih;
   T dvl = dxl + (L.v[k] - L.v[k - W]) * L.ih;
   T dvr = dxr + (L.v[k + 1] - L.v[k + 1 - W]) * L.ih;
@@ -173,15 +187,18 @@ __device__ __forceinline__ T op_u(const Prm<T>& P, const Lv<T>& L, int k) {
                             (vr * dvr - vl * dvl) * T(1.0 / 3.0));
   return time + conv + press + st + visc;
 }
+template <typename T>
+__device__ __forceinline__ T op_u(const Prm<T>& P, const Lv<T>& L, int k) {
+  return op_u(P, L, k, T(0.5) * (rho_of(P, L.c[k]) + rho_of(P, L.c[k + 1])));
+}
 
 // y row of (pm-num-mx) at edge v_{i,j+1/2} (index k = at(i,j)); cells k (bottom), k+W (top),
 // vertices k (east, (i+1/2, j+1/2)) and k-1 (west); plus gravity (1/Fr) A_y rho^n
 template <typename T>
-__device__ __forceinline__ T op_v(const Prm<T>& P, const Lv<T>& L, int k) {
+__device__ __forceinline__ T op_v(const Prm<T>& P, const Lv<T>& L, int k, T Ar) {
   const int W = L.pitch;
   const T *v = L.v, *vis = L.visn, *rn = L.rhon;
   T ve = v[k];
-  T Ar = T(0.5) * (rho_of(P, L.c[k]) + rho_of(P, L.c[k + W]));
   T dyb = (ve - v[k - W]) * L.ih, dyt = (v[k + W] - ve) * L.ih;
   T dvb = dyb + (L.u[k] - L.u[k - 1]) * L.ih;
   T dvt = dyt + (L.u[k + W] - L.u[k + W - 1]) * L.ih;
@@ -195,6 +212,10 @@ __device__ __forceinline__ T op_v(const Prm<T>& P, const Lv<T>& L, int k) {
   T visc = -P.iRe * L.ih * ((L.Av[k] * De - L.Av[k - 1] * Dw) + (vt * dyt - vb * dyb) +
                             (vt * dvt - vb * dvb) * T(1.0 / 3.0));
   return time + conv + press + st + visc + P.Fr_inv * Arn;
+}
+template <typename T>
+__device__ __forceinline__ T op_v(const Prm<T>& P, const Lv<T>& L, int k) {
+  return op_v(P, L, k, T(0.5) * (rho_of(P, L.c[k]) + rho_of(P, L.c[k + L.pitch])));
 }
 
 // ---------------------------------------------------------------------------

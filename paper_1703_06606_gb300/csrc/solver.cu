@@ -5,6 +5,7 @@
 // kernels of kernels.cu; this file only allocates, sequences and copies.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -360,16 +361,27 @@ int fused_from(const qnsch_s* s, const std::vector<Lv<T>>& Ls) {
   return s->nlev;
 }
 
+// Sweeps on the coarsest grid: nu_coarse on a grid at most 4 cells across,
+// nu_coarse * ceil(n/4)^2 when its longest side n is larger (a periodic width
+// that stopped coarsening under a tall domain), since the pressure and
+// chemical-potential modes there decay at a rate set by n.
+static int coarse_sweeps(const qnsch_s* s) {
+  int n = std::max(s->L[s->nlev - 1].m1, s->L[s->nlev - 1].m2);
+  int q = std::max(1, (n + 3) / 4);
+  return s->nuc * q * q;
+}
+
 // FAS V-cycle (Sec. 7.1) from level l on the level set Ls
 template <typename T, class Form>
 void vcycle(qnsch_s* s, const std::vector<Lv<T>>& Ls, const Prm<T>& P, int l) {
   if (l >= fused_from(s, Ls)) {
-    qn::launch_coarse_vcycle<T, Form>(P, &Ls[l], s->nlev - l, s->nu1, s->nu2, s->nuc, s->kcol,
-                                      (T)s->omega, s->coupled, s->stream);
+    qn::launch_coarse_vcycle<T, Form>(P, &Ls[l], s->nlev - l, s->nu1, s->nu2, coarse_sweeps(s),
+                                      s->kcol, (T)s->omega, s->coupled, s->stream);
     return;
   }
   if (l == s->nlev - 1) {
-    for (int k = 0; k < s->nuc; ++k) smooth<T, Form>(s, Ls, P, l);
+    int nc = coarse_sweeps(s);
+    for (int k = 0; k < nc; ++k) smooth<T, Form>(s, Ls, P, l);
     return;
   }
   for (int k = 0; k < s->nu1; ++k) smooth<T, Form>(s, Ls, P, l);
@@ -566,7 +578,7 @@ int cycle_graph(qnsch_s* s, const Prm<double>& P) {
     drop_graph(s);
     s->ev_used = 0;
     if (s->prof) {  // create the timing events before capture begins
-      int pairs = s->L[0].kcol * (s->nlev == 1 ? s->nuc : s->nu1 + s->nu2);
+      int pairs = s->L[0].kcol * (s->nlev == 1 ? coarse_sweeps(s) : s->nu1 + s->nu2);
       while ((int)s->ev.size() < 2 * pairs && (int)s->ev.size() < MAX_PROF_EVENTS) {
         cudaEvent_t e;
         if (cudaEventCreate(&e) != cudaSuccess) {

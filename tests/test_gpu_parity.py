@@ -268,11 +268,12 @@ def test_mixed_precision_step_meets_fp64_tolerance(qn, case):
     assert abs(m1[0] - m0[0]) <= 1e-12 * m0[0] and abs(m1[1] - m0[1]) <= 1e-12 * m0[1]
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_fused_coarse_levels_match_per_level_launches(qn, precision):
-    """The single-block V-cycle of the small levels runs the same per-cell code in
-    the same colour order as the per-level launches: the iterates agree to rounding."""
-    P = W.small_case(64, 96, False)
+@pytest.mark.parametrize("precision,px", [(0, False), (0, True), (1, False), (1, True)])
+def test_fused_coarse_levels_match_per_level_launches(qn, precision, px):
+    """The single-block V-cycle of the small levels (FP64: four-lane Vanka teams
+    on the smallest) runs the same arithmetic in the same colour order as the
+    per-level launches: the iterates agree to rounding."""
+    P = W.small_case(64, 96, px)
     f = P.fields()
     out = []
     for fuse in (0, 10 ** 6):
@@ -339,3 +340,52 @@ def test_coupled_mixed_step_512(qn):
     assert resg <= P.tol and ng <= nr + 4
     errs = {k: relerr(v, r.get_fields()[k]) for k, v in g.get_fields().items()}
     assert max(errs.values()) <= 1e-7, errs
+
+
+def _rt(m1, m2):
+    P = W.rayleigh_taylor_1024x4096()
+    P.m1, P.m2 = m1, m2
+    P.Cn = 2.5 / m1
+    P.Pe = 1.0 / P.Cn
+    return P
+
+
+@pytest.mark.parametrize("coupled,fuse", [(0, 512), (1, 512), (0, 0)])
+def test_vcycle_parity_tall_periodic(qn, coupled, fuse):
+    """Periodic 1 x 4 box: width stops at 4, coarsest grid 4 x 16 with the
+    scaled coarsest sweeps; fused and per-level coarse paths both match."""
+    P = _rt(64, 256)
+    g = qn.Solver(**P.create_kwargs(), coupled=coupled, fuse_cells=fuse)
+    r = RefSolver(**P.create_kwargs(), coupled=coupled)
+    for s in (g, r):
+        s.set_fields(P.fields())
+        s.begin_step(P.dt)
+    assert g.levels == r.levels == 5
+    for _ in range(3):
+        ng = g.vcycle()
+        nr = r.vcycle()
+        same_fields(g.get_iterate(), r.get_iterate(), 1e-10)
+        assert np.allclose(ng, nr, rtol=1e-6, atol=1e-14)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_rayleigh_taylor_full_size_step(qn, precision):
+    """Rayleigh-Taylor 1024 x 4096 (4.2 M cells, 9 levels): one coupled step
+    converges; the oracle's own residual of the GPU's new state is at the
+    tolerance, and mass is conserved to round-off."""
+    P = W.rayleigh_taylor_1024x4096()
+    f0 = P.fields()
+    g = qn.Solver(**P.create_kwargs(), tol=P.tol, coupled=1, precision=precision)
+    g.set_fields(f0)
+    m0 = g.mass()
+    ng, res = g.step(P.dt)
+    assert res <= P.tol and ng < 50
+    f1 = g.get_fields()
+    m1 = g.mass()
+    assert abs(m1[0] - m0[0]) <= 1e-12 * abs(m0[0]) and abs(m1[1] - m0[1]) <= 1e-12 * abs(m0[1])
+    r = RefSolver(**P.create_kwargs(), tol=P.tol, coupled=1)
+    r.set_fields(f0)
+    r.begin_step(P.dt)
+    r.set_iterate(f1)
+    _, norms = r.residual()
+    assert max(norms[:5]) <= 2 * P.tol, norms[:5]

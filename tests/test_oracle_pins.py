@@ -579,3 +579,21 @@ def test_vcycle_contracts():
         hist = [max(s.vcycle()[:5]) for _ in range(6)]
         rates = [hist[k + 1] / hist[k] for k in range(1, 5)]
         assert max(rates) < 0.35, hist
+
+
+@pytest.mark.parametrize("coupled", [0, 1])
+def test_vcycle_contracts_on_tall_periodic_domain(coupled):
+    """A periodic 1 x 4 box stops coarsening at width 4, leaving a 4 x 16
+    coarsest grid; with the coarsest sweeps scaled by its long side the cycle
+    still contracts (a fixed 4 sweeps stalls near 0.9 per cycle here)."""
+    P = W.rayleigh_taylor_1024x4096()
+    P.m1, P.m2 = 32, 128
+    P.Cn = 0.08
+    P.Pe = 1.0 / P.Cn
+    s = RefSolver(**P.create_kwargs(), coupled=coupled)
+    s.set_fields(P.fields())
+    assert s.levels == 4
+    s.begin_step(P.dt)
+    hist = [max(s.vcycle()[:5]) for _ in range(7)]
+    rates = [hist[k + 1] / hist[k] for k in range(2, 6)]
+    assert max(rates) < 0.4, hist
