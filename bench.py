@@ -358,7 +358,7 @@ def run_ours(args, rank, world, local_rank):
                      "frac": achieved / peak, "traffic": VANKA_FP64_TRAFFIC_BYTES,
                      "kernel": "k_vanka<double> finest level",
                      "launches_timed": prof_n, "avg_launch_us": avg_ms * 1e3,
-                     "peak_source": "measured FP64 FMA throughput (profiles/fp64_fp32_peak_probe.md)"},
+                     "peak_source": "measured FP64 FMA throughput of this GPU model (DFMA loop probe)"},
         "clocks": clk.summary(),
     }
     if variants:
@@ -380,12 +380,12 @@ def run_ours(args, rank, world, local_rank):
 
 
 # algorithmic FP64 operations per Vanka cell visit (add/sub/mul/div = 1, fused
-# multiply-add = 2), counted from the formulas of k_vanka; see the design doc
-VANKA_FP64_FLOPS_PER_VISIT = 620.0
+# multiply-add = 2), counted from the formulas of one 5x5 Vanka block (Sec. 7.1)
+VANKA_FP64_FLOPS_PER_VISIT = 557.0
 # dram__bytes_read.sum + dram__bytes_write.sum of one finest-level k_vanka<double> launch at
-# 256x512 (ncu, profiles/k_vanka_fp64_drop_1024x1024.md and the design doc); None once the kernel
-# changes after the capture
-VANKA_FP64_TRAFFIC_BYTES = 26.47e6
+# 256x512 from one ncu capture of the current kernel; None once the kernel changes after
+# the capture
+VANKA_FP64_TRAFFIC_BYTES = 26.466e6
 # measured FP64 FMA throughput of one GB300 (dependent-chain-free DFMA loop)
 FP64_PEAK_TFLOPS = 1.193
 

@@ -87,7 +87,8 @@ int qnsch_destroy(qnsch_t* h);
 int qnsch_footprint(const qnsch_grid* grid, int precision, size_t* bytes);
 
 /* Options (key: default): "nu1": 2, "nu2": 2 (pre/post smoothing steps),
-   "nu_coarse": 4 (smoothing steps on the coarsest level), "tol": 1e-9,
+   "nu_coarse": 4 (smoothing steps on the coarsest level; a coarsest grid whose
+   longest side n exceeds 4 cells gets nu_coarse * ceil(n/4)^2), "tol": 1e-9,
    "maxcyc": 50, "omega_vanka": 1, "M": Cn, "eta_st": eta(rho1, rho2),
    "eps_mob": Cn, "precision": 0, "graphs": 1, "fuse_cells": 512,
    "fuse_cells32": 2048, "coupled": 0.  Unknown keys give QNSCH_EINVAL.

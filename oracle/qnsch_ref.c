@@ -15,7 +15,7 @@
  * Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg use it.
  * It shares no code with the CUDA library.
  *
- * Readings of the paper that this file takes (each also listed in the design doc):
+ * Readings of the paper that this file takes:
  *   R1 (e1e1-2): the divergence correction of the x-momentum row is
  *       1/2[D_x(rho a_x u^n) + Dfrak_y(Acal rho Acal_x v^n)] u, and of the
  *       y-row 1/2[Dfrak_x(Acal rho Acal_y u^n) + D_y(rho a_y v^n)] v; these are
@@ -1038,7 +1038,7 @@ static double energy_of(const ref_params* P, const ref_level* L, const double* c
    squares: 1/2||sqrt(rho^n)(u - u^n)||^2 + (dt/Re)||sqrt(mu^n) grad_d u||^2
    + (dt/(3Re))||sqrt(mu^n) div_d u||^2 + (dt/(M Pe))||sqrt(m^n) grad_D(mu + alpha p)||^2.
    Vertex terms carry weight 1/2 on walls (vertex inner product, App. A.3),
-   evaluated with the reflected ghosts (reading R10 in the design doc). */
+   evaluated with the reflected ghosts. */
 static double dissipation_of(const ref_params* P, const ref_level* L, double dt) {
   double h = L->h, h2 = h * h;
   double kin = 0.0, vc = 0.0, vv = 0.0, div = 0.0, ch = 0.0;

@@ -326,11 +326,15 @@ def _newton(s, x0):
     return _unpack(s, z, like), np.max(np.abs(F(z)))
 
 
-@pytest.mark.parametrize("m1,m2,px", [(8, 8, False), (8, 8, True), (8, 12, False)])
-def test_multigrid_fixed_point_equals_newton_direct_solve(m1, m2, px):
+@pytest.mark.parametrize("m1,m2,px,coupled", [(8, 8, False, 0), (8, 8, True, 0), (8, 12, False, 0),
+                                              (8, 8, False, 1), (8, 12, True, 1)])
+def test_multigrid_fixed_point_equals_newton_direct_solve(m1, m2, px, coupled):
+    """The converged V-cycle iteration (paper's separate sweeps, or the coupled
+    7x7 block) lands on the solution that Newton's method with a direct solve
+    of each linearised system finds for the same discrete equations."""
     P = W.small_case(m1, m2, px)
     P.Cn, P.Pe = 0.1, 10.0
-    s = RefSolver(**P.create_kwargs(), tol=1e-13, maxcyc=200)
+    s = RefSolver(**P.create_kwargs(), tol=1e-13, maxcyc=200, coupled=coupled)
     f0 = P.fields()
     s.set_fields(f0)
     n, res = s.step(P.dt)
