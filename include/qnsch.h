@@ -143,6 +143,28 @@ int qnsch_vcycle(qnsch_t* h, double* residual_norms10);
 /* Accept the iterate as level n+1. */
 int qnsch_commit_step(qnsch_t* h);
 
+/* Diagnostics of the experiments of Sec. 8, reduced in FP64 on the device from
+   the committed state (the fields qnsch_get_fields returns) into host out[9]:
+     out[0] V_c = sum c a_y(v) / sum c, the rise velocity of Sec. 8.2 (a_y(v)
+            the mean of the cell's two ns edges);
+     out[1] sum c y / sum c, the height of the c = 1 fluid's centroid;
+     out[2] max |div|, out[3] (h^2 sum div^2)^(1/2), out[4] max(div, 0),
+            out[5] max(-div, 0), div = d_x u + d_y v per cell (Sec. 8.2);
+     out[6] a1 = (2/m1) sum_i eta_i cos(2 pi x_i / Lx), eta_i = h sum_j c_ij:
+            the first cosine mode of the c = 1 column height; for an interface
+            y0 + a cos(2 pi x / Lx) with c = 1 below, a1 = a (the capillary-wave
+            amplitude of Sec. 8.1);
+     out[7], out[8] the highest and lowest upward crossing c_j >= 1/2 > c_{j+1}
+            over all columns, linear between cell centres: the top of the rising
+            and the bottom of the falling fluid of Sec. 8.3 (0 and Ly if none).
+   Wall-normal edge velocities count as zero; periodic edges wrap.  Blocks
+   until the values are on the host. */
+#define QNSCH_NDIAG 9
+int qnsch_diagnostics(const qnsch_t* h, double* out);
+/* d_x u + d_y v of the committed state into host div[(j-1)*m1 + (i-1)],
+   m1*m2 doubles.  Blocks until copied. */
+int qnsch_divergence(const qnsch_t* h, double* div);
+
 /* Mass of the committed state (Thm. 6.1): h^2 sum rho(c), h^2 sum rho(c) c. */
 int qnsch_mass(const qnsch_t* h, double* mass_rho, double* mass_rhoc);
 /* Discrete energy E_h of the committed state (Thm. 6.2, norms of App. A.7), and

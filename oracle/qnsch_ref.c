@@ -1474,6 +1474,100 @@ int qnsch_ref_energy(const ref_solver* s, double* E) {
   return REF_OK;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Diagnostics of the experiments of Sec. 8, on the committed state          */
+/* ------------------------------------------------------------------------ */
+
+/* u_{i+1/2,j}, i = 0..m1: zero on no-slip walls, period m1 in x */
+static double edge_u(const ref_solver* s, int i, int j) {
+  const ref_level* L = &s->lev[0];
+  if (!L->px && (i == 0 || i == L->m1)) return 0.0;
+  if (L->px && i == 0) i = L->m1;
+  return s->u[UI(L, i, j)];
+}
+
+/* v_{i,j+1/2}, j = 0..m2: zero on the no-slip walls in y */
+static double edge_v(const ref_solver* s, int i, int j) {
+  const ref_level* L = &s->lev[0];
+  if (j == 0 || j == L->m2) return 0.0;
+  return s->v[VI(L, i, j)];
+}
+
+/* discrete divergence d_x u + d_y v of cell (i,j) (Sec. 5; the quantity
+   plotted for the rising droplet, Sec. 8.2) */
+static double div_at(const ref_solver* s, int i, int j) {
+  double h = s->lev[0].h;
+  return (edge_u(s, i, j) - edge_u(s, i - 1, j)) / h + (edge_v(s, i, j) - edge_v(s, i, j - 1)) / h;
+}
+
+int qnsch_ref_divergence(const ref_solver* s, double* out) {
+  if (!s || !out) return REF_EINVAL;
+  const ref_level* L = &s->lev[0];
+  for (int j = 1; j <= L->m2; ++j)
+    for (int i = 1; i <= L->m1; ++i) out[(size_t)(j - 1) * L->m1 + (i - 1)] = div_at(s, i, j);
+  return REF_OK;
+}
+
+/* out[0] rise velocity V_c = sum c a_y(v) / sum c (Sec. 8.2), a_y(v) the mean
+   of the two ns edges of the cell; out[1] centroid height sum c y / sum c;
+   out[2] max |div|, out[3] (h^2 sum div^2)^(1/2), out[4] max(div, 0),
+   out[5] max(-div, 0); out[6] a1 = (2/m1) sum_i eta_i cos(2 pi x_i / Lx), the
+   first cosine mode of the column height eta_i = h sum_j c_ij of the c = 1
+   fluid: for an interface y0 + a cos(2 pi x / Lx) with c = 1 below, a1 = a
+   (the capillary-wave amplitude of Sec. 8.1, where the paper's interface
+   0.5 - H0 cos(2 pi x) has a1 = -H0); out[7], out[8] the highest and lowest
+   upward crossing c_j >= 1/2 > c_{j+1} over all columns, by linear
+   interpolation between cell centres (top of the rising and bottom of the
+   falling fluid, Sec. 8.3); 0 and Ly when no column has a crossing. */
+int qnsch_ref_diagnostics(const ref_solver* s, double* out) {
+  if (!s || !out) return REF_EINVAL;
+  const ref_level* L = &s->lev[0];
+  const int m1 = L->m1, m2 = L->m2;
+  const double h = L->h, Lx = m1 * h, Ly = m2 * h;
+  const double pi = 3.14159265358979323846;
+  double sc = 0.0, scv = 0.0, scy = 0.0, d2 = 0.0, dmax = 0.0, dpos = 0.0, dneg = 0.0;
+  for (int j = 1; j <= m2; ++j)
+    for (int i = 1; i <= m1; ++i) {
+      double c = s->c[CI(L, i, j)];
+      double vbar = 0.5 * (edge_v(s, i, j) + edge_v(s, i, j - 1));
+      double d = div_at(s, i, j);
+      sc += c;
+      scv += c * vbar;
+      scy += c * ((j - 0.5) * h);
+      d2 += d * d;
+      if (fabs(d) > dmax) dmax = fabs(d);
+      if (d > dpos) dpos = d;
+      if (-d > dneg) dneg = -d;
+    }
+  double Hs = 0.0, ytop = 0.0, ybot = Ly;
+  int found = 0;
+  for (int i = 1; i <= m1; ++i) {
+    double eta = 0.0;
+    for (int j = 1; j <= m2; ++j) eta += s->c[CI(L, i, j)];
+    eta *= h;
+    Hs += eta * cos(2.0 * pi * ((i - 0.5) * h) / Lx);
+    for (int j = 1; j < m2; ++j) {
+      double a = s->c[CI(L, i, j)], b = s->c[CI(L, i, j + 1)];
+      if (a >= 0.5 && b < 0.5) {
+        double y = (j - 0.5) * h + h * (a - 0.5) / (a - b);
+        if (!found || y > ytop) ytop = y;
+        if (!found || y < ybot) ybot = y;
+        found = 1;
+      }
+    }
+  }
+  out[0] = scv / sc;
+  out[1] = scy / sc;
+  out[2] = dmax;
+  out[3] = sqrt(h * h * d2);
+  out[4] = dpos;
+  out[5] = dneg;
+  out[6] = 2.0 / m1 * Hs;
+  out[7] = ytop;
+  out[8] = ybot;
+  return REF_OK;
+}
+
 int qnsch_ref_iterate_energy(const ref_solver* s, double* E) {
   if (!s || !E) return REF_EINVAL;
   if (!s->pending) return REF_ESTATE;

@@ -79,6 +79,11 @@ int qnsch_ref_energy(const ref_solver* s, double* E);
 int qnsch_ref_iterate_energy(const ref_solver* s, double* E);
 int qnsch_ref_iterate_dissipation(const ref_solver* s, double* D);
 int qnsch_ref_params(const ref_solver* s, double* out8);
+/* Sec. 8 diagnostics of the committed state (see qnsch_ref.c): out9 = {V_c,
+   centroid y, max|div|, l2 div, max expansion, max compression, a1, y_top,
+   y_bottom}; divergence field out[(j-1)*m1 + (i-1)], m1*m2 values. */
+int qnsch_ref_diagnostics(const ref_solver* s, double* out9);
+int qnsch_ref_divergence(const ref_solver* s, double* out);
 
 #ifdef __cplusplus
 }

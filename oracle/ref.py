@@ -68,6 +68,8 @@ def lib():
         L.qnsch_ref_iterate_energy.argtypes = [vp, p]
         L.qnsch_ref_iterate_dissipation.argtypes = [vp, p]
         L.qnsch_ref_params.argtypes = [vp, p]
+        L.qnsch_ref_diagnostics.argtypes = [vp, p]
+        L.qnsch_ref_divergence.argtypes = [vp, p]
         _lib = L
     return _lib
 
@@ -235,6 +237,22 @@ class RefSolver:
         e = ctypes.c_double()
         _check(lib().qnsch_ref_energy(self._h, ctypes.byref(e)), "energy")
         return e.value
+
+    DIAG_KEYS = ("Vc", "yc", "div_max", "div_l2", "div_expansion", "div_compression", "a1",
+                 "y_top", "y_bottom")
+
+    def diagnostics(self):
+        """Sec. 8 diagnostics of the committed state (rise velocity, centroid,
+        divergence extremes and l2 norm, capillary amplitude, interface tips)."""
+        out = np.zeros(9)
+        _check(lib().qnsch_ref_diagnostics(self._h, _ptr(out)), "diagnostics")
+        return dict(zip(self.DIAG_KEYS, out.tolist()))
+
+    def divergence(self):
+        """d_x u + d_y v of the committed state, shape (m2, m1)."""
+        out = np.zeros((self.m2, self.m1))
+        _check(lib().qnsch_ref_divergence(self._h, _ptr(out)), "divergence")
+        return out
 
     def iterate_energy(self):
         e = ctypes.c_double()

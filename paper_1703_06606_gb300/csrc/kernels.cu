@@ -1324,6 +1324,93 @@ __global__ void k_mass(Prm<T> P, Lv<T> L, const T* c, double* part) {
   block_sum_store<2>(val, part, 0);
 }
 
+// --------------------------------------------------------------------------
+// diagnostics of the experiments of Sec. 8 (FP64, committed state)
+// --------------------------------------------------------------------------
+// u_{i+1/2,j} for i = 0..m1 and v_{i,j+1/2} for j = 0..m2: zero on no-slip
+// walls, period m1 in x
+__device__ __forceinline__ double diag_u(const Lv<double>& L, const double* u, int i, int j) {
+  if (!L.px && (i == 0 || i == L.m1)) return 0.0;
+  if (L.px && i == 0) i = L.m1;
+  return u[L.at(i, j)];
+}
+__device__ __forceinline__ double diag_v(const Lv<double>& L, const double* v, int i, int j) {
+  if (j == 0 || j == L.m2) return 0.0;
+  return v[L.at(i, j)];
+}
+// d_x u + d_y v of cell (i,j)
+__device__ __forceinline__ double diag_div(const Lv<double>& L, const double* u, const double* v,
+                                           int i, int j) {
+  return (diag_u(L, u, i, j) - diag_u(L, u, i - 1, j)) / L.h +
+         (diag_v(L, v, i, j) - diag_v(L, v, i, j - 1)) / L.h;
+}
+
+// per cell: [0] |div|, [1] max(div, 0), [2] max(-div, 0) (block maxima), then
+// the sums [3] c, [4] c a_y(v), [5] c y, [6] div^2
+__global__ void k_diag_cells(Lv<double> L, const double* c, const double* u, const double* v,
+                             double* part) {
+  int i = blockIdx.x * BX + threadIdx.x + 1;
+  int j = blockIdx.y * BY + threadIdx.y + 1;
+  double val[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  if (i <= L.m1 && j <= L.m2) {
+    double d = diag_div(L, u, v, i, j);
+    double cc = c[L.at(i, j)];
+    double vbar = 0.5 * (diag_v(L, v, i, j) + diag_v(L, v, i, j - 1));
+    val[0] = fabs(d);
+    val[1] = fmax(d, 0.0);
+    val[2] = fmax(-d, 0.0);
+    val[3] = cc;
+    val[4] = cc * vbar;
+    val[5] = cc * ((j - 0.5) * L.h);
+    val[6] = d * d;
+  }
+  block_sum_store<7>(val, part, 3);
+}
+
+// one thread per column i: eta_i = h sum_j c_ij and the upward crossings
+// c_j >= 1/2 > c_{j+1} (linear between cell centres); [0] highest crossing,
+// [1] Ly - lowest crossing (block maxima), then the sums [2] eta_i cos(2 pi
+// x_i / Lx) and [3] columns with a crossing
+__global__ void __launch_bounds__(NT) k_diag_cols(Lv<double> L, const double* c, double* part) {
+  int i = blockIdx.x * NT + threadIdx.x + 1;
+  double val[4] = {0.0, 0.0, 0.0, 0.0};
+  if (i <= L.m1) {
+    const double h = L.h, Ly = L.m2 * h, Lx = L.m1 * h;
+    const double pi = 3.14159265358979323846;
+    double eta = 0.0, ytop = 0.0, ybot = Ly;
+    bool found = false;
+    double a = c[L.at(i, 1)];
+    eta += a;
+    for (int j = 1; j < L.m2; ++j) {
+      double b = c[L.at(i, j + 1)];
+      eta += b;
+      if (a >= 0.5 && b < 0.5) {
+        double y = (j - 0.5) * h + h * (a - 0.5) / (a - b);
+        if (!found || y > ytop) ytop = y;
+        if (!found || y < ybot) ybot = y;
+        found = true;
+      }
+      a = b;
+    }
+    eta *= h;
+    val[2] = eta * cos(2.0 * pi * ((i - 0.5) * h) / Lx);
+    if (found) {
+      val[0] = ytop;
+      val[1] = Ly - ybot;
+      val[3] = 1.0;
+    }
+  }
+  block_sum_store<4>(val, part, 2);
+}
+
+// divergence field, packed out[(j-1)*m1 + (i-1)]
+__global__ void k_div_field(Lv<double> L, const double* u, const double* v, double* out) {
+  int i = blockIdx.x * BX + threadIdx.x + 1;
+  int j = blockIdx.y * BY + threadIdx.y + 1;
+  if (i > L.m1 || j > L.m2) return;
+  out[(size_t)(j - 1) * L.m1 + (i - 1)] = diag_div(L, u, v, i, j);
+}
+
 // energy E_h (Thm. 6.2): per cell rho [a_x(u^2) + a_y(v^2)]/2 + (eps eta/(2We)) rho G(c)
 // + (eta/(eps We)) rho F(c) + rho y / Fr; weights passed in w[0..2]
 template <typename T>
@@ -1554,6 +1641,20 @@ void launch_norms_finalize(const Lv<T>& L, double* part, double* out10, cudaStre
   // part rows are [max x5, sum of squares x5]; out10 = [l2 x5, max x5] after the
   // host applies sqrt(h^2 *) to the sums; here: out[0..4] = max, out[5..9] = h^2 sum
   k_finalize<<<1, 256, 0, s>>>(part, nparts_cells(L), 10, 5, (double)L.h * (double)L.h, out10);
+  ++g_launches;
+}
+void launch_diag(const Lv<double>& L, const double* c, const double* u, const double* v,
+                 double* part, double* out11, cudaStream_t s) {
+  k_diag_cells<<<grid2(L.m1, L.m2), dim3(BX, BY), 0, s>>>(L, c, u, v, part);
+  k_finalize<<<1, 256, 0, s>>>(part, nparts_cells(L), 7, 3, 1.0, out11);
+  int nb = (L.m1 + NT - 1) / NT;
+  k_diag_cols<<<nb, NT, 0, s>>>(L, c, part);
+  k_finalize<<<1, 256, 0, s>>>(part, nb, 4, 2, 1.0, out11 + 7);
+  g_launches += 4;
+}
+void launch_div_field(const Lv<double>& L, const double* u, const double* v, double* out,
+                      cudaStream_t s) {
+  k_div_field<<<grid2(L.m1, L.m2), dim3(BX, BY), 0, s>>>(L, u, v, out);
   ++g_launches;
 }
 template <typename T>

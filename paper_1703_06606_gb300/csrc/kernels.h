@@ -36,6 +36,13 @@ template <typename T> void launch_restrict_frozen(const Lv<T>& F, const Lv<T>& C
 template <typename T> void launch_prolong(const Lv<T>& F, const Lv<T>& C, cudaStream_t s);
 template <typename T> void launch_gauge(const Lv<T>& L, double* part, double* scal, cudaStream_t s);
 template <typename T> void launch_norms_finalize(const Lv<T>& L, double* part, double* out10, cudaStream_t s);
+// Sec. 8 diagnostics of (c, u, v) on level L: out11[0..6] from the cells
+// (max|div|, max div+, max div-, sum c, sum c a_y v, sum c y, sum div^2),
+// out11[7..10] from the columns (max y_top, max Ly - y_bot, sum eta cos, count)
+void launch_diag(const Lv<double>& L, const double* c, const double* u, const double* v,
+                 double* part, double* out11, cudaStream_t s);
+void launch_div_field(const Lv<double>& L, const double* u, const double* v, double* out,
+                      cudaStream_t s);
 template <typename T>
 void launch_mass(const Prm<T>& P, const Lv<T>& L, const T* c, double* part, double* out2, cudaStream_t s);
 template <typename T>

@@ -118,7 +118,8 @@ struct qnsch_s {
   double *sc = nullptr, *smu = nullptr, *sp = nullptr, *su = nullptr, *sv = nullptr;
   // scratch: block partials and small results
   double* part = nullptr;
-  double* scal = nullptr;  // [0..9] norms, [16] p sum, [20..21] mass, [24] energy, [25] diss
+  double* scal = nullptr;  // [0..9] norms, [16] p sum, [20..21] mass, [24] energy, [25] diss,
+                           // [32..42] diagnostics
   double* hbuf = nullptr;  // pinned host mirror of scal
   double* stage = nullptr;  // device staging buffer for host-array I/O (one field)
   cudaStream_t stream = nullptr;       // work stream: the user's, else own_stream
@@ -259,10 +260,10 @@ int alloc_all(qnsch_s* s) {
   s->stage = (double*)dev_alloc(nstage * sizeof(double));
   if (!s->stage) return QNSCH_ENOMEM;
   s->blocks.push_back(s->stage);
-  s->scal = (double*)dev_alloc(32 * sizeof(double));
+  s->scal = (double*)dev_alloc(64 * sizeof(double));
   if (!s->scal) return QNSCH_ENOMEM;
   s->blocks.push_back(s->scal);
-  if (cudaMallocHost(&s->hbuf, 32 * sizeof(double)) != cudaSuccess) {
+  if (cudaMallocHost(&s->hbuf, 64 * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     return QNSCH_ENOMEM;
   }
@@ -762,7 +763,7 @@ int qnsch_footprint(const qnsch_grid* grid, int precision, size_t* bytes) {
   total += n0 * 5 * sizeof(double);                                           // committed state
   total += (size_t)qn::partial_rows_needed(grid->m1, grid->m2) * 10 * sizeof(double);
   total += (size_t)(grid->m1 + 1) * (grid->m2 + 1) * sizeof(double);         // staging
-  total += 32 * sizeof(double);
+  total += 64 * sizeof(double);
   *bytes = total;
   return QNSCH_OK;
 }
@@ -964,6 +965,42 @@ int qnsch_mass(const qnsch_t* s, double* mass_rho, double* mass_rhoc) {
   *mass_rho = m->hbuf[20];
   *mass_rhoc = m->hbuf[21];
   return QNSCH_OK;
+}
+
+int qnsch_diagnostics(const qnsch_t* s, double* out) {
+  if (!s || !out) return QNSCH_EINVAL;
+  qnsch_s* m = const_cast<qnsch_s*>(s);
+  const Lv<double>& F = s->L[0];
+  qn::launch_diag(F, s->sc, s->su, s->sv, s->part, s->scal + 32, s->stream);
+  cudaMemcpyAsync(m->hbuf + 32, s->scal + 32, 11 * sizeof(double), cudaMemcpyDeviceToHost,
+                  s->stream);
+  int rc = sync(s);
+  if (rc) return rc;
+  const double* a = m->hbuf + 32;  // cells: max x3, sums x4; columns: max x2, sums x2
+  double h = s->h, Ly = s->m2 * s->h;
+  out[0] = a[4] / a[3];
+  out[1] = a[5] / a[3];
+  out[2] = a[0];
+  out[3] = std::sqrt(h * h * a[6]);
+  out[4] = a[1];
+  out[5] = a[2];
+  out[6] = 2.0 / s->m1 * a[9];
+  bool any = a[10] > 0.0;
+  out[7] = any ? a[7] : 0.0;
+  out[8] = any ? Ly - a[8] : Ly;
+  return QNSCH_OK;
+}
+
+int qnsch_divergence(const qnsch_t* s, double* div) {
+  if (!s || !div) return QNSCH_EINVAL;
+  const Lv<double>& F = s->L[0];
+  qn::launch_div_field(F, s->su, s->sv, s->stage, s->stream);
+  if (cudaMemcpyAsync(div, s->stage, (size_t)s->m1 * s->m2 * sizeof(double),
+                      cudaMemcpyDeviceToHost, s->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return QNSCH_ECUDA;
+  }
+  return sync(s);
 }
 
 static int energy_of(const qnsch_s* s, const double* c, const double* u, const double* v,

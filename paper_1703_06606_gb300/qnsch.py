@@ -63,6 +63,8 @@ def lib():
         L.qnsch_vcycle.argtypes = [_VP, p]
         L.qnsch_commit_step.argtypes = [_VP]
         L.qnsch_mass.argtypes = [_VP, p, p]
+        L.qnsch_diagnostics.argtypes = [_VP, p]
+        L.qnsch_divergence.argtypes = [_VP, p]
         L.qnsch_energy.argtypes = [_VP, p, p]
         L.qnsch_iterate_energy.argtypes = [_VP, p, p]
         L.qnsch_residual.argtypes = [_VP, _VP, _VP, _VP, _VP, _VP, p]
@@ -277,6 +279,23 @@ class Solver:
         e, d = ctypes.c_double(), ctypes.c_double()
         _check(lib().qnsch_energy(self._h, ctypes.byref(e), ctypes.byref(d)), "qnsch_energy")
         return e.value, d.value
+
+    DIAG_KEYS = ("Vc", "yc", "div_max", "div_l2", "div_expansion", "div_compression", "a1",
+                 "y_top", "y_bottom")
+
+    def diagnostics(self):
+        """qnsch_diagnostics: Sec. 8 diagnostics of the committed state as a dict."""
+        out = np.zeros(9)
+        _check(lib().qnsch_diagnostics(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+               "qnsch_diagnostics")
+        return dict(zip(self.DIAG_KEYS, out.tolist()))
+
+    def divergence(self):
+        """qnsch_divergence: d_x u + d_y v of the committed state, shape (m2, m1)."""
+        out = np.zeros((self.m2, self.m1))
+        _check(lib().qnsch_divergence(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+               "qnsch_divergence")
+        return out
 
     def iterate_energy(self):
         e, d = ctypes.c_double(), ctypes.c_double()
