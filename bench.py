@@ -244,6 +244,37 @@ def run_ours(args, rank, world, local_rank):
                             "CH 2x2 red-black + Vanka 5x5 (5 colours)"}
             sv.close()
 
+    # ---- high-ratio stress cases: capillary wave at density ratio 1:1000 (256^2)
+    # and the droplet with the paper's own parameters (256x512, periodic x),
+    # FP64 with the paper's smoother and mixed precision with the coupled block
+    stress = None
+    if not args.no_stress:
+        stress = {}
+        for Ps in (workloads.capillary_ratio1000_256(), workloads.droplet_paper_256x512()):
+            for prec, coup in ((0, 0), (1, 1)):
+                ss = qnsch.Solver(**Ps.create_kwargs(), tol=Ps.tol, stream=stream,
+                                  precision=prec, coupled=coup)
+                ss.set_fields(Ps.fields())
+                for _ in range(min(args.warmup, 2)):
+                    ss.step(Ps.dt)
+                sev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                       for _ in range(5)]
+                scyc = []
+                torch.cuda.synchronize()
+                for k in range(5):
+                    flush.fill_(float(k))
+                    sev[k][0].record(stream)
+                    n, res = ss.step(Ps.dt)
+                    sev[k][1].record(stream)
+                    scyc.append(n)
+                torch.cuda.synchronize()
+                sms = [a.elapsed_time(b) for a, b in sev]
+                stress["%s/%s" % (Ps.name, "mixed_coupled" if prec else "fp64")] = {
+                    "value": Ps.cells * 5 / (sum(sms) / 1e3), "unit": UNIT,
+                    "ms_per_step": float(np.mean(sms)), "vcycles_per_step": float(np.mean(scyc)),
+                    "final_residual": res, "steps": 5, "tol": Ps.tol}
+                ss.close()
+
     # ---- batched: the 64-drop workload (grids 64^2 .. 512^2, rho ratio 2..100,
     # viscosity ratio 1..50), mixed precision, coupled smoother, all instances
     # advanced together by qnsch_batch_step
@@ -363,6 +394,8 @@ def run_ours(args, rank, world, local_rank):
     }
     if variants:
         line["variants"] = variants
+    if stress is not None:
+        line["stress"] = stress
     if batched is not None:
         line["batched"] = batched
     if serving is not None:
@@ -427,6 +460,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-stress", action="store_true")
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=32)

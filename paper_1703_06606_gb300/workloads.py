@@ -122,6 +122,26 @@ def rayleigh_taylor_1024x4096():
                    tol=1e-9, init="rt", init_args=dict(y0=2.0, A=0.1))
 
 
+def capillary_ratio1000_256():
+    """Capillary wave at density ratio 1:1000 (case 2 of Sec. 8.1): 256x256 on
+    [0,1]^2, periodic x, equal kinematic viscosities (mu = rho), Re = 100,
+    We = 1, Fr = 1, Cn = 0.005, Pe = 1/Cn, dt = 1e-3.  The heavy fluid (c = 1)
+    lies below the interface 0.5 + 0.01 cos(2 pi x), a gravity-capillary wave."""
+    return Problem("capillary_ratio1000_256", 256, 256, 1.0, True, 0, 1000.0, 1.0, 1000.0, 1.0,
+                   Re=100.0, We=1.0, Pe=200.0, Cn=0.005, Fr=1.0, dt=1e-3, steps=20, tol=1e-9,
+                   init="capillary", init_args=dict(y0=0.5, H0=0.01))
+
+
+def droplet_paper_256x512():
+    """The droplet with the paper's own parameters (Sec. 8.2): rho and mu ratio
+    1:10 (drop c = 1 light), Re = 100, We = 1, Fr = 0.98, Cn = 0.005, Pe = 1/Cn,
+    dt = 1e-3, on [0,1]x[0,2], 256x512, periodic x, drop of radius 0.25 at
+    (0.5, 0.5)."""
+    return Problem("droplet_paper_256x512", 256, 512, 1.0, True, 0, 0.1, 1.0, 0.1, 1.0,
+                   Re=100.0, We=1.0, Pe=200.0, Cn=0.005, Fr=0.98, dt=1e-3, steps=20, tol=1e-9,
+                   init="drop", init_args=dict(x0=0.5, y0=0.5, R=0.25))
+
+
 def batch_drops(n=64, seed=SEED):
     """n independent rising-drop instances with seeded grids and parameters."""
     rng = np.random.default_rng(seed)
