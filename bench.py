@@ -275,6 +275,34 @@ def run_ours(args, rank, world, local_rank):
                     "final_residual": res, "steps": 5, "tol": Ps.tol}
                 ss.close()
 
+    # ---- per-step cost on the workload of Sec. 9 (the paper's Table 2: CPU
+    # seconds per step of the primitive method, m = 16..256, dt = 16 h^2), FP64
+    table2 = None
+    if not args.no_table2:
+        paper_s = {16: 2.913e-2, 32: 1.659e-1, 64: 2.659e-1, 128: 1.027, 256: 2.622}
+        table2 = {}
+        for m in (16, 32, 64, 128, 256):
+            Pm = workloads.convergence_test(m)
+            sm = qnsch.Solver(**Pm.create_kwargs(), tol=Pm.tol, maxcyc=100, stream=stream)
+            sm.set_fields(Pm.fields())
+            sm.step(Pm.dt)
+            mev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(4)]
+            mcyc = []
+            torch.cuda.synchronize()
+            for k in range(4):
+                mev[k][0].record(stream)
+                n, _ = sm.step(Pm.dt)
+                mev[k][1].record(stream)
+                mcyc.append(n)
+            torch.cuda.synchronize()
+            mms = [a.elapsed_time(b) for a, b in mev]
+            table2[str(m)] = {"ms_per_step": float(np.mean(mms)),
+                              "cell_updates_per_s": m * m / (float(np.mean(mms)) / 1e3),
+                              "vcycles_per_step": float(np.mean(mcyc)), "tol": Pm.tol,
+                              "paper_cpu_s_per_step": paper_s[m]}
+            sm.close()
+
     # ---- batched: the 64-drop workload (grids 64^2 .. 512^2, rho ratio 2..100,
     # viscosity ratio 1..50), mixed precision, coupled smoother, all instances
     # advanced together by qnsch_batch_step
@@ -396,6 +424,8 @@ def run_ours(args, rank, world, local_rank):
         line["variants"] = variants
     if stress is not None:
         line["stress"] = stress
+    if table2 is not None:
+        line["table2"] = table2
     if batched is not None:
         line["batched"] = batched
     if serving is not None:
@@ -461,6 +491,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-stress", action="store_true")
+    ap.add_argument("--no-table2", action="store_true")
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=32)

@@ -89,6 +89,9 @@ def initial_fields(P: Problem):
         # light fluid (c = 1) below y = y0 + A cos(2 pi x), Sec. 8.3
         y0, A = a.get("y0", 2.0), a.get("A", 0.1)
         c = _profile(Y - y0 - A * np.cos(2.0 * math.pi * X / P.Lx), P.Cn)
+    elif P.init == "cosines":
+        # c = cos(2 pi x) + cos(2 pi y), the initial state of the convergence test (Sec. 9)
+        c = np.cos(2.0 * math.pi * X) + np.cos(2.0 * math.pi * Y)
     else:
         raise ValueError(P.init)
     z = dict(c=c, mu=np.zeros((P.m2, P.m1)), p=np.zeros((P.m2, P.m1)),
@@ -140,6 +143,18 @@ def droplet_paper_256x512():
     return Problem("droplet_paper_256x512", 256, 512, 1.0, True, 0, 0.1, 1.0, 0.1, 1.0,
                    Re=100.0, We=1.0, Pe=200.0, Cn=0.005, Fr=0.98, dt=1e-3, steps=20, tol=1e-9,
                    init="drop", init_args=dict(x0=0.5, y0=0.5, R=0.25))
+
+
+def convergence_test(m):
+    """The self-convergence test of Sec. 9 on level m (m = 16, 32, ..., 256):
+    [0,1]^2 with walls, c = cos(2 pi x) + cos(2 pi y), everything else zero,
+    dt = 16 h^2 (1/16 at m = 16, 1/4096 at m = 256).  The paper leaves the
+    physical parameters open; c reaches -2 and 2, where rho(c) would be
+    singular for rho1 != rho2, so rho1 = rho2 = 1, mu1 = mu2 = 1, Re = 100,
+    We = 10, Cn = 0.05, Pe = 1/Cn, no gravity."""
+    return Problem("convergence_%d" % m, m, m, 1.0, False, 0, 1.0, 1.0, 1.0, 1.0,
+                   Re=100.0, We=10.0, Pe=20.0, Cn=0.05, Fr=math.inf, dt=16.0 / (m * m),
+                   steps=m * m // 256, tol=1e-11, init="cosines")
 
 
 def batch_drops(n=64, seed=SEED):
