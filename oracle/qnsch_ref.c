@@ -60,6 +60,7 @@ typedef struct {
   double alpha; /* (rho2 - rho1)/(rho1 rho2), Sec. 2.1 */
   double K;     /* M eta / (eps We): coefficient of the bulk terms of (pm-num-chem) */
   double Lam;   /* eps eta M / We : coefficient of the gradient terms */
+  int scheme;   /* 0: primitive method (Sec. 6.1); 1: projection method (Sec. 6.2) */
 } ref_params;
 
 /* rho(c) = rho1 rho2 / ((rho2 - rho1) c + rho1), Sec. 2.1 */
@@ -318,7 +319,9 @@ static double N_mu(const ref_params* P, const ref_level* L, int i, int j) {
     div += 0.5 * (rhalf + rb) * (chb - chp);
   }
   div /= h2;
-  return rho * L->mu[CI(L, i, j)] - P->K * bulk - grad + P->Lam * div;
+  /* (pj-num-chem) of the projection method has rho^n mu on the left */
+  double rmu = P->scheme ? rhon : rho;
+  return rmu * L->mu[CI(L, i, j)] - P->K * bulk - grad + P->Lam * div;
 }
 
 /* (pm-num-mass): N_p = d_x u + d_y v - (alpha/Pe) grad_d.(A m^n grad_D mu)
@@ -331,6 +334,9 @@ static double N_p(const ref_params* P, const ref_level* L, int i, int j) {
   double dp = div_A_grad(L, L->mobn, L->p, i, j);
   return du + dv - P->alpha / P->Pe * dmu - P->alpha * P->alpha / P->Pe * dp;
 }
+
+/* index of the u unknown at x-edge index e (periodic: edge 0 is edge m1) */
+static int uwrap(const ref_level* L, int e) { return (L->px && e == 0) ? L->m1 : e; }
 
 /* centre-to-vertex average Acal phi at vertex (i+1/2, j+1/2), App. A.2 */
 static double Avtx(const ref_level* L, const double* a, int i, int j) {
@@ -376,6 +382,9 @@ static double N_u(const ref_params* P, const ref_level* L, double dt, int i, int
   double t_visc = -((vis[CI(L, i + 1, j)] * dxu_r - vis[CI(L, i, j)] * dxu_l) / h +
                     (Av_t * Dyu_t - Av_b * Dyu_b) / h) / P->Re;
   double t_visc3 = -(vis[CI(L, i + 1, j)] * divu_r - vis[CI(L, i, j)] * divu_l) / h / (3.0 * P->Re);
+  /* (pj-num-mx) of the projection method: the intermediate velocity's row has
+     no pressure and no surface tension (they act in (pj-num-pjx)) */
+  if (P->scheme) t_p = t_st = 0.0;
   return t_time + t_convx + t_convy + t_rho + t_div + t_p + t_st + t_visc + t_visc3;
 }
 
@@ -413,7 +422,80 @@ static double N_v(const ref_params* P, const ref_level* L, double dt, int i, int
                     (vis[CI(L, i, j + 1)] * dyv_t - vis[CI(L, i, j)] * dyv_b) / h) / P->Re;
   double t_visc3 = -(vis[CI(L, i, j + 1)] * divu_t - vis[CI(L, i, j)] * divu_b) / h / (3.0 * P->Re);
   double t_grav = P->Fr_inv * Arn;
+  /* projection method: pressure, surface tension and gravity act in the
+     projection equation (reading R24) */
+  if (P->scheme) t_p = t_st = t_grav = 0.0;
   return t_time + t_convx + t_convy + t_rho + t_div + t_p + t_st + t_visc + t_visc3 + t_grav;
+}
+
+/* ---- projection method (Sec. 6.2) ----------------------------------------
+   The unknowns of a step are c, mu, p and the intermediate velocity (ut, vt),
+   held in the u, v arrays of every level (same staggering, no-slip ghosts).
+   The new velocity follows from the projection equation (pj-num-pjx),
+     A rho(c) (u - ut)/dt = -(1/M) D p + (1/M) rho mu D c  [- (1/Fr) A_y rho(c) in y],
+   with rho = rho(c^{n+1}) and the surface-tension pairing of (e1e1) at level
+   n+1: 1/2 (rho_{i+1} mu_i + rho_i mu_{i+1}) D_x c.  Gravity sits in this
+   equation, tested with u^{n+1} in the energy proof (reading R24). */
+
+/* u^{n+1} at x-edge e (u_{e+1/2,j}); 0 on no-slip walls */
+static double proj_u(const ref_params* P, const ref_level* L, double dt, int e, int j) {
+  if (!L->px && (e <= 0 || e >= L->m1)) return 0.0;
+  e = uwrap(L, e);
+  double h = L->h;
+  double cl = L->c[CI(L, e, j)], cr = L->c[CI(L, e + 1, j)];
+  double rl = rho_of(P, cl), rr = rho_of(P, cr);
+  double Ar = 0.5 * (rl + rr);
+  double dp = (L->p[CI(L, e + 1, j)] - L->p[CI(L, e, j)]) / h;
+  double st = 0.5 * (rr * L->mu[CI(L, e, j)] + rl * L->mu[CI(L, e + 1, j)]) * (cr - cl) / h;
+  return L->u[UI(L, e, j)] + dt / Ar * (st - dp) / P->M;
+}
+
+/* v^{n+1} at y-edge e (v_{i,e+1/2}); 0 on the walls in y */
+static double proj_v(const ref_params* P, const ref_level* L, double dt, int i, int e) {
+  if (e <= 0 || e >= L->m2) return 0.0;
+  double h = L->h;
+  double cb = L->c[CI(L, i, e)], ct = L->c[CI(L, i, e + 1)];
+  double rb = rho_of(P, cb), rt = rho_of(P, ct);
+  double Ar = 0.5 * (rb + rt);
+  double dp = (L->p[CI(L, i, e + 1)] - L->p[CI(L, i, e)]) / h;
+  double st = 0.5 * (rt * L->mu[CI(L, i, e)] + rb * L->mu[CI(L, i, e + 1)]) * (ct - cb) / h;
+  return L->v[VI(L, i, e)] + dt / Ar * (st - dp) / P->M - dt * P->Fr_inv;
+}
+
+/* (pj-num-phase): rho^n (c - c^n)/dt + a_x(rho_ew D_x c u^{n+1}) + a_y(rho_ns D_y c v^{n+1})
+   - (1/Pe) grad_d.(A m^n grad_D mu) - (alpha/Pe) grad_d.(A m^n grad_D p),
+   with rho = rho(c^{n+1}) and c = c^{n+1} in the advection (the (e1e2) form) */
+static double Np_c(const ref_params* P, const ref_level* L, double dt, int i, int j) {
+  double h = L->h;
+  const double* c = L->c;
+  double ck = c[CI(L, i, j)];
+  double t = L->rhon[CI(L, i, j)] * (ck - L->cn[CI(L, i, j)]) / dt;
+  double ax = 0.5 * (rho_of(P, c[CI(L, i + 1, j)]) * (c[CI(L, i + 1, j)] - ck) / h * proj_u(P, L, dt, i, j) +
+                     rho_of(P, c[CI(L, i - 1, j)]) * (ck - c[CI(L, i - 1, j)]) / h * proj_u(P, L, dt, i - 1, j));
+  double ay = 0.5 * (rho_of(P, c[CI(L, i, j + 1)]) * (c[CI(L, i, j + 1)] - ck) / h * proj_v(P, L, dt, i, j) +
+                     rho_of(P, c[CI(L, i, j - 1)]) * (ck - c[CI(L, i, j - 1)]) / h * proj_v(P, L, dt, i, j - 1));
+  double dmu = div_A_grad(L, L->mobn, L->mu, i, j);
+  double dp = div_A_grad(L, L->mobn, L->p, i, j);
+  return t + ax + ay - dmu / P->Pe - P->alpha / P->Pe * dp;
+}
+
+/* (pj-num-mass): d_x u^{n+1} + d_y v^{n+1} - (alpha/Pe) grad_d.(A m^n grad_D mu)
+                  - (alpha^2/Pe) grad_d.(A m^n grad_D p) */
+static double Np_p(const ref_params* P, const ref_level* L, double dt, int i, int j) {
+  double h = L->h;
+  double du = (proj_u(P, L, dt, i, j) - proj_u(P, L, dt, i - 1, j)) / h;
+  double dv = (proj_v(P, L, dt, i, j) - proj_v(P, L, dt, i, j - 1)) / h;
+  double dmu = div_A_grad(L, L->mobn, L->mu, i, j);
+  double dp = div_A_grad(L, L->mobn, L->p, i, j);
+  return du + dv - P->alpha / P->Pe * dmu - P->alpha * P->alpha / P->Pe * dp;
+}
+
+/* the cell families of the scheme in use */
+static double Ncell_c(const ref_params* P, const ref_level* L, double dt, int i, int j) {
+  return P->scheme ? Np_c(P, L, dt, i, j) : N_c(P, L, dt, i, j);
+}
+static double Ncell_p(const ref_params* P, const ref_level* L, double dt, int i, int j) {
+  return P->scheme ? Np_p(P, L, dt, i, j) : N_p(P, L, i, j);
 }
 
 /* residual r = f - N(x) on all unknowns of a level; optional norms
@@ -423,9 +505,9 @@ static void residual(const ref_params* P, ref_level* L, double dt, double* norms
   for (int j = 1; j <= L->m2; ++j)
     for (int i = 1; i <= L->m1; ++i) {
       size_t k = CI(L, i, j);
-      L->rc[k] = L->fc[k] - N_c(P, L, dt, i, j);
+      L->rc[k] = L->fc[k] - Ncell_c(P, L, dt, i, j);
       L->rmu[k] = L->fmu[k] - N_mu(P, L, i, j);
-      L->rp[k] = L->fp[k] - N_p(P, L, i, j);
+      L->rp[k] = L->fp[k] - Ncell_p(P, L, dt, i, j);
       double a[3] = {L->rc[k], L->rmu[k], L->rp[k]};
       for (int q = 0; q < 3; ++q) {
         s[q] += a[q] * a[q];
@@ -505,10 +587,21 @@ static void ch_jac(const ref_params* P, const ref_level* L, double dt, int i, in
   J[1] = sm / (P->Pe * h2);
   J[2] = drho * mu - P->K * dbulk - dgrad + P->Lam * ddiv;
   J[3] = rho;
+  if (P->scheme) {
+    /* projection method: rho^n in the time derivative and in front of mu; the
+       advection a(rho(c) D c u^{n+1}) differentiated in c_ij through D c only,
+       with rho(c) of the neighbours and u^{n+1} held at the iterate (a choice
+       of smoother; the fixed point is the scheme's) */
+    double ue = proj_u(P, L, dt, i, j), uw = proj_u(P, L, dt, i - 1, j);
+    double vn_ = proj_v(P, L, dt, i, j), vs = proj_v(P, L, dt, i, j - 1);
+    double h = L->h;
+    J[0] = rhon / dt + 0.5 * (-rho_of(P, L->c[CI(L, i + 1, j)]) * ue + rho_of(P, L->c[CI(L, i - 1, j)]) * uw) / h +
+           0.5 * (-rho_of(P, L->c[CI(L, i, j + 1)]) * vn_ + rho_of(P, L->c[CI(L, i, j - 1)]) * vs) / h;
+    J[2] = -P->K * dbulk - dgrad + P->Lam * ddiv;
+    J[3] = rhon;
+  }
 }
 
-/* index of the u unknown at x-edge index e (periodic: edge 0 is edge m1) */
-static int uwrap(const ref_level* L, int e) { return (L->px && e == 0) ? L->m1 : e; }
 
 /* write u_{e+1/2,j} and every ghost that mirrors it */
 static void set_u(const ref_level* L, double* u, int e, int j, double x) {
@@ -642,7 +735,7 @@ static void vanka_block(const ref_params* P, const ref_level* L, double dt, int 
   R[1] = act[1] ? N_u(P, L, dt, eE, j) - L->fu[UI(L, eE, j)] : 0.0;
   R[2] = act[2] ? N_v(P, L, dt, i, j - 1) - L->fv[VI(L, i, j - 1)] : 0.0;
   R[3] = act[3] ? N_v(P, L, dt, i, j) - L->fv[VI(L, i, j)] : 0.0;
-  R[4] = N_p(P, L, i, j) - L->fp[CI(L, i, j)];
+  R[4] = Ncell_p(P, L, dt, i, j) - L->fp[CI(L, i, j)];
   for (int q = 0; q < 5; ++q)
     if (!act[q])
       for (int k = 0; k < 5; ++k) {
@@ -701,7 +794,7 @@ static int vanka_colour(const ref_level* L, int kcol, int i, int j) {
 /* CH step 1 of Sec. 7.1 at cell (i,j): one Newton step on the 2x2 local system */
 static void ch_point(const ref_params* P, ref_level* L, double dt, int i, int j) {
   size_t k = CI(L, i, j);
-  double Rc = N_c(P, L, dt, i, j) - L->fc[k];
+  double Rc = Ncell_c(P, L, dt, i, j) - L->fc[k];
   double Rm = N_mu(P, L, i, j) - L->fmu[k];
   double J[4];
   ch_jac(P, L, dt, i, j, J);
@@ -797,6 +890,44 @@ static void coupled_point(const ref_params* P, ref_level* L, double dt, int i, i
   sync_cell(L, L->p, i, j);
 }
 
+/* projection method, Sec. 7.2 step 2: exact solve of the 4x4 block of the
+   intermediate velocities (ut_W, ut_E, vt_S, vt_N) of cell (i,j) in the rows of
+   (pj-num-mx); the pressure is not part of the block */
+static void vanka4_point(const ref_params* P, ref_level* L, double dt, int i, int j, double omega) {
+  double J5[25], R5[5], J[16], R[4];
+  int act[5];
+  vanka_block(P, L, dt, i, j, J5, R5, act);
+  for (int a = 0; a < 4; ++a) {
+    R[a] = R5[a];
+    for (int b = 0; b < 4; ++b) J[a * 4 + b] = J5[a * 5 + b];
+  }
+  solve_dense(4, J, R);
+  int eW = uwrap(L, i - 1);
+  if (act[0]) set_u(L, L->u, eW, j, L->u[UI(L, eW, j)] - omega * R[0]);
+  if (act[1]) set_u(L, L->u, i, j, L->u[UI(L, i, j)] - omega * R[1]);
+  if (act[2]) set_v(L, L->v, i, j - 1, L->v[VI(L, i, j - 1)] - omega * R[2]);
+  if (act[3]) set_v(L, L->v, i, j, L->v[VI(L, i, j)] - omega * R[3]);
+}
+
+/* projection method, Sec. 7.2 step 3: Gauss-Seidel on (pj-num-mass) for p_ij.
+   The row is affine in p_ij: u^{n+1} on an open face carries -dt/(M h A rho) p
+   of each adjacent cell, and the diffusion term (alpha^2/Pe) A m / h^2 */
+static void pgs_point(const ref_params* P, ref_level* L, double dt, int i, int j) {
+  static const int di[4] = {1, -1, 0, 0}, dj[4] = {0, 0, 1, -1};
+  double h2 = L->h * L->h;
+  size_t k = CI(L, i, j);
+  double R = Np_p(P, L, dt, i, j) - L->fp[k];
+  double rk = rho_of(P, L->c[k]), d = 0.0;
+  for (int f = 0; f < 4; ++f) {
+    if (wall_face(L, i, j, f)) continue;
+    size_t q = CI(L, i + di[f], j + dj[f]);
+    double Ar = 0.5 * (rk + rho_of(P, L->c[q]));
+    d += dt / (P->M * h2 * Ar) + P->alpha * P->alpha / P->Pe * 0.5 * (L->mobn[k] + L->mobn[q]) / h2;
+  }
+  L->p[k] -= R / d;
+  sync_cell(L, L->p, i, j);
+}
+
 static void smooth_ch(const ref_params* P, ref_level* L, double dt, int colour) {
   for (int j = 1; j <= L->m2; ++j)
     for (int i = 1; i <= L->m1; ++i)
@@ -820,6 +951,21 @@ static void smooth_coupled(const ref_params* P, ref_level* L, double dt, int kco
 /* one smoothing step.  Decoupled (Sec. 7.1): CH red, CH black, then the Vanka
    colours 0..K-1.  Coupled option: the 7x7 block over the K Vanka colours. */
 static void smooth(const ref_solver* s, ref_level* L) {
+  if (s->P.scheme) {
+    /* projection method (Sec. 7.2): CH red-black, the intermediate-velocity
+       blocks over the Vanka colours, pressure Gauss-Seidel red-black */
+    smooth_ch(&s->P, L, s->dt, 0);
+    smooth_ch(&s->P, L, s->dt, 1);
+    for (int col = 0; col < L->kcol; ++col)
+      for (int j = 1; j <= L->m2; ++j)
+        for (int i = 1; i <= L->m1; ++i)
+          if (vanka_colour(L, L->kcol, i, j) == col) vanka4_point(&s->P, L, s->dt, i, j, s->omega);
+    for (int col = 0; col < 2; ++col)
+      for (int j = 1; j <= L->m2; ++j)
+        for (int i = 1; i <= L->m1; ++i)
+          if (((i + j) & 1) == col) pgs_point(&s->P, L, s->dt, i, j);
+    return;
+  }
   if (s->coupled) {
     for (int col = 0; col < L->kcol; ++col) smooth_coupled(&s->P, L, s->dt, L->kcol, col, s->omega);
     return;
@@ -974,9 +1120,9 @@ static void vcycle(ref_solver* s, int l) {
   for (int J = 1; J <= C->m2; ++J)
     for (int I = 1; I <= C->m1; ++I) {
       size_t k = CI(C, I, J);
-      C->fc[k] += N_c(&s->P, C, s->dt, I, J);
+      C->fc[k] += Ncell_c(&s->P, C, s->dt, I, J);
       C->fmu[k] += N_mu(&s->P, C, I, J);
-      C->fp[k] += N_p(&s->P, C, I, J);
+      C->fp[k] += Ncell_p(&s->P, C, s->dt, I, J);
     }
   for (int J = 1; J <= C->m2; ++J)
     for (int I = ulo(C); I <= uhi(C); ++I) C->fu[UI(C, I, J)] += N_u(&s->P, C, s->dt, I, J);
@@ -1086,6 +1232,34 @@ static double dissipation_of(const ref_params* P, const ref_level* L, double dt)
     }
   return h2 * (0.5 * kin + dt / P->Re * (vc + vv) + dt / (3.0 * P->Re) * div +
                dt / (P->M * P->Pe) * ch);
+}
+
+/* u^{n+1}, v^{n+1} of the projection method on level L (interior edges from
+   (pj-num-pjx), then the ghost rules of App. A.6) */
+static void projected_velocity(const ref_params* P, const ref_level* L, double dt, double* u,
+                               double* v) {
+  for (int j = 1; j <= L->m2; ++j)
+    for (int e = 0; e <= L->m1; ++e) u[UI(L, e, j)] = proj_u(P, L, dt, e, j);
+  for (int e = 0; e <= L->m2; ++e)
+    for (int i = 1; i <= L->m1; ++i) v[VI(L, i, e)] = proj_v(P, L, dt, i, e);
+  bc_u(L, u);
+  bc_v(L, v);
+}
+
+/* the extra dissipation of the projection method (Thm. 6.4):
+   1/2 ||sqrt(rho(c)) (u^{n+1} - ut)||^2 over both velocity components, in the
+   cell-averaged form of the kinetic energy */
+static double projection_dissipation(const ref_params* P, const ref_level* L, const double* u,
+                                     const double* v) {
+  double s = 0.0;
+  for (int j = 1; j <= L->m2; ++j)
+    for (int i = 1; i <= L->m1; ++i) {
+      double r = rho_of(P, L->c[CI(L, i, j)]);
+      double a = u[UI(L, i, j)] - L->u[UI(L, i, j)], b = u[UI(L, i - 1, j)] - L->u[UI(L, i - 1, j)];
+      double c = v[VI(L, i, j)] - L->v[VI(L, i, j)], d = v[VI(L, i, j - 1)] - L->v[VI(L, i, j - 1)];
+      s += r * (0.5 * (a * a + b * b) + 0.5 * (c * c + d * d));
+    }
+  return 0.5 * L->h * L->h * s;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -1257,13 +1431,20 @@ int qnsch_ref_set_option(ref_solver* s, const char* key, double value) {
   if (!strcmp(key, "nu1")) s->nu1 = (int)value;
   else if (!strcmp(key, "nu2")) s->nu2 = (int)value;
   else if (!strcmp(key, "nu_coarse")) s->nuc = (int)value;
+  else if (!strcmp(key, "scheme")) {
+    if (s->pending || (value != 0.0 && value != 1.0) || (value == 1.0 && s->coupled)) return REF_EINVAL;
+    s->P.scheme = (int)value;
+  }
   else if (!strcmp(key, "maxcyc")) s->maxcyc = (int)value;
   else if (!strcmp(key, "tol")) s->tol = value;
   else if (!strcmp(key, "omega_vanka")) s->omega = value;
   else if (!strcmp(key, "M")) { s->P.M = value; derive_params(&s->P); }
   else if (!strcmp(key, "eta_st")) { s->P.eta = value; derive_params(&s->P); }
   else if (!strcmp(key, "eps_mob")) s->P.eps_m = value;
-  else if (!strcmp(key, "coupled")) s->coupled = value != 0.0;
+  else if (!strcmp(key, "coupled")) {
+    if (value != 0.0 && s->P.scheme) return REF_EINVAL; /* the 7x7 block is a primitive-method smoother */
+    s->coupled = value != 0.0;
+  }
   else return REF_EINVAL;
   return REF_OK;
 }
@@ -1273,6 +1454,7 @@ int qnsch_ref_get_option(const ref_solver* s, const char* key, double* value) {
   if (!strcmp(key, "nu1")) *value = s->nu1;
   else if (!strcmp(key, "nu2")) *value = s->nu2;
   else if (!strcmp(key, "nu_coarse")) *value = s->nuc;
+  else if (!strcmp(key, "scheme")) *value = s->P.scheme;
   else if (!strcmp(key, "maxcyc")) *value = s->maxcyc;
   else if (!strcmp(key, "tol")) *value = s->tol;
   else if (!strcmp(key, "omega_vanka")) *value = s->omega;
@@ -1363,8 +1545,13 @@ int qnsch_ref_commit_step(ref_solver* s) {
   memcpy(s->c, F->c, ncell(F) * sizeof(double));
   memcpy(s->mu, F->mu, ncell(F) * sizeof(double));
   memcpy(s->p, F->p, ncell(F) * sizeof(double));
-  memcpy(s->u, F->u, nu_(F) * sizeof(double));
-  memcpy(s->v, F->v, nv_(F) * sizeof(double));
+  if (s->P.scheme) {
+    /* projection method: the committed velocity is u^{n+1} of (pj-num-pjx) */
+    projected_velocity(&s->P, F, s->dt, s->u, s->v);
+  } else {
+    memcpy(s->u, F->u, nu_(F) * sizeof(double));
+    memcpy(s->v, F->v, nv_(F) * sizeof(double));
+  }
   s->pending = 0;
   return REF_OK;
 }
@@ -1572,13 +1759,58 @@ int qnsch_ref_iterate_energy(const ref_solver* s, double* E) {
   if (!s || !E) return REF_EINVAL;
   if (!s->pending) return REF_ESTATE;
   const ref_level* F = &s->lev[0];
-  *E = energy_of(&s->P, F, F->c, F->u, F->v);
+  if (s->P.scheme) {
+    double *u = zalloc(nu_(F)), *v = zalloc(nv_(F));
+    if (!u || !v) {
+      free(u);
+      free(v);
+      return REF_ENOMEM;
+    }
+    projected_velocity(&s->P, F, s->dt, u, v);
+    *E = energy_of(&s->P, F, F->c, u, v);
+    free(u);
+    free(v);
+  } else {
+    *E = energy_of(&s->P, F, F->c, F->u, F->v);
+  }
   return REF_OK;
 }
 
 int qnsch_ref_iterate_dissipation(const ref_solver* s, double* D) {
   if (!s || !D) return REF_EINVAL;
   if (!s->pending) return REF_ESTATE;
-  *D = dissipation_of(&s->P, &s->lev[0], s->dt);
+  const ref_level* F = &s->lev[0];
+  *D = dissipation_of(&s->P, F, s->dt);
+  if (s->P.scheme) {
+    double *u = zalloc(nu_(F)), *v = zalloc(nv_(F));
+    if (!u || !v) {
+      free(u);
+      free(v);
+      return REF_ENOMEM;
+    }
+    projected_velocity(&s->P, F, s->dt, u, v);
+    *D += projection_dissipation(&s->P, F, u, v);
+    free(u);
+    free(v);
+  }
+  return REF_OK;
+}
+
+/* projection method: u^{n+1}, v^{n+1} of the current iterate in the host
+   layout of qnsch_ref_get_fields */
+int qnsch_ref_projected_velocity(const ref_solver* s, double* hu, double* hv) {
+  if (!s || !hu || !hv) return REF_EINVAL;
+  if (!s->pending || !s->P.scheme) return REF_ESTATE;
+  const ref_level* F = &s->lev[0];
+  double *u = zalloc(nu_(F)), *v = zalloc(nv_(F));
+  if (!u || !v) {
+    free(u);
+    free(v);
+    return REF_ENOMEM;
+  }
+  projected_velocity(&s->P, F, s->dt, u, v);
+  pack_out(F, NULL, NULL, NULL, u, v, NULL, NULL, NULL, hu, hv);
+  free(u);
+  free(v);
   return REF_OK;
 }

@@ -83,6 +83,9 @@ int qnsch_ref_params(const ref_solver* s, double* out8);
    centroid y, max|div|, l2 div, max expansion, max compression, a1, y_top,
    y_bottom}; divergence field out[(j-1)*m1 + (i-1)], m1*m2 values. */
 int qnsch_ref_diagnostics(const ref_solver* s, double* out9);
+/* projection method (option "scheme" = 1): u^{n+1}, v^{n+1} of the pending
+   iterate, host layout of qnsch_ref_get_fields */
+int qnsch_ref_projected_velocity(const ref_solver* s, double* hu, double* hv);
 int qnsch_ref_divergence(const ref_solver* s, double* out);
 
 #ifdef __cplusplus

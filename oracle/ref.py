@@ -69,6 +69,7 @@ def lib():
         L.qnsch_ref_iterate_dissipation.argtypes = [vp, p]
         L.qnsch_ref_params.argtypes = [vp, p]
         L.qnsch_ref_diagnostics.argtypes = [vp, p]
+        L.qnsch_ref_projected_velocity.argtypes = [vp, p, p]
         L.qnsch_ref_divergence.argtypes = [vp, p]
         _lib = L
     return _lib
@@ -247,6 +248,13 @@ class RefSolver:
         out = np.zeros(9)
         _check(lib().qnsch_ref_diagnostics(self._h, _ptr(out)), "diagnostics")
         return dict(zip(self.DIAG_KEYS, out.tolist()))
+
+    def projected_velocity(self):
+        """Projection method: u^{n+1}, v^{n+1} of the pending iterate."""
+        a = self.zeros()
+        _check(lib().qnsch_ref_projected_velocity(self._h, _ptr(a["u"]), _ptr(a["v"])),
+               "projected_velocity")
+        return a["u"], a["v"]
 
     def divergence(self):
         """d_x u + d_y v of the committed state, shape (m2, m1)."""
