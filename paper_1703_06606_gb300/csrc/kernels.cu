@@ -97,6 +97,12 @@ __device__ __forceinline__ void residual_cell(const Prm<T>& P, const Lv<T>& L, i
     np = op_p(P, L, k);
     nu = hu ? op_u(P, L, k, T(0.5) * (rk + rq[0])) : T(0);
     nv = hv ? op_v(P, L, k, T(0.5) * (rk + rq[2])) : T(0);
+  } else if constexpr (std::is_same<Form, ProjForm>::value) {
+    nc = opp_c(P, L, i, j);
+    nm = opp_mu(P, L, k);
+    np = opp_p(P, L, i, j);
+    nu = hu ? opp_u(P, L, k) : T(0);
+    nv = hv ? opp_v(P, L, k) : T(0);
   } else {
     nc = Form::Nc(P, L, k);
     nm = Form::Nmu(P, L, k);
@@ -158,6 +164,9 @@ __device__ __forceinline__ void ch_system(const Prm<T>& P, const Lv<T>& L, int i
   if constexpr (std::is_same<Form, FullForm>::value) {
     Rc = op_c(P, L, k, rho) - L.fc[k];
     Rm = op_mu(P, L, k, rho, rq4) - L.fmu[k];
+  } else if constexpr (std::is_same<Form, ProjForm>::value) {
+    Rc = opp_c(P, L, i, j) - L.fc[k];
+    Rm = op_mu_r(P, L, k, rho, rq4, L.rhon[k]) - L.fmu[k];
   } else {
     Rc = Form::Nc(P, L, k) - L.fc[k];
     Rm = Form::Nmu(P, L, k) - L.fmu[k];
@@ -193,6 +202,18 @@ __device__ __forceinline__ void ch_system(const Prm<T>& P, const Lv<T>& L, int i
   T dgrad = T(0.25) * P.Lam * (dG * L.ih2 * r + Gs * dr);
   T J21 = drho * mk - P.K * dbulk - dgrad + P.Lam * T(0.25) * L.ih2 * dd;
   T J22 = rho;
+  if constexpr (std::is_same<Form, ProjForm>::value) {
+    // projection method: rho^n in the time derivative and in front of mu; the
+    // advection a(rho(c) D c u^{n+1}) differentiated in c_ij through D c only,
+    // with rho(c) of the neighbours and u^{n+1} at the iterate (the smoother's
+    // choice; the fixed point is the scheme's)
+    T ue = proj_u(P, L, i, j), uw = proj_u(P, L, i - 1, j);
+    T vn = proj_v(P, L, i, j), vs = proj_v(P, L, i, j - 1);
+    J11 = rnk * P.idt + T(0.5) * (-rq4[0] * ue + rq4[1] * uw) * L.ih +
+          T(0.5) * (-rq4[2] * vn + rq4[3] * vs) * L.ih;
+    J21 = -P.K * dbulk - dgrad + P.Lam * T(0.25) * L.ih2 * dd;
+    J22 = rnk;
+  }
   J[0][0] = J11;
   J[0][1] = J12;
   J[1][0] = J21;
@@ -377,7 +398,8 @@ __device__ __forceinline__ void vanka_system(const Prm<T>& P, const Lv<T>& L, in
     b[2] = act[2] ? Form::Nv(P, L, k - W) - L.fv[k - W] : T(0);
     b[3] = act[3] ? Form::Nv(P, L, k) - L.fv[k] : T(0);
   }
-  b[4] = Form::Np(P, L, k) - L.fp[k];
+  if constexpr (std::is_same<Form, ProjForm>::value) b[4] = T(0);  // the 4x4 block has no p row
+  else b[4] = Form::Np(P, L, k) - L.fp[k];
 #pragma unroll
   for (int q = 0; q < 4; ++q)
     if (!act[q]) {
@@ -605,6 +627,146 @@ __global__ void __launch_bounds__(SNT) k_coupled(Prm<T> P, Lv<T> L, int colour, 
   int i, j;
   if (t >= cs.n || !vanka_slot_cell(L, colour, cs, t, i, j)) return;
   coupled_cell<T, Form>(P, L, i, j, omega);
+}
+
+// --------------------------------------------------------------------------
+// projection method (Sec. 7.2): the intermediate-velocity block, pressure
+// Gauss-Seidel, the projected velocity and the projection dissipation
+// --------------------------------------------------------------------------
+// Gaussian elimination with partial pivoting (compare-and-swap) on N x N
+template <typename T, int N>
+__device__ __forceinline__ void solve_n(T (&A)[N][N], T (&b)[N]) {
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+#pragma unroll
+    for (int r = k + 1; r < N; ++r) {
+      if (fabs(A[r][k]) > fabs(A[k][k])) {
+#pragma unroll
+        for (int c = k; c < N; ++c) {
+          T t = A[k][c];
+          A[k][c] = A[r][c];
+          A[r][c] = t;
+        }
+        T t = b[k];
+        b[k] = b[r];
+        b[r] = t;
+      }
+    }
+    T inv = T(1) / A[k][k];
+#pragma unroll
+    for (int r = k + 1; r < N; ++r) {
+      T l = A[r][k] * inv;
+#pragma unroll
+      for (int c = k + 1; c < N; ++c) A[r][c] -= l * A[k][c];
+      b[r] -= l * b[k];
+    }
+    A[k][k] = inv;
+  }
+#pragma unroll
+  for (int k = N - 1; k >= 0; --k) {
+    T t = b[k];
+#pragma unroll
+    for (int c = k + 1; c < N; ++c) t -= A[k][c] * b[c];
+    b[k] = t * A[k][k];
+  }
+}
+
+// step 2: exact solve of the 4x4 block of the intermediate velocities
+// (ut_W, ut_E, vt_S, vt_N) of cell (i,j) in the rows of (pj-num-mx)
+template <typename T, class Form>
+__device__ __forceinline__ void vanka4_cell(const Prm<T>& P, const Lv<T>& L, int i, int j, T omega) {
+  T A5[5][5], b5[5];
+  bool act[5];
+  vanka_system<T, Form>(P, L, i, j, A5, b5, act);
+  T A[4][4], b[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    b[r] = b5[r];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) A[r][c] = A5[r][c];
+  }
+  solve_n<T, 4>(A, b);
+  const int W = L.pitch;
+  int k = L.at(i, j);
+  int eW = (L.px && i == 1) ? L.m1 : i - 1;
+  int kW = L.at(eW, j);
+  if (act[0]) store_u(L, eW, j, L.u[kW] - omega * b[0]);
+  if (act[1]) store_u(L, i, j, L.u[k] - omega * b[1]);
+  if (act[2]) store_v(L, i, j - 1, L.v[k - W] - omega * b[2]);
+  if (act[3]) store_v(L, i, j, L.v[k] - omega * b[3]);
+}
+
+template <typename T, class Form>
+__global__ void __launch_bounds__(SNT) k_vanka4(Prm<T> P, Lv<T> L, int colour, T omega) {
+  ColourSlots cs = vanka_slots(L, colour);
+  int t = blockIdx.x * SNT + threadIdx.x;
+  int i, j;
+  if (t >= cs.n || !vanka_slot_cell(L, colour, cs, t, i, j)) return;
+  vanka4_cell<T, Form>(P, L, i, j, omega);
+}
+
+// step 3: Gauss-Seidel on (pj-num-mass) for p_ij.  The row is affine in p_ij:
+// u^{n+1} on an open face carries -dt/(M h A rho(c)) times the pressure of each
+// adjacent cell, plus the diffusion term (alpha^2/Pe) A m / h^2.
+template <typename T>
+__device__ __forceinline__ void pgs_cell(const Prm<T>& P, const Lv<T>& L, int i, int j) {
+  const int W = L.pitch;
+  int k = L.at(i, j);
+  T R = opp_p(P, L, i, j) - L.fp[k];
+  T rk = rho_of(P, L.c[k]);
+  const bool wall[4] = {!L.px && i == L.m1, !L.px && i == 1, j == L.m2, j == 1};
+  const int off[4] = {1, -1, W, -W};
+  T d = T(0);
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    if (wall[f]) continue;
+    int q = k + off[f];
+    T Ar = T(0.5) * (rk + rho_of(P, L.c[q]));
+    d += P.iM / (Ar * P.idt) * L.ih2 + P.alpha * P.alpha * P.iPe * T(0.5) * (L.mobn[k] + L.mobn[q]) * L.ih2;
+  }
+  store_cell(L, L.p, i, j, L.p[k] - R / d);
+}
+
+// cells of colour (i + j) % 2 == colour, packed as in k_ch
+template <typename T>
+__global__ void __launch_bounds__(64) k_pgs(Prm<T> P, Lv<T> L, int colour) {
+  int mpr = (L.m1 + 1) / 2;
+  int t = blockIdx.x * 64 + threadIdx.x;
+  if (t >= mpr * L.m2) return;
+  int j = t / mpr + 1;
+  int i = (((colour - j) & 1) ? 1 : 2) + 2 * (t % mpr);
+  if (i > L.m1) return;
+  pgs_cell<T>(P, L, i, j);
+}
+
+// u^{n+1} on the x-edges i = 0..m1 (rows 1..m2) and v^{n+1} on the y-edges
+// j = 0..m2 (columns 1..m1), into uo, vo (level layout); ghosts are filled after
+template <typename T>
+__global__ void k_proj_velocity(Prm<T> P, Lv<T> L, T* uo, T* vo) {
+  int i = blockIdx.x * BX + threadIdx.x;
+  int j = blockIdx.y * BY + threadIdx.y;
+  if (i > L.m1 || j > L.m2) return;
+  int k = L.at(i, j);
+  if (j >= 1) uo[k] = proj_u(P, L, i, j);
+  if (i >= 1) vo[k] = proj_v(P, L, i, j);
+}
+
+// the projection method's extra dissipation, 1/2 ||sqrt(rho(c)) (u^{n+1} - ut)||^2
+// in the cell-averaged form of the kinetic energy; per cell before the h^2/2
+template <typename T>
+__global__ void k_proj_diss(Prm<T> P, Lv<T> L, const T* uo, const T* vo, double* part) {
+  int i = blockIdx.x * BX + threadIdx.x + 1;
+  int j = blockIdx.y * BY + threadIdx.y + 1;
+  double val[1] = {0.0};
+  if (i <= L.m1 && j <= L.m2) {
+    const int W = L.pitch;
+    int k = L.at(i, j);
+    double r = 1.0 / ((double)P.ia * (double)L.c[k] + (double)P.ib);
+    double a = (double)uo[k] - (double)L.u[k], b = (double)uo[k - 1] - (double)L.u[k - 1];
+    double c = (double)vo[k] - (double)L.v[k], d = (double)vo[k - W] - (double)L.v[k - W];
+    val[0] = r * (0.5 * (a * a + b * b) + 0.5 * (c * c + d * d));
+  }
+  block_sum_store<1>(val, part, 0);
 }
 
 // --------------------------------------------------------------------------
@@ -1551,6 +1713,33 @@ void launch_coarse_vcycle(const Prm<T>& P, const Lv<T>* levels, int n, int nu1, 
 }
 
 template <typename T, class Form>
+void launch_vanka4(const Prm<T>& P, const Lv<T>& L, int colour, T omega, cudaStream_t s) {
+  int n = vanka_slots(L, colour).n;
+  if (n <= 0) return;
+  k_vanka4<T, Form><<<(n + SNT - 1) / SNT, SNT, 0, s>>>(P, L, colour, omega);
+  ++g_launches;
+}
+template <typename T>
+void launch_pgs(const Prm<T>& P, const Lv<T>& L, int colour, cudaStream_t s) {
+  int n = (L.m1 + 1) / 2 * L.m2;
+  if (n <= 0) return;
+  k_pgs<T><<<(n + 63) / 64, 64, 0, s>>>(P, L, colour);
+  ++g_launches;
+}
+template <typename T>
+void launch_proj_velocity(const Prm<T>& P, const Lv<T>& L, T* uo, T* vo, cudaStream_t s) {
+  k_proj_velocity<T><<<grid2(L.m1 + 1, L.m2 + 1), dim3(BX, BY), 0, s>>>(P, L, uo, vo);
+  ++g_launches;
+}
+template <typename T>
+void launch_proj_diss(const Prm<T>& P, const Lv<T>& L, const T* uo, const T* vo, double* part,
+                      double* out1, cudaStream_t s) {
+  k_proj_diss<T><<<grid2(L.m1, L.m2), dim3(BX, BY), 0, s>>>(P, L, uo, vo, part);
+  ++g_launches;
+  k_finalize<<<1, 256, 0, s>>>(part, nparts_cells(L), 1, 0, 0.5 * (double)L.h * (double)L.h, out1);
+  ++g_launches;
+}
+template <typename T, class Form>
 void launch_coupled(const Prm<T>& P, const Lv<T>& L, int colour, T omega, cudaStream_t s) {
   int n = vanka_slots(L, colour).n;
   if (n <= 0) return;
@@ -1738,5 +1927,17 @@ QN_INSTANTIATE(float)
 QN_INSTANTIATE_FORM(double, FullForm)
 QN_INSTANTIATE_FORM(double, ErrForm)
 QN_INSTANTIATE_FORM(float, ErrForm)
+// projection method (FP64, per-level launches)
+template void launch_residual<double, ProjForm>(const Prm<double>&, const Lv<double>&, double*,
+                                                cudaStream_t);
+template void launch_add_op<double, ProjForm>(const Prm<double>&, const Lv<double>&, cudaStream_t);
+template void launch_ch<double, ProjForm>(const Prm<double>&, const Lv<double>&, int, cudaStream_t);
+template void launch_vanka4<double, ProjForm>(const Prm<double>&, const Lv<double>&, int, double,
+                                              cudaStream_t);
+template void launch_pgs<double>(const Prm<double>&, const Lv<double>&, int, cudaStream_t);
+template void launch_proj_velocity<double>(const Prm<double>&, const Lv<double>&, double*, double*,
+                                           cudaStream_t);
+template void launch_proj_diss<double>(const Prm<double>&, const Lv<double>&, const double*,
+                                       const double*, double*, double*, cudaStream_t);
 
 }  // namespace qn

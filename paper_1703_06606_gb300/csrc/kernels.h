@@ -23,6 +23,18 @@ void launch_coarse_vcycle(const Prm<T>& P, const Lv<T>* levels, int n, int nu1, 
 // one colour of the coupled 7x7 smoother (option "coupled")
 template <typename T, class Form>
 void launch_coupled(const Prm<T>& P, const Lv<T>& L, int colour, T omega, cudaStream_t s);
+// projection method (Sec. 7.2): 4x4 intermediate-velocity blocks of one Vanka
+// colour; pressure Gauss-Seidel on one red-black colour; the projected velocity
+// u^{n+1}, v^{n+1} into uo, vo (level layout, interior and boundary edges); the
+// extra dissipation 1/2||sqrt(rho)(u^{n+1} - ut)||^2 into out1
+template <typename T, class Form>
+void launch_vanka4(const Prm<T>& P, const Lv<T>& L, int colour, T omega, cudaStream_t s);
+template <typename T> void launch_pgs(const Prm<T>& P, const Lv<T>& L, int colour, cudaStream_t s);
+template <typename T>
+void launch_proj_velocity(const Prm<T>& P, const Lv<T>& L, T* uo, T* vo, cudaStream_t s);
+template <typename T>
+void launch_proj_diss(const Prm<T>& P, const Lv<T>& L, const T* uo, const T* vo, double* part,
+                      double* out1, cudaStream_t s);
 // defect correction: E (error-equation level) from the FP64 level D
 template <typename T> void launch_cast_frozen(const Lv<double>& D, const Lv<T>& E, cudaStream_t s);
 template <typename T> void launch_start_correction(const Lv<double>& D, const Lv<T>& E, cudaStream_t s);

@@ -122,9 +122,11 @@ __device__ __forceinline__ T op_c(const Prm<T>& P, const Lv<T>& L, int k) {
 }
 
 // (pm-num-chem) with the time-averaged gradient term (pointwise G)
-// rq[f]: rho(c) of the neighbours k + 1, k - 1, k + W, k - W
+// rq[f]: rho(c) of the neighbours k + 1, k - 1, k + W, k - W; rmu multiplies mu
+// (rho(c) in (pm-num-chem), rho^n in the projection method's (pj-num-chem))
 template <typename T>
-__device__ __forceinline__ T op_mu(const Prm<T>& P, const Lv<T>& L, int k, T rho, const T (&rq)[4]) {
+__device__ __forceinline__ T op_mu_r(const Prm<T>& P, const Lv<T>& L, int k, T rho, const T (&rq)[4],
+                                     T rmu) {
   const int W = L.pitch;
   const T* c = L.c;
   const T* cn = L.cn;
@@ -146,7 +148,11 @@ __device__ __forceinline__ T op_mu(const Prm<T>& P, const Lv<T>& L, int k, T rho
     div += (rh + rf) * ((c[q] + cn[q]) - chk);
   }
   div *= T(0.25) * L.ih2;  // 1/2 (face average) * 1/2 (c^{n+1/2}) / h^2
-  return rho * L.mu[k] - P.K * bulk - grad + P.Lam * div;
+  return rmu * L.mu[k] - P.K * bulk - grad + P.Lam * div;
+}
+template <typename T>
+__device__ __forceinline__ T op_mu(const Prm<T>& P, const Lv<T>& L, int k, T rho, const T (&rq)[4]) {
+  return op_mu_r(P, L, k, rho, rq, rho);
 }
 template <typename T>
 __device__ __forceinline__ T op_mu(const Prm<T>& P, const Lv<T>& L, int k) {
@@ -167,8 +173,10 @@ __device__ __forceinline__ T op_p(const Prm<T>& P, const Lv<T>& L, int k) {
 
 // x row of (pm-num-mx) at edge u_{i+1/2,j} (array index k = at(i,j)); cells k (left), k+1 (right),
 // vertices k (top, (i+1/2, j+1/2)) and k-W (bottom); (e1e1-1), (e1e1-2) and (e1e1)
-// (Ar = (rho(c_k) + rho(c_{k+1})) / 2, the density average on the edge)
-template <typename T>
+// (Ar = (rho(c_k) + rho(c_{k+1})) / 2, the density average on the edge).  PST =
+// false drops the pressure and surface-tension terms: the intermediate-velocity
+// row of the projection method (pj-num-mx).
+template <typename T, bool PST = true>
 __device__ __forceinline__ T op_u(const Prm<T>& P, const Lv<T>& L, int k, T Ar) {
   const int W = L.pitch;
   const T *u = L.u, *vis = L.visn, *rn = L.rhon;
@@ -180,12 +188,16 @@ __device__ __forceinline__ T op_u(const Prm<T>& P, const Lv<T>& L, int k, T Ar) 
   T Arn = L.Aru[k];
   T conv = T(0.5) * (L.Sx[k + 1] * dxr + L.Sx[k] * dxl + L.Qx[k] * Dt + L.Qx[k - W] * Db);
   T time = Arn * (ue - L.un[k]) * P.idt + T(0.5) * (Ar - Arn) * P.idt * ue + L.Dvu[k] * ue;
-  T press = (L.p[k + 1] - L.p[k]) * L.ih * P.iM;
-  T st = -(rn[k + 1] * L.mu[k] + rn[k] * L.mu[k + 1]) * L.Tx[k] * P.iM;
+  T r = time + conv;
+  if constexpr (PST) {
+    T press = (L.p[k + 1] - L.p[k]) * L.ih * P.iM;
+    T st = -(rn[k + 1] * L.mu[k] + rn[k] * L.mu[k + 1]) * L.Tx[k] * P.iM;
+    r = r + press + st;
+  }
   T vl = vis[k], vr = vis[k + 1];
   T visc = -P.iRe * L.ih * ((vr * dxr - vl * dxl) + (L.Av[k] * Dt - L.Av[k - W] * Db) +
                             (vr * dvr - vl * dvl) * T(1.0 / 3.0));
-  return time + conv + press + st + visc;
+  return r + visc;
 }
 template <typename T>
 __device__ __forceinline__ T op_u(const Prm<T>& P, const Lv<T>& L, int k) {
@@ -194,7 +206,9 @@ __device__ __forceinline__ T op_u(const Prm<T>& P, const Lv<T>& L, int k) {
 
 // y row of (pm-num-mx) at edge v_{i,j+1/2} (index k = at(i,j)); cells k (bottom), k+W (top),
 // vertices k (east, (i+1/2, j+1/2)) and k-1 (west); plus gravity (1/Fr) A_y rho^n
-template <typename T>
+// PST = false: the projection method's intermediate-velocity row, without
+// pressure, surface tension and gravity (those act in (pj-num-pjx))
+template <typename T, bool PST = true>
 __device__ __forceinline__ T op_v(const Prm<T>& P, const Lv<T>& L, int k, T Ar) {
   const int W = L.pitch;
   const T *v = L.v, *vis = L.visn, *rn = L.rhon;
@@ -206,16 +220,96 @@ __device__ __forceinline__ T op_v(const Prm<T>& P, const Lv<T>& L, int k, T Ar) 
   T Arn = L.Arv[k];
   T conv = T(0.5) * (L.Qy[k] * De + L.Qy[k - 1] * Dw + L.Sy[k + W] * dyt + L.Sy[k] * dyb);
   T time = Arn * (ve - L.vn[k]) * P.idt + T(0.5) * (Ar - Arn) * P.idt * ve + L.Dvv[k] * ve;
-  T press = (L.p[k + W] - L.p[k]) * L.ih * P.iM;
-  T st = -(rn[k + W] * L.mu[k] + rn[k] * L.mu[k + W]) * L.Ty[k] * P.iM;
+  T r = time + conv;
+  if constexpr (PST) {
+    T press = (L.p[k + W] - L.p[k]) * L.ih * P.iM;
+    T st = -(rn[k + W] * L.mu[k] + rn[k] * L.mu[k + W]) * L.Ty[k] * P.iM;
+    r = r + press + st;
+  }
   T vb = vis[k], vt = vis[k + W];
   T visc = -P.iRe * L.ih * ((L.Av[k] * De - L.Av[k - 1] * Dw) + (vt * dyt - vb * dyb) +
                             (vt * dvt - vb * dvb) * T(1.0 / 3.0));
-  return time + conv + press + st + visc + P.Fr_inv * Arn;
+  if constexpr (PST) return r + visc + P.Fr_inv * Arn;
+  return r + visc;
 }
 template <typename T>
 __device__ __forceinline__ T op_v(const Prm<T>& P, const Lv<T>& L, int k) {
   return op_v(P, L, k, T(0.5) * (rho_of(P, L.c[k]) + rho_of(P, L.c[k + L.pitch])));
+}
+
+// ---------------------------------------------------------------------------
+// projection method (Sec. 6.2): the iterate's u, v arrays hold the
+// intermediate velocity; the new velocity follows from the projection
+// equation (pj-num-pjx), A rho(c) (u - ut)/dt = -(1/M) D p + (1/M) ST(c, mu)
+// [- (1/Fr) A_y rho(c) in y], ST the surface-tension pairing of (e1e1) at
+// level n+1.  Gravity acts here, tested with u^{n+1} in the energy proof.
+// ---------------------------------------------------------------------------
+// u^{n+1} at edge (i+1/2, j), i = 0..m1; zero on no-slip walls
+template <typename T>
+__device__ __forceinline__ T proj_u(const Prm<T>& P, const Lv<T>& L, int i, int j) {
+  if (!L.px && (i <= 0 || i >= L.m1)) return T(0);
+  int k = L.at(i, j);
+  T cl = L.c[k], cr = L.c[k + 1];
+  T rl = rho_of(P, cl), rr = rho_of(P, cr);
+  T Ar = T(0.5) * (rl + rr);
+  T dp = (L.p[k + 1] - L.p[k]) * L.ih;
+  T st = T(0.5) * (rr * L.mu[k] + rl * L.mu[k + 1]) * (cr - cl) * L.ih;
+  return L.u[k] + (st - dp) * P.iM / (Ar * P.idt);
+}
+// v^{n+1} at edge (i, j+1/2), j = 0..m2; zero on the walls in y
+template <typename T>
+__device__ __forceinline__ T proj_v(const Prm<T>& P, const Lv<T>& L, int i, int j) {
+  if (j <= 0 || j >= L.m2) return T(0);
+  const int W = L.pitch;
+  int k = L.at(i, j);
+  T cb = L.c[k], ct = L.c[k + W];
+  T rb = rho_of(P, cb), rt = rho_of(P, ct);
+  T Ar = T(0.5) * (rb + rt);
+  T dp = (L.p[k + W] - L.p[k]) * L.ih;
+  T st = T(0.5) * (rt * L.mu[k] + rb * L.mu[k + W]) * (ct - cb) * L.ih;
+  return L.v[k] + (st - dp) * P.iM / (Ar * P.idt) - P.Fr_inv / P.idt;
+}
+// (pj-num-phase): rho^n (c - c^n)/dt + a_x(rho_ew D_x c u^{n+1}) + a_y(...)
+// - (1/Pe) grad_d.(A m^n grad_D mu) - (alpha/Pe) grad_d.(A m^n grad_D p), with
+// rho = rho(c^{n+1}) and c^{n+1} in the advection
+template <typename T>
+__device__ __forceinline__ T opp_c(const Prm<T>& P, const Lv<T>& L, int i, int j) {
+  const int W = L.pitch;
+  int k = L.at(i, j);
+  const T* c = L.c;
+  T ck = c[k];
+  T t = L.rhon[k] * (ck - L.cn[k]) * P.idt;
+  T ax = T(0.5) * (rho_of(P, c[k + 1]) * (c[k + 1] - ck) * L.ih * proj_u(P, L, i, j) +
+                   rho_of(P, c[k - 1]) * (ck - c[k - 1]) * L.ih * proj_u(P, L, i - 1, j));
+  T ay = T(0.5) * (rho_of(P, c[k + W]) * (c[k + W] - ck) * L.ih * proj_v(P, L, i, j) +
+                   rho_of(P, c[k - W]) * (ck - c[k - W]) * L.ih * proj_v(P, L, i, j - 1));
+  T diff = lap_h2(L.mobn, L.mu, k, W) + P.alpha * lap_h2(L.mobn, L.p, k, W);
+  return t + ax + ay - P.iPe * L.ih2 * diff;
+}
+// (pj-num-mass): d_x u^{n+1} + d_y v^{n+1} - (alpha/Pe)(grad.(A m grad mu) + alpha grad.(A m grad p))
+template <typename T>
+__device__ __forceinline__ T opp_p(const Prm<T>& P, const Lv<T>& L, int i, int j) {
+  const int W = L.pitch;
+  int k = L.at(i, j);
+  T dv = (proj_u(P, L, i, j) - proj_u(P, L, i - 1, j) + proj_v(P, L, i, j) - proj_v(P, L, i, j - 1)) * L.ih;
+  T diff = lap_h2(L.mobn, L.mu, k, W) + P.alpha * lap_h2(L.mobn, L.p, k, W);
+  return dv - P.alpha * P.iPe * L.ih2 * diff;
+}
+// (pj-num-chem): as (pm-num-chem) with rho^n in front of mu
+template <typename T>
+__device__ __forceinline__ T opp_mu(const Prm<T>& P, const Lv<T>& L, int k) {
+  const int W = L.pitch;
+  const T rq[4] = {rho_of(P, L.c[k + 1]), rho_of(P, L.c[k - 1]), rho_of(P, L.c[k + W]),
+                   rho_of(P, L.c[k - W])};
+  return op_mu_r(P, L, k, rho_of(P, L.c[k]), rq, L.rhon[k]);
+}
+template <typename T>
+__device__ __forceinline__ T opp_u(const Prm<T>& P, const Lv<T>& L, int k) {
+  return op_u<T, false>(P, L, k, T(0.5) * (rho_of(P, L.c[k]) + rho_of(P, L.c[k + 1])));
+}
+template <typename T>
+__device__ __forceinline__ T opp_v(const Prm<T>& P, const Lv<T>& L, int k) {
+  return op_v<T, false>(P, L, k, T(0.5) * (rho_of(P, L.c[k]) + rho_of(P, L.c[k + L.pitch])));
 }
 
 // ---------------------------------------------------------------------------
@@ -405,6 +499,18 @@ struct FullForm {
   template <typename T> static __device__ __forceinline__ T Np(const Prm<T>& P, const Lv<T>& L, int k) { return op_p(P, L, k); }
   template <typename T> static __device__ __forceinline__ T Nu(const Prm<T>& P, const Lv<T>& L, int k) { return op_u(P, L, k); }
   template <typename T> static __device__ __forceinline__ T Nv(const Prm<T>& P, const Lv<T>& L, int k) { return op_v(P, L, k); }
+};
+// The projection method on the full iterate (u, v arrays hold the intermediate
+// velocity).  Its N_c and N_p need the cell index (i, j) (wall edges of the
+// projected velocity), so the kernels call opp_c / opp_p directly.
+struct ProjForm {
+  template <typename T> static __device__ __forceinline__ T val_c(const Lv<T>& L, int k) { return L.c[k]; }
+  template <typename T> static __device__ __forceinline__ T val_u(const Lv<T>& L, int k) { return L.u[k]; }
+  template <typename T> static __device__ __forceinline__ T val_v(const Lv<T>& L, int k) { return L.v[k]; }
+  template <typename T> static __device__ __forceinline__ T val_mu(const Lv<T>& L, int k) { return L.mu[k]; }
+  template <typename T> static __device__ __forceinline__ T Nmu(const Prm<T>& P, const Lv<T>& L, int k) { return opp_mu(P, L, k); }
+  template <typename T> static __device__ __forceinline__ T Nu(const Prm<T>& P, const Lv<T>& L, int k) { return opp_u(P, L, k); }
+  template <typename T> static __device__ __forceinline__ T Nv(const Prm<T>& P, const Lv<T>& L, int k) { return opp_v(P, L, k); }
 };
 struct ErrForm {
   template <typename T> static __device__ __forceinline__ T val_c(const Lv<T>& L, int k) { return L.Bc[k] + L.c[k]; }

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -18,6 +19,7 @@
 
 using qn::ErrForm;
 using qn::FullForm;
+using qn::ProjForm;
 using qn::Lv;
 using qn::Prm;
 
@@ -106,6 +108,8 @@ struct qnsch_s {
   int fuse64 = 512, fuse32 = 2048;
   // 0: the paper's separate CH and Vanka sweeps; 1: the coupled 7x7 block
   int coupled = 0;
+  // 0: the primitive method (Sec. 6.1); 1: the projection method (Sec. 6.2)
+  int scheme = 0;
   // grid
   int m1, m2, px, nlev, kcol;
   double h;
@@ -330,6 +334,31 @@ constexpr int MAX_PROF_EVENTS = 8192;
 template <typename T, class Form>
 void smooth(qnsch_s* s, const std::vector<Lv<T>>& Ls, const Prm<T>& P, int l) {
   const Lv<T>& L = Ls[l];
+  if constexpr (std::is_same<Form, ProjForm>::value) {
+    // projection method (Sec. 7.2): CH red-black, the intermediate-velocity
+    // blocks over the Vanka colours, pressure Gauss-Seidel red-black
+    qn::launch_ch<T, Form>(P, L, 0, s->stream);
+    qn::launch_ch<T, Form>(P, L, 1, s->stream);
+    for (int c = 0; c < L.kcol; ++c) {
+      bool rec = s->prof && l == 0 && s->ev_used + 2 <= MAX_PROF_EVENTS;
+      if (rec) {
+        while ((int)s->ev.size() < s->ev_used + 2) {
+          cudaEvent_t e;
+          if (cudaEventCreate(&e) != cudaSuccess) { rec = false; break; }
+          s->ev.push_back(e);
+        }
+      }
+      if (rec) cudaEventRecord(s->ev[s->ev_used], s->stream);
+      qn::launch_vanka4<T, Form>(P, L, c, (T)s->omega, s->stream);
+      if (rec) {
+        cudaEventRecord(s->ev[s->ev_used + 1], s->stream);
+        s->ev_used += 2;
+      }
+    }
+    qn::launch_pgs<T>(P, L, 0, s->stream);
+    qn::launch_pgs<T>(P, L, 1, s->stream);
+    return;
+  }
   if (!s->coupled) {
     qn::launch_ch<T, Form>(P, L, 0, s->stream);
     qn::launch_ch<T, Form>(P, L, 1, s->stream);
@@ -375,10 +404,12 @@ static int coarse_sweeps(const qnsch_s* s) {
 // FAS V-cycle (Sec. 7.1) from level l on the level set Ls
 template <typename T, class Form>
 void vcycle(qnsch_s* s, const std::vector<Lv<T>>& Ls, const Prm<T>& P, int l) {
-  if (l >= fused_from(s, Ls)) {
-    qn::launch_coarse_vcycle<T, Form>(P, &Ls[l], s->nlev - l, s->nu1, s->nu2, coarse_sweeps(s),
-                                      s->kcol, (T)s->omega, s->coupled, s->stream);
-    return;
+  if constexpr (!std::is_same<Form, ProjForm>::value) {  // projection: per-level launches
+    if (l >= fused_from(s, Ls)) {
+      qn::launch_coarse_vcycle<T, Form>(P, &Ls[l], s->nlev - l, s->nu1, s->nu2, coarse_sweeps(s),
+                                        s->kcol, (T)s->omega, s->coupled, s->stream);
+      return;
+    }
   }
   if (l == s->nlev - 1) {
     int nc = coarse_sweeps(s);
@@ -425,7 +456,8 @@ void enter(qnsch_s* s) {
 // queue the finest FP64 residual, its norms and their copy to s->hbuf[0..9]
 void enqueue_norms(qnsch_s* s, const Prm<double>& P) {
   const Lv<double>& F = s->L[0];
-  qn::launch_residual<double, FullForm>(P, F, s->part, s->stream);
+  if (s->scheme) qn::launch_residual<double, ProjForm>(P, F, s->part, s->stream);
+  else qn::launch_residual<double, FullForm>(P, F, s->part, s->stream);
   qn::launch_norms_finalize(F, s->part, s->scal, s->stream);
   cudaMemcpyAsync(s->hbuf, s->scal, 10 * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
 }
@@ -556,7 +588,8 @@ void correction_cycle(qnsch_s* s, std::vector<Lv<T>>& E) {
 // FP64 residual with norms and their copy to the host
 void cycle_body(qnsch_s* s, const Prm<double>& P) {
   if (s->precision == 0) {
-    vcycle<double, FullForm>(s, s->L, P, 0);
+    if (s->scheme) vcycle<double, ProjForm>(s, s->L, P, 0);
+    else vcycle<double, FullForm>(s, s->L, P, 0);
   } else {
     // the residual arrays hold r(x) of the current iterate (see one_cycle)
     if (s->precision == 1) correction_cycle<float>(s, s->Ef);
@@ -660,16 +693,29 @@ void launch_commit(qnsch_s* s) {
   int pitch = F.pitch;
   double* src[5] = {F.c, F.mu, F.p, F.u, F.v};
   double* dst[5] = {s->sc, s->smu, s->sp, s->su, s->sv};
-  for (int q = 0; q < 5; ++q)
+  int nq = s->scheme ? 3 : 5;  // projection: the velocity is u^{n+1} of (pj-num-pjx)
+  for (int q = 0; q < nq; ++q)
     cudaMemcpyAsync(dst[q] - pitch - 1, src[q] - pitch - 1, bytes, cudaMemcpyDeviceToDevice,
                     s->stream);
-  cudaMemcpyAsync(s->hbuf + 25, s->scal + 25, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+  if (s->scheme) {
+    qn::launch_proj_velocity(P, F, s->su, s->sv, s->stream);
+    Lv<double> S = F;  // the committed arrays, to fill their ghosts
+    S.c = s->sc;
+    S.mu = s->smu;
+    S.p = s->sp;
+    S.u = s->su;
+    S.v = s->sv;
+    qn::launch_bc_unknowns(S, s->stream);
+    qn::launch_proj_diss(P, F, s->su, s->sv, s->part, s->scal + 26, s->stream);
+  }
+  cudaMemcpyAsync(s->hbuf + 25, s->scal + 25, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                  s->stream);
 }
 
 int finish_commit(qnsch_s* s) {
   int rc = sync(s);
   if (rc) return rc;
-  s->last_diss = s->hbuf[25];
+  s->last_diss = s->hbuf[25] + (s->scheme ? s->hbuf[26] : 0.0);
   s->pending = 0;
   return QNSCH_OK;
 }
@@ -792,13 +838,21 @@ int qnsch_set_option(qnsch_t* s, const char* key, double value) {
   else if (k == "eps_mob") s->eps_m = value;
   else if (k == "graphs") s->use_graphs = value != 0.0;
   else if (k == "fuse_cells") s->fuse64 = (int)value;
-  else if (k == "coupled") s->coupled = value != 0.0;
-  else if (k == "fuse_cells32") s->fuse32 = (int)value;
+  else if (k == "coupled") {
+    if (value != 0.0 && s->scheme) return QNSCH_EINVAL;  // a primitive-method smoother
+    s->coupled = value != 0.0;
+  } else if (k == "fuse_cells32") s->fuse32 = (int)value;
   else if (k == "precision") {
     int p = (int)value;
     if (p < 0 || p > 2 || (double)p != value) return QNSCH_EINVAL;
+    if (p != 0 && s->scheme) return QNSCH_EINVAL;  // the projection method runs in FP64
     if (s->pending) return QNSCH_ESTATE;
     s->precision = p;
+  } else if (k == "scheme") {
+    if (value != 0.0 && value != 1.0) return QNSCH_EINVAL;
+    if (value == 1.0 && (s->coupled || s->precision != 0)) return QNSCH_EINVAL;
+    if (s->pending) return QNSCH_ESTATE;
+    s->scheme = (int)value;
   } else return QNSCH_EINVAL;
   return QNSCH_OK;
 }
@@ -820,6 +874,7 @@ int qnsch_get_option(const qnsch_t* s, const char* key, double* value) {
   else if (k == "fuse_cells") *value = s->fuse64;
   else if (k == "coupled") *value = s->coupled;
   else if (k == "fuse_cells32") *value = s->fuse32;
+  else if (k == "scheme") *value = s->scheme;
   else return QNSCH_EINVAL;
   return QNSCH_OK;
 }
@@ -1087,7 +1142,8 @@ int qnsch_smooth_ch(qnsch_t* s, int colour) {
   if (s) s->res_valid = 0;
   if (!s || colour < 0 || colour > 1) return QNSCH_EINVAL;
   if (!s->pending) return QNSCH_ESTATE;
-  qn::launch_ch<double, FullForm>(make_prm(s), s->L[0], colour, s->stream);
+  if (s->scheme) qn::launch_ch<double, ProjForm>(make_prm(s), s->L[0], colour, s->stream);
+  else qn::launch_ch<double, FullForm>(make_prm(s), s->L[0], colour, s->stream);
   return sync(s);
 }
 
@@ -1095,7 +1151,8 @@ int qnsch_smooth_vanka(qnsch_t* s, int colour) {
   if (s) s->res_valid = 0;
   if (!s || colour < 0 || colour >= s->kcol) return QNSCH_EINVAL;
   if (!s->pending) return QNSCH_ESTATE;
-  qn::launch_vanka<double, FullForm>(make_prm(s), s->L[0], colour, s->omega, s->stream);
+  if (s->scheme) qn::launch_vanka4<double, ProjForm>(make_prm(s), s->L[0], colour, s->omega, s->stream);
+  else qn::launch_vanka<double, FullForm>(make_prm(s), s->L[0], colour, s->omega, s->stream);
   return sync(s);
 }
 
@@ -1206,7 +1263,10 @@ int qnsch_smooth(qnsch_t* s, int sweeps) {
   if (!s || sweeps < 0) return QNSCH_EINVAL;
   if (!s->pending) return QNSCH_ESTATE;
   Prm<double> P = make_prm(s);
-  for (int k = 0; k < sweeps; ++k) smooth<double, FullForm>(s, s->L, P, 0);
+  for (int k = 0; k < sweeps; ++k) {
+    if (s->scheme) smooth<double, ProjForm>(s, s->L, P, 0);
+    else smooth<double, FullForm>(s, s->L, P, 0);
+  }
   return sync(s);
 }
 
