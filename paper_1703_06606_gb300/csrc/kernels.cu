@@ -98,11 +98,17 @@ __device__ __forceinline__ void residual_cell(const Prm<T>& P, const Lv<T>& L, i
     nu = hu ? op_u(P, L, k, T(0.5) * (rk + rq[0])) : T(0);
     nv = hv ? op_v(P, L, k, T(0.5) * (rk + rq[2])) : T(0);
   } else if constexpr (std::is_same<Form, ProjForm>::value) {
-    nc = opp_c(P, L, i, j);
-    nm = opp_mu(P, L, k);
-    np = opp_p(P, L, i, j);
-    nu = hu ? opp_u(P, L, k) : T(0);
-    nv = hv ? opp_v(P, L, k) : T(0);
+    const int W = L.pitch;
+    T rk = rho_of(P, L.c[k]);
+    const T rq[4] = {rho_of(P, L.c[k + 1]), rho_of(P, L.c[k - 1]), rho_of(P, L.c[k + W]),
+                     rho_of(P, L.c[k - W])};
+    T w[4];
+    proj_faces(P, L, i, j, rk, rq, w);
+    nc = opp_c_w(P, L, k, rq, w);
+    nm = op_mu_r(P, L, k, rk, rq, L.rhon[k]);
+    np = opp_p_w(P, L, k, w);
+    nu = hu ? op_u<T, false>(P, L, k, T(0.5) * (rk + rq[0])) : T(0);
+    nv = hv ? op_v<T, false>(P, L, k, T(0.5) * (rk + rq[2])) : T(0);
   } else {
     nc = Form::Nc(P, L, k);
     nm = Form::Nmu(P, L, k);
@@ -161,11 +167,13 @@ __device__ __forceinline__ void ch_system(const Prm<T>& P, const Lv<T>& L, int i
 #pragma unroll
   for (int f = 0; f < 4; ++f) rq4[f] = rho_of(P, Form::val_c(L, k + off[f]));
   T Rc, Rm;
+  T wf[4];  // projection method: the face velocities u^{n+1} (E, W, N, S)
   if constexpr (std::is_same<Form, FullForm>::value) {
     Rc = op_c(P, L, k, rho) - L.fc[k];
     Rm = op_mu(P, L, k, rho, rq4) - L.fmu[k];
   } else if constexpr (std::is_same<Form, ProjForm>::value) {
-    Rc = opp_c(P, L, i, j) - L.fc[k];
+    proj_faces(P, L, i, j, rho, rq4, wf);
+    Rc = opp_c_w(P, L, k, rq4, wf) - L.fc[k];
     Rm = op_mu_r(P, L, k, rho, rq4, L.rhon[k]) - L.fmu[k];
   } else {
     Rc = Form::Nc(P, L, k) - L.fc[k];
@@ -207,10 +215,8 @@ __device__ __forceinline__ void ch_system(const Prm<T>& P, const Lv<T>& L, int i
     // advection a(rho(c) D c u^{n+1}) differentiated in c_ij through D c only,
     // with rho(c) of the neighbours and u^{n+1} at the iterate (the smoother's
     // choice; the fixed point is the scheme's)
-    T ue = proj_u(P, L, i, j), uw = proj_u(P, L, i - 1, j);
-    T vn = proj_v(P, L, i, j), vs = proj_v(P, L, i, j - 1);
-    J11 = rnk * P.idt + T(0.5) * (-rq4[0] * ue + rq4[1] * uw) * L.ih +
-          T(0.5) * (-rq4[2] * vn + rq4[3] * vs) * L.ih;
+    J11 = rnk * P.idt + T(0.5) * (-rq4[0] * wf[0] + rq4[1] * wf[1]) * L.ih +
+          T(0.5) * (-rq4[2] * wf[2] + rq4[3] * wf[3]) * L.ih;
     J21 = -P.K * dbulk - dgrad + P.Lam * T(0.25) * L.ih2 * dd;
     J22 = rnk;
   }
@@ -392,6 +398,11 @@ __device__ __forceinline__ void vanka_system(const Prm<T>& P, const Lv<T>& L, in
     b[1] = act[1] ? op_u(P, L, k, Arq[1]) - L.fu[k] : T(0);
     b[2] = act[2] ? op_v(P, L, k - W, Arq[2]) - L.fv[k - W] : T(0);
     b[3] = act[3] ? op_v(P, L, k, Arq[3]) - L.fv[k] : T(0);
+  } else if constexpr (std::is_same<Form, ProjForm>::value) {
+    b[0] = act[0] ? op_u<T, false>(P, L, kW, Arq[0]) - L.fu[kW] : T(0);
+    b[1] = act[1] ? op_u<T, false>(P, L, k, Arq[1]) - L.fu[k] : T(0);
+    b[2] = act[2] ? op_v<T, false>(P, L, k - W, Arq[2]) - L.fv[k - W] : T(0);
+    b[3] = act[3] ? op_v<T, false>(P, L, k, Arq[3]) - L.fv[k] : T(0);
   } else {
     b[0] = act[0] ? Form::Nu(P, L, kW) - L.fu[kW] : T(0);
     b[1] = act[1] ? Form::Nu(P, L, k) - L.fu[k] : T(0);
@@ -712,8 +723,12 @@ template <typename T>
 __device__ __forceinline__ void pgs_cell(const Prm<T>& P, const Lv<T>& L, int i, int j) {
   const int W = L.pitch;
   int k = L.at(i, j);
-  T R = opp_p(P, L, i, j) - L.fp[k];
   T rk = rho_of(P, L.c[k]);
+  const T rq[4] = {rho_of(P, L.c[k + 1]), rho_of(P, L.c[k - 1]), rho_of(P, L.c[k + W]),
+                   rho_of(P, L.c[k - W])};
+  T w[4];
+  proj_faces(P, L, i, j, rk, rq, w);
+  T R = opp_p_w(P, L, k, w) - L.fp[k];
   const bool wall[4] = {!L.px && i == L.m1, !L.px && i == 1, j == L.m2, j == 1};
   const int off[4] = {1, -1, W, -W};
   T d = T(0);
@@ -721,7 +736,7 @@ __device__ __forceinline__ void pgs_cell(const Prm<T>& P, const Lv<T>& L, int i,
   for (int f = 0; f < 4; ++f) {
     if (wall[f]) continue;
     int q = k + off[f];
-    T Ar = T(0.5) * (rk + rho_of(P, L.c[q]));
+    T Ar = T(0.5) * (rk + rq[f]);
     d += P.iM / (Ar * P.idt) * L.ih2 + P.alpha * P.alpha * P.iPe * T(0.5) * (L.mobn[k] + L.mobn[q]) * L.ih2;
   }
   store_cell(L, L.p, i, j, L.p[k] - R / d);
@@ -1274,6 +1289,36 @@ constexpr int QN_TEAM_MAX_SLOTS = 32;
 template <typename T, class Form>
 __device__ void smooth_block(const Prm<T>& P, const Lv<T>& L, T omega, int coupled) {
   const int kcol = L.kcol;
+  if constexpr (std::is_same<Form, ProjForm>::value) {
+    // projection method (Sec. 7.2): CH red-black, intermediate-velocity blocks
+    // over the Vanka colours, pressure Gauss-Seidel red-black
+    const int mpr = (L.m1 + 1) / 2;
+    for (int col = 0; col < 2; ++col) {
+      for (int t = threadIdx.x; t < mpr * L.m2; t += blockDim.x) {
+        int j = t / mpr + 1;
+        int i = (((col - j) & 1) ? 1 : 2) + 2 * (t % mpr);
+        if (i <= L.m1) ch_cell<T, Form>(P, L, i, j);
+      }
+      __syncthreads();
+    }
+    for (int col = 0; col < kcol; ++col) {
+      ColourSlots cs = vanka_slots(L, col);
+      for (int t = threadIdx.x; t < cs.n; t += blockDim.x) {
+        int i, j;
+        if (vanka_slot_cell(L, col, cs, t, i, j)) vanka4_cell<T, Form>(P, L, i, j, omega);
+      }
+      __syncthreads();
+    }
+    for (int col = 0; col < 2; ++col) {
+      for (int t = threadIdx.x; t < mpr * L.m2; t += blockDim.x) {
+        int j = t / mpr + 1;
+        int i = (((col - j) & 1) ? 1 : 2) + 2 * (t % mpr);
+        if (i <= L.m1) pgs_cell<T>(P, L, i, j);
+      }
+      __syncthreads();
+    }
+    return;
+  }
   if (coupled) {
     for (int col = 0; col < kcol; ++col) {
       ColourSlots cs = vanka_slots(L, col);
@@ -1930,6 +1975,8 @@ QN_INSTANTIATE_FORM(float, ErrForm)
 // projection method (FP64, per-level launches)
 template void launch_residual<double, ProjForm>(const Prm<double>&, const Lv<double>&, double*,
                                                 cudaStream_t);
+template void launch_coarse_vcycle<double, ProjForm>(const Prm<double>&, const Lv<double>*, int, int,
+                                                     int, int, int, double, int, cudaStream_t);
 template void launch_add_op<double, ProjForm>(const Prm<double>&, const Lv<double>&, cudaStream_t);
 template void launch_ch<double, ProjForm>(const Prm<double>&, const Lv<double>&, int, cudaStream_t);
 template void launch_vanka4<double, ProjForm>(const Prm<double>&, const Lv<double>&, int, double,

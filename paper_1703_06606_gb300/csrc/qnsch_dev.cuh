@@ -269,6 +269,49 @@ __device__ __forceinline__ T proj_v(const Prm<T>& P, const Lv<T>& L, int i, int 
   T st = T(0.5) * (rt * L.mu[k] + rb * L.mu[k + W]) * (ct - cb) * L.ih;
   return L.v[k] + (st - dp) * P.iM / (Ar * P.idt) - P.Fr_inv / P.idt;
 }
+// The four face velocities u^{n+1} of cell (i,j) (E, W, N, S), from rho(c) of the
+// cell (rk) and of its neighbours (rq[f] for k + 1, k - 1, k + W, k - W): the
+// same values as proj_u / proj_v without re-evaluating the densities.
+template <typename T>
+__device__ __forceinline__ void proj_faces(const Prm<T>& P, const Lv<T>& L, int i, int j, T rk,
+                                           const T (&rq)[4], T (&w)[4]) {
+  const int W = L.pitch;
+  int k = L.at(i, j);
+  const T *c = L.c, *mu = L.mu, *p = L.p;
+  const T g = P.Fr_inv / P.idt;
+  // face between cells a (left/below) and b = a + off, velocity array at a
+  auto face = [&](int a, int off, const T* vel, T ra, T rb, T grav) {
+    T Ar = T(0.5) * (ra + rb);
+    T dp = (p[a + off] - p[a]) * L.ih;
+    T st = T(0.5) * (rb * mu[a] + ra * mu[a + off]) * (c[a + off] - c[a]) * L.ih;
+    return vel[a] + (st - dp) * P.iM / (Ar * P.idt) - grav;
+  };
+  w[0] = (!L.px && i == L.m1) ? T(0) : face(k, 1, L.u, rk, rq[0], T(0));
+  w[1] = (!L.px && i == 1) ? T(0) : face(k - 1, 1, L.u, rq[1], rk, T(0));
+  w[2] = (j == L.m2) ? T(0) : face(k, W, L.v, rk, rq[2], g);
+  w[3] = (j == 1) ? T(0) : face(k - W, W, L.v, rq[3], rk, g);
+}
+// opp_c and opp_p from the shared densities and face velocities
+template <typename T>
+__device__ __forceinline__ T opp_c_w(const Prm<T>& P, const Lv<T>& L, int k, const T (&rq)[4],
+                                     const T (&w)[4]) {
+  const int W = L.pitch;
+  const T* c = L.c;
+  T ck = c[k];
+  T t = L.rhon[k] * (ck - L.cn[k]) * P.idt;
+  T ax = T(0.5) * (rq[0] * (c[k + 1] - ck) * L.ih * w[0] + rq[1] * (ck - c[k - 1]) * L.ih * w[1]);
+  T ay = T(0.5) * (rq[2] * (c[k + W] - ck) * L.ih * w[2] + rq[3] * (ck - c[k - W]) * L.ih * w[3]);
+  T diff = lap_h2(L.mobn, L.mu, k, W) + P.alpha * lap_h2(L.mobn, L.p, k, W);
+  return t + ax + ay - P.iPe * L.ih2 * diff;
+}
+template <typename T>
+__device__ __forceinline__ T opp_p_w(const Prm<T>& P, const Lv<T>& L, int k, const T (&w)[4]) {
+  const int W = L.pitch;
+  T dv = (w[0] - w[1] + w[2] - w[3]) * L.ih;
+  T diff = lap_h2(L.mobn, L.mu, k, W) + P.alpha * lap_h2(L.mobn, L.p, k, W);
+  return dv - P.alpha * P.iPe * L.ih2 * diff;
+}
+
 // (pj-num-phase): rho^n (c - c^n)/dt + a_x(rho_ew D_x c u^{n+1}) + a_y(...)
 // - (1/Pe) grad_d.(A m^n grad_D mu) - (alpha/Pe) grad_d.(A m^n grad_D p), with
 // rho = rho(c^{n+1}) and c^{n+1} in the advection

@@ -404,12 +404,10 @@ static int coarse_sweeps(const qnsch_s* s) {
 // FAS V-cycle (Sec. 7.1) from level l on the level set Ls
 template <typename T, class Form>
 void vcycle(qnsch_s* s, const std::vector<Lv<T>>& Ls, const Prm<T>& P, int l) {
-  if constexpr (!std::is_same<Form, ProjForm>::value) {  // projection: per-level launches
-    if (l >= fused_from(s, Ls)) {
-      qn::launch_coarse_vcycle<T, Form>(P, &Ls[l], s->nlev - l, s->nu1, s->nu2, coarse_sweeps(s),
-                                        s->kcol, (T)s->omega, s->coupled, s->stream);
-      return;
-    }
+  if (l >= fused_from(s, Ls)) {
+    qn::launch_coarse_vcycle<T, Form>(P, &Ls[l], s->nlev - l, s->nu1, s->nu2, coarse_sweeps(s),
+                                      s->kcol, (T)s->omega, s->coupled, s->stream);
+    return;
   }
   if (l == s->nlev - 1) {
     int nc = coarse_sweeps(s);

@@ -120,3 +120,19 @@ def test_projection_option_rules(qn):
     h = qn.Solver(16, 16, precision=1)
     with pytest.raises(qn.QnschError):
         h.set_option("scheme", 1)
+
+
+@pytest.mark.parametrize("px", [False, True])
+def test_projection_fused_coarse_levels_match_per_level_launches(qn, px):
+    """The single-block V-cycle of the small levels runs the projection
+    smoother in the same colour order as the per-level launches."""
+    P = W.small_case(64, 96, px)
+    out = []
+    for fuse in (0, 10 ** 6):
+        g = qn.Solver(**P.create_kwargs(), scheme=1, fuse_cells=fuse)
+        g.set_fields(P.fields())
+        g.begin_step(P.dt)
+        for _ in range(2):
+            g.vcycle()
+        out.append(g.get_iterate())
+    same_fields(out[0], out[1], 1e-12)
