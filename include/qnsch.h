@@ -91,7 +91,14 @@ int qnsch_footprint(const qnsch_grid* grid, int precision, size_t* bytes);
    longest side n exceeds 4 cells gets nu_coarse * ceil(n/4)^2), "tol": 1e-9,
    "maxcyc": 50, "omega_vanka": 1, "M": Cn, "eta_st": eta(rho1, rho2),
    "eps_mob": Cn, "precision": 0, "graphs": 1, "fuse_cells": 512,
-   "fuse_cells32": 2048, "coupled": 0.  Unknown keys give QNSCH_EINVAL.
+   "fuse_cells32": 2048, "coupled": 0, "scheme": 0, "vanka_team_max": 8192.
+   Unknown keys give QNSCH_EINVAL.
+   scheme: 0 the primitive method (Sec. 6.1); 1 the projection method
+   (Sec. 6.2; precision 0 and coupled 0 only).
+   vanka_team_max: FP64 levels with at most this many cells per Vanka colour
+   run the per-level Vanka launches with four lanes per 5x5 block (same
+   arithmetic, shorter critical path when the colour leaves most of the GPU
+   idle).
    coupled: 0 smooths with the paper's separate sweeps (CH 2x2 red-black, then
    the Vanka 5x5 colours, Sec. 7.1); 1 replaces them by one sweep over the
    Vanka colours of a coupled 7x7 Newton block in (c, mu, u_W, u_E, v_S, v_N, p).

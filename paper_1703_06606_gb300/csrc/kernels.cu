@@ -336,6 +336,10 @@ __device__ __forceinline__ void vanka_system(const Prm<T>& P, const Lv<T>& L, in
     T Arn = L.Aru[ke];
     T Ar = Arq[q];
     T gt = (j == L.m2) ? T(2) : T(1), gb = (j == 1) ? T(2) : T(1);
+    if constexpr (!std::is_same<Form, ErrForm>::value) {  // per-step coefficients
+      A[q][q] = L.Dgu[ke] + T(0.5) * P.idt * Ar;
+      continue;
+    }
     A[q][q] = Arn * P.idt + T(0.5) * (Ar - Arn) * P.idt +
               T(0.5) * ih * (-L.Sx[ke + 1] + L.Sx[ke] - L.Qx[ke] * gt + L.Qx[ke - W] * gb) +
               L.Dvu[ke] +
@@ -361,6 +365,10 @@ __device__ __forceinline__ void vanka_system(const Prm<T>& P, const Lv<T>& L, in
     T Arn = L.Arv[ke];
     T Ar = Arq[q];
     T ge = (!L.px && i == L.m1) ? T(2) : T(1), gw = (!L.px && i == 1) ? T(2) : T(1);
+    if constexpr (!std::is_same<Form, ErrForm>::value) {  // per-step coefficients
+      A[q][q] = L.Dgv[ke] + T(0.5) * P.idt * Ar;
+      continue;
+    }
     A[q][q] = Arn * P.idt + T(0.5) * (Ar - Arn) * P.idt +
               T(0.5) * ih * (-L.Qy[ke] * ge + L.Qy[ke - 1] * gw - L.Sy[ke + W] + L.Sy[ke]) +
               L.Dvv[ke] +
@@ -420,14 +428,59 @@ __device__ __forceinline__ void vanka_system(const Prm<T>& P, const Lv<T>& L, in
     }
 }
 
+// Exact solve of the Vanka system A d = b by its structure.  The velocity block
+// is A_vv = B + v3 w w^T: every coupling between an x-edge and a y-edge of the
+// cell is +-v3 (the grad-div term), w = (1, -1, 1, -1) on active edges and 0 on
+// wall edges, and B is block-diagonal (the x pair and the y pair).  The
+// pressure column is a w (a = 1/(M h)) and the pressure row -w/h.  With
+// y = B^-1 b_v, z = B^-1 w, s = w.z, t = w.y, g = 1/(1 + v3 s)
+// (Sherman-Morrison), p = (b_p + t g/h)/(A_pp + a s g/h) and
+// d_v = y - z g (v3 t + a p): two 2x2 solves and three divisions in place of
+// 5x5 elimination.  B is diagonally dominant and s, g > 0, so no pivoting.
+// NP = 5 solves the full system, NP = 4 the velocity block alone.
+template <typename T, int NP>
+__device__ __forceinline__ void solve_vanka(const T (&A)[5][5], T (&b)[5], const bool (&act)[5],
+                                            T v3, T a, T ih) {
+  // w_q is +1, -1 or 0, so the products with w are selections
+  T y[4], z[4];
+#pragma unroll
+  for (int blk = 0; blk < 4; blk += 2) {
+    const int p0 = blk, p1 = blk + 1;
+    const bool a0 = act[p0], a1 = act[p1];
+    // B = A_vv - v3 w w^T on this pair: w_p0 w_p0 = a0, w_p1 w_p1 = a1, w_p0 w_p1 = -(a0 a1)
+    T B00 = a0 ? A[p0][p0] - v3 : A[p0][p0];
+    T B11 = a1 ? A[p1][p1] - v3 : A[p1][p1];
+    T B01 = (a0 && a1) ? A[p0][p1] + v3 : A[p0][p1];
+    T B10 = (a0 && a1) ? A[p1][p0] + v3 : A[p1][p0];
+    T idet = T(1) / (B00 * B11 - B01 * B10);
+    y[p0] = (B11 * b[p0] - B01 * b[p1]) * idet;
+    y[p1] = (B00 * b[p1] - B10 * b[p0]) * idet;
+    // z = B^-1 w with w_p0 = a0 ? 1 : 0, w_p1 = a1 ? -1 : 0
+    T zn0 = (a0 ? B11 : T(0)) + (a1 ? B01 : T(0));
+    T zn1 = -((a1 ? B00 : T(0)) + (a0 ? B10 : T(0)));
+    z[p0] = zn0 * idet;
+    z[p1] = zn1 * idet;
+  }
+  // inactive entries of y and z are 0 (identity rows, b = 0, w = 0)
+  T sdot = (z[0] - z[1]) + (z[2] - z[3]);
+  T tdot = (y[0] - y[1]) + (y[2] - y[3]);
+  T g = T(1) / (T(1) + v3 * sdot);
+  T pr = T(0);
+  if constexpr (NP == 5) pr = (b[4] + ih * tdot * g) / (A[4][4] + ih * a * sdot * g);
+  T f = g * (v3 * tdot + a * pr);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) b[q] = y[q] - z[q] * f;
+  if constexpr (NP == 5) b[4] = pr;
+}
+
 template <typename T, class Form>
 __device__ __forceinline__ void vanka_cell(const Prm<T>& P, const Lv<T>& L, int i, int j, T omega) {
   T A[5][5], b[5];
   bool act[5];
   vanka_system<T, Form>(P, L, i, j, A, b, act);
-  solve5(A, b);
   const int W = L.pitch;
   int k = L.at(i, j);
+  solve_vanka<T, 5>(A, b, act, L.visn[k] * P.iRe * L.ih2 * T(1.0 / 3.0), L.ih * P.iM, L.ih);
   int eW = (L.px && i == 1) ? L.m1 : i - 1;
   int kW = L.at(eW, j);
   if (act[0]) store_u(L, eW, j, L.u[kW] - omega * b[0]);
@@ -689,16 +742,10 @@ __device__ __forceinline__ void vanka4_cell(const Prm<T>& P, const Lv<T>& L, int
   T A5[5][5], b5[5];
   bool act[5];
   vanka_system<T, Form>(P, L, i, j, A5, b5, act);
-  T A[4][4], b[4];
-#pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    b[r] = b5[r];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) A[r][c] = A5[r][c];
-  }
-  solve_n<T, 4>(A, b);
   const int W = L.pitch;
   int k = L.at(i, j);
+  solve_vanka<T, 4>(A5, b5, act, L.visn[k] * P.iRe * L.ih2 * T(1.0 / 3.0), L.ih * P.iM, L.ih);
+  const T(&b)[5] = b5;
   int eW = (L.px && i == 1) ? L.m1 : i - 1;
   int kW = L.at(eW, j);
   if (act[0]) store_u(L, eW, j, L.u[kW] - omega * b[0]);
@@ -943,6 +990,39 @@ __global__ void k_frozen_coef2(Lv<T> L) {
   if (i >= 1) L.Dvv[k] = T(0.5) * ((L.Qy[k] - L.Qy[k - 1]) + (L.Sy[k + W] - L.Sy[k])) * L.ih;
 }
 
+// per-step row coefficients of the momentum rows (needs k_frozen_coef2): time =
+// x T1 + T0 + A rho(c) x/(2dt); Dg = the iterate-independent part of the
+// diagonal entry (the whole entry is Dg + A rho(c)/(2dt)), with the reflected
+// no-slip ghosts doubling the tangential wall terms (g = 2)
+template <typename T>
+__global__ void k_frozen_coef3(Prm<T> P, Lv<T> L) {
+  int i = blockIdx.x * BX + threadIdx.x;
+  int j = blockIdx.y * BY + threadIdx.y;
+  if (i > L.m1 || j > L.m2) return;
+  const int W = L.pitch;
+  int k = L.at(i, j);
+  const T* vis = L.visn;
+  const T third = T(1.0 / 3.0);
+  if (j >= 1) {  // x-edge (i+1/2, j)
+    T Arn = L.Aru[k];
+    T gt = (j == L.m2) ? T(2) : T(1), gb = (j == 1) ? T(2) : T(1);
+    T t1 = T(0.5) * Arn * P.idt + L.Dvu[k];
+    L.T1u[k] = t1;
+    L.T0u[k] = -Arn * L.un[k] * P.idt;
+    L.Dgu[k] = t1 + T(0.5) * L.ih * (-L.Sx[k + 1] + L.Sx[k] - L.Qx[k] * gt + L.Qx[k - W] * gb) +
+               P.iRe * L.ih2 * ((vis[k + 1] + vis[k]) * (T(1) + third) + gt * L.Av[k] + gb * L.Av[k - W]);
+  }
+  if (i >= 1) {  // y-edge (i, j+1/2)
+    T Arn = L.Arv[k];
+    T ge = (!L.px && i == L.m1) ? T(2) : T(1), gw = (!L.px && i == 1) ? T(2) : T(1);
+    T t1 = T(0.5) * Arn * P.idt + L.Dvv[k];
+    L.T1v[k] = t1;
+    L.T0v[k] = -Arn * L.vn[k] * P.idt;
+    L.Dgv[k] = t1 + T(0.5) * L.ih * (-L.Qy[k] * ge + L.Qy[k - 1] * gw - L.Sy[k + W] + L.Sy[k]) +
+               P.iRe * L.ih2 * (ge * L.Av[k] + gw * L.Av[k - 1] + (vis[k + W] + vis[k]) * (T(1) + third));
+  }
+}
+
 // --------------------------------------------------------------------------
 // FAS transfers
 // --------------------------------------------------------------------------
@@ -1141,7 +1221,7 @@ __device__ __forceinline__ void bc_unknowns_block(const Lv<T>& L) {
 // normal, t across it).
 template <typename T>
 struct MomRow {
-  const T *a, *b, *S, *Q, *Tf, *Arn, *Dv, *an, *f;
+  const T *a, *b, *S, *Q, *Tf, *Arn, *T1, *T0, *Dg, *f;
   int s, t;
   T grav;
 };
@@ -1155,8 +1235,9 @@ __device__ __forceinline__ MomRow<T> mom_row(const Prm<T>& P, const Lv<T>& L, in
   R.Q = d ? L.Qy : L.Qx;
   R.Tf = d ? L.Ty : L.Tx;
   R.Arn = d ? L.Arv : L.Aru;
-  R.Dv = d ? L.Dvv : L.Dvu;
-  R.an = d ? L.vn : L.un;
+  R.T1 = d ? L.T1v : L.T1u;
+  R.T0 = d ? L.T0v : L.T0u;
+  R.Dg = d ? L.Dgv : L.Dgu;
   R.f = d ? L.fv : L.fu;
   R.s = d ? L.pitch : 1;
   R.t = d ? 1 : L.pitch;
@@ -1176,15 +1257,14 @@ __device__ __forceinline__ T mom_residual(const Prm<T>& P, const Lv<T>& L, const
   T dvl = dl + (b[k] - b[k - t]) * L.ih;
   T dvr = dr + (b[k + s] - b[k + s - t]) * L.ih;
   T Dp = (a[k + t] - ae) * L.ih, Dm = (ae - a[k - t]) * L.ih;
-  T Arn = R.Arn[k];
   T conv = T(0.5) * (R.S[k + s] * dr + R.S[k] * dl + R.Q[k] * Dp + R.Q[k - t] * Dm);
-  T time = Arn * (ae - R.an[k]) * P.idt + T(0.5) * (Ar - Arn) * P.idt * ae + R.Dv[k] * ae;
+  T time = ae * R.T1[k] + R.T0[k] + T(0.5) * P.idt * Ar * ae;
   T press = (L.p[k + s] - L.p[k]) * L.ih * P.iM;
   T st = -(rn[k + s] * L.mu[k] + rn[k] * L.mu[k + s]) * R.Tf[k] * P.iM;
   T vl = vis[k], vr = vis[k + s];
   T visc = -P.iRe * L.ih * ((vr * dr - vl * dl) + (L.Av[k] * Dp - L.Av[k - t] * Dm) +
                             (vr * dvr - vl * dvl) * T(1.0 / 3.0));
-  return time + conv + press + st + visc + R.grav * Arn - R.f[k];
+  return time + conv + press + st + visc + R.grav * R.Arn[k] - R.f[k];
 }
 
 // Vanka block of cell (i,j) by a team of four lanes (lane & 3 = q): lane q
@@ -1208,14 +1288,8 @@ __device__ __forceinline__ void vanka_team(const Prm<T>& P, const Lv<T>& L, int 
   int ke = q == 0 ? kW : (q == 2 ? k - W : k);
   MomRow<T> R = mom_row(P, L, d);
   T Ar = T(0.5) * (rho_of(P, L.c[ke]) + rho_of(P, L.c[ke + R.s]));
-  T gp = d ? ((!L.px && i == L.m1) ? T(2) : T(1)) : ((j == L.m2) ? T(2) : T(1));
-  T gm = d ? ((!L.px && i == 1) ? T(2) : T(1)) : ((j == 1) ? T(2) : T(1));
   const T* vis = L.visn;
-  T Arn = R.Arn[ke];
-  T dq = Arn * P.idt + T(0.5) * (Ar - Arn) * P.idt +
-         T(0.5) * ih * (-R.S[ke + R.s] + R.S[ke] - R.Q[ke] * gp + R.Q[ke - R.t] * gm) + R.Dv[ke] +
-         P.iRe * ih2 * ((vis[ke + R.s] + vis[ke]) * (T(1) + third) + gp * L.Av[ke] +
-                        gm * L.Av[ke - R.t]);
+  T dq = R.Dg[ke] + T(0.5) * P.idt * Ar;
   T bq = T(0);
   if (mine) bq = mom_residual(P, L, R, ke, Ar);
   T A[5][5], b[5];
@@ -1260,7 +1334,7 @@ __device__ __forceinline__ void vanka_team(const Prm<T>& P, const Lv<T>& L, int 
     A[4][4] = T(0.5) * P.alpha * P.alpha * P.iPe * sm * ih2;
   }
   b[4] = op_p(P, L, k) - L.fp[k];
-  const bool act[4] = {a0, a1, a2, a3};
+  const bool act[5] = {a0, a1, a2, a3, true};
 #pragma unroll
   for (int r = 0; r < 4; ++r)
     if (!act[r]) {
@@ -1271,7 +1345,7 @@ __device__ __forceinline__ void vanka_team(const Prm<T>& P, const Lv<T>& L, int 
       }
       A[r][r] = T(1);
     }
-  solve5(A, b);
+  solve_vanka<T, 5>(A, b, act, v3, ih * P.iM, ih);
   if (!ok) return;
   T x = q == 0 ? b[0] : q == 1 ? b[1] : q == 2 ? b[2] : b[3];
   if (mine) {
@@ -1281,6 +1355,21 @@ __device__ __forceinline__ void vanka_team(const Prm<T>& P, const Lv<T>& L, int 
     else store_v(L, i, j, L.v[k] - omega * x);
   }
   if (q == 0) store_cell(L, L.p, i, j, L.p[k] - omega * b[4]);
+}
+
+// Per-level launch with four lanes per Vanka block (vanka_team): a level whose
+// colour leaves most SM sub-partitions idle runs each block's critical path
+// split over four lanes.  Whole warps past the last team return together, so
+// every warp that calls vanka_team has all 32 lanes in it.
+template <typename T>
+__global__ void __launch_bounds__(SNT) k_vanka_team(Prm<T> P, Lv<T> L, int colour, T omega) {
+  ColourSlots cs = vanka_slots(L, colour);
+  int t = blockIdx.x * SNT + threadIdx.x;
+  if ((t & ~31) >= 4 * cs.n) return;  // warp-uniform
+  int i = 1, j = 1;
+  bool ok = (t >> 2) < cs.n && vanka_slot_cell(L, colour, cs, t >> 2, i, j);
+  if (!ok) i = j = 1;
+  vanka_team<T>(P, L, i, j, ok, omega);
 }
 
 // teams of four lanes while the colour fits in four warps (one per sub-partition)
@@ -1740,9 +1829,17 @@ void launch_ch(const Prm<T>& P, const Lv<T>& L, int colour, cudaStream_t s) {
   ++g_launches;
 }
 template <typename T, class Form>
-void launch_vanka(const Prm<T>& P, const Lv<T>& L, int colour, T omega, cudaStream_t s) {
+void launch_vanka(const Prm<T>& P, const Lv<T>& L, int colour, T omega, cudaStream_t s,
+                  int team_max) {
   int n = vanka_slots(L, colour).n;
   if (n <= 0) return;
+  if constexpr (std::is_same<Form, FullForm>::value && sizeof(T) == 8) {
+    if (n <= team_max) {  // four lanes per block: shorter critical path per visit
+      k_vanka_team<T><<<(4 * n + SNT - 1) / SNT, SNT, 0, s>>>(P, L, colour, omega);
+      ++g_launches;
+      return;
+    }
+  }
   k_vanka<T, Form><<<(n + SNT - 1) / SNT, SNT, 0, s>>>(P, L, colour, omega);
   ++g_launches;
 }
@@ -1838,6 +1935,10 @@ void launch_frozen(const Prm<T>& P, const Lv<T>& L, cudaStream_t s) {
   k_frozen_coef1<T><<<grid2(L.m1 + 2, L.m2 + 2), dim3(BX, BY), 0, s>>>(L);
   ++g_launches;
   k_frozen_coef2<T><<<grid2(L.m1 + 1, L.m2 + 1), dim3(BX, BY), 0, s>>>(L);
+  if (L.T1u) {  // FP64 full-iterate levels
+    k_frozen_coef3<T><<<grid2(L.m1 + 1, L.m2 + 1), dim3(BX, BY), 0, s>>>(P, L);
+    ++g_launches;
+  }
   ++g_launches;
 }
 template <typename T>
@@ -1943,7 +2044,7 @@ int partial_rows_needed(int m1, int m2) {
   template void launch_residual<T, F>(const Prm<T>&, const Lv<T>&, double*, cudaStream_t);       \
   template void launch_add_op<T, F>(const Prm<T>&, const Lv<T>&, cudaStream_t);                  \
   template void launch_ch<T, F>(const Prm<T>&, const Lv<T>&, int, cudaStream_t);                 \
-  template void launch_vanka<T, F>(const Prm<T>&, const Lv<T>&, int, T, cudaStream_t);
+  template void launch_vanka<T, F>(const Prm<T>&, const Lv<T>&, int, T, cudaStream_t, int);
 
 #define QN_INSTANTIATE(T)                                                                        \
   template void launch_cast_frozen<T>(const Lv<double>&, const Lv<T>&, cudaStream_t);            \

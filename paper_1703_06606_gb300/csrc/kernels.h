@@ -14,8 +14,11 @@ namespace qn {
 template <typename T, class Form> void launch_residual(const Prm<T>& P, const Lv<T>& L, double* part, cudaStream_t s);
 template <typename T, class Form> void launch_add_op(const Prm<T>& P, const Lv<T>& L, cudaStream_t s);
 template <typename T, class Form> void launch_ch(const Prm<T>& P, const Lv<T>& L, int colour, cudaStream_t s);
+// team_max: FP64 full-iterate levels with at most this many cells per colour
+// use four lanes per Vanka block
 template <typename T, class Form>
-void launch_vanka(const Prm<T>& P, const Lv<T>& L, int colour, T omega, cudaStream_t s);
+void launch_vanka(const Prm<T>& P, const Lv<T>& L, int colour, T omega, cudaStream_t s,
+                  int team_max = 0);
 // the V-cycle on levels[0..n-1] (levels[0] is its finest) in one thread block
 template <typename T, class Form>
 void launch_coarse_vcycle(const Prm<T>& P, const Lv<T>* levels, int n, int nu1, int nu2, int nuc,

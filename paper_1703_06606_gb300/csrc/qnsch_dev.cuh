@@ -47,6 +47,12 @@ struct Lv {
   // the divergence corrections 1/2[D_x(rho a_x u) + Dfrak_y(..)] (x-edges)
   // and 1/2[Dfrak_x(..) + D_y(rho a_y v)] (y-edges) of (e1e1-2)
   T *Aru, *Arv, *Sx, *Sy, *Qx, *Qy, *Av, *Tx, *Ty, *Dvu, *Dvv;
+  // FP64 full-iterate levels only, built per step (they depend on dt): for each
+  // momentum row (x-edges *u, y-edges *v) the time-term coefficients, time =
+  // x T1 + T0 + (dt^-1/2) A rho(c) x with T1 = A rho^n/(2dt) + Dv and T0 =
+  // -A rho^n x^n/dt, and Dg, the part of the row's diagonal entry that does not
+  // depend on the iterate (the whole diagonal is Dg + A rho(c)/(2dt))
+  T *T1u = nullptr, *T1v = nullptr, *T0u = nullptr, *T0v = nullptr, *Dgu = nullptr, *Dgv = nullptr;
   // error-equation (defect-correction) levels only: base state X the iterate
   // e is a correction to, and X.c - c^n formed in FP64 before rounding
   T *Bc = nullptr, *Bmu = nullptr, *Bu = nullptr, *Bv = nullptr, *Bdc = nullptr;
@@ -185,9 +191,8 @@ __device__ __forceinline__ T op_u(const Prm<T>& P, const Lv<T>& L, int k, T Ar) 
   T dvl = dxl + (L.v[k] - L.v[k - W]) * L.ih;
   T dvr = dxr + (L.v[k + 1] - L.v[k + 1 - W]) * L.ih;
   T Dt = (u[k + W] - ue) * L.ih, Db = (ue - u[k - W]) * L.ih;
-  T Arn = L.Aru[k];
   T conv = T(0.5) * (L.Sx[k + 1] * dxr + L.Sx[k] * dxl + L.Qx[k] * Dt + L.Qx[k - W] * Db);
-  T time = Arn * (ue - L.un[k]) * P.idt + T(0.5) * (Ar - Arn) * P.idt * ue + L.Dvu[k] * ue;
+  T time = ue * L.T1u[k] + L.T0u[k] + T(0.5) * P.idt * Ar * ue;
   T r = time + conv;
   if constexpr (PST) {
     T press = (L.p[k + 1] - L.p[k]) * L.ih * P.iM;
@@ -217,9 +222,8 @@ __device__ __forceinline__ T op_v(const Prm<T>& P, const Lv<T>& L, int k, T Ar) 
   T dvb = dyb + (L.u[k] - L.u[k - 1]) * L.ih;
   T dvt = dyt + (L.u[k + W] - L.u[k + W - 1]) * L.ih;
   T De = (v[k + 1] - ve) * L.ih, Dw = (ve - v[k - 1]) * L.ih;
-  T Arn = L.Arv[k];
   T conv = T(0.5) * (L.Qy[k] * De + L.Qy[k - 1] * Dw + L.Sy[k + W] * dyt + L.Sy[k] * dyb);
-  T time = Arn * (ve - L.vn[k]) * P.idt + T(0.5) * (Ar - Arn) * P.idt * ve + L.Dvv[k] * ve;
+  T time = ve * L.T1v[k] + L.T0v[k] + T(0.5) * P.idt * Ar * ve;
   T r = time + conv;
   if constexpr (PST) {
     T press = (L.p[k + W] - L.p[k]) * L.ih * P.iM;
@@ -229,7 +233,7 @@ __device__ __forceinline__ T op_v(const Prm<T>& P, const Lv<T>& L, int k, T Ar) 
   T vb = vis[k], vt = vis[k + W];
   T visc = -P.iRe * L.ih * ((L.Av[k] * De - L.Av[k - 1] * Dw) + (vt * dyt - vb * dyb) +
                             (vt * dvt - vb * dvb) * T(1.0 / 3.0));
-  if constexpr (PST) return r + visc + P.Fr_inv * Arn;
+  if constexpr (PST) return r + visc + P.Fr_inv * L.Arv[k];
   return r + visc;
 }
 template <typename T>

@@ -49,7 +49,7 @@ void dev_free(void* p) {
   else cudaFree(p);
 }
 
-constexpr int NFIELD = 38;  // arrays per level (see Lv)
+constexpr int NFIELD = 44;  // arrays per level (see Lv)
 
 // surface-tension ratio eta(rho1, rho2) of Sec. 8.1; near rho1 = rho2 the
 // formula is 0/0 and the Taylor series of x^2 - 1 - 2x ln x in q = x - 1 is used
@@ -110,6 +110,9 @@ struct qnsch_s {
   int coupled = 0;
   // 0: the primitive method (Sec. 6.1); 1: the projection method (Sec. 6.2)
   int scheme = 0;
+  // FP64 levels with at most this many cells per Vanka colour smooth with four
+  // lanes per block in the per-level launches
+  int team_max = 8192;
   // grid
   int m1, m2, px, nlev, kcol;
   double h;
@@ -239,7 +242,8 @@ int alloc_all(qnsch_s* s) {
                           &L.fu, &L.fv,  &L.rc,   &L.rmu,  &L.rp,   &L.ru, &L.rv,  &L.sc,
                           &L.smu, &L.sp, &L.su,   &L.sv,   &L.cn,   &L.un, &L.vn,  &L.rhon,
                           &L.mobn, &L.visn, &L.Gn, &L.Aru, &L.Arv,  &L.Sx, &L.Sy,  &L.Qx,
-                          &L.Qy, &L.Av,  &L.Tx,   &L.Ty,   &L.Dvu,  &L.Dvv};
+                          &L.Qy, &L.Av,  &L.Tx,   &L.Ty,   &L.Dvu,  &L.Dvv, &L.T1u, &L.T1v,
+                          &L.T0u, &L.T0v, &L.Dgu, &L.Dgv};
     for (int q = 0; q < NFIELD; ++q) *f[q] = base + (size_t)q * n + pitch + 1;  // origin (0,0)
     a /= 2;
     b /= 2;
@@ -274,7 +278,10 @@ int alloc_all(qnsch_s* s) {
   return sync(s);
 }
 
-constexpr int NFIELD_ERR = NFIELD + 5;  // + base Bc, Bmu, Bu, Bv, Bdc
+// error-equation levels: the 38 arrays of a level without the per-step row
+// coefficients (their operators do not use them), plus the base Bc, Bmu, Bu,
+// Bv, Bdc
+constexpr int NFIELD_ERR = NFIELD - 6 + 5;
 
 template <typename T>
 int alloc_err_levels(qnsch_s* s, std::vector<Lv<T>>& E) {
@@ -374,7 +381,7 @@ void smooth(qnsch_s* s, const std::vector<Lv<T>>& Ls, const Prm<T>& P, int l) {
     }
     if (rec) cudaEventRecord(s->ev[s->ev_used], s->stream);
     if (s->coupled) qn::launch_coupled<T, Form>(P, L, c, (T)s->omega, s->stream);
-    else qn::launch_vanka<T, Form>(P, L, c, (T)s->omega, s->stream);
+    else qn::launch_vanka<T, Form>(P, L, c, (T)s->omega, s->stream, s->team_max);
     if (rec) {
       cudaEventRecord(s->ev[s->ev_used + 1], s->stream);
       s->ev_used += 2;
@@ -840,6 +847,7 @@ int qnsch_set_option(qnsch_t* s, const char* key, double value) {
     if (value != 0.0 && s->scheme) return QNSCH_EINVAL;  // a primitive-method smoother
     s->coupled = value != 0.0;
   } else if (k == "fuse_cells32") s->fuse32 = (int)value;
+  else if (k == "vanka_team_max") s->team_max = (int)value;
   else if (k == "precision") {
     int p = (int)value;
     if (p < 0 || p > 2 || (double)p != value) return QNSCH_EINVAL;
@@ -873,6 +881,7 @@ int qnsch_get_option(const qnsch_t* s, const char* key, double* value) {
   else if (k == "coupled") *value = s->coupled;
   else if (k == "fuse_cells32") *value = s->fuse32;
   else if (k == "scheme") *value = s->scheme;
+  else if (k == "vanka_team_max") *value = s->team_max;
   else return QNSCH_EINVAL;
   return QNSCH_OK;
 }
@@ -1150,7 +1159,8 @@ int qnsch_smooth_vanka(qnsch_t* s, int colour) {
   if (!s || colour < 0 || colour >= s->kcol) return QNSCH_EINVAL;
   if (!s->pending) return QNSCH_ESTATE;
   if (s->scheme) qn::launch_vanka4<double, ProjForm>(make_prm(s), s->L[0], colour, s->omega, s->stream);
-  else qn::launch_vanka<double, FullForm>(make_prm(s), s->L[0], colour, s->omega, s->stream);
+  else qn::launch_vanka<double, FullForm>(make_prm(s), s->L[0], colour, s->omega, s->stream,
+                                          s->team_max);
   return sync(s);
 }
 
