@@ -252,6 +252,89 @@ __global__ void __launch_bounds__(64) k_ch(Prm<T> P, Lv<T> L, int colour) {
   ch_cell<T, Form>(P, L, i, j);
 }
 
+// CH step of cell (i,j) by a team of four lanes (lane & 3 = face f: E, W, N, S).
+// Each lane evaluates its face's terms of N_c, N_mu and of the 2x2 Jacobian,
+// with rho(c) of its neighbour; two butterfly shuffles add the face terms;
+// every lane then forms N_c, N_mu, J and solves; lane 0 stores.  All 32 lanes
+// of the warp call this (ok = false: a spare team on cell (1,1), no store).
+template <typename T>
+__device__ __forceinline__ void ch_team(const Prm<T>& P, const Lv<T>& L, int i, int j, bool ok) {
+  const unsigned FULL = 0xffffffffu;
+  const int W = L.pitch;
+  const int f = threadIdx.x & 3;
+  int k = L.at(i, j);
+  const int off = f == 0 ? 1 : f == 1 ? -1 : f == 2 ? W : -W;
+  const bool wall = f == 0 ? (!L.px && i == L.m1) : f == 1 ? (!L.px && i == 1) : f == 2 ? (j == L.m2) : (j == 1);
+  const int q = k + off;
+  const int kv = f == 1 ? k - 1 : f == 3 ? k - W : k;  // edge of face f
+  const T *c = L.c, *cn = L.cn, *rn = L.rhon, *mob = L.mobn;
+  T ck = c[k], cnk = cn[k], mk = L.mu[k], rnk = rn[k];
+  T rho = rho_of(P, ck);
+  T cq = c[q];
+  T rq = rho_of(P, cq);
+  T drho = -P.alpha * rho * rho;
+  T rh = T(0.5) * (rho + rnk);
+  T chk = ck + cnk;
+  T d = cq - ck;
+  T am = T(0.5) * (mob[q] + mob[k]);
+  T rqh = T(0.5) * (rq + rn[q]);
+  T cqh = (cq + cn[q]) - chk;
+  T v[8];
+  v[0] = rn[q] * (f < 2 ? L.Tx[kv] : L.Ty[kv]) * (f < 2 ? L.u[kv] : L.v[kv]);  // advection
+  v[1] = am * (L.mu[q] - mk);                                                   // h^2 lap mu
+  v[2] = am * (L.p[q] - L.p[k]);                                                // h^2 lap p
+  v[3] = (rh + rqh) * cqh;                                                      // div term
+  v[4] = d * d;                                                                 // 2 h^2 G(c)
+  v[5] = wall ? T(0) : mob[k] + mob[q];                                         // 2 sum A m
+  v[6] = wall ? T(0) : -d;                                                      // h^2 dG/dc
+  v[7] = wall ? T(0) : T(0.5) * drho * cqh - (rh + rqh);                        // dd
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    v[a] += __shfl_xor_sync(FULL, v[a], 1);
+    v[a] += __shfl_xor_sync(FULL, v[a], 2);
+  }
+  T r = -P.alpha * rho * rnk, dr = -P.alpha * drho * rnk;
+  T Nc = rho * (ck - cnk) * P.idt + v[0] - P.iPe * L.ih2 * (v[1] + P.alpha * v[2]);
+  T bulk = rh * gsec(ck, cnk) + T(0.5) * (Fdw(ck) + Fdw(cnk)) * r;
+  T Gs = T(0.5) * v[4] * L.ih2 + L.Gn[k];
+  T grad = T(0.25) * P.Lam * Gs * r;
+  T Nm = rho * mk - P.K * bulk - grad + P.Lam * T(0.25) * L.ih2 * v[3];
+  T Rc = Nc - L.fc[k], Rm = Nm - L.fmu[k];
+  T J11 = (rho + drho * (ck - cnk)) * P.idt;
+  T J12 = T(0.5) * v[5] * P.iPe * L.ih2;
+  T dbulk = T(0.5) * drho * gsec(ck, cnk) + rh * gsec_da(ck, cnk) + T(0.5) * fdw(ck) * r +
+            T(0.5) * (Fdw(ck) + Fdw(cnk)) * dr;
+  T dgrad = T(0.25) * P.Lam * (v[6] * L.ih2 * r + Gs * dr);
+  T J21 = drho * mk - P.K * dbulk - dgrad + P.Lam * T(0.25) * L.ih2 * v[7];
+  T J22 = rho;
+  T idet = T(1) / (J11 * J22 - J12 * J21);
+  T dc = (J22 * Rc - J12 * Rm) * idet;
+  T dm = (J11 * Rm - J21 * Rc) * idet;
+  if (ok && f == 0) {
+    store_cell(L, L.c, i, j, ck - dc);
+    store_cell(L, L.mu, i, j, mk - dm);
+  }
+}
+
+// per-level CH launch with four lanes per cell (colour (i + j) % 2, packed)
+template <typename T>
+__global__ void __launch_bounds__(64) k_ch_team(Prm<T> P, Lv<T> L, int colour) {
+  int mpr = (L.m1 + 1) / 2;
+  int n = mpr * L.m2;
+  int t = blockIdx.x * 64 + threadIdx.x;
+  if ((t & ~31) >= 4 * n) return;  // warp-uniform
+  int s = t >> 2;
+  int j = 1, i = 1;
+  bool ok = false;
+  if (s < n) {
+    j = s / mpr + 1;
+    i = (((colour - j) & 1) ? 1 : 2) + 2 * (s % mpr);
+    ok = i <= L.m1;
+  }
+  if (!ok) i = j = 1;
+  ch_team<T>(P, L, i, j, ok);
+}
+
 // --------------------------------------------------------------------------
 // Vanka step 2 of Sec. 7.1: exact solve of the 5x5 block of cell (i,j):
 // unknowns (u_W, u_E, v_S, v_N, p), equations (N_u W, N_u E, N_v S, N_v N, N_p).
@@ -1420,15 +1503,30 @@ __device__ void smooth_block(const Prm<T>& P, const Lv<T>& L, T omega, int coupl
     return;
   }
   const int mpr = (L.m1 + 1) / 2;
+  constexpr bool team_ok = std::is_same<Form, FullForm>::value && sizeof(T) == 8;
   for (int col = 0; col < 2; ++col) {
-    for (int t = threadIdx.x; t < mpr * L.m2; t += blockDim.x) {
-      int j = t / mpr + 1;
-      int i = (((col - j) & 1) ? 1 : 2) + 2 * (t % mpr);
-      if (i <= L.m1) ch_cell<T, Form>(P, L, i, j);
+    if (team_ok && 4 * mpr * L.m2 <= (int)blockDim.x) {
+      int t = threadIdx.x;
+      if ((t & ~31) < 4 * mpr * L.m2) {  // warp-uniform
+        int sl = t >> 2, j = 1, i = 1;
+        bool ok = false;
+        if (sl < mpr * L.m2) {
+          j = sl / mpr + 1;
+          i = (((col - j) & 1) ? 1 : 2) + 2 * (sl % mpr);
+          ok = i <= L.m1;
+        }
+        if (!ok) i = j = 1;
+        ch_team<T>(P, L, i, j, ok);
+      }
+    } else {
+      for (int t = threadIdx.x; t < mpr * L.m2; t += blockDim.x) {
+        int j = t / mpr + 1;
+        int i = (((col - j) & 1) ? 1 : 2) + 2 * (t % mpr);
+        if (i <= L.m1) ch_cell<T, Form>(P, L, i, j);
+      }
     }
     __syncthreads();
   }
-  constexpr bool team_ok = std::is_same<Form, FullForm>::value && sizeof(T) == 8;
   for (int col = 0; col < kcol; ++col) {
     ColourSlots cs = vanka_slots(L, col);
     if (team_ok && cs.n <= QN_TEAM_MAX_SLOTS) {
@@ -1822,9 +1920,16 @@ void launch_add_op(const Prm<T>& P, const Lv<T>& L, cudaStream_t s) {
   ++g_launches;
 }
 template <typename T, class Form>
-void launch_ch(const Prm<T>& P, const Lv<T>& L, int colour, cudaStream_t s) {
+void launch_ch(const Prm<T>& P, const Lv<T>& L, int colour, cudaStream_t s, int team_max) {
   int n = (L.m1 + 1) / 2 * L.m2;
   if (n <= 0) return;
+  if constexpr (std::is_same<Form, FullForm>::value && sizeof(T) == 8) {
+    if (n <= team_max) {  // four lanes per cell: shorter critical path per visit
+      k_ch_team<T><<<(4 * n + 63) / 64, 64, 0, s>>>(P, L, colour);
+      ++g_launches;
+      return;
+    }
+  }
   k_ch<T, Form><<<(n + 63) / 64, 64, 0, s>>>(P, L, colour);
   ++g_launches;
 }
@@ -2043,7 +2148,7 @@ int partial_rows_needed(int m1, int m2) {
   template void launch_coupled<T, F>(const Prm<T>&, const Lv<T>&, int, T, cudaStream_t);          \
   template void launch_residual<T, F>(const Prm<T>&, const Lv<T>&, double*, cudaStream_t);       \
   template void launch_add_op<T, F>(const Prm<T>&, const Lv<T>&, cudaStream_t);                  \
-  template void launch_ch<T, F>(const Prm<T>&, const Lv<T>&, int, cudaStream_t);                 \
+  template void launch_ch<T, F>(const Prm<T>&, const Lv<T>&, int, cudaStream_t, int);            \
   template void launch_vanka<T, F>(const Prm<T>&, const Lv<T>&, int, T, cudaStream_t, int);
 
 #define QN_INSTANTIATE(T)                                                                        \
@@ -2079,7 +2184,8 @@ template void launch_residual<double, ProjForm>(const Prm<double>&, const Lv<dou
 template void launch_coarse_vcycle<double, ProjForm>(const Prm<double>&, const Lv<double>*, int, int,
                                                      int, int, int, double, int, cudaStream_t);
 template void launch_add_op<double, ProjForm>(const Prm<double>&, const Lv<double>&, cudaStream_t);
-template void launch_ch<double, ProjForm>(const Prm<double>&, const Lv<double>&, int, cudaStream_t);
+template void launch_ch<double, ProjForm>(const Prm<double>&, const Lv<double>&, int, cudaStream_t,
+                                          int);
 template void launch_vanka4<double, ProjForm>(const Prm<double>&, const Lv<double>&, int, double,
                                               cudaStream_t);
 template void launch_pgs<double>(const Prm<double>&, const Lv<double>&, int, cudaStream_t);

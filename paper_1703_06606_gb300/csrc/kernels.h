@@ -13,7 +13,10 @@ namespace qn {
 // a base X; the operator is N(X + e) - N(X))
 template <typename T, class Form> void launch_residual(const Prm<T>& P, const Lv<T>& L, double* part, cudaStream_t s);
 template <typename T, class Form> void launch_add_op(const Prm<T>& P, const Lv<T>& L, cudaStream_t s);
-template <typename T, class Form> void launch_ch(const Prm<T>& P, const Lv<T>& L, int colour, cudaStream_t s);
+// team_max: FP64 full-iterate levels with at most this many cells per colour
+// use four lanes per cell
+template <typename T, class Form>
+void launch_ch(const Prm<T>& P, const Lv<T>& L, int colour, cudaStream_t s, int team_max = 0);
 // team_max: FP64 full-iterate levels with at most this many cells per colour
 // use four lanes per Vanka block
 template <typename T, class Form>

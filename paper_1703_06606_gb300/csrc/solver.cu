@@ -105,7 +105,7 @@ struct qnsch_s {
   int precision = 0;
   // levels with at most this many cells run as one fused single-block V-cycle
   // (0: never); separate thresholds for FP64 and FP32 levels
-  int fuse64 = 512, fuse32 = 2048;
+  int fuse64 = 128, fuse32 = 2048;
   // 0: the paper's separate CH and Vanka sweeps; 1: the coupled 7x7 block
   int coupled = 0;
   // 0: the primitive method (Sec. 6.1); 1: the projection method (Sec. 6.2)
@@ -113,6 +113,8 @@ struct qnsch_s {
   // FP64 levels with at most this many cells per Vanka colour smooth with four
   // lanes per block in the per-level launches
   int team_max = 8192;
+  // the same for the CH smoother's per-level launches (cells per red-black colour)
+  int ch_team_max = 4096;
   // grid
   int m1, m2, px, nlev, kcol;
   double h;
@@ -344,8 +346,8 @@ void smooth(qnsch_s* s, const std::vector<Lv<T>>& Ls, const Prm<T>& P, int l) {
   if constexpr (std::is_same<Form, ProjForm>::value) {
     // projection method (Sec. 7.2): CH red-black, the intermediate-velocity
     // blocks over the Vanka colours, pressure Gauss-Seidel red-black
-    qn::launch_ch<T, Form>(P, L, 0, s->stream);
-    qn::launch_ch<T, Form>(P, L, 1, s->stream);
+    qn::launch_ch<T, Form>(P, L, 0, s->stream, s->ch_team_max);
+    qn::launch_ch<T, Form>(P, L, 1, s->stream, s->ch_team_max);
     for (int c = 0; c < L.kcol; ++c) {
       bool rec = s->prof && l == 0 && s->ev_used + 2 <= MAX_PROF_EVENTS;
       if (rec) {
@@ -367,8 +369,8 @@ void smooth(qnsch_s* s, const std::vector<Lv<T>>& Ls, const Prm<T>& P, int l) {
     return;
   }
   if (!s->coupled) {
-    qn::launch_ch<T, Form>(P, L, 0, s->stream);
-    qn::launch_ch<T, Form>(P, L, 1, s->stream);
+    qn::launch_ch<T, Form>(P, L, 0, s->stream, s->ch_team_max);
+    qn::launch_ch<T, Form>(P, L, 1, s->stream, s->ch_team_max);
   }
   for (int c = 0; c < L.kcol; ++c) {
     bool rec = s->prof && l == 0 && s->ev_used + 2 <= MAX_PROF_EVENTS;
@@ -848,6 +850,7 @@ int qnsch_set_option(qnsch_t* s, const char* key, double value) {
     s->coupled = value != 0.0;
   } else if (k == "fuse_cells32") s->fuse32 = (int)value;
   else if (k == "vanka_team_max") s->team_max = (int)value;
+  else if (k == "ch_team_max") s->ch_team_max = (int)value;
   else if (k == "precision") {
     int p = (int)value;
     if (p < 0 || p > 2 || (double)p != value) return QNSCH_EINVAL;
@@ -882,6 +885,7 @@ int qnsch_get_option(const qnsch_t* s, const char* key, double* value) {
   else if (k == "fuse_cells32") *value = s->fuse32;
   else if (k == "scheme") *value = s->scheme;
   else if (k == "vanka_team_max") *value = s->team_max;
+  else if (k == "ch_team_max") *value = s->ch_team_max;
   else return QNSCH_EINVAL;
   return QNSCH_OK;
 }
@@ -1150,7 +1154,7 @@ int qnsch_smooth_ch(qnsch_t* s, int colour) {
   if (!s || colour < 0 || colour > 1) return QNSCH_EINVAL;
   if (!s->pending) return QNSCH_ESTATE;
   if (s->scheme) qn::launch_ch<double, ProjForm>(make_prm(s), s->L[0], colour, s->stream);
-  else qn::launch_ch<double, FullForm>(make_prm(s), s->L[0], colour, s->stream);
+  else qn::launch_ch<double, FullForm>(make_prm(s), s->L[0], colour, s->stream, s->ch_team_max);
   return sync(s);
 }
 

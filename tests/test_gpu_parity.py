@@ -393,14 +393,14 @@ def test_rayleigh_taylor_full_size_step(qn, precision):
 
 @pytest.mark.parametrize("px", [False, True])
 def test_team_vanka_launches_match_single_lane(qn, px):
-    """Per-level Vanka launches with four lanes per block (vanka_team_max) do the
-    same arithmetic as one lane per block, with the terms of the momentum rows
+    """Per-level Vanka and CH launches with four lanes per block (vanka_team_max,
+    ch_team_max) do the same arithmetic as one lane per block, with some terms
     summed in another order: after two V-cycles the iterates agree within the
     1e-10 parity bar (measured 2e-12)."""
     P = W.small_case(128, 192, px)
     out = []
     for tm in (0, 10 ** 9):
-        g = qn.Solver(**P.create_kwargs(), vanka_team_max=tm)
+        g = qn.Solver(**P.create_kwargs(), vanka_team_max=tm, ch_team_max=tm)
         g.set_fields(P.fields())
         g.begin_step(P.dt)
         for _ in range(2):
