@@ -453,11 +453,14 @@ def run_ours(args, rank, world, local_rank):
 
 # algorithmic FP64 operations per Vanka cell visit (add/sub/mul/div = 1, fused
 # multiply-add = 2), counted from the formulas of one 5x5 Vanka block (Sec. 7.1)
-VANKA_FP64_FLOPS_PER_VISIT = 557.0
+# as the kernel evaluates it: 5 densities, 4 edge averages, 4 diagonals from the
+# per-step row coefficients, off-diagonals and the mass row, 4 momentum and 1
+# mass residual, the structured block solve, 5 updates
+VANKA_FP64_FLOPS_PER_VISIT = 406.0
 # dram__bytes_read.sum + dram__bytes_write.sum of one finest-level k_vanka<double> launch at
 # 256x512 from one ncu capture of the current kernel; None once the kernel changes after
 # the capture
-VANKA_FP64_TRAFFIC_BYTES = 26.466e6
+VANKA_FP64_TRAFFIC_BYTES = 27.537e6
 # measured FP64 FMA throughput of one GB300 (dependent-chain-free DFMA loop)
 FP64_PEAK_TFLOPS = 1.193
 
