@@ -95,8 +95,8 @@ __device__ __forceinline__ void residual_cell(const Prm<T>& P, const Lv<T>& L, i
     nc = op_c(P, L, k, rk);
     nm = op_mu(P, L, k, rk, rq);
     np = op_p(P, L, k);
-    nu = hu ? op_u(P, L, k, T(0.5) * (rk + rq[0])) : T(0);
-    nv = hv ? op_v(P, L, k, T(0.5) * (rk + rq[2])) : T(0);
+    nu = op_u(P, L, k, T(0.5) * (rk + rq[0]));  // also on boundary edges (padded arrays); masked below
+    nv = op_v(P, L, k, T(0.5) * (rk + rq[2]));  // also on boundary edges (padded arrays); masked below
   } else if constexpr (std::is_same<Form, ProjForm>::value) {
     const int W = L.pitch;
     T rk = rho_of(P, L.c[k]);
@@ -107,14 +107,14 @@ __device__ __forceinline__ void residual_cell(const Prm<T>& P, const Lv<T>& L, i
     nc = opp_c_w(P, L, k, rq, w);
     nm = op_mu_r(P, L, k, rk, rq, L.rhon[k]);
     np = opp_p_w(P, L, k, w);
-    nu = hu ? op_u<T, false>(P, L, k, T(0.5) * (rk + rq[0])) : T(0);
-    nv = hv ? op_v<T, false>(P, L, k, T(0.5) * (rk + rq[2])) : T(0);
+    nu = op_u<T, false>(P, L, k, T(0.5) * (rk + rq[0]));  // also on boundary edges (padded arrays); masked below
+    nv = op_v<T, false>(P, L, k, T(0.5) * (rk + rq[2]));  // also on boundary edges (padded arrays); masked below
   } else {
     nc = Form::Nc(P, L, k);
     nm = Form::Nmu(P, L, k);
     np = Form::Np(P, L, k);
-    nu = hu ? Form::Nu(P, L, k) : T(0);
-    nv = hv ? Form::Nv(P, L, k) : T(0);
+    nu = Form::Nu(P, L, k);  // also on boundary edges (padded arrays); masked below
+    nv = Form::Nv(P, L, k);  // also on boundary edges (padded arrays); masked below
   }
   if (MODE == 0) {
     T r[5] = {L.fc[k] - nc, L.fmu[k] - nm, L.fp[k] - np, hu ? L.fu[k] - nu : T(0),
@@ -340,46 +340,6 @@ __global__ void __launch_bounds__(64) k_ch_team(Prm<T> P, Lv<T> L, int colour) {
 // unknowns (u_W, u_E, v_S, v_N, p), equations (N_u W, N_u E, N_v S, N_v N, N_p).
 // Colours: (i + 2j) % 5 (walls in x) or (2i + j) % 8 (periodic x).
 // --------------------------------------------------------------------------
-// Gaussian elimination with partial pivoting on a 5x5 system held in registers.
-// Pivoting by compare-and-swap with compile-time row indices: after the inner
-// loop row k holds the largest |A[r][k]| of rows k..4 (the argmax row).
-template <typename T>
-__device__ __forceinline__ void solve5(T (&A)[5][5], T (&b)[5]) {
-#pragma unroll
-  for (int k = 0; k < 5; ++k) {
-#pragma unroll
-    for (int r = k + 1; r < 5; ++r) {
-      if (fabs(A[r][k]) > fabs(A[k][k])) {
-#pragma unroll
-        for (int c = k; c < 5; ++c) {
-          T t = A[k][c];
-          A[k][c] = A[r][c];
-          A[r][c] = t;
-        }
-        T t = b[k];
-        b[k] = b[r];
-        b[r] = t;
-      }
-    }
-    T inv = T(1) / A[k][k];
-#pragma unroll
-    for (int r = k + 1; r < 5; ++r) {
-      T l = A[r][k] * inv;
-#pragma unroll
-      for (int c = k + 1; c < 5; ++c) A[r][c] -= l * A[k][c];
-      b[r] -= l * b[k];
-    }
-    A[k][k] = inv;
-  }
-#pragma unroll
-  for (int k = 4; k >= 0; --k) {
-    T s = b[k];
-#pragma unroll
-    for (int c = k + 1; c < 5; ++c) s -= A[k][c] * b[c];
-    b[k] = s * A[k][k];
-  }
-}
-
 // The 5x5 Vanka system of cell (i,j): A = Jacobian of (N_u W, N_u E, N_v S,
 // N_v N, N_p) in (u_W, u_E, v_S, v_N, p), b = residuals N - f; rows and
 // columns of wall edges (act = false) replaced by the identity
@@ -485,20 +445,56 @@ __device__ __forceinline__ void vanka_system(const Prm<T>& P, const Lv<T>& L, in
     A[4][4] = T(0.5) * P.alpha * P.alpha * P.iPe * sm * ih2;
   }
   if constexpr (std::is_same<Form, FullForm>::value) {
-    b[0] = act[0] ? op_u(P, L, kW, Arq[0]) - L.fu[kW] : T(0);
-    b[1] = act[1] ? op_u(P, L, k, Arq[1]) - L.fu[k] : T(0);
-    b[2] = act[2] ? op_v(P, L, k - W, Arq[2]) - L.fv[k - W] : T(0);
-    b[3] = act[3] ? op_v(P, L, k, Arq[3]) - L.fv[k] : T(0);
+    {
+      T nq = op_u(P, L, kW, Arq[0]);  // evaluated on wall edges too (padded arrays), then discarded
+      b[0] = act[0] ? nq - L.fu[kW] : T(0);
+    }
+    {
+      T nq = op_u(P, L, k, Arq[1]);  // evaluated on wall edges too (padded arrays), then discarded
+      b[1] = act[1] ? nq - L.fu[k] : T(0);
+    }
+    {
+      T nq = op_v(P, L, k - W, Arq[2]);  // evaluated on wall edges too (padded arrays), then discarded
+      b[2] = act[2] ? nq - L.fv[k - W] : T(0);
+    }
+    {
+      T nq = op_v(P, L, k, Arq[3]);  // evaluated on wall edges too (padded arrays), then discarded
+      b[3] = act[3] ? nq - L.fv[k] : T(0);
+    }
   } else if constexpr (std::is_same<Form, ProjForm>::value) {
-    b[0] = act[0] ? op_u<T, false>(P, L, kW, Arq[0]) - L.fu[kW] : T(0);
-    b[1] = act[1] ? op_u<T, false>(P, L, k, Arq[1]) - L.fu[k] : T(0);
-    b[2] = act[2] ? op_v<T, false>(P, L, k - W, Arq[2]) - L.fv[k - W] : T(0);
-    b[3] = act[3] ? op_v<T, false>(P, L, k, Arq[3]) - L.fv[k] : T(0);
+    {
+      T nq = op_u<T, false>(P, L, kW, Arq[0]);  // evaluated on wall edges too (padded arrays), then discarded
+      b[0] = act[0] ? nq - L.fu[kW] : T(0);
+    }
+    {
+      T nq = op_u<T, false>(P, L, k, Arq[1]);  // evaluated on wall edges too (padded arrays), then discarded
+      b[1] = act[1] ? nq - L.fu[k] : T(0);
+    }
+    {
+      T nq = op_v<T, false>(P, L, k - W, Arq[2]);  // evaluated on wall edges too (padded arrays), then discarded
+      b[2] = act[2] ? nq - L.fv[k - W] : T(0);
+    }
+    {
+      T nq = op_v<T, false>(P, L, k, Arq[3]);  // evaluated on wall edges too (padded arrays), then discarded
+      b[3] = act[3] ? nq - L.fv[k] : T(0);
+    }
   } else {
-    b[0] = act[0] ? Form::Nu(P, L, kW) - L.fu[kW] : T(0);
-    b[1] = act[1] ? Form::Nu(P, L, k) - L.fu[k] : T(0);
-    b[2] = act[2] ? Form::Nv(P, L, k - W) - L.fv[k - W] : T(0);
-    b[3] = act[3] ? Form::Nv(P, L, k) - L.fv[k] : T(0);
+    {
+      T nq = Form::Nu(P, L, kW);  // evaluated on wall edges too (padded arrays), then discarded
+      b[0] = act[0] ? nq - L.fu[kW] : T(0);
+    }
+    {
+      T nq = Form::Nu(P, L, k);  // evaluated on wall edges too (padded arrays), then discarded
+      b[1] = act[1] ? nq - L.fu[k] : T(0);
+    }
+    {
+      T nq = Form::Nv(P, L, k - W);  // evaluated on wall edges too (padded arrays), then discarded
+      b[2] = act[2] ? nq - L.fv[k - W] : T(0);
+    }
+    {
+      T nq = Form::Nv(P, L, k);  // evaluated on wall edges too (padded arrays), then discarded
+      b[3] = act[3] ? nq - L.fv[k] : T(0);
+    }
   }
   if constexpr (std::is_same<Form, ProjForm>::value) b[4] = T(0);  // the 4x4 block has no p row
   else b[4] = Form::Np(P, L, k) - L.fp[k];
@@ -780,44 +776,6 @@ __global__ void __launch_bounds__(SNT) k_coupled(Prm<T> P, Lv<T> L, int colour, 
 // projection method (Sec. 7.2): the intermediate-velocity block, pressure
 // Gauss-Seidel, the projected velocity and the projection dissipation
 // --------------------------------------------------------------------------
-// Gaussian elimination with partial pivoting (compare-and-swap) on N x N
-template <typename T, int N>
-__device__ __forceinline__ void solve_n(T (&A)[N][N], T (&b)[N]) {
-#pragma unroll
-  for (int k = 0; k < N; ++k) {
-#pragma unroll
-    for (int r = k + 1; r < N; ++r) {
-      if (fabs(A[r][k]) > fabs(A[k][k])) {
-#pragma unroll
-        for (int c = k; c < N; ++c) {
-          T t = A[k][c];
-          A[k][c] = A[r][c];
-          A[r][c] = t;
-        }
-        T t = b[k];
-        b[k] = b[r];
-        b[r] = t;
-      }
-    }
-    T inv = T(1) / A[k][k];
-#pragma unroll
-    for (int r = k + 1; r < N; ++r) {
-      T l = A[r][k] * inv;
-#pragma unroll
-      for (int c = k + 1; c < N; ++c) A[r][c] -= l * A[k][c];
-      b[r] -= l * b[k];
-    }
-    A[k][k] = inv;
-  }
-#pragma unroll
-  for (int k = N - 1; k >= 0; --k) {
-    T t = b[k];
-#pragma unroll
-    for (int c = k + 1; c < N; ++c) t -= A[k][c] * b[c];
-    b[k] = t * A[k][k];
-  }
-}
-
 // step 2: exact solve of the 4x4 block of the intermediate velocities
 // (ut_W, ut_E, vt_S, vt_N) of cell (i,j) in the rows of (pj-num-mx)
 template <typename T, class Form>
@@ -1373,8 +1331,8 @@ __device__ __forceinline__ void vanka_team(const Prm<T>& P, const Lv<T>& L, int 
   T Ar = T(0.5) * (rho_of(P, L.c[ke]) + rho_of(P, L.c[ke + R.s]));
   const T* vis = L.visn;
   T dq = R.Dg[ke] + T(0.5) * P.idt * Ar;
-  T bq = T(0);
-  if (mine) bq = mom_residual(P, L, R, ke, Ar);
+  T bq = mom_residual(P, L, R, ke, Ar);  // wall edges too (padded arrays), then discarded
+  if (!mine) bq = T(0);
   T A[5][5], b[5];
 #pragma unroll
   for (int r = 0; r < 5; ++r)

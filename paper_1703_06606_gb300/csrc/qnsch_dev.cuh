@@ -295,7 +295,11 @@ __device__ __forceinline__ void proj_faces(const Prm<T>& P, const Lv<T>& L, int 
   w[2] = (j == L.m2) ? T(0) : face(k, W, L.v, rk, rq[2], g);
   w[3] = (j == 1) ? T(0) : face(k - W, W, L.v, rq[3], rk, g);
 }
-// opp_c and opp_p from the shared densities and face velocities
+// (pj-num-phase): rho^n (c - c^n)/dt + a_x(rho_ew D_x c u^{n+1}) + a_y(...)
+// - (1/Pe) grad_d.(A m^n grad_D mu) - (alpha/Pe) grad_d.(A m^n grad_D p), with
+// rho = rho(c^{n+1}) and c^{n+1} in the advection; and (pj-num-mass): d_x u^{n+1}
+// + d_y v^{n+1} - (alpha/Pe)(grad.(A m grad mu) + alpha grad.(A m grad p)).
+// Both from the shared densities rq and the face velocities w of proj_faces.
 template <typename T>
 __device__ __forceinline__ T opp_c_w(const Prm<T>& P, const Lv<T>& L, int k, const T (&rq)[4],
                                      const T (&w)[4]) {
@@ -316,32 +320,6 @@ __device__ __forceinline__ T opp_p_w(const Prm<T>& P, const Lv<T>& L, int k, con
   return dv - P.alpha * P.iPe * L.ih2 * diff;
 }
 
-// (pj-num-phase): rho^n (c - c^n)/dt + a_x(rho_ew D_x c u^{n+1}) + a_y(...)
-// - (1/Pe) grad_d.(A m^n grad_D mu) - (alpha/Pe) grad_d.(A m^n grad_D p), with
-// rho = rho(c^{n+1}) and c^{n+1} in the advection
-template <typename T>
-__device__ __forceinline__ T opp_c(const Prm<T>& P, const Lv<T>& L, int i, int j) {
-  const int W = L.pitch;
-  int k = L.at(i, j);
-  const T* c = L.c;
-  T ck = c[k];
-  T t = L.rhon[k] * (ck - L.cn[k]) * P.idt;
-  T ax = T(0.5) * (rho_of(P, c[k + 1]) * (c[k + 1] - ck) * L.ih * proj_u(P, L, i, j) +
-                   rho_of(P, c[k - 1]) * (ck - c[k - 1]) * L.ih * proj_u(P, L, i - 1, j));
-  T ay = T(0.5) * (rho_of(P, c[k + W]) * (c[k + W] - ck) * L.ih * proj_v(P, L, i, j) +
-                   rho_of(P, c[k - W]) * (ck - c[k - W]) * L.ih * proj_v(P, L, i, j - 1));
-  T diff = lap_h2(L.mobn, L.mu, k, W) + P.alpha * lap_h2(L.mobn, L.p, k, W);
-  return t + ax + ay - P.iPe * L.ih2 * diff;
-}
-// (pj-num-mass): d_x u^{n+1} + d_y v^{n+1} - (alpha/Pe)(grad.(A m grad mu) + alpha grad.(A m grad p))
-template <typename T>
-__device__ __forceinline__ T opp_p(const Prm<T>& P, const Lv<T>& L, int i, int j) {
-  const int W = L.pitch;
-  int k = L.at(i, j);
-  T dv = (proj_u(P, L, i, j) - proj_u(P, L, i - 1, j) + proj_v(P, L, i, j) - proj_v(P, L, i, j - 1)) * L.ih;
-  T diff = lap_h2(L.mobn, L.mu, k, W) + P.alpha * lap_h2(L.mobn, L.p, k, W);
-  return dv - P.alpha * P.iPe * L.ih2 * diff;
-}
 // (pj-num-chem): as (pm-num-chem) with rho^n in front of mu
 template <typename T>
 __device__ __forceinline__ T opp_mu(const Prm<T>& P, const Lv<T>& L, int k) {
@@ -548,8 +526,9 @@ struct FullForm {
   template <typename T> static __device__ __forceinline__ T Nv(const Prm<T>& P, const Lv<T>& L, int k) { return op_v(P, L, k); }
 };
 // The projection method on the full iterate (u, v arrays hold the intermediate
-// velocity).  Its N_c and N_p need the cell index (i, j) (wall edges of the
-// projected velocity), so the kernels call opp_c / opp_p directly.
+// velocity).  Its N_c and N_p need the cell's face velocities (proj_faces,
+// which needs the cell index for the wall edges), so the kernels call
+// opp_c_w / opp_p_w directly.
 struct ProjForm {
   template <typename T> static __device__ __forceinline__ T val_c(const Lv<T>& L, int k) { return L.c[k]; }
   template <typename T> static __device__ __forceinline__ T val_u(const Lv<T>& L, int k) { return L.u[k]; }
