@@ -1262,14 +1262,19 @@ __device__ __forceinline__ void bc_unknowns_block(const Lv<T>& L) {
 // normal, t across it).
 template <typename T>
 struct MomRow {
-  const T *a, *b, *S, *Q, *Tf, *Arn, *T1, *T0, *Dg, *f;
+  const T *a, *b, *S, *Q, *Tf, *Arn, *Dv, *T1, *T0, *Dg, *B, *f;
   int s, t;
   T grav;
 };
 
-template <typename T>
+// FullForm uses the per-step row coefficients T1, T0, Dg; ErrForm (the error
+// equation of the defect correction) has none of them, adds the base-state term
+// of the time derivative and has no gravity (it cancels in N(X + e) - N(X))
+template <typename T, class Form>
 __device__ __forceinline__ MomRow<T> mom_row(const Prm<T>& P, const Lv<T>& L, int d) {
   MomRow<T> R;
+  R.Dv = d ? L.Dvv : L.Dvu;
+  R.B = d ? L.Bv : L.Bu;
   R.a = d ? L.v : L.u;
   R.b = d ? L.u : L.v;
   R.S = d ? L.Sy : L.Sx;
@@ -1282,15 +1287,16 @@ __device__ __forceinline__ MomRow<T> mom_row(const Prm<T>& P, const Lv<T>& L, in
   R.f = d ? L.fv : L.fu;
   R.s = d ? L.pitch : 1;
   R.t = d ? 1 : L.pitch;
-  R.grav = d ? P.Fr_inv : T(0);
+  R.grav = (d && !std::is_same<Form, ErrForm>::value) ? P.Fr_inv : T(0);
   return R;
 }
 
-// N - f of the momentum row at edge index k (op_u / op_v with the density
-// average Ar of the edge passed in)
-template <typename T>
+// N - f of the momentum row at edge index k (op_u / op_v, or opd_u / opd_v for
+// ErrForm), from rho(c) of the edge's two cells (full values) passed in
+template <typename T, class Form>
 __device__ __forceinline__ T mom_residual(const Prm<T>& P, const Lv<T>& L, const MomRow<T>& R, int k,
-                                          T Ar) {
+                                          T rl, T rr) {
+  T Ar = T(0.5) * (rl + rr);
   const int s = R.s, t = R.t;
   const T *a = R.a, *b = R.b, *vis = L.visn, *rn = L.rhon;
   T ae = a[k];
@@ -1299,7 +1305,17 @@ __device__ __forceinline__ T mom_residual(const Prm<T>& P, const Lv<T>& L, const
   T dvr = dr + (b[k + s] - b[k + s - t]) * L.ih;
   T Dp = (a[k + t] - ae) * L.ih, Dm = (ae - a[k - t]) * L.ih;
   T conv = T(0.5) * (R.S[k + s] * dr + R.S[k] * dl + R.Q[k] * Dp + R.Q[k - t] * Dm);
-  T time = ae * R.T1[k] + R.T0[k] + T(0.5) * P.idt * Ar * ae;
+  T time;
+  if constexpr (std::is_same<Form, ErrForm>::value) {
+    // rho(X + e) - rho(X) of the two cells by the secant of rho, times the base velocity
+    T dAr = T(0.5) * (rsec_(P, rl, rho_of(P, L.Bc[k])) * L.c[k] +
+                      rsec_(P, rr, rho_of(P, L.Bc[k + s])) * L.c[k + s]);
+    T Arn = R.Arn[k];
+    time = Arn * ae * P.idt + T(0.5) * (Ar - Arn) * P.idt * ae + T(0.5) * dAr * P.idt * R.B[k] +
+           R.Dv[k] * ae;
+  } else {
+    time = ae * R.T1[k] + R.T0[k] + T(0.5) * P.idt * Ar * ae;
+  }
   T press = (L.p[k + s] - L.p[k]) * L.ih * P.iM;
   T st = -(rn[k + s] * L.mu[k] + rn[k] * L.mu[k + s]) * R.Tf[k] * P.iM;
   T vl = vis[k], vr = vis[k + s];
@@ -1314,7 +1330,7 @@ __device__ __forceinline__ T mom_residual(const Prm<T>& P, const Lv<T>& L, const
 // lane q writes edge q and lane 0 the pressure.  All 32 lanes of the warp
 // call this (ok = false: a spare team, which computes on cell (1,1) and
 // stores nothing).
-template <typename T>
+template <typename T, class Form>
 __device__ __forceinline__ void vanka_team(const Prm<T>& P, const Lv<T>& L, int i, int j, bool ok,
                                            T omega) {
   const unsigned FULL = 0xffffffffu;
@@ -1327,11 +1343,23 @@ __device__ __forceinline__ void vanka_team(const Prm<T>& P, const Lv<T>& L, int 
   bool a0 = L.px || i > 1, a1 = L.px || i < L.m1, a2 = j > 1, a3 = j < L.m2;
   bool mine = q == 0 ? a0 : q == 1 ? a1 : q == 2 ? a2 : a3;
   int ke = q == 0 ? kW : (q == 2 ? k - W : k);
-  MomRow<T> R = mom_row(P, L, d);
-  T Ar = T(0.5) * (rho_of(P, L.c[ke]) + rho_of(P, L.c[ke + R.s]));
+  MomRow<T> R = mom_row<T, Form>(P, L, d);
+  T rl = rho_of(P, Form::val_c(L, ke)), rr = rho_of(P, Form::val_c(L, ke + R.s));
+  T Ar = T(0.5) * (rl + rr);
   const T* vis = L.visn;
-  T dq = R.Dg[ke] + T(0.5) * P.idt * Ar;
-  T bq = mom_residual(P, L, R, ke, Ar);  // wall edges too (padded arrays), then discarded
+  T dq;
+  if constexpr (std::is_same<Form, ErrForm>::value) {
+    // the diagonal from the frozen arrays (error levels carry no row coefficients)
+    T gp = d ? ((!L.px && i == L.m1) ? T(2) : T(1)) : ((j == L.m2) ? T(2) : T(1));
+    T gm = d ? ((!L.px && i == 1) ? T(2) : T(1)) : ((j == 1) ? T(2) : T(1));
+    T Arn = R.Arn[ke];
+    dq = Arn * P.idt + T(0.5) * (Ar - Arn) * P.idt +
+         T(0.5) * ih * (-R.S[ke + R.s] + R.S[ke] - R.Q[ke] * gp + R.Q[ke - R.t] * gm) + R.Dv[ke] +
+         P.iRe * ih2 * ((vis[ke + R.s] + vis[ke]) * (T(1) + third) + gp * L.Av[ke] + gm * L.Av[ke - R.t]);
+  } else {
+    dq = R.Dg[ke] + T(0.5) * P.idt * Ar;
+  }
+  T bq = mom_residual<T, Form>(P, L, R, ke, rl, rr);  // wall edges too (padded arrays), then discarded
   if (!mine) bq = T(0);
   T A[5][5], b[5];
 #pragma unroll
@@ -1374,7 +1402,7 @@ __device__ __forceinline__ void vanka_team(const Prm<T>& P, const Lv<T>& L, int 
     A[4][3] = ih;
     A[4][4] = T(0.5) * P.alpha * P.alpha * P.iPe * sm * ih2;
   }
-  b[4] = op_p(P, L, k) - L.fp[k];
+  b[4] = Form::Np(P, L, k) - L.fp[k];
   const bool act[5] = {a0, a1, a2, a3, true};
 #pragma unroll
   for (int r = 0; r < 4; ++r)
@@ -1402,7 +1430,7 @@ __device__ __forceinline__ void vanka_team(const Prm<T>& P, const Lv<T>& L, int 
 // colour leaves most SM sub-partitions idle runs each block's critical path
 // split over four lanes.  Whole warps past the last team return together, so
 // every warp that calls vanka_team has all 32 lanes in it.
-template <typename T>
+template <typename T, class Form>
 __global__ void __launch_bounds__(SNT) k_vanka_team(Prm<T> P, Lv<T> L, int colour, T omega) {
   ColourSlots cs = vanka_slots(L, colour);
   int t = blockIdx.x * SNT + threadIdx.x;
@@ -1410,7 +1438,7 @@ __global__ void __launch_bounds__(SNT) k_vanka_team(Prm<T> P, Lv<T> L, int colou
   int i = 1, j = 1;
   bool ok = (t >> 2) < cs.n && vanka_slot_cell(L, colour, cs, t >> 2, i, j);
   if (!ok) i = j = 1;
-  vanka_team<T>(P, L, i, j, ok, omega);
+  vanka_team<T, Form>(P, L, i, j, ok, omega);
 }
 
 // teams of four lanes while the colour fits in four warps (one per sub-partition)
@@ -1447,8 +1475,7 @@ __device__ void smooth_block(const Prm<T>& P, const Lv<T>& L, T omega, int coupl
       }
       __syncthreads();
     }
-    return;
-  }
+  } else {  // primitive method (full iterate or error equation)
   if (coupled) {
     for (int col = 0; col < kcol; ++col) {
       ColourSlots cs = vanka_slots(L, col);
@@ -1462,6 +1489,7 @@ __device__ void smooth_block(const Prm<T>& P, const Lv<T>& L, T omega, int coupl
   }
   const int mpr = (L.m1 + 1) / 2;
   constexpr bool team_ok = std::is_same<Form, FullForm>::value && sizeof(T) == 8;
+  constexpr bool vteam_ok = team_ok || std::is_same<Form, ErrForm>::value;
   for (int col = 0; col < 2; ++col) {
     if (team_ok && 4 * mpr * L.m2 <= (int)blockDim.x) {
       int t = threadIdx.x;
@@ -1487,13 +1515,16 @@ __device__ void smooth_block(const Prm<T>& P, const Lv<T>& L, T omega, int coupl
   }
   for (int col = 0; col < kcol; ++col) {
     ColourSlots cs = vanka_slots(L, col);
-    if (team_ok && cs.n <= QN_TEAM_MAX_SLOTS) {
+    // FP64: while the colour fits four warps (one per sub-partition); the
+    // latency-bound FP32 error levels: while it fits the block in one pass
+    const int team_slots = team_ok ? QN_TEAM_MAX_SLOTS : (int)blockDim.x / 4;
+    if (vteam_ok && cs.n <= team_slots) {
       int t = threadIdx.x;
       if ((t & ~31) < 4 * cs.n) {  // warp-uniform: the warp holds at least one team
         int i = 1, j = 1;
         bool ok = (t >> 2) < cs.n && vanka_slot_cell(L, col, cs, t >> 2, i, j);
         if (!ok) i = j = 1;
-        vanka_team<T>(P, L, i, j, ok, omega);
+        vanka_team<T, Form>(P, L, i, j, ok, omega);
       }
     } else {
       for (int t = threadIdx.x; t < cs.n; t += blockDim.x) {
@@ -1503,6 +1534,7 @@ __device__ void smooth_block(const Prm<T>& P, const Lv<T>& L, T omega, int coupl
     }
     __syncthreads();
   }
+  }  // primitive method
 }
 
 template <typename T, class Form, int NT>
@@ -1896,9 +1928,10 @@ void launch_vanka(const Prm<T>& P, const Lv<T>& L, int colour, T omega, cudaStre
                   int team_max) {
   int n = vanka_slots(L, colour).n;
   if (n <= 0) return;
-  if constexpr (std::is_same<Form, FullForm>::value && sizeof(T) == 8) {
+  if constexpr ((std::is_same<Form, FullForm>::value && sizeof(T) == 8) ||
+                std::is_same<Form, ErrForm>::value) {
     if (n <= team_max) {  // four lanes per block: shorter critical path per visit
-      k_vanka_team<T><<<(4 * n + SNT - 1) / SNT, SNT, 0, s>>>(P, L, colour, omega);
+      k_vanka_team<T, Form><<<(4 * n + SNT - 1) / SNT, SNT, 0, s>>>(P, L, colour, omega);
       ++g_launches;
       return;
     }

@@ -115,6 +115,8 @@ struct qnsch_s {
   int team_max = 8192;
   // the same for the CH smoother's per-level launches (cells per red-black colour)
   int ch_team_max = 4096;
+  // error-equation levels of the defect correction (latency-bound at every size)
+  int team_max32 = 1 << 30;
   // grid
   int m1, m2, px, nlev, kcol;
   double h;
@@ -383,7 +385,8 @@ void smooth(qnsch_s* s, const std::vector<Lv<T>>& Ls, const Prm<T>& P, int l) {
     }
     if (rec) cudaEventRecord(s->ev[s->ev_used], s->stream);
     if (s->coupled) qn::launch_coupled<T, Form>(P, L, c, (T)s->omega, s->stream);
-    else qn::launch_vanka<T, Form>(P, L, c, (T)s->omega, s->stream, s->team_max);
+    else qn::launch_vanka<T, Form>(P, L, c, (T)s->omega, s->stream,
+                                   std::is_same<Form, ErrForm>::value ? s->team_max32 : s->team_max);
     if (rec) {
       cudaEventRecord(s->ev[s->ev_used + 1], s->stream);
       s->ev_used += 2;
@@ -851,6 +854,7 @@ int qnsch_set_option(qnsch_t* s, const char* key, double value) {
   } else if (k == "fuse_cells32") s->fuse32 = (int)value;
   else if (k == "vanka_team_max") s->team_max = (int)value;
   else if (k == "ch_team_max") s->ch_team_max = (int)value;
+  else if (k == "vanka_team_max32") s->team_max32 = (int)value;
   else if (k == "precision") {
     int p = (int)value;
     if (p < 0 || p > 2 || (double)p != value) return QNSCH_EINVAL;
@@ -886,6 +890,7 @@ int qnsch_get_option(const qnsch_t* s, const char* key, double* value) {
   else if (k == "scheme") *value = s->scheme;
   else if (k == "vanka_team_max") *value = s->team_max;
   else if (k == "ch_team_max") *value = s->ch_team_max;
+  else if (k == "vanka_team_max32") *value = s->team_max32;
   else return QNSCH_EINVAL;
   return QNSCH_OK;
 }
