@@ -92,7 +92,7 @@ int qnsch_footprint(const qnsch_grid* grid, int precision, size_t* bytes);
    "maxcyc": 50, "omega_vanka": 1, "M": Cn, "eta_st": eta(rho1, rho2),
    "eps_mob": Cn, "precision": 0, "graphs": 1, "fuse_cells": 128,
    "fuse_cells32": 2048, "coupled": 0, "scheme": 0, "vanka_team_max": 8192,
-   "ch_team_max": 4096, "vanka_team_max32": 2^30.
+   "ch_team_max": 4096, "vanka_team_max32": 2^30, "pdl": 1.
    Unknown keys give QNSCH_EINVAL.
    scheme: 0 the primitive method (Sec. 6.1); 1 the projection method
    (Sec. 6.2; precision 0 and coupled 0 only).
@@ -103,6 +103,11 @@ int qnsch_footprint(const qnsch_grid* grid, int precision, size_t* bytes);
    per cell, one face each); vanka_team_max32 for the Vanka launches on the
    error-equation levels of the defect correction (precision 1 and 2), which
    are latency-bound at every size.
+   pdl: 1 launches every kernel with programmatic dependent launch, so that
+   a kernel is scheduled as its predecessor's blocks exit and waits on the GPU
+   for the predecessor's results before touching memory (same results); 0
+   launches in plain stream order.  It applies to every handle of the process
+   and takes effect at the next graph capture.
    coupled: 0 smooths with the paper's separate sweeps (CH 2x2 red-black, then
    the Vanka 5x5 colours, Sec. 7.1); 1 replaces them by one sweep over the
    Vanka colours of a coupled 7x7 Newton block in (c, mu, u_W, u_E, v_S, v_N, p).

@@ -74,6 +74,9 @@ template <typename T> void launch_pack_out(const Lv<T>& L, double* dst, const T*
 
 // kernels issued by this library since it was loaded
 long long launches_issued();
+// launch every kernel with programmatic dependent launch (1, the default) or
+// in plain stream order (0); applies to all handles of the process
+void set_pdl(int on);
 
 // rows of block partials any reduction on an m1 x m2 level may write
 int partial_rows_needed(int m1, int m2);

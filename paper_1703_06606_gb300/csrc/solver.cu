@@ -51,6 +51,9 @@ void dev_free(void* p) {
 
 constexpr int NFIELD = 44;  // arrays per level (see Lv)
 
+// option "pdl": programmatic dependent launch of every kernel (process-wide)
+static int g_pdl_option = 1;
+
 // surface-tension ratio eta(rho1, rho2) of Sec. 8.1; near rho1 = rho2 the
 // formula is 0/0 and the Taylor series of x^2 - 1 - 2x ln x in q = x - 1 is used
 double eta_st(double r1, double r2) {
@@ -855,6 +858,10 @@ int qnsch_set_option(qnsch_t* s, const char* key, double value) {
   else if (k == "vanka_team_max") s->team_max = (int)value;
   else if (k == "ch_team_max") s->ch_team_max = (int)value;
   else if (k == "vanka_team_max32") s->team_max32 = (int)value;
+  else if (k == "pdl") {
+    g_pdl_option = value != 0.0;
+    qn::set_pdl(g_pdl_option);
+  }
   else if (k == "precision") {
     int p = (int)value;
     if (p < 0 || p > 2 || (double)p != value) return QNSCH_EINVAL;
@@ -891,6 +898,7 @@ int qnsch_get_option(const qnsch_t* s, const char* key, double* value) {
   else if (k == "vanka_team_max") *value = s->team_max;
   else if (k == "ch_team_max") *value = s->ch_team_max;
   else if (k == "vanka_team_max32") *value = s->team_max32;
+  else if (k == "pdl") *value = g_pdl_option;
   else return QNSCH_EINVAL;
   return QNSCH_OK;
 }
