@@ -1442,19 +1442,28 @@ __device__ __forceinline__ void vanka_team(const Prm<T>& P, const Lv<T>& L, int 
   A[2][4] = ih * P.iM;
   A[3][4] = -ih * P.iM;
   {
+    // the mass row by faces: lane q takes face q (W, E, S, N) of the cell, the
+    // face of its own edge: its velocity in d.u, its flux of
+    // grad.(A m grad(mu + alpha p)) and, if open, its share of sum A m
     const T* mob = L.mobn;
-    T sm = T(0);
-    if (L.px || i < L.m1) sm += mob[k] + mob[k + 1];
-    if (L.px || i > 1) sm += mob[k] + mob[k - 1];
-    if (j < L.m2) sm += mob[k] + mob[k + W];
-    if (j > 1) sm += mob[k] + mob[k - W];
+    const int nq = k + (q == 0 ? -1 : q == 1 ? 1 : q == 2 ? -W : W);
+    T am = mob[nq] + mob[k];
+    T f3[3];
+    f3[0] = (q & 1) ? (d ? L.v[k] : L.u[k]) : -(d ? L.v[k - W] : L.u[k - 1]);
+    f3[1] = T(0.5) * am * ((L.mu[nq] - L.mu[k]) + P.alpha * (L.p[nq] - L.p[k]));
+    f3[2] = mine ? am : T(0);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      f3[a] += __shfl_xor_sync(FULL, f3[a], 1);
+      f3[a] += __shfl_xor_sync(FULL, f3[a], 2);
+    }
     A[4][0] = -ih;
     A[4][1] = ih;
     A[4][2] = -ih;
     A[4][3] = ih;
-    A[4][4] = T(0.5) * P.alpha * P.alpha * P.iPe * sm * ih2;
+    A[4][4] = T(0.5) * P.alpha * P.alpha * P.iPe * f3[2] * ih2;
+    b[4] = f3[0] * ih - P.alpha * P.iPe * ih2 * f3[1] - L.fp[k];
   }
-  b[4] = Form::Np(P, L, k) - L.fp[k];
   const bool act[5] = {a0, a1, a2, a3, true};
 #pragma unroll
   for (int r = 0; r < 4; ++r)
