@@ -605,42 +605,73 @@ __device__ __forceinline__ void vanka_cell(const Prm<T>& P, const Lv<T>& L, int 
   store_cell(L, L.p, i, j, L.p[k] - omega * b[4]);
 }
 
-// Gaussian elimination with partial pivoting (compare-and-swap) on a 7x7 system
+// Exact solve of the coupled 7x7 system of coupled_cell by blocks.  Its NS part
+// A[2..6][2..6] is a Vanka block (see solve_vanka): it is factored once and
+// applied to three right-hand sides, b_NS and the two columns through which c
+// and mu enter the NS rows.  What remains for (dc, dmu) is the 2x2 Schur
+// complement S = J_CH - C (A_NS^-1 C'), solved directly; the NS unknowns follow
+// by back substitution.  Row 1 (N_mu) does not involve u, v or p, so its
+// coupling entries are zero and its Schur row is that of J_CH.
 template <typename T>
-__device__ __forceinline__ void solve7(T (&A)[7][7], T (&b)[7]) {
+__device__ __forceinline__ void solve_coupled7(const T (&A)[7][7], T (&b)[7], const bool (&act)[5],
+                                               T v3, T a, T ih) {
+  T B00[2], B01[2], B10[2], B11[2], idet[2], z[4];
 #pragma unroll
-  for (int k = 0; k < 7; ++k) {
-#pragma unroll
-    for (int r = k + 1; r < 7; ++r) {
-      if (fabs(A[r][k]) > fabs(A[k][k])) {
-#pragma unroll
-        for (int c = k; c < 7; ++c) {
-          T t = A[k][c];
-          A[k][c] = A[r][c];
-          A[r][c] = t;
-        }
-        T t = b[k];
-        b[k] = b[r];
-        b[r] = t;
-      }
-    }
-    T inv = T(1) / A[k][k];
-#pragma unroll
-    for (int r = k + 1; r < 7; ++r) {
-      T l = A[r][k] * inv;
-#pragma unroll
-      for (int c = k + 1; c < 7; ++c) A[r][c] -= l * A[k][c];
-      b[r] -= l * b[k];
-    }
-    A[k][k] = inv;
+  for (int blk = 0; blk < 2; ++blk) {
+    const int p0 = 2 * blk, p1 = p0 + 1;
+    const bool a0 = act[p0], a1 = act[p1];
+    B00[blk] = a0 ? A[2 + p0][2 + p0] - v3 : A[2 + p0][2 + p0];
+    B11[blk] = a1 ? A[2 + p1][2 + p1] - v3 : A[2 + p1][2 + p1];
+    B01[blk] = (a0 && a1) ? A[2 + p0][2 + p1] + v3 : A[2 + p0][2 + p1];
+    B10[blk] = (a0 && a1) ? A[2 + p1][2 + p0] + v3 : A[2 + p1][2 + p0];
+    idet[blk] = T(1) / (B00[blk] * B11[blk] - B01[blk] * B10[blk]);
+    z[p0] = ((a0 ? B11[blk] : T(0)) + (a1 ? B01[blk] : T(0))) * idet[blk];
+    z[p1] = -((a1 ? B00[blk] : T(0)) + (a0 ? B10[blk] : T(0))) * idet[blk];
   }
+  const T sdot = (z[0] - z[1]) + (z[2] - z[3]);
+  const T g = T(1) / (T(1) + v3 * sdot);
+  const T iden = T(1) / (A[6][6] + ih * a * sdot * g);
+  // x = A_NS^-1 r for a right-hand side r over (u_W, u_E, v_S, v_N, p)
+  auto apply = [&](const T (&r)[5], T (&x)[5]) {
+    T y[4];
 #pragma unroll
-  for (int k = 6; k >= 0; --k) {
-    T t = b[k];
+    for (int blk = 0; blk < 2; ++blk) {
+      const int p0 = 2 * blk, p1 = p0 + 1;
+      y[p0] = (B11[blk] * r[p0] - B01[blk] * r[p1]) * idet[blk];
+      y[p1] = (B00[blk] * r[p1] - B10[blk] * r[p0]) * idet[blk];
+    }
+    T t = (y[0] - y[1]) + (y[2] - y[3]);
+    T pr = (r[4] + ih * t * g) * iden;
+    T f = g * (v3 * t + a * pr);
 #pragma unroll
-    for (int c = k + 1; c < 7; ++c) t -= A[k][c] * b[c];
-    b[k] = t * A[k][k];
+    for (int q = 0; q < 4; ++q) x[q] = y[q] - z[q] * f;
+    x[4] = pr;
+  };
+  T r0[5], r1[5], r2[5], X0[5], X1[5], X2[5];
+#pragma unroll
+  for (int m = 0; m < 5; ++m) {
+    r0[m] = b[2 + m];
+    r1[m] = A[2 + m][0];
+    r2[m] = A[2 + m][1];
   }
+  apply(r0, X0);
+  apply(r1, X1);
+  apply(r2, X2);
+  T S00 = A[0][0], S01 = A[0][1], rhs0 = b[0];
+#pragma unroll
+  for (int m = 0; m < 5; ++m) {
+    S00 -= A[0][2 + m] * X1[m];
+    S01 -= A[0][2 + m] * X2[m];
+    rhs0 -= A[0][2 + m] * X0[m];
+  }
+  const T S10 = A[1][0], S11 = A[1][1], rhs1 = b[1];
+  T id2 = T(1) / (S00 * S11 - S01 * S10);
+  T dc = (S11 * rhs0 - S01 * rhs1) * id2;
+  T dm = (S00 * rhs1 - S10 * rhs0) * id2;
+  b[0] = dc;
+  b[1] = dm;
+#pragma unroll
+  for (int m = 0; m < 5; ++m) b[2 + m] = X0[m] - X1[m] * dc - X2[m] * dm;
 }
 
 // Coupled block (an option; the paper's smoother keeps the two blocks
@@ -717,7 +748,7 @@ __device__ __forceinline__ void coupled_cell(const Prm<T>& P, const Lv<T>& L, in
       }
       A[2 + q][2 + q] = T(1);
     }
-  solve7(A, b);
+  solve_coupled7(A, b, act, L.visn[k] * P.iRe * L.ih2 * T(1.0 / 3.0), L.ih * P.iM, L.ih);
   store_cell(L, L.c, i, j, L.c[k] - omega * b[0]);
   store_cell(L, L.mu, i, j, L.mu[k] - omega * b[1]);
   if (act[0]) store_u(L, eW, j, L.u[kW] - omega * b[2]);
