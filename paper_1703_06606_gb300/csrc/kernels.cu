@@ -122,9 +122,9 @@ __device__ __forceinline__ void residual_cell(const Prm<T>& P, const Lv<T>& L, i
   if constexpr (std::is_same<Form, FullForm>::value) {
     // rho(c) of the cell and its neighbours, shared by the five rows
     const int W = L.pitch;
-    T rk = rho_of(P, L.c[k]);
-    const T rq[4] = {rho_of(P, L.c[k + 1]), rho_of(P, L.c[k - 1]), rho_of(P, L.c[k + W]),
-                     rho_of(P, L.c[k - W])};
+    const T* rc = L.rhoc;
+    T rk = rc[k];
+    const T rq[4] = {rc[k + 1], rc[k - 1], rc[k + W], rc[k - W]};
     nc = op_c(P, L, k, rk);
     nm = op_mu(P, L, k, rk, rq);
     np = op_p(P, L, k);
@@ -132,9 +132,9 @@ __device__ __forceinline__ void residual_cell(const Prm<T>& P, const Lv<T>& L, i
     nv = op_v(P, L, k, T(0.5) * (rk + rq[2]));  // also on boundary edges (padded arrays); masked below
   } else if constexpr (std::is_same<Form, ProjForm>::value) {
     const int W = L.pitch;
-    T rk = rho_of(P, L.c[k]);
-    const T rq[4] = {rho_of(P, L.c[k + 1]), rho_of(P, L.c[k - 1]), rho_of(P, L.c[k + W]),
-                     rho_of(P, L.c[k - W])};
+    const T* rc = L.rhoc;
+    T rk = rc[k];
+    const T rq[4] = {rc[k + 1], rc[k - 1], rc[k + W], rc[k - W]};
     T w[4];
     proj_faces(P, L, i, j, rk, rq, w);
     nc = opp_c_w(P, L, k, rq, w);
@@ -197,9 +197,9 @@ __device__ __forceinline__ void ch_system(const Prm<T>& P, const Lv<T>& L, int i
   const int off[4] = {1, -1, W, -W};
   // rho(c) of the cell and its four neighbours, shared by N_c, N_mu and J
   T rho, rq4[4];
-  rho = rho_of(P, Form::val_c(L, k));
+  rho = Form::rho(P, L, k);
 #pragma unroll
-  for (int f = 0; f < 4; ++f) rq4[f] = rho_of(P, Form::val_c(L, k + off[f]));
+  for (int f = 0; f < 4; ++f) rq4[f] = Form::rho(P, L, k + off[f]);
   T Rc, Rm;
   T wf[4];  // projection method: the face velocities u^{n+1} (E, W, N, S)
   if constexpr (std::is_same<Form, FullForm>::value) {
@@ -270,7 +270,9 @@ __device__ __forceinline__ void ch_cell(const Prm<T>& P, const Lv<T>& L, int i, 
   T dc = (J[1][1] * R[0] - J[0][1] * R[1]) * idet;
   T dm = (J[0][0] * R[1] - J[1][0] * R[0]) * idet;
   int k = L.at(i, j);
-  store_cell(L, L.c, i, j, L.c[k] - dc);
+  T cnew = L.c[k] - dc;
+  store_cell(L, L.c, i, j, cnew);
+  if constexpr (!std::is_same<Form, ErrForm>::value) store_cell(L, L.rhoc, i, j, rho_of(P, cnew));
   store_cell(L, L.mu, i, j, L.mu[k] - dm);
 }
 
@@ -304,9 +306,9 @@ __device__ __forceinline__ void ch_team(const Prm<T>& P, const Lv<T>& L, int i, 
   const int kv = f == 1 ? k - 1 : f == 3 ? k - W : k;  // edge of face f
   const T *c = L.c, *cn = L.cn, *rn = L.rhon, *mob = L.mobn;
   T ck = c[k], cnk = cn[k], mk = L.mu[k], rnk = rn[k];
-  T rho = rho_of(P, ck);
+  T rho = L.rhoc[k];
   T cq = c[q];
-  T rq = rho_of(P, cq);
+  T rq = L.rhoc[q];
   T drho = -P.alpha * rho * rho;
   T rh = T(0.5) * (rho + rnk);
   T chk = ck + cnk;
@@ -347,6 +349,7 @@ __device__ __forceinline__ void ch_team(const Prm<T>& P, const Lv<T>& L, int i, 
   T dm = (J11 * Rm - J21 * Rc) * idet;
   if (ok && f == 0) {
     store_cell(L, L.c, i, j, ck - dc);
+    store_cell(L, L.rhoc, i, j, rho_of(P, ck - dc));
     store_cell(L, L.mu, i, j, mk - dm);
   }
 }
@@ -402,11 +405,11 @@ __device__ __forceinline__ void vanka_system(const Prm<T>& P, const Lv<T>& L, in
   // neighbours (c at kW + 1 is c at k, exactly: ghosts are copies)
   T Arq[4];
   {
-    T rk = rho_of(P, Form::val_c(L, k));
-    Arq[0] = T(0.5) * (rho_of(P, Form::val_c(L, kW)) + rk);
-    Arq[1] = T(0.5) * (rk + rho_of(P, Form::val_c(L, k + 1)));
-    Arq[2] = T(0.5) * (rho_of(P, Form::val_c(L, k - W)) + rk);
-    Arq[3] = T(0.5) * (rk + rho_of(P, Form::val_c(L, k + W)));
+    T rk = Form::rho(P, L, k);
+    Arq[0] = T(0.5) * (Form::rho(P, L, kW) + rk);
+    Arq[1] = T(0.5) * (rk + Form::rho(P, L, k + 1));
+    Arq[2] = T(0.5) * (Form::rho(P, L, k - W) + rk);
+    Arq[3] = T(0.5) * (rk + Form::rho(P, L, k + W));
   }
   // x-edge rows: q = 0 (west edge, index kW), q = 1 (east edge, index k)
 #pragma unroll
@@ -715,8 +718,7 @@ __device__ __forceinline__ void coupled_cell(const Prm<T>& P, const Lv<T>& L, in
 #pragma unroll
   for (int f = 0; f < 4; ++f)
     if (!wall[f]) sm += mob[k] + mob[k + off[f]];
-  T cfull = Form::val_c(L, k);
-  T rho = rho_of(P, cfull), drho = -P.alpha * rho * rho;
+  T rho = Form::rho(P, L, k), drho = -P.alpha * rho * rho;
   // rho^n D c^n / 2 at the four faces of the cell, as in (e1e2) and (e1e1)
   T gW = rn[k - 1] * L.Tx[k - 1];
   T gE = rn[k + 1] * L.Tx[k];
@@ -749,7 +751,9 @@ __device__ __forceinline__ void coupled_cell(const Prm<T>& P, const Lv<T>& L, in
       A[2 + q][2 + q] = T(1);
     }
   solve_coupled7(A, b, act, L.visn[k] * P.iRe * L.ih2 * T(1.0 / 3.0), L.ih * P.iM, L.ih);
-  store_cell(L, L.c, i, j, L.c[k] - omega * b[0]);
+  T cnew = L.c[k] - omega * b[0];
+  store_cell(L, L.c, i, j, cnew);
+  if constexpr (!std::is_same<Form, ErrForm>::value) store_cell(L, L.rhoc, i, j, rho_of(P, cnew));
   store_cell(L, L.mu, i, j, L.mu[k] - omega * b[1]);
   if (act[0]) store_u(L, eW, j, L.u[kW] - omega * b[2]);
   if (act[1]) store_u(L, i, j, L.u[k] - omega * b[3]);
@@ -881,9 +885,9 @@ template <typename T>
 __device__ __forceinline__ void pgs_cell(const Prm<T>& P, const Lv<T>& L, int i, int j) {
   const int W = L.pitch;
   int k = L.at(i, j);
-  T rk = rho_of(P, L.c[k]);
-  const T rq[4] = {rho_of(P, L.c[k + 1]), rho_of(P, L.c[k - 1]), rho_of(P, L.c[k + W]),
-                   rho_of(P, L.c[k - W])};
+  const T* rc = L.rhoc;
+  T rk = rc[k];
+  const T rq[4] = {rc[k + 1], rc[k - 1], rc[k + W], rc[k - W]};
   T w[4];
   proj_faces(P, L, i, j, rk, rq, w);
   T R = opp_p_w(P, L, k, w) - L.fp[k];
@@ -1040,6 +1044,7 @@ __global__ void k_bc_unknowns(Lv<T> L) {
   int I, J;
   if (!frame_pos(t, L.m1, L.m2, I, J)) return;
   fill_cell_ghost(L, L.c, I, J);
+  if (L.rhoc) fill_cell_ghost(L, L.rhoc, I, J);
   fill_cell_ghost(L, L.mu, I, J);
   fill_cell_ghost(L, L.p, I, J);
   fill_u_ghost(L, L.u, I, J);
@@ -1149,7 +1154,8 @@ __global__ void k_frozen_coef3(Prm<T> P, Lv<T> L) {
 // coarse iterate = R x_h (cells: 4-mean; edges: mean of the 2 coincident fine edges),
 // and a copy kept for the correction
 template <typename T>
-__device__ __forceinline__ void restrict_state_cell(const Lv<T>& F, const Lv<T>& C, int I, int J) {
+__device__ __forceinline__ void restrict_state_cell(const Prm<T>& P, const Lv<T>& F, const Lv<T>& C,
+                                                    int I, int J) {
   int kc = C.at(I, J);
   if (I >= 1 && J >= 1) {
     int kf = F.at(2 * I - 1, 2 * J - 1), W = F.pitch;
@@ -1157,6 +1163,7 @@ __device__ __forceinline__ void restrict_state_cell(const Lv<T>& F, const Lv<T>&
     T b = T(0.25) * (F.mu[kf] + F.mu[kf + 1] + F.mu[kf + W] + F.mu[kf + W + 1]);
     T d = T(0.25) * (F.p[kf] + F.p[kf + 1] + F.p[kf + W] + F.p[kf + W + 1]);
     C.c[kc] = a; C.sc[kc] = a;
+    if (C.rhoc) C.rhoc[kc] = rho_of(P, a);
     C.mu[kc] = b; C.smu[kc] = b;
     C.p[kc] = d; C.sp[kc] = d;
   }
@@ -1175,12 +1182,12 @@ __device__ __forceinline__ void restrict_state_cell(const Lv<T>& F, const Lv<T>&
 // coarse iterate = R x_h (cells: 4-mean; edges: mean of the 2 coincident fine edges),
 // and a copy kept for the correction
 template <typename T>
-__global__ void k_restrict_state(Lv<T> F, Lv<T> C) {
+__global__ void k_restrict_state(Prm<T> P, Lv<T> F, Lv<T> C) {
   pdl_enter();
   int I = blockIdx.x * BX + threadIdx.x;
   int J = blockIdx.y * BY + threadIdx.y;
   if (I > C.m1 || J > C.m2) return;
-  restrict_state_cell(F, C, I, J);
+  restrict_state_cell(P, F, C, I, J);
 }
 
 template <typename T>
@@ -1263,11 +1270,13 @@ __global__ void k_restrict_frozen(Lv<T> F, Lv<T> C) {
 // x_h += P(x_H - saved_H): cells piecewise constant; edges coincident or linear
 // in the normal direction, constant in the tangential direction
 template <typename T>
-__device__ __forceinline__ void prolong_cell(const Lv<T>& F, const Lv<T>& C, int i, int j) {
+__device__ __forceinline__ void prolong_cell(const Prm<T>& P, const Lv<T>& F, const Lv<T>& C, int i,
+                                             int j) {
   int k = F.at(i, j);
   int I = (i + 1) >> 1, J = (j + 1) >> 1;
   int kc = C.at(I, J);
   F.c[k] += C.c[kc] - C.sc[kc];
+  if (F.rhoc) F.rhoc[k] = rho_of(P, F.c[k]);
   F.mu[k] += C.mu[kc] - C.smu[kc];
   F.p[k] += C.p[kc] - C.sp[kc];
   if (i <= F.uhi()) {
@@ -1295,12 +1304,12 @@ __device__ __forceinline__ void prolong_cell(const Lv<T>& F, const Lv<T>& C, int
 }
 
 template <typename T>
-__global__ void k_prolong(Lv<T> F, Lv<T> C) {
+__global__ void k_prolong(Prm<T> P, Lv<T> F, Lv<T> C) {
   pdl_enter();
   int i = blockIdx.x * BX + threadIdx.x + 1;
   int j = blockIdx.y * BY + threadIdx.y + 1;
   if (i > F.m1 || j > F.m2) return;
-  prolong_cell(F, C, i, j);
+  prolong_cell(P, F, C, i, j);
 }
 
 // --------------------------------------------------------------------------
@@ -1323,6 +1332,7 @@ __device__ __forceinline__ void bc_unknowns_block(const Lv<T>& L) {
     int I, J;
     if (!frame_pos(t, L.m1, L.m2, I, J)) continue;
     fill_cell_ghost(L, L.c, I, J);
+    if (L.rhoc) fill_cell_ghost(L, L.rhoc, I, J);
     fill_cell_ghost(L, L.mu, I, J);
     fill_cell_ghost(L, L.p, I, J);
     fill_u_ghost(L, L.u, I, J);
@@ -1427,7 +1437,7 @@ __device__ __forceinline__ void vanka_team(const Prm<T>& P, const Lv<T>& L, int 
   bool mine = q == 0 ? a0 : q == 1 ? a1 : q == 2 ? a2 : a3;
   int ke = q == 0 ? kW : (q == 2 ? k - W : k);
   MomRow<T> R = mom_row<T, Form>(P, L, d);
-  T rl = rho_of(P, Form::val_c(L, ke)), rr = rho_of(P, Form::val_c(L, ke + R.s));
+  T rl = Form::rho(P, L, ke), rr = Form::rho(P, L, ke + R.s);
   T Ar = T(0.5) * (rl + rr);
   const T* vis = L.visn;
   T dq;
@@ -1644,7 +1654,7 @@ __global__ void __launch_bounds__(NT) k_coarse_vcycle(Prm<T> P, CoarseLevels<T> 
       residual_cell<T, 0, Form>(P, F, t % F.m1 + 1, t / F.m1 + 1, dummy);
     __syncthreads();
     for (int t = threadIdx.x; t < (G.m1 + 1) * (G.m2 + 1); t += NT)
-      restrict_state_cell(F, G, t % (G.m1 + 1), t / (G.m1 + 1));
+      restrict_state_cell(P, F, G, t % (G.m1 + 1), t / (G.m1 + 1));
     __syncthreads();
     bc_unknowns_block(G);
     for (int t = threadIdx.x; t < G.m1 * G.m2; t += NT)
@@ -1659,7 +1669,7 @@ __global__ void __launch_bounds__(NT) k_coarse_vcycle(Prm<T> P, CoarseLevels<T> 
     const Lv<T>& F = C.L[l];
     const Lv<T>& G = C.L[l + 1];
     for (int t = threadIdx.x; t < F.m1 * F.m2; t += NT)
-      prolong_cell(F, G, t % F.m1 + 1, t / F.m1 + 1);
+      prolong_cell(P, F, G, t % F.m1 + 1, t / F.m1 + 1);
     __syncthreads();
     bc_unknowns_block(F);
     for (int s = 0; s < nu2; ++s) smooth_block<T, Form>(P, F, omega, coupled);
@@ -1723,16 +1733,27 @@ __global__ void k_start_correction(Lv<double> D, Lv<T> E, long long n, int off) 
 
 // x += e on the whole padded arrays (ghost rules are linear, so ghosts stay valid)
 template <typename T>
-__global__ void k_apply_correction(Lv<double> D, Lv<T> E, long long n, int off) {
+__global__ void k_apply_correction(Prm<double> P, Lv<double> D, Lv<T> E, long long n, int off) {
   pdl_enter();
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   long long q = t - off;
   D.c[q] += (double)E.c[q];
+  D.rhoc[q] = rho_of(P, D.c[q]);
   D.mu[q] += (double)E.mu[q];
   D.p[q] += (double)E.p[q];
   D.u[q] += (double)E.u[q];
   D.v[q] += (double)E.v[q];
+}
+
+// rho(c) of the iterate over the whole padded array, after c was written in
+// bulk (a new step's start, fields set from the host)
+__global__ void k_rho_fill(Prm<double> P, Lv<double> L, long long n, int off) {
+  pdl_enter();
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  long long q = t - off;
+  L.rhoc[q] = rho_of(P, L.c[q]);
 }
 
 // coarse base X_H = R X_h (cells: 4-mean; edges: 2 coincident fine edges)
@@ -2111,9 +2132,15 @@ void launch_start_correction(const Lv<double>& D, const Lv<T>& E, cudaStream_t s
   ++g_launches;
 }
 template <typename T>
-void launch_apply_correction(const Lv<double>& D, const Lv<T>& E, cudaStream_t s) {
+void launch_apply_correction(const Prm<double>& P, const Lv<double>& D, const Lv<T>& E,
+                             cudaStream_t s) {
   long long n = padded_n(D.m1, D.m2);
-  qlaunch(&k_apply_correction<T>, (unsigned)((n + 255) / 256), 256, 0, s, D, E, n, D.pitch + 1);
+  qlaunch(&k_apply_correction<T>, (unsigned)((n + 255) / 256), 256, 0, s, P, D, E, n, D.pitch + 1);
+  ++g_launches;
+}
+void launch_rho_fill(const Prm<double>& P, const Lv<double>& L, cudaStream_t s) {
+  long long n = padded_n(L.m1, L.m2);
+  qlaunch(&k_rho_fill, (unsigned)((n + 255) / 256), 256, 0, s, P, L, n, L.pitch + 1);
   ++g_launches;
 }
 template <typename T>
@@ -2147,8 +2174,8 @@ void launch_frozen(const Prm<T>& P, const Lv<T>& L, cudaStream_t s) {
   ++g_launches;
 }
 template <typename T>
-void launch_restrict_state(const Lv<T>& F, const Lv<T>& C, cudaStream_t s) {
-  qlaunch(&k_restrict_state<T>, grid2(C.m1 + 1, C.m2 + 1), dim3(BX, BY), 0, s, F, C);
+void launch_restrict_state(const Prm<T>& P, const Lv<T>& F, const Lv<T>& C, cudaStream_t s) {
+  qlaunch(&k_restrict_state<T>, grid2(C.m1 + 1, C.m2 + 1), dim3(BX, BY), 0, s, P, F, C);
   ++g_launches;
 }
 template <typename T>
@@ -2162,8 +2189,8 @@ void launch_restrict_frozen(const Lv<T>& F, const Lv<T>& C, cudaStream_t s) {
   ++g_launches;
 }
 template <typename T>
-void launch_prolong(const Lv<T>& F, const Lv<T>& C, cudaStream_t s) {
-  qlaunch(&k_prolong<T>, grid2(F.m1, F.m2), dim3(BX, BY), 0, s, F, C);
+void launch_prolong(const Prm<T>& P, const Lv<T>& F, const Lv<T>& C, cudaStream_t s) {
+  qlaunch(&k_prolong<T>, grid2(F.m1, F.m2), dim3(BX, BY), 0, s, P, F, C);
   ++g_launches;
 }
 template <typename T>
@@ -2254,14 +2281,15 @@ int partial_rows_needed(int m1, int m2) {
 #define QN_INSTANTIATE(T)                                                                        \
   template void launch_cast_frozen<T>(const Lv<double>&, const Lv<T>&, cudaStream_t);            \
   template void launch_start_correction<T>(const Lv<double>&, const Lv<T>&, cudaStream_t);       \
-  template void launch_apply_correction<T>(const Lv<double>&, const Lv<T>&, cudaStream_t);       \
+  template void launch_apply_correction<T>(const Prm<double>&, const Lv<double>&, const Lv<T>&,    \
+                                            cudaStream_t);                                          \
   template void launch_restrict_base<T>(const Lv<T>&, const Lv<T>&, cudaStream_t);               \
   template void launch_bc_unknowns<T>(const Lv<T>&, cudaStream_t);                               \
   template void launch_frozen<T>(const Prm<T>&, const Lv<T>&, cudaStream_t);                     \
-  template void launch_restrict_state<T>(const Lv<T>&, const Lv<T>&, cudaStream_t);              \
+  template void launch_restrict_state<T>(const Prm<T>&, const Lv<T>&, const Lv<T>&, cudaStream_t); \
   template void launch_restrict_res<T>(const Lv<T>&, const Lv<T>&, cudaStream_t);                \
   template void launch_restrict_frozen<T>(const Lv<T>&, const Lv<T>&, cudaStream_t);             \
-  template void launch_prolong<T>(const Lv<T>&, const Lv<T>&, cudaStream_t);                     \
+  template void launch_prolong<T>(const Prm<T>&, const Lv<T>&, const Lv<T>&, cudaStream_t);        \
   template void launch_gauge<T>(const Lv<T>&, double*, double*, cudaStream_t);                   \
   template void launch_norms_finalize<T>(const Lv<T>&, double*, double*, cudaStream_t);          \
   template void launch_mass<T>(const Prm<T>&, const Lv<T>&, const T*, double*, double*,          \

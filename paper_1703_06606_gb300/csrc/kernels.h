@@ -44,14 +44,17 @@ void launch_proj_diss(const Prm<T>& P, const Lv<T>& L, const T* uo, const T* vo,
 // defect correction: E (error-equation level) from the FP64 level D
 template <typename T> void launch_cast_frozen(const Lv<double>& D, const Lv<T>& E, cudaStream_t s);
 template <typename T> void launch_start_correction(const Lv<double>& D, const Lv<T>& E, cudaStream_t s);
-template <typename T> void launch_apply_correction(const Lv<double>& D, const Lv<T>& E, cudaStream_t s);
+template <typename T>
+void launch_apply_correction(const Prm<double>& P, const Lv<double>& D, const Lv<T>& E, cudaStream_t s);
+// rho(c) of the iterate over the whole padded arrays of an FP64 full-iterate level
+void launch_rho_fill(const Prm<double>& P, const Lv<double>& L, cudaStream_t s);
 template <typename T> void launch_restrict_base(const Lv<T>& F, const Lv<T>& C, cudaStream_t s);
 template <typename T> void launch_bc_unknowns(const Lv<T>& L, cudaStream_t s);
 template <typename T> void launch_frozen(const Prm<T>& P, const Lv<T>& L, cudaStream_t s);
-template <typename T> void launch_restrict_state(const Lv<T>& F, const Lv<T>& C, cudaStream_t s);
+template <typename T> void launch_restrict_state(const Prm<T>& P, const Lv<T>& F, const Lv<T>& C, cudaStream_t s);
 template <typename T> void launch_restrict_res(const Lv<T>& F, const Lv<T>& C, cudaStream_t s);
 template <typename T> void launch_restrict_frozen(const Lv<T>& F, const Lv<T>& C, cudaStream_t s);
-template <typename T> void launch_prolong(const Lv<T>& F, const Lv<T>& C, cudaStream_t s);
+template <typename T> void launch_prolong(const Prm<T>& P, const Lv<T>& F, const Lv<T>& C, cudaStream_t s);
 template <typename T> void launch_gauge(const Lv<T>& L, double* part, double* scal, cudaStream_t s);
 template <typename T> void launch_norms_finalize(const Lv<T>& L, double* part, double* out10, cudaStream_t s);
 // Sec. 8 diagnostics of (c, u, v) on level L: out11[0..6] from the cells

@@ -53,6 +53,11 @@ struct Lv {
   // -A rho^n x^n/dt, and Dg, the part of the row's diagonal entry that does not
   // depend on the iterate (the whole diagonal is Dg + A rho(c)/(2dt))
   T *T1u = nullptr, *T1v = nullptr, *T0u = nullptr, *T0v = nullptr, *Dgu = nullptr, *Dgv = nullptr;
+  // FP64 full-iterate levels only: rho(c) of the iterate, ghosts included.
+  // Every kernel that writes c writes rho(c) beside it, so the smoothers and
+  // the residual read the density instead of dividing for it; the values are
+  // those rho_of gives.
+  T* rhoc = nullptr;
   // error-equation (defect-correction) levels only: base state X the iterate
   // e is a correction to, and X.c - c^n formed in FP64 before rounding
   T *Bc = nullptr, *Bmu = nullptr, *Bu = nullptr, *Bv = nullptr, *Bdc = nullptr;
@@ -516,6 +521,7 @@ __device__ __forceinline__ T opd_v(const Prm<T>& P, const Lv<T>& L, int k) {
 // value c, mu that the local Jacobians of the smoothers are evaluated at.
 struct FullForm {
   template <typename T> static __device__ __forceinline__ T val_c(const Lv<T>& L, int k) { return L.c[k]; }
+  template <typename T> static __device__ __forceinline__ T rho(const Prm<T>&, const Lv<T>& L, int k) { return L.rhoc[k]; }
   template <typename T> static __device__ __forceinline__ T val_u(const Lv<T>& L, int k) { return L.u[k]; }
   template <typename T> static __device__ __forceinline__ T val_v(const Lv<T>& L, int k) { return L.v[k]; }
   template <typename T> static __device__ __forceinline__ T val_mu(const Lv<T>& L, int k) { return L.mu[k]; }
@@ -531,6 +537,7 @@ struct FullForm {
 // opp_c_w / opp_p_w directly.
 struct ProjForm {
   template <typename T> static __device__ __forceinline__ T val_c(const Lv<T>& L, int k) { return L.c[k]; }
+  template <typename T> static __device__ __forceinline__ T rho(const Prm<T>&, const Lv<T>& L, int k) { return L.rhoc[k]; }
   template <typename T> static __device__ __forceinline__ T val_u(const Lv<T>& L, int k) { return L.u[k]; }
   template <typename T> static __device__ __forceinline__ T val_v(const Lv<T>& L, int k) { return L.v[k]; }
   template <typename T> static __device__ __forceinline__ T val_mu(const Lv<T>& L, int k) { return L.mu[k]; }
@@ -540,6 +547,7 @@ struct ProjForm {
 };
 struct ErrForm {
   template <typename T> static __device__ __forceinline__ T val_c(const Lv<T>& L, int k) { return L.Bc[k] + L.c[k]; }
+  template <typename T> static __device__ __forceinline__ T rho(const Prm<T>& P, const Lv<T>& L, int k) { return rho_of(P, val_c(L, k)); }
   template <typename T> static __device__ __forceinline__ T val_u(const Lv<T>& L, int k) { return L.Bu[k] + L.u[k]; }
   template <typename T> static __device__ __forceinline__ T val_v(const Lv<T>& L, int k) { return L.Bv[k] + L.v[k]; }
   template <typename T> static __device__ __forceinline__ T val_mu(const Lv<T>& L, int k) { return L.Bmu[k] + L.mu[k]; }

@@ -49,7 +49,7 @@ void dev_free(void* p) {
   else cudaFree(p);
 }
 
-constexpr int NFIELD = 44;  // arrays per level (see Lv)
+constexpr int NFIELD = 45;  // arrays per level (see Lv)
 
 // option "pdl": programmatic dependent launch of every kernel (process-wide)
 static int g_pdl_option = 1;
@@ -250,7 +250,7 @@ int alloc_all(qnsch_s* s) {
                           &L.smu, &L.sp, &L.su,   &L.sv,   &L.cn,   &L.un, &L.vn,  &L.rhon,
                           &L.mobn, &L.visn, &L.Gn, &L.Aru, &L.Arv,  &L.Sx, &L.Sy,  &L.Qx,
                           &L.Qy, &L.Av,  &L.Tx,   &L.Ty,   &L.Dvu,  &L.Dvv, &L.T1u, &L.T1v,
-                          &L.T0u, &L.T0v, &L.Dgu, &L.Dgv};
+                          &L.T0u, &L.T0v, &L.Dgu, &L.Dgv, &L.rhoc};
     for (int q = 0; q < NFIELD; ++q) *f[q] = base + (size_t)q * n + pitch + 1;  // origin (0,0)
     a /= 2;
     b /= 2;
@@ -286,9 +286,9 @@ int alloc_all(qnsch_s* s) {
 }
 
 // error-equation levels: the 38 arrays of a level without the per-step row
-// coefficients (their operators do not use them), plus the base Bc, Bmu, Bu,
-// Bv, Bdc
-constexpr int NFIELD_ERR = NFIELD - 6 + 5;
+// coefficients and rho(c) of the iterate (their operators do not use them),
+// plus the base Bc, Bmu, Bu, Bv, Bdc
+constexpr int NFIELD_ERR = NFIELD - 7 + 5;
 
 template <typename T>
 int alloc_err_levels(qnsch_s* s, std::vector<Lv<T>>& E) {
@@ -433,12 +433,12 @@ void vcycle(qnsch_s* s, const std::vector<Lv<T>>& Ls, const Prm<T>& P, int l) {
   const Lv<T>& F = Ls[l];
   const Lv<T>& C = Ls[l + 1];
   qn::launch_residual<T, Form>(P, F, (double*)nullptr, s->stream);
-  qn::launch_restrict_state(F, C, s->stream);
+  qn::launch_restrict_state(P, F, C, s->stream);
   qn::launch_bc_unknowns(C, s->stream);
   qn::launch_restrict_res(F, C, s->stream);
   qn::launch_add_op<T, Form>(P, C, s->stream);
   vcycle<T, Form>(s, Ls, P, l + 1);
-  qn::launch_prolong(F, C, s->stream);
+  qn::launch_prolong(P, F, C, s->stream);
   qn::launch_bc_unknowns(F, s->stream);
   for (int k = 0; k < s->nu2; ++k) smooth<T, Form>(s, Ls, P, l);
 }
@@ -527,7 +527,9 @@ int copy_fields_in(qnsch_s* s, double* const dst[5], const double* const src[5],
   W.u = dst[2];
   W.v = dst[3];
   W.p = dst[4];
+  if (dst[0] != V.c) W.rhoc = nullptr;  // not the iterate: no density array beside it
   qn::launch_bc_unknowns(W, s->stream);
+  if (dst[0] == V.c) qn::launch_rho_fill(make_prm(s), V, s->stream);
   return sync(s);
 }
 
@@ -566,6 +568,7 @@ int begin(qnsch_s* s, double dt) {
   cudaMemcpyAsync(F.cn - pitch - 1, s->sc - pitch - 1, bytes, cudaMemcpyDeviceToDevice, s->stream);
   cudaMemcpyAsync(F.un - pitch - 1, s->su - pitch - 1, bytes, cudaMemcpyDeviceToDevice, s->stream);
   cudaMemcpyAsync(F.vn - pitch - 1, s->sv - pitch - 1, bytes, cudaMemcpyDeviceToDevice, s->stream);
+  qn::launch_rho_fill(P, F, s->stream);
   qn::launch_frozen(P, F, s->stream);
   for (int l = 1; l < s->nlev; ++l) {
     qn::launch_restrict_frozen(s->L[l - 1], s->L[l], s->stream);
@@ -594,7 +597,7 @@ void correction_cycle(qnsch_s* s, std::vector<Lv<T>>& E) {
   qn::launch_start_correction(s->L[0], E[0], s->stream);
   for (int l = 1; l < s->nlev; ++l) qn::launch_restrict_base(E[l - 1], E[l], s->stream);
   vcycle<T, ErrForm>(s, E, P, 0);
-  qn::launch_apply_correction(s->L[0], E[0], s->stream);
+  qn::launch_apply_correction(P64, s->L[0], E[0], s->stream);
 }
 
 // all work of one outer cycle: V-cycle (or defect-correction cycle), gauge,
@@ -718,6 +721,7 @@ void launch_commit(qnsch_s* s) {
     S.p = s->sp;
     S.u = s->su;
     S.v = s->sv;
+    S.rhoc = nullptr;
     qn::launch_bc_unknowns(S, s->stream);
     qn::launch_proj_diss(P, F, s->su, s->sv, s->part, s->scal + 26, s->stream);
   }

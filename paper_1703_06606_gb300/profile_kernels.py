@@ -1,11 +1,14 @@
 """Run single kernels of libqnsch.so on a chosen grid, for profilers (ncu).
 
     python -m paper_1703_06606_gb300.profile_kernels --kernel vanka --m1 1024 --m2 1024 --reps 3
+    python -m paper_1703_06606_gb300.profile_kernels --workload rt --kernel step --precision 1
 
-Sets up the drop workload at the given size, freezes a time step and issues
-`reps` launches of one finest-level kernel (vanka: colour 0 of the Vanka
-smoother; ch: colour 0 of the CH smoother; step: whole time steps, in the
-FP64 (--precision 0) or mixed (--precision 1) path).
+Sets up the drop workload at the given size (default 1024 x 1024), or the
+Rayleigh-Taylor workload at its full 1024 x 4096 size, freezes a time step
+and issues `reps` launches of one finest-level kernel (vanka: colour 0 of the
+Vanka smoother; ch: colour 0 of the CH smoother; residual: the residual and
+its norms; step: whole time steps, in the FP64 (--precision 0) or mixed
+(--precision 1) path).
 """
 from __future__ import annotations
 
@@ -17,14 +20,18 @@ from . import qnsch, workloads
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--kernel", default="vanka", choices=["vanka", "ch", "residual", "step"])
+    ap.add_argument("--workload", default="drop", choices=["drop", "rt"])
     ap.add_argument("--m1", type=int, default=1024)
     ap.add_argument("--m2", type=int, default=1024)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2])
     a = ap.parse_args()
-    P = workloads.rising_drop_256x512()
-    P.m1, P.m2, P.Lx = a.m1, a.m2, 1.0
-    P.init_args = dict(x0=0.5, y0=0.25 * a.m2 / a.m1, R=0.2)
+    if a.workload == "rt":
+        P = workloads.rayleigh_taylor_1024x4096()
+    else:
+        P = workloads.rising_drop_256x512()
+        P.m1, P.m2, P.Lx = a.m1, a.m2, 1.0
+        P.init_args = dict(x0=0.5, y0=0.25 * a.m2 / a.m1, R=0.2)
     s = qnsch.Solver(**P.create_kwargs(), tol=P.tol, precision=a.precision)
     s.set_fields(P.fields())
     if a.kernel == "step":
