@@ -1418,9 +1418,10 @@ __device__ __forceinline__ T mom_residual(const Prm<T>& P, const Lv<T>& L, const
 }
 
 // Vanka block of cell (i,j) by a team of four lanes (lane & 3 = q): lane q
-// builds row q (diagonal entry and residual of edge q: W, E, S, N); the rows
-// are gathered by shuffles and every lane of the team solves the 5x5 system;
-// lane q writes edge q and lane 0 the pressure.  All 32 lanes of the warp
+// builds row q (diagonal entry and residual of edge q: W, E, S, N) and face
+// q's share of the mass row; the team solves the 5x5 system together (each
+// lane its own row of the pair solves); lane q writes edge q and lane 0 the
+// pressure.  All 32 lanes of the warp
 // call this (ok = false: a spare team, which computes on cell (1,1) and
 // stores nothing).
 template <typename T, class Form>
@@ -1454,38 +1455,14 @@ __device__ __forceinline__ void vanka_team(const Prm<T>& P, const Lv<T>& L, int 
   }
   T bq = mom_residual<T, Form>(P, L, R, ke, rl, rr);  // wall edges too (padded arrays), then discarded
   if (!mine) bq = T(0);
-  T A[5][5], b[5];
-#pragma unroll
-  for (int r = 0; r < 5; ++r)
-#pragma unroll
-    for (int c = 0; c < 5; ++c) A[r][c] = T(0);
-#pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    A[r][r] = __shfl_sync(FULL, dq, lead + r);
-    b[r] = __shfl_sync(FULL, bq, lead + r);
-  }
   T vc = vis[k];
   T v3 = vc * P.iRe * ih2 * third;
-  A[0][1] = T(0.5) * L.Sx[k] * ih - vc * P.iRe * ih2 - v3;
-  A[1][0] = -T(0.5) * L.Sx[k] * ih - vc * P.iRe * ih2 - v3;
-  A[0][2] = v3;
-  A[0][3] = -v3;
-  A[1][2] = -v3;
-  A[1][3] = v3;
-  A[0][4] = ih * P.iM;
-  A[1][4] = -ih * P.iM;
-  A[2][3] = T(0.5) * L.Sy[k] * ih - vc * P.iRe * ih2 - v3;
-  A[3][2] = -T(0.5) * L.Sy[k] * ih - vc * P.iRe * ih2 - v3;
-  A[2][0] = v3;
-  A[2][1] = -v3;
-  A[3][0] = -v3;
-  A[3][1] = v3;
-  A[2][4] = ih * P.iM;
-  A[3][4] = -ih * P.iM;
+  const T a = ih * P.iM;
+  // the mass row by faces: lane q takes face q (W, E, S, N) of the cell, the
+  // face of its own edge: its velocity in d.u, its flux of
+  // grad.(A m grad(mu + alpha p)) and, if open, its share of sum A m
+  T A44, b4;
   {
-    // the mass row by faces: lane q takes face q (W, E, S, N) of the cell, the
-    // face of its own edge: its velocity in d.u, its flux of
-    // grad.(A m grad(mu + alpha p)) and, if open, its share of sum A m
     const T* mob = L.mobn;
     const int nq = k + (q == 0 ? -1 : q == 1 ? 1 : q == 2 ? -W : W);
     T am = mob[nq] + mob[k];
@@ -1494,38 +1471,49 @@ __device__ __forceinline__ void vanka_team(const Prm<T>& P, const Lv<T>& L, int 
     f3[1] = T(0.5) * am * ((L.mu[nq] - L.mu[k]) + P.alpha * (L.p[nq] - L.p[k]));
     f3[2] = mine ? am : T(0);
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      f3[a] += __shfl_xor_sync(FULL, f3[a], 1);
-      f3[a] += __shfl_xor_sync(FULL, f3[a], 2);
+    for (int c = 0; c < 3; ++c) {
+      f3[c] += __shfl_xor_sync(FULL, f3[c], 1);
+      f3[c] += __shfl_xor_sync(FULL, f3[c], 2);
     }
-    A[4][0] = -ih;
-    A[4][1] = ih;
-    A[4][2] = -ih;
-    A[4][3] = ih;
-    A[4][4] = T(0.5) * P.alpha * P.alpha * P.iPe * f3[2] * ih2;
-    b[4] = f3[0] * ih - P.alpha * P.iPe * ih2 * f3[1] - L.fp[k];
+    A44 = T(0.5) * P.alpha * P.alpha * P.iPe * f3[2] * ih2;
+    b4 = f3[0] * ih - P.alpha * P.iPe * ih2 * f3[1] - L.fp[k];
   }
-  const bool act[5] = {a0, a1, a2, a3, true};
-#pragma unroll
-  for (int r = 0; r < 4; ++r)
-    if (!act[r]) {
-#pragma unroll
-      for (int c = 0; c < 5; ++c) {
-        A[r][c] = T(0);
-        A[c][r] = T(0);
-      }
-      A[r][r] = T(1);
-    }
-  solve_vanka<T, 5>(A, b, act, v3, ih * P.iM, ih);
+  // The structured solve of solve_vanka, split over the team: the velocity
+  // block is B + v3 w w^T with B block diagonal over the pairs (W, E) and
+  // (S, N).  Lane q forms the 2x2 block of its pair (p0, p1) = (q & 2, q | 1)
+  // exactly as its partner does, and row q of y = B^-1 b and z = B^-1 w; two
+  // butterflies give s = w.z and t = w.y; every lane then has the pressure and
+  // its own edge's correction.  Rows of wall edges are identity rows.
+  const bool odd = q & 1;
+  const bool ap0 = d ? a2 : a0, ap1 = d ? a3 : a1;
+  T dqo = __shfl_xor_sync(FULL, dq, 1), bqo = __shfl_xor_sync(FULL, bq, 1);
+  T D0 = odd ? dqo : dq, D1 = odd ? dq : dqo;
+  T r0 = odd ? bqo : bq, r1 = odd ? bq : bqo;
+  T S = d ? L.Sy[k] : L.Sx[k];
+  T B00 = ap0 ? D0 - v3 : T(1);
+  T B11 = ap1 ? D1 - v3 : T(1);
+  T B01 = (ap0 && ap1) ? T(0.5) * S * ih - vc * P.iRe * ih2 : T(0);
+  T B10 = (ap0 && ap1) ? -T(0.5) * S * ih - vc * P.iRe * ih2 : T(0);
+  T idet = T(1) / (B00 * B11 - B01 * B10);
+  T y = ((odd ? B00 : B11) * (odd ? r1 : r0) - (odd ? B10 : B01) * (odd ? r0 : r1)) * idet;
+  T zn = odd ? ((ap1 ? B00 : T(0)) + (ap0 ? B10 : T(0))) : ((ap0 ? B11 : T(0)) + (ap1 ? B01 : T(0)));
+  T z = (odd ? -zn : zn) * idet;
+  T sdot = odd ? -z : z, tdot = odd ? -y : y;
+  sdot += __shfl_xor_sync(FULL, sdot, 1);
+  tdot += __shfl_xor_sync(FULL, tdot, 1);
+  sdot += __shfl_xor_sync(FULL, sdot, 2);
+  tdot += __shfl_xor_sync(FULL, tdot, 2);
+  T g = T(1) / (T(1) + v3 * sdot);
+  T pr = (b4 + ih * tdot * g) / (A44 + ih * a * sdot * g);
+  T x = y - z * (g * (v3 * tdot + a * pr));
   if (!ok) return;
-  T x = q == 0 ? b[0] : q == 1 ? b[1] : q == 2 ? b[2] : b[3];
   if (mine) {
     if (q == 0) store_u(L, eW, j, L.u[kW] - omega * x);
     else if (q == 1) store_u(L, i, j, L.u[k] - omega * x);
     else if (q == 2) store_v(L, i, j - 1, L.v[k - W] - omega * x);
     else store_v(L, i, j, L.v[k] - omega * x);
   }
-  if (q == 0) store_cell(L, L.p, i, j, L.p[k] - omega * b[4]);
+  if (q == 0) store_cell(L, L.p, i, j, L.p[k] - omega * pr);
 }
 
 // Per-level launch with four lanes per Vanka block (vanka_team): a level whose
