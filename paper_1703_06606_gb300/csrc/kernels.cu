@@ -1417,31 +1417,18 @@ __device__ __forceinline__ T mom_residual(const Prm<T>& P, const Lv<T>& L, const
   return time + conv + press + st + visc + R.grav * R.Arn[k] - R.f[k];
 }
 
-// Vanka block of cell (i,j) by a team of four lanes (lane & 3 = q): lane q
-// builds row q (diagonal entry and residual of edge q: W, E, S, N) and face
-// q's share of the mass row; the team solves the 5x5 system together (each
-// lane its own row of the pair solves); lane q writes edge q and lane 0 the
-// pressure.  All 32 lanes of the warp
-// call this (ok = false: a spare team, which computes on cell (1,1) and
-// stores nothing).
+// Diagonal entry dq and residual bq = N - f (0 on a wall edge) of momentum row
+// q of the Vanka block of cell (i,j), for lane q of a team: direction d (0:
+// x-edge, 1: y-edge), edge index ke.  The x and y rows run the same
+// instruction stream on different arrays and strides (mom_row).
 template <typename T, class Form>
-__device__ __forceinline__ void vanka_team(const Prm<T>& P, const Lv<T>& L, int i, int j, bool ok,
-                                           T omega) {
-  const unsigned FULL = 0xffffffffu;
-  const int W = L.pitch;
-  const int lane = threadIdx.x & 31, q = lane & 3, d = q >> 1, lead = lane & ~3;
+__device__ __forceinline__ void team_row(const Prm<T>& P, const Lv<T>& L, int i, int j, int d, int ke,
+                                         bool mine, T& dq, T& bq) {
   const T ih = L.ih, ih2 = L.ih2, third = T(1.0 / 3.0);
-  int k = L.at(i, j);
-  int eW = (L.px && i == 1) ? L.m1 : i - 1;
-  int kW = L.at(eW, j);
-  bool a0 = L.px || i > 1, a1 = L.px || i < L.m1, a2 = j > 1, a3 = j < L.m2;
-  bool mine = q == 0 ? a0 : q == 1 ? a1 : q == 2 ? a2 : a3;
-  int ke = q == 0 ? kW : (q == 2 ? k - W : k);
   MomRow<T> R = mom_row<T, Form>(P, L, d);
   T rl = Form::rho(P, L, ke), rr = Form::rho(P, L, ke + R.s);
   T Ar = T(0.5) * (rl + rr);
   const T* vis = L.visn;
-  T dq;
   if constexpr (std::is_same<Form, ErrForm>::value) {
     // the diagonal from the frozen arrays (error levels carry no row coefficients)
     T gp = d ? ((!L.px && i == L.m1) ? T(2) : T(1)) : ((j == L.m2) ? T(2) : T(1));
@@ -1453,59 +1440,97 @@ __device__ __forceinline__ void vanka_team(const Prm<T>& P, const Lv<T>& L, int 
   } else {
     dq = R.Dg[ke] + T(0.5) * P.idt * Ar;
   }
-  T bq = mom_residual<T, Form>(P, L, R, ke, rl, rr);  // wall edges too (padded arrays), then discarded
+  bq = mom_residual<T, Form>(P, L, R, ke, rl, rr);  // wall edges too (padded arrays), then discarded
   if (!mine) bq = T(0);
-  T vc = vis[k];
-  T v3 = vc * P.iRe * ih2 * third;
-  const T a = ih * P.iM;
+}
+
+// The structured solve of solve_vanka, split over a team of four lanes.  The
+// velocity block is B + v3 w w^T with B block diagonal over the pairs (W, E)
+// and (S, N).  Lane q forms the 2x2 block of its pair (p0, p1) = (q & 2, q | 1)
+// exactly as its partner does, and row q of z = B^-1 w; a butterfly gives
+// s = w.z.  apply() then takes a right-hand side (row rq on lane q, pressure
+// entry r4), forms row q of y = B^-1 r, t = w.y by a butterfly, and returns
+// row q of the solution with the pressure in pr.  Rows of wall edges are
+// identity rows with rq = 0.
+template <typename T>
+struct TeamSolve {
+  T B00, B01, B10, B11, idet, z, g, iden, v3, a, ih;
+  bool odd;
+  __device__ __forceinline__ TeamSolve(const Prm<T>& P, const Lv<T>& L, int q, T dq, bool ap0, bool ap1,
+                                       T S, T vc, T A44) {
+    const unsigned FULL = 0xffffffffu;
+    ih = L.ih;
+    v3 = vc * P.iRe * L.ih2 * T(1.0 / 3.0);
+    a = L.ih * P.iM;
+    odd = q & 1;
+    T dqo = __shfl_xor_sync(FULL, dq, 1);
+    T D0 = odd ? dqo : dq, D1 = odd ? dq : dqo;
+    B00 = ap0 ? D0 - v3 : T(1);
+    B11 = ap1 ? D1 - v3 : T(1);
+    B01 = (ap0 && ap1) ? T(0.5) * S * ih - vc * P.iRe * L.ih2 : T(0);
+    B10 = (ap0 && ap1) ? -T(0.5) * S * ih - vc * P.iRe * L.ih2 : T(0);
+    idet = T(1) / (B00 * B11 - B01 * B10);
+    T zn = odd ? ((ap1 ? B00 : T(0)) + (ap0 ? B10 : T(0))) : ((ap0 ? B11 : T(0)) + (ap1 ? B01 : T(0)));
+    z = (odd ? -zn : zn) * idet;
+    T sdot = odd ? -z : z;
+    sdot += __shfl_xor_sync(FULL, sdot, 1);
+    sdot += __shfl_xor_sync(FULL, sdot, 2);
+    g = T(1) / (T(1) + v3 * sdot);
+    iden = T(1) / (A44 + ih * a * sdot * g);
+  }
+  __device__ __forceinline__ T apply(T rq, T r4, T& pr) const {
+    const unsigned FULL = 0xffffffffu;
+    T rqo = __shfl_xor_sync(FULL, rq, 1);
+    T r0 = odd ? rqo : rq, r1 = odd ? rq : rqo;
+    T y = ((odd ? B00 : B11) * (odd ? r1 : r0) - (odd ? B10 : B01) * (odd ? r0 : r1)) * idet;
+    T tdot = odd ? -y : y;
+    tdot += __shfl_xor_sync(FULL, tdot, 1);
+    tdot += __shfl_xor_sync(FULL, tdot, 2);
+    pr = (r4 + ih * tdot * g) * iden;
+    return y - z * (g * (v3 * tdot + a * pr));
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ T team_sum(T v) {
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  return v + __shfl_xor_sync(0xffffffffu, v, 2);
+}
+
+// Vanka block of cell (i,j) by a team of four lanes (lane & 3 = q): lane q
+// builds row q (diagonal entry and residual of edge q: W, E, S, N) and face
+// q's share of the mass row; the team solves the 5x5 system together
+// (TeamSolve); lane q writes edge q and lane 0 the pressure.  All 32 lanes of
+// the warp call this (ok = false: a spare team, which computes on cell (1,1)
+// and stores nothing).
+template <typename T, class Form>
+__device__ __forceinline__ void vanka_team(const Prm<T>& P, const Lv<T>& L, int i, int j, bool ok,
+                                           T omega) {
+  const int W = L.pitch;
+  const int q = threadIdx.x & 3, d = q >> 1;
+  const T ih = L.ih, ih2 = L.ih2;
+  int k = L.at(i, j);
+  int eW = (L.px && i == 1) ? L.m1 : i - 1;
+  int kW = L.at(eW, j);
+  bool a0 = L.px || i > 1, a1 = L.px || i < L.m1, a2 = j > 1, a3 = j < L.m2;
+  bool mine = q == 0 ? a0 : q == 1 ? a1 : q == 2 ? a2 : a3;
+  int ke = q == 0 ? kW : (q == 2 ? k - W : k);
+  T dq, bq;
+  team_row<T, Form>(P, L, i, j, d, ke, mine, dq, bq);
   // the mass row by faces: lane q takes face q (W, E, S, N) of the cell, the
   // face of its own edge: its velocity in d.u, its flux of
   // grad.(A m grad(mu + alpha p)) and, if open, its share of sum A m
-  T A44, b4;
-  {
-    const T* mob = L.mobn;
-    const int nq = k + (q == 0 ? -1 : q == 1 ? 1 : q == 2 ? -W : W);
-    T am = mob[nq] + mob[k];
-    T f3[3];
-    f3[0] = (q & 1) ? (d ? L.v[k] : L.u[k]) : -(d ? L.v[k - W] : L.u[k - 1]);
-    f3[1] = T(0.5) * am * ((L.mu[nq] - L.mu[k]) + P.alpha * (L.p[nq] - L.p[k]));
-    f3[2] = mine ? am : T(0);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      f3[c] += __shfl_xor_sync(FULL, f3[c], 1);
-      f3[c] += __shfl_xor_sync(FULL, f3[c], 2);
-    }
-    A44 = T(0.5) * P.alpha * P.alpha * P.iPe * f3[2] * ih2;
-    b4 = f3[0] * ih - P.alpha * P.iPe * ih2 * f3[1] - L.fp[k];
-  }
-  // The structured solve of solve_vanka, split over the team: the velocity
-  // block is B + v3 w w^T with B block diagonal over the pairs (W, E) and
-  // (S, N).  Lane q forms the 2x2 block of its pair (p0, p1) = (q & 2, q | 1)
-  // exactly as its partner does, and row q of y = B^-1 b and z = B^-1 w; two
-  // butterflies give s = w.z and t = w.y; every lane then has the pressure and
-  // its own edge's correction.  Rows of wall edges are identity rows.
-  const bool odd = q & 1;
-  const bool ap0 = d ? a2 : a0, ap1 = d ? a3 : a1;
-  T dqo = __shfl_xor_sync(FULL, dq, 1), bqo = __shfl_xor_sync(FULL, bq, 1);
-  T D0 = odd ? dqo : dq, D1 = odd ? dq : dqo;
-  T r0 = odd ? bqo : bq, r1 = odd ? bq : bqo;
-  T S = d ? L.Sy[k] : L.Sx[k];
-  T B00 = ap0 ? D0 - v3 : T(1);
-  T B11 = ap1 ? D1 - v3 : T(1);
-  T B01 = (ap0 && ap1) ? T(0.5) * S * ih - vc * P.iRe * ih2 : T(0);
-  T B10 = (ap0 && ap1) ? -T(0.5) * S * ih - vc * P.iRe * ih2 : T(0);
-  T idet = T(1) / (B00 * B11 - B01 * B10);
-  T y = ((odd ? B00 : B11) * (odd ? r1 : r0) - (odd ? B10 : B01) * (odd ? r0 : r1)) * idet;
-  T zn = odd ? ((ap1 ? B00 : T(0)) + (ap0 ? B10 : T(0))) : ((ap0 ? B11 : T(0)) + (ap1 ? B01 : T(0)));
-  T z = (odd ? -zn : zn) * idet;
-  T sdot = odd ? -z : z, tdot = odd ? -y : y;
-  sdot += __shfl_xor_sync(FULL, sdot, 1);
-  tdot += __shfl_xor_sync(FULL, tdot, 1);
-  sdot += __shfl_xor_sync(FULL, sdot, 2);
-  tdot += __shfl_xor_sync(FULL, tdot, 2);
-  T g = T(1) / (T(1) + v3 * sdot);
-  T pr = (b4 + ih * tdot * g) / (A44 + ih * a * sdot * g);
-  T x = y - z * (g * (v3 * tdot + a * pr));
+  const T* mob = L.mobn;
+  const int nq = k + (q == 0 ? -1 : q == 1 ? 1 : q == 2 ? -W : W);
+  T am = mob[nq] + mob[k];
+  T f0 = team_sum<T>((q & 1) ? (d ? L.v[k] : L.u[k]) : -(d ? L.v[k - W] : L.u[k - 1]));
+  T f1 = team_sum<T>(T(0.5) * am * ((L.mu[nq] - L.mu[k]) + P.alpha * (L.p[nq] - L.p[k])));
+  T f2 = team_sum<T>(mine ? am : T(0));
+  T A44 = T(0.5) * P.alpha * P.alpha * P.iPe * f2 * ih2;
+  T b4 = f0 * ih - P.alpha * P.iPe * ih2 * f1 - L.fp[k];
+  TeamSolve<T> ts(P, L, q, dq, d ? a2 : a0, d ? a3 : a1, d ? L.Sy[k] : L.Sx[k], L.visn[k], A44);
+  T pr;
+  T x = ts.apply(bq, b4, pr);
   if (!ok) return;
   if (mine) {
     if (q == 0) store_u(L, eW, j, L.u[kW] - omega * x);
@@ -1516,10 +1541,144 @@ __device__ __forceinline__ void vanka_team(const Prm<T>& P, const Lv<T>& L, int 
   if (q == 0) store_cell(L, L.p, i, j, L.p[k] - omega * pr);
 }
 
+// Coupled 7x7 block of coupled_cell by a team of four lanes (lane & 3 = q:
+// edge and face W, E, S, N).  Lane q builds momentum row q, face q's terms of
+// the mass row, of N_c, N_mu and of the CH Jacobian's face sums, and the
+// couplings of edge q; butterflies add the face terms and every lane forms
+// the cell terms.  The solve follows solve_coupled7: the NS block's
+// structured solve (TeamSolve) applied to three right-hand sides, then the
+// 2x2 Schur system for (dc, dmu).  Lane q writes edge q, lane 0 c, mu, p.
+template <typename T, class Form>
+__device__ __forceinline__ void coupled_team(const Prm<T>& P, const Lv<T>& L, int i, int j, bool ok,
+                                             T omega) {
+  const int W = L.pitch;
+  const int q = threadIdx.x & 3, d = q >> 1;
+  const T ih = L.ih, ih2 = L.ih2;
+  int k = L.at(i, j);
+  int eW = (L.px && i == 1) ? L.m1 : i - 1;
+  int kW = L.at(eW, j);
+  bool a0 = L.px || i > 1, a1 = L.px || i < L.m1, a2 = j > 1, a3 = j < L.m2;
+  bool mine = q == 0 ? a0 : q == 1 ? a1 : q == 2 ? a2 : a3;
+  int ke = q == 0 ? kW : (q == 2 ? k - W : k);
+  T dq, bq;
+  team_row<T, Form>(P, L, i, j, d, ke, mine, dq, bq);
+  const T *mob = L.mobn, *cn = L.cn, *rn = L.rhon;
+  const int nq = k + (q == 0 ? -1 : q == 1 ? 1 : q == 2 ? -W : W);
+  // full values at the cell and at the face's neighbour
+  T ck = Form::val_c(L, k), cnk = cn[k], mk = Form::val_mu(L, k), rnk = rn[k];
+  T rho = Form::rho(P, L, k);
+  T cq = Form::val_c(L, nq), rq = Form::rho(P, L, nq);
+  T drho = -P.alpha * rho * rho;
+  T rh = T(0.5) * (rho + rnk);
+  T chk = ck + cnk;
+  T am = mob[nq] + mob[k];
+  const int kf = q == 0 ? k - 1 : (q == 2 ? k - W : k);  // edge q seen from the cell
+  T gq = rn[nq] * (d ? L.Ty[kf] : L.Tx[kf]);  // rho^n D c^n / 2 at face q
+  T dlt = cq - ck;
+  // face sums: d.u, diffusion flux (mass row and N_c), sum A m over open faces,
+  // advection of N_c, and the CH Jacobian's G, dG/dc and d(div)/dc terms
+  T sdiv = team_sum<T>((q & 1) ? (d ? L.v[k] : L.u[k]) : -(d ? L.v[k - W] : L.u[k - 1]));
+  T sflux = team_sum<T>(T(0.5) * am * ((L.mu[nq] - L.mu[k]) + P.alpha * (L.p[nq] - L.p[k])));
+  T sm = team_sum<T>(mine ? am : T(0));
+  T sadv = team_sum<T>(gq * (d ? L.v[kf] : L.u[kf]));
+  T G2 = team_sum<T>(dlt * dlt);
+  T dG = team_sum<T>(mine ? -dlt : T(0));
+  T dd = team_sum<T>(mine ? T(0.5) * drho * ((cq + cn[nq]) - chk) - (rh + T(0.5) * (rq + rn[nq])) : T(0));
+  T Nc, Nm;
+  if constexpr (std::is_same<Form, ErrForm>::value) {
+    // opd_c and opd_mu by faces
+    const T *e = L.c, *B = L.Bc;
+    T ek = e[k], Ck = B[k];
+    T rC = rho_of(P, Ck);
+    Nc = ek * (rho + rsec_(P, rho, rC) * L.Bdc[k]) * P.idt + sadv - P.iPe * ih2 * sflux;
+    T dC = B[nq] - Ck, de = e[nq] - ek;
+    T rCq = rho_of(P, B[nq]);
+    T dr = rsec_(P, rho, rC) * ek;
+    T drq = rsec_(P, rq, rCq) * e[nq];
+    T chP = Ck + cnk;
+    T sdGe = team_sum<T>(de * (T(2) * dC + de));
+    T sGC = team_sum<T>(dC * dC);
+    T sddiv = team_sum<T>((rh + T(0.5) * (rq + rn[nq])) * de + T(0.5) * (dr + drq) * ((B[nq] + cn[nq]) - chP));
+    T r_new = rsec_(P, rho, rnk);
+    T d_r = -P.alpha * rnk * dr;
+    T dF = gsec(ck, Ck) * ek;
+    T dbulk = rh * dgsec(Ck, cnk, ek) + T(0.5) * dr * gsec(Ck, cnk) + T(0.5) * dF * r_new +
+              T(0.5) * (Fdw(Ck) + Fdw(cnk)) * d_r;
+    T dgrad = T(0.25) * P.Lam * (T(0.5) * sdGe * ih2 * r_new + (T(0.5) * sGC * ih2 + L.Gn[k]) * d_r);
+    Nm = rho * L.mu[k] + dr * L.Bmu[k] - P.K * dbulk - dgrad + P.Lam * T(0.25) * ih2 * sddiv;
+  } else {
+    // op_c and op_mu by faces
+    Nc = rho * (ck - cnk) * P.idt + sadv - P.iPe * ih2 * sflux;
+    T sdv = team_sum<T>((rh + T(0.5) * (rq + rn[nq])) * ((cq + cn[nq]) - chk));
+    T r = -P.alpha * rho * rnk;
+    T bulk = rh * gsec(ck, cnk) + T(0.5) * (Fdw(ck) + Fdw(cnk)) * r;
+    T grad = T(0.25) * P.Lam * (T(0.5) * G2 * ih2 + L.Gn[k]) * r;
+    Nm = rho * mk - P.K * bulk - grad + P.Lam * T(0.25) * ih2 * sdv;
+  }
+  T Rc = Nc - L.fc[k], Rm = Nm - L.fmu[k];
+  // the CH Jacobian (ch_system)
+  T r = -P.alpha * rho * rnk, drr = -P.alpha * drho * rnk;
+  T J11 = (rho + drho * (ck - cnk)) * P.idt;
+  T J12 = T(0.5) * sm * P.iPe * ih2;
+  T Gs = T(0.5) * G2 * ih2 + L.Gn[k];
+  T dbulkJ = T(0.5) * drho * gsec(ck, cnk) + rh * gsec_da(ck, cnk) + T(0.5) * fdw(ck) * r +
+             T(0.5) * (Fdw(ck) + Fdw(cnk)) * drr;
+  T dgradJ = T(0.25) * P.Lam * (dG * ih2 * r + Gs * drr);
+  T J21 = drho * mk - P.K * dbulkJ - dgradJ + P.Lam * T(0.25) * ih2 * dd;
+  T J22 = rho;
+  // the mass row and the couplings of edge q: d N_q/dc, d N_q/dmu (rows of
+  // the two CH columns), d N_c/d x_q = g_q (the CH row), d N_p/dmu = d N_c/dp
+  T A44 = T(0.5) * P.alpha * P.alpha * P.iPe * sm * ih2;
+  T b4 = sdiv * ih - P.alpha * P.iPe * ih2 * sflux - L.fp[k];
+  T diffc = T(0.5) * P.alpha * P.iPe * sm * ih2;
+  T gm = mine ? gq : T(0);
+  T cq0 = mine ? T(0.25) * drho * P.idt * (d ? Form::val_v(L, ke) : Form::val_u(L, ke)) : T(0);
+  T cq1 = mine ? -gq * P.iM : T(0);
+  TeamSolve<T> ts(P, L, q, dq, d ? a2 : a0, d ? a3 : a1, d ? L.Sy[k] : L.Sx[k], L.visn[k], A44);
+  T p0, p1, p2;
+  T x0 = ts.apply(bq, b4, p0);
+  T x1 = ts.apply(cq0, T(0), p1);
+  T x2 = ts.apply(cq1, diffc, p2);
+  T S00 = J11 - (team_sum<T>(gm * x1) + diffc * p1);
+  T S01 = J12 - (team_sum<T>(gm * x2) + diffc * p2);
+  T rhs0 = Rc - (team_sum<T>(gm * x0) + diffc * p0);
+  T id2 = T(1) / (S00 * J22 - S01 * J21);
+  T dc = (J22 * rhs0 - S01 * Rm) * id2;
+  T dm = (S00 * Rm - J21 * rhs0) * id2;
+  T x = x0 - x1 * dc - x2 * dm;
+  T pr = p0 - p1 * dc - p2 * dm;
+  if (!ok) return;
+  if (mine) {
+    if (q == 0) store_u(L, eW, j, L.u[kW] - omega * x);
+    else if (q == 1) store_u(L, i, j, L.u[k] - omega * x);
+    else if (q == 2) store_v(L, i, j - 1, L.v[k - W] - omega * x);
+    else store_v(L, i, j, L.v[k] - omega * x);
+  }
+  if (q == 0) {
+    T cnew = L.c[k] - omega * dc;
+    store_cell(L, L.c, i, j, cnew);
+    if constexpr (!std::is_same<Form, ErrForm>::value) store_cell(L, L.rhoc, i, j, rho_of(P, cnew));
+    store_cell(L, L.mu, i, j, L.mu[k] - omega * dm);
+    store_cell(L, L.p, i, j, L.p[k] - omega * pr);
+  }
+}
+
 // Per-level launch with four lanes per Vanka block (vanka_team): a level whose
 // colour leaves most SM sub-partitions idle runs each block's critical path
 // split over four lanes.  Whole warps past the last team return together, so
 // every warp that calls vanka_team has all 32 lanes in it.
+template <typename T, class Form>
+__global__ void __launch_bounds__(SNT) k_coupled_team(Prm<T> P, Lv<T> L, int colour, T omega) {
+  pdl_enter();
+  ColourSlots cs = vanka_slots(L, colour);
+  int t = blockIdx.x * SNT + threadIdx.x;
+  if ((t & ~31) >= 4 * cs.n) return;  // warp-uniform
+  int i = 1, j = 1;
+  bool ok = (t >> 2) < cs.n && vanka_slot_cell(L, colour, cs, t >> 2, i, j);
+  if (!ok) i = j = 1;
+  coupled_team<T, Form>(P, L, i, j, ok, omega);
+}
+
 template <typename T, class Form>
 __global__ void __launch_bounds__(SNT) k_vanka_team(Prm<T> P, Lv<T> L, int colour, T omega) {
   pdl_enter();
@@ -1570,9 +1729,20 @@ __device__ void smooth_block(const Prm<T>& P, const Lv<T>& L, T omega, int coupl
   if (coupled) {
     for (int col = 0; col < kcol; ++col) {
       ColourSlots cs = vanka_slots(L, col);
-      for (int t = threadIdx.x; t < cs.n; t += blockDim.x) {
-        int i, j;
-        if (vanka_slot_cell(L, col, cs, t, i, j)) coupled_cell<T, Form>(P, L, i, j, omega);
+      // four lanes per block while the colour fits the block in one pass
+      if (4 * cs.n <= (int)blockDim.x) {
+        int t = threadIdx.x;
+        if ((t & ~31) < 4 * cs.n) {  // warp-uniform: the warp holds at least one team
+          int i = 1, j = 1;
+          bool ok = (t >> 2) < cs.n && vanka_slot_cell(L, col, cs, t >> 2, i, j);
+          if (!ok) i = j = 1;
+          coupled_team<T, Form>(P, L, i, j, ok, omega);
+        }
+      } else {
+        for (int t = threadIdx.x; t < cs.n; t += blockDim.x) {
+          int i, j;
+          if (vanka_slot_cell(L, col, cs, t, i, j)) coupled_cell<T, Form>(P, L, i, j, omega);
+        }
       }
       __syncthreads();
     }
@@ -2096,9 +2266,15 @@ void launch_proj_diss(const Prm<T>& P, const Lv<T>& L, const T* uo, const T* vo,
   ++g_launches;
 }
 template <typename T, class Form>
-void launch_coupled(const Prm<T>& P, const Lv<T>& L, int colour, T omega, cudaStream_t s) {
+void launch_coupled(const Prm<T>& P, const Lv<T>& L, int colour, T omega, cudaStream_t s,
+                    int team_max) {
   int n = vanka_slots(L, colour).n;
   if (n <= 0) return;
+  if (n <= team_max) {  // four lanes per block: shorter critical path per visit
+    qlaunch(&k_coupled_team<T, Form>, (4 * n + SNT - 1) / SNT, SNT, 0, s, P, L, colour, omega);
+    ++g_launches;
+    return;
+  }
   qlaunch(&k_coupled<T, Form>, (n + SNT - 1) / SNT, SNT, 0, s, P, L, colour, omega);
   ++g_launches;
 }
@@ -2260,7 +2436,7 @@ int partial_rows_needed(int m1, int m2) {
 #define QN_INSTANTIATE_FORM(T, F)                                                                \
   template void launch_coarse_vcycle<T, F>(const Prm<T>&, const Lv<T>*, int, int, int, int, int,  \
                                            T, int, cudaStream_t);                                \
-  template void launch_coupled<T, F>(const Prm<T>&, const Lv<T>&, int, T, cudaStream_t);          \
+  template void launch_coupled<T, F>(const Prm<T>&, const Lv<T>&, int, T, cudaStream_t, int);     \
   template void launch_residual<T, F>(const Prm<T>&, const Lv<T>&, double*, cudaStream_t);       \
   template void launch_add_op<T, F>(const Prm<T>&, const Lv<T>&, cudaStream_t);                  \
   template void launch_ch<T, F>(const Prm<T>&, const Lv<T>&, int, cudaStream_t, int);            \

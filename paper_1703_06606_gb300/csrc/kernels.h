@@ -28,7 +28,8 @@ void launch_coarse_vcycle(const Prm<T>& P, const Lv<T>* levels, int n, int nu1, 
                           int kcol, T omega, int coupled, cudaStream_t s);
 // one colour of the coupled 7x7 smoother (option "coupled")
 template <typename T, class Form>
-void launch_coupled(const Prm<T>& P, const Lv<T>& L, int colour, T omega, cudaStream_t s);
+void launch_coupled(const Prm<T>& P, const Lv<T>& L, int colour, T omega, cudaStream_t s,
+                    int team_max = 0);
 // projection method (Sec. 7.2): 4x4 intermediate-velocity blocks of one Vanka
 // colour; pressure Gauss-Seidel on one red-black colour; the projected velocity
 // u^{n+1}, v^{n+1} into uo, vo (level layout, interior and boundary edges); the

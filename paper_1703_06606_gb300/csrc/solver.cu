@@ -108,7 +108,7 @@ struct qnsch_s {
   int precision = 0;
   // levels with at most this many cells run as one fused single-block V-cycle
   // (0: never); separate thresholds for FP64 and FP32 levels
-  int fuse64 = 128, fuse32 = 2048;
+  int fuse64 = 128, fuse32 = 512;
   // 0: the paper's separate CH and Vanka sweeps; 1: the coupled 7x7 block
   int coupled = 0;
   // 0: the primitive method (Sec. 6.1); 1: the projection method (Sec. 6.2)
@@ -387,7 +387,8 @@ void smooth(qnsch_s* s, const std::vector<Lv<T>>& Ls, const Prm<T>& P, int l) {
       }
     }
     if (rec) cudaEventRecord(s->ev[s->ev_used], s->stream);
-    if (s->coupled) qn::launch_coupled<T, Form>(P, L, c, (T)s->omega, s->stream);
+    if (s->coupled) qn::launch_coupled<T, Form>(P, L, c, (T)s->omega, s->stream,
+                                                std::is_same<Form, ErrForm>::value ? s->team_max32 : s->team_max);
     else qn::launch_vanka<T, Form>(P, L, c, (T)s->omega, s->stream,
                                    std::is_same<Form, ErrForm>::value ? s->team_max32 : s->team_max);
     if (rec) {

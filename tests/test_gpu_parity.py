@@ -392,15 +392,17 @@ def test_rayleigh_taylor_full_size_step(qn, precision):
 
 
 @pytest.mark.parametrize("px", [False, True])
-def test_team_vanka_launches_match_single_lane(qn, px):
-    """Per-level Vanka and CH launches with four lanes per block (vanka_team_max,
-    ch_team_max) do the same arithmetic as one lane per block, with some terms
-    summed in another order: after two V-cycles the iterates agree within the
-    1e-10 parity bar (measured 2e-12)."""
+@pytest.mark.parametrize("coupled", [0, 1])
+def test_team_vanka_launches_match_single_lane(qn, px, coupled):
+    """Per-level Vanka (or coupled-block) and CH launches with four lanes per
+    block (vanka_team_max, ch_team_max) do the same arithmetic as one lane per
+    block, with some terms summed in another order: after two V-cycles the
+    iterates agree within the 1e-10 parity bar (measured 2e-12)."""
     P = W.small_case(128, 192, px)
     out = []
     for tm in (0, 10 ** 9):
-        g = qn.Solver(**P.create_kwargs(), vanka_team_max=tm, ch_team_max=tm)
+        g = qn.Solver(**P.create_kwargs(), vanka_team_max=tm, ch_team_max=tm, coupled=coupled,
+                      fuse_cells=0)
         g.set_fields(P.fields())
         g.begin_step(P.dt)
         for _ in range(2):
@@ -409,16 +411,18 @@ def test_team_vanka_launches_match_single_lane(qn, px):
     same_fields(out[0], out[1], 1e-10)
 
 
+@pytest.mark.parametrize("coupled", [0, 1])
 @pytest.mark.parametrize("precision,tol", [(2, 1e-10), (1, 1e-5)])
-def test_team_vanka_on_error_levels_matches_single_lane(qn, precision, tol):
+def test_team_vanka_on_error_levels_matches_single_lane(qn, precision, tol, coupled):
     """The error-equation levels of the defect correction (FP64 check form and
-    FP32) smoothed with four lanes per Vanka block agree with one lane per
-    block: to the parity bar in FP64, to FP32 rounding in the mixed cycle."""
+    FP32) smoothed with four lanes per Vanka (or coupled) block agree with one
+    lane per block: to the parity bar in FP64, to FP32 rounding in the mixed
+    cycle."""
     P = W.small_case(128, 192, False)
     out = []
     for tm in (0, 10 ** 9):
         g = qn.Solver(**P.create_kwargs(), precision=precision, vanka_team_max32=tm,
-                      fuse_cells32=0)
+                      fuse_cells32=0, coupled=coupled)
         g.set_fields(P.fields())
         g.begin_step(P.dt)
         for _ in range(2):
