@@ -289,73 +289,124 @@ __global__ void __launch_bounds__(64) k_ch(Prm<T> P, Lv<T> L, int colour) {
   ch_cell<T, Form>(P, L, i, j);
 }
 
-// CH step of cell (i,j) by a team of four lanes (lane & 3 = face f: E, W, N, S).
-// Each lane evaluates its face's terms of N_c, N_mu and of the 2x2 Jacobian,
-// with rho(c) of its neighbour; two butterfly shuffles add the face terms;
-// every lane then forms N_c, N_mu, J and solves; lane 0 stores.  All 32 lanes
-// of the warp call this (ok = false: a spare team on cell (1,1), no store).
+// sum over the four lanes of a team (lanes 4t .. 4t+3)
 template <typename T>
-__device__ __forceinline__ void ch_team(const Prm<T>& P, const Lv<T>& L, int i, int j, bool ok) {
-  const unsigned FULL = 0xffffffffu;
+__device__ __forceinline__ T team_sum(T v) {
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  return v + __shfl_xor_sync(0xffffffffu, v, 2);
+}
+
+// The CH rows of cell (i,j) for a team of four lanes (lane & 3 = q: face W,
+// E, S, N; open = face q is not a wall): residuals Rc = N_c - f_c,
+// Rm = N_mu - f_mu and the 2x2 Jacobian of ch_system, and for the coupled
+// block the open-face sum of A m, the diffusion flux sum, d rho/dc and face
+// q's rho^n D c^n / 2.  Lane q evaluates face q's terms of N_c, N_mu (op_c and
+// op_mu, or opd_c and opd_mu on error levels) and of the Jacobian's face
+// sums; butterflies add them and every lane forms the cell terms.
+template <typename T>
+struct ChRows {
+  T Rc, Rm, J11, J12, J21, J22;
+  T sm, sflux, drho, gq;
+};
+
+template <typename T, class Form>
+__device__ __forceinline__ ChRows<T> ch_team_rows(const Prm<T>& P, const Lv<T>& L, int i, int j, int q,
+                                                  bool open) {
   const int W = L.pitch;
-  const int f = threadIdx.x & 3;
+  const int d = q >> 1;
+  const T ih2 = L.ih2;
   int k = L.at(i, j);
-  const int off = f == 0 ? 1 : f == 1 ? -1 : f == 2 ? W : -W;
-  const bool wall = f == 0 ? (!L.px && i == L.m1) : f == 1 ? (!L.px && i == 1) : f == 2 ? (j == L.m2) : (j == 1);
-  const int q = k + off;
-  const int kv = f == 1 ? k - 1 : f == 3 ? k - W : k;  // edge of face f
-  const T *c = L.c, *cn = L.cn, *rn = L.rhon, *mob = L.mobn;
-  T ck = c[k], cnk = cn[k], mk = L.mu[k], rnk = rn[k];
-  T rho = L.rhoc[k];
-  T cq = c[q];
-  T rq = L.rhoc[q];
+  const T *mob = L.mobn, *cn = L.cn, *rn = L.rhon;
+  const int nq = k + (q == 0 ? -1 : q == 1 ? 1 : q == 2 ? -W : W);
+  const int kf = q == 0 ? k - 1 : (q == 2 ? k - W : k);  // edge of face q
+  // full values at the cell and at the face's neighbour
+  T ck = Form::val_c(L, k), cnk = cn[k], mk = Form::val_mu(L, k), rnk = rn[k];
+  T rho = Form::rho(P, L, k);
+  T cq = Form::val_c(L, nq), rq = Form::rho(P, L, nq);
   T drho = -P.alpha * rho * rho;
   T rh = T(0.5) * (rho + rnk);
   T chk = ck + cnk;
-  T d = cq - ck;
-  T am = T(0.5) * (mob[q] + mob[k]);
-  T rqh = T(0.5) * (rq + rn[q]);
-  T cqh = (cq + cn[q]) - chk;
-  T v[8];
-  v[0] = rn[q] * (f < 2 ? L.Tx[kv] : L.Ty[kv]) * (f < 2 ? L.u[kv] : L.v[kv]);  // advection
-  v[1] = am * (L.mu[q] - mk);                                                   // h^2 lap mu
-  v[2] = am * (L.p[q] - L.p[k]);                                                // h^2 lap p
-  v[3] = (rh + rqh) * cqh;                                                      // div term
-  v[4] = d * d;                                                                 // 2 h^2 G(c)
-  v[5] = wall ? T(0) : mob[k] + mob[q];                                         // 2 sum A m
-  v[6] = wall ? T(0) : -d;                                                      // h^2 dG/dc
-  v[7] = wall ? T(0) : T(0.5) * drho * cqh - (rh + rqh);                        // dd
-#pragma unroll
-  for (int a = 0; a < 8; ++a) {
-    v[a] += __shfl_xor_sync(FULL, v[a], 1);
-    v[a] += __shfl_xor_sync(FULL, v[a], 2);
+  T am = mob[nq] + mob[k];
+  T gq = rn[nq] * (d ? L.Ty[kf] : L.Tx[kf]);  // rho^n D c^n / 2 at face q
+  T dlt = cq - ck;
+  // face sums: diffusion flux (N_c and the mass row), sum A m over open faces,
+  // advection of N_c, and the Jacobian's G, dG/dc and d(div)/dc terms
+  T sflux = team_sum<T>(T(0.5) * am * ((L.mu[nq] - L.mu[k]) + P.alpha * (L.p[nq] - L.p[k])));
+  T sm = team_sum<T>(open ? am : T(0));
+  T sadv = team_sum<T>(gq * (d ? L.v[kf] : L.u[kf]));
+  T G2 = team_sum<T>(dlt * dlt);
+  T dG = team_sum<T>(open ? -dlt : T(0));
+  T dd = team_sum<T>(open ? T(0.5) * drho * ((cq + cn[nq]) - chk) - (rh + T(0.5) * (rq + rn[nq])) : T(0));
+  T Nc, Nm;
+  if constexpr (std::is_same<Form, ErrForm>::value) {
+    const T *e = L.c, *B = L.Bc;
+    T ek = e[k], Ck = B[k];
+    T rC = rho_of(P, Ck);
+    Nc = ek * (rho + rsec_(P, rho, rC) * L.Bdc[k]) * P.idt + sadv - P.iPe * ih2 * sflux;
+    T dC = B[nq] - Ck, de = e[nq] - ek;
+    T rCq = rho_of(P, B[nq]);
+    T dr = rsec_(P, rho, rC) * ek;
+    T drq = rsec_(P, rq, rCq) * e[nq];
+    T chP = Ck + cnk;
+    T sdGe = team_sum<T>(de * (T(2) * dC + de));
+    T sGC = team_sum<T>(dC * dC);
+    T sddiv = team_sum<T>((rh + T(0.5) * (rq + rn[nq])) * de + T(0.5) * (dr + drq) * ((B[nq] + cn[nq]) - chP));
+    T r_new = rsec_(P, rho, rnk);
+    T d_r = -P.alpha * rnk * dr;
+    T dF = gsec(ck, Ck) * ek;
+    T dbulk = rh * dgsec(Ck, cnk, ek) + T(0.5) * dr * gsec(Ck, cnk) + T(0.5) * dF * r_new +
+              T(0.5) * (Fdw(Ck) + Fdw(cnk)) * d_r;
+    T dgrad = T(0.25) * P.Lam * (T(0.5) * sdGe * ih2 * r_new + (T(0.5) * sGC * ih2 + L.Gn[k]) * d_r);
+    Nm = rho * L.mu[k] + dr * L.Bmu[k] - P.K * dbulk - dgrad + P.Lam * T(0.25) * ih2 * sddiv;
+  } else {
+    Nc = rho * (ck - cnk) * P.idt + sadv - P.iPe * ih2 * sflux;
+    T sdv = team_sum<T>((rh + T(0.5) * (rq + rn[nq])) * ((cq + cn[nq]) - chk));
+    T r = -P.alpha * rho * rnk;
+    T bulk = rh * gsec(ck, cnk) + T(0.5) * (Fdw(ck) + Fdw(cnk)) * r;
+    T grad = T(0.25) * P.Lam * (T(0.5) * G2 * ih2 + L.Gn[k]) * r;
+    Nm = rho * mk - P.K * bulk - grad + P.Lam * T(0.25) * ih2 * sdv;
   }
-  T r = -P.alpha * rho * rnk, dr = -P.alpha * drho * rnk;
-  T Nc = rho * (ck - cnk) * P.idt + v[0] - P.iPe * L.ih2 * (v[1] + P.alpha * v[2]);
-  T bulk = rh * gsec(ck, cnk) + T(0.5) * (Fdw(ck) + Fdw(cnk)) * r;
-  T Gs = T(0.5) * v[4] * L.ih2 + L.Gn[k];
-  T grad = T(0.25) * P.Lam * Gs * r;
-  T Nm = rho * mk - P.K * bulk - grad + P.Lam * T(0.25) * L.ih2 * v[3];
-  T Rc = Nc - L.fc[k], Rm = Nm - L.fmu[k];
-  T J11 = (rho + drho * (ck - cnk)) * P.idt;
-  T J12 = T(0.5) * v[5] * P.iPe * L.ih2;
-  T dbulk = T(0.5) * drho * gsec(ck, cnk) + rh * gsec_da(ck, cnk) + T(0.5) * fdw(ck) * r +
-            T(0.5) * (Fdw(ck) + Fdw(cnk)) * dr;
-  T dgrad = T(0.25) * P.Lam * (v[6] * L.ih2 * r + Gs * dr);
-  T J21 = drho * mk - P.K * dbulk - dgrad + P.Lam * T(0.25) * L.ih2 * v[7];
-  T J22 = rho;
-  T idet = T(1) / (J11 * J22 - J12 * J21);
-  T dc = (J22 * Rc - J12 * Rm) * idet;
-  T dm = (J11 * Rm - J21 * Rc) * idet;
-  if (ok && f == 0) {
-    store_cell(L, L.c, i, j, ck - dc);
-    store_cell(L, L.rhoc, i, j, rho_of(P, ck - dc));
-    store_cell(L, L.mu, i, j, mk - dm);
+  ChRows<T> R;
+  R.Rc = Nc - L.fc[k];
+  R.Rm = Nm - L.fmu[k];
+  T r = -P.alpha * rho * rnk, drr = -P.alpha * drho * rnk;
+  R.J11 = (rho + drho * (ck - cnk)) * P.idt;
+  R.J12 = T(0.5) * sm * P.iPe * ih2;
+  T Gs = T(0.5) * G2 * ih2 + L.Gn[k];
+  T dbulkJ = T(0.5) * drho * gsec(ck, cnk) + rh * gsec_da(ck, cnk) + T(0.5) * fdw(ck) * r +
+             T(0.5) * (Fdw(ck) + Fdw(cnk)) * drr;
+  T dgradJ = T(0.25) * P.Lam * (dG * ih2 * r + Gs * drr);
+  R.J21 = drho * mk - P.K * dbulkJ - dgradJ + P.Lam * T(0.25) * ih2 * dd;
+  R.J22 = rho;
+  R.sm = sm;
+  R.sflux = sflux;
+  R.drho = drho;
+  R.gq = gq;
+  return R;
+}
+
+// CH step of cell (i,j) by a team of four lanes (ch_team_rows), every lane
+// solving the 2x2 Newton step; lane 0 stores.  All 32 lanes of the warp call
+// this (ok = false: a spare team on cell (1,1), no store).
+template <typename T, class Form>
+__device__ __forceinline__ void ch_team(const Prm<T>& P, const Lv<T>& L, int i, int j, bool ok) {
+  const int q = threadIdx.x & 3;
+  const bool open = q == 0 ? (L.px || i > 1) : q == 1 ? (L.px || i < L.m1) : q == 2 ? j > 1 : j < L.m2;
+  ChRows<T> R = ch_team_rows<T, Form>(P, L, i, j, q, open);
+  T idet = T(1) / (R.J11 * R.J22 - R.J12 * R.J21);
+  T dc = (R.J22 * R.Rc - R.J12 * R.Rm) * idet;
+  T dm = (R.J11 * R.Rm - R.J21 * R.Rc) * idet;
+  if (ok && q == 0) {
+    int k = L.at(i, j);
+    T cnew = L.c[k] - dc;
+    store_cell(L, L.c, i, j, cnew);
+    if constexpr (!std::is_same<Form, ErrForm>::value) store_cell(L, L.rhoc, i, j, rho_of(P, cnew));
+    store_cell(L, L.mu, i, j, L.mu[k] - dm);
   }
 }
 
 // per-level CH launch with four lanes per cell (colour (i + j) % 2, packed)
-template <typename T>
+template <typename T, class Form>
 __global__ void __launch_bounds__(64) k_ch_team(Prm<T> P, Lv<T> L, int colour) {
   pdl_enter();
   int mpr = (L.m1 + 1) / 2;
@@ -371,7 +422,7 @@ __global__ void __launch_bounds__(64) k_ch_team(Prm<T> P, Lv<T> L, int colour) {
     ok = i <= L.m1;
   }
   if (!ok) i = j = 1;
-  ch_team<T>(P, L, i, j, ok);
+  ch_team<T, Form>(P, L, i, j, ok);
 }
 
 // --------------------------------------------------------------------------
@@ -1491,12 +1542,6 @@ struct TeamSolve {
   }
 };
 
-template <typename T>
-__device__ __forceinline__ T team_sum(T v) {
-  v += __shfl_xor_sync(0xffffffffu, v, 1);
-  return v + __shfl_xor_sync(0xffffffffu, v, 2);
-}
-
 // Vanka block of cell (i,j) by a team of four lanes (lane & 3 = q): lane q
 // builds row q (diagonal entry and residual of edge q: W, E, S, N) and face
 // q's share of the mass row; the team solves the 5x5 system together
@@ -1562,77 +1607,17 @@ __device__ __forceinline__ void coupled_team(const Prm<T>& P, const Lv<T>& L, in
   int ke = q == 0 ? kW : (q == 2 ? k - W : k);
   T dq, bq;
   team_row<T, Form>(P, L, i, j, d, ke, mine, dq, bq);
-  const T *mob = L.mobn, *cn = L.cn, *rn = L.rhon;
-  const int nq = k + (q == 0 ? -1 : q == 1 ? 1 : q == 2 ? -W : W);
-  // full values at the cell and at the face's neighbour
-  T ck = Form::val_c(L, k), cnk = cn[k], mk = Form::val_mu(L, k), rnk = rn[k];
-  T rho = Form::rho(P, L, k);
-  T cq = Form::val_c(L, nq), rq = Form::rho(P, L, nq);
-  T drho = -P.alpha * rho * rho;
-  T rh = T(0.5) * (rho + rnk);
-  T chk = ck + cnk;
-  T am = mob[nq] + mob[k];
-  const int kf = q == 0 ? k - 1 : (q == 2 ? k - W : k);  // edge q seen from the cell
-  T gq = rn[nq] * (d ? L.Ty[kf] : L.Tx[kf]);  // rho^n D c^n / 2 at face q
-  T dlt = cq - ck;
-  // face sums: d.u, diffusion flux (mass row and N_c), sum A m over open faces,
-  // advection of N_c, and the CH Jacobian's G, dG/dc and d(div)/dc terms
+  ChRows<T> C = ch_team_rows<T, Form>(P, L, i, j, q, mine);
   T sdiv = team_sum<T>((q & 1) ? (d ? L.v[k] : L.u[k]) : -(d ? L.v[k - W] : L.u[k - 1]));
-  T sflux = team_sum<T>(T(0.5) * am * ((L.mu[nq] - L.mu[k]) + P.alpha * (L.p[nq] - L.p[k])));
-  T sm = team_sum<T>(mine ? am : T(0));
-  T sadv = team_sum<T>(gq * (d ? L.v[kf] : L.u[kf]));
-  T G2 = team_sum<T>(dlt * dlt);
-  T dG = team_sum<T>(mine ? -dlt : T(0));
-  T dd = team_sum<T>(mine ? T(0.5) * drho * ((cq + cn[nq]) - chk) - (rh + T(0.5) * (rq + rn[nq])) : T(0));
-  T Nc, Nm;
-  if constexpr (std::is_same<Form, ErrForm>::value) {
-    // opd_c and opd_mu by faces
-    const T *e = L.c, *B = L.Bc;
-    T ek = e[k], Ck = B[k];
-    T rC = rho_of(P, Ck);
-    Nc = ek * (rho + rsec_(P, rho, rC) * L.Bdc[k]) * P.idt + sadv - P.iPe * ih2 * sflux;
-    T dC = B[nq] - Ck, de = e[nq] - ek;
-    T rCq = rho_of(P, B[nq]);
-    T dr = rsec_(P, rho, rC) * ek;
-    T drq = rsec_(P, rq, rCq) * e[nq];
-    T chP = Ck + cnk;
-    T sdGe = team_sum<T>(de * (T(2) * dC + de));
-    T sGC = team_sum<T>(dC * dC);
-    T sddiv = team_sum<T>((rh + T(0.5) * (rq + rn[nq])) * de + T(0.5) * (dr + drq) * ((B[nq] + cn[nq]) - chP));
-    T r_new = rsec_(P, rho, rnk);
-    T d_r = -P.alpha * rnk * dr;
-    T dF = gsec(ck, Ck) * ek;
-    T dbulk = rh * dgsec(Ck, cnk, ek) + T(0.5) * dr * gsec(Ck, cnk) + T(0.5) * dF * r_new +
-              T(0.5) * (Fdw(Ck) + Fdw(cnk)) * d_r;
-    T dgrad = T(0.25) * P.Lam * (T(0.5) * sdGe * ih2 * r_new + (T(0.5) * sGC * ih2 + L.Gn[k]) * d_r);
-    Nm = rho * L.mu[k] + dr * L.Bmu[k] - P.K * dbulk - dgrad + P.Lam * T(0.25) * ih2 * sddiv;
-  } else {
-    // op_c and op_mu by faces
-    Nc = rho * (ck - cnk) * P.idt + sadv - P.iPe * ih2 * sflux;
-    T sdv = team_sum<T>((rh + T(0.5) * (rq + rn[nq])) * ((cq + cn[nq]) - chk));
-    T r = -P.alpha * rho * rnk;
-    T bulk = rh * gsec(ck, cnk) + T(0.5) * (Fdw(ck) + Fdw(cnk)) * r;
-    T grad = T(0.25) * P.Lam * (T(0.5) * G2 * ih2 + L.Gn[k]) * r;
-    Nm = rho * mk - P.K * bulk - grad + P.Lam * T(0.25) * ih2 * sdv;
-  }
-  T Rc = Nc - L.fc[k], Rm = Nm - L.fmu[k];
-  // the CH Jacobian (ch_system)
-  T r = -P.alpha * rho * rnk, drr = -P.alpha * drho * rnk;
-  T J11 = (rho + drho * (ck - cnk)) * P.idt;
-  T J12 = T(0.5) * sm * P.iPe * ih2;
-  T Gs = T(0.5) * G2 * ih2 + L.Gn[k];
-  T dbulkJ = T(0.5) * drho * gsec(ck, cnk) + rh * gsec_da(ck, cnk) + T(0.5) * fdw(ck) * r +
-             T(0.5) * (Fdw(ck) + Fdw(cnk)) * drr;
-  T dgradJ = T(0.25) * P.Lam * (dG * ih2 * r + Gs * drr);
-  T J21 = drho * mk - P.K * dbulkJ - dgradJ + P.Lam * T(0.25) * ih2 * dd;
-  T J22 = rho;
+  T sm = C.sm, sflux = C.sflux, gq = C.gq;
+  T J11 = C.J11, J12 = C.J12, J21 = C.J21, J22 = C.J22, Rc = C.Rc, Rm = C.Rm;
   // the mass row and the couplings of edge q: d N_q/dc, d N_q/dmu (rows of
   // the two CH columns), d N_c/d x_q = g_q (the CH row), d N_p/dmu = d N_c/dp
   T A44 = T(0.5) * P.alpha * P.alpha * P.iPe * sm * ih2;
   T b4 = sdiv * ih - P.alpha * P.iPe * ih2 * sflux - L.fp[k];
   T diffc = T(0.5) * P.alpha * P.iPe * sm * ih2;
   T gm = mine ? gq : T(0);
-  T cq0 = mine ? T(0.25) * drho * P.idt * (d ? Form::val_v(L, ke) : Form::val_u(L, ke)) : T(0);
+  T cq0 = mine ? T(0.25) * C.drho * P.idt * (d ? Form::val_v(L, ke) : Form::val_u(L, ke)) : T(0);
   T cq1 = mine ? -gq * P.iM : T(0);
   TeamSolve<T> ts(P, L, q, dq, d ? a2 : a0, d ? a3 : a1, d ? L.Sy[k] : L.Sx[k], L.visn[k], A44);
   T p0, p1, p2;
@@ -1752,7 +1737,7 @@ __device__ void smooth_block(const Prm<T>& P, const Lv<T>& L, T omega, int coupl
   constexpr bool team_ok = std::is_same<Form, FullForm>::value && sizeof(T) == 8;
   constexpr bool vteam_ok = team_ok || std::is_same<Form, ErrForm>::value;
   for (int col = 0; col < 2; ++col) {
-    if (team_ok && 4 * mpr * L.m2 <= (int)blockDim.x) {
+    if (vteam_ok && 4 * mpr * L.m2 <= (int)blockDim.x) {
       int t = threadIdx.x;
       if ((t & ~31) < 4 * mpr * L.m2) {  // warp-uniform
         int sl = t >> 2, j = 1, i = 1;
@@ -1763,7 +1748,7 @@ __device__ void smooth_block(const Prm<T>& P, const Lv<T>& L, T omega, int coupl
           ok = i <= L.m1;
         }
         if (!ok) i = j = 1;
-        ch_team<T>(P, L, i, j, ok);
+        ch_team<T, Form>(P, L, i, j, ok);
       }
     } else {
       for (int t = threadIdx.x; t < mpr * L.m2; t += blockDim.x) {
@@ -2201,9 +2186,10 @@ template <typename T, class Form>
 void launch_ch(const Prm<T>& P, const Lv<T>& L, int colour, cudaStream_t s, int team_max) {
   int n = (L.m1 + 1) / 2 * L.m2;
   if (n <= 0) return;
-  if constexpr (std::is_same<Form, FullForm>::value && sizeof(T) == 8) {
+  if constexpr ((std::is_same<Form, FullForm>::value && sizeof(T) == 8) ||
+                std::is_same<Form, ErrForm>::value) {
     if (n <= team_max) {  // four lanes per cell: shorter critical path per visit
-      qlaunch(&k_ch_team<T>, (4 * n + 63) / 64, 64, 0, s, P, L, colour);
+      qlaunch(&k_ch_team<T, Form>, (4 * n + 63) / 64, 64, 0, s, P, L, colour);
       ++g_launches;
       return;
     }

@@ -117,7 +117,7 @@ struct qnsch_s {
   // lanes per block in the per-level launches
   int team_max = 8192;
   // the same for the CH smoother's per-level launches (cells per red-black colour)
-  int ch_team_max = 4096;
+  int ch_team_max = 4096, ch_team_max32 = 0;
   // error-equation levels of the defect correction (latency-bound at every size)
   int team_max32 = 1 << 30;
   // grid
@@ -348,11 +348,12 @@ constexpr int MAX_PROF_EVENTS = 8192;
 template <typename T, class Form>
 void smooth(qnsch_s* s, const std::vector<Lv<T>>& Ls, const Prm<T>& P, int l) {
   const Lv<T>& L = Ls[l];
+  const int ch_max = std::is_same<Form, ErrForm>::value ? s->ch_team_max32 : s->ch_team_max;
   if constexpr (std::is_same<Form, ProjForm>::value) {
     // projection method (Sec. 7.2): CH red-black, the intermediate-velocity
     // blocks over the Vanka colours, pressure Gauss-Seidel red-black
-    qn::launch_ch<T, Form>(P, L, 0, s->stream, s->ch_team_max);
-    qn::launch_ch<T, Form>(P, L, 1, s->stream, s->ch_team_max);
+    qn::launch_ch<T, Form>(P, L, 0, s->stream, ch_max);
+    qn::launch_ch<T, Form>(P, L, 1, s->stream, ch_max);
     for (int c = 0; c < L.kcol; ++c) {
       bool rec = s->prof && l == 0 && s->ev_used + 2 <= MAX_PROF_EVENTS;
       if (rec) {
@@ -374,8 +375,8 @@ void smooth(qnsch_s* s, const std::vector<Lv<T>>& Ls, const Prm<T>& P, int l) {
     return;
   }
   if (!s->coupled) {
-    qn::launch_ch<T, Form>(P, L, 0, s->stream, s->ch_team_max);
-    qn::launch_ch<T, Form>(P, L, 1, s->stream, s->ch_team_max);
+    qn::launch_ch<T, Form>(P, L, 0, s->stream, ch_max);
+    qn::launch_ch<T, Form>(P, L, 1, s->stream, ch_max);
   }
   for (int c = 0; c < L.kcol; ++c) {
     bool rec = s->prof && l == 0 && s->ev_used + 2 <= MAX_PROF_EVENTS;
@@ -862,6 +863,7 @@ int qnsch_set_option(qnsch_t* s, const char* key, double value) {
   } else if (k == "fuse_cells32") s->fuse32 = (int)value;
   else if (k == "vanka_team_max") s->team_max = (int)value;
   else if (k == "ch_team_max") s->ch_team_max = (int)value;
+  else if (k == "ch_team_max32") s->ch_team_max32 = (int)value;
   else if (k == "vanka_team_max32") s->team_max32 = (int)value;
   else if (k == "pdl") {
     g_pdl_option = value != 0.0;
@@ -902,6 +904,7 @@ int qnsch_get_option(const qnsch_t* s, const char* key, double* value) {
   else if (k == "scheme") *value = s->scheme;
   else if (k == "vanka_team_max") *value = s->team_max;
   else if (k == "ch_team_max") *value = s->ch_team_max;
+  else if (k == "ch_team_max32") *value = s->ch_team_max32;
   else if (k == "vanka_team_max32") *value = s->team_max32;
   else if (k == "pdl") *value = g_pdl_option;
   else return QNSCH_EINVAL;

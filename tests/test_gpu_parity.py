@@ -415,14 +415,14 @@ def test_team_vanka_launches_match_single_lane(qn, px, coupled):
 @pytest.mark.parametrize("precision,tol", [(2, 1e-10), (1, 1e-5)])
 def test_team_vanka_on_error_levels_matches_single_lane(qn, precision, tol, coupled):
     """The error-equation levels of the defect correction (FP64 check form and
-    FP32) smoothed with four lanes per Vanka (or coupled) block agree with one
-    lane per block: to the parity bar in FP64, to FP32 rounding in the mixed
-    cycle."""
+    FP32) smoothed with four lanes per Vanka (or coupled) block and per CH cell
+    agree with one lane per block: to the parity bar in FP64, to FP32 rounding
+    in the mixed cycle."""
     P = W.small_case(128, 192, False)
     out = []
     for tm in (0, 10 ** 9):
         g = qn.Solver(**P.create_kwargs(), precision=precision, vanka_team_max32=tm,
-                      fuse_cells32=0, coupled=coupled)
+                      ch_team_max32=tm, fuse_cells32=0, coupled=coupled)
         g.set_fields(P.fields())
         g.begin_step(P.dt)
         for _ in range(2):
