@@ -140,6 +140,7 @@ struct qnsch_s {
   cudaStream_t user_stream = nullptr;  // set by qnsch_set_stream (NULL: legacy default stream)
   cudaStream_t own_stream = nullptr;   // non-blocking stream used when user_stream is NULL
   cudaEvent_t ev_entry = nullptr;      // orders own_stream after the legacy stream at entry
+  cudaEvent_t ev_norms = nullptr;      // recorded after the norms' copy to hbuf (batch polling)
   int pending = 0;
   // one outer cycle captured as a CUDA graph and replayed (option "graphs")
   int use_graphs = 1;
@@ -208,6 +209,8 @@ void free_all(qnsch_s* s) {
   s->ev.clear();
   if (s->ev_entry) cudaEventDestroy(s->ev_entry);
   s->ev_entry = nullptr;
+  if (s->ev_norms) cudaEventDestroy(s->ev_norms);
+  s->ev_norms = nullptr;
   if (s->own_stream) cudaStreamDestroy(s->own_stream);
   s->own_stream = nullptr;
   for (void* b : s->blocks) dev_free(b);
@@ -218,7 +221,8 @@ void free_all(qnsch_s* s) {
 
 int alloc_all(qnsch_s* s) {
   if (cudaStreamCreateWithFlags(&s->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&s->ev_entry, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&s->ev_entry, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->ev_norms, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     return QNSCH_ECUDA;
   }
@@ -477,14 +481,33 @@ void enqueue_norms(qnsch_s* s, const Prm<double>& P) {
   cudaMemcpyAsync(s->hbuf, s->scal, 10 * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
 }
 
-int read_norms(qnsch_s* s, double* norms10) {
-  int rc = sync(s);
-  if (rc) return rc;
+void norms_from_host(const qnsch_s* s, double* norms10) {
   for (int q = 0; q < 5; ++q) {
     norms10[q] = std::sqrt(s->hbuf[5 + q]);
     norms10[5 + q] = s->hbuf[q];
   }
+}
+
+int read_norms(qnsch_s* s, double* norms10) {
+  int rc = sync(s);
+  if (rc) return rc;
+  norms_from_host(s, norms10);
   return QNSCH_OK;
+}
+
+// batch polling: s->ev_norms marks the norms' arrival in s->hbuf.  Returns 1
+// with norms10 filled once they have arrived, 0 while they are on their way,
+// QNSCH_ECUDA if the work before the event failed.
+int poll_norms(qnsch_s* s, double* norms10) {
+  cudaError_t e = cudaEventQuery(s->ev_norms);
+  if (e == cudaErrorNotReady) return 0;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return QNSCH_ECUDA;
+  }
+  if (s->prof) prof_collect(s);
+  norms_from_host(s, norms10);
+  return 1;
 }
 
 // finest residual + norms as [l2 x5, max x5]
@@ -1224,6 +1247,7 @@ int qnsch_batch_step(qnsch_batch_t* B, const double* dt, int* status, int* n_vcy
   for (int a = 0; a < n; ++a)
     if (!(dt[a] > 0) || B->inst[a]->pending) return QNSCH_EINVAL;
   std::vector<int> live(n, 1), cyc(n, 0);
+  std::vector<char> wait(n, 0);
   std::vector<double> res(n, 0.0);
   double nrm[10];
   for (int a = 0; a < n; ++a) {
@@ -1235,36 +1259,35 @@ int qnsch_batch_step(qnsch_batch_t* B, const double* dt, int* status, int* n_vcy
     }
     enqueue_norms(s, make_prm(s));
     s->res_valid = 1;
+    cudaEventRecord(s->ev_norms, s->stream);
+    wait[a] = 1;
   }
-  for (int a = 0; a < n; ++a) {
-    if (!live[a]) continue;
-    status[a] = read_norms(B->inst[a], nrm);
-    res[a] = maxfam(nrm);
-    if (status[a]) live[a] = 0;
-  }
-  // outer cycles: queue one cycle on every unfinished instance, then collect
-  std::vector<char> queued(n, 0);
-  for (;;) {
-    int any = 0;
+  // outer cycles: each instance queues its next cycle as soon as its norms
+  // arrive, so instances of different sizes do not wait for one another
+  for (int pending = 1; pending;) {
+    pending = 0;
     for (int a = 0; a < n; ++a) {
+      if (!wait[a]) continue;
       qnsch_s* s = B->inst[a];
-      queued[a] = live[a] && res[a] == res[a] && res[a] > s->tol && cyc[a] < s->maxcyc;
-      if (!queued[a]) continue;
-      launch_cycle(s);
-      ++cyc[a];
-      any = 1;
-    }
-    if (!any) break;
-    for (int a = 0; a < n; ++a) {
-      if (!queued[a]) continue;
-      qnsch_s* s = B->inst[a];
-      int rc = finish_cycle(s, nrm);
-      if (rc) {
-        status[a] = rc;
+      int got = poll_norms(s, nrm);
+      if (got == 0) {
+        pending = 1;
+        continue;
+      }
+      wait[a] = 0;
+      if (got < 0) {
+        status[a] = got;
         live[a] = 0;
         continue;
       }
       res[a] = maxfam(nrm);
+      if (res[a] == res[a] && res[a] > s->tol && cyc[a] < s->maxcyc) {
+        launch_cycle(s);
+        cudaEventRecord(s->ev_norms, s->stream);
+        ++cyc[a];
+        wait[a] = 1;
+        pending = 1;
+      }
     }
   }
   for (int a = 0; a < n; ++a) {
