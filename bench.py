@@ -67,6 +67,7 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.lines = []
+        self.first = 0
 
     def __enter__(self):
         try:
@@ -79,6 +80,15 @@ class ClockSampler:
         except OSError:
             self.proc = None
         return self
+
+    def ready(self, timeout_s=10.0):
+        """Wait for the sampler's first line (its start-up queries the driver,
+        which should not fall inside the timed region); samples from here on
+        are the ones summarised."""
+        t0 = time.perf_counter()
+        while self.proc and not self.lines and time.perf_counter() - t0 < timeout_s:
+            time.sleep(0.01)
+        self.first = len(self.lines)
 
     def _read(self):
         for ln in self.proc.stdout:
@@ -95,7 +105,8 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        lines = self.lines[self.first:] or self.lines[-1:]
+        for ln in lines:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -173,10 +184,11 @@ def run_ours(args, rank, world, local_rank):
     cyc = []
     s.profile(True)
     l0 = qnsch.kernel_launches()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
     with ClockSampler(local_rank) as clk:
+        clk.ready()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
         for k in range(args.steps):
             flush.fill_(float(k))
             evs[k][0].record(stream)
