@@ -296,6 +296,23 @@ __device__ __forceinline__ T team_sum(T v) {
   return v + __shfl_xor_sync(0xffffffffu, v, 2);
 }
 
+// u^{n+1} at face q (W, E, S, N) of cell k (0 on a wall face), as proj_faces
+// gives it: rho(c) of the cell rk and of the face's neighbour rn
+template <typename T>
+__device__ __forceinline__ T proj_face_team(const Prm<T>& P, const Lv<T>& L, int k, int q, bool open, T rk,
+                                            T rn) {
+  const int d = q >> 1, off = d ? L.pitch : 1;
+  const bool hi = q & 1;  // E or N: the face's velocity sits at k
+  const int a = hi ? k : k - off;
+  const T *vel = d ? L.v : L.u, *c = L.c, *mu = L.mu, *p = L.p;
+  T ra = hi ? rk : rn, rb = hi ? rn : rk;
+  T Ar = T(0.5) * (ra + rb);
+  T dp = (p[a + off] - p[a]) * L.ih;
+  T st = T(0.5) * (rb * mu[a] + ra * mu[a + off]) * (c[a + off] - c[a]) * L.ih;
+  T grav = d ? P.Fr_inv / P.idt : T(0);
+  return open ? vel[a] + (st - dp) * P.iM / (Ar * P.idt) - grav : T(0);
+}
+
 // The CH rows of cell (i,j) for a team of four lanes (lane & 3 = q: face W,
 // E, S, N; open = face q is not a wall): residuals Rc = N_c - f_c,
 // Rm = N_mu - f_mu and the 2x2 Jacobian of ch_system, and for the coupled
@@ -338,7 +355,19 @@ __device__ __forceinline__ ChRows<T> ch_team_rows(const Prm<T>& P, const Lv<T>& 
   T dG = team_sum<T>(open ? -dlt : T(0));
   T dd = team_sum<T>(open ? T(0.5) * drho * ((cq + cn[nq]) - chk) - (rh + T(0.5) * (rq + rn[nq])) : T(0));
   T Nc, Nm;
-  if constexpr (std::is_same<Form, ErrForm>::value) {
+  T wq = T(0), sJ11 = T(0);  // projection method: u^{n+1} at face q, its advection Jacobian
+  if constexpr (std::is_same<Form, ProjForm>::value) {
+    wq = proj_face_team(P, L, k, q, open, rho, rq);
+    // advection a(rho(c) D c u^{n+1}) of (pj-num-phase) by faces
+    T sadvp = team_sum<T>(T(0.5) * rq * ((q & 1) ? (cq - ck) : (ck - cq)) * L.ih * wq);
+    Nc = rnk * (ck - cnk) * P.idt + sadvp - P.iPe * ih2 * sflux;
+    T sdv = team_sum<T>((rh + T(0.5) * (rq + rn[nq])) * ((cq + cn[nq]) - chk));
+    T r = -P.alpha * rho * rnk;
+    T bulk = rh * gsec(ck, cnk) + T(0.5) * (Fdw(ck) + Fdw(cnk)) * r;
+    T grad = T(0.25) * P.Lam * (T(0.5) * G2 * ih2 + L.Gn[k]) * r;
+    Nm = rnk * mk - P.K * bulk - grad + P.Lam * T(0.25) * ih2 * sdv;
+    sJ11 = team_sum<T>(T(0.5) * ((q & 1) ? -rq * wq : rq * wq) * L.ih);
+  } else if constexpr (std::is_same<Form, ErrForm>::value) {
     const T *e = L.c, *B = L.Bc;
     T ek = e[k], Ck = B[k];
     T rC = rho_of(P, Ck);
@@ -378,6 +407,13 @@ __device__ __forceinline__ ChRows<T> ch_team_rows(const Prm<T>& P, const Lv<T>& 
   T dgradJ = T(0.25) * P.Lam * (dG * ih2 * r + Gs * drr);
   R.J21 = drho * mk - P.K * dbulkJ - dgradJ + P.Lam * T(0.25) * ih2 * dd;
   R.J22 = rho;
+  if constexpr (std::is_same<Form, ProjForm>::value) {
+    // ch_system's projection branch: rho^n in the time derivative and in front
+    // of mu; the advection differentiated through D c only
+    R.J11 = rnk * P.idt + sJ11;
+    R.J21 = -P.K * dbulkJ - dgradJ + P.Lam * T(0.25) * ih2 * dd;
+    R.J22 = rnk;
+  }
   R.sm = sm;
   R.sflux = sflux;
   R.drho = drho;
@@ -955,6 +991,46 @@ __device__ __forceinline__ void pgs_cell(const Prm<T>& P, const Lv<T>& L, int i,
   store_cell(L, L.p, i, j, L.p[k] - R / d);
 }
 
+// pgs_cell by a team of four lanes (lane & 3 = q: face W, E, S, N): lane q
+// takes u^{n+1} at face q, its share of the mass row and of the row's
+// derivative in p_ij; butterflies add them; lane 0 stores.
+template <typename T>
+__device__ __forceinline__ void pgs_team(const Prm<T>& P, const Lv<T>& L, int i, int j, bool ok) {
+  const int W = L.pitch;
+  const int q = threadIdx.x & 3;
+  const bool open = q == 0 ? (L.px || i > 1) : q == 1 ? (L.px || i < L.m1) : q == 2 ? j > 1 : j < L.m2;
+  int k = L.at(i, j);
+  const int nq = k + (q == 0 ? -1 : q == 1 ? 1 : q == 2 ? -W : W);
+  T rk = L.rhoc[k], rq = L.rhoc[nq];
+  T wq = proj_face_team(P, L, k, q, open, rk, rq);
+  T am = L.mobn[nq] + L.mobn[k];
+  T sdiv = team_sum<T>((q & 1) ? wq : -wq);
+  T sflux = team_sum<T>(T(0.5) * am * ((L.mu[nq] - L.mu[k]) + P.alpha * (L.p[nq] - L.p[k])));
+  T Ar = T(0.5) * (rk + rq);
+  T sd = team_sum<T>(open ? P.iM / (Ar * P.idt) * L.ih2 + P.alpha * P.alpha * P.iPe * T(0.5) * am * L.ih2 : T(0));
+  T R = sdiv * L.ih - P.alpha * P.iPe * L.ih2 * sflux - L.fp[k];
+  if (ok && q == 0) store_cell(L, L.p, i, j, L.p[k] - R / sd);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(64) k_pgs_team(Prm<T> P, Lv<T> L, int colour) {
+  pdl_enter();
+  int mpr = (L.m1 + 1) / 2;
+  int n = mpr * L.m2;
+  int t = blockIdx.x * 64 + threadIdx.x;
+  if ((t & ~31) >= 4 * n) return;  // warp-uniform
+  int s = t >> 2;
+  int j = 1, i = 1;
+  bool ok = false;
+  if (s < n) {
+    j = s / mpr + 1;
+    i = (((colour - j) & 1) ? 1 : 2) + 2 * (s % mpr);
+    ok = i <= L.m1;
+  }
+  if (!ok) i = j = 1;
+  pgs_team<T>(P, L, i, j, ok);
+}
+
 // cells of colour (i + j) % 2 == colour, packed as in k_ch
 template <typename T>
 __global__ void __launch_bounds__(64) k_pgs(Prm<T> P, Lv<T> L, int colour) {
@@ -1431,7 +1507,9 @@ __device__ __forceinline__ MomRow<T> mom_row(const Prm<T>& P, const Lv<T>& L, in
   R.f = d ? L.fv : L.fu;
   R.s = d ? L.pitch : 1;
   R.t = d ? 1 : L.pitch;
-  R.grav = (d && !std::is_same<Form, ErrForm>::value) ? P.Fr_inv : T(0);
+  // gravity: the primitive momentum row only (the error equation cancels it,
+  // the projection method puts it in the projection equation)
+  R.grav = (d && std::is_same<Form, FullForm>::value) ? P.Fr_inv : T(0);
   return R;
 }
 
@@ -1460,8 +1538,11 @@ __device__ __forceinline__ T mom_residual(const Prm<T>& P, const Lv<T>& L, const
   } else {
     time = ae * R.T1[k] + R.T0[k] + T(0.5) * P.idt * Ar * ae;
   }
-  T press = (L.p[k + s] - L.p[k]) * L.ih * P.iM;
-  T st = -(rn[k + s] * L.mu[k] + rn[k] * L.mu[k + s]) * R.Tf[k] * P.iM;
+  T press = T(0), st = T(0);  // the projection method's intermediate-velocity row has neither
+  if constexpr (!std::is_same<Form, ProjForm>::value) {
+    press = (L.p[k + s] - L.p[k]) * L.ih * P.iM;
+    st = -(rn[k + s] * L.mu[k] + rn[k] * L.mu[k + s]) * R.Tf[k] * P.iM;
+  }
   T vl = vis[k], vr = vis[k + s];
   T visc = -P.iRe * L.ih * ((vr * dr - vl * dl) + (L.Av[k] * Dp - L.Av[k - t] * Dm) +
                             (vr * dvr - vl * dvl) * T(1.0 / 3.0));
@@ -1507,12 +1588,14 @@ template <typename T>
 struct TeamSolve {
   T B00, B01, B10, B11, idet, z, g, iden, v3, a, ih;
   bool odd;
+  // with_p = false: the 4x4 velocity block alone (the projection method's
+  // intermediate-velocity block), solved as solve_vanka<T, 4> does
   __device__ __forceinline__ TeamSolve(const Prm<T>& P, const Lv<T>& L, int q, T dq, bool ap0, bool ap1,
-                                       T S, T vc, T A44) {
+                                       T S, T vc, T A44, bool with_p = true) {
     const unsigned FULL = 0xffffffffu;
     ih = L.ih;
     v3 = vc * P.iRe * L.ih2 * T(1.0 / 3.0);
-    a = L.ih * P.iM;
+    a = with_p ? L.ih * P.iM : T(0);
     odd = q & 1;
     T dqo = __shfl_xor_sync(FULL, dq, 1);
     T D0 = odd ? dqo : dq, D1 = odd ? dq : dqo;
@@ -1527,7 +1610,7 @@ struct TeamSolve {
     sdot += __shfl_xor_sync(FULL, sdot, 1);
     sdot += __shfl_xor_sync(FULL, sdot, 2);
     g = T(1) / (T(1) + v3 * sdot);
-    iden = T(1) / (A44 + ih * a * sdot * g);
+    iden = with_p ? T(1) / (A44 + ih * a * sdot * g) : T(0);
   }
   __device__ __forceinline__ T apply(T rq, T r4, T& pr) const {
     const unsigned FULL = 0xffffffffu;
@@ -1584,6 +1667,33 @@ __device__ __forceinline__ void vanka_team(const Prm<T>& P, const Lv<T>& L, int 
     else store_v(L, i, j, L.v[k] - omega * x);
   }
   if (q == 0) store_cell(L, L.p, i, j, L.p[k] - omega * pr);
+}
+
+// The projection method's 4x4 intermediate-velocity block (vanka4_cell) by a
+// team of four lanes: lane q builds row q (team_row without pressure, surface
+// tension and gravity) and the team solves the block (TeamSolve without the
+// pressure row); lane q writes edge q.
+template <typename T>
+__device__ __forceinline__ void vanka4_team(const Prm<T>& P, const Lv<T>& L, int i, int j, bool ok,
+                                            T omega) {
+  const int W = L.pitch;
+  const int q = threadIdx.x & 3, d = q >> 1;
+  int k = L.at(i, j);
+  int eW = (L.px && i == 1) ? L.m1 : i - 1;
+  int kW = L.at(eW, j);
+  bool a0 = L.px || i > 1, a1 = L.px || i < L.m1, a2 = j > 1, a3 = j < L.m2;
+  bool mine = q == 0 ? a0 : q == 1 ? a1 : q == 2 ? a2 : a3;
+  int ke = q == 0 ? kW : (q == 2 ? k - W : k);
+  T dq, bq;
+  team_row<T, ProjForm>(P, L, i, j, d, ke, mine, dq, bq);
+  TeamSolve<T> ts(P, L, q, dq, d ? a2 : a0, d ? a3 : a1, d ? L.Sy[k] : L.Sx[k], L.visn[k], T(0), false);
+  T pr;
+  T x = ts.apply(bq, T(0), pr);
+  if (!ok || !mine) return;
+  if (q == 0) store_u(L, eW, j, L.u[kW] - omega * x);
+  else if (q == 1) store_u(L, i, j, L.u[k] - omega * x);
+  else if (q == 2) store_v(L, i, j - 1, L.v[k - W] - omega * x);
+  else store_v(L, i, j, L.v[k] - omega * x);
 }
 
 // Coupled 7x7 block of coupled_cell by a team of four lanes (lane & 3 = q:
@@ -1652,6 +1762,18 @@ __device__ __forceinline__ void coupled_team(const Prm<T>& P, const Lv<T>& L, in
 // colour leaves most SM sub-partitions idle runs each block's critical path
 // split over four lanes.  Whole warps past the last team return together, so
 // every warp that calls vanka_team has all 32 lanes in it.
+template <typename T>
+__global__ void __launch_bounds__(SNT) k_vanka4_team(Prm<T> P, Lv<T> L, int colour, T omega) {
+  pdl_enter();
+  ColourSlots cs = vanka_slots(L, colour);
+  int t = blockIdx.x * SNT + threadIdx.x;
+  if ((t & ~31) >= 4 * cs.n) return;  // warp-uniform
+  int i = 1, j = 1;
+  bool ok = (t >> 2) < cs.n && vanka_slot_cell(L, colour, cs, t >> 2, i, j);
+  if (!ok) i = j = 1;
+  vanka4_team<T>(P, L, i, j, ok, omega);
+}
+
 template <typename T, class Form>
 __global__ void __launch_bounds__(SNT) k_coupled_team(Prm<T> P, Lv<T> L, int colour, T omega) {
   pdl_enter();
@@ -1686,27 +1808,63 @@ __device__ void smooth_block(const Prm<T>& P, const Lv<T>& L, T omega, int coupl
     // projection method (Sec. 7.2): CH red-black, intermediate-velocity blocks
     // over the Vanka colours, pressure Gauss-Seidel red-black
     const int mpr = (L.m1 + 1) / 2;
+    // four lanes per cell while a colour fits the block in one pass
+    const bool cteam = 4 * mpr * L.m2 <= (int)blockDim.x;
     for (int col = 0; col < 2; ++col) {
-      for (int t = threadIdx.x; t < mpr * L.m2; t += blockDim.x) {
-        int j = t / mpr + 1;
-        int i = (((col - j) & 1) ? 1 : 2) + 2 * (t % mpr);
-        if (i <= L.m1) ch_cell<T, Form>(P, L, i, j);
+      if (cteam) {
+        int t = threadIdx.x, sl = t >> 2, j = 1, i = 1;
+        bool ok = false;
+        if (sl < mpr * L.m2) {
+          j = sl / mpr + 1;
+          i = (((col - j) & 1) ? 1 : 2) + 2 * (sl % mpr);
+          ok = i <= L.m1;
+        }
+        if (!ok) i = j = 1;
+        if ((t & ~31) < 4 * mpr * L.m2) ch_team<T, Form>(P, L, i, j, ok);  // warp-uniform
+      } else {
+        for (int t = threadIdx.x; t < mpr * L.m2; t += blockDim.x) {
+          int j = t / mpr + 1;
+          int i = (((col - j) & 1) ? 1 : 2) + 2 * (t % mpr);
+          if (i <= L.m1) ch_cell<T, Form>(P, L, i, j);
+        }
       }
       __syncthreads();
     }
     for (int col = 0; col < kcol; ++col) {
       ColourSlots cs = vanka_slots(L, col);
-      for (int t = threadIdx.x; t < cs.n; t += blockDim.x) {
-        int i, j;
-        if (vanka_slot_cell(L, col, cs, t, i, j)) vanka4_cell<T, Form>(P, L, i, j, omega);
+      if (sizeof(T) == 8 && cs.n <= QN_TEAM_MAX_SLOTS) {  // one warp per sub-partition
+        int t = threadIdx.x;
+        if ((t & ~31) < 4 * cs.n) {  // warp-uniform: the warp holds at least one team
+          int i = 1, j = 1;
+          bool ok = (t >> 2) < cs.n && vanka_slot_cell(L, col, cs, t >> 2, i, j);
+          if (!ok) i = j = 1;
+          vanka4_team<T>(P, L, i, j, ok, omega);
+        }
+      } else {
+        for (int t = threadIdx.x; t < cs.n; t += blockDim.x) {
+          int i, j;
+          if (vanka_slot_cell(L, col, cs, t, i, j)) vanka4_cell<T, Form>(P, L, i, j, omega);
+        }
       }
       __syncthreads();
     }
     for (int col = 0; col < 2; ++col) {
-      for (int t = threadIdx.x; t < mpr * L.m2; t += blockDim.x) {
-        int j = t / mpr + 1;
-        int i = (((col - j) & 1) ? 1 : 2) + 2 * (t % mpr);
-        if (i <= L.m1) pgs_cell<T>(P, L, i, j);
+      if (cteam) {
+        int t = threadIdx.x, sl = t >> 2, j = 1, i = 1;
+        bool ok = false;
+        if (sl < mpr * L.m2) {
+          j = sl / mpr + 1;
+          i = (((col - j) & 1) ? 1 : 2) + 2 * (sl % mpr);
+          ok = i <= L.m1;
+        }
+        if (!ok) i = j = 1;
+        if ((t & ~31) < 4 * mpr * L.m2) pgs_team<T>(P, L, i, j, ok);  // warp-uniform
+      } else {
+        for (int t = threadIdx.x; t < mpr * L.m2; t += blockDim.x) {
+          int j = t / mpr + 1;
+          int i = (((col - j) & 1) ? 1 : 2) + 2 * (t % mpr);
+          if (i <= L.m1) pgs_cell<T>(P, L, i, j);
+        }
       }
       __syncthreads();
     }
@@ -2186,8 +2344,7 @@ template <typename T, class Form>
 void launch_ch(const Prm<T>& P, const Lv<T>& L, int colour, cudaStream_t s, int team_max) {
   int n = (L.m1 + 1) / 2 * L.m2;
   if (n <= 0) return;
-  if constexpr ((std::is_same<Form, FullForm>::value && sizeof(T) == 8) ||
-                std::is_same<Form, ErrForm>::value) {
+  if constexpr (sizeof(T) == 8 || std::is_same<Form, ErrForm>::value) {
     if (n <= team_max) {  // four lanes per cell: shorter critical path per visit
       qlaunch(&k_ch_team<T, Form>, (4 * n + 63) / 64, 64, 0, s, P, L, colour);
       ++g_launches;
@@ -2225,16 +2382,29 @@ void launch_coarse_vcycle(const Prm<T>& P, const Lv<T>* levels, int n, int nu1, 
 }
 
 template <typename T, class Form>
-void launch_vanka4(const Prm<T>& P, const Lv<T>& L, int colour, T omega, cudaStream_t s) {
+void launch_vanka4(const Prm<T>& P, const Lv<T>& L, int colour, T omega, cudaStream_t s,
+                   int team_max) {
   int n = vanka_slots(L, colour).n;
   if (n <= 0) return;
+  if constexpr (std::is_same<Form, ProjForm>::value && sizeof(T) == 8) {
+    if (n <= team_max) {  // four lanes per block: shorter critical path per visit
+      qlaunch(&k_vanka4_team<T>, (4 * n + SNT - 1) / SNT, SNT, 0, s, P, L, colour, omega);
+      ++g_launches;
+      return;
+    }
+  }
   qlaunch(&k_vanka4<T, Form>, (n + SNT - 1) / SNT, SNT, 0, s, P, L, colour, omega);
   ++g_launches;
 }
 template <typename T>
-void launch_pgs(const Prm<T>& P, const Lv<T>& L, int colour, cudaStream_t s) {
+void launch_pgs(const Prm<T>& P, const Lv<T>& L, int colour, cudaStream_t s, int team_max) {
   int n = (L.m1 + 1) / 2 * L.m2;
   if (n <= 0) return;
+  if (n <= team_max) {  // four lanes per cell: shorter critical path per visit
+    qlaunch(&k_pgs_team<T>, (4 * n + 63) / 64, 64, 0, s, P, L, colour);
+    ++g_launches;
+    return;
+  }
   qlaunch(&k_pgs<T>, (n + 63) / 64, 64, 0, s, P, L, colour);
   ++g_launches;
 }
@@ -2465,8 +2635,8 @@ template void launch_add_op<double, ProjForm>(const Prm<double>&, const Lv<doubl
 template void launch_ch<double, ProjForm>(const Prm<double>&, const Lv<double>&, int, cudaStream_t,
                                           int);
 template void launch_vanka4<double, ProjForm>(const Prm<double>&, const Lv<double>&, int, double,
-                                              cudaStream_t);
-template void launch_pgs<double>(const Prm<double>&, const Lv<double>&, int, cudaStream_t);
+                                               cudaStream_t, int);
+template void launch_pgs<double>(const Prm<double>&, const Lv<double>&, int, cudaStream_t, int);
 template void launch_proj_velocity<double>(const Prm<double>&, const Lv<double>&, double*, double*,
                                            cudaStream_t);
 template void launch_proj_diss<double>(const Prm<double>&, const Lv<double>&, const double*,

@@ -35,8 +35,10 @@ void launch_coupled(const Prm<T>& P, const Lv<T>& L, int colour, T omega, cudaSt
 // u^{n+1}, v^{n+1} into uo, vo (level layout, interior and boundary edges); the
 // extra dissipation 1/2||sqrt(rho)(u^{n+1} - ut)||^2 into out1
 template <typename T, class Form>
-void launch_vanka4(const Prm<T>& P, const Lv<T>& L, int colour, T omega, cudaStream_t s);
-template <typename T> void launch_pgs(const Prm<T>& P, const Lv<T>& L, int colour, cudaStream_t s);
+void launch_vanka4(const Prm<T>& P, const Lv<T>& L, int colour, T omega, cudaStream_t s,
+                   int team_max = 0);
+template <typename T>
+void launch_pgs(const Prm<T>& P, const Lv<T>& L, int colour, cudaStream_t s, int team_max = 0);
 template <typename T>
 void launch_proj_velocity(const Prm<T>& P, const Lv<T>& L, T* uo, T* vo, cudaStream_t s);
 template <typename T>

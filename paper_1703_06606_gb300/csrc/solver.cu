@@ -368,14 +368,14 @@ void smooth(qnsch_s* s, const std::vector<Lv<T>>& Ls, const Prm<T>& P, int l) {
         }
       }
       if (rec) cudaEventRecord(s->ev[s->ev_used], s->stream);
-      qn::launch_vanka4<T, Form>(P, L, c, (T)s->omega, s->stream);
+      qn::launch_vanka4<T, Form>(P, L, c, (T)s->omega, s->stream, s->team_max);
       if (rec) {
         cudaEventRecord(s->ev[s->ev_used + 1], s->stream);
         s->ev_used += 2;
       }
     }
-    qn::launch_pgs<T>(P, L, 0, s->stream);
-    qn::launch_pgs<T>(P, L, 1, s->stream);
+    qn::launch_pgs<T>(P, L, 0, s->stream, ch_max);
+    qn::launch_pgs<T>(P, L, 1, s->stream, ch_max);
     return;
   }
   if (!s->coupled) {
@@ -1206,7 +1206,8 @@ int qnsch_smooth_vanka(qnsch_t* s, int colour) {
   if (s) s->res_valid = 0;
   if (!s || colour < 0 || colour >= s->kcol) return QNSCH_EINVAL;
   if (!s->pending) return QNSCH_ESTATE;
-  if (s->scheme) qn::launch_vanka4<double, ProjForm>(make_prm(s), s->L[0], colour, s->omega, s->stream);
+  if (s->scheme)
+    qn::launch_vanka4<double, ProjForm>(make_prm(s), s->L[0], colour, s->omega, s->stream, s->team_max);
   else qn::launch_vanka<double, FullForm>(make_prm(s), s->L[0], colour, s->omega, s->stream,
                                           s->team_max);
   return sync(s);

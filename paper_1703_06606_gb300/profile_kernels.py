@@ -9,7 +9,7 @@ and issues `reps` launches of one finest-level kernel (vanka: colour 0 of the
 Vanka smoother; ch: colour 0 of the CH smoother; residual: the residual and
 its norms; step: whole time steps, in the FP64 (--precision 0) or mixed
 (--precision 1) path, with the paper's smoother or the coupled block
-(--coupled 1)).
+(--coupled 1), or the projection method (--scheme 1)).
 """
 from __future__ import annotations
 
@@ -27,6 +27,7 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2])
     ap.add_argument("--coupled", type=int, default=0, choices=[0, 1])
+    ap.add_argument("--scheme", type=int, default=0, choices=[0, 1])
     a = ap.parse_args()
     if a.workload == "rt":
         P = workloads.rayleigh_taylor_1024x4096()
@@ -34,7 +35,8 @@ def main():
         P = workloads.rising_drop_256x512()
         P.m1, P.m2, P.Lx = a.m1, a.m2, 1.0
         P.init_args = dict(x0=0.5, y0=0.25 * a.m2 / a.m1, R=0.2)
-    s = qnsch.Solver(**P.create_kwargs(), tol=P.tol, precision=a.precision, coupled=a.coupled)
+    s = qnsch.Solver(**P.create_kwargs(), tol=P.tol, precision=a.precision, coupled=a.coupled,
+                     scheme=a.scheme)
     s.set_fields(P.fields())
     if a.kernel == "step":
         for _ in range(a.reps):
