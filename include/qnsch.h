@@ -92,7 +92,7 @@ int qnsch_footprint(const qnsch_grid* grid, int precision, size_t* bytes);
    "maxcyc": 50, "omega_vanka": 1, "M": Cn, "eta_st": eta(rho1, rho2),
    "eps_mob": Cn, "precision": 0, "graphs": 1, "fuse_cells": 128,
    "fuse_cells32": 512, "coupled": 0, "scheme": 0, "vanka_team_max": 8192,
-   "ch_team_max": 4096, "vanka_team_max32": 2^30, "ch_team_max32": 0,
+   "ch_team_max": 4096, "vanka_team_max32": 131072, "ch_team_max32": 0,
    "pdl": 1.
    Unknown keys give QNSCH_EINVAL.
    scheme: 0 the primitive method (Sec. 6.1); 1 the projection method
@@ -103,7 +103,8 @@ int qnsch_footprint(const qnsch_grid* grid, int precision, size_t* bytes);
    idle); ch_team_max does the same for the CH 2x2 Newton launches (four lanes
    per cell, one face each); vanka_team_max32 for the Vanka launches on the
    error-equation levels of the defect correction (precision 1 and 2), which
-   are latency-bound at every size, and ch_team_max32 for their CH launches.
+   are latency-bound up to a few hundred thousand cells per colour, and
+   ch_team_max32 for their CH launches.
    vanka_team_max and vanka_team_max32 also choose the four-lane launches of
    the coupled 7x7 block (coupled = 1).
    pdl: 1 launches every kernel with programmatic dependent launch, so that
