@@ -72,6 +72,13 @@ struct Lv {
 template <typename T> __device__ __forceinline__ T rho_of(const Prm<T>& P, T c) {
   return T(1) / (P.ia * c + P.ib);
 }
+// a / b: in FP32 (the error-equation smoothers) the fast division, within 2
+// ulp, whose rounding the FP64 defect correction absorbs; IEEE division in FP64
+template <typename T> __device__ __forceinline__ T qdiv(T a, T b) { return a / b; }
+template <> __device__ __forceinline__ float qdiv(float a, float b) { return __fdividef(a, b); }
+template <> __device__ __forceinline__ float rho_of(const Prm<float>& P, float c) {
+  return qdiv(1.0f, P.ia * c + P.ib);
+}
 template <typename T> __device__ __forceinline__ T visc_of(const Prm<T>& P, T c) {
   return T(1) / (P.va * c + P.vb);
 }
