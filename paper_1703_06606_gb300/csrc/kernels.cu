@@ -1446,10 +1446,41 @@ __global__ void k_prolong(Prm<T> P, Lv<T> F, Lv<T> C) {
 // dozens.  Per-cell work is the same device code as the grid kernels above,
 // in the same colour order, so the results are the same.
 // --------------------------------------------------------------------------
+// coarse base X_H = R X_h (cells: 4-mean; edges: 2 coincident fine edges), one entry
+template <typename T>
+__device__ __forceinline__ void restrict_base_cell(const Lv<T>& F, const Lv<T>& C, int I, int J) {
+  int kc = C.at(I, J);
+  if (I >= 1 && J >= 1) {
+    int kf = F.at(2 * I - 1, 2 * J - 1), W = F.pitch;
+    C.Bc[kc] = T(0.25) * (F.Bc[kf] + F.Bc[kf + 1] + F.Bc[kf + W] + F.Bc[kf + W + 1]);
+    C.Bmu[kc] = T(0.25) * (F.Bmu[kf] + F.Bmu[kf + 1] + F.Bmu[kf + W] + F.Bmu[kf + W + 1]);
+    C.Bdc[kc] = T(0.25) * (F.Bdc[kf] + F.Bdc[kf + 1] + F.Bdc[kf + W] + F.Bdc[kf + W + 1]);
+  }
+  if (J >= 1) {
+    int kf = F.at(2 * I, 2 * J - 1);
+    C.Bu[kc] = T(0.5) * (F.Bu[kf] + F.Bu[kf + F.pitch]);
+  }
+  if (I >= 1) {
+    int kf = F.at(2 * I - 1, 2 * J);
+    C.Bv[kc] = T(0.5) * (F.Bv[kf] + F.Bv[kf + 1]);
+  }
+}
+
+// ghosts of the base arrays
+template <typename T>
+__device__ __forceinline__ void bc_base_cell(const Lv<T>& L, int I, int J) {
+  fill_cell_ghost(L, L.Bc, I, J);
+  fill_cell_ghost(L, L.Bmu, I, J);
+  fill_cell_ghost(L, L.Bdc, I, J);
+  fill_u_ghost(L, L.Bu, I, J);
+  fill_v_ghost(L, L.Bv, I, J);
+}
+
 template <typename T>
 struct CoarseLevels {
   Lv<T> L[QN_MAX_FUSED_LEVELS];
   int n;
+  int base;  // error equation: restrict the base state to L[1..n-1] first
 };
 
 template <typename T>
@@ -1947,6 +1978,21 @@ __global__ void __launch_bounds__(NT) k_coarse_vcycle(Prm<T> P, CoarseLevels<T> 
   pdl_enter();
   const int n = C.n;
   double dummy[10];
+  if (C.base) {
+    for (int l = 1; l < n; ++l) {
+      const Lv<T>& F = C.L[l - 1];
+      const Lv<T>& G = C.L[l];
+      for (int t = threadIdx.x; t < (G.m1 + 1) * (G.m2 + 1); t += NT)
+        restrict_base_cell(F, G, t % (G.m1 + 1), t / (G.m1 + 1));
+      __syncthreads();
+      const int nf = 4 * (G.m1 + 3) + 4 * (G.m2 + 3);
+      for (int t = threadIdx.x; t < nf; t += NT) {
+        int I, J;
+        if (frame_pos(t, G.m1, G.m2, I, J)) bc_base_cell(G, I, J);
+      }
+      __syncthreads();
+    }
+  }
   for (int l = 0; l < n - 1; ++l) {
     const Lv<T>& F = C.L[l];
     const Lv<T>& G = C.L[l + 1];
@@ -2064,21 +2110,7 @@ __global__ void k_restrict_base(Lv<T> F, Lv<T> C) {
   int I = blockIdx.x * BX + threadIdx.x;
   int J = blockIdx.y * BY + threadIdx.y;
   if (I > C.m1 || J > C.m2) return;
-  int kc = C.at(I, J);
-  if (I >= 1 && J >= 1) {
-    int kf = F.at(2 * I - 1, 2 * J - 1), W = F.pitch;
-    C.Bc[kc] = T(0.25) * (F.Bc[kf] + F.Bc[kf + 1] + F.Bc[kf + W] + F.Bc[kf + W + 1]);
-    C.Bmu[kc] = T(0.25) * (F.Bmu[kf] + F.Bmu[kf + 1] + F.Bmu[kf + W] + F.Bmu[kf + W + 1]);
-    C.Bdc[kc] = T(0.25) * (F.Bdc[kf] + F.Bdc[kf + 1] + F.Bdc[kf + W] + F.Bdc[kf + W + 1]);
-  }
-  if (J >= 1) {
-    int kf = F.at(2 * I, 2 * J - 1);
-    C.Bu[kc] = T(0.5) * (F.Bu[kf] + F.Bu[kf + F.pitch]);
-  }
-  if (I >= 1) {
-    int kf = F.at(2 * I - 1, 2 * J);
-    C.Bv[kc] = T(0.5) * (F.Bv[kf] + F.Bv[kf + 1]);
-  }
+  restrict_base_cell(F, C, I, J);
 }
 
 template <typename T>
@@ -2087,12 +2119,9 @@ __global__ void k_bc_base(Lv<T> L) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   int I, J;
   if (!frame_pos(t, L.m1, L.m2, I, J)) return;
-  fill_cell_ghost(L, L.Bc, I, J);
-  fill_cell_ghost(L, L.Bmu, I, J);
-  fill_cell_ghost(L, L.Bdc, I, J);
-  fill_u_ghost(L, L.Bu, I, J);
-  fill_v_ghost(L, L.Bv, I, J);
+  bc_base_cell(L, I, J);
 }
+
 
 // --------------------------------------------------------------------------
 // reductions
@@ -2375,6 +2404,7 @@ void launch_coarse_vcycle(const Prm<T>& P, const Lv<T>* levels, int n, int nu1, 
                           int kcol, T omega, int coupled, cudaStream_t s) {
   CoarseLevels<T> C;
   C.n = n;
+  C.base = std::is_same<Form, ErrForm>::value;
   for (int l = 0; l < n; ++l) C.L[l] = levels[l];
   constexpr int NT = sizeof(T) == 8 ? 256 : 512;
   qlaunch(&k_coarse_vcycle<T, Form, NT>, 1, NT, 0, s, P, C, nu1, nu2, nuc, kcol, omega, coupled);

@@ -620,7 +620,10 @@ void correction_cycle(qnsch_s* s, std::vector<Lv<T>>& E) {
   Prm<double> P64 = make_prm(s);
   Prm<T> P = cast_prm<T>(P64);
   qn::launch_start_correction(s->L[0], E[0], s->stream);
-  for (int l = 1; l < s->nlev; ++l) qn::launch_restrict_base(E[l - 1], E[l], s->stream);
+  // the base state on every level; the single-block V-cycle restricts it to
+  // the levels below its first one itself
+  int f = fused_from(s, E);
+  for (int l = 1; l < s->nlev && l <= f; ++l) qn::launch_restrict_base(E[l - 1], E[l], s->stream);
   vcycle<T, ErrForm>(s, E, P, 0);
   qn::launch_apply_correction(P64, s->L[0], E[0], s->stream);
 }
