@@ -21,7 +21,7 @@ import time
 
 import numpy as np
 
-from . import qnsch, workloads
+from . import autotune, qnsch, workloads
 
 
 @dataclasses.dataclass
@@ -67,11 +67,24 @@ def poisson_requests(n, rate, seed=workloads.SEED, n_min=128, n_max=1024, steps=
 
 
 class Server:
-    def __init__(self, budget_bytes=150e9, max_slots=256, precision=1, coupled=1):
+    def __init__(self, budget_bytes=150e9, max_slots=256, precision=1, coupled=1,
+                 tuned_table=None):
+        """tuned_table: an autotune table (dict, or the path of its JSON file)
+        whose entries give the launch-shape options of matching requests."""
         self.budget = budget_bytes
         self.max_slots = max_slots
         self.precision = precision
         self.coupled = coupled
+        if isinstance(tuned_table, str):
+            tuned_table = autotune.load_table(tuned_table)
+        self.tuned = tuned_table or {}
+        self.device = autotune.device_name() if self.tuned else ""
+
+    def options(self, P):
+        """Launch-shape options of a request from the tuned table ({} if none)."""
+        if not self.tuned:
+            return {}
+        return autotune.lookup(self.tuned, P, self.precision, self.coupled, 0, self.device)
 
     def footprint(self, P):
         return qnsch.footprint(P.m1, P.m2, P.periodic_x, P.levels, self.precision, P.Lx)
@@ -98,7 +111,7 @@ class Server:
                 waiting.pop(0)
                 P = r.problem
                 s = qnsch.Solver(**P.create_kwargs(), tol=P.tol, precision=self.precision,
-                                 coupled=self.coupled)
+                                 coupled=self.coupled, **self.options(P))
                 s.set_fields(P.fields())
                 r.admitted = time.perf_counter() - t0
                 resident.append((r, s, fp))
