@@ -92,7 +92,7 @@ int qnsch_footprint(const qnsch_grid* grid, int precision, size_t* bytes);
    "maxcyc": 50, "omega_vanka": 1, "M": Cn, "eta_st": eta(rho1, rho2),
    "eps_mob": Cn, "precision": 0, "graphs": 1, "fuse_cells": 128,
    "fuse_cells32": 512, "coupled": 0, "scheme": 0, "vanka_team_max": 8192,
-   "ch_team_max": 4096, "vanka_team_max32": 131072, "ch_team_max32": 0,
+   "ch_team_max": 4096, "vanka_team_max32": 65536, "ch_team_max32": 0,
    "pdl": 1.
    Unknown keys give QNSCH_EINVAL.
    scheme: 0 the primitive method (Sec. 6.1); 1 the projection method

@@ -119,7 +119,7 @@ struct qnsch_s {
   // the same for the CH smoother's per-level launches (cells per red-black colour)
   int ch_team_max = 4096, ch_team_max32 = 0;
   // error-equation levels of the defect correction (latency-bound at every size)
-  int team_max32 = 131072;
+  int team_max32 = 65536;
   // grid
   int m1, m2, px, nlev, kcol;
   double h;
