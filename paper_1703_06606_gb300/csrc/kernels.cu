@@ -57,15 +57,24 @@ static void qlaunch(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, 
 // --------------------------------------------------------------------------
 template <int NV>
 __device__ __forceinline__ void block_sum_store(double (&val)[NV], double* part, int nmax_first) {
-  // first `nmax_first` values are reduced with max, the rest with sum
+  // first `nmax_first` values are reduced with max, the rest with sum.  The
+  // max values are non-negative (or NaN), whose bit patterns order as the
+  // values do (a NaN above everything), so the warp stage takes their max as
+  // 64-bit integers, off the FP64 pipe.
   __shared__ double sh[NT / 32][NV];
   int lane = (threadIdx.y * BX + threadIdx.x) & 31, warp = (threadIdx.y * BX + threadIdx.x) >> 5;
 #pragma unroll
   for (int q = 0; q < NV; ++q) {
     double x = val[q];
-    for (int o = 16; o > 0; o >>= 1) {
-      double y = __shfl_down_sync(0xffffffffu, x, o);
-      x = (q < nmax_first) ? fmax(x, y) : x + y;
+    if (q < nmax_first) {
+      long long b = __double_as_longlong(x);
+      for (int o = 16; o > 0; o >>= 1) {
+        long long c = __shfl_down_sync(0xffffffffu, b, o);
+        b = c > b ? c : b;
+      }
+      x = __longlong_as_double(b);
+    } else {
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
     }
     if (lane == 0) sh[warp][q] = x;
   }
