@@ -181,14 +181,35 @@ __device__ __forceinline__ void residual_cell(const Prm<T>& P, const Lv<T>& L, i
   }
 }
 
-template <typename T, int MODE, class Form>
+// ROWS = 2 (large levels): each thread takes rows j and j + BY of a block of
+// 2 BY rows, so that a 256x512 grid fits the GPU in one round of blocks and
+// the norms' reduction is shared by two cells.
+template <typename T, int MODE, class Form, int ROWS>
 __global__ void k_residual(Prm<T> P, Lv<T> L, double* part) {
   pdl_enter();
   int i = blockIdx.x * BX + threadIdx.x + 1;
-  int j = blockIdx.y * BY + threadIdx.y + 1;
+  int j = blockIdx.y * (ROWS * BY) + threadIdx.y + 1;
   double val[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};  // max x5 then sum of squares x5
   if (i <= L.m1 && j <= L.m2) residual_cell<T, MODE, Form>(P, L, i, j, val);
+  if (ROWS == 2 && i <= L.m1 && j + BY <= L.m2) {
+    double v2[10];
+    residual_cell<T, MODE, Form>(P, L, i, j + BY, v2);
+    if (MODE == 0) {
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {  // |r| >= 0 or NaN: the bit patterns order as the values
+        long long a = __double_as_longlong(val[q]), b = __double_as_longlong(v2[q]);
+        val[q] = __longlong_as_double(a > b ? a : b);
+        val[5 + q] += v2[5 + q];
+      }
+    }
+  }
   if (MODE == 0 && part) block_sum_store<10>(val, part, 5);
+}
+
+// rows per residual thread on level L: two on levels of at least 65536 cells
+template <typename T>
+static int residual_rows(const Lv<T>& L) {
+  return (long long)L.m1 * L.m2 >= 65536 ? 2 : 1;
 }
 
 // --------------------------------------------------------------------------
@@ -2370,12 +2391,18 @@ int nparts_cells(const Lv<T>& L) {
 
 template <typename T, class Form>
 void launch_residual(const Prm<T>& P, const Lv<T>& L, double* part, cudaStream_t s) {
-  qlaunch(&k_residual<T, 0, Form>, grid2(L.m1, L.m2), dim3(BX, BY), 0, s, P, L, part);
+  if (residual_rows(L) == 2)
+    qlaunch(&k_residual<T, 0, Form, 2>, grid2(L.m1, (L.m2 + 1) / 2), dim3(BX, BY), 0, s, P, L, part);
+  else
+    qlaunch(&k_residual<T, 0, Form, 1>, grid2(L.m1, L.m2), dim3(BX, BY), 0, s, P, L, part);
   ++g_launches;
 }
 template <typename T, class Form>
 void launch_add_op(const Prm<T>& P, const Lv<T>& L, cudaStream_t s) {
-  qlaunch(&k_residual<T, 1, Form>, grid2(L.m1, L.m2), dim3(BX, BY), 0, s, P, L, nullptr);
+  if (residual_rows(L) == 2)
+    qlaunch(&k_residual<T, 1, Form, 2>, grid2(L.m1, (L.m2 + 1) / 2), dim3(BX, BY), 0, s, P, L, nullptr);
+  else
+    qlaunch(&k_residual<T, 1, Form, 1>, grid2(L.m1, L.m2), dim3(BX, BY), 0, s, P, L, nullptr);
   ++g_launches;
 }
 template <typename T, class Form>
@@ -2566,7 +2593,8 @@ template <typename T>
 void launch_norms_finalize(const Lv<T>& L, double* part, double* out10, cudaStream_t s) {
   // part rows are [max x5, sum of squares x5]; out10 = [l2 x5, max x5] after the
   // host applies sqrt(h^2 *) to the sums; here: out[0..4] = max, out[5..9] = h^2 sum
-  qlaunch(&k_finalize, 1, 256, 0, s, part, nparts_cells(L), 10, 5, (double)L.h * (double)L.h, out10);
+  dim3 g = grid2(L.m1, (L.m2 + residual_rows(L) - 1) / residual_rows(L));  // k_residual's blocks
+  qlaunch(&k_finalize, 1, 256, 0, s, part, (int)(g.x * g.y), 10, 5, (double)L.h * (double)L.h, out10);
   ++g_launches;
 }
 void launch_diag(const Lv<double>& L, const double* c, const double* u, const double* v,
