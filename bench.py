@@ -34,7 +34,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_1703_06606_gb300 import workloads  # noqa: E402
+from paper_1703_06606_gb300 import replicas, workloads  # noqa: E402
 
 METRIC = ("cell-updates/s per time step at residual 1e-9 (FP64 plain vs batched mixed) "
           "+ p99 latency")
@@ -209,11 +209,8 @@ def run_ours(args, rank, world, local_rank):
         s.set_option("graphs", 1)
     s.profile(False)
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    total_s = sum(step_ms) / 1e3
+    total_s = replicas.slowest(sum(step_ms) / 1e3, dev)
     if world > 1:
-        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
         dist.barrier()
 
     # ---- the same workload in the other solver variants: mixed precision (FP32
@@ -240,11 +237,7 @@ def run_ours(args, rank, world, local_rank):
                 vcyc.append(n)
             torch.cuda.synchronize()
             vms = [a.elapsed_time(b) for a, b in vev]
-            vtot = sum(vms) / 1e3
-            if world > 1:
-                t = torch.tensor([vtot], device=dev, dtype=torch.float64)
-                dist.all_reduce(t, op=dist.ReduceOp.MAX)
-                vtot = float(t.item())
+            vtot = replicas.slowest(sum(vms) / 1e3, dev)
             variants[name] = {
                 "value": world * P.cells * args.steps / vtot, "unit": UNIT,
                 "ms_per_step": float(np.mean(vms)),
@@ -358,11 +351,7 @@ def run_ours(args, rank, world, local_rank):
             bad += sum(1 for x in st if x != 0)
             bcyc.append(float(np.mean(cy)))
         bcells = sum(Pb.cells for Pb in probs)
-        btot = sum(bms) / 1e3
-        if world > 1:
-            t = torch.tensor([btot], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            btot = float(t.item())
+        btot = replicas.slowest(sum(bms) / 1e3, dev)
         batched = {"value": world * bcells * args.steps / btot, "unit": UNIT,
                    "instances": len(probs), "cells": bcells,
                    "ms_per_batch_step": float(np.mean(bms)),
@@ -408,11 +397,7 @@ def run_ours(args, rank, world, local_rank):
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
         for q in host_in:
             host_in[q][...] = out[q]
-    e2e_total = sum(e2e_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
+    e2e_total = replicas.slowest(sum(e2e_ms) / 1e3, dev)
 
     if rank != 0:
         if world > 1:
