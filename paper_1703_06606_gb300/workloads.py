@@ -78,9 +78,10 @@ def initial_fields(P: Problem):
     X, Y = cell_centres(P.m1, P.m2, P.h)
     a = P.init_args
     if P.init == "capillary":
-        # interface y = y0 + H0 cos(2 pi x / Lx); c = 1 below (Sec. 8.1 profile)
-        y0, H0 = a.get("y0", 0.5 * P.m2 * P.h), a.get("H0", 0.01)
-        c = _profile(Y - y0 - H0 * np.cos(2.0 * math.pi * X / P.Lx), P.Cn)
+        # interface y = y0 + H0 cos(2 pi k x / Lx), k = 1 unless given; c = 1 below
+        # (Sec. 8.1 profile)
+        y0, H0, kx = a.get("y0", 0.5 * P.m2 * P.h), a.get("H0", 0.01), a.get("k", 1)
+        c = _profile(Y - y0 - H0 * np.cos(2.0 * math.pi * kx * X / P.Lx), P.Cn)
     elif P.init == "drop":
         # circular drop (c = 1) of radius R centred at (x0, y0), Sec. 8.2
         x0, y0, R = a.get("x0", 0.5), a.get("y0", 0.5), a.get("R", 0.25)
