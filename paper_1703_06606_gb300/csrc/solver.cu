@@ -118,7 +118,8 @@ struct qnsch_s {
   int team_max = 8192;
   // the same for the CH smoother's per-level launches (cells per red-black colour)
   int ch_team_max = 4096, ch_team_max32 = 0;
-  // error-equation levels of the defect correction (latency-bound at every size)
+  // the same on the error-equation levels of the defect correction (their
+  // visits are latency-bound up to this size; larger levels stream from HBM)
   int team_max32 = 65536;
   // grid
   int m1, m2, px, nlev, kcol;
