@@ -124,6 +124,20 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def paper_table2():
+    """The paper's Table 2 (Sec. 9), CPU seconds per step of the primitive and
+    the projection method by m, as printed (tests/golden/paper_tables_sec9.txt)."""
+    prim, proj = {}, {}
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden",
+                        "paper_tables_sec9.txt")
+    with open(path) as f:
+        for ln in f:
+            w = ln.split()
+            if w and w[0] == "table2":
+                prim[int(w[1])], proj[int(w[1])] = float(w[2]), float(w[3])
+    return prim, proj
+
+
 # ---------------------------------------------------------------------------
 # the CPU oracle (reference arm and cpu_baseline)
 # ---------------------------------------------------------------------------
@@ -287,8 +301,7 @@ def run_ours(args, rank, world, local_rank):
     # seconds per step of the primitive method, m = 16..256, dt = 16 h^2), FP64
     table2 = None
     if not args.no_table2:
-        paper_s = {16: 2.913e-2, 32: 1.659e-1, 64: 2.659e-1, 128: 1.027, 256: 2.622}
-        paper_proj_s = {16: 1.075e-2, 32: 3.816e-2, 64: 1.149e-1, 128: 4.170e-1, 256: 1.246}
+        paper_s, paper_proj_s = paper_table2()
         table2 = {}
         # the projection column starts at m = 32: at m = 16, dt = 1/16 its point
         # smoothers diverge on this workload (the discrete system itself is
