@@ -92,9 +92,10 @@ def main():
     ap.add_argument("--m", type=int, nargs="+", default=[16, 32, 64, 128, 256])
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--coupled", type=int, default=0)
+    ap.add_argument("--scheme", type=int, default=0)
     a = ap.parse_args()
     from . import qnsch
-    for row in run(qnsch.Solver, a.m, precision=a.precision, coupled=a.coupled):
+    for row in run(qnsch.Solver, a.m, precision=a.precision, coupled=a.coupled, scheme=a.scheme):
         print(json.dumps(row))
 
 

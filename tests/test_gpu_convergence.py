@@ -30,3 +30,13 @@ def test_self_convergence_second_order_to_256(qn):
     e = [r["error"] for r in rows[1:]]
     assert all(e[k + 1] < e[k] for k in range(len(e) - 1)), rows
     assert 1.8 <= rows[-1]["rate"] <= 2.5 and 1.8 <= rows[-2]["rate"] <= 2.5, rows
+
+
+def test_projection_self_convergence_second_order(qn):
+    """The projection method on the same schedule from m = 32 (at m = 16,
+    dt = 1/16 its point smoothers diverge): second-order Cauchy rates, as in
+    the projection column of the paper's Table 1."""
+    rows = convergence.run(qn.Solver, (32, 64, 128, 256), scheme=1)
+    e = [r["error"] for r in rows[1:]]
+    assert all(e[k + 1] < e[k] for k in range(len(e) - 1)), rows
+    assert 1.7 <= rows[-1]["rate"] <= 2.5, rows
