@@ -297,6 +297,37 @@ def run_ours(args, rank, world, local_rank):
                     "final_residual": res, "steps": 5, "tol": Ps.tol}
                 ss.close()
 
+    # ---- the other workloads of Sec. 8 at their sizes: the capillary wave (64^2,
+    # FP64, tol 1e-10) and the Rayleigh-Taylor instability (1024x4096, mixed
+    # precision, the paper's smoother)
+    paper_workloads = None
+    if not args.no_workloads:
+        paper_workloads = {}
+        for Pw, prec, nsteps in ((workloads.capillary_64(), 0, 10),
+                                 (workloads.rayleigh_taylor_1024x4096(), 1, 3)):
+            sw = qnsch.Solver(**Pw.create_kwargs(), tol=Pw.tol, stream=stream, precision=prec)
+            sw.set_fields(Pw.fields())
+            sw.step(Pw.dt)
+            wev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(nsteps)]
+            wcyc = []
+            torch.cuda.synchronize()
+            for k in range(nsteps):
+                flush.fill_(float(k))
+                wev[k][0].record(stream)
+                n, res = sw.step(Pw.dt)
+                wev[k][1].record(stream)
+                wcyc.append(n)
+            torch.cuda.synchronize()
+            wms = [a.elapsed_time(b) for a, b in wev]
+            wtot = replicas.slowest(sum(wms) / 1e3, dev)
+            paper_workloads[Pw.name] = {
+                "value": world * Pw.cells * nsteps / wtot, "unit": UNIT,
+                "ms_per_step": float(np.mean(wms)), "vcycles_per_step": float(np.mean(wcyc)),
+                "precision": "mixed" if prec else "FP64", "steps": nsteps, "tol": Pw.tol,
+                "final_residual": res}
+            sw.close()
+
     # ---- per-step cost on the workload of Sec. 9 (the paper's Table 2: CPU
     # seconds per step of the primitive method, m = 16..256, dt = 16 h^2), FP64
     table2 = None
@@ -449,6 +480,8 @@ def run_ours(args, rank, world, local_rank):
         line["variants"] = variants
     if stress is not None:
         line["stress"] = stress
+    if paper_workloads is not None:
+        line["workloads"] = paper_workloads
     if table2 is not None:
         line["table2"] = table2
     if batched is not None:
@@ -520,6 +553,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-stress", action="store_true")
+    ap.add_argument("--no-workloads", action="store_true")
     ap.add_argument("--no-table2", action="store_true")
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--no-serve", action="store_true")
