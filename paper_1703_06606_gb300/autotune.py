@@ -28,7 +28,7 @@ import time
 CANDIDATES = {
     "vanka_team_max": [8192, 2048, 32768, 0],
     "ch_team_max": [4096, 0, 16384],
-    "fuse_cells": [128, 32, 512],
+    "fuse_cells": [128, 32, 512, 4096],
     "vanka_team_max32": [65536, 0, 8192, 131072, 1 << 30],
     "ch_team_max32": [0, 4096],
     "fuse_cells32": [512, 128, 2048],
