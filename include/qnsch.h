@@ -221,6 +221,16 @@ int qnsch_profile_read(qnsch_t* h, long long* launches, double* total_ms);
 /* Number of CUDA kernels this library has issued since it was loaded
    (process-wide, counted on the host at launch). */
 int qnsch_kernel_launches(long long* n);
+/* FMA throughput probe of the current device (a measurement utility with no
+   counterpart in the paper).  It launches blocks_per_sm x (SM count) blocks of
+   256 threads; each thread runs eight independent chains of 16 x iters fused
+   multiply-adds in FP64 (fp64 != 0) or FP32, and the call times five launches
+   after three untimed ones with CUDA events on the legacy default stream.
+   *tflops receives 2 x FMAs / seconds / 1e12.  It allocates and frees one
+   scratch array of blocks x 256 elements and synchronises before returning.
+   blocks_per_sm must lie in [1, 64] and iters in [1, 2^24], else QNSCH_EINVAL;
+   no device gives QNSCH_ENODEV. */
+int qnsch_fma_probe(int fp64, int blocks_per_sm, int iters, double* tflops);
 
 /* Batches of independent instances (no counterpart in the paper; the way a
    GPU runs many small problems at once).  A batch refers to n existing

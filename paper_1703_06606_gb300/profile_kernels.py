@@ -2,6 +2,7 @@
 
     python -m paper_1703_06606_gb300.profile_kernels --kernel vanka --m1 1024 --m2 1024 --reps 3
     python -m paper_1703_06606_gb300.profile_kernels --workload rt --kernel step --precision 1
+    python -m paper_1703_06606_gb300.profile_kernels --kernel fmapeak
 
 Sets up the drop workload at the given size (default 1024 x 1024), or the
 Rayleigh-Taylor workload at its full 1024 x 4096 size, freezes a time step
@@ -9,7 +10,10 @@ and issues `reps` launches of one finest-level kernel (vanka: colour 0 of the
 Vanka smoother; ch: colour 0 of the CH smoother; residual: the residual and
 its norms; step: whole time steps, in the FP64 (--precision 0) or mixed
 (--precision 1) path, with the paper's smoother or the coupled block
-(--coupled 1), or the projection method (--scheme 1)).
+(--coupled 1), or the projection method (--scheme 1)).  fmapeak times the
+library's FMA throughput probe (qnsch_fma_probe) in FP64 and FP32 over a few
+launch shapes and prints the rates; the best FP64 rate is the peak of the
+FP64 kernels' ALU roofline.
 """
 from __future__ import annotations
 
@@ -20,7 +24,7 @@ from . import qnsch, workloads
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--kernel", default="vanka", choices=["vanka", "ch", "residual", "step"])
+    ap.add_argument("--kernel", default="vanka", choices=["vanka", "ch", "residual", "step", "fmapeak"])
     ap.add_argument("--workload", default="drop", choices=["drop", "rt"])
     ap.add_argument("--m1", type=int, default=1024)
     ap.add_argument("--m2", type=int, default=1024)
@@ -29,6 +33,13 @@ def main():
     ap.add_argument("--coupled", type=int, default=0, choices=[0, 1])
     ap.add_argument("--scheme", type=int, default=0, choices=[0, 1])
     a = ap.parse_args()
+    if a.kernel == "fmapeak":
+        for fp64 in (True, False):
+            rates = {b: qnsch.fma_probe(fp64, b, 1024) for b in (4, 8, 16)}
+            for b, r in rates.items():
+                print("%s blocks/SM %2d: %.4f TFLOP/s" % ("FP64" if fp64 else "FP32", b, r))
+            print("%s best: %.4f TFLOP/s" % ("FP64" if fp64 else "FP32", max(rates.values())))
+        return
     if a.workload == "rt":
         P = workloads.rayleigh_taylor_1024x4096()
     else:

@@ -75,6 +75,7 @@ def lib():
         L.qnsch_profile.argtypes = [_VP, i]
         L.qnsch_profile_read.argtypes = [_VP, ctypes.POINTER(ctypes.c_longlong), p]
         L.qnsch_kernel_launches.argtypes = [ctypes.POINTER(ctypes.c_longlong)]
+        L.qnsch_fma_probe.argtypes = [i, i, i, p]
         L.qnsch_mass_noalloc.argtypes = [_VP, i, i, d, d, d, _VP, _VP]
         L.qnsch_batch_create.argtypes = [i, ctypes.POINTER(_VP), ctypes.POINTER(_VP)]
         L.qnsch_batch_step.argtypes = [_VP, p, ctypes.POINTER(i), ctypes.POINTER(i)]
@@ -90,6 +91,15 @@ def kernel_launches():
     n = ctypes.c_longlong()
     _check(lib().qnsch_kernel_launches(ctypes.byref(n)), "qnsch_kernel_launches")
     return n.value
+
+
+def fma_probe(fp64=True, blocks_per_sm=8, iters=4096):
+    """qnsch_fma_probe: FMA throughput of the current device in TFLOP/s (FP64
+    or FP32), the denominator of the FP64 kernels' ALU roofline."""
+    t = ctypes.c_double()
+    _check(lib().qnsch_fma_probe(int(bool(fp64)), int(blocks_per_sm), int(iters),
+                                 ctypes.byref(t)), "qnsch_fma_probe")
+    return t.value
 
 
 def mass_noalloc(c, h, rho1, rho2, out2, stream=None):

@@ -38,3 +38,19 @@ def test_create_without_device_reports_enodev():
     with pytest.raises(qnsch.QnschError) as e:
         qnsch.Solver(16, 16)
     assert e.value.code == -2
+
+
+def test_fma_probe_checks_arguments_then_device():
+    """qnsch_fma_probe rejects out-of-range shapes with QNSCH_EINVAL before it
+    touches the device, and reports QNSCH_ENODEV without one."""
+    from paper_1703_06606_gb300 import qnsch
+    for bad in ((0, 16), (65, 16), (8, 0), (8, (1 << 24) + 1)):
+        with pytest.raises(qnsch.QnschError) as e:
+            qnsch.fma_probe(True, *bad)
+        assert e.value.code == -1, bad
+    import torch
+    if torch.cuda.is_available():
+        return
+    with pytest.raises(qnsch.QnschError) as e:
+        qnsch.fma_probe(True, 8, 16)
+    assert e.value.code == -2
