@@ -231,6 +231,20 @@ int qnsch_kernel_launches(long long* n);
    blocks_per_sm must lie in [1, 64] and iters in [1, 2^24], else QNSCH_EINVAL;
    no device gives QNSCH_ENODEV. */
 int qnsch_fma_probe(int fp64, int blocks_per_sm, int iters, double* tflops);
+/* FP64 issue-cost probe (a measurement utility with no counterpart in the
+   paper).  It launches one block of warps_per_block warps per SM; in every warp
+   the lanes below active_lanes run `chains` independent chains (1, 2, 4 or 8)
+   of 16 x iters FP64 fused multiply-adds, the other lanes idle.  The block's
+   thread 0 reads the SM cycle counter around the loop.  *cycles_per_instr
+   receives the slowest block's cycles, best of three launches after one
+   untimed one, divided by the FMAs one warp issues and by the warps sharing
+   one of the SM's four sub-partitions (ceil(warps_per_block / 4)).  It
+   allocates and frees SM-count x 32 x warps_per_block doubles and SM-count
+   counters, and synchronises before returning.  warps_per_block in [1, 32],
+   active_lanes in [1, 32], iters in [1, 2^20], else QNSCH_EINVAL; no device
+   gives QNSCH_ENODEV. */
+int qnsch_fp64_issue_probe(int warps_per_block, int active_lanes, int chains, int iters,
+                           double* cycles_per_instr);
 
 /* Batches of independent instances (no counterpart in the paper; the way a
    GPU runs many small problems at once).  A batch refers to n existing

@@ -1,7 +1,10 @@
-// probe.cu -- FMA throughput probe of the GPU (a measurement utility, not part
-// of the scheme): the FP64 figure is the peak that bench.py divides the FP64
-// kernels' achieved rate by.  Each thread runs eight independent FMA chains,
-// so the pipe, not the dependent-instruction latency, sets the rate.
+// probe.cu -- FMA probes of the GPU (measurement utilities, not part of the
+// scheme).  qnsch_fma_probe gives the FP64 peak that bench.py divides the FP64
+// kernels' achieved rate by: each thread runs eight independent FMA chains, so
+// the pipe, not the dependent-instruction latency, sets the rate.
+// qnsch_fp64_issue_probe gives the SM cycles one warp-wide FP64 FMA holds a
+// sub-partition for, as a function of the active lanes and of the independent
+// chains per lane: the cost model behind the solver's launch shapes.
 #include <cuda_runtime.h>
 
 #include "qnsch.h"
@@ -67,7 +70,97 @@ int run_probe(int blocks_per_sm, int iters, double* tflops) {
   return rc;
 }
 
+// One block per SM.  The first `active` lanes of every warp run `CH`
+// independent chains of 16 x iters FMAs; thread 0 records the block's elapsed
+// SM cycles between two barriers.
+template <typename T, int CH>
+__global__ void k_issue_probe(T* out, long long* cycles, int iters, int active, T b) {
+  T a[CH];
+#pragma unroll
+  for (int c = 0; c < CH; ++c) a[c] = T(threadIdx.x) * T(1e-3) + T(c);
+  const T m = T(0.999);
+  __syncthreads();
+  const long long t0 = clock64();
+  if ((int)(threadIdx.x & 31) < active) {
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+#pragma unroll
+        for (int c = 0; c < CH; ++c) a[c] = fma(a[c], m, b);
+      }
+    }
+  }
+  __syncthreads();
+  const long long t1 = clock64();
+  if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
+  T s = T(0);
+#pragma unroll
+  for (int c = 0; c < CH; ++c) s += a[c];
+  out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+int run_issue_probe(int warps, int active, int chains, int iters, double* cpi) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return QNSCH_ENODEV;
+  }
+  const int threads = 32 * warps;
+  double* out = nullptr;
+  long long* cyc = nullptr;
+  if (cudaMalloc(&out, (size_t)sms * threads * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&cyc, (size_t)sms * sizeof(long long)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(out);
+    return QNSCH_ENOMEM;
+  }
+  long long* host = new long long[sms];
+  long long best = -1;
+  int rc = QNSCH_OK;
+  for (int k = 0; k < 4 && rc == QNSCH_OK; ++k) {  // first launch warms up
+    switch (chains) {
+      case 1: k_issue_probe<double, 1><<<sms, threads>>>(out, cyc, iters, active, 1e-3); break;
+      case 2: k_issue_probe<double, 2><<<sms, threads>>>(out, cyc, iters, active, 1e-3); break;
+      case 4: k_issue_probe<double, 4><<<sms, threads>>>(out, cyc, iters, active, 1e-3); break;
+      default: k_issue_probe<double, 8><<<sms, threads>>>(out, cyc, iters, active, 1e-3); break;
+    }
+    if (cudaMemcpy(host, cyc, (size_t)sms * sizeof(long long), cudaMemcpyDeviceToHost) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      rc = QNSCH_ECUDA;
+      break;
+    }
+    if (k == 0) continue;
+    long long worst = 0;
+    for (int b = 0; b < sms; ++b) worst = host[b] > worst ? host[b] : worst;
+    if (best < 0 || worst < best) best = worst;
+  }
+  if (rc == QNSCH_OK) {
+    const int per_sp = (warps + 3) / 4;  // warps on the busiest of 4 sub-partitions
+    *cpi = (double)best / (16.0 * chains * (double)iters * per_sp);
+  }
+  delete[] host;
+  cudaFree(out);
+  cudaFree(cyc);
+  return rc;
+}
+
 }  // namespace
+
+extern "C" int qnsch_fp64_issue_probe(int warps_per_block, int active_lanes, int chains, int iters,
+                                      double* cycles_per_instr) {
+  if (!cycles_per_instr || warps_per_block < 1 || warps_per_block > 32 || active_lanes < 1 ||
+      active_lanes > 32 || !(chains == 1 || chains == 2 || chains == 4 || chains == 8) ||
+      iters < 1 || iters > (1 << 20))
+    return QNSCH_EINVAL;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) {
+    cudaGetLastError();
+    return QNSCH_ENODEV;
+  }
+  return run_issue_probe(warps_per_block, active_lanes, chains, iters, cycles_per_instr);
+}
 
 extern "C" int qnsch_fma_probe(int fp64, int blocks_per_sm, int iters, double* tflops) {
   if (!tflops || blocks_per_sm < 1 || blocks_per_sm > 64 || iters < 1 || iters > (1 << 24))

@@ -3,6 +3,7 @@
     python -m paper_1703_06606_gb300.profile_kernels --kernel vanka --m1 1024 --m2 1024 --reps 3
     python -m paper_1703_06606_gb300.profile_kernels --workload rt --kernel step --precision 1
     python -m paper_1703_06606_gb300.profile_kernels --kernel fmapeak
+    python -m paper_1703_06606_gb300.profile_kernels --kernel fp64issue
 
 Sets up the drop workload at the given size (default 1024 x 1024), or the
 Rayleigh-Taylor workload at its full 1024 x 4096 size, freezes a time step
@@ -13,7 +14,9 @@ its norms; step: whole time steps, in the FP64 (--precision 0) or mixed
 (--coupled 1), or the projection method (--scheme 1)).  fmapeak times the
 library's FMA throughput probe (qnsch_fma_probe) in FP64 and FP32 over a few
 launch shapes and prints the rates; the best FP64 rate is the peak of the
-FP64 kernels' ALU roofline.
+FP64 kernels' ALU roofline.  fp64issue runs qnsch_fp64_issue_probe over active
+lanes, independent chains and warps per block and prints the SM cycles one
+warp-wide FP64 FMA holds a sub-partition for.
 """
 from __future__ import annotations
 
@@ -24,7 +27,8 @@ from . import qnsch, workloads
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--kernel", default="vanka", choices=["vanka", "ch", "residual", "step", "fmapeak"])
+    ap.add_argument("--kernel", default="vanka", choices=["vanka", "ch", "residual", "step", "fmapeak",
+                                                              "fp64issue"])
     ap.add_argument("--workload", default="drop", choices=["drop", "rt"])
     ap.add_argument("--m1", type=int, default=1024)
     ap.add_argument("--m2", type=int, default=1024)
@@ -39,6 +43,14 @@ def main():
             for b, r in rates.items():
                 print("%s blocks/SM %2d: %.4f TFLOP/s" % ("FP64" if fp64 else "FP32", b, r))
             print("%s best: %.4f TFLOP/s" % ("FP64" if fp64 else "FP32", max(rates.values())))
+        return
+    if a.kernel == "fp64issue":
+        print("warps/block  active lanes  chains  cycles per warp FMA")
+        for warps in (4, 16):
+            for active in (1, 32):
+                for chains in (1, 8):
+                    c = qnsch.fp64_issue_probe(warps, active, chains, 1024)
+                    print("%11d  %12d  %6d  %.1f" % (warps, active, chains, c))
         return
     if a.workload == "rt":
         P = workloads.rayleigh_taylor_1024x4096()

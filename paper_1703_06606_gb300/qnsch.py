@@ -76,6 +76,7 @@ def lib():
         L.qnsch_profile_read.argtypes = [_VP, ctypes.POINTER(ctypes.c_longlong), p]
         L.qnsch_kernel_launches.argtypes = [ctypes.POINTER(ctypes.c_longlong)]
         L.qnsch_fma_probe.argtypes = [i, i, i, p]
+        L.qnsch_fp64_issue_probe.argtypes = [i, i, i, i, p]
         L.qnsch_mass_noalloc.argtypes = [_VP, i, i, d, d, d, _VP, _VP]
         L.qnsch_batch_create.argtypes = [i, ctypes.POINTER(_VP), ctypes.POINTER(_VP)]
         L.qnsch_batch_step.argtypes = [_VP, p, ctypes.POINTER(i), ctypes.POINTER(i)]
@@ -99,6 +100,16 @@ def fma_probe(fp64=True, blocks_per_sm=8, iters=4096):
     t = ctypes.c_double()
     _check(lib().qnsch_fma_probe(int(bool(fp64)), int(blocks_per_sm), int(iters),
                                  ctypes.byref(t)), "qnsch_fma_probe")
+    return t.value
+
+
+def fp64_issue_probe(warps_per_block=4, active_lanes=32, chains=8, iters=1024):
+    """qnsch_fp64_issue_probe: SM cycles one warp-wide FP64 FMA holds a
+    sub-partition for, with `active_lanes` lanes and `chains` independent
+    chains per lane."""
+    t = ctypes.c_double()
+    _check(lib().qnsch_fp64_issue_probe(int(warps_per_block), int(active_lanes), int(chains),
+                                        int(iters), ctypes.byref(t)), "qnsch_fp64_issue_probe")
     return t.value
 
 

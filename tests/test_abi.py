@@ -54,3 +54,18 @@ def test_fma_probe_checks_arguments_then_device():
     with pytest.raises(qnsch.QnschError) as e:
         qnsch.fma_probe(True, 8, 16)
     assert e.value.code == -2
+
+
+def test_fp64_issue_probe_checks_arguments_then_device():
+    from paper_1703_06606_gb300 import qnsch
+    for bad in ((0, 32, 8, 16), (33, 32, 8, 16), (4, 0, 8, 16), (4, 33, 8, 16), (4, 32, 3, 16),
+                (4, 32, 8, 0), (4, 32, 8, (1 << 20) + 1)):
+        with pytest.raises(qnsch.QnschError) as e:
+            qnsch.fp64_issue_probe(*bad)
+        assert e.value.code == -1, bad
+    import torch
+    if torch.cuda.is_available():
+        return
+    with pytest.raises(qnsch.QnschError) as e:
+        qnsch.fp64_issue_probe(4, 32, 8, 16)
+    assert e.value.code == -2

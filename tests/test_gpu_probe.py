@@ -1,6 +1,11 @@
-"""The FMA throughput probe that gives the FP64 kernels' ALU-roofline peak:
-it runs, and its rates are of the right order (FP32 far above FP64 on a part
-whose FP64 rate is a small fraction of its FP32 rate)."""
+"""The FMA probes behind the FP64 cost model: the throughput probe (the FP64
+kernels' ALU-roofline peak) runs and its rates are of the right order (FP32
+far above FP64 on a part whose FP64 rate is a small fraction of its FP32
+rate); the issue-cost probe gives a positive, finite cycle count per warp FMA
+that does not fall when lanes go idle (the pipe's cost is per warp
+instruction, not per active lane)."""
+import math
+
 import pytest
 
 pytestmark = pytest.mark.gpu
@@ -12,3 +17,11 @@ def test_fma_probe_rates():
     f32 = qnsch.fma_probe(False, 4, 256)
     assert 0.05 < f64 < 100.0, f64
     assert f32 > 5.0 * f64, (f32, f64)
+
+
+def test_fp64_issue_probe_cost_is_per_warp_instruction():
+    from paper_1703_06606_gb300 import qnsch
+    full = qnsch.fp64_issue_probe(4, 32, 8, 64)
+    one = qnsch.fp64_issue_probe(4, 1, 8, 64)
+    assert math.isfinite(full) and 1.0 < full < 1000.0, full
+    assert one > 0.5 * full, (one, full)
