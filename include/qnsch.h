@@ -52,6 +52,8 @@ extern "C" {
 #define QNSCH_ENOMEM (-3)   /* allocation failed */
 #define QNSCH_ENOTCONV (-4) /* maxcyc V-cycles without reaching tol; step not committed */
 #define QNSCH_ENAN (-5)     /* non-finite residual; step not committed */
+#define QNSCH_ETIMEOUT (-6) /* step_time_limit reached before tol; step not committed */
+#define QNSCH_EBUDGET (-7)  /* the device-memory budget (qnsch_set_budget) would be exceeded */
 #define QNSCH_ESTATE (-8)   /* call not valid in the current state (e.g. vcycle outside a step) */
 #define QNSCH_ECUDA (-9)    /* a CUDA call failed */
 
@@ -78,10 +80,28 @@ int qnsch_set_allocator(void* (*alloc)(size_t bytes, void* ctx),
    parameter epsilon; Fr: Froude number, INFINITY (or <= 0) for no gravity.
    Derived (Sec. 8): M = Cn, eta = eta(rho1, rho2) of Sec. 8.1, mobility
    regularisation eps = Cn; each can be overridden with qnsch_set_option.
-   Returns QNSCH_ENODEV without a CUDA device. */
+   Returns QNSCH_EINVAL for an invalid grid or parameter, QNSCH_EBUDGET when
+   the handle's footprint would exceed the budget (qnsch_set_budget), and
+   QNSCH_ENODEV without a CUDA device, checked in that order. */
 int qnsch_create(const qnsch_grid* grid, double rho1, double rho2, double eta1, double eta2,
                  double Re, double We, double Pe, double Cn, double Fr, qnsch_t** out);
 int qnsch_destroy(qnsch_t* h);
+
+/* Device-memory budget of the process (no counterpart in the paper; the limit a
+   server admits work under).  qnsch_set_budget(bytes) sets it; 0 (the default)
+   means none.  Every handle reserves its qnsch_footprint at creation
+   (precision 0) and the error-equation levels' bytes when the first step at
+   precision 1 or 2 allocates them; qnsch_destroy releases both.  A creation or
+   a step whose reservation would take the reserved total above the budget
+   fails with QNSCH_EBUDGET and allocates nothing (a step so refused is not
+   started).  qnsch_create checks the budget before it looks for a device, so
+   the refusal also comes without one.  Reservations are atomic, so threads
+   creating handles at once never overshoot.  Lowering the budget below what
+   is reserved frees nothing; it only refuses new reservations.
+   qnsch_budget writes the budget and the bytes reserved (either pointer may be
+   NULL, not both). */
+int qnsch_set_budget(size_t bytes);
+int qnsch_budget(size_t* budget, size_t* in_use);
 /* Device bytes a handle for `grid` holds once created and stepped with the
    given "precision" option (0, 1 or 2), computed without allocating. */
 int qnsch_footprint(const qnsch_grid* grid, int precision, size_t* bytes);
@@ -93,8 +113,18 @@ int qnsch_footprint(const qnsch_grid* grid, int precision, size_t* bytes);
    "eps_mob": Cn, "precision": 0, "graphs": 1, "fuse_cells": 128,
    "fuse_cells32": 512, "coupled": 0, "scheme": 0, "vanka_team_max": 8192,
    "ch_team_max": 4096, "vanka_team_max32": 65536, "ch_team_max32": 0,
-   "pdl": 1.
+   "pdl": 1, "step_time_limit": 0, "diverge_cycles": 0.
    Unknown keys give QNSCH_EINVAL.
+   step_time_limit (seconds, >= 0; 0: none): before each outer cycle of a
+   step, qnsch_step checks the wall time since the call began (qnsch_batch_step:
+   since its call began) and, once it exceeds the limit with the residual still
+   above tol, stops and returns QNSCH_ETIMEOUT without committing the step.  A
+   cycle already queued runs to its end, so a step can overrun the limit by one
+   outer cycle.
+   diverge_cycles (integer >= 0; 0: never): a step whose largest family
+   residual has grown over this many consecutive outer cycles stops early and
+   returns QNSCH_ENOTCONV without committing (failure detection for a step that
+   would otherwise spend maxcyc cycles diverging).
    scheme: 0 the primitive method (Sec. 6.1); 1 the projection method
    (Sec. 6.2; precision 0 and coupled 0 only).
    vanka_team_max: FP64 levels with at most this many cells per Vanka colour
@@ -150,8 +180,10 @@ int qnsch_get_fields_device(const qnsch_t* h, double* c, double* mu, double* u, 
 /* One time step: qnsch_begin_step, then V-cycles until the largest scaled
    residual norm is <= tol, then qnsch_commit_step.  Writes the number of
    V-cycles and the final norm (either pointer may be NULL).  Returns
-   QNSCH_ENOTCONV or QNSCH_ENAN, leaving the state at level n, when the
-   iteration does not converge. */
+   QNSCH_ENOTCONV, QNSCH_ENAN or QNSCH_ETIMEOUT, leaving the state at level n,
+   when the iteration does not converge (maxcyc cycles, or diverge_cycles
+   cycles of growth), turns non-finite or runs past step_time_limit; a
+   refused budget reservation gives QNSCH_EBUDGET before any cycle. */
 int qnsch_step(qnsch_t* h, double dt, int* n_vcycles, double* final_residual);
 /* Freeze level-n data on every level (restrict c^n, u^n, v^n; derive rho^n,
    m(c^n), mu(c^n), G(c^n)) and start the iterate at the level-n fields. */

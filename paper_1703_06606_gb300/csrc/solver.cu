@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <type_traits>
 #include <cmath>
 #include <cstdlib>
@@ -47,6 +49,30 @@ void dev_free(void* p) {
   if (!p) return;
   if (g_free) g_free(p, g_ctx);
   else cudaFree(p);
+}
+
+// process-wide device-memory budget (qnsch_set_budget; 0 = none) and the bytes
+// reserved against it by live handles
+std::atomic<size_t> g_budget{0};
+std::atomic<size_t> g_reserved{0};
+
+bool over_budget(size_t more) {
+  size_t b = g_budget.load();
+  return b != 0 && g_reserved.load() + more > b;
+}
+
+// reserve `bytes` against the budget, or fail without reserving anything
+bool reserve_bytes(size_t bytes) {
+  size_t cur = g_reserved.load();
+  for (;;) {
+    size_t b = g_budget.load();
+    if (b != 0 && cur + bytes > b) return false;
+    if (g_reserved.compare_exchange_weak(cur, cur + bytes)) return true;
+  }
+}
+
+double seconds_since(std::chrono::steady_clock::time_point t0) {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
 }
 
 constexpr int NFIELD = 45;  // arrays per level (see Lv)
@@ -121,6 +147,13 @@ struct qnsch_s {
   // the same on the error-equation levels of the defect correction (their
   // visits are latency-bound up to this size; larger levels stream from HBM)
   int team_max32 = 65536;
+  // failure detection: a step stops once it has run this many seconds of wall
+  // time (0: no limit), or once its residual has grown over this many
+  // consecutive outer cycles (0: never)
+  double time_limit = 0.0;
+  int diverge = 0;
+  // device bytes reserved against the process-wide budget
+  size_t reserved = 0;
   // grid
   int m1, m2, px, nlev, kcol;
   double h;
@@ -216,6 +249,8 @@ void free_all(qnsch_s* s) {
   s->own_stream = nullptr;
   for (void* b : s->blocks) dev_free(b);
   s->blocks.clear();
+  g_reserved -= s->reserved;
+  s->reserved = 0;
   if (s->hbuf) cudaFreeHost(s->hbuf);
   s->hbuf = nullptr;
 }
@@ -298,16 +333,29 @@ constexpr int NFIELD_ERR = NFIELD - 7 + 5;
 template <typename T>
 int alloc_err_levels(qnsch_s* s, std::vector<Lv<T>>& E) {
   if (!E.empty()) return QNSCH_OK;
+  size_t need = 0;
+  for (int l = 0; l < s->nlev; ++l)
+    need += (size_t)s->L[l].pitch * (size_t)(s->L[l].m2 + 3) * NFIELD_ERR * sizeof(T);
+  if (!reserve_bytes(need)) return QNSCH_EBUDGET;
   std::vector<Lv<T>> out(s->nlev);
+  std::vector<void*> got;
+  auto fail = [&](int rc) {  // give back what this call took
+    cudaStreamSynchronize(s->stream);
+    for (void* b : got) dev_free(b);
+    g_reserved -= need;
+    return rc;
+  };
   for (int l = 0; l < s->nlev; ++l) {
     const Lv<double>& D = s->L[l];
     Lv<T>& L = out[l];
     size_t n = (size_t)D.pitch * (size_t)(D.m2 + 3);
     T* base = (T*)dev_alloc(n * NFIELD_ERR * sizeof(T));
-    if (!base) return QNSCH_ENOMEM;
-    s->blocks.push_back(base);
-    if (cudaMemsetAsync(base, 0, n * NFIELD_ERR * sizeof(T), s->stream) != cudaSuccess)
-      return QNSCH_ECUDA;
+    if (!base) return fail(QNSCH_ENOMEM);
+    got.push_back(base);
+    if (cudaMemsetAsync(base, 0, n * NFIELD_ERR * sizeof(T), s->stream) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(QNSCH_ECUDA);
+    }
     L.m1 = D.m1;
     L.m2 = D.m2;
     L.px = D.px;
@@ -325,6 +373,8 @@ int alloc_err_levels(qnsch_s* s, std::vector<Lv<T>>& E) {
                          &L.Bu,  &L.Bv,  &L.Bdc};
     for (int q = 0; q < NFIELD_ERR; ++q) *f[q] = base + (size_t)q * n + D.pitch + 1;
   }
+  s->blocks.insert(s->blocks.end(), got.begin(), got.end());
+  s->reserved += need;
   E.swap(out);
   return QNSCH_OK;
 }
@@ -580,6 +630,14 @@ int copy_fields_out(const qnsch_s* s, double* const src[5], double* const dst[5]
 }
 
 int begin(qnsch_s* s, double dt) {
+  // the error-equation levels first: a refused allocation leaves nothing queued
+  if (s->precision == 1) {
+    int rc = alloc_err_levels(s, s->Ef);
+    if (rc) return rc;
+  } else if (s->precision == 2) {
+    int rc = alloc_err_levels(s, s->Ed);
+    if (rc) return rc;
+  }
   s->dt = dt;
   s->res_valid = 0;
   Prm<double> P = make_prm(s);
@@ -601,12 +659,8 @@ int begin(qnsch_s* s, double dt) {
     qn::launch_frozen(P, s->L[l], s->stream);
   }
   if (s->precision == 1) {
-    int rc = alloc_err_levels(s, s->Ef);
-    if (rc) return rc;
     for (int l = 0; l < s->nlev; ++l) qn::launch_cast_frozen(s->L[l], s->Ef[l], s->stream);
   } else if (s->precision == 2) {
-    int rc = alloc_err_levels(s, s->Ed);
-    if (rc) return rc;
     for (int l = 0; l < s->nlev; ++l) qn::launch_cast_frozen(s->L[l], s->Ed[l], s->stream);
   }
   s->pending = 1;
@@ -789,11 +843,6 @@ int qnsch_set_allocator(void* (*alloc)(size_t, void*), void (*free_fn)(void*, vo
 int qnsch_create(const qnsch_grid* grid, double rho1, double rho2, double eta1, double eta2,
                  double Re, double We, double Pe, double Cn, double Fr, qnsch_t** out) {
   if (!grid || !out) return QNSCH_EINVAL;
-  int ndev = 0;
-  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
-    cudaGetLastError();
-    return QNSCH_ENODEV;
-  }
   if (grid->m1 < 2 || grid->m2 < 2 || !(grid->Lx > 0) || grid->periodic_y) return QNSCH_EINVAL;
   if (grid->periodic_x && (grid->m1 % 2 != 0 || grid->m1 < 4)) return QNSCH_EINVAL;
   if (!(rho1 > 0) || !(rho2 > 0) || !(eta1 > 0) || !(eta2 > 0) || !(Re > 0) || !(We > 0) ||
@@ -802,8 +851,21 @@ int qnsch_create(const qnsch_grid* grid, double rho1, double rho2, double eta1, 
   int lmax = max_levels(grid->m1, grid->m2, grid->periodic_x);
   int lev = grid->levels <= 0 ? lmax : grid->levels;
   if (lev > lmax) return QNSCH_EINVAL;
+  size_t need = 0;
+  if (qnsch_footprint(grid, 0, &need) != QNSCH_OK) return QNSCH_EINVAL;
+  if (over_budget(need)) return QNSCH_EBUDGET;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return QNSCH_ENODEV;
+  }
   qnsch_s* s = new (std::nothrow) qnsch_s();
   if (!s) return QNSCH_ENOMEM;
+  if (!reserve_bytes(need)) {
+    delete s;
+    return QNSCH_EBUDGET;
+  }
+  s->reserved = need;
   s->rho1 = rho1;
   s->rho2 = rho2;
   s->mu1 = eta1;
@@ -860,6 +922,18 @@ int qnsch_footprint(const qnsch_grid* grid, int precision, size_t* bytes) {
   return QNSCH_OK;
 }
 
+int qnsch_set_budget(size_t bytes) {
+  g_budget = bytes;
+  return QNSCH_OK;
+}
+
+int qnsch_budget(size_t* budget, size_t* in_use) {
+  if (!budget && !in_use) return QNSCH_EINVAL;
+  if (budget) *budget = g_budget.load();
+  if (in_use) *in_use = g_reserved.load();
+  return QNSCH_OK;
+}
+
 int qnsch_destroy(qnsch_t* s) {
   if (!s) return QNSCH_EINVAL;
   if (s->stream) cudaStreamSynchronize(s->stream);
@@ -883,7 +957,13 @@ int qnsch_set_option(qnsch_t* s, const char* key, double value) {
   else if (k == "eta_st") s->eta = value;
   else if (k == "eps_mob") s->eps_m = value;
   else if (k == "graphs") s->use_graphs = value != 0.0;
-  else if (k == "fuse_cells") s->fuse64 = (int)value;
+  else if (k == "step_time_limit") {
+    if (!(value >= 0.0)) return QNSCH_EINVAL;
+    s->time_limit = value;
+  } else if (k == "diverge_cycles") {
+    if (!(value >= 0.0) || value != (double)(int)value) return QNSCH_EINVAL;
+    s->diverge = (int)value;
+  } else if (k == "fuse_cells") s->fuse64 = (int)value;
   else if (k == "coupled") {
     if (value != 0.0 && s->scheme) return QNSCH_EINVAL;  // a primitive-method smoother
     s->coupled = value != 0.0;
@@ -925,6 +1005,8 @@ int qnsch_get_option(const qnsch_t* s, const char* key, double* value) {
   else if (k == "eps_mob") *value = s->eps_m;
   else if (k == "precision") *value = s->precision;
   else if (k == "graphs") *value = s->use_graphs;
+  else if (k == "step_time_limit") *value = s->time_limit;
+  else if (k == "diverge_cycles") *value = s->diverge;
   else if (k == "fuse_cells") *value = s->fuse64;
   else if (k == "coupled") *value = s->coupled;
   else if (k == "fuse_cells32") *value = s->fuse32;
@@ -1040,25 +1122,37 @@ int qnsch_commit_step(qnsch_t* s) {
 int qnsch_step(qnsch_t* s, double dt, int* n_vcycles, double* final_residual) {
   if (!s || !(dt > 0)) return QNSCH_EINVAL;
   if (s->pending) return QNSCH_ESTATE;
+  const auto t0 = std::chrono::steady_clock::now();
   int rc = begin(s, dt);
   if (rc) return rc;
   Prm<double> P = make_prm(s);
   double n[10];
   rc = residual_norms(s, P, n);
   if (rc) return rc;
-  int k = 0;
+  int k = 0, grew = 0, late = 0;
   double r = maxfam(n);
   while (r == r && r > s->tol && k < s->maxcyc) {
+    if (s->time_limit > 0.0 && seconds_since(t0) > s->time_limit) {
+      late = 1;
+      break;
+    }
+    const double prev = r;
     rc = one_cycle(s, n);
     if (rc) return rc;
     r = maxfam(n);
     ++k;
+    grew = r > prev ? grew + 1 : 0;
+    if (s->diverge > 0 && grew >= s->diverge) break;
   }
   if (n_vcycles) *n_vcycles = k;
   if (final_residual) *final_residual = r;
   if (!(r == r)) {
     s->pending = 0;
     return QNSCH_ENAN;
+  }
+  if (late) {
+    s->pending = 0;
+    return QNSCH_ETIMEOUT;
   }
   if (r > s->tol) {
     s->pending = 0;
@@ -1251,9 +1345,10 @@ int qnsch_batch_step(qnsch_batch_t* B, const double* dt, int* status, int* n_vcy
   const int n = (int)B->inst.size();
   for (int a = 0; a < n; ++a)
     if (!(dt[a] > 0) || B->inst[a]->pending) return QNSCH_EINVAL;
-  std::vector<int> live(n, 1), cyc(n, 0);
-  std::vector<char> wait(n, 0);
-  std::vector<double> res(n, 0.0);
+  std::vector<int> live(n, 1), cyc(n, 0), grew(n, 0);
+  std::vector<char> wait(n, 0), late(n, 0);
+  std::vector<double> res(n, HUGE_VAL);
+  const auto t0 = std::chrono::steady_clock::now();
   double nrm[10];
   for (int a = 0; a < n; ++a) {
     qnsch_s* s = B->inst[a];
@@ -1285,7 +1380,15 @@ int qnsch_batch_step(qnsch_batch_t* B, const double* dt, int* status, int* n_vcy
         live[a] = 0;
         continue;
       }
+      const double prev = res[a];
       res[a] = maxfam(nrm);
+      grew[a] = cyc[a] > 0 && res[a] > prev ? grew[a] + 1 : 0;
+      if (s->diverge > 0 && grew[a] >= s->diverge) continue;
+      if (res[a] == res[a] && res[a] > s->tol && s->time_limit > 0.0 &&
+          seconds_since(t0) > s->time_limit) {
+        late[a] = 1;
+        continue;
+      }
       if (res[a] == res[a] && res[a] > s->tol && cyc[a] < s->maxcyc) {
         launch_cycle(s);
         cudaEventRecord(s->ev_norms, s->stream);
@@ -1304,6 +1407,9 @@ int qnsch_batch_step(qnsch_batch_t* B, const double* dt, int* status, int* n_vcy
     }
     if (!(res[a] == res[a])) {
       status[a] = QNSCH_ENAN;
+      s->pending = 0;
+    } else if (late[a]) {
+      status[a] = QNSCH_ETIMEOUT;
       s->pending = 0;
     } else if (res[a] > s->tol) {
       status[a] = QNSCH_ENOTCONV;

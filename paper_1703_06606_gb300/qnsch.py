@@ -20,7 +20,7 @@ _D = ctypes.POINTER(ctypes.c_double)
 _VP = ctypes.c_void_p
 
 STATUS = {0: "OK", -1: "EINVAL", -2: "ENODEV", -3: "ENOMEM", -4: "ENOTCONV", -5: "ENAN",
-          -8: "ESTATE", -9: "ECUDA"}
+          -6: "ETIMEOUT", -7: "EBUDGET", -8: "ESTATE", -9: "ECUDA"}
 
 
 class QnschError(RuntimeError):
@@ -76,6 +76,8 @@ def lib():
         L.qnsch_profile_read.argtypes = [_VP, ctypes.POINTER(ctypes.c_longlong), p]
         L.qnsch_kernel_launches.argtypes = [ctypes.POINTER(ctypes.c_longlong)]
         L.qnsch_fma_probe.argtypes = [i, i, i, p]
+        L.qnsch_set_budget.argtypes = [ctypes.c_size_t]
+        L.qnsch_budget.argtypes = [ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]
         L.qnsch_fp64_issue_probe.argtypes = [i, i, i, i, p]
         L.qnsch_mass_noalloc.argtypes = [_VP, i, i, d, d, d, _VP, _VP]
         L.qnsch_batch_create.argtypes = [i, ctypes.POINTER(_VP), ctypes.POINTER(_VP)]
@@ -92,6 +94,18 @@ def kernel_launches():
     n = ctypes.c_longlong()
     _check(lib().qnsch_kernel_launches(ctypes.byref(n)), "qnsch_kernel_launches")
     return n.value
+
+
+def set_budget(nbytes):
+    """qnsch_set_budget: the process's device-memory budget in bytes (0: none)."""
+    _check(lib().qnsch_set_budget(int(nbytes)), "qnsch_set_budget")
+
+
+def budget():
+    """qnsch_budget: (budget in bytes, bytes reserved by live handles)."""
+    b, u = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(lib().qnsch_budget(ctypes.byref(b), ctypes.byref(u)), "qnsch_budget")
+    return b.value, u.value
 
 
 def fma_probe(fp64=True, blocks_per_sm=8, iters=4096):

@@ -69,3 +69,35 @@ def test_fp64_issue_probe_checks_arguments_then_device():
     with pytest.raises(qnsch.QnschError) as e:
         qnsch.fp64_issue_probe(4, 32, 8, 16)
     assert e.value.code == -2
+
+
+def test_status_names_match_the_header():
+    from paper_1703_06606_gb300 import qnsch
+    text = open(os.path.join(ROOT, "include", "qnsch.h")).read()
+    codes = {int(v): k for k, v in re.findall(r"#define QNSCH_(\w+) \((-?\d+)\)", text)}
+    codes[0] = "OK"
+    assert codes == qnsch.STATUS
+
+
+def test_budget_refuses_creation_before_looking_for_a_device():
+    """qnsch_create checks its arguments, then the budget, then the device."""
+    from paper_1703_06606_gb300 import qnsch
+    fp = qnsch.footprint(16, 16)
+    try:
+        qnsch.set_budget(fp - 1)
+        assert qnsch.budget()[0] == fp - 1
+        with pytest.raises(qnsch.QnschError) as e:
+            qnsch.Solver(16, 16)
+        assert e.value.code == -7
+        with pytest.raises(qnsch.QnschError) as e:
+            qnsch.Solver(16, 16, Re=-1.0)
+        assert e.value.code == -1
+        import torch
+        if not torch.cuda.is_available():
+            qnsch.set_budget(fp)
+            with pytest.raises(qnsch.QnschError) as e:
+                qnsch.Solver(16, 16)
+            assert e.value.code == -2
+    finally:
+        qnsch.set_budget(0)
+    assert qnsch.budget()[0] == 0

@@ -1,0 +1,140 @@
+"""Failure detection of a step, made on the host without any GPU fault:
+step_time_limit ends a step with QNSCH_ETIMEOUT, diverge_cycles ends a
+diverging step early with QNSCH_ENOTCONV, and the device-memory budget refuses
+a creation or a mixed-precision step with QNSCH_EBUDGET.  Each failure leaves
+the committed state as it was and the handle usable."""
+import ctypes
+import gc
+
+import numpy as np
+import pytest
+
+from paper_1703_06606_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qn():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1703_06606_gb300 import qnsch
+    return qnsch
+
+
+def _pair(qn, P, **opts):
+    out = []
+    for _ in range(2):
+        s = qn.Solver(**P.create_kwargs(), tol=P.tol, **opts)
+        s.set_fields(P.fields())
+        out.append(s)
+    return out
+
+
+def _same(a, b):
+    fa, fb = a.get_fields(), b.get_fields()
+    return all(np.array_equal(fa[k], fb[k]) for k in fa)
+
+
+def test_step_time_limit(qn):
+    """A limit far below one cycle's time stops the step before its first
+    cycle; the state stays at level n and, with the limit lifted, the next
+    step gives exactly what an untouched handle gives."""
+    P = W.small_case()
+    a, b = _pair(qn, P)
+    f0 = a.get_fields()
+    a.set_option("step_time_limit", 1e-9)
+    with pytest.raises(qn.QnschError) as e:
+        a.step(P.dt)
+    assert e.value.code == -6
+    f1 = a.get_fields()
+    assert all(np.array_equal(f0[k], f1[k]) for k in f0)
+    a.set_option("step_time_limit", 0.0)
+    na, _ = a.step(P.dt)
+    nb, _ = b.step(P.dt)
+    assert na == nb and _same(a, b)
+
+
+def test_step_time_limit_in_a_batch(qn):
+    """In a batch only the instance with the limit times out; the others step
+    as they do alone."""
+    probs = [W.small_case(), W.small_case(48, 64, False), W.capillary_64()]
+    batch, alone = [], []
+    for P in probs:
+        x, y = _pair(qn, P)
+        batch.append(x)
+        alone.append(y)
+    batch[1].set_option("step_time_limit", 1e-9)
+    f0 = batch[1].get_fields()
+    st, _ = qn.Batch(batch).step([P.dt for P in probs])
+    assert st == [0, -6, 0], st
+    f1 = batch[1].get_fields()
+    assert all(np.array_equal(f0[k], f1[k]) for k in f0)
+    for i in (0, 2):
+        alone[i].step(probs[i].dt)
+        assert _same(batch[i], alone[i])
+
+
+def test_diverge_cycles_stops_a_diverging_step(qn):
+    """omega_vanka = 2.5 makes the smoother diverge (the residual grows by
+    orders of magnitude every cycle).  With diverge_cycles = 2 the step ends
+    after two cycles of growth with QNSCH_ENOTCONV instead of running to a
+    non-finite residual; the state stays at level n."""
+    P = W.small_case()
+    s = qn.Solver(**P.create_kwargs(), tol=P.tol, omega_vanka=2.5, diverge_cycles=2, maxcyc=50)
+    s.set_fields(P.fields())
+    f0 = s.get_fields()
+    n, r = ctypes.c_int(), ctypes.c_double()
+    rc = qn.lib().qnsch_step(s._h, float(P.dt), ctypes.byref(n), ctypes.byref(r))
+    assert rc == -4 and n.value == 2, (rc, n.value, r.value)
+    f1 = s.get_fields()
+    assert all(np.array_equal(f0[k], f1[k]) for k in f0)
+
+
+def test_diverge_cycles_keeps_a_converging_step(qn):
+    """The capillary wave's first step grows its residual over the first cycle
+    and then converges; diverge_cycles = 2 leaves it, and its result, as it is."""
+    P = W.capillary_64()
+    a, b = _pair(qn, P)
+    a.set_option("diverge_cycles", 2)
+    for _ in range(2):
+        na, _ = a.step(P.dt)
+        nb, _ = b.step(P.dt)
+        assert na == nb
+    assert _same(a, b)
+
+
+def test_budget_refuses_and_releases(qn):
+    """Each handle reserves its footprint; a creation past the budget fails with
+    QNSCH_EBUDGET, destroying a handle gives its bytes back, and a mixed step
+    reserves its error levels' bytes (footprint at precision 1) or is refused."""
+    P = W.small_case()
+    fp0 = qn.footprint(P.m1, P.m2, P.periodic_x, P.levels, 0, P.Lx)
+    fp1 = qn.footprint(P.m1, P.m2, P.periodic_x, P.levels, 1, P.Lx)
+    gc.collect()
+    _, u0 = qn.budget()
+    try:
+        # room for one handle, not for a second one nor for its error levels
+        assert fp0 < fp1 < 2 * fp0
+        qn.set_budget(u0 + fp0 + (fp1 - fp0) // 2)
+        a = qn.Solver(**P.create_kwargs(), tol=P.tol)
+        assert qn.budget()[1] == u0 + fp0
+        with pytest.raises(qn.QnschError) as e:
+            qn.Solver(**P.create_kwargs(), tol=P.tol)
+        assert e.value.code == -7
+        assert qn.budget()[1] == u0 + fp0
+        a.set_fields(P.fields())
+        a.set_option("precision", 1)
+        with pytest.raises(qn.QnschError) as e:
+            a.step(P.dt)
+        assert e.value.code == -7
+        qn.set_budget(u0 + fp1)
+        a.step(P.dt)
+        assert qn.budget()[1] == u0 + fp1
+        a.close()
+        assert qn.budget()[1] == u0
+        b = qn.Solver(**P.create_kwargs(), tol=P.tol)
+        b.close()
+    finally:
+        qn.set_budget(0)
