@@ -121,6 +121,23 @@ def test_vcycle_parity_from_physical_state(qn, m1, m2, px):
         assert np.allclose(ng, nr, rtol=1e-6, atol=1e-14)
 
 
+@pytest.mark.parametrize("coupled", [0, 1])
+def test_vcycle_parity_under_relaxed(qn, coupled):
+    """omega_vanka = 0.8 (every block update scaled by omega on both sides):
+    V-cycles from the level-n state, per-level and fused coarse levels."""
+    P = W.small_case(32, 48, False)
+    g = qn.Solver(**P.create_kwargs(), omega_vanka=0.8, coupled=coupled)
+    r = RefSolver(**P.create_kwargs(), omega_vanka=0.8, coupled=coupled)
+    for s in (g, r):
+        s.set_fields(P.fields())
+        s.begin_step(P.dt)
+    for _ in range(3):
+        ng = g.vcycle()
+        nr = r.vcycle()
+        same_fields(g.get_iterate(), r.get_iterate(), 1e-9 if coupled else 1e-10)
+        assert np.allclose(ng, nr, rtol=1e-6, atol=1e-14)
+
+
 def _step_both(qn, P, steps=1, **opt):
     g = qn.Solver(**P.create_kwargs(), tol=P.tol, **opt)
     r = RefSolver(**P.create_kwargs(), tol=P.tol, **opt)
