@@ -17,6 +17,10 @@ ranks over the slowest rank's time.
 
 --impl reference times the FP64 CPU oracle (serial C, host cores) on the same
 workload and prints the same JSON line with "impl": "reference".
+
+cpu_baseline is the serial oracle on a few steps of the workload;
+cpu_baseline.all_cores runs one independent oracle replica per host core
+(spawned processes, started together) for the whole-job CPU throughput.
 """
 from __future__ import annotations
 
@@ -157,6 +161,67 @@ def oracle_rate(P, steps, budget_s):
         if time.perf_counter() - t_all > budget_s:
             break
     return times, cycles
+
+
+def _oracle_replica(workload, steps, barrier, out):
+    """One host core's share of the all-cores oracle baseline: an independent
+    oracle instance of `workload` steps `steps` times from its initial state,
+    starting together with the other replicas; puts (seconds, V-cycles), or
+    None if the start barrier breaks."""
+    from oracle.ref import RefSolver
+    P = getattr(workloads, workload)()
+    r = RefSolver(**P.create_kwargs(), tol=P.tol)
+    r.set_fields(P.fields())
+    try:
+        barrier.wait(timeout=120)
+    except Exception:
+        out.put(None)
+        return
+    cycles = []
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        cycles.append(r.step(P.dt)[0])
+    out.put((time.perf_counter() - t0, cycles))
+
+
+def oracle_all_cores(workload="rising_drop_256x512", steps=1, procs=None, timeout=300.0):
+    """Throughput of the FP64 oracle, as it stands, on every host core: one
+    independent replica of the workload per core (spawned processes, so no
+    CUDA state is inherited), started together; whole-job cell-updates/s =
+    replicas x cells x steps / the slowest replica's seconds.  None if a
+    replica fails or the run exceeds `timeout`."""
+    import multiprocessing as mp
+    from oracle.ref import lib as oracle_lib
+    oracle_lib()  # compiled once here, before the replicas load it
+    n = procs or os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    barrier, out = ctx.Barrier(n), ctx.Queue()
+    ps = [ctx.Process(target=_oracle_replica, args=(workload, steps, barrier, out), daemon=True)
+          for _ in range(n)]
+    for p in ps:
+        p.start()
+    deadline = time.time() + timeout
+    res = []
+    try:
+        for _ in range(n):
+            res.append(out.get(timeout=max(1.0, deadline - time.time())))
+    except Exception:
+        res.append(None)
+    for p in ps:
+        p.join(timeout=5)
+        if p.is_alive():
+            p.kill()
+    if len(res) != n or any(r is None for r in res):
+        return None
+    P = getattr(workloads, workload)()
+    slowest = max(t for t, _ in res)
+    return {"value": n * P.cells * steps / slowest, "unit": UNIT, "cores": n,
+            "kind": "oracle replicas",
+            "sample": "%d independent serial FP64 oracle instances of %s, one per host core, "
+                      "%d step(s) each from the initial state, started together; slowest "
+                      "replica %.1f s (V-cycles %s)"
+                      % (n, P.name, steps, slowest, "/".join(str(c[0]) for _, c in res[:4]) +
+                         ("/..." if n > 4 else ""))}
 
 
 # ---------------------------------------------------------------------------
@@ -495,6 +560,8 @@ def run_ours(args, rank, world, local_rank):
             "sample": "first %d time step(s) of the rising-droplet 256x512 workload from its "
                       "initial state, serial FP64 oracle (%s V-cycles), %.1f s"
                       % (len(times), "/".join(map(str, cycles)), sum(times))}
+        if not args.no_cpu_all_cores:
+            line["cpu_baseline"]["all_cores"] = oracle_all_cores(steps=1)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -550,6 +617,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cpu-all-cores", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-stress", action="store_true")

@@ -46,3 +46,13 @@ def test_reference_arm_two_ranks():
     lines = _lines(r.stdout)
     assert len(lines) == 1
     _check(lines[0], 2)
+
+
+def test_oracle_all_cores_replicas():
+    """The all-cores baseline runs one oracle replica per process (spawned) and
+    reports the whole job: replicas x cells x steps / slowest replica."""
+    sys.path.insert(0, ROOT)
+    import bench
+    r = bench.oracle_all_cores("capillary_64", steps=1, procs=2, timeout=120.0)
+    assert r is not None and r["cores"] == 2 and r["kind"] == "oracle replicas"
+    assert r["value"] > 0 and r["unit"] == "cell-updates/s"
