@@ -235,7 +235,9 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
+        import datetime
+        dist.init_process_group("nccl", device_id=dev,
+                                timeout=datetime.timedelta(seconds=replicas.PG_TIMEOUT_S))
     if rank == 0:
         qnsch.lib()  # build once
     if world > 1:
@@ -263,18 +265,25 @@ def run_ours(args, rank, world, local_rank):
     cyc = []
     s.profile(True)
     l0 = qnsch.kernel_launches()
+    failed = None
     with ClockSampler(local_rank) as clk:
         clk.ready()
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
-        for k in range(args.steps):
-            flush.fill_(float(k))
-            evs[k][0].record(stream)
-            n, res = s.step(P.dt)
-            evs[k][1].record(stream)
-            cyc.append(n)
+        try:
+            for k in range(args.steps):
+                flush.fill_(float(k))
+                evs[k][0].record(stream)
+                n, res = s.step(P.dt)
+                evs[k][1].record(stream)
+                cyc.append(n)
+        except qnsch.QnschError as e:
+            failed = e
         torch.cuda.synchronize()
+    if failed is not None:
+        print("bench: a timed step failed: %s" % failed, file=sys.stderr, flush=True)
+        replicas.slowest(0.0, dev, ok=False)  # every rank stops here
     launches = qnsch.kernel_launches() - l0
     prof_n, prof_ms = s.profile_read()
     if prof_n == 0:
