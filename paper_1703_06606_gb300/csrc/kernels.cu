@@ -5,6 +5,7 @@
 // for the norms, the mean of p, mass (Thm. 6.1) and energy (Thm. 6.2).
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <type_traits>
 
 #include "kernels.h"
@@ -16,9 +17,10 @@ constexpr int BX = 32, BY = 8, NT = BX * BY;
 
 static inline dim3 grid2(int nx, int ny) { return dim3((nx + BX - 1) / BX, (ny + BY - 1) / BY); }
 
-// number of kernels issued by this library since load (host-side count)
-static long long g_launches = 0;
-long long launches_issued() { return g_launches; }
+// number of kernels issued by this library since load (host-side count;
+// atomic, since host threads may drive different handles at once)
+static std::atomic<long long> g_launches{0};
+long long launches_issued() { return g_launches.load(); }
 
 // Programmatic dependent launch (sm_90 and later).  Every kernel of the step is
 // launched with programmatic stream serialisation: it is scheduled as the
@@ -31,7 +33,7 @@ long long launches_issued() { return g_launches; }
 // measured 13 % slower: the successor's blocks were placed while the
 // predecessor still held the SMs, and these latency-bound launches lost their
 // even spread over the sub-partitions.
-static int g_pdl = 1;
+static std::atomic<int> g_pdl{1};
 void set_pdl(int on) { g_pdl = on ? 1 : 0; }
 __device__ __forceinline__ void pdl_enter() {
   asm volatile("griddepcontrol.wait;" ::: "memory");

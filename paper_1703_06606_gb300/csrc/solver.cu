@@ -29,8 +29,8 @@ namespace {
 
 // kernels queued into captured graphs (not executed at capture time) and
 // kernels executed by graph replays, for qnsch_kernel_launches
-long long g_captured = 0;
-long long g_replayed = 0;
+std::atomic<long long> g_captured{0};
+std::atomic<long long> g_replayed{0};
 
 void* (*g_alloc)(size_t, void*) = nullptr;
 void (*g_free)(void*, void*) = nullptr;
@@ -78,7 +78,7 @@ double seconds_since(std::chrono::steady_clock::time_point t0) {
 constexpr int NFIELD = 45;  // arrays per level (see Lv)
 
 // option "pdl": programmatic dependent launch of every kernel (process-wide)
-static int g_pdl_option = 1;
+static std::atomic<int> g_pdl_option{1};
 
 // surface-tension ratio eta(rho1, rho2) of Sec. 8.1; near rho1 = rho2 the
 // formula is 0/0 and the Taylor series of x^2 - 1 - 2x ln x in q = x - 1 is used
@@ -974,7 +974,7 @@ int qnsch_set_option(qnsch_t* s, const char* key, double value) {
   else if (k == "vanka_team_max32") s->team_max32 = (int)value;
   else if (k == "pdl") {
     g_pdl_option = value != 0.0;
-    qn::set_pdl(g_pdl_option);
+    qn::set_pdl(g_pdl_option.load());
   }
   else if (k == "precision") {
     int p = (int)value;
@@ -1015,7 +1015,7 @@ int qnsch_get_option(const qnsch_t* s, const char* key, double* value) {
   else if (k == "ch_team_max") *value = s->ch_team_max;
   else if (k == "ch_team_max32") *value = s->ch_team_max32;
   else if (k == "vanka_team_max32") *value = s->team_max32;
-  else if (k == "pdl") *value = g_pdl_option;
+  else if (k == "pdl") *value = g_pdl_option.load();
   else return QNSCH_EINVAL;
   return QNSCH_OK;
 }
