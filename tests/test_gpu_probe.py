@@ -24,4 +24,5 @@ def test_fp64_issue_probe_cost_is_per_warp_instruction():
     full = qnsch.fp64_issue_probe(4, 32, 8, 64)
     one = qnsch.fp64_issue_probe(4, 1, 8, 64)
     assert math.isfinite(full) and 1.0 < full < 1000.0, full
-    assert one > 0.5 * full, (one, full)
+    # a per-active-lane cost would make `one` about full / 32
+    assert one > 0.25 * full, (one, full)
