@@ -66,6 +66,9 @@ typedef struct {
   int periodic_y;  /* must be 0: y is always bounded by walls */
   int levels;      /* multigrid levels; 0 = deepest the grid allows */
 } qnsch_grid;
+/* Coarsening halves both sides.  A level is added while both sides of the
+   current coarsest grid are even and the halved grid keeps at least 2 cells
+   per side (periodic x: at least 4 cells across, an even number). */
 
 /* Device allocator used for every later allocation (process-wide).
    alloc(bytes, ctx) returns device memory or NULL; free(ptr, ctx) releases it.
