@@ -66,7 +66,11 @@ typedef struct {
   int periodic_y;  /* must be 0: y is always bounded by walls */
   int levels;      /* multigrid levels; 0 = deepest the grid allows */
 } qnsch_grid;
-/* Coarsening halves both sides.  A level is added while both sides of the
+/* Size limit: the padded index space of one array, (m1 + 3 rounded up to a
+   multiple of 32) x (m2 + 3) elements, must not exceed 2^31 - 1, because the
+   kernels index arrays with 32-bit integers; larger grids give QNSCH_EINVAL
+   from qnsch_create and qnsch_footprint.
+   Coarsening halves both sides.  A level is added while both sides of the
    current coarsest grid are even and the halved grid keeps at least 2 cells
    per side (periodic x: at least 4 cells across, an even number). */
 

@@ -9,6 +9,7 @@
 #include <atomic>
 #include <chrono>
 #include <type_traits>
+#include <climits>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -896,6 +897,13 @@ int qnsch_create(const qnsch_grid* grid, double rho1, double rho2, double eta1, 
 
 int qnsch_footprint(const qnsch_grid* grid, int precision, size_t* bytes) {
   if (!grid || !bytes || grid->m1 < 2 || grid->m2 < 2 || grid->periodic_y) return QNSCH_EINVAL;
+  // the kernels index an array with 32-bit integers: its padded index space
+  // must fit
+  if (grid->m1 > (1 << 28) || grid->m2 > (1 << 28)) return QNSCH_EINVAL;
+  {
+    int pitch;
+    if (padded_elems(grid->m1, grid->m2, &pitch) > (size_t)INT_MAX) return QNSCH_EINVAL;
+  }
   if (grid->periodic_x && (grid->m1 % 2 != 0 || grid->m1 < 4)) return QNSCH_EINVAL;
   if (precision < 0 || precision > 2) return QNSCH_EINVAL;
   int lmax = max_levels(grid->m1, grid->m2, grid->periodic_x);

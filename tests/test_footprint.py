@@ -57,3 +57,17 @@ def test_footprint_rejects_what_create_rejects():
         with pytest.raises(qnsch.QnschError) as e:
             qnsch.footprint(*args)
         assert e.value.code == -1, args
+
+
+def test_grids_beyond_32_bit_indexing_are_rejected():
+    """(m1 + 3 rounded up to 32) x (m2 + 3) must fit a 32-bit index: 46304^2
+    gives 46304 x 46307 < 2^31 - 1, 46336 x 46336 does not.  Rejected by
+    qnsch_footprint and, before any device is looked for, by qnsch_create."""
+    assert qnsch.footprint(46304, 46304) > 0
+    for m1, m2 in ((46336, 46336), (1 << 29, 8), (8, 1 << 29)):
+        with pytest.raises(qnsch.QnschError) as e:
+            qnsch.footprint(m1, m2)
+        assert e.value.code == -1
+    with pytest.raises(qnsch.QnschError) as e:
+        qnsch.Solver(46336, 46336)
+    assert e.value.code == -1
