@@ -121,7 +121,12 @@ int qnsch_footprint(const qnsch_grid* grid, int precision, size_t* bytes);
    "fuse_cells32": 512, "coupled": 0, "scheme": 0, "vanka_team_max": 8192,
    "ch_team_max": 4096, "vanka_team_max32": 65536, "ch_team_max32": 0,
    "pdl": 1, "step_time_limit": 0, "diverge_cycles": 0.
-   Unknown keys give QNSCH_EINVAL.
+   Unknown keys give QNSCH_EINVAL, and so do values out of range, which leave
+   the option unchanged: NaN for any key; counts that are not integers in
+   their range (nu1, nu2, nu_coarse: 0..1000; maxcyc, diverge_cycles:
+   0..10^6; precision: 0..2; scheme: 0..1; fuse_cells, fuse_cells32 and the
+   four team thresholds: 0..2^31 - 1); tol or step_time_limit negative or
+   infinite; omega_vanka, M, eta_st or eps_mob not positive and finite.
    step_time_limit (seconds, >= 0; 0: none): before each outer cycle of a
    step, qnsch_step checks the wall time since the call began (qnsch_batch_step:
    since its call began) and, once it exceeds the limit with the residual still

@@ -951,52 +951,80 @@ int qnsch_destroy(qnsch_t* s) {
   return QNSCH_OK;
 }
 
-int qnsch_set_option(qnsch_t* s, const char* key, double value) {
-  if (!s || !key) return QNSCH_EINVAL;
-  std::string k(key);
-  ++s->opt_version;
-  if (k == "nu1") s->nu1 = (int)value;
-  else if (k == "nu2") s->nu2 = (int)value;
-  else if (k == "nu_coarse") s->nuc = (int)value;
-  else if (k == "maxcyc") s->maxcyc = (int)value;
-  else if (k == "tol") s->tol = value;
-  else if (k == "omega_vanka") s->omega = value;
-  else if (k == "M") s->M = value;
-  else if (k == "eta_st") s->eta = value;
-  else if (k == "eps_mob") s->eps_m = value;
-  else if (k == "graphs") s->use_graphs = value != 0.0;
-  else if (k == "step_time_limit") {
-    if (!(value >= 0.0)) return QNSCH_EINVAL;
+namespace {
+
+// an option that counts something: an integer in [lo, hi] (NaN, infinities
+// and fractions are refused before any conversion)
+bool count_of(double v, double lo, double hi, int* out) {
+  if (!(v >= lo && v <= hi) || v != std::floor(v)) return false;
+  *out = (int)v;
+  return true;
+}
+
+bool positive(double v) { return v > 0.0 && std::isfinite(v); }
+
+int set_option(qnsch_s* s, const std::string& k, double value) {
+  if (std::isnan(value)) return QNSCH_EINVAL;
+  int n = 0;
+  const double imax = (double)INT_MAX;
+  if (k == "nu1" || k == "nu2" || k == "nu_coarse") {
+    if (!count_of(value, 0, 1000, &n)) return QNSCH_EINVAL;
+    (k == "nu1" ? s->nu1 : k == "nu2" ? s->nu2 : s->nuc) = n;
+  } else if (k == "maxcyc") {
+    if (!count_of(value, 0, 1e6, &n)) return QNSCH_EINVAL;
+    s->maxcyc = n;
+  } else if (k == "tol") {
+    if (!(value >= 0.0) || !std::isfinite(value)) return QNSCH_EINVAL;
+    s->tol = value;
+  } else if (k == "omega_vanka") {
+    if (!positive(value)) return QNSCH_EINVAL;
+    s->omega = value;
+  } else if (k == "M" || k == "eta_st" || k == "eps_mob") {
+    if (!positive(value)) return QNSCH_EINVAL;
+    (k == "M" ? s->M : k == "eta_st" ? s->eta : s->eps_m) = value;
+  } else if (k == "graphs") {
+    s->use_graphs = value != 0.0;
+  } else if (k == "step_time_limit") {
+    if (!(value >= 0.0) || !std::isfinite(value)) return QNSCH_EINVAL;
     s->time_limit = value;
   } else if (k == "diverge_cycles") {
-    if (!(value >= 0.0) || value != (double)(int)value) return QNSCH_EINVAL;
-    s->diverge = (int)value;
-  } else if (k == "fuse_cells") s->fuse64 = (int)value;
-  else if (k == "coupled") {
+    if (!count_of(value, 0, 1e6, &n)) return QNSCH_EINVAL;
+    s->diverge = n;
+  } else if (k == "fuse_cells" || k == "fuse_cells32" || k == "vanka_team_max" ||
+             k == "ch_team_max" || k == "ch_team_max32" || k == "vanka_team_max32") {
+    if (!count_of(value, 0, imax, &n)) return QNSCH_EINVAL;
+    (k == "fuse_cells" ? s->fuse64 : k == "fuse_cells32" ? s->fuse32
+     : k == "vanka_team_max" ? s->team_max : k == "ch_team_max" ? s->ch_team_max
+     : k == "ch_team_max32" ? s->ch_team_max32 : s->team_max32) = n;
+  } else if (k == "coupled") {
     if (value != 0.0 && s->scheme) return QNSCH_EINVAL;  // a primitive-method smoother
     s->coupled = value != 0.0;
-  } else if (k == "fuse_cells32") s->fuse32 = (int)value;
-  else if (k == "vanka_team_max") s->team_max = (int)value;
-  else if (k == "ch_team_max") s->ch_team_max = (int)value;
-  else if (k == "ch_team_max32") s->ch_team_max32 = (int)value;
-  else if (k == "vanka_team_max32") s->team_max32 = (int)value;
-  else if (k == "pdl") {
+  } else if (k == "pdl") {
     g_pdl_option = value != 0.0;
     qn::set_pdl(g_pdl_option.load());
-  }
-  else if (k == "precision") {
-    int p = (int)value;
-    if (p < 0 || p > 2 || (double)p != value) return QNSCH_EINVAL;
-    if (p != 0 && s->scheme) return QNSCH_EINVAL;  // the projection method runs in FP64
+  } else if (k == "precision") {
+    if (!count_of(value, 0, 2, &n)) return QNSCH_EINVAL;
+    if (n != 0 && s->scheme) return QNSCH_EINVAL;  // the projection method runs in FP64
     if (s->pending) return QNSCH_ESTATE;
-    s->precision = p;
+    s->precision = n;
   } else if (k == "scheme") {
-    if (value != 0.0 && value != 1.0) return QNSCH_EINVAL;
-    if (value == 1.0 && (s->coupled || s->precision != 0)) return QNSCH_EINVAL;
+    if (!count_of(value, 0, 1, &n)) return QNSCH_EINVAL;
+    if (n == 1 && (s->coupled || s->precision != 0)) return QNSCH_EINVAL;
     if (s->pending) return QNSCH_ESTATE;
-    s->scheme = (int)value;
-  } else return QNSCH_EINVAL;
+    s->scheme = n;
+  } else {
+    return QNSCH_EINVAL;
+  }
   return QNSCH_OK;
+}
+
+}  // namespace
+
+int qnsch_set_option(qnsch_t* s, const char* key, double value) {
+  if (!s || !key) return QNSCH_EINVAL;
+  int rc = set_option(s, std::string(key), value);
+  if (rc == QNSCH_OK) ++s->opt_version;  // the next cycle recaptures its graph
+  return rc;
 }
 
 int qnsch_get_option(const qnsch_t* s, const char* key, double* value) {

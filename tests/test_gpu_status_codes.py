@@ -142,3 +142,25 @@ def test_budget_refuses_and_releases(qn):
     finally:
         qn.set_budget(0)
         gc.enable()
+
+
+def test_option_values_out_of_range_are_refused(qn):
+    """A refused value gives QNSCH_EINVAL and leaves the option as it was (a NaN
+    tol would otherwise end every step before its first cycle)."""
+    s = qn.Solver(16, 16)
+    bad = [("tol", float("nan")), ("tol", -1.0), ("tol", float("inf")), ("nu1", -1),
+           ("nu2", 1.5), ("nu_coarse", 1001), ("maxcyc", -2), ("omega_vanka", 0.0),
+           ("M", 0.0), ("eta_st", -1.0), ("eps_mob", float("inf")), ("fuse_cells", -1),
+           ("vanka_team_max", float("nan")), ("ch_team_max32", 2.0 ** 31),
+           ("diverge_cycles", 0.5), ("step_time_limit", -1.0), ("precision", 3),
+           ("precision", float("nan")), ("scheme", 0.5), ("coupled", float("nan"))]
+    for key, value in bad:
+        before = s.get_option(key)
+        with pytest.raises(qn.QnschError) as e:
+            s.set_option(key, value)
+        assert e.value.code == -1, (key, value)
+        assert s.get_option(key) == before, key
+    for key, value in [("tol", 0.0), ("nu1", 0), ("maxcyc", 0), ("vanka_team_max", 2 ** 31 - 1),
+                       ("omega_vanka", 1.5), ("step_time_limit", 0.25)]:
+        s.set_option(key, value)
+        assert s.get_option(key) == value, key
