@@ -87,7 +87,8 @@ int qnsch_set_allocator(void* (*alloc)(size_t bytes, void* ctx),
    parameter epsilon; Fr: Froude number, INFINITY (or <= 0) for no gravity.
    Derived (Sec. 8): M = Cn, eta = eta(rho1, rho2) of Sec. 8.1, mobility
    regularisation eps = Cn; each can be overridden with qnsch_set_option.
-   Returns QNSCH_EINVAL for an invalid grid or parameter, QNSCH_EBUDGET when
+   Returns QNSCH_EINVAL for an invalid grid or parameter (a non-finite Lx, a
+   NaN Fr, a density, viscosity, Re, We, Pe or Cn that is not > 0), QNSCH_EBUDGET when
    the handle's footprint would exceed the budget (qnsch_set_budget), and
    QNSCH_ENODEV without a CUDA device, checked in that order. */
 int qnsch_create(const qnsch_grid* grid, double rho1, double rho2, double eta1, double eta2,

@@ -844,7 +844,10 @@ int qnsch_set_allocator(void* (*alloc)(size_t, void*), void (*free_fn)(void*, vo
 int qnsch_create(const qnsch_grid* grid, double rho1, double rho2, double eta1, double eta2,
                  double Re, double We, double Pe, double Cn, double Fr, qnsch_t** out) {
   if (!grid || !out) return QNSCH_EINVAL;
-  if (grid->m1 < 2 || grid->m2 < 2 || !(grid->Lx > 0) || grid->periodic_y) return QNSCH_EINVAL;
+  if (grid->m1 < 2 || grid->m2 < 2 || !(grid->Lx > 0) || !std::isfinite(grid->Lx) ||
+      grid->periodic_y)
+    return QNSCH_EINVAL;
+  if (std::isnan(Fr)) return QNSCH_EINVAL;
   if (grid->periodic_x && (grid->m1 % 2 != 0 || grid->m1 < 4)) return QNSCH_EINVAL;
   if (!(rho1 > 0) || !(rho2 > 0) || !(eta1 > 0) || !(eta2 > 0) || !(Re > 0) || !(We > 0) ||
       !(Pe > 0) || !(Cn > 0))

@@ -101,3 +101,12 @@ def test_budget_refuses_creation_before_looking_for_a_device():
     finally:
         qnsch.set_budget(0)
     assert qnsch.budget()[0] == 0
+
+
+def test_create_rejects_nan_and_infinite_geometry_before_the_device():
+    from paper_1703_06606_gb300 import qnsch
+    for kw in (dict(Fr=float("nan")), dict(Lx=float("inf")), dict(Lx=float("nan")),
+               dict(rho1=float("nan")), dict(Cn=0.0)):
+        with pytest.raises(qnsch.QnschError) as e:
+            qnsch.Solver(16, 16, **kw)
+        assert e.value.code == -1, kw
