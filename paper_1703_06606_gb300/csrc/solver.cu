@@ -1136,7 +1136,7 @@ int qnsch_get_fields_device(const qnsch_t* s, double* c, double* mu, double* u, 
 }
 
 int qnsch_begin_step(qnsch_t* s, double dt) {
-  if (!s || !(dt > 0)) return QNSCH_EINVAL;
+  if (!s || !(dt > 0) || !std::isfinite(dt)) return QNSCH_EINVAL;
   int rc = begin(s, dt);
   if (rc) return rc;
   return sync(s);
@@ -1159,7 +1159,7 @@ int qnsch_commit_step(qnsch_t* s) {
 }
 
 int qnsch_step(qnsch_t* s, double dt, int* n_vcycles, double* final_residual) {
-  if (!s || !(dt > 0)) return QNSCH_EINVAL;
+  if (!s || !(dt > 0) || !std::isfinite(dt)) return QNSCH_EINVAL;
   if (s->pending) return QNSCH_ESTATE;
   const auto t0 = std::chrono::steady_clock::now();
   int rc = begin(s, dt);
@@ -1383,7 +1383,7 @@ int qnsch_batch_step(qnsch_batch_t* B, const double* dt, int* status, int* n_vcy
   if (!B || !dt || !status) return QNSCH_EINVAL;
   const int n = (int)B->inst.size();
   for (int a = 0; a < n; ++a)
-    if (!(dt[a] > 0) || B->inst[a]->pending) return QNSCH_EINVAL;
+    if (!(dt[a] > 0) || !std::isfinite(dt[a]) || B->inst[a]->pending) return QNSCH_EINVAL;
   std::vector<int> live(n, 1), cyc(n, 0), grew(n, 0);
   std::vector<char> wait(n, 0), late(n, 0);
   std::vector<double> res(n, HUGE_VAL);

@@ -164,3 +164,20 @@ def test_option_values_out_of_range_are_refused(qn):
                        ("omega_vanka", 1.5), ("step_time_limit", 0.25)]:
         s.set_option(key, value)
         assert s.get_option(key) == value, key
+
+
+def test_time_step_must_be_positive_and_finite(qn):
+    P = W.small_case()
+    s = qn.Solver(**P.create_kwargs(), tol=P.tol)
+    s.set_fields(P.fields())
+    for dt in (0.0, -1e-3, float("inf"), float("nan")):
+        with pytest.raises(qn.QnschError) as e:
+            s.step(dt)
+        assert e.value.code == -1, dt
+        with pytest.raises(qn.QnschError) as e:
+            s.begin_step(dt)
+        assert e.value.code == -1, dt
+    with pytest.raises(qn.QnschError) as e:
+        qn.Batch([s]).step([float("inf")])
+    assert e.value.code == -1
+    s.step(P.dt)
