@@ -68,9 +68,13 @@ def poisson_requests(n, rate, seed=workloads.SEED, n_min=128, n_max=1024, steps=
 
 class Server:
     def __init__(self, budget_bytes=150e9, max_slots=256, precision=1, coupled=1,
-                 tuned_table=None):
+                 tuned_table=None, backend=None):
         """tuned_table: an autotune table (dict, or the path of its JSON file)
-        whose entries give the launch-shape options of matching requests."""
+        whose entries give the launch-shape options of matching requests.
+        backend: the module that provides Solver, Batch and footprint (the
+        qnsch binding; another object with the same three names drives the
+        admission and batching logic without a GPU)."""
+        self.qn = backend or qnsch
         self.budget = budget_bytes
         self.max_slots = max_slots
         self.precision = precision
@@ -87,7 +91,7 @@ class Server:
         return autotune.lookup(self.tuned, P, self.precision, self.coupled, 0, self.device)
 
     def footprint(self, P):
-        return qnsch.footprint(P.m1, P.m2, P.periodic_x, P.levels, self.precision, P.Lx)
+        return self.qn.footprint(P.m1, P.m2, P.periodic_x, P.levels, self.precision, P.Lx)
 
     def run(self, requests, keep_fields=False):
         """Serve `requests` (arrival times relative to now) to completion; returns
@@ -110,8 +114,8 @@ class Server:
                     break  # first in line waits for memory
                 waiting.pop(0)
                 P = r.problem
-                s = qnsch.Solver(**P.create_kwargs(), tol=P.tol, precision=self.precision,
-                                 coupled=self.coupled, **self.options(P))
+                s = self.qn.Solver(**P.create_kwargs(), tol=P.tol, precision=self.precision,
+                                   coupled=self.coupled, **self.options(P))
                 s.set_fields(P.fields())
                 r.admitted = time.perf_counter() - t0
                 resident.append((r, s, fp))
@@ -120,7 +124,7 @@ class Server:
             if not resident:
                 time.sleep(max(0.0, waiting[0].arrival - (time.perf_counter() - t0)))
                 continue
-            B = qnsch.Batch([s for _, s, _ in resident])
+            B = self.qn.Batch([s for _, s, _ in resident])
             ts = time.perf_counter()
             st, cyc = B.step([r.problem.dt for r, _, _ in resident])
             dur = (time.perf_counter() - ts) * 1e3
