@@ -162,6 +162,11 @@ class Solver:
         self.m1, self.m2 = int(m1), int(m2)
         self.periodic_x = bool(periodic_x)
         self.h = Lx / m1
+        # the creation parameters, as a checkpoint records them
+        self.params = dict(m1=self.m1, m2=self.m2, Lx=float(Lx), periodic_x=self.periodic_x,
+                           levels=int(levels), rho1=float(rho1), rho2=float(rho2),
+                           eta1=float(eta1), eta2=float(eta2), Re=float(Re), We=float(We),
+                           Pe=float(Pe), Cn=float(Cn), Fr=float(Fr))
         g = _Grid(self.m1, self.m2, float(Lx), int(periodic_x), 0, int(levels))
         h = _VP()
         _check(lib().qnsch_create(ctypes.byref(g), rho1, rho2, eta1, eta2, Re, We, Pe, Cn, Fr,
@@ -196,6 +201,30 @@ class Solver:
         out = ctypes.c_double()
         _check(lib().qnsch_get_option(self._h, key.encode(), ctypes.byref(out)), "get_option")
         return out.value
+
+    def options(self):
+        """Every per-handle option (the keys a checkpoint records) -> value."""
+        from . import checkpoint
+        return {k: self.get_option(k) for k in checkpoint.OPTIONS}
+
+    # ---- checkpoint / resume ----
+    def save_checkpoint(self, path, t=0.0, n=0):
+        """Write the committed state, creation parameters and options (plus the
+        caller's time t and step count n) to the .npz file `path`."""
+        from . import checkpoint
+        checkpoint.save(path, self.get_fields(), self.params, self.options(), t, n)
+
+    @classmethod
+    def from_checkpoint(cls, path, stream=None, **overrides):
+        """A new Solver in the state a checkpoint recorded: (solver, t, n).
+        `overrides` replace recorded options (e.g. a different tol)."""
+        from . import checkpoint
+        fields, params, opts, t, n = checkpoint.load(path)
+        s = cls(**params, stream=stream)
+        for k, v in dict(opts, **overrides).items():
+            s.set_option(k, v)
+        s.set_fields(fields)
+        return s, t, n
 
     @property
     def levels(self):

@@ -1,0 +1,48 @@
+"""Checkpoint files on CPU: a save/load round trip keeps the fields bit for
+bit, the parameters (an infinite Froude number included), the options, t and
+n; wrong shapes, missing parameters and an unknown format are refused; a
+failed write leaves no partial file in place."""
+import json
+
+import numpy as np
+import pytest
+
+from paper_1703_06606_gb300 import checkpoint as C
+from paper_1703_06606_gb300 import workloads as W
+
+
+def _state(m1=24, m2=16, px=True):
+    P = W.small_case(m1, m2, px)
+    params = dict(P.create_kwargs())
+    rng = np.random.default_rng(3)
+    fields = {k: rng.standard_normal(s) for k, s in C.field_shapes(m1, m2).items()}
+    opts = {"scheme": 0.0, "precision": 1.0, "coupled": 1.0, "tol": 1e-9, "fuse_cells32": 2048.0}
+    return fields, params, opts
+
+
+def test_round_trip(tmp_path):
+    fields, params, opts = _state()
+    params["Fr"] = float("inf")
+    path = str(tmp_path / "a.npz")
+    C.save(path, fields, params, opts, t=0.125, n=17)
+    f2, p2, o2, t, n = C.load(path)
+    for k in C.FIELDS:
+        assert f2[k].dtype == np.float64 and np.array_equal(f2[k], fields[k])
+    assert p2 == params and o2 == opts and t == 0.125 and n == 17
+    assert list(o2) == [k for k in C.OPTIONS if k in opts]  # restore order
+
+
+def test_refusals(tmp_path):
+    fields, params, opts = _state()
+    bad = dict(fields, u=fields["u"][:, :-1])
+    with pytest.raises(ValueError):
+        C.save(str(tmp_path / "b.npz"), bad, params, opts)
+    with pytest.raises(ValueError):
+        C.save(str(tmp_path / "b.npz"), fields, {k: v for k, v in params.items() if k != "Re"},
+               opts)
+    assert not list(tmp_path.iterdir())
+    path = str(tmp_path / "c.npz")
+    meta = {"format": 99, "params": params, "options": {}, "t": 0.0, "n": 0}
+    np.savez(path, meta=np.array(json.dumps(meta)), **fields)
+    with pytest.raises(ValueError):
+        C.load(path)
