@@ -145,6 +145,27 @@ def paper_table2():
 # ---------------------------------------------------------------------------
 # the CPU oracle (reference arm and cpu_baseline)
 # ---------------------------------------------------------------------------
+def host_cpu():
+    """The host the CPU baselines ran on: architecture, CPU model (lscpu, else
+    /proc/cpuinfo) and logical cores."""
+    import platform
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        model = next((ln.split(":", 1)[1].strip() for ln in out.splitlines()
+                      if ln.lower().startswith("model name")), None)
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as f:
+                model = next((ln.split(":", 1)[1].strip() for ln in f
+                              if ln.lower().startswith("model name")), None)
+        except OSError:
+            pass
+    return {"arch": platform.machine(), "model": model, "nproc": os.cpu_count()}
+
+
 def oracle_rate(P, steps, budget_s):
     """Time the FP64 oracle (serial, as it stands) on the workload: up to `steps`
     implicit steps from the initial state, stopping once `budget_s` is spent."""
@@ -569,6 +590,7 @@ def run_ours(args, rank, world, local_rank):
             "sample": "first %d time step(s) of the rising-droplet 256x512 workload from its "
                       "initial state, serial FP64 oracle (%s V-cycles), %.1f s"
                       % (len(times), "/".join(map(str, cycles)), sum(times))}
+        line["cpu_baseline"]["host"] = host_cpu()
         if not args.no_cpu_all_cores:
             line["cpu_baseline"]["all_cores"] = oracle_all_cores(steps=1)
     print(json.dumps(line), flush=True)
@@ -611,6 +633,7 @@ def run_reference(args, rank, world):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": config_of(P, 8), "impl": "reference",
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "host": host_cpu(),
                          "sample": "first %d time step(s) of the workload from its initial "
                                    "state (%s V-cycles)" % (len(times),
                                                             "/".join(map(str, cycles)))},

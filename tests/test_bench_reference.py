@@ -22,6 +22,8 @@ def _check(line, n_gpus):
     assert line["value"] > 0 and line["unit"] == "cell-updates/s"
     assert line["config"]["workload"] == "rising_droplet_256x512"
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    host = line["cpu_baseline"]["host"]
+    assert host["nproc"] >= 1 and host["arch"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
 
 
