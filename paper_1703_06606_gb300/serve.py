@@ -167,6 +167,18 @@ def summarize(reqs, wall, max_resident):
             "mean_vcycles_per_step": float(np.mean([c for r in reqs for c in r.vcycles]))}
 
 
+def request_record(r):
+    """One request's log line: its grid and steps, arrival, admission and
+    finish times (seconds from the start of the run), per-step latencies (ms),
+    V-cycles per step and final status."""
+    return {"request": r.rid, "workload": r.problem.name, "grid": [r.problem.m1, r.problem.m2],
+            "steps": r.steps, "done_steps": r.done_steps, "status": r.status,
+            "arrival_s": r.arrival, "admitted_s": r.admitted, "finished_s": r.finished,
+            "queue_wait_ms": 1e3 * (r.admitted - r.arrival),
+            "latency_ms": 1e3 * (r.finished - r.arrival),
+            "step_ms": list(r.step_ms), "vcycles": list(r.vcycles)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--requests", type=int, default=40)
@@ -175,10 +187,15 @@ def main():
     ap.add_argument("--nmin", type=int, default=128)
     ap.add_argument("--nmax", type=int, default=1024)
     ap.add_argument("--budget-gb", type=float, default=150.0)
+    ap.add_argument("--log", default=None, help="JSON lines, one per request")
     a = ap.parse_args()
     reqs = poisson_requests(a.requests, a.rate, n_min=a.nmin, n_max=a.nmax, steps=a.steps)
     srv = Server(budget_bytes=a.budget_gb * 1e9)
     reqs, _ = srv.run(reqs)
+    if a.log:
+        with open(a.log, "w") as f:
+            for r in reqs:
+                f.write(json.dumps(request_record(r)) + "\n")
     print(json.dumps(summarize(reqs, srv.wall, srv.max_resident)))
 
 

@@ -111,3 +111,17 @@ def test_a_request_larger_than_the_budget_is_refused():
     srv = serve.Server(budget_bytes=1000, backend=FakeBackend())
     with pytest.raises(ValueError):
         srv.run(reqs)
+
+
+def test_request_records():
+    import json
+    reqs = _requests([(32, 32)] * 3, [2, 1, 3])
+    be = FakeBackend(fail_names={"r1"})
+    reqs, _ = serve.Server(budget_bytes=1e9, backend=be).run(reqs)
+    recs = [json.loads(json.dumps(serve.request_record(r))) for r in reqs]
+    assert [(x["request"], x["status"], x["done_steps"]) for x in recs] == [
+        (0, 0, 2), (1, -4, 1), (2, 0, 3)]
+    for x in recs:
+        assert len(x["step_ms"]) == len(x["vcycles"]) == x["done_steps"]
+        assert x["arrival_s"] <= x["admitted_s"] <= x["finished_s"]
+        assert x["latency_ms"] >= x["queue_wait_ms"] >= 0.0
