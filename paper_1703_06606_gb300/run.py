@@ -72,6 +72,8 @@ WORKLOADS = {"drop": "rising_drop_256x512", "capillary": "capillary_64",
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="drop", choices=sorted(WORKLOADS))
+    ap.add_argument("--config", default=None,
+                    help="a JSON problem (workloads.Problem.to_json) instead of --workload")
     ap.add_argument("--resume", default=None, help="checkpoint to start from")
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--dt", type=float, default=None, help="default: the workload's")
@@ -83,7 +85,11 @@ def main(argv=None):
     ap.add_argument("--checkpoint", default=None)
     ap.add_argument("--every", type=int, default=0)
     a = ap.parse_args(argv)
-    P = getattr(workloads, WORKLOADS[a.workload])()
+    if a.config:
+        with open(a.config) as f:
+            P = workloads.Problem.from_json(f.read())
+    else:
+        P = getattr(workloads, WORKLOADS[a.workload])()
     over = {k: v for k, v in (("scheme", a.scheme), ("precision", a.precision),
                               ("coupled", a.coupled), ("tol", a.tol)) if v is not None}
     if a.resume:

@@ -17,6 +17,7 @@ Array layouts (numpy, C order, no ghost cells):
 from __future__ import annotations
 
 import dataclasses
+import json
 import math
 
 import numpy as np
@@ -62,6 +63,21 @@ class Problem:
 
     def fields(self):
         return initial_fields(self)
+
+    def to_json(self):
+        """The problem as a JSON object (an infinite Froude number as Infinity)."""
+        return json.dumps(dataclasses.asdict(self), sort_keys=True)
+
+    @classmethod
+    def from_json(cls, text):
+        """A problem from to_json's text, or from a hand-written JSON object
+        with the same keys (init and init_args may be left out)."""
+        d = json.loads(text)
+        names = {f.name for f in dataclasses.fields(cls)}
+        unknown = set(d) - names
+        if unknown:
+            raise ValueError("unknown problem keys: %s" % sorted(unknown))
+        return cls(**d)
 
 
 def cell_centres(m1, m2, h):

@@ -46,3 +46,14 @@ def test_refusals(tmp_path):
     np.savez(path, meta=np.array(json.dumps(meta)), **fields)
     with pytest.raises(ValueError):
         C.load(path)
+
+
+def test_problem_json_round_trip():
+    for P in (W.rising_drop_256x512(), W.capillary_64(), W.rayleigh_taylor_1024x4096(),
+              W.small_case(24, 16, True)):
+        Q = W.Problem.from_json(P.to_json())
+        assert Q == P
+        for k, a in P.fields().items():
+            assert np.array_equal(Q.fields()[k], a)
+    with pytest.raises(ValueError):
+        W.Problem.from_json('{"name": "x", "grid": 3}')
