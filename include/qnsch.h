@@ -74,9 +74,11 @@ typedef struct {
    current coarsest grid are even and the halved grid keeps at least 2 cells
    per side (periodic x: at least 4 cells across, an even number). */
 
-/* Device allocator used for every later allocation (process-wide).
+/* Device allocator of the handles created from now on (process-wide).
    alloc(bytes, ctx) returns device memory or NULL; free(ptr, ctx) releases it.
-   Passing NULL for both restores cudaMalloc/cudaFree. */
+   Passing NULL for both restores cudaMalloc/cudaFree.  A handle allocates and
+   frees through the allocator in effect when it was created, for its whole
+   life: changing the allocator affects only handles created afterwards. */
 int qnsch_set_allocator(void* (*alloc)(size_t bytes, void* ctx),
                         void (*free_fn)(void* ptr, void* ctx), void* ctx);
 

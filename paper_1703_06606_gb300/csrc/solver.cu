@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <mutex>
 #include <type_traits>
 #include <climits>
 #include <cmath>
@@ -36,9 +37,18 @@ std::atomic<long long> g_replayed{0};
 void* (*g_alloc)(size_t, void*) = nullptr;
 void (*g_free)(void*, void*) = nullptr;
 void* g_ctx = nullptr;
+std::mutex g_alloc_mu;  // guards the three above
 
-void* dev_alloc(size_t bytes) {
-  if (g_alloc) return g_alloc(bytes, g_ctx);
+// the allocator a handle uses for its whole life: the one in effect when it
+// was created (qnsch_set_allocator later changes only new handles)
+struct Allocator {
+  void* (*alloc)(size_t, void*) = nullptr;  // NULL: cudaMalloc / cudaFree
+  void (*free)(void*, void*) = nullptr;
+  void* ctx = nullptr;
+};
+
+void* dev_alloc(const Allocator& A, size_t bytes) {
+  if (A.alloc) return A.alloc(bytes, A.ctx);
   void* p = nullptr;
   if (cudaMalloc(&p, bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -46,9 +56,9 @@ void* dev_alloc(size_t bytes) {
   }
   return p;
 }
-void dev_free(void* p) {
+void dev_free(const Allocator& A, void* p) {
   if (!p) return;
-  if (g_free) g_free(p, g_ctx);
+  if (A.free) A.free(p, A.ctx);
   else cudaFree(p);
 }
 
@@ -155,6 +165,8 @@ struct qnsch_s {
   int diverge = 0;
   // device bytes reserved against the process-wide budget
   size_t reserved = 0;
+  // the allocator of every device block of this handle
+  Allocator mem;
   // grid
   int m1, m2, px, nlev, kcol;
   double h;
@@ -238,6 +250,9 @@ size_t padded_elems(int m1, int m2, int* pitch) {
 }
 
 void free_all(qnsch_s* s) {
+  // work still queued on the handle's own stream (the zero fills of a
+  // creation that failed part way) ends before its memory goes back
+  if (s->own_stream) cudaStreamSynchronize(s->own_stream);
   if (s->gexec) cudaGraphExecDestroy(s->gexec);
   s->gexec = nullptr;
   for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
@@ -248,7 +263,7 @@ void free_all(qnsch_s* s) {
   s->ev_norms = nullptr;
   if (s->own_stream) cudaStreamDestroy(s->own_stream);
   s->own_stream = nullptr;
-  for (void* b : s->blocks) dev_free(b);
+  for (void* b : s->blocks) dev_free(s->mem, b);
   s->blocks.clear();
   g_reserved -= s->reserved;
   s->reserved = 0;
@@ -272,7 +287,7 @@ int alloc_all(qnsch_s* s) {
     int pitch;
     size_t n = padded_elems(a, b, &pitch);
     if (l == 0) s->level_elems0 = n;
-    double* base = (double*)dev_alloc(n * NFIELD * sizeof(double));
+    double* base = (double*)dev_alloc(s->mem, n * NFIELD * sizeof(double));
     if (!base) return QNSCH_ENOMEM;
     s->blocks.push_back(base);
     if (cudaMemsetAsync(base, 0, n * NFIELD * sizeof(double), s->stream) != cudaSuccess)
@@ -298,7 +313,7 @@ int alloc_all(qnsch_s* s) {
     h *= 2.0;
   }
   size_t n0 = s->level_elems0;
-  double* st = (double*)dev_alloc(n0 * 5 * sizeof(double));
+  double* st = (double*)dev_alloc(s->mem, n0 * 5 * sizeof(double));
   if (!st) return QNSCH_ENOMEM;
   s->blocks.push_back(st);
   cudaMemsetAsync(st, 0, n0 * 5 * sizeof(double), s->stream);
@@ -309,14 +324,14 @@ int alloc_all(qnsch_s* s) {
   s->su = st + 3 * n0 + pitch0 + 1;
   s->sv = st + 4 * n0 + pitch0 + 1;
   int rows = qn::partial_rows_needed(s->m1, s->m2);
-  s->part = (double*)dev_alloc((size_t)rows * 10 * sizeof(double));
+  s->part = (double*)dev_alloc(s->mem, (size_t)rows * 10 * sizeof(double));
   if (!s->part) return QNSCH_ENOMEM;
   s->blocks.push_back(s->part);
   size_t nstage = (size_t)(s->m1 + 1) * (s->m2 + 1);
-  s->stage = (double*)dev_alloc(nstage * sizeof(double));
+  s->stage = (double*)dev_alloc(s->mem, nstage * sizeof(double));
   if (!s->stage) return QNSCH_ENOMEM;
   s->blocks.push_back(s->stage);
-  s->scal = (double*)dev_alloc(64 * sizeof(double));
+  s->scal = (double*)dev_alloc(s->mem, 64 * sizeof(double));
   if (!s->scal) return QNSCH_ENOMEM;
   s->blocks.push_back(s->scal);
   if (cudaMallocHost(&s->hbuf, 64 * sizeof(double)) != cudaSuccess) {
@@ -342,7 +357,7 @@ int alloc_err_levels(qnsch_s* s, std::vector<Lv<T>>& E) {
   std::vector<void*> got;
   auto fail = [&](int rc) {  // give back what this call took
     cudaStreamSynchronize(s->stream);
-    for (void* b : got) dev_free(b);
+    for (void* b : got) dev_free(s->mem, b);
     g_reserved -= need;
     return rc;
   };
@@ -350,7 +365,7 @@ int alloc_err_levels(qnsch_s* s, std::vector<Lv<T>>& E) {
     const Lv<double>& D = s->L[l];
     Lv<T>& L = out[l];
     size_t n = (size_t)D.pitch * (size_t)(D.m2 + 3);
-    T* base = (T*)dev_alloc(n * NFIELD_ERR * sizeof(T));
+    T* base = (T*)dev_alloc(s->mem, n * NFIELD_ERR * sizeof(T));
     if (!base) return fail(QNSCH_ENOMEM);
     got.push_back(base);
     if (cudaMemsetAsync(base, 0, n * NFIELD_ERR * sizeof(T), s->stream) != cudaSuccess) {
@@ -835,6 +850,7 @@ extern "C" {
 
 int qnsch_set_allocator(void* (*alloc)(size_t, void*), void (*free_fn)(void*, void*), void* ctx) {
   if ((alloc == nullptr) != (free_fn == nullptr)) return QNSCH_EINVAL;
+  std::lock_guard<std::mutex> lock(g_alloc_mu);
   g_alloc = alloc;
   g_free = free_fn;
   g_ctx = ctx;
@@ -870,6 +886,12 @@ int qnsch_create(const qnsch_grid* grid, double rho1, double rho2, double eta1, 
     return QNSCH_EBUDGET;
   }
   s->reserved = need;
+  {
+    std::lock_guard<std::mutex> lock(g_alloc_mu);
+    s->mem.alloc = g_alloc;
+    s->mem.free = g_free;
+    s->mem.ctx = g_ctx;
+  }
   s->rho1 = rho1;
   s->rho2 = rho2;
   s->mu1 = eta1;

@@ -181,3 +181,59 @@ def test_time_step_must_be_positive_and_finite(qn):
         qn.Batch([s]).step([float("inf")])
     assert e.value.code == -1
     s.step(P.dt)
+
+
+def test_allocator_hook_and_an_injected_allocation_failure(qn):
+    """Allocation faults injected on the host.  A handle created under a caller's
+    allocator takes every block from it and gives every block back on destroy,
+    with the same step result as cudaMalloc memory. It keeps that allocator
+    after the hook is reset. An allocator that fails part way makes
+    qnsch_create return QNSCH_ENOMEM, give back what it took and release its
+    budget reservation."""
+    import torch
+    ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+    FREE = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+    live, state = {}, {"left": None, "allocs": 0}
+
+    def alloc(nbytes, ctx):
+        if state["left"] is not None:
+            if state["left"] == 0:
+                return None
+            state["left"] -= 1
+        p = torch.cuda.caching_allocator_alloc(int(nbytes))
+        live[p] = int(nbytes)
+        state["allocs"] += 1
+        return p
+
+    def free(ptr, ctx):
+        if live.pop(ptr, None) is not None:
+            torch.cuda.caching_allocator_delete(ptr)
+
+    a_cb, f_cb = ALLOC(alloc), FREE(free)
+    L = qn.lib()
+    P = W.small_case()
+    ref = qn.Solver(**P.create_kwargs(), tol=P.tol)
+    ref.set_fields(P.fields())
+    ref.step(P.dt)
+    gc.collect()
+    _, u0 = qn.budget()
+    try:
+        assert L.qnsch_set_allocator(ctypes.cast(a_cb, ctypes.c_void_p),
+                                     ctypes.cast(f_cb, ctypes.c_void_p), None) == 0
+        s = qn.Solver(**P.create_kwargs(), tol=P.tol)
+        assert L.qnsch_set_allocator(None, None, None) == 0  # s keeps its allocator
+        s.set_fields(P.fields())
+        s.step(P.dt)
+        assert state["allocs"] > 0 and len(live) == state["allocs"]
+        assert _same(s, ref)
+        s.close()
+        assert not live
+        assert L.qnsch_set_allocator(ctypes.cast(a_cb, ctypes.c_void_p),
+                                     ctypes.cast(f_cb, ctypes.c_void_p), None) == 0
+        state["left"] = 2
+        with pytest.raises(qn.QnschError) as e:
+            qn.Solver(**P.create_kwargs(), tol=P.tol)
+        assert e.value.code == -3
+        assert not live and qn.budget()[1] == u0
+    finally:
+        L.qnsch_set_allocator(None, None, None)
