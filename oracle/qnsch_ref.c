@@ -1482,6 +1482,18 @@ int qnsch_ref_params(const ref_solver* s, double* out8) {
   return REF_OK;
 }
 
+int qnsch_ref_secants(const ref_solver* s, double a, double b, double* out7) {
+  if (!s || !out7) return REF_EINVAL;
+  out7[0] = Fdw(a);
+  out7[1] = Fdw(b);
+  out7[2] = gsec(a, b);
+  out7[3] = gsec_da(a, b);
+  out7[4] = rho_of(&s->P, a);
+  out7[5] = rho_of(&s->P, b);
+  out7[6] = rsec(&s->P, a, b);
+  return REF_OK;
+}
+
 int qnsch_ref_set_fields(ref_solver* s, const double* c, const double* mu, const double* u,
                          const double* v, const double* p) {
   if (!s || !c || !mu || !u || !v || !p) return REF_EINVAL;

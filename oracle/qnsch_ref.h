@@ -79,6 +79,9 @@ int qnsch_ref_energy(const ref_solver* s, double* E);
 int qnsch_ref_iterate_energy(const ref_solver* s, double* E);
 int qnsch_ref_iterate_dissipation(const ref_solver* s, double* D);
 int qnsch_ref_params(const ref_solver* s, double* out8);
+/* The pointwise functions of Sec. 2.1 and the secants of Sec. 4.1 at (a, b), for
+   tests: F(a), F(b), g(a,b), dg/da(a,b), rho(a), rho(b), r(a,b). */
+int qnsch_ref_secants(const ref_solver* s, double a, double b, double* out7);
 /* Sec. 8 diagnostics of the committed state (see qnsch_ref.c): out9 = {V_c,
    centroid y, max|div|, l2 div, max expansion, max compression, a1, y_top,
    y_bottom}; divergence field out[(j-1)*m1 + (i-1)], m1*m2 values. */

@@ -68,6 +68,7 @@ def lib():
         L.qnsch_ref_iterate_energy.argtypes = [vp, p]
         L.qnsch_ref_iterate_dissipation.argtypes = [vp, p]
         L.qnsch_ref_params.argtypes = [vp, p]
+        L.qnsch_ref_secants.argtypes = [vp, d, d, p]
         L.qnsch_ref_diagnostics.argtypes = [vp, p]
         L.qnsch_ref_projected_velocity.argtypes = [vp, p, p]
         L.qnsch_ref_divergence.argtypes = [vp, p]
@@ -145,6 +146,13 @@ class RefSolver:
         out = np.zeros(8)
         _check(lib().qnsch_ref_params(self._h, _ptr(out)), "params")
         keys = ("alpha", "eta", "K", "Lam", "M", "Fr_inv", "eps_m", "h")
+        return dict(zip(keys, out.tolist()))
+
+    def secants(self, a, b):
+        """F(a), F(b), g(a,b), dg/da(a,b), rho(a), rho(b), r(a,b) (Secs. 2.1, 4.1)."""
+        out = np.zeros(7)
+        _check(lib().qnsch_ref_secants(self._h, float(a), float(b), _ptr(out)), "secants")
+        keys = ("Fa", "Fb", "g", "g_a", "rho_a", "rho_b", "r")
         return dict(zip(keys, out.tolist()))
 
     # ---- fields ----

@@ -1,0 +1,79 @@
+"""Exact identities of the oracle's building blocks, on random inputs.
+
+Secants (Sec. 4.1): F(a) - F(b) = g(a,b)(a - b) for the double well
+F(c) = c^2 (c-1)^2 / 4, with g(a,a) = F'(a) = a(a-1)(a-1/2); rho(a) - rho(b) =
+r(a,b)(a - b) for rho(c) = rho1 rho2 / ((rho2 - rho1) c + rho1) and
+r = -alpha rho(a) rho(b); rho(1) = rho1, rho(0) = rho2; dg/da against central
+differences.
+
+Summation by parts (App. A): the CH operator L phi = grad_d.(A m^n grad_D phi)
+is read off the residual of (pm-num-phase) with c = c^n, u = v = p = 0 and
+mu = phi, where the time, advection and pressure terms vanish and
+r_c = (1/Pe) L phi.  With Neumann walls or periodic x, for random positive
+mobility and random phi, psi: <psi, L phi> = <phi, L psi> (self-adjoint),
+<phi, L phi> < 0 for non-constant phi and sum L phi = 0 (the fluxes cancel),
+L 1 = 0.  A wrong ghost value, a one-sided average or a dropped face breaks
+one of them."""
+import numpy as np
+import pytest
+
+from oracle.ref import RefSolver
+from paper_1703_06606_gb300 import workloads as W
+
+
+def _solver(m1=12, m2=10, px=False, rho1=1.0, rho2=3.0):
+    return RefSolver(m1, m2, periodic_x=px, rho1=rho1, rho2=rho2, eta1=1.0, eta2=2.0, Re=50.0,
+                     We=5.0, Pe=20.0, Cn=0.05, Fr=0.8)
+
+
+@pytest.mark.parametrize("rho1,rho2", [(1.0, 3.0), (1000.0, 1.0), (0.1, 1.0)])
+def test_secant_identities(rho1, rho2):
+    s = _solver(rho1=rho1, rho2=rho2)
+    rng = np.random.default_rng(11)
+    for a, b in rng.uniform(-0.5, 1.5, size=(200, 2)):
+        x = s.secants(a, b)
+        scale = 1.0 + abs(x["Fa"]) + abs(x["Fb"])
+        assert abs((x["Fa"] - x["Fb"]) - x["g"] * (a - b)) <= 4e-16 * scale * 8
+        rs = max(abs(x["rho_a"]), abs(x["rho_b"]))
+        assert abs((x["rho_a"] - x["rho_b"]) - x["r"] * (a - b)) <= 1e-14 * rs * (1 + abs(a - b))
+        e = 1e-6
+        fd = (s.secants(a + e, b)["g"] - s.secants(a - e, b)["g"]) / (2 * e)
+        assert abs(fd - x["g_a"]) <= 1e-8 * (1 + abs(fd))
+        assert abs(s.secants(a, a)["g"] - a * (a - 1) * (a - 0.5)) <= 1e-15 * (1 + abs(a) ** 3)
+    one, zero = s.secants(1.0, 0.0)["rho_a"], s.secants(1.0, 0.0)["rho_b"]
+    assert abs(one - rho1) <= 1e-14 * rho1 and abs(zero - rho2) <= 1e-14 * rho2
+
+
+def _begin(s, cn, dt=1e-2):
+    """Freeze c^n (and u^n = v^n = 0) for the operators of the step."""
+    s.set_fields(dict(s.zeros(), c=cn))
+    s.begin_step(dt)
+
+
+def _L(s, cn, phi):
+    """(1/Pe) grad_d.(A m(c^n) grad_D phi), up to the residual's sign, from the
+    residual of N_c at the iterate c = c^n, u = v = p = 0, mu = phi."""
+    s.set_iterate(dict(s.zeros(), c=cn, mu=phi))
+    r, _ = s.residual()
+    return r["c"]
+
+
+@pytest.mark.parametrize("px", [False, True])
+def test_ch_operator_is_self_adjoint_and_conservative(px):
+    m1, m2 = 12, 10
+    s = _solver(m1, m2, px)
+    rng = np.random.default_rng(5 + int(px))
+    cn = rng.uniform(0.05, 0.95, size=(m2, m1))
+    phi, psi = rng.standard_normal((2, m2, m1))
+    _begin(s, cn)
+    Lphi, Lpsi = _L(s, cn, phi), _L(s, cn, psi)
+    a, b = float(np.sum(psi * Lphi)), float(np.sum(phi * Lpsi))
+    assert abs(a - b) <= 1e-12 * (abs(a) + abs(b)), (a, b)
+    q1, q2 = float(np.sum(phi * Lphi)), float(np.sum(psi * Lpsi))
+    assert q1 != 0.0 and np.sign(q1) == np.sign(q2)
+    assert abs(np.sum(Lphi)) <= 1e-12 * np.sum(np.abs(Lphi))
+    L1 = _L(s, cn, np.ones((m2, m1)))
+    assert np.max(np.abs(L1)) <= 1e-12
+    # the sign is that of -(1/Pe)<grad phi, A m grad phi> on either side of the
+    # residual convention; both quadratic forms agree, and a constant is in
+    # the kernel, so the operator is semi-definite on this grid
