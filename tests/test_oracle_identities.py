@@ -77,3 +77,37 @@ def test_ch_operator_is_self_adjoint_and_conservative(px):
     # the sign is that of -(1/Pe)<grad phi, A m grad phi> on either side of the
     # residual convention; both quadratic forms agree, and a constant is in
     # the kernel, so the operator is semi-definite on this grid
+
+
+@pytest.mark.parametrize("px", [False, True])
+def test_pressure_gradient_is_minus_adjoint_of_divergence(px):
+    """h^2 sum_cells p (d.u) = -h^2 sum_edges (D p).u for u vanishing on walls
+    (App. A): the (1/M) D p of (pm-num-mx) and the d.u of (pm-num-mass), read
+    off the residuals.  With u^n = v^n = 0, c = c^n, mu = 0 and no gravity,
+    a state with only p nonzero gives r_u = -(1/M) D_x p, r_v = -(1/M) D_y p,
+    and a state with only u, v nonzero gives r_p = -(d_x u + d_y v)."""
+    m1, m2 = 12, 10
+    s = RefSolver(m1, m2, periodic_x=px, rho1=1.0, rho2=3.0, eta1=1.0, eta2=2.0, Re=50.0,
+                  We=5.0, Pe=20.0, Cn=0.05, Fr=float("inf"))
+    M = s.params()["M"]
+    rng = np.random.default_rng(9 + int(px))
+    cn = rng.uniform(0.05, 0.95, size=(m2, m1))
+    _begin(s, cn)
+    z = s.zeros()
+    p = rng.standard_normal((m2, m1))
+    u, v = rng.standard_normal(z["u"].shape), rng.standard_normal(z["v"].shape)
+    v[0, :] = v[-1, :] = 0.0  # walls in y
+    if px:
+        u[:, 0] = u[:, -1]  # one unknown
+    else:
+        u[:, 0] = u[:, -1] = 0.0  # walls in x
+    s.set_iterate(dict(z, c=cn, p=p))
+    rp_state, _ = s.residual()
+    s.set_iterate(dict(z, c=cn, u=u, v=v))
+    ru_state, _ = s.residual()
+    cols = slice(1, m1 + 1)  # periodic: columns 0 and m1 are one edge
+    lhs = float(np.sum(p * -ru_state["p"]))                    # sum p (d.u)
+    Du = -M * rp_state["u"][:, cols]                          # D_x p on the x-edges
+    Dv = -M * rp_state["v"]                                   # D_y p on the y-edges
+    rhs = -(float(np.sum(Du * u[:, cols])) + float(np.sum(Dv * v)))
+    assert abs(lhs - rhs) <= 1e-12 * (abs(lhs) + abs(rhs)), (lhs, rhs)
