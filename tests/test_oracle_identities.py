@@ -111,3 +111,58 @@ def test_pressure_gradient_is_minus_adjoint_of_divergence(px):
     Dv = -M * rp_state["v"]                                   # D_y p on the y-edges
     rhs = -(float(np.sum(Du * u[:, cols])) + float(np.sum(Dv * v)))
     assert abs(lhs - rhs) <= 1e-12 * (abs(lhs) + abs(rhs)), (lhs, rhs)
+
+
+def _edge_parts(r, m1, px):
+    """The unknowns of the x- and y-edge arrays (periodic x: columns 0 and m1
+    are one edge; walls: their entries are not unknowns)."""
+    if px:
+        return r["u"][:, 1:m1 + 1], r["v"][1:-1, :]
+    return r["u"][:, 1:m1], r["v"][1:-1, :]
+
+
+@pytest.mark.parametrize("px", [False, True])
+def test_momentum_operator_at_rest_is_symmetric_positive(px):
+    """With u^n = v^n = 0, c = c^n, mu = p = 0 and no gravity, the momentum rows
+    of (pm-num-mx) reduce to A rho^n u/dt (diagonal) plus the viscous terms,
+    (e1e1) included: a symmetric, positive definite operator on the interior
+    edges (its quadratic form is the kinetic-energy term plus the viscous
+    dissipation of Thm. 6.2).  Read off the residuals, r = -N."""
+    m1, m2 = 12, 10
+    s = RefSolver(m1, m2, periodic_x=px, rho1=1.0, rho2=3.0, eta1=1.0, eta2=20.0, Re=0.5,
+                  We=5.0, Pe=20.0, Cn=0.05, Fr=float("inf"))
+    rng = np.random.default_rng(13 + int(px))
+    cn = rng.uniform(0.05, 0.95, size=(m2, m1))
+    _begin(s, cn, dt=1.0)
+    z = s.zeros()
+
+    def field(seed):
+        g = np.random.default_rng(seed)
+        u, v = g.standard_normal(z["u"].shape), g.standard_normal(z["v"].shape)
+        v[0, :] = v[-1, :] = 0.0
+        if px:
+            u[:, 0] = u[:, -1]
+        else:
+            u[:, 0] = u[:, -1] = 0.0
+        return u, v
+
+    def N(u, v):
+        s.set_iterate(dict(z, c=cn, u=u, v=v))
+        r, _ = s.residual()
+        nu, nv = _edge_parts(r, m1, px)
+        return -nu, -nv
+
+    (u1, v1), (u2, v2) = field(1), field(2)
+    a_u, a_v = N(u1, v1)
+    b_u, b_v = N(u2, v2)
+    e1u, e1v = _edge_parts({"u": u1, "v": v1}, m1, px)
+    e2u, e2v = _edge_parts({"u": u2, "v": v2}, m1, px)
+    x = float(np.sum(e2u * a_u) + np.sum(e2v * a_v))
+    y = float(np.sum(e1u * b_u) + np.sum(e1v * b_v))
+    # the cross terms cancel between entries of order mu/(Re h^2): rounding is
+    # relative to the sum of the products' magnitudes
+    mag = float(np.sum(np.abs(e2u * a_u)) + np.sum(np.abs(e2v * a_v)))
+    assert abs(x - y) <= 1e-13 * mag, (x, y, mag)
+    q = float(np.sum(e1u * a_u) + np.sum(e1v * a_v))
+    kin = float(np.sum(e1u ** 2) + np.sum(e1v ** 2))
+    assert q > 0.0 and q > 0.1 * kin  # the time term alone gives about rho * kin
