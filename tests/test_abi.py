@@ -110,3 +110,59 @@ def test_create_rejects_nan_and_infinite_geometry_before_the_device():
         with pytest.raises(qnsch.QnschError) as e:
             qnsch.Solver(16, 16, **kw)
         assert e.value.code == -1, kw
+
+
+C_PROGRAM = r"""
+#include <stdio.h>
+#include "qnsch.h"
+
+typedef void (*any_fn)(void);
+static const any_fn every_call[] = {
+%s
+};
+
+int main(void) {
+  qnsch_grid g = {256, 512, 1.0, 0, 0, 0};
+  size_t fp = 0, b = 0, used = 0;
+  qnsch_t* h = NULL;
+  int rc_fp = qnsch_footprint(&g, 0, &fp);
+  qnsch_set_budget(fp - 1);
+  int rc_budget = qnsch_create(&g, 0.1, 1.0, 0.1, 1.0, 35.0, 10.0, 100.0, 0.01, 1.0, &h);
+  qnsch_budget(&b, &used);
+  qnsch_set_budget(0);
+  int rc_create = qnsch_create(&g, 0.1, 1.0, 0.1, 1.0, 35.0, 10.0, 100.0, 0.01, 1.0, &h);
+  if (rc_create == QNSCH_OK) qnsch_destroy(h);
+  printf("%%d %%zu %%d %%zu %%d %%d\n", rc_fp, fp, rc_budget, b, rc_create,
+         (int)(sizeof(every_call) / sizeof(every_call[0])));
+  return 0;
+}
+"""
+
+
+def test_header_is_plain_c_and_the_library_links_from_c(tmp_path):
+    """A C99 program (-pedantic -Werror) takes the address of every declared
+    call, links against libqnsch.so and runs the calls that need no device:
+    qnsch_footprint, the budget, and qnsch_create's refusals."""
+    import shutil
+    import subprocess
+    from paper_1703_06606_gb300 import qnsch
+    if not shutil.which("gcc"):
+        pytest.skip("no C compiler")
+    lib = qbuild.build()
+    names = declared_symbols()
+    src = tmp_path / "abi.c"
+    src.write_text(C_PROGRAM % ",\n".join("  (any_fn)%s" % n for n in names))
+    exe = tmp_path / "abi"
+    libdir = os.path.dirname(lib)
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                    "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe),
+                    "-L", libdir, "-l:" + os.path.basename(lib), "-Wl,-rpath," + libdir],
+                   check=True, capture_output=True, text=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True,
+                         timeout=60).stdout.split()
+    rc_fp, fp, rc_budget, b, rc_create, n = map(int, out)
+    assert rc_fp == 0 and fp == qnsch.footprint(256, 512)
+    assert rc_budget == -7 and b == fp - 1
+    import torch
+    assert rc_create == (0 if torch.cuda.is_available() else -2)
+    assert n == len(names)
