@@ -25,7 +25,9 @@ class FakeBackend:
         return m1 * m2
 
     def Solver(self, m1, m2, **kw):
-        return FakeSolver(self, m1, m2)
+        s = FakeSolver(self, m1, m2)
+        s.kw = kw
+        return s
 
     def Batch(self, solvers):
         return FakeBatch(self, solvers)
@@ -125,3 +127,20 @@ def test_request_records():
         assert len(x["step_ms"]) == len(x["vcycles"]) == x["done_steps"]
         assert x["arrival_s"] <= x["admitted_s"] <= x["finished_s"]
         assert x["latency_ms"] >= x["queue_wait_ms"] >= 0.0
+
+
+def test_tuned_options_reach_the_matching_requests():
+    """A tuned table's entry (autotune.key_of: device, grid, boundary,
+    precision, smoother) applies its launch-shape options to the requests it
+    matches, and to no other."""
+    from paper_1703_06606_gb300 import autotune
+    reqs = _requests([(32, 32), (64, 32), (32, 32)], [1, 1, 1])
+    P = reqs[1].problem
+    table = {autotune.key_of(P, 1, 1, 0, autotune.device_name()):
+             {"options": {"fuse_cells32": 2048, "vanka_team_max32": 0}, "ms_per_step": 1.0}}
+    be = FakeBackend()
+    serve.Server(budget_bytes=1e9, backend=be, tuned_table=table).run(reqs)
+    kws = {s.name: s.kw for s in be.created}
+    assert kws["r1"]["fuse_cells32"] == 2048 and kws["r1"]["vanka_team_max32"] == 0
+    assert "fuse_cells32" not in kws["r0"] and "fuse_cells32" not in kws["r2"]
+    assert all(kw["precision"] == 1 and kw["coupled"] == 1 for kw in kws.values())
