@@ -33,6 +33,8 @@ CANDIDATES = {
     "ch_team_max32": [0, 4096],
     "fuse_cells32": [512, 128, 2048],
 }
+# a candidate's steps are cut off at this multiple of the best time per step
+CUTOFF = 20.0
 # the options that shape the launches of each precision (0 FP64, 1 mixed,
 # 2 FP64 error form: its error levels use the FP64 thresholds)
 KNOBS = {
@@ -92,9 +94,15 @@ def tune(P, precision=0, coupled=0, scheme=0, steps=4, warmup=2, solver_cls=None
     def measure(opts):
         key = tuple(sorted(opts.items()))
         if key not in seen:
-            seen[key] = time_steps(solver_cls, P, dict(base, **opts), steps, warmup, clock)
+            # once a time is known, a candidate whose step takes 20 times as
+            # long is cut off by the step's time limit (QNSCH_ETIMEOUT) and
+            # counts as failed, so one pathological shape cannot stall the search
+            cap = {} if best_t is None else {"step_time_limit": max(CUTOFF * best_t, 2.0)}
+            seen[key] = time_steps(solver_cls, P, dict(base, **opts, **cap), steps, warmup,
+                                   clock)
         return seen[key]
 
+    best_t = None
     best_t = measure(best)
     for _ in range(rounds):
         changed = False

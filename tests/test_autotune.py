@@ -86,3 +86,24 @@ def test_every_knob_has_the_library_default_first():
         assert autotune.CANDIDATES[k][0] == v
     for p, knobs in autotune.KNOBS.items():
         assert all(k in autotune.CANDIDATES for k in knobs)
+
+
+def test_slow_candidates_are_cut_off_by_the_step_time_limit():
+    """After the first measurement every trial carries step_time_limit =
+    20 x the best time per step; a candidate slower than that fails its step
+    (as qnsch_step's QNSCH_ETIMEOUT would) and is skipped."""
+    clock, calls = FakeClock(), []
+
+    def cost(kw):
+        c = 100.0 if kw["fuse_cells"] == 4096 else 1.0
+        lim = kw.get("step_time_limit", 0.0)
+        if lim and c > lim:
+            raise RuntimeError("QNSCH_ETIMEOUT")
+        return c
+    P = W.small_case(32, 32, False)
+    best, t, hist = autotune.tune(P, precision=0, steps=2, warmup=0,
+                                  solver_cls=make_solver(clock, cost, calls), clock=clock)
+    assert "step_time_limit" not in calls[0] and "step_time_limit" not in best
+    assert all(c["step_time_limit"] == pytest.approx(20.0) for c in calls[1:])
+    assert best["fuse_cells"] != 4096 and t == pytest.approx(1.0)
+    assert any(h[0]["fuse_cells"] == 4096 and h[1] is None for h in hist)
