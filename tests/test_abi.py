@@ -166,3 +166,12 @@ def test_header_is_plain_c_and_the_library_links_from_c(tmp_path):
     import torch
     assert rc_create == (0 if torch.cuda.is_available() else -2)
     assert n == len(names)
+
+
+def test_binding_sets_argument_types_for_every_call():
+    """Every call the header declares has its ctypes argument types set in the
+    binding, so no Python value is passed by a guessed convention."""
+    from paper_1703_06606_gb300 import qnsch
+    L = qnsch.lib()
+    missing = [n for n in declared_symbols() if getattr(L, n).argtypes is None]
+    assert not missing, missing
