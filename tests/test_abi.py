@@ -175,3 +175,11 @@ def test_binding_sets_argument_types_for_every_call():
     L = qnsch.lib()
     missing = [n for n in declared_symbols() if getattr(L, n).argtypes is None]
     assert not missing, missing
+
+
+def test_oracle_binding_sets_argument_types_for_every_call():
+    from oracle import ref
+    text = open(os.path.join(ROOT, "oracle", "qnsch_ref.h")).read()
+    names = sorted(set(re.findall(r"^int\s+(qnsch_ref_\w+)\s*\(", text, flags=re.M)))
+    L = ref.lib()
+    assert names and not [n for n in names if getattr(L, n).argtypes is None]
