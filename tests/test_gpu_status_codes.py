@@ -1,8 +1,10 @@
-"""Failure detection of a step, made on the host without any GPU fault:
+"""Failure detection and refusals, made on the host without any GPU fault:
 step_time_limit ends a step with QNSCH_ETIMEOUT, diverge_cycles ends a
-diverging step early with QNSCH_ENOTCONV, and the device-memory budget refuses
-a creation or a mixed-precision step with QNSCH_EBUDGET.  Each failure leaves
-the committed state as it was and the handle usable."""
+diverging step early with QNSCH_ENOTCONV, the device-memory budget refuses a
+creation or a mixed-precision step with QNSCH_EBUDGET, out-of-range option
+values and time steps give QNSCH_EINVAL, and allocation failures injected
+through a caller's allocator give QNSCH_ENOMEM with every block returned.
+Each failure leaves the committed state as it was and the handle usable."""
 import ctypes
 import gc
 
