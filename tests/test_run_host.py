@@ -60,3 +60,50 @@ def test_failure_is_logged_and_checkpointed():
     recs = [json.loads(x) for x in log.getvalue().splitlines()]
     assert [(r["step"], r["status"]) for r in recs] == [(1, 0), (2, 0), (3, -4)]
     assert s.saved == [("ck.npz", 1.0, 2, 2)]
+
+
+class CliSolver(FakeSolver):
+    """Stand-in for qnsch.Solver in run.main: records its construction."""
+    made = []
+
+    def __init__(self, **kw):
+        super().__init__()
+        self.kw = kw
+        CliSolver.made.append(self)
+
+    def set_fields(self, f):
+        self.fields = f
+
+    def save_checkpoint(self, path, t=0.0, n=0):
+        with open(path, "w") as f:
+            json.dump({"t": t, "n": n}, f)
+
+    @classmethod
+    def from_checkpoint(cls, path, stream=None, **over):
+        with open(path) as f:
+            d = json.load(f)
+        s = cls(resumed=True, **over)
+        return s, d["t"], d["n"]
+
+
+def test_cli_wiring(tmp_path, monkeypatch, capsys):
+    from paper_1703_06606_gb300 import workloads as W
+    monkeypatch.setattr(run.qnsch, "Solver", CliSolver)
+    CliSolver.made.clear()
+    log, ck = str(tmp_path / "s.jsonl"), str(tmp_path / "s.ck")
+    run.main(["--workload", "small", "--steps", "3", "--tol", "1e-8", "--log", log,
+              "--checkpoint", ck, "--every", "2"])
+    s = CliSolver.made[-1]
+    assert s.kw["tol"] == 1e-8 and s.kw["m1"] == 32 and "c" in s.fields
+    assert len(open(log).read().splitlines()) == 3
+    assert json.loads(capsys.readouterr().out)["steps"] == 3
+    run.main(["--resume", ck, "--steps", "2", "--coupled", "1", "--log", log])
+    s = CliSolver.made[-1]
+    assert s.kw == {"resumed": True, "coupled": 1}
+    assert [json.loads(x)["step"] for x in open(log).read().splitlines()] == [1, 2, 3, 4, 5]
+    cfg = tmp_path / "p.json"
+    P = W.small_case(24, 16, False)
+    cfg.write_text(P.to_json())
+    run.main(["--config", str(cfg), "--steps", "1"])
+    s = CliSolver.made[-1]
+    assert (s.kw["m1"], s.kw["m2"], s.kw["periodic_x"], s.kw["tol"]) == (24, 16, False, P.tol)
