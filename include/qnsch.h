@@ -46,6 +46,12 @@
 extern "C" {
 #endif
 
+/* Version of this interface.  The major number changes when a call's meaning
+   or signature changes, the minor number when calls or options are added. */
+#define QNSCH_VERSION_MAJOR 1
+#define QNSCH_VERSION_MINOR 0
+#define QNSCH_VERSION_PATCH 0
+
 #define QNSCH_OK 0
 #define QNSCH_EINVAL (-1)   /* bad argument or option */
 #define QNSCH_ENODEV (-2)   /* no CUDA device */
@@ -56,6 +62,10 @@ extern "C" {
 #define QNSCH_EBUDGET (-7)  /* the device-memory budget (qnsch_set_budget) would be exceeded */
 #define QNSCH_ESTATE (-8)   /* call not valid in the current state (e.g. vcycle outside a step) */
 #define QNSCH_ECUDA (-9)    /* a CUDA call failed */
+
+/* The library's version (any pointer may be NULL): compare with the
+   QNSCH_VERSION_* macros of the header a program was compiled against. */
+int qnsch_version(int* major, int* minor, int* patch);
 
 typedef struct qnsch_s qnsch_t;
 

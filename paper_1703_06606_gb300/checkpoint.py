@@ -40,9 +40,10 @@ def field_shapes(m1, m2):
     return {"c": (m2, m1), "mu": (m2, m1), "p": (m2, m1), "u": (m2, m1 + 1), "v": (m2 + 1, m1)}
 
 
-def save(path, fields, params, options, t=0.0, n=0):
+def save(path, fields, params, options, t=0.0, n=0, library=None):
     """Write one checkpoint.  fields: the five arrays; params: the creation
-    parameters (PARAMS); options: option key -> value."""
+    parameters (PARAMS); options: option key -> value; library: the version of
+    the library that computed the state (recorded, not checked on load)."""
     missing = [k for k in PARAMS if k not in params]
     if missing:
         raise ValueError("checkpoint parameters missing: %s" % missing)
@@ -54,7 +55,8 @@ def save(path, fields, params, options, t=0.0, n=0):
             raise ValueError("field %s has shape %s, expected %s" % (k, a.shape, shapes[k]))
         arrays[k] = a
     meta = {"format": FORMAT, "params": {k: params[k] for k in PARAMS},
-            "options": {k: float(v) for k, v in options.items()}, "t": float(t), "n": int(n)}
+            "options": {k: float(v) for k, v in options.items()}, "t": float(t), "n": int(n),
+            "library": None if library is None else list(library)}
     tmp = "%s.tmp%d" % (path, os.getpid())
     with open(tmp, "wb") as f:
         np.savez(f, meta=np.array(json.dumps(meta)), **arrays)

@@ -955,6 +955,13 @@ int qnsch_footprint(const qnsch_grid* grid, int precision, size_t* bytes) {
   return QNSCH_OK;
 }
 
+int qnsch_version(int* major, int* minor, int* patch) {
+  if (major) *major = QNSCH_VERSION_MAJOR;
+  if (minor) *minor = QNSCH_VERSION_MINOR;
+  if (patch) *patch = QNSCH_VERSION_PATCH;
+  return QNSCH_OK;
+}
+
 int qnsch_set_budget(size_t bytes) {
   g_budget = bytes;
   return QNSCH_OK;

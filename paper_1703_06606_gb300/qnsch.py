@@ -77,6 +77,7 @@ def lib():
         L.qnsch_kernel_launches.argtypes = [ctypes.POINTER(ctypes.c_longlong)]
         L.qnsch_fma_probe.argtypes = [i, i, i, p]
         L.qnsch_set_budget.argtypes = [ctypes.c_size_t]
+        L.qnsch_version.argtypes = [ctypes.POINTER(i)] * 3
         L.qnsch_budget.argtypes = [ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]
         L.qnsch_fp64_issue_probe.argtypes = [i, i, i, i, p]
         L.qnsch_mass_noalloc.argtypes = [_VP, i, i, d, d, d, _VP, _VP]
@@ -94,6 +95,13 @@ def kernel_launches():
     n = ctypes.c_longlong()
     _check(lib().qnsch_kernel_launches(ctypes.byref(n)), "qnsch_kernel_launches")
     return n.value
+
+
+def version():
+    """qnsch_version: (major, minor, patch) of the loaded library."""
+    v = [ctypes.c_int() for _ in range(3)]
+    _check(lib().qnsch_version(*[ctypes.byref(x) for x in v]), "qnsch_version")
+    return tuple(x.value for x in v)
 
 
 def set_budget(nbytes):
@@ -212,7 +220,8 @@ class Solver:
         """Write the committed state, creation parameters and options (plus the
         caller's time t and step count n) to the .npz file `path`."""
         from . import checkpoint
-        checkpoint.save(path, self.get_fields(), self.params, self.options(), t, n)
+        checkpoint.save(path, self.get_fields(), self.params, self.options(), t, n,
+                        library=version())
 
     @classmethod
     def from_checkpoint(cls, path, stream=None, **overrides):

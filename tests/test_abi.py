@@ -132,8 +132,11 @@ int main(void) {
   qnsch_set_budget(0);
   int rc_create = qnsch_create(&g, 0.1, 1.0, 0.1, 1.0, 35.0, 10.0, 100.0, 0.01, 1.0, &h);
   if (rc_create == QNSCH_OK) qnsch_destroy(h);
-  printf("%%d %%zu %%d %%zu %%d %%d\n", rc_fp, fp, rc_budget, b, rc_create,
-         (int)(sizeof(every_call) / sizeof(every_call[0])));
+  int ma = -1, mi = -1, pa = -1;
+  qnsch_version(&ma, &mi, &pa);
+  int same = ma == QNSCH_VERSION_MAJOR && mi == QNSCH_VERSION_MINOR && pa == QNSCH_VERSION_PATCH;
+  printf("%%d %%zu %%d %%zu %%d %%d %%d\n", rc_fp, fp, rc_budget, b, rc_create,
+         (int)(sizeof(every_call) / sizeof(every_call[0])), same);
   return 0;
 }
 """
@@ -160,7 +163,8 @@ def test_header_is_plain_c_and_the_library_links_from_c(tmp_path):
                    check=True, capture_output=True, text=True)
     out = subprocess.run([str(exe)], check=True, capture_output=True, text=True,
                          timeout=60).stdout.split()
-    rc_fp, fp, rc_budget, b, rc_create, n = map(int, out)
+    rc_fp, fp, rc_budget, b, rc_create, n, same_version = map(int, out)
+    assert same_version == 1
     assert rc_fp == 0 and fp == qnsch.footprint(256, 512)
     assert rc_budget == -7 and b == fp - 1
     import torch
@@ -183,3 +187,11 @@ def test_oracle_binding_sets_argument_types_for_every_call():
     names = sorted(set(re.findall(r"^int\s+(qnsch_ref_\w+)\s*\(", text, flags=re.M)))
     L = ref.lib()
     assert names and not [n for n in names if getattr(L, n).argtypes is None]
+
+
+def test_version_matches_the_header():
+    from paper_1703_06606_gb300 import qnsch
+    text = open(os.path.join(ROOT, "include", "qnsch.h")).read()
+    want = tuple(int(re.search(r"#define QNSCH_VERSION_%s (\d+)" % k, text).group(1))
+                 for k in ("MAJOR", "MINOR", "PATCH"))
+    assert qnsch.version() == want
