@@ -202,22 +202,31 @@ int qnsch_set_fields_device(qnsch_t* h, const double* c, const double* mu, const
 int qnsch_get_fields_device(const qnsch_t* h, double* c, double* mu, double* u, double* v,
                             double* p);
 
-/* One time step: qnsch_begin_step, then V-cycles until the largest scaled
-   residual norm is <= tol, then qnsch_commit_step.  Writes the number of
-   V-cycles and the final norm (either pointer may be NULL).  Returns
+/* One time step of the scheme of Sec. 6.1 (primitive) or Sec. 6.2
+   (projection, option scheme = 1), solved by the FAS V-cycles of Sec. 7.1 /
+   7.2: qnsch_begin_step, then V-cycles until the largest scaled residual norm
+   is <= tol, then qnsch_commit_step.  Writes the number of V-cycles and the
+   final norm (either pointer may be NULL).  dt must be > 0 and finite
+   (QNSCH_EINVAL); a step begun with qnsch_begin_step and not committed gives
+   QNSCH_ESTATE.  Returns
    QNSCH_ENOTCONV, QNSCH_ENAN or QNSCH_ETIMEOUT, leaving the state at level n,
    when the iteration does not converge (maxcyc cycles, or diverge_cycles
    cycles of growth), turns non-finite or runs past step_time_limit; a
    refused budget reservation gives QNSCH_EBUDGET before any cycle. */
 int qnsch_step(qnsch_t* h, double dt, int* n_vcycles, double* final_residual);
-/* Freeze level-n data on every level (restrict c^n, u^n, v^n; derive rho^n,
-   m(c^n), mu(c^n), G(c^n)) and start the iterate at the level-n fields. */
+/* Freeze the level-n data of the step on every level (Sec. 6.1: restrict c^n,
+   u^n, v^n; derive rho^n, m(c^n), mu(c^n), G(c^n) and the momentum rows'
+   frozen coefficients) and start the iterate at the level-n fields.  dt > 0
+   and finite, else QNSCH_EINVAL; a pending step is discarded and begun
+   again. */
 int qnsch_begin_step(qnsch_t* h, double dt);
-/* One outer FAS V-cycle on the pending step, followed by removal of the mean of
-   p; writes [scaled l2 norms of r_c, r_mu, r_p, r_u, r_v, then their max norms]
-   after the cycle (NULL allowed). */
+/* One outer FAS V-cycle (Sec. 7.1; in mixed precision one defect-correction
+   cycle) on the pending step, followed by removal of the mean of p; writes
+   [scaled l2 norms of r_c, r_mu, r_p, r_u, r_v, then their max norms] after the
+   cycle into host memory (NULL allowed).  QNSCH_ESTATE without a pending step. */
 int qnsch_vcycle(qnsch_t* h, double* residual_norms10);
-/* Accept the iterate as level n+1. */
+/* Accept the iterate as level n+1 (whatever its residual) and record the
+   step's dissipation (Thm. 6.2).  QNSCH_ESTATE without a pending step. */
 int qnsch_commit_step(qnsch_t* h);
 
 /* Diagnostics of the experiments of Sec. 8, reduced in FP64 on the device from
@@ -248,23 +257,29 @@ int qnsch_mass(const qnsch_t* h, double* mass_rho, double* mass_rhoc);
    the dissipation of the last committed step (0 before the first step). */
 int qnsch_energy(const qnsch_t* h, double* E, double* last_dissipation);
 
-/* Inspection of a pending step (valid between begin_step and commit_step). */
+/* Inspection of a pending step, host arrays in the layouts above (valid
+   between begin_step and commit_step, else QNSCH_ESTATE; NULL arrays give
+   QNSCH_EINVAL for set_iterate and are skipped by get_iterate). */
 int qnsch_set_iterate(qnsch_t* h, const double* c, const double* mu, const double* u,
                       const double* v, const double* p);
 int qnsch_get_iterate(const qnsch_t* h, double* c, double* mu, double* u, double* v, double* p);
-/* r = f - N(x) on the finest level (f = 0 there) into host arrays (NULL skips a
-   family) and the ten norms of qnsch_vcycle. */
+/* r = f - N(x) on the finest level (f = 0 there; N the discrete operator of
+   Sec. 6.1 or 6.2) into host arrays (NULL skips a family) and the ten norms of
+   qnsch_vcycle.  QNSCH_ESTATE without a pending step. */
 int qnsch_residual(qnsch_t* h, double* rc, double* rmu, double* rp, double* ru, double* rv,
                    double* norms10);
 /* Smoother pieces on the finest level (Sec. 7.1): one colour of the CH
    nonlinear Gauss-Seidel (colour 0: (i+j) even), one colour of the Vanka
    smoother ((i+2j) mod 5 with walls in x; with periodic x (2i+j) mod 8 when
    m1 = 0 mod 4, else (i+2j) mod K, K the smallest divisor >= 5 of m1), or
-   `sweeps` full smoothing steps (CH red, CH black, Vanka colours 0..K-1). */
+   `sweeps` full smoothing steps (CH red, CH black, Vanka colours 0..K-1).
+   A colour out of range or sweeps < 0 gives QNSCH_EINVAL, no pending step
+   QNSCH_ESTATE. */
 int qnsch_smooth_ch(qnsch_t* h, int colour);
 int qnsch_smooth_vanka(qnsch_t* h, int colour);
 int qnsch_smooth(qnsch_t* h, int sweeps);
-/* Energy and dissipation of the pending iterate against the frozen data. */
+/* Energy E_h of the pending iterate and the dissipation D_h of the step from
+   the frozen data to it (Thm. 6.2).  QNSCH_ESTATE without a pending step. */
 int qnsch_iterate_energy(const qnsch_t* h, double* E, double* D);
 
 /* Measurement hooks (no counterpart in the paper).  qnsch_profile(h, 1) starts
