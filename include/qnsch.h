@@ -188,15 +188,23 @@ int qnsch_footprint(const qnsch_grid* grid, int precision, size_t* bytes);
    "precision" cannot change between qnsch_begin_step and qnsch_commit_step. */
 int qnsch_set_option(qnsch_t* h, const char* key, double value);
 int qnsch_get_option(const qnsch_t* h, const char* key, double* value);
+/* Issue the handle's work on `cuda_stream` (a cudaStream_t; NULL: a private
+   non-blocking stream ordered after the legacy default stream at each call).
+   Waits for the work queued so far on the previous stream. */
 int qnsch_set_stream(qnsch_t* h, void* cuda_stream);
 int qnsch_levels(const qnsch_t* h);          /* number of levels, or < 0 */
 int qnsch_ncolours_vanka(const qnsch_t* h);  /* Vanka colours on the finest level */
 
-/* Committed state (time level n): host arrays in the layouts above. */
+/* Committed state (time level n, the fields of the scheme of Sec. 6.1): host
+   arrays in the layouts above, copied in or out before the call returns.
+   set_fields needs all five pointers (QNSCH_EINVAL) and no pending step
+   (QNSCH_ESTATE); get_fields skips NULL pointers. */
 int qnsch_set_fields(qnsch_t* h, const double* c, const double* mu, const double* u,
                      const double* v, const double* p);
 int qnsch_get_fields(const qnsch_t* h, double* c, double* mu, double* u, double* v, double* p);
-/* Same, with device pointers in the same (dense, ghost-free) layouts. */
+/* Same, with device pointers in the same (dense, ghost-free) layouts, ordered
+   after the caller's earlier work on the legacy default stream (or on the
+   handle's stream if one was set). */
 int qnsch_set_fields_device(qnsch_t* h, const double* c, const double* mu, const double* u,
                             const double* v, const double* p);
 int qnsch_get_fields_device(const qnsch_t* h, double* c, double* mu, double* u, double* v,
