@@ -188,9 +188,10 @@ int qnsch_footprint(const qnsch_grid* grid, int precision, size_t* bytes);
    "precision" cannot change between qnsch_begin_step and qnsch_commit_step. */
 int qnsch_set_option(qnsch_t* h, const char* key, double value);
 int qnsch_get_option(const qnsch_t* h, const char* key, double* value);
-/* Issue the handle's work on `cuda_stream` (a cudaStream_t; NULL: a private
-   non-blocking stream ordered after the legacy default stream at each call).
-   Waits for the work queued so far on the previous stream. */
+/* Issue the handle's work on `cuda_stream` (a cudaStream_t; NULL: the
+   handle's private non-blocking stream, which the device-array calls order
+   after the caller's earlier work on the legacy default stream).  Waits for
+   the work queued so far on the previous stream. */
 int qnsch_set_stream(qnsch_t* h, void* cuda_stream);
 int qnsch_levels(const qnsch_t* h);          /* number of levels, or < 0 */
 int qnsch_ncolours_vanka(const qnsch_t* h);  /* Vanka colours on the finest level */
@@ -202,9 +203,10 @@ int qnsch_ncolours_vanka(const qnsch_t* h);  /* Vanka colours on the finest leve
 int qnsch_set_fields(qnsch_t* h, const double* c, const double* mu, const double* u,
                      const double* v, const double* p);
 int qnsch_get_fields(const qnsch_t* h, double* c, double* mu, double* u, double* v, double* p);
-/* Same, with device pointers in the same (dense, ghost-free) layouts, ordered
-   after the caller's earlier work on the legacy default stream (or on the
-   handle's stream if one was set). */
+/* Same, with device pointers in the same (dense, ghost-free) layouts.  Without
+   a stream set by qnsch_set_stream they are ordered after the caller's earlier
+   work on the legacy default stream; with one, the caller orders its own work
+   on that stream. */
 int qnsch_set_fields_device(qnsch_t* h, const double* c, const double* mu, const double* u,
                             const double* v, const double* p);
 int qnsch_get_fields_device(const qnsch_t* h, double* c, double* mu, double* u, double* v,
