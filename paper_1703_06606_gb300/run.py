@@ -81,6 +81,10 @@ def main(argv=None):
     ap.add_argument("--coupled", type=int, default=None, choices=[0, 1])
     ap.add_argument("--scheme", type=int, default=None, choices=[0, 1])
     ap.add_argument("--tol", type=float, default=None)
+    ap.add_argument("--step-time-limit", type=float, default=None,
+                    help="seconds; a longer step fails with QNSCH_ETIMEOUT")
+    ap.add_argument("--diverge-cycles", type=int, default=None,
+                    help="stop a step whose residual grew over this many cycles")
     ap.add_argument("--log", default=None, help="JSON-lines step log (appended)")
     ap.add_argument("--checkpoint", default=None)
     ap.add_argument("--every", type=int, default=0)
@@ -91,7 +95,9 @@ def main(argv=None):
     else:
         P = getattr(workloads, WORKLOADS[a.workload])()
     over = {k: v for k, v in (("scheme", a.scheme), ("precision", a.precision),
-                              ("coupled", a.coupled), ("tol", a.tol)) if v is not None}
+                              ("coupled", a.coupled), ("tol", a.tol),
+                              ("step_time_limit", a.step_time_limit),
+                              ("diverge_cycles", a.diverge_cycles)) if v is not None}
     if a.resume:
         s, t, n = qnsch.Solver.from_checkpoint(a.resume, **over)
     else:

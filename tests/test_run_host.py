@@ -97,9 +97,10 @@ def test_cli_wiring(tmp_path, monkeypatch, capsys):
     assert s.kw["tol"] == 1e-8 and s.kw["m1"] == 32 and "c" in s.fields
     assert len(open(log).read().splitlines()) == 3
     assert json.loads(capsys.readouterr().out)["steps"] == 3
-    run.main(["--resume", ck, "--steps", "2", "--coupled", "1", "--log", log])
+    run.main(["--resume", ck, "--steps", "2", "--coupled", "1", "--log", log,
+              "--step-time-limit", "2.5", "--diverge-cycles", "3"])
     s = CliSolver.made[-1]
-    assert s.kw == {"resumed": True, "coupled": 1}
+    assert s.kw == {"resumed": True, "coupled": 1, "step_time_limit": 2.5, "diverge_cycles": 3}
     assert [json.loads(x)["step"] for x in open(log).read().splitlines()] == [1, 2, 3, 4, 5]
     cfg = tmp_path / "p.json"
     P = W.small_case(24, 16, False)
