@@ -1482,6 +1482,86 @@ int qnsch_ref_params(const ref_solver* s, double* out8) {
   return REF_OK;
 }
 
+/* host layout <-> ghosted level array, for one family (0 cell, 1 u, 2 v) */
+static void host_to_level(const ref_level* L, int fam, const double* h, double* a) {
+  int m1 = L->m1, m2 = L->m2;
+  if (fam == 0) {
+    for (int j = 1; j <= m2; ++j)
+      for (int i = 1; i <= m1; ++i) a[CI(L, i, j)] = h[(size_t)(j - 1) * m1 + (i - 1)];
+  } else if (fam == 1) {
+    for (int j = 1; j <= m2; ++j)
+      for (int i = 0; i <= m1; ++i) a[UI(L, i, j)] = h[(size_t)(j - 1) * (m1 + 1) + i];
+  } else {
+    for (int j = 0; j <= m2; ++j)
+      for (int i = 1; i <= m1; ++i) a[VI(L, i, j)] = h[(size_t)j * m1 + (i - 1)];
+  }
+}
+static void level_to_host(const ref_level* L, int fam, const double* a, double* h) {
+  int m1 = L->m1, m2 = L->m2;
+  if (fam == 0) {
+    for (int j = 1; j <= m2; ++j)
+      for (int i = 1; i <= m1; ++i) h[(size_t)(j - 1) * m1 + (i - 1)] = a[CI(L, i, j)];
+  } else if (fam == 1) {
+    for (int j = 1; j <= m2; ++j)
+      for (int i = 0; i <= m1; ++i) h[(size_t)(j - 1) * (m1 + 1) + i] = a[UI(L, i, j)];
+  } else {
+    for (int j = 0; j <= m2; ++j)
+      for (int i = 1; i <= m1; ++i) h[(size_t)j * m1 + (i - 1)] = a[VI(L, i, j)];
+  }
+}
+static size_t fam_size(const ref_level* L, int fam) {
+  return fam == 0 ? ncell(L) : fam == 1 ? nu_(L) : nv_(L);
+}
+
+int qnsch_ref_transfer(const ref_solver* s, int l, int op, const double* in, double* out) {
+  if (!s || !in || !out || l < 0 || l + 1 >= s->nlev || op < 0 || op > 5) return REF_EINVAL;
+  const ref_level* F = &s->lev[l];
+  const ref_level* C = &s->lev[l + 1];
+  int fam = op % 3;
+  if (op < 3) { /* residual restriction, fine -> coarse */
+    double* a = (double*)calloc(fam_size(F, fam), sizeof(double));
+    double* b = (double*)calloc(fam_size(C, fam), sizeof(double));
+    if (!a || !b) {
+      free(a);
+      free(b);
+      return REF_ENOMEM;
+    }
+    host_to_level(F, fam, in, a);
+    if (fam == 0) restrict_cell(F, C, a, b);
+    else if (fam == 1) restrict_u_fw(F, C, a, b);
+    else restrict_v_fw(F, C, a, b);
+    level_to_host(C, fam, b, out);
+    free(a);
+    free(b);
+    return REF_OK;
+  }
+  /* prolongation of a coarse correction, coarse -> fine, on copies of the two
+     levels whose iterate and saved arrays are zero except the input */
+  ref_level Ft = *F, Ct = *C;
+  size_t nf[3] = {ncell(F), nu_(F), nv_(F)}, nc[3] = {ncell(C), nu_(C), nv_(C)};
+  double* buf[4] = {NULL, NULL, NULL, NULL};
+  buf[0] = (double*)calloc(3 * nf[0] + nf[1] + nf[2], sizeof(double)); /* fine x */
+  buf[1] = (double*)calloc(3 * nc[0] + nc[1] + nc[2], sizeof(double)); /* coarse x */
+  buf[2] = (double*)calloc(3 * nc[0] + nc[1] + nc[2], sizeof(double)); /* coarse saved */
+  if (!buf[0] || !buf[1] || !buf[2]) {
+    free(buf[0]);
+    free(buf[1]);
+    free(buf[2]);
+    return REF_ENOMEM;
+  }
+  Ft.c = buf[0]; Ft.mu = Ft.c + nf[0]; Ft.p = Ft.mu + nf[0]; Ft.u = Ft.p + nf[0]; Ft.v = Ft.u + nf[1];
+  Ct.c = buf[1]; Ct.mu = Ct.c + nc[0]; Ct.p = Ct.mu + nc[0]; Ct.u = Ct.p + nc[0]; Ct.v = Ct.u + nc[1];
+  Ct.sc = buf[2]; Ct.smu = Ct.sc + nc[0]; Ct.sp = Ct.smu + nc[0]; Ct.su = Ct.sp + nc[0];
+  Ct.sv = Ct.su + nc[1];
+  host_to_level(C, fam, in, fam == 0 ? Ct.c : fam == 1 ? Ct.u : Ct.v);
+  prolong_correct(&Ft, &Ct);
+  level_to_host(F, fam, fam == 0 ? Ft.c : fam == 1 ? Ft.u : Ft.v, out);
+  free(buf[0]);
+  free(buf[1]);
+  free(buf[2]);
+  return REF_OK;
+}
+
 int qnsch_ref_secants(const ref_solver* s, double a, double b, double* out7) {
   if (!s || !out7) return REF_EINVAL;
   out7[0] = Fdw(a);

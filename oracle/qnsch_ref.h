@@ -82,6 +82,12 @@ int qnsch_ref_params(const ref_solver* s, double* out8);
 /* The pointwise functions of Sec. 2.1 and the secants of Sec. 4.1 at (a, b), for
    tests: F(a), F(b), g(a,b), dg/da(a,b), rho(a), rho(b), r(a,b). */
 int qnsch_ref_secants(const ref_solver* s, double a, double b, double* out7);
+/* The FAS grid transfers between level l and l+1 (reading R8), for tests, in
+   the host layouts of qnsch_ref_get_fields: op 0, 1, 2 restrict a fine
+   residual of cells, x-edges, y-edges to the coarse level (cell average;
+   full weighting on edges); op 3, 4, 5 prolongate a coarse correction of
+   cells, x-edges, y-edges to the fine level. */
+int qnsch_ref_transfer(const ref_solver* s, int l, int op, const double* in, double* out);
 /* Sec. 8 diagnostics of the committed state (see qnsch_ref.c): out9 = {V_c,
    centroid y, max|div|, l2 div, max expansion, max compression, a1, y_top,
    y_bottom}; divergence field out[(j-1)*m1 + (i-1)], m1*m2 values. */

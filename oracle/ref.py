@@ -69,6 +69,7 @@ def lib():
         L.qnsch_ref_iterate_dissipation.argtypes = [vp, p]
         L.qnsch_ref_params.argtypes = [vp, p]
         L.qnsch_ref_secants.argtypes = [vp, d, d, p]
+        L.qnsch_ref_transfer.argtypes = [vp, i, i, p, p]
         L.qnsch_ref_diagnostics.argtypes = [vp, p]
         L.qnsch_ref_projected_velocity.argtypes = [vp, p, p]
         L.qnsch_ref_divergence.argtypes = [vp, p]
@@ -147,6 +148,15 @@ class RefSolver:
         _check(lib().qnsch_ref_params(self._h, _ptr(out)), "params")
         keys = ("alpha", "eta", "K", "Lam", "M", "Fr_inv", "eps_m", "h")
         return dict(zip(keys, out.tolist()))
+
+    def transfer(self, level, op, a, out_shape):
+        """qnsch_ref_transfer: op 0-2 restrict fine cells / x-edges / y-edges of
+        level `level` to level + 1, op 3-5 prolongate from level + 1."""
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        out = np.zeros(out_shape)
+        _check(lib().qnsch_ref_transfer(self._h, int(level), int(op), _ptr(a), _ptr(out)),
+               "transfer")
+        return out
 
     def secants(self, a, b):
         """F(a), F(b), g(a,b), dg/da(a,b), rho(a), rho(b), r(a,b) (Secs. 2.1, 4.1)."""

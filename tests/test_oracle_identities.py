@@ -166,3 +166,48 @@ def test_momentum_operator_at_rest_is_symmetric_positive(px):
     q = float(np.sum(e1u * a_u) + np.sum(e1v * a_v))
     kin = float(np.sum(e1u ** 2) + np.sum(e1v ** 2))
     assert q > 0.0 and q > 0.1 * kin  # the time term alone gives about rho * kin
+
+
+def _shapes(m1, m2):
+    return {0: (m2, m1), 1: (m2, m1 + 1), 2: (m2 + 1, m1)}
+
+
+def _unknowns(fam, m1, m2, px):
+    """Mask of the unknowns of a family in its host layout (walls excluded;
+    with periodic x, x-edge 0 is edge m1)."""
+    mask = np.ones(_shapes(m1, m2)[fam], dtype=bool)
+    if fam == 1:
+        mask[:, 0] = False
+        if not px:
+            mask[:, m1] = False
+    if fam == 2:
+        mask[0, :] = mask[m2, :] = False
+    return mask
+
+
+@pytest.mark.parametrize("px", [False, True])
+def test_transfers_restriction_is_the_scaled_adjoint_of_prolongation(px):
+    """Reading R8: with area weights h^2 on the fine and (2h)^2 on the coarse
+    level, <R r, e>_H = <r, P e>_h for cells (average / piecewise constant) and
+    for both edge families (full weighting / linear in the normal direction),
+    over the unknowns; and R P = I on cells."""
+    m1, m2 = 16, 12
+    s = _solver(m1, m2, px)
+    rng = np.random.default_rng(21 + int(px))
+    M1, M2 = m1 // 2, m2 // 2
+    for fam in (0, 1, 2):
+        fine_mask = _unknowns(fam, m1, m2, px)
+        coarse_mask = _unknowns(fam, M1, M2, px)
+        r = rng.standard_normal(_shapes(m1, m2)[fam]) * fine_mask
+        e = rng.standard_normal(_shapes(M1, M2)[fam]) * coarse_mask
+        if fam == 1 and px:  # edge 0 is edge m1: the same unknown
+            r[:, 0] = r[:, m1]
+            e[:, 0] = e[:, M1]
+        Rr = s.transfer(0, fam, r, _shapes(M1, M2)[fam])
+        Pe = s.transfer(0, 3 + fam, e, _shapes(m1, m2)[fam])
+        lhs = 4.0 * float(np.sum((Rr * e)[coarse_mask]))
+        rhs = float(np.sum((r * Pe)[fine_mask]))
+        assert abs(lhs - rhs) <= 1e-13 * (np.sum(np.abs(r)) * np.max(np.abs(e))), (fam, lhs, rhs)
+    ec = rng.standard_normal((M2, M1))
+    back = s.transfer(0, 0, s.transfer(0, 3, ec, (m2, m1)), (M2, M1))
+    assert np.array_equal(back, ec)
