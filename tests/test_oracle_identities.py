@@ -13,7 +13,15 @@ r_c = (1/Pe) L phi.  With Neumann walls or periodic x, for random positive
 mobility and random phi, psi: <psi, L phi> = <phi, L psi> (self-adjoint),
 <phi, L phi> < 0 for non-constant phi and sum L phi = 0 (the fluxes cancel),
 L 1 = 0.  A wrong ghost value, a one-sided average or a dropped face breaks
-one of them."""
+one of them.
+
+Adjointness and definiteness of the momentum and mass rows: the discrete
+pressure gradient is minus the adjoint of the discrete divergence, and the
+momentum rows at rest are symmetric positive definite.
+
+Grid transfers (reading R8): the residual restriction is the area-weighted
+adjoint of the correction prolongation, for cells and both edge families,
+and R P = I on cells."""
 import numpy as np
 import pytest
 
