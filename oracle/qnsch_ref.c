@@ -1514,11 +1514,11 @@ static size_t fam_size(const ref_level* L, int fam) {
 }
 
 int qnsch_ref_transfer(const ref_solver* s, int l, int op, const double* in, double* out) {
-  if (!s || !in || !out || l < 0 || l + 1 >= s->nlev || op < 0 || op > 5) return REF_EINVAL;
+  if (!s || !in || !out || l < 0 || l + 1 >= s->nlev || op < 0 || op > 7) return REF_EINVAL;
   const ref_level* F = &s->lev[l];
   const ref_level* C = &s->lev[l + 1];
-  int fam = op % 3;
-  if (op < 3) { /* residual restriction, fine -> coarse */
+  int fam = op >= 6 ? op - 5 : op % 3;
+  if (op < 3 || op >= 6) { /* residual or state restriction, fine -> coarse */
     double* a = (double*)calloc(fam_size(F, fam), sizeof(double));
     double* b = (double*)calloc(fam_size(C, fam), sizeof(double));
     if (!a || !b) {
@@ -1527,7 +1527,9 @@ int qnsch_ref_transfer(const ref_solver* s, int l, int op, const double* in, dou
       return REF_ENOMEM;
     }
     host_to_level(F, fam, in, a);
-    if (fam == 0) restrict_cell(F, C, a, b);
+    if (op == 6) restrict_u(F, C, a, b);
+    else if (op == 7) restrict_v(F, C, a, b);
+    else if (fam == 0) restrict_cell(F, C, a, b);
     else if (fam == 1) restrict_u_fw(F, C, a, b);
     else restrict_v_fw(F, C, a, b);
     level_to_host(C, fam, b, out);

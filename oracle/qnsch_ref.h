@@ -86,7 +86,8 @@ int qnsch_ref_secants(const ref_solver* s, double a, double b, double* out7);
    the host layouts of qnsch_ref_get_fields: op 0, 1, 2 restrict a fine
    residual of cells, x-edges, y-edges to the coarse level (cell average;
    full weighting on edges); op 3, 4, 5 prolongate a coarse correction of
-   cells, x-edges, y-edges to the fine level. */
+   cells, x-edges, y-edges to the fine level; op 6, 7 restrict the iterate's
+   x-edges, y-edges (the mean of the two coincident fine edges; cells use op 0). */
 int qnsch_ref_transfer(const ref_solver* s, int l, int op, const double* in, double* out);
 /* Sec. 8 diagnostics of the committed state (see qnsch_ref.c): out9 = {V_c,
    centroid y, max|div|, l2 div, max expansion, max compression, a1, y_top,

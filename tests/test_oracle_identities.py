@@ -219,3 +219,33 @@ def test_transfers_restriction_is_the_scaled_adjoint_of_prolongation(px):
     ec = rng.standard_normal((M2, M1))
     back = s.transfer(0, 0, s.transfer(0, 3, ec, (m2, m1)), (M2, M1))
     assert np.array_equal(back, ec)
+
+
+@pytest.mark.parametrize("px", [False, True])
+def test_state_restriction_of_edges(px):
+    """Reading R8: a coarse edge's state is the mean of the two fine edges that
+    lie on it.  So a fine field that is antisymmetric across each such pair
+    restricts to zero, a constant stays constant, and restricting a
+    prolongated coarse field returns it."""
+    m1, m2 = 16, 12
+    s = _solver(m1, m2, px)
+    M1, M2 = m1 // 2, m2 // 2
+    rng = np.random.default_rng(31 + int(px))
+    # x-edges: fine rows 2J-1 and 2J lie on coarse row J
+    a = rng.standard_normal((M2, m1 + 1))
+    u = np.repeat(a, 2, axis=0) * np.tile([1.0, -1.0], M2)[:, None]
+    assert np.max(np.abs(s.transfer(0, 6, u, (M2, M1 + 1)))) == 0.0
+    ones = s.transfer(0, 6, np.full((m2, m1 + 1), 1.5), (M2, M1 + 1))
+    assert np.all(ones == 1.5)
+    # y-edges: fine columns 2I-1 and 2I lie on coarse column I
+    b = rng.standard_normal((m2 + 1, M1))
+    v = np.repeat(b, 2, axis=1) * np.tile([1.0, -1.0], M1)[None, :]
+    assert np.max(np.abs(s.transfer(0, 7, v, (M2 + 1, M1)))) == 0.0
+    for fam, op, shape_c, shape_f in ((1, 6, (M2, M1 + 1), (m2, m1 + 1)),
+                                      (2, 7, (M2 + 1, M1), (m2 + 1, m1))):
+        e = rng.standard_normal(shape_c) * _unknowns(fam, M1, M2, px)
+        if fam == 1 and px:
+            e[:, 0] = e[:, M1]
+        back = s.transfer(0, op, s.transfer(0, 3 + fam, e, shape_f), shape_c)
+        mask = _unknowns(fam, M1, M2, px)
+        assert np.allclose(back[mask], e[mask], rtol=0, atol=1e-15)
