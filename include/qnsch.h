@@ -339,7 +339,10 @@ int qnsch_fp64_issue_probe(int warps_per_block, int active_lanes, int chains, in
    qnsch_step on that handle, so its result does not depend on the batch.
    status[a] receives that instance's qnsch_step status (0, QNSCH_ENOTCONV,
    QNSCH_ENAN, ...), n_vcycles[a] (may be NULL) its V-cycle count.  The call
-   returns QNSCH_OK unless its arguments are invalid.  The batch does not own
+   returns QNSCH_OK unless its arguments are invalid: a dt that is not > 0 and
+   finite, a member with a pending step, or two members that have come to
+   share a stream (qnsch_set_stream after qnsch_batch_create) give
+   QNSCH_EINVAL before any work is queued.  The batch does not own
    the handles; destroy it before them. */
 typedef struct qnsch_batch_s qnsch_batch_t;
 int qnsch_batch_create(int n, qnsch_t* const* insts, qnsch_batch_t** out);

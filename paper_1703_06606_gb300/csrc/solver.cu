@@ -1411,8 +1411,13 @@ int qnsch_batch_size(const qnsch_batch_t* B) { return B ? (int)B->inst.size() : 
 int qnsch_batch_step(qnsch_batch_t* B, const double* dt, int* status, int* n_vcycles) {
   if (!B || !dt || !status) return QNSCH_EINVAL;
   const int n = (int)B->inst.size();
-  for (int a = 0; a < n; ++a)
+  for (int a = 0; a < n; ++a) {
     if (!(dt[a] > 0) || !std::isfinite(dt[a]) || B->inst[a]->pending) return QNSCH_EINVAL;
+    // a member moved onto another member's stream (qnsch_set_stream after
+    // qnsch_batch_create) would serialise their cycles and share their events
+    for (int b = 0; b < a; ++b)
+      if (B->inst[a]->stream == B->inst[b]->stream) return QNSCH_EINVAL;
+  }
   std::vector<int> live(n, 1), cyc(n, 0), grew(n, 0);
   std::vector<char> wait(n, 0), late(n, 0);
   std::vector<double> res(n, HUGE_VAL);

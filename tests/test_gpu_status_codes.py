@@ -239,3 +239,20 @@ def test_allocator_hook_and_an_injected_allocation_failure(qn):
         assert not live and qn.budget()[1] == u0
     finally:
         L.qnsch_set_allocator(None, None, None)
+
+
+def test_batch_refuses_members_that_came_to_share_a_stream(qn):
+    import torch
+    P = W.small_case()
+    a, b = _pair(qn, P)
+    B = qn.Batch([a, b])
+    st = torch.cuda.Stream()
+    a.set_stream(st)
+    b.set_stream(st)
+    with pytest.raises(qn.QnschError) as e:
+        B.step([P.dt, P.dt])
+    assert e.value.code == -1
+    a.set_stream(None)
+    b.set_stream(None)
+    status, _ = B.step([P.dt, P.dt])
+    assert status == [0, 0] and _same(a, b)
