@@ -163,7 +163,8 @@ def host_cpu():
                               if ln.lower().startswith("model name")), None)
         except OSError:
             pass
-    return {"arch": platform.machine(), "model": model, "nproc": os.cpu_count()}
+    return {"arch": platform.machine(), "model": model, "nproc": os.cpu_count(),
+            "usable": usable_cores(cap=1 << 20)}
 
 
 def oracle_rate(P, steps, budget_s):
@@ -205,6 +206,16 @@ def _oracle_replica(workload, steps, barrier, out):
     out.put((time.perf_counter() - t0, cycles))
 
 
+def usable_cores(cap=64):
+    """Cores this process may run on (its CPU affinity, which a container's
+    cpuset limits), else the machine's count; at most `cap`."""
+    try:
+        n = len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        n = os.cpu_count() or 1
+    return max(1, min(n, cap))
+
+
 def oracle_all_cores(workload="rising_drop_256x512", steps=1, procs=None, timeout=300.0):
     """Throughput of the FP64 oracle, as it stands, on every host core: one
     independent replica of the workload per core (spawned processes, so no
@@ -214,7 +225,7 @@ def oracle_all_cores(workload="rising_drop_256x512", steps=1, procs=None, timeou
     import multiprocessing as mp
     from oracle.ref import lib as oracle_lib
     oracle_lib()  # compiled once here, before the replicas load it
-    n = procs or os.cpu_count() or 1
+    n = procs or usable_cores()
     ctx = mp.get_context("spawn")
     barrier, out = ctx.Barrier(n), ctx.Queue()
     ps = [ctx.Process(target=_oracle_replica, args=(workload, steps, barrier, out), daemon=True)
