@@ -57,3 +57,16 @@ def test_problem_json_round_trip():
             assert np.array_equal(Q.fields()[k], a)
     with pytest.raises(ValueError):
         W.Problem.from_json('{"name": "x", "grid": 3}')
+
+
+def test_hand_written_problem_json():
+    """A problem written by hand: init and init_args may be left out (a flat
+    interface at mid-height, the capillary profile), Infinity is no gravity."""
+    text = ('{"name": "mine", "m1": 48, "m2": 32, "Lx": 1.5, "periodic_x": true, "levels": 0,'
+            ' "rho1": 1.0, "rho2": 2.0, "eta1": 1.0, "eta2": 1.0, "Re": 100.0, "We": 10.0,'
+            ' "Pe": 50.0, "Cn": 0.02, "Fr": Infinity, "dt": 0.001, "steps": 5, "tol": 1e-9}')
+    P = W.Problem.from_json(text)
+    assert P.init == "capillary" and P.init_args == {} and np.isinf(P.Fr)
+    assert P.h == 1.5 / 48 and P.create_kwargs()["periodic_x"] is True
+    c = P.fields()["c"]
+    assert c.shape == (32, 48) and c[0, 0] > 0.99 and c[-1, 0] < 0.01
