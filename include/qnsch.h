@@ -303,31 +303,6 @@ int qnsch_profile_read(qnsch_t* h, long long* launches, double* total_ms);
 /* Number of CUDA kernels this library has issued since it was loaded
    (process-wide, counted on the host at launch). */
 int qnsch_kernel_launches(long long* n);
-/* FMA throughput probe of the current device (a measurement utility with no
-   counterpart in the paper).  It launches blocks_per_sm x (SM count) blocks of
-   256 threads; each thread runs eight independent chains of 16 x iters fused
-   multiply-adds in FP64 (fp64 != 0) or FP32, and the call times five launches
-   after three untimed ones with CUDA events on the legacy default stream.
-   *tflops receives 2 x FMAs / seconds / 1e12.  It allocates and frees one
-   scratch array of blocks x 256 elements and synchronises before returning.
-   blocks_per_sm must lie in [1, 64] and iters in [1, 2^24], else QNSCH_EINVAL;
-   no device gives QNSCH_ENODEV. */
-int qnsch_fma_probe(int fp64, int blocks_per_sm, int iters, double* tflops);
-/* FP64 issue-cost probe (a measurement utility with no counterpart in the
-   paper).  It launches one block of warps_per_block warps per SM; in every warp
-   the lanes below active_lanes run `chains` independent chains (1, 2, 4 or 8)
-   of 16 x iters FP64 fused multiply-adds, the other lanes idle.  The block's
-   thread 0 reads the SM cycle counter around the loop.  *cycles_per_instr
-   receives the slowest block's cycles, best of three launches after one
-   untimed one, divided by the FMAs one warp issues and by the warps sharing
-   one of the SM's four sub-partitions (ceil(warps_per_block / 4)).  It
-   allocates and frees SM-count x 32 x warps_per_block doubles and SM-count
-   counters, and synchronises before returning.  warps_per_block in [1, 32],
-   active_lanes in [1, 32], iters in [1, 2^20], else QNSCH_EINVAL; no device
-   gives QNSCH_ENODEV. */
-int qnsch_fp64_issue_probe(int warps_per_block, int active_lanes, int chains, int iters,
-                           double* cycles_per_instr);
-
 /* Batches of independent instances (no counterpart in the paper; the way a
    GPU runs many small problems at once).  A batch refers to n existing
    handles, each with its own stream (handles created without qnsch_set_stream
@@ -352,10 +327,11 @@ int qnsch_batch_destroy(qnsch_batch_t* b);
 
 /* Mass reduction that allocates nothing (the paper has no counterpart: this is
    an interface for callers, not a step of the method).  It is meant for code
-   that cannot allocate device memory when it needs the result: work issued
-   while a stream is being captured into a CUDA graph, code running inside an
-   allocator or memory-pool callback, and programs whose device memory is fully
-   reserved up front by another framework.  It creates no handle and calls no
+   that cannot allocate device memory when it needs the result: code running
+   inside an allocator or memory-pool callback, where an allocation would
+   re-enter the allocator; programs whose device memory is fully reserved up
+   front by another framework; and loops that must not call cudaMalloc because
+   it can synchronise the device.  It creates no handle and calls no
    cudaMalloc, cudaFree or allocating library routine.
 
    c: device pointer to the m2 x m1 cell array (layout above); h: cell size;
@@ -367,13 +343,16 @@ int qnsch_batch_destroy(qnsch_batch_t* b);
 
    Limit: m1 * m2 <= QNSCH_NOALLOC_MAX_CELLS, else QNSCH_EINVAL.  Its scratch is
    one file-scope device array of 64 KiB (QNSCH_NOALLOC_MAX_CELLS / 2048 pairs
-   of doubles) that every GPU loading the library holds until the process
-   exits.  All calls share that array, so calls whose work overlaps on the GPU
-   (other streams, other host threads) race and must be serialised by the
-   caller; each call writes every entry it reads, so no clearing is needed.
-   The first call on a device looks up the array's device address
-   (cudaGetSymbolAddress) with that device current: make that first call
-   before starting any stream capture. */
+   of doubles).  It is placed on a device when the library's device code is
+   first loaded there (with lazy module loading, at this call's first use on
+   that device) and stays until the process exits.  All calls share that
+   array, so calls whose work overlaps on the GPU (other streams, other host
+   threads) race and must be serialised by the caller; each call writes every
+   entry it reads, so no clearing is needed.  The first call on a device looks
+   up the array's device address (cudaGetSymbolAddress) with that device
+   current and keeps it for the life of the process: make that first call
+   before starting any stream capture, and do not call this entry point again
+   after a reset of that device (cudaDeviceReset) in the same process. */
 #define QNSCH_NOALLOC_MAX_CELLS 8388608
 int qnsch_mass_noalloc(const double* c, int m1, int m2, double h, double rho1, double rho2,
                        double* out2, void* stream);

@@ -1,10 +1,13 @@
-"""Build the CUDA library libqnsch.so in-tree for sm_103a (GB300).
+"""Build the CUDA libraries in-tree for sm_103a (GB300).
 
     python -m paper_1703_06606_gb300.build [--force] [--verbose]
 
 Translation units are compiled in parallel with one -gencode
 (arch=compute_103a, code=sm_103a) and linked into
-paper_1703_06606_gb300/libqnsch.so next to this file.
+paper_1703_06606_gb300/libqnsch.so (the solver's C ABI, include/qnsch.h) and
+paper_1703_06606_gb300/libqnsch_probe.so (the FMA throughput and issue-cost
+probes that measure the FP64 roofline's denominator; measurement tooling, not
+part of the solver's ABI), both next to this file.
 """
 from __future__ import annotations
 
@@ -20,7 +23,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libqnsch.so")
-SOURCES = ["kernels.cu", "solver.cu", "noalloc.cu", "probe.cu"]
+PROBE_LIB = os.path.join(HERE, "libqnsch_probe.so")
+SOURCES = ["kernels.cu", "solver.cu", "noalloc.cu"]
+PROBE_SOURCES = ["probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -38,10 +43,13 @@ def _deps():
 
 
 def is_stale():
-    if not os.path.exists(LIB):
-        return True
-    t = os.path.getmtime(LIB)
-    return any(os.path.getmtime(d) > t for d in _deps())
+    for lib in (LIB, PROBE_LIB):
+        if not os.path.exists(lib):
+            return True
+        t = os.path.getmtime(lib)
+        if any(os.path.getmtime(d) > t for d in _deps()):
+            return True
+    return False
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
@@ -61,17 +69,19 @@ def build(force: bool = False, verbose: bool = False) -> str:
             raise RuntimeError("nvcc failed on %s:\n%s\n%s" % (src, r.stdout, r.stderr))
         return obj, r.stderr
 
-    with cf.ThreadPoolExecutor(len(SOURCES)) as ex:
-        res = list(ex.map(compile_one, SOURCES))
+    with cf.ThreadPoolExecutor(len(SOURCES) + len(PROBE_SOURCES)) as ex:
+        res = list(ex.map(compile_one, SOURCES + PROBE_SOURCES))
     if verbose:
         for _, err in res:
             sys.stderr.write(err)
-    tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in res]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
+    objs = [o for o, _ in res]
+    for lib, part in ((LIB, objs[:len(SOURCES)]), (PROBE_LIB, objs[len(SOURCES):])):
+        tmp = lib + ".tmp%d" % os.getpid()
+        cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + part
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
+        os.replace(tmp, lib)
     return LIB
 
 

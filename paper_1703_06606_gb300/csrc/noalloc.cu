@@ -1,13 +1,15 @@
 // noalloc.cu -- mass reduction that allocates no memory (qnsch_mass_noalloc).
 //
 // Some callers cannot allocate device memory at the moment they need a result:
-// code that runs while a stream is being captured into a CUDA graph (cudaMalloc
-// is not allowed there), code that runs inside a memory-pool or allocator
-// callback, and host programs whose memory budget is fully reserved up front by
-// another framework.  The handle-based qnsch_mass needs a solver handle, which
-// allocates the whole multigrid hierarchy.  This entry point instead takes the
-// caller's concentration array and output pointer and keeps its only scratch
-// (one partial sum pair per thread block) in a fixed, file-scope device array.
+// code that runs inside a memory-pool or allocator callback (an allocation
+// there would re-enter the allocator), host programs whose device memory is
+// fully reserved up front by another framework (a caching allocator that holds
+// all of HBM), and latency-critical loops that must not call cudaMalloc,
+// which can synchronise the device.  The handle-based qnsch_mass needs a
+// solver handle, which allocates the whole multigrid hierarchy.  This entry
+// point instead takes the caller's concentration array and output pointer and
+// keeps its only scratch (one partial sum pair per thread block) in a fixed,
+// file-scope device array.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -30,7 +32,11 @@ void* g_partials_addr[NA_MAX_DEVICES] = {};
 std::mutex g_setup_mu;
 
 // Device address of g_mass_partials for the current device (the host-side
-// symbol is only a stand-in and must never be passed to a kernel).
+// symbol is only a stand-in and must never be passed to a kernel).  The
+// address is looked up once per device ordinal and kept for the life of the
+// process; a device reset (cudaDeviceReset) unloads the module and leaves it
+// stale, so a program that resets a device must not call this entry point
+// again in the same process.
 int partials_address(void** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) {

@@ -1,10 +1,47 @@
-// probe.cu -- FMA probes of the GPU (measurement utilities, not part of the
-// scheme).  qnsch_fma_probe gives the FP64 peak that bench.py divides the FP64
-// kernels' achieved rate by: each thread runs eight independent FMA chains, so
-// the pipe, not the dependent-instruction latency, sets the rate.
-// qnsch_fp64_issue_probe gives the SM cycles one warp-wide FP64 FMA holds a
-// sub-partition for, as a function of the active lanes and of the independent
-// chains per lane: the cost model behind the solver's launch shapes.
+// probe.cu -- FMA probes of the GPU, built as libqnsch_probe.so: measurement
+// tooling with no counterpart in the paper and no part of the solver's ABI
+// (include/qnsch.h).  bench.py runs qnsch_fma_probe in its own process to get
+// the FP64 peak it divides the FP64 kernels' achieved rate by: each thread runs
+// eight independent FMA chains, so the pipe, not the dependent-instruction
+// latency, sets the rate.  qnsch_fp64_issue_probe gives the SM cycles one
+// warp-wide FP64 FMA holds a sub-partition for, as a function of the active
+// lanes and of the independent chains per lane: the cost model behind the
+// solver's launch shapes.
+//
+// Exported calls (status: 0 ok, -1 invalid argument, -2 no device, -3 out of
+// memory, -9 CUDA error; the codes of include/qnsch.h):
+//
+//   int qnsch_fma_probe(int fp64, int blocks_per_sm, int iters, double* tflops);
+//     blocks_per_sm x (SM count) blocks of 256 threads; each thread runs eight
+//     independent chains of 16 x iters fused multiply-adds in FP64 (fp64 != 0)
+//     or FP32; five launches are timed after three untimed ones with CUDA
+//     events on the legacy default stream.  *tflops = 2 x FMAs / s / 1e12.
+//     Allocates and frees one scratch array of blocks x 256 elements and
+//     synchronises.  blocks_per_sm in [1, 64], iters in [1, 2^24].
+//
+//   int qnsch_fp64_issue_probe(int warps_per_block, int active_lanes, int chains,
+//                              int iters, double* cycles_per_instr);
+//     one block of warps_per_block warps per SM; in every warp the lanes below
+//     active_lanes run `chains` (1, 2, 4 or 8) independent chains of 16 x iters
+//     FP64 FMAs; thread 0 reads the SM cycle counter around the loop.
+//     *cycles_per_instr = the slowest block's cycles (best of three launches
+//     after one untimed) / FMAs one warp issues / warps sharing one of the
+//     SM's four sub-partitions.  warps_per_block and active_lanes in [1, 32],
+//     iters in [1, 2^20].
+//
+//   int qnsch_stage_probe(int mode, int threads, int nb, int K, int stages,
+//                         double* us_per_stage);
+//     the cost of one dependent stage of a multigrid sweep: `stages` stages in
+//     which nb thread blocks of `threads` threads each run a dependent chain
+//     of K FP64 FMAs per thread.  mode 0: one cooperative launch of one block
+//     per SM, the stages separated by an inter-block barrier (an arrival
+//     counter in global memory, every wait bounded by about 2 s of SM clock;
+//     blocks >= nb skip the stages); mode 1: one launch per stage, captured
+//     into a CUDA graph, each with programmatic stream serialisation (the
+//     solver's own launch form).  *us_per_stage = best of five timed runs /
+//     stages, in microseconds.  threads in {32, 64, ..., 1024}, nb in
+//     [1, SM count], K in [0, 4096], stages in [1, 4096]; a barrier wait that
+//     runs out of time gives -6 (QNSCH_ETIMEOUT).
 #include <cuda_runtime.h>
 
 #include "qnsch.h"
@@ -146,7 +183,159 @@ int run_issue_probe(int warps, int active, int chains, int iters, double* cpi) {
   return rc;
 }
 
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// mode 0 of qnsch_stage_probe: the stages in one launch, blocks [0, nb) in
+// each, separated by an arrival counter (cumulative target nb per stage)
+__global__ void k_stage_persist(unsigned* ctr, int* err, double* sink, int S, int nb, int K) {
+  double x = 1.0 + threadIdx.x;
+  unsigned target = 0;
+  for (int s = 0; s < S; ++s) {
+    if ((int)blockIdx.x < nb) {
+      if (nb > 1 && s > 0) {
+        if (threadIdx.x == 0) {
+          const long long t0 = clock64();
+          while (ld_acquire_u32(ctr) < target) {
+            if (*(volatile int*)err) break;
+            if (clock64() - t0 > 4000000000LL) {
+              atomicExch(err, 1);
+              break;
+            }
+          }
+          __threadfence();
+        }
+        __syncthreads();
+      }
+      for (int k = 0; k < K; ++k) x = fma(x, 1.0000001, 1e-9);
+      __syncthreads();
+      if (nb > 1 && threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(ctr, 1u);
+      }
+    }
+    target += nb;
+  }
+  sink[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = x;
+}
+
+// mode 1 of qnsch_stage_probe: one stage per launch
+__global__ void k_stage_one(double* sink, int K) {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  double x = 1.0 + threadIdx.x;
+  for (int k = 0; k < K; ++k) x = fma(x, 1.0000001, 1e-9);
+  sink[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = x;
+}
+
+int run_stage_probe(int mode, int threads, int nb, int K, int S, double* us) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return QNSCH_ENODEV;
+  }
+  if (nb > sms) return QNSCH_EINVAL;
+  unsigned* ctr = nullptr;
+  int* err = nullptr;
+  double* sink = nullptr;
+  if (cudaMalloc(&ctr, sizeof(unsigned)) != cudaSuccess || cudaMalloc(&err, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&sink, (size_t)sms * threads * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(ctr);
+    cudaFree(err);
+    return QNSCH_ENOMEM;
+  }
+  cudaStream_t st = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  int rc = QNSCH_OK;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    rc = QNSCH_ECUDA;
+  if (rc == QNSCH_OK && mode == 1) {  // the graph of S dependent launches
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = QNSCH_ECUDA;
+    for (int s = 0; s < S && rc == QNSCH_OK; ++s) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(nb);
+      cfg.blockDim = dim3(threads);
+      cfg.stream = st;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      at[0].val.programmaticStreamSerializationAllowed = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      if (cudaLaunchKernelEx(&cfg, k_stage_one, sink, K) != cudaSuccess) rc = QNSCH_ECUDA;
+    }
+    if (rc == QNSCH_OK) {
+      if (cudaStreamEndCapture(st, &g) != cudaSuccess || cudaGraphInstantiate(&ge, g, 0) != cudaSuccess)
+        rc = QNSCH_ECUDA;
+    }
+    if (g) cudaGraphDestroy(g);
+  }
+  float best = 0.f;
+  for (int rep = 0; rep < 6 && rc == QNSCH_OK; ++rep) {  // the first run warms up
+    if (mode == 0) {
+      cudaMemsetAsync(ctr, 0, sizeof(unsigned), st);
+      cudaMemsetAsync(err, 0, sizeof(int), st);
+    }
+    cudaEventRecord(e0, st);
+    if (mode == 0) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(sms);
+      cfg.blockDim = dim3(threads);
+      cfg.stream = st;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeCooperative;
+      at[0].val.cooperative = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      if (cudaLaunchKernelEx(&cfg, k_stage_persist, ctr, err, sink, S, nb, K) != cudaSuccess)
+        rc = QNSCH_ECUDA;
+    } else if (cudaGraphLaunch(ge, st) != cudaSuccess) {
+      rc = QNSCH_ECUDA;
+    }
+    cudaEventRecord(e1, st);
+    float ms = 0.f;
+    if (rc == QNSCH_OK && (cudaStreamSynchronize(st) != cudaSuccess ||
+                           cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+      rc = QNSCH_ECUDA;
+    if (rc == QNSCH_OK && mode == 0) {
+      int herr = 0;
+      if (cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) rc = QNSCH_ECUDA;
+      else if (herr) rc = QNSCH_ETIMEOUT;
+    }
+    if (rc == QNSCH_OK && rep > 0 && (best == 0.f || ms < best)) best = ms;
+  }
+  if (rc == QNSCH_OK) *us = 1e3 * (double)best / S;
+  if (rc != QNSCH_OK) cudaGetLastError();
+  if (ge) cudaGraphExecDestroy(ge);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (st) cudaStreamDestroy(st);
+  cudaFree(ctr);
+  cudaFree(err);
+  cudaFree(sink);
+  return rc;
+}
+
 }  // namespace
+
+extern "C" int qnsch_stage_probe(int mode, int threads, int nb, int K, int stages,
+                                 double* us_per_stage) {
+  if (!us_per_stage || (mode != 0 && mode != 1) || threads < 32 || threads > 1024 ||
+      threads % 32 || nb < 1 || K < 0 || K > 4096 || stages < 1 || stages > 4096)
+    return QNSCH_EINVAL;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) {
+    cudaGetLastError();
+    return QNSCH_ENODEV;
+  }
+  return run_stage_probe(mode, threads, nb, K, stages, us_per_stage);
+}
 
 extern "C" int qnsch_fp64_issue_probe(int warps_per_block, int active_lanes, int chains, int iters,
                                       double* cycles_per_instr) {

@@ -75,11 +75,9 @@ def lib():
         L.qnsch_profile.argtypes = [_VP, i]
         L.qnsch_profile_read.argtypes = [_VP, ctypes.POINTER(ctypes.c_longlong), p]
         L.qnsch_kernel_launches.argtypes = [ctypes.POINTER(ctypes.c_longlong)]
-        L.qnsch_fma_probe.argtypes = [i, i, i, p]
         L.qnsch_set_budget.argtypes = [ctypes.c_size_t]
         L.qnsch_version.argtypes = [ctypes.POINTER(i)] * 3
         L.qnsch_budget.argtypes = [ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]
-        L.qnsch_fp64_issue_probe.argtypes = [i, i, i, i, p]
         L.qnsch_mass_noalloc.argtypes = [_VP, i, i, d, d, d, _VP, _VP]
         L.qnsch_batch_create.argtypes = [i, ctypes.POINTER(_VP), ctypes.POINTER(_VP)]
         L.qnsch_batch_step.argtypes = [_VP, p, ctypes.POINTER(i), ctypes.POINTER(i)]
@@ -114,25 +112,6 @@ def budget():
     b, u = ctypes.c_size_t(), ctypes.c_size_t()
     _check(lib().qnsch_budget(ctypes.byref(b), ctypes.byref(u)), "qnsch_budget")
     return b.value, u.value
-
-
-def fma_probe(fp64=True, blocks_per_sm=8, iters=4096):
-    """qnsch_fma_probe: FMA throughput of the current device in TFLOP/s (FP64
-    or FP32), the denominator of the FP64 kernels' ALU roofline."""
-    t = ctypes.c_double()
-    _check(lib().qnsch_fma_probe(int(bool(fp64)), int(blocks_per_sm), int(iters),
-                                 ctypes.byref(t)), "qnsch_fma_probe")
-    return t.value
-
-
-def fp64_issue_probe(warps_per_block=4, active_lanes=32, chains=8, iters=1024):
-    """qnsch_fp64_issue_probe: SM cycles one warp-wide FP64 FMA holds a
-    sub-partition for, with `active_lanes` lanes and `chains` independent
-    chains per lane."""
-    t = ctypes.c_double()
-    _check(lib().qnsch_fp64_issue_probe(int(warps_per_block), int(active_lanes), int(chains),
-                                        int(iters), ctypes.byref(t)), "qnsch_fp64_issue_probe")
-    return t.value
 
 
 def mass_noalloc(c, h, rho1, rho2, out2, stream=None):

@@ -41,34 +41,48 @@ def test_create_without_device_reports_enodev():
 
 
 def test_fma_probe_checks_arguments_then_device():
-    """qnsch_fma_probe rejects out-of-range shapes with QNSCH_EINVAL before it
-    touches the device, and reports QNSCH_ENODEV without one."""
-    from paper_1703_06606_gb300 import qnsch
+    """qnsch_fma_probe (libqnsch_probe.so) rejects out-of-range shapes with
+    QNSCH_EINVAL before it touches the device, and reports QNSCH_ENODEV
+    without one."""
+    from paper_1703_06606_gb300 import probe, qnsch
     for bad in ((0, 16), (65, 16), (8, 0), (8, (1 << 24) + 1)):
         with pytest.raises(qnsch.QnschError) as e:
-            qnsch.fma_probe(True, *bad)
+            probe.fma_probe(True, *bad)
         assert e.value.code == -1, bad
     import torch
     if torch.cuda.is_available():
         return
     with pytest.raises(qnsch.QnschError) as e:
-        qnsch.fma_probe(True, 8, 16)
+        probe.fma_probe(True, 8, 16)
     assert e.value.code == -2
 
 
 def test_fp64_issue_probe_checks_arguments_then_device():
-    from paper_1703_06606_gb300 import qnsch
+    from paper_1703_06606_gb300 import probe, qnsch
     for bad in ((0, 32, 8, 16), (33, 32, 8, 16), (4, 0, 8, 16), (4, 33, 8, 16), (4, 32, 3, 16),
                 (4, 32, 8, 0), (4, 32, 8, (1 << 20) + 1)):
         with pytest.raises(qnsch.QnschError) as e:
-            qnsch.fp64_issue_probe(*bad)
+            probe.fp64_issue_probe(*bad)
         assert e.value.code == -1, bad
     import torch
     if torch.cuda.is_available():
         return
     with pytest.raises(qnsch.QnschError) as e:
-        qnsch.fp64_issue_probe(4, 32, 8, 16)
+        probe.fp64_issue_probe(4, 32, 8, 16)
     assert e.value.code == -2
+
+
+def test_probes_are_not_in_the_solver_abi():
+    """The probes are measurement tooling: libqnsch.so does not export them and
+    include/qnsch.h does not declare them."""
+    import ctypes
+    from paper_1703_06606_gb300 import build, qnsch
+    qnsch.lib()
+    solver = ctypes.CDLL(build.LIB)
+    for name in ("qnsch_fma_probe", "qnsch_fp64_issue_probe"):
+        assert not hasattr(solver, name), name
+    hdr = open(os.path.join(ROOT, "include", "qnsch.h")).read()
+    assert "probe" not in hdr
 
 
 def test_status_names_match_the_header():

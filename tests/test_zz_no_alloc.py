@@ -1,8 +1,9 @@
 """qnsch_mass_noalloc: the mass reduction for callers that must not allocate.
 
-Code that runs during CUDA graph capture, inside an allocator callback, or under
-a device-memory budget reserved by another framework cannot call cudaMalloc when
-it needs a result.  qnsch_mass_noalloc serves them: it reads the caller's array,
+Code that runs inside an allocator or memory-pool callback, under a
+device-memory budget that another framework has reserved in full, or in a loop
+that must not synchronise the device cannot call cudaMalloc when it needs a
+result.  qnsch_mass_noalloc serves them: it reads the caller's array,
 writes the caller's output and keeps its scratch in a fixed device array of the
 library.  This test checks it, through the C ABI, against the handle-based
 qnsch_mass on the same fields, on two consecutive calls (the second call must
