@@ -167,12 +167,13 @@ def host_cpu():
             "usable": usable_cores(cap=1 << 20)}
 
 
-def oracle_rate(P, steps, budget_s):
+def oracle_rate(P, steps, budget_s, fields=None):
     """Time the FP64 oracle (serial, as it stands) on the workload: up to `steps`
-    implicit steps from the initial state, stopping once `budget_s` is spent."""
+    implicit steps from `fields` (default: the initial state), stopping once
+    `budget_s` is spent."""
     from oracle.ref import RefSolver
     r = RefSolver(**P.create_kwargs(), tol=P.tol)
-    r.set_fields(P.fields())
+    r.set_fields(P.fields() if fields is None else fields)
     times, cycles = [], []
     t_all = time.perf_counter()
     for _ in range(steps):
@@ -261,7 +262,7 @@ def oracle_all_cores(workload="rising_drop_256x512", steps=1, procs=None, timeou
 # ---------------------------------------------------------------------------
 def run_ours(args, rank, world, local_rank):
     import torch
-    from paper_1703_06606_gb300 import qnsch
+    from paper_1703_06606_gb300 import probe, qnsch
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
@@ -286,16 +287,18 @@ def run_ours(args, rank, world, local_rank):
     s.set_fields_device(dev_fields)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    s.profile(True)  # event timing of the finest Vanka launches is part of the replayed graph
     for _ in range(args.warmup):
         s.step(P.dt)
     torch.cuda.synchronize()
+    # the committed state the timed steps start from (the CPU baseline starts
+    # the oracle from it, so both time the same steps)
+    start_fields = s.get_fields()
 
-    # ---- timed region: K steps, device time per step (CUDA events on our stream)
+    # ---- timed region: K steps, device time per step (CUDA events on our
+    # stream); each step is one graph whose outer-cycle loop runs on the device
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
     cyc = []
-    s.profile(True)
     l0 = qnsch.kernel_launches()
     failed = None
     with ClockSampler(local_rank) as clk:
@@ -317,21 +320,19 @@ def run_ours(args, rank, world, local_rank):
         print("bench: a timed step failed: %s" % failed, file=sys.stderr, flush=True)
         replicas.slowest(0.0, dev, ok=False)  # every rank stops here
     launches = qnsch.kernel_launches() - l0
-    prof_n, prof_ms = s.profile_read()
-    if prof_n == 0:
-        # event timing unavailable inside the replayed graph: time the same kernel
-        # launches on two extra steps issued without the graph
-        s.set_option("graphs", 0)
-        s.profile(True)
-        for _ in range(2):
-            s.step(P.dt)
-        prof_n, prof_ms = s.profile_read()
-        s.set_option("graphs", 1)
-    s.profile(False)
+    device_loop = s.get_option("device_loop")
     step_ms = [a.elapsed_time(b) for a, b in evs]
     total_s = replicas.slowest(sum(step_ms) / 1e3, dev)
     if world > 1:
         dist.barrier()
+
+    # ---- kernel timing by kind on the same workload, right after the timed
+    # region: CUDA events around every launch of each kind inside the replayed
+    # cycle graphs (event records cannot sit inside the device-side loop's
+    # conditional body, so these steps drive their cycles from the host; the
+    # kernels and their launch shapes are the same)
+    kinds = prof_kinds(s, P, stream, flush, nsteps=max(2, min(args.steps, 5)))
+    fp64_peak = probe.fp64_peak_tflops()
 
     # ---- the same workload in the other solver variants: mixed precision (FP32
     # FAS cycles on the error equation under FP64 defect correction) and the
@@ -557,13 +558,14 @@ def run_ours(args, rank, world, local_rank):
     cells = P.cells
     value = world * cells * args.steps / total_s
     e2e_value = world * cells * args.steps / e2e_total
-    # dominant kernel: the FP64 Vanka smoother on the finest level, colour sweep
-    # = m1*m2/5 cell visits; algorithmic FP64 operations per visit from the kernel
-    visits = cells / 5.0
-    flops_per_visit = VANKA_FP64_FLOPS_PER_VISIT
-    avg_ms = prof_ms / max(prof_n, 1)
-    achieved = visits * flops_per_visit / (avg_ms * 1e-3) / 1e12
-    peak = FP64_PEAK_TFLOPS
+    roofline = roofline_of(kinds, fp64_peak)
+    step_flops = step_fp64_flops(s, P, float(np.mean(cyc)))
+    roofline["step"] = {
+        "achieved": step_flops / (float(np.mean(step_ms)) * 1e-3) / 1e12,
+        "flops_per_step": step_flops,
+        "frac": step_flops / (float(np.mean(step_ms)) * 1e-3) / 1e12 / fp64_peak,
+        "what": "algorithmic FP64 operations of a whole step (per-visit counts of the Vanka, "
+                "CH and residual kernels over every level, sweep and V-cycle) over ms_per_step"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)),
@@ -575,11 +577,10 @@ def run_ours(args, rank, world, local_rank):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": field_bytes(P),
                 "d2h_bytes_per_step": field_bytes(P)},
         "gpu_launches": int(launches),
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": VANKA_FP64_TRAFFIC_BYTES,
-                     "kernel": "k_vanka<double> finest level",
-                     "launches_timed": prof_n, "avg_launch_us": avg_ms * 1e3,
-                     "peak_source": "measured FP64 FMA throughput of this GPU model (DFMA loop probe)"},
+        "device_loop": bool(device_loop),
+        "roofline": roofline,
+        "kernel_shares": {k: {kk: v[kk] for kk in ("launches", "ms_per_step", "share", "visits")}
+                          for k, v in kinds["kinds"].items()},
         "clocks": clk.summary(),
     }
     if variants:
@@ -595,12 +596,15 @@ def run_ours(args, rank, world, local_rank):
     if serving is not None:
         line["serving"] = serving
     if world == 1 and not args.no_cpu_baseline:
-        times, cycles = oracle_rate(P, steps=3, budget_s=args.cpu_budget)
+        times, cycles = oracle_rate(P, steps=3, budget_s=args.cpu_budget, fields=start_fields)
         line["cpu_baseline"] = {
             "value": cells * len(times) / sum(times), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "first %d time step(s) of the rising-droplet 256x512 workload from its "
-                      "initial state, serial FP64 oracle (%s V-cycles), %.1f s"
-                      % (len(times), "/".join(map(str, cycles)), sum(times))}
+            "sample": "time steps %d..%d of the rising-droplet 256x512 workload (the first %d "
+                      "of the GPU's timed steps, from the GPU's committed state after its %d "
+                      "warm-up steps), serial FP64 oracle, %.1f s"
+                      % (args.warmup + 1, args.warmup + len(times), len(times), args.warmup,
+                         sum(times)),
+            "vcycles": cycles, "gpu_vcycles_same_steps": cyc[:len(times)]}
         line["cpu_baseline"]["host"] = host_cpu()
         if not args.no_cpu_all_cores:
             line["cpu_baseline"]["all_cores"] = oracle_all_cores(steps=1)
@@ -616,12 +620,103 @@ def run_ours(args, rank, world, local_rank):
 # coefficients, off-diagonals and the mass row, 4 momentum and 1 mass
 # residual, the structured block solve, 5 updates
 VANKA_FP64_FLOPS_PER_VISIT = 391.0
-# dram__bytes_read.sum + dram__bytes_write.sum of one finest-level k_vanka<double> launch at
-# 256x512 from one ncu capture of the current kernel; None once the kernel changes after
-# the capture
-VANKA_FP64_TRAFFIC_BYTES = 27.572e6
-# measured FP64 FMA throughput of one GB300 (dependent-chain-free DFMA loop)
-FP64_PEAK_TFLOPS = 1.193
+# FP64 operations per CH cell visit (N_c, N_mu, the 2x2 Jacobian, its solve and
+# rho of the new c) and per residual cell (all five families), as ncu counts
+# them executed (add, mul = 1, fma = 2) on the FP64 kernels
+CH_FP64_FLOPS_PER_VISIT = 241.0
+RESIDUAL_FP64_FLOPS_PER_CELL = 327.0
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of a timed kind, from one
+# ncu capture of the same kernel build (profiles/ file named beside it); a kind
+# without a capture of the current build reports traffic null
+TRAFFIC_BYTES = {}
+# words per cell a sweep moves at one pass over the arrays it needs (Sec. 7.1
+# smoothers; read c^n, u^n, v^n, c, mu, u, v, p and the three right-hand sides,
+# write u, v, p for the Vanka block; c^n, u, v, c, mu, p and two right-hand
+# sides, write c, mu for the CH block)
+VANKA_WORDS_PER_CELL = 14
+CH_WORDS_PER_CELL = 10
+
+
+def prof_kinds(s, P, stream, flush, nsteps):
+    """Time each kind of launch (qnsch_profile's kinds) with CUDA events over
+    `nsteps` steps of the workload, and the steps themselves; per kind: launches,
+    ms per step, share of the step's device time, cell visits per step."""
+    import torch
+    s.profile(15)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(nsteps)]
+    cyc = []
+    for k in range(nsteps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        n, _ = s.step(P.dt)
+        ev[k][1].record(stream)
+        cyc.append(n)
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    out = {"steps": nsteps, "ms_per_step": float(np.mean(ms)), "vcycles": cyc, "kinds": {}}
+    for kind in s.PROFILE_KINDS:
+        n, tot, vis = s.profile_read_kind(kind)
+        out["kinds"][kind] = {"launches": n, "ms_per_step": tot / nsteps,
+                              "share": tot / max(sum(ms), 1e-30), "visits": vis / nsteps,
+                              "avg_launch_us": 1e3 * tot / max(n, 1),
+                              "visits_per_launch": vis / max(n, 1)}
+    s.profile(False)
+    return out
+
+
+def roofline_of(kinds, fp64_peak):
+    """The roofline entry of the dominant kind of launch (largest share of the
+    step's device time): algorithmic FP64 operations per launch over its
+    average event-timed duration, against the FP64 peak measured in this run."""
+    name, k = max(kinds["kinds"].items(), key=lambda kv: kv[1]["share"])
+    per_visit = {"vanka_finest": VANKA_FP64_FLOPS_PER_VISIT,
+                 "vanka_levels": VANKA_FP64_FLOPS_PER_VISIT,
+                 "coarse_vcycle": VANKA_FP64_FLOPS_PER_VISIT + CH_FP64_FLOPS_PER_VISIT,
+                 "ch": CH_FP64_FLOPS_PER_VISIT}[name]
+    flops = k["visits_per_launch"] * per_visit
+    achieved = flops / (k["avg_launch_us"] * 1e-6) / 1e12
+    kernel = {"vanka_finest": "k_vanka<double> (finest level)",
+              "vanka_levels": "k_vanka_team<double> (levels below the finest)",
+              "coarse_vcycle": "k_coarse_vcycle<double> (fused coarse levels)",
+              "ch": "k_ch<double> (finest level)"}[name]
+    tr = TRAFFIC_BYTES.get(name)
+    return {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+            "frac": achieved / fp64_peak, "traffic": tr[0] if tr else None,
+            "traffic_source": tr[1] if tr else None,
+            "kernel": kernel, "share_of_step": k["share"], "launches_timed": k["launches"],
+            "avg_launch_us": k["avg_launch_us"], "flops_per_launch": flops,
+            "peak_source": "qnsch_fma_probe (FP64 FMA throughput, 8 independent chains per "
+                           "thread, best of 4/8/16 blocks per SM), run in this process",
+            "other_kinds": {n: {"share_of_step": v["share"],
+                                "avg_launch_us": v["avg_launch_us"]}
+                            for n, v in kinds["kinds"].items() if n != name}}
+
+
+def step_fp64_flops(s, P, cycles):
+    """Algorithmic FP64 operations of one step of `cycles` V-cycles: per V-cycle
+    on every level (m1/2^l x m2/2^l cells) nu1 + nu2 smoothing steps (one
+    Vanka and one CH visit per cell each; the coarsest level nu_coarse
+    ceil(n/4)^2 of them), one residual per level above the coarsest and one
+    coarse-operator evaluation per level below the finest; per step one
+    residual of the initial state and one per V-cycle with the norms."""
+    nlev = s.levels
+    nu = s.get_option("nu1") + s.get_option("nu2")
+    nuc = s.get_option("nu_coarse")
+    smooth = VANKA_FP64_FLOPS_PER_VISIT + CH_FP64_FLOPS_PER_VISIT
+    per_cycle = 0.0
+    for l in range(nlev):
+        c = (P.m1 >> l) * (P.m2 >> l)
+        if l == nlev - 1:
+            n = max(P.m1 >> l, P.m2 >> l)
+            q = max(1, (n + 3) // 4)
+            per_cycle += nuc * q * q * c * smooth
+        else:
+            per_cycle += nu * c * smooth + c * RESIDUAL_FP64_FLOPS_PER_CELL
+        if l > 0:
+            per_cycle += c * RESIDUAL_FP64_FLOPS_PER_CELL
+    per_cycle += P.cells * RESIDUAL_FP64_FLOPS_PER_CELL  # the norms' residual
+    return cycles * per_cycle + P.cells * RESIDUAL_FP64_FLOPS_PER_CELL
 
 
 def run_reference(args, rank, world):

@@ -29,9 +29,12 @@
  * the stream set by qnsch_set_stream; without one, on a private stream of the
  * handle that the device-array calls order after the caller's earlier work on
  * the legacy default stream.  Every call returns only after its work has
- * completed, unless stated.  Each outer V-cycle is captured once as a CUDA
- * graph and replayed (option "graphs", default 1; recaptured when dt or an
- * option changes).
+ * completed, unless stated.  qnsch_step runs the whole step as one CUDA
+ * graph whose outer-cycle loop and convergence test run on the device
+ * (option "device_loop", default 1); qnsch_vcycle, profiling and
+ * device_loop = 0 capture each outer V-cycle as a graph instead, with the
+ * host reading the norms between cycles (option "graphs", default 1).  Graphs
+ * are recaptured when dt or an option changes.
  *
  * Every call returns an int status: 0 on success, a negative QNSCH_E* code on
  * failure.  On failure no output is written and, unless stated, the handle is
@@ -133,7 +136,7 @@ int qnsch_footprint(const qnsch_grid* grid, int precision, size_t* bytes);
    "eps_mob": Cn, "precision": 0, "graphs": 1, "fuse_cells": 128,
    "fuse_cells32": 512, "coupled": 0, "scheme": 0, "vanka_team_max": 8192,
    "ch_team_max": 4096, "vanka_team_max32": 65536, "ch_team_max32": 0,
-   "pdl": 1, "step_time_limit": 0, "diverge_cycles": 0.
+   "pdl": 1, "step_time_limit": 0, "diverge_cycles": 0, "device_loop": 1.
    Unknown keys give QNSCH_EINVAL, and so do values out of range, which leave
    the option unchanged: NaN for any key; counts that are not integers in
    their range (nu1, nu2, nu_coarse: 0..1000; maxcyc, diverge_cycles:
@@ -141,11 +144,21 @@ int qnsch_footprint(const qnsch_grid* grid, int precision, size_t* bytes);
    four team thresholds: 0..2^31 - 1); tol or step_time_limit negative or
    infinite; omega_vanka, M, eta_st or eps_mob not positive and finite.
    step_time_limit (seconds, >= 0; 0: none): before each outer cycle of a
-   step, qnsch_step checks the wall time since the call began (qnsch_batch_step:
-   since its call began) and, once it exceeds the limit with the residual still
-   above tol, stops and returns QNSCH_ETIMEOUT without committing the step.  A
-   cycle already queued runs to its end, so a step can overrun the limit by one
-   outer cycle.
+   step, the step checks the time since it began (with device_loop, the GPU's
+   global timer since the step's first kernel; without, the host's wall clock
+   since the call began, or since qnsch_batch_step's call began) and, once it
+   exceeds the limit with the residual still above tol, stops and returns
+   QNSCH_ETIMEOUT without committing the step.  A cycle already running goes
+   to its end, so a step can overrun the limit by one outer cycle.
+   device_loop: 1 (with graphs = 1 and profiling off) runs qnsch_step and
+   qnsch_batch_step as one graph per step: the initial residual, a
+   conditional WHILE node around the outer cycle whose last kernel applies the
+   stopping rules above (tol, maxcyc, diverge_cycles, step_time_limit) on the
+   device, a conditional IF node around the commit, and one copy of the
+   outcome to the host; no host round trip per cycle.  Results, cycle counts
+   and statuses are those of the host-driven loop (0).  If the runtime refuses
+   to build that graph the handle sets device_loop to 0 and steps with the
+   host-driven loop.
    diverge_cycles (integer >= 0; 0: never): a step whose largest family
    residual has grown over this many consecutive outer cycles stops early and
    returns QNSCH_ENOTCONV without committing (failure detection for a step that
@@ -292,17 +305,44 @@ int qnsch_smooth(qnsch_t* h, int sweeps);
    the frozen data to it (Thm. 6.2).  QNSCH_ESTATE without a pending step. */
 int qnsch_iterate_energy(const qnsch_t* h, double* E, double* D);
 
-/* Measurement hooks (no counterpart in the paper).  qnsch_profile(h, 1) starts
-   bracketing every launch of the Vanka smoother on the finest level with a pair
-   of CUDA events on the handle's stream (at most 4096 launches between reads)
-   and resets the totals; qnsch_profile(h, 0) stops.  qnsch_profile_read
-   synchronises the stream and returns the number of timed launches and their
-   summed device time in milliseconds. */
+/* Measurement hooks (no counterpart in the paper).  qnsch_profile(h, mask)
+   starts bracketing launches with pairs of CUDA events on the handle's stream
+   (at most 4096 launches between reads) and resets the totals; mask 0 stops.
+   Bit k of mask (0..15, else QNSCH_EINVAL) times the launches of kind k:
+   0 the Vanka (or coupled, or projection 4x4) smoother on the finest level,
+   1 the same smoother's per-level launches on the levels below it,
+   2 the fused single-block V-cycle of the coarse levels, 3 the CH smoother on
+   the finest level.  Timing inserts event records into the replayed cycle
+   graph, so while any bit is set qnsch_step drives its cycles from the host
+   (device_loop is not used).  qnsch_profile_read synchronises the stream and
+   returns the number of timed launches and their summed device time in
+   milliseconds over all kinds; qnsch_profile_read_kind returns the same for
+   one kind plus the cell visits those launches made (for the fused V-cycle:
+   one visit per cell of each of its levels per smoothing step). */
 int qnsch_profile(qnsch_t* h, int enable);
 int qnsch_profile_read(qnsch_t* h, long long* launches, double* total_ms);
+int qnsch_profile_read_kind(qnsch_t* h, int kind, long long* launches, double* total_ms,
+                            double* visits);
 /* Number of CUDA kernels this library has issued since it was loaded
    (process-wide, counted on the host at launch). */
 int qnsch_kernel_launches(long long* n);
+/* Asynchronous step (no counterpart in the paper; the interface a server
+   uses to advance many instances without waiting for the slowest).
+   qnsch_step_launch queues one whole step of size dt on the handle's stream
+   and returns without waiting (with device_loop on: the step graph; without
+   it, the host-driven step runs inside the call).  Until qnsch_step_poll has
+   reported it done, the handle refuses other stepping calls with
+   QNSCH_ESTATE.  qnsch_step_poll does not wait: *done = 0 while the step is
+   on the GPU; once it has finished, *done = 1 and n_vcycles, final_residual,
+   status (what qnsch_step would have returned: 0, QNSCH_ENOTCONV, QNSCH_ENAN,
+   QNSCH_ETIMEOUT, ...) and device_ms (the step's device time between CUDA
+   events recorded around it on the handle's stream) receive the outcome;
+   any of those four may be NULL.  qnsch_step_poll without a launched step
+   gives QNSCH_ESTATE.  The result equals qnsch_step's on the same state. */
+int qnsch_step_launch(qnsch_t* h, double dt);
+int qnsch_step_poll(qnsch_t* h, int* done, int* n_vcycles, double* final_residual, int* status,
+                    double* device_ms);
+
 /* Batches of independent instances (no counterpart in the paper; the way a
    GPU runs many small problems at once).  A batch refers to n existing
    handles, each with its own stream (handles created without qnsch_set_stream

@@ -4,6 +4,7 @@
 // transfers, frozen-data setup, ghost filling (App. A.6), and FP64 reductions
 // for the norms, the mean of p, mass (Thm. 6.1) and energy (Thm. 6.2).
 #include <cuda_runtime.h>
+#include <math_constants.h>
 
 #include <atomic>
 #include <type_traits>
@@ -2356,6 +2357,68 @@ __global__ void k_dissipation(Prm<T> P, Lv<T> L, double w_visc, double w_div, do
 }
 
 // --------------------------------------------------------------------------
+// the outer-cycle loop of one step on the device (the step as one CUDA graph:
+// a conditional WHILE node repeats the cycle, a conditional IF node commits).
+// Control block ctl (doubles): [0] largest family residual r (scaled l2, NaN
+// if any family is not finite), [1] cycles done k, [2] consecutive cycles the
+// residual grew, [3] stopped by the time limit, [4] stopped by growth,
+// [5] commit, [6..10] l2 norms, [11..15] max norms, [16] (as a 64-bit
+// integer) the global timer in ns at the start of the step.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ long long global_ns() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__global__ void k_loop_clock(double* ctl) {
+  pdl_enter();
+  *reinterpret_cast<long long*>(ctl + 16) = global_ns();
+}
+
+// nrm: the norms of k_finalize ([0..4] max, [5..9] h^2 sum r^2).  The stopping
+// rule is the host loop's: continue while r is finite, r > tol and k < maxcyc;
+// stop after `diverge` consecutive cycles of growth; before a further cycle,
+// stop as late once the step has run longer than limit_ns.
+__global__ void k_loop_ctl(const double* nrm, double* ctl, cudaGraphConditionalHandle hl,
+                           cudaGraphConditionalHandle hc, double tol, int maxcyc, int diverge,
+                           double limit_ns, int first) {
+  pdl_enter();
+  double r = 0.0;
+  bool nan = false;
+  for (int q = 0; q < 5; ++q) {
+    double l2 = sqrt(nrm[5 + q]);
+    ctl[6 + q] = l2;
+    ctl[11 + q] = nrm[q];
+    if (!(l2 == l2)) nan = true;
+    else if (l2 > r) r = l2;
+  }
+  if (nan) r = CUDART_NAN;
+  double k = 0.0, grew = 0.0;
+  if (!first) {
+    k = ctl[1] + 1.0;
+    grew = r > ctl[0] ? ctl[2] + 1.0 : 0.0;
+  }
+  const bool div = !first && diverge > 0 && grew >= (double)diverge;
+  bool cont = !div && r == r && r > tol && k < (double)maxcyc;
+  bool late = false;
+  if (cont && limit_ns > 0.0 &&
+      (double)(global_ns() - *reinterpret_cast<const long long*>(ctl + 16)) > limit_ns) {
+    cont = false;
+    late = true;
+  }
+  const bool commit = !cont && r == r && !late && r <= tol;
+  ctl[0] = r;
+  ctl[1] = k;
+  ctl[2] = grew;
+  ctl[3] = late ? 1.0 : 0.0;
+  ctl[4] = div ? 1.0 : 0.0;
+  ctl[5] = commit ? 1.0 : 0.0;
+  cudaGraphSetConditional(hl, cont ? 1u : 0u);
+  cudaGraphSetConditional(hc, commit ? 1u : 0u);
+}
+
+// --------------------------------------------------------------------------
 // host layout <-> padded layout
 // --------------------------------------------------------------------------
 // kind 0: cell (m2 x m1), 1: u (m2 x (m1+1)), 2: v ((m2+1) x m1)
@@ -2650,6 +2713,17 @@ template <typename T>
 void launch_pack_out(const Lv<T>& L, double* dst, const T* src, int kind, cudaStream_t s) {
   int nx = kind == 1 ? L.m1 + 1 : L.m1, ny = kind == 2 ? L.m2 + 1 : L.m2;
   qlaunch(&k_pack_out<T>, grid2(nx, ny), dim3(BX, BY), 0, s, L, dst, src, kind);
+  ++g_launches;
+}
+
+void launch_loop_clock(double* ctl, cudaStream_t s) {
+  qlaunch(&k_loop_clock, 1, 1, 0, s, ctl);
+  ++g_launches;
+}
+void launch_loop_ctl(const double* nrm, double* ctl, cudaGraphConditionalHandle hl,
+                     cudaGraphConditionalHandle hc, double tol, int maxcyc, int diverge,
+                     double limit_ns, int first, cudaStream_t s) {
+  qlaunch(&k_loop_ctl, 1, 1, 0, s, nrm, ctl, hl, hc, tol, maxcyc, diverge, limit_ns, first);
   ++g_launches;
 }
 

@@ -78,6 +78,16 @@ void launch_dissipation(const Prm<T>& P, const Lv<T>& L, double w_visc, double w
 template <typename T> void launch_pack_in(const Lv<T>& L, T* dst, const double* src, int kind, cudaStream_t s);
 template <typename T> void launch_pack_out(const Lv<T>& L, double* dst, const T* src, int kind, cudaStream_t s);
 
+// the outer-cycle loop of a step on the device: ctl is the loop's control
+// block (layout in kernels.cu); launch_loop_clock records the step's start
+// time, launch_loop_ctl (first = 1 after the initial residual, 0 after each
+// cycle) updates the block from the norms nrm and sets the WHILE (hl) and
+// commit IF (hc) conditions of the step graph
+void launch_loop_clock(double* ctl, cudaStream_t s);
+void launch_loop_ctl(const double* nrm, double* ctl, cudaGraphConditionalHandle hl,
+                     cudaGraphConditionalHandle hc, double tol, int maxcyc, int diverge,
+                     double limit_ns, int first, cudaStream_t s);
+
 // kernels issued by this library since it was loaded
 long long launches_issued();
 // launch every kernel with programmatic dependent launch (1, the default) or

@@ -87,6 +87,11 @@ double seconds_since(std::chrono::steady_clock::time_point t0) {
 }
 
 constexpr int NFIELD = 45;  // arrays per level (see Lv)
+// doubles in s->scal and its pinned host mirror s->hbuf, and the offset of the
+// device-side step loop's control block in them (layout in kernels.cu)
+constexpr int NSCAL = 128;
+constexpr int CTL = 64;
+constexpr int CTL_LEN = 18;
 
 // option "pdl": programmatic dependent launch of every kernel (process-wide)
 static std::atomic<int> g_pdl_option{1};
@@ -197,14 +202,38 @@ struct qnsch_s {
   int g_precision = -1, g_prof = -1, g_ev_used = 0;
   unsigned g_opt = ~0u;
   long long g_nodes = 0;  // kernels in the captured graph
+  // the whole step as one graph whose outer-cycle loop runs on the device:
+  // the initial residual, a conditional WHILE node around the cycle, a
+  // conditional IF node around the commit, one copy of the results to the
+  // host (option "device_loop"; with it off, or while profiling, the host
+  // reads the norms after every cycle and queues the next one)
+  int device_loop = 1;
+  cudaGraphExec_t sexec = nullptr;
+  double s_dt = -1.0;
+  int s_precision = -1;
+  unsigned s_opt = ~0u;
+  long long s_pro = 0, s_body = 0, s_commit = 0;  // kernels in the graph's three parts
+  // a step queued by qnsch_step_launch and not yet collected by
+  // qnsch_step_poll: 1 on the device-side loop (events ev_s0/ev_s1 around it),
+  // 2 already run by the host-driven loop (its outcome kept below)
+  int async = 0;
+  int a_status = 0, a_cycles = 0;
+  double a_res = 0.0;
+  cudaEvent_t ev_s0 = nullptr, ev_s1 = nullptr;
   // the FP64 residual arrays of level 0 hold r(x) of the current iterate
   int res_valid = 0;
-  // optional CUDA-event timing of the finest-level Vanka launches
+  // optional CUDA-event timing of launches by kind (bit k of prof: kind k,
+  // see PK_*); every event pair carries its kind and the cell visits of the
+  // timed launch
   int prof = 0;
   std::vector<cudaEvent_t> ev;
+  std::vector<int> ev_kind;
+  std::vector<double> ev_visits;
   int ev_used = 0;
   long long prof_launches = 0;
   double prof_ms = 0.0;
+  long long pk_n[4] = {0, 0, 0, 0};
+  double pk_ms[4] = {0, 0, 0, 0}, pk_visits[4] = {0, 0, 0, 0};
   double dt = 0.0;
   double last_diss = 0.0;
 };
@@ -255,12 +284,17 @@ void free_all(qnsch_s* s) {
   if (s->own_stream) cudaStreamSynchronize(s->own_stream);
   if (s->gexec) cudaGraphExecDestroy(s->gexec);
   s->gexec = nullptr;
+  if (s->sexec) cudaGraphExecDestroy(s->sexec);
+  s->sexec = nullptr;
   for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
   s->ev.clear();
   if (s->ev_entry) cudaEventDestroy(s->ev_entry);
   s->ev_entry = nullptr;
   if (s->ev_norms) cudaEventDestroy(s->ev_norms);
   s->ev_norms = nullptr;
+  if (s->ev_s0) cudaEventDestroy(s->ev_s0);
+  if (s->ev_s1) cudaEventDestroy(s->ev_s1);
+  s->ev_s0 = s->ev_s1 = nullptr;
   if (s->own_stream) cudaStreamDestroy(s->own_stream);
   s->own_stream = nullptr;
   for (void* b : s->blocks) dev_free(s->mem, b);
@@ -274,7 +308,8 @@ void free_all(qnsch_s* s) {
 int alloc_all(qnsch_s* s) {
   if (cudaStreamCreateWithFlags(&s->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&s->ev_entry, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&s->ev_norms, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&s->ev_norms, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreate(&s->ev_s0) != cudaSuccess || cudaEventCreate(&s->ev_s1) != cudaSuccess) {
     cudaGetLastError();
     return QNSCH_ECUDA;
   }
@@ -331,10 +366,10 @@ int alloc_all(qnsch_s* s) {
   s->stage = (double*)dev_alloc(s->mem, nstage * sizeof(double));
   if (!s->stage) return QNSCH_ENOMEM;
   s->blocks.push_back(s->stage);
-  s->scal = (double*)dev_alloc(s->mem, 64 * sizeof(double));
+  s->scal = (double*)dev_alloc(s->mem, NSCAL * sizeof(double));
   if (!s->scal) return QNSCH_ENOMEM;
   s->blocks.push_back(s->scal);
-  if (cudaMallocHost(&s->hbuf, 64 * sizeof(double)) != cudaSuccess) {
+  if (cudaMallocHost(&s->hbuf, NSCAL * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     return QNSCH_ENOMEM;
   }
@@ -415,6 +450,55 @@ Prm<T> cast_prm(const Prm<double>& P) {
 }
 
 constexpr int MAX_PROF_EVENTS = 8192;
+// kinds of timed launches (qnsch_profile's bit mask)
+enum { PK_VANKA0 = 0, PK_VANKA = 1, PK_COARSE = 2, PK_CH = 3, PK_N = 4 };
+
+// cells of Vanka colour `colour` on an m1 x m2 level (the colourings of
+// colours_of: (2i + j) mod 8 when c8, else (i + 2j) mod kcol)
+long long colour_cells(int m1, int m2, int kcol, int c8, int colour) {
+  auto in_row = [m1](int K, int r) -> long long {  // i in [1, m1] with i % K == r
+    if (r == 0) return m1 / K;
+    return r <= m1 ? (m1 - r) / K + 1 : 0;
+  };
+  long long n = 0;
+  for (int j = 1; j <= m2; ++j) {
+    if (c8) {
+      int d = ((colour - j) % 8 + 8) % 8;
+      if (!(d & 1)) n += in_row(4, d / 2);
+    } else {
+      n += in_row(kcol, ((colour - 2 * j) % kcol + kcol) % kcol);
+    }
+  }
+  return n;
+}
+
+// open an event pair of `kind` around the launch queued next (-1: not timed)
+int prof_open(qnsch_s* s, int kind, double visits) {
+  if (!((s->prof >> kind) & 1) || s->ev_used + 2 > MAX_PROF_EVENTS) return -1;
+  while ((int)s->ev.size() < s->ev_used + 2) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      return -1;
+    }
+    s->ev.push_back(e);
+  }
+  const int pair = s->ev_used / 2;
+  if ((int)s->ev_kind.size() <= pair) {
+    s->ev_kind.resize(pair + 1);
+    s->ev_visits.resize(pair + 1);
+  }
+  s->ev_kind[pair] = kind;
+  s->ev_visits[pair] = visits;
+  cudaEventRecord(s->ev[s->ev_used], s->stream);
+  return s->ev_used;
+}
+
+void prof_close(qnsch_s* s, int q) {
+  if (q < 0) return;
+  cudaEventRecord(s->ev[q + 1], s->stream);
+  s->ev_used = q + 2;
+}
 
 template <typename T, class Form>
 void smooth(qnsch_s* s, const std::vector<Lv<T>>& Ls, const Prm<T>& P, int l) {
@@ -423,50 +507,38 @@ void smooth(qnsch_s* s, const std::vector<Lv<T>>& Ls, const Prm<T>& P, int l) {
   if constexpr (std::is_same<Form, ProjForm>::value) {
     // projection method (Sec. 7.2): CH red-black, the intermediate-velocity
     // blocks over the Vanka colours, pressure Gauss-Seidel red-black
-    qn::launch_ch<T, Form>(P, L, 0, s->stream, ch_max);
-    qn::launch_ch<T, Form>(P, L, 1, s->stream, ch_max);
+    const double ch_cells = 0.5 * (double)L.m1 * L.m2;
+    for (int c = 0; c < 2; ++c) {
+      int q = l == 0 ? prof_open(s, PK_CH, ch_cells) : -1;
+      qn::launch_ch<T, Form>(P, L, c, s->stream, ch_max);
+      prof_close(s, q);
+    }
     for (int c = 0; c < L.kcol; ++c) {
-      bool rec = s->prof && l == 0 && s->ev_used + 2 <= MAX_PROF_EVENTS;
-      if (rec) {
-        while ((int)s->ev.size() < s->ev_used + 2) {
-          cudaEvent_t e;
-          if (cudaEventCreate(&e) != cudaSuccess) { rec = false; break; }
-          s->ev.push_back(e);
-        }
-      }
-      if (rec) cudaEventRecord(s->ev[s->ev_used], s->stream);
+      int q = prof_open(s, l == 0 ? PK_VANKA0 : PK_VANKA,
+                        (double)colour_cells(L.m1, L.m2, L.kcol, L.c8, c));
       qn::launch_vanka4<T, Form>(P, L, c, (T)s->omega, s->stream, s->team_max);
-      if (rec) {
-        cudaEventRecord(s->ev[s->ev_used + 1], s->stream);
-        s->ev_used += 2;
-      }
+      prof_close(s, q);
     }
     qn::launch_pgs<T>(P, L, 0, s->stream, ch_max);
     qn::launch_pgs<T>(P, L, 1, s->stream, ch_max);
     return;
   }
   if (!s->coupled) {
-    qn::launch_ch<T, Form>(P, L, 0, s->stream, ch_max);
-    qn::launch_ch<T, Form>(P, L, 1, s->stream, ch_max);
+    const double ch_cells = 0.5 * (double)L.m1 * L.m2;
+    for (int c = 0; c < 2; ++c) {
+      int q = l == 0 ? prof_open(s, PK_CH, ch_cells) : -1;
+      qn::launch_ch<T, Form>(P, L, c, s->stream, ch_max);
+      prof_close(s, q);
+    }
   }
   for (int c = 0; c < L.kcol; ++c) {
-    bool rec = s->prof && l == 0 && s->ev_used + 2 <= MAX_PROF_EVENTS;
-    if (rec) {
-      while ((int)s->ev.size() < s->ev_used + 2) {
-        cudaEvent_t e;
-        if (cudaEventCreate(&e) != cudaSuccess) { rec = false; break; }
-        s->ev.push_back(e);
-      }
-    }
-    if (rec) cudaEventRecord(s->ev[s->ev_used], s->stream);
+    int q = prof_open(s, l == 0 ? PK_VANKA0 : PK_VANKA,
+                      (double)colour_cells(L.m1, L.m2, L.kcol, L.c8, c));
     if (s->coupled) qn::launch_coupled<T, Form>(P, L, c, (T)s->omega, s->stream,
                                                 std::is_same<Form, ErrForm>::value ? s->team_max32 : s->team_max);
     else qn::launch_vanka<T, Form>(P, L, c, (T)s->omega, s->stream,
                                    std::is_same<Form, ErrForm>::value ? s->team_max32 : s->team_max);
-    if (rec) {
-      cudaEventRecord(s->ev[s->ev_used + 1], s->stream);
-      s->ev_used += 2;
-    }
+    prof_close(s, q);
   }
 }
 
@@ -493,8 +565,16 @@ static int coarse_sweeps(const qnsch_s* s) {
 template <typename T, class Form>
 void vcycle(qnsch_s* s, const std::vector<Lv<T>>& Ls, const Prm<T>& P, int l) {
   if (l >= fused_from(s, Ls)) {
+    // visits of the Vanka (or coupled) block inside the fused V-cycle: every
+    // cell once per smoothing step
+    double visits = 0.0;
+    for (int m = l; m < s->nlev; ++m)
+      visits += (double)Ls[m].m1 * Ls[m].m2 *
+                (m == s->nlev - 1 ? coarse_sweeps(s) : s->nu1 + s->nu2);
+    int q = prof_open(s, PK_COARSE, visits);
     qn::launch_coarse_vcycle<T, Form>(P, &Ls[l], s->nlev - l, s->nu1, s->nu2, coarse_sweeps(s),
                                       s->kcol, (T)s->omega, s->coupled, s->stream);
+    prof_close(s, q);
     return;
   }
   if (l == s->nlev - 1) {
@@ -523,6 +603,10 @@ void prof_collect(qnsch_s* s) {
     if (cudaEventElapsedTime(&ms, s->ev[q], s->ev[q + 1]) == cudaSuccess) {
       s->prof_ms += ms;
       s->prof_launches += 1;
+      const int k = s->ev_kind[q / 2];
+      s->pk_ms[k] += ms;
+      s->pk_n[k] += 1;
+      s->pk_visits[k] += s->ev_visits[q / 2];
     }
   }
   cudaGetLastError();
@@ -539,13 +623,15 @@ void enter(qnsch_s* s) {
   }
 }
 
-// queue the finest FP64 residual, its norms and their copy to s->hbuf[0..9]
-void enqueue_norms(qnsch_s* s, const Prm<double>& P) {
+// queue the finest FP64 residual, its norms and (to_host) their copy to
+// s->hbuf[0..9]
+void enqueue_norms(qnsch_s* s, const Prm<double>& P, bool to_host = true) {
   const Lv<double>& F = s->L[0];
   if (s->scheme) qn::launch_residual<double, ProjForm>(P, F, s->part, s->stream);
   else qn::launch_residual<double, FullForm>(P, F, s->part, s->stream);
   qn::launch_norms_finalize(F, s->part, s->scal, s->stream);
-  cudaMemcpyAsync(s->hbuf, s->scal, 10 * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+  if (to_host)
+    cudaMemcpyAsync(s->hbuf, s->scal, 10 * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
 }
 
 void norms_from_host(const qnsch_s* s, double* norms10) {
@@ -645,15 +731,16 @@ int copy_fields_out(const qnsch_s* s, double* const src[5], double* const dst[5]
   return sync(s);
 }
 
-int begin(qnsch_s* s, double dt) {
-  // the error-equation levels first: a refused allocation leaves nothing queued
-  if (s->precision == 1) {
-    int rc = alloc_err_levels(s, s->Ef);
-    if (rc) return rc;
-  } else if (s->precision == 2) {
-    int rc = alloc_err_levels(s, s->Ed);
-    if (rc) return rc;
-  }
+// the error-equation levels of the precision in use (allocated once)
+int alloc_err(qnsch_s* s) {
+  if (s->precision == 1) return alloc_err_levels(s, s->Ef);
+  if (s->precision == 2) return alloc_err_levels(s, s->Ed);
+  return QNSCH_OK;
+}
+
+// the queued part of a step's start: the committed state into the iterate and
+// the frozen level-n data, then the frozen data of every level (A2)
+void queue_begin(qnsch_s* s, double dt) {
   s->dt = dt;
   s->res_valid = 0;
   Prm<double> P = make_prm(s);
@@ -679,6 +766,13 @@ int begin(qnsch_s* s, double dt) {
   } else if (s->precision == 2) {
     for (int l = 0; l < s->nlev; ++l) qn::launch_cast_frozen(s->L[l], s->Ed[l], s->stream);
   }
+}
+
+int begin(qnsch_s* s, double dt) {
+  // the error-equation levels first: a refused allocation leaves nothing queued
+  int rc = alloc_err(s);
+  if (rc) return rc;
+  queue_begin(s, dt);
   s->pending = 1;
   return cuda_status();
 }
@@ -701,7 +795,7 @@ void correction_cycle(qnsch_s* s, std::vector<Lv<T>>& E) {
 
 // all work of one outer cycle: V-cycle (or defect-correction cycle), gauge,
 // FP64 residual with norms and their copy to the host
-void cycle_body(qnsch_s* s, const Prm<double>& P) {
+void cycle_body(qnsch_s* s, const Prm<double>& P, bool to_host = true) {
   if (s->precision == 0) {
     if (s->scheme) vcycle<double, ProjForm>(s, s->L, P, 0);
     else vcycle<double, FullForm>(s, s->L, P, 0);
@@ -711,7 +805,7 @@ void cycle_body(qnsch_s* s, const Prm<double>& P) {
     else correction_cycle<double>(s, s->Ed);
   }
   qn::launch_gauge(s->L[0], s->part, s->scal + 16, s->stream);
-  enqueue_norms(s, P);
+  enqueue_norms(s, P, to_host);
 }
 
 void drop_graph(qnsch_s* s) {
@@ -727,7 +821,9 @@ int cycle_graph(qnsch_s* s, const Prm<double>& P) {
     drop_graph(s);
     s->ev_used = 0;
     if (s->prof) {  // create the timing events before capture begins
-      int pairs = s->L[0].kcol * (s->nlev == 1 ? coarse_sweeps(s) : s->nu1 + s->nu2);
+      int pairs = 1;
+      for (int l = 0; l < s->nlev; ++l)
+        pairs += (s->L[l].kcol + 2) * (l == s->nlev - 1 ? coarse_sweeps(s) : s->nu1 + s->nu2);
       while ((int)s->ev.size() < 2 * pairs && (int)s->ev.size() < MAX_PROF_EVENTS) {
         cudaEvent_t e;
         if (cudaEventCreate(&e) != cudaSuccess) {
@@ -797,9 +893,10 @@ int one_cycle(qnsch_s* s, double* norms10) {
   return finish_cycle(s, norms10);
 }
 
-// queue the dissipation of the step (Thm. 6.2) and the copy of the iterate into
-// the committed state; finish_commit waits and records
-void launch_commit(qnsch_s* s) {
+// queue the dissipation of the step (Thm. 6.2), the copy of the iterate into
+// the committed state and (to_host) the dissipation's copy to s->hbuf[25..26];
+// finish_commit waits and records
+void queue_commit(qnsch_s* s, bool to_host) {
   Prm<double> P = make_prm(s);
   const Lv<double>& F = s->L[0];
   double w_visc = s->dt / s->Re, w_div = s->dt / (3.0 * s->Re), w_ch = s->dt / (s->M * s->Pe);
@@ -824,9 +921,12 @@ void launch_commit(qnsch_s* s) {
     qn::launch_bc_unknowns(S, s->stream);
     qn::launch_proj_diss(P, F, s->su, s->sv, s->part, s->scal + 26, s->stream);
   }
-  cudaMemcpyAsync(s->hbuf + 25, s->scal + 25, 2 * sizeof(double), cudaMemcpyDeviceToHost,
-                  s->stream);
+  if (to_host)
+    cudaMemcpyAsync(s->hbuf + 25, s->scal + 25, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                    s->stream);
 }
+
+void launch_commit(qnsch_s* s) { queue_commit(s, true); }
 
 int finish_commit(qnsch_s* s) {
   int rc = sync(s);
@@ -839,6 +939,170 @@ int finish_commit(qnsch_s* s) {
 int commit(qnsch_s* s) {
   launch_commit(s);
   return finish_commit(s);
+}
+
+void drop_step_graph(qnsch_s* s) {
+  if (s->sexec) cudaGraphExecDestroy(s->sexec);
+  s->sexec = nullptr;
+}
+
+// end a capture that a failure left open on s->stream
+void abandon_capture(qnsch_s* s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s->stream, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+    cudaGraph_t g = nullptr;
+    cudaStreamEndCapture(s->stream, &g);
+    if (g) cudaGraphDestroy(g);
+  }
+  cudaGetLastError();
+}
+
+// Capture one whole step of size dt as a graph:
+//   prologue: start time, begin (A2), initial FP64 residual and norms, loop
+//             control (first = 1);
+//   WHILE (hl): one outer cycle (cycle_body) and the loop control;
+//   IF (hc): the commit (dissipation and the copy into the committed state);
+//   epilogue: the scalars and the control block to the host.
+// Returns QNSCH_ECUDA if the runtime refuses any part; nothing is then left
+// captured and the caller runs the step with the host-driven loop.
+int build_step_graph(qnsch_s* s, double dt) {
+  drop_step_graph(s);
+  int rc = alloc_err(s);
+  if (rc) return rc;
+  const auto mode = cudaStreamCaptureModeThreadLocal;
+  double* ctl = s->scal + CTL;
+  const double limit_ns = s->time_limit > 0.0 ? s->time_limit * 1e9 : 0.0;
+  cudaGraph_t G = nullptr;
+  cudaGraphConditionalHandle hl = 0, hc = 0;
+  bool ok = cudaGraphCreate(&G, 0) == cudaSuccess &&
+            cudaGraphConditionalHandleCreate(&hl, G, 0, cudaGraphCondAssignDefault) == cudaSuccess &&
+            cudaGraphConditionalHandleCreate(&hc, G, 0, cudaGraphCondAssignDefault) == cudaSuccess;
+  const long long c0 = qn::launches_issued();
+  long long c1 = c0, c2 = c0, c3 = c0;
+  std::vector<cudaGraphNode_t> deps;
+  cudaGraphNode_t wn = nullptr, in = nullptr;
+  // prologue
+  if (ok) ok = cudaStreamBeginCaptureToGraph(s->stream, G, nullptr, nullptr, 0, mode) == cudaSuccess;
+  if (ok) {
+    qn::launch_loop_clock(ctl, s->stream);
+    queue_begin(s, dt);
+    Prm<double> P = make_prm(s);
+    enqueue_norms(s, P, false);
+    qn::launch_loop_ctl(s->scal, ctl, hl, hc, s->tol, s->maxcyc, s->diverge, limit_ns, 1, s->stream);
+    cudaStreamCaptureStatus cs;
+    const cudaGraphNode_t* d = nullptr;
+    size_t nd = 0;
+    ok = cudaStreamGetCaptureInfo(s->stream, &cs, nullptr, nullptr, &d, nullptr, &nd) == cudaSuccess &&
+         cs == cudaStreamCaptureStatusActive;
+    if (ok) deps.assign(d, d + nd);
+    cudaGraph_t g = G;
+    ok = cudaStreamEndCapture(s->stream, &g) == cudaSuccess && ok;
+    c1 = qn::launches_issued();
+  }
+  // WHILE: the outer cycle
+  if (ok) {
+    cudaGraphNodeParams wp = {};
+    wp.type = cudaGraphNodeTypeConditional;
+    wp.conditional.handle = hl;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    ok = cudaGraphAddNode(&wn, G, deps.data(), nullptr, deps.size(), &wp) == cudaSuccess;
+    cudaGraph_t body = ok ? wp.conditional.phGraph_out[0] : nullptr;
+    if (ok) ok = cudaStreamBeginCaptureToGraph(s->stream, body, nullptr, nullptr, 0, mode) == cudaSuccess;
+    if (ok) {
+      Prm<double> P = make_prm(s);
+      cycle_body(s, P, false);
+      qn::launch_loop_ctl(s->scal, ctl, hl, hc, s->tol, s->maxcyc, s->diverge, limit_ns, 0,
+                          s->stream);
+      ok = cudaStreamEndCapture(s->stream, &body) == cudaSuccess;
+      c2 = qn::launches_issued();
+    }
+  }
+  // IF: the commit
+  if (ok) {
+    cudaGraphNodeParams ip = {};
+    ip.type = cudaGraphNodeTypeConditional;
+    ip.conditional.handle = hc;
+    ip.conditional.type = cudaGraphCondTypeIf;
+    ip.conditional.size = 1;
+    ok = cudaGraphAddNode(&in, G, &wn, nullptr, 1, &ip) == cudaSuccess;
+    cudaGraph_t body = ok ? ip.conditional.phGraph_out[0] : nullptr;
+    if (ok) ok = cudaStreamBeginCaptureToGraph(s->stream, body, nullptr, nullptr, 0, mode) == cudaSuccess;
+    if (ok) {
+      queue_commit(s, false);
+      ok = cudaStreamEndCapture(s->stream, &body) == cudaSuccess;
+      c3 = qn::launches_issued();
+    }
+  }
+  // epilogue: scalars (dissipation) and the control block to the host
+  if (ok) ok = cudaStreamBeginCaptureToGraph(s->stream, G, &in, nullptr, 1, mode) == cudaSuccess;
+  if (ok) {
+    cudaMemcpyAsync(s->hbuf, s->scal, (CTL + CTL_LEN) * sizeof(double), cudaMemcpyDeviceToHost,
+                    s->stream);
+    cudaGraph_t g = G;
+    ok = cudaStreamEndCapture(s->stream, &g) == cudaSuccess;
+  }
+  if (ok) ok = cudaGraphInstantiate(&s->sexec, G, 0) == cudaSuccess;
+  const long long issued = qn::launches_issued() - c0;
+  g_captured += issued;  // none of these ran: the graph's replays count them
+  if (G) cudaGraphDestroy(G);
+  if (!ok) {
+    abandon_capture(s);
+    s->sexec = nullptr;
+    return QNSCH_ECUDA;
+  }
+  s->s_pro = c1 - c0;
+  s->s_body = c2 - c1;
+  s->s_commit = c3 - c2;
+  s->s_dt = dt;
+  s->s_precision = s->precision;
+  s->s_opt = s->opt_version;
+  return QNSCH_OK;
+}
+
+// the step runs as one graph when the handle allows it: graphs on, no
+// profiling (event records cannot sit inside conditional bodies)
+bool device_loop_on(const qnsch_s* s) { return s->device_loop && s->use_graphs && !s->prof; }
+
+// queue one whole step as a graph replay; QNSCH_ECUDA if the graph cannot be
+// built (the handle then falls back to the host-driven loop for good)
+int launch_device_step(qnsch_s* s, double dt) {
+  const bool fresh = s->sexec && s->s_dt == dt && s->s_precision == s->precision &&
+                     s->s_opt == s->opt_version;
+  if (!fresh) {
+    int rc = build_step_graph(s, dt);
+    if (rc == QNSCH_ECUDA) s->device_loop = 0;
+    if (rc) return rc;
+  }
+  s->dt = dt;
+  s->pending = 1;
+  if (cudaGraphLaunch(s->sexec, s->stream) != cudaSuccess) {
+    cudaGetLastError();
+    s->pending = 0;
+    return QNSCH_ECUDA;
+  }
+  return QNSCH_OK;
+}
+
+// wait for a step queued by launch_device_step and read its outcome; the
+// status rules are those of the host-driven loop
+int finish_device_step(qnsch_s* s, int* n_vcycles, double* final_residual) {
+  int rc = sync(s);
+  s->pending = 0;
+  if (rc) return rc;
+  const double* c = s->hbuf + CTL;
+  const int k = (int)c[1];
+  const double r = c[0];
+  const bool late = c[3] != 0.0, committed = c[5] != 0.0;
+  g_replayed += s->s_pro + (long long)k * s->s_body + (committed ? s->s_commit : 0);
+  s->res_valid = 1;
+  if (n_vcycles) *n_vcycles = k;
+  if (final_residual) *final_residual = r;
+  if (!(r == r)) return QNSCH_ENAN;
+  if (late) return QNSCH_ETIMEOUT;
+  if (!committed) return QNSCH_ENOTCONV;
+  s->last_diss = s->hbuf[25] + (s->scheme ? s->hbuf[26] : 0.0);
+  return QNSCH_OK;
 }
 
 }  // namespace
@@ -950,7 +1214,7 @@ int qnsch_footprint(const qnsch_grid* grid, int precision, size_t* bytes) {
   total += n0 * 5 * sizeof(double);                                           // committed state
   total += (size_t)qn::partial_rows_needed(grid->m1, grid->m2) * 10 * sizeof(double);
   total += (size_t)(grid->m1 + 1) * (grid->m2 + 1) * sizeof(double);         // staging
-  total += 64 * sizeof(double);
+  total += NSCAL * sizeof(double);
   *bytes = total;
   return QNSCH_OK;
 }
@@ -1016,6 +1280,8 @@ int set_option(qnsch_s* s, const std::string& k, double value) {
     (k == "M" ? s->M : k == "eta_st" ? s->eta : s->eps_m) = value;
   } else if (k == "graphs") {
     s->use_graphs = value != 0.0;
+  } else if (k == "device_loop") {
+    s->device_loop = value != 0.0;
   } else if (k == "step_time_limit") {
     if (!(value >= 0.0) || !std::isfinite(value)) return QNSCH_EINVAL;
     s->time_limit = value;
@@ -1073,6 +1339,7 @@ int qnsch_get_option(const qnsch_t* s, const char* key, double* value) {
   else if (k == "eps_mob") *value = s->eps_m;
   else if (k == "precision") *value = s->precision;
   else if (k == "graphs") *value = s->use_graphs;
+  else if (k == "device_loop") *value = s->device_loop;
   else if (k == "step_time_limit") *value = s->time_limit;
   else if (k == "diverge_cycles") *value = s->diverge;
   else if (k == "fuse_cells") *value = s->fuse64;
@@ -1102,9 +1369,29 @@ int qnsch_profile(qnsch_t* s, int enable) {
     cudaStreamSynchronize(s->stream);
     prof_collect(s);
   }
-  s->prof = enable ? 1 : 0;
+  if (enable < 0 || enable > 15) return QNSCH_EINVAL;
+  s->prof = enable;
   s->prof_launches = 0;
   s->prof_ms = 0.0;
+  for (int k = 0; k < PK_N; ++k) {
+    s->pk_n[k] = 0;
+    s->pk_ms[k] = 0.0;
+    s->pk_visits[k] = 0.0;
+  }
+  return QNSCH_OK;
+}
+
+int qnsch_profile_read_kind(qnsch_t* s, int kind, long long* launches, double* total_ms,
+                            double* visits) {
+  if (!s || kind < 0 || kind >= PK_N || !launches || !total_ms || !visits) return QNSCH_EINVAL;
+  if (s->ev_used) {
+    int rc = sync(s);
+    if (rc) return rc;
+    prof_collect(s);
+  }
+  *launches = s->pk_n[kind];
+  *total_ms = s->pk_ms[kind];
+  *visits = s->pk_visits[kind];
   return QNSCH_OK;
 }
 
@@ -1166,6 +1453,7 @@ int qnsch_get_fields_device(const qnsch_t* s, double* c, double* mu, double* u, 
 
 int qnsch_begin_step(qnsch_t* s, double dt) {
   if (!s || !(dt > 0) || !std::isfinite(dt)) return QNSCH_EINVAL;
+  if (s->async) return QNSCH_ESTATE;
   int rc = begin(s, dt);
   if (rc) return rc;
   return sync(s);
@@ -1173,7 +1461,7 @@ int qnsch_begin_step(qnsch_t* s, double dt) {
 
 int qnsch_vcycle(qnsch_t* s, double* norms10) {
   if (!s) return QNSCH_EINVAL;
-  if (!s->pending) return QNSCH_ESTATE;
+  if (!s->pending || s->async) return QNSCH_ESTATE;
   double n[10];
   int rc = one_cycle(s, n);
   if (rc) return rc;
@@ -1183,13 +1471,19 @@ int qnsch_vcycle(qnsch_t* s, double* norms10) {
 
 int qnsch_commit_step(qnsch_t* s) {
   if (!s) return QNSCH_EINVAL;
-  if (!s->pending) return QNSCH_ESTATE;
+  if (!s->pending || s->async) return QNSCH_ESTATE;
   return commit(s);
 }
 
 int qnsch_step(qnsch_t* s, double dt, int* n_vcycles, double* final_residual) {
   if (!s || !(dt > 0) || !std::isfinite(dt)) return QNSCH_EINVAL;
-  if (s->pending) return QNSCH_ESTATE;
+  if (s->pending || s->async) return QNSCH_ESTATE;
+  if (device_loop_on(s)) {
+    int rc = launch_device_step(s, dt);
+    if (rc == QNSCH_OK) return finish_device_step(s, n_vcycles, final_residual);
+    if (rc != QNSCH_ECUDA || device_loop_on(s)) return rc;
+    // the runtime refused the step graph: the host-driven loop below
+  }
   const auto t0 = std::chrono::steady_clock::now();
   int rc = begin(s, dt);
   if (rc) return rc;
@@ -1227,6 +1521,54 @@ int qnsch_step(qnsch_t* s, double dt, int* n_vcycles, double* final_residual) {
     return QNSCH_ENOTCONV;
   }
   return commit(s);
+}
+
+int qnsch_step_launch(qnsch_t* s, double dt) {
+  if (!s || !(dt > 0) || !std::isfinite(dt)) return QNSCH_EINVAL;
+  if (s->pending || s->async) return QNSCH_ESTATE;
+  if (device_loop_on(s)) {
+    cudaEventRecord(s->ev_s0, s->stream);
+    int rc = launch_device_step(s, dt);
+    if (rc == QNSCH_OK) {
+      cudaEventRecord(s->ev_s1, s->stream);
+      s->async = 1;
+      return QNSCH_OK;
+    }
+    if (rc != QNSCH_ECUDA || device_loop_on(s)) return rc;
+  }
+  // no device-side loop: the step runs here and the poll reports its outcome
+  cudaEventRecord(s->ev_s0, s->stream);
+  s->a_status = qnsch_step(s, dt, &s->a_cycles, &s->a_res);
+  cudaEventRecord(s->ev_s1, s->stream);
+  s->async = 2;
+  return QNSCH_OK;
+}
+
+int qnsch_step_poll(qnsch_t* s, int* done, int* n_vcycles, double* final_residual, int* status,
+                    double* device_ms) {
+  if (!s || !done) return QNSCH_EINVAL;
+  if (!s->async) return QNSCH_ESTATE;
+  cudaError_t e = cudaEventQuery(s->ev_s1);
+  if (e == cudaErrorNotReady) {
+    *done = 0;
+    return QNSCH_OK;
+  }
+  if (e != cudaSuccess) cudaGetLastError();
+  int st = s->a_status, k = s->a_cycles;
+  double r = s->a_res;
+  if (s->async == 1) st = finish_device_step(s, &k, &r);
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, s->ev_s0, s->ev_s1) != cudaSuccess) {
+    cudaGetLastError();
+    ms = -1.f;
+  }
+  s->async = 0;
+  *done = 1;
+  if (n_vcycles) *n_vcycles = k;
+  if (final_residual) *final_residual = r;
+  if (status) *status = st;
+  if (device_ms) *device_ms = ms;
+  return QNSCH_OK;
 }
 
 int qnsch_mass(const qnsch_t* s, double* mass_rho, double* mass_rhoc) {
@@ -1306,7 +1648,7 @@ int qnsch_energy(const qnsch_t* s, double* E, double* last_dissipation) {
 
 int qnsch_iterate_energy(const qnsch_t* s, double* E, double* D) {
   if (!s || !E) return QNSCH_EINVAL;
-  if (!s->pending) return QNSCH_ESTATE;
+  if (!s->pending || s->async) return QNSCH_ESTATE;
   const Lv<double>& F = s->L[0];
   int rc = energy_of(s, F.c, F.u, F.v, E);
   if (rc) return rc;
@@ -1328,7 +1670,7 @@ int qnsch_set_iterate(qnsch_t* s, const double* c, const double* mu, const doubl
                       const double* v, const double* p) {
   if (s) s->res_valid = 0;
   if (!s || !c || !mu || !u || !v || !p) return QNSCH_EINVAL;
-  if (!s->pending) return QNSCH_ESTATE;
+  if (!s->pending || s->async) return QNSCH_ESTATE;
   const Lv<double>& F = s->L[0];
   double* dst[5] = {F.c, F.mu, F.u, F.v, F.p};
   const double* src[5] = {c, mu, u, v, p};
@@ -1337,7 +1679,7 @@ int qnsch_set_iterate(qnsch_t* s, const double* c, const double* mu, const doubl
 
 int qnsch_get_iterate(const qnsch_t* s, double* c, double* mu, double* u, double* v, double* p) {
   if (!s) return QNSCH_EINVAL;
-  if (!s->pending) return QNSCH_ESTATE;
+  if (!s->pending || s->async) return QNSCH_ESTATE;
   const Lv<double>& F = s->L[0];
   double* src[5] = {F.c, F.mu, F.u, F.v, F.p};
   double* dst[5] = {c, mu, u, v, p};
@@ -1347,7 +1689,7 @@ int qnsch_get_iterate(const qnsch_t* s, double* c, double* mu, double* u, double
 int qnsch_residual(qnsch_t* s, double* rc_, double* rmu, double* rp, double* ru, double* rv,
                    double* norms10) {
   if (!s) return QNSCH_EINVAL;
-  if (!s->pending) return QNSCH_ESTATE;
+  if (!s->pending || s->async) return QNSCH_ESTATE;
   Prm<double> P = make_prm(s);
   double n[10];
   int rc = residual_norms(s, P, n);
@@ -1362,7 +1704,7 @@ int qnsch_residual(qnsch_t* s, double* rc_, double* rmu, double* rp, double* ru,
 int qnsch_smooth_ch(qnsch_t* s, int colour) {
   if (s) s->res_valid = 0;
   if (!s || colour < 0 || colour > 1) return QNSCH_EINVAL;
-  if (!s->pending) return QNSCH_ESTATE;
+  if (!s->pending || s->async) return QNSCH_ESTATE;
   if (s->scheme) qn::launch_ch<double, ProjForm>(make_prm(s), s->L[0], colour, s->stream);
   else qn::launch_ch<double, FullForm>(make_prm(s), s->L[0], colour, s->stream, s->ch_team_max);
   return sync(s);
@@ -1371,7 +1713,7 @@ int qnsch_smooth_ch(qnsch_t* s, int colour) {
 int qnsch_smooth_vanka(qnsch_t* s, int colour) {
   if (s) s->res_valid = 0;
   if (!s || colour < 0 || colour >= s->kcol) return QNSCH_EINVAL;
-  if (!s->pending) return QNSCH_ESTATE;
+  if (!s->pending || s->async) return QNSCH_ESTATE;
   if (s->scheme)
     qn::launch_vanka4<double, ProjForm>(make_prm(s), s->L[0], colour, s->omega, s->stream, s->team_max);
   else qn::launch_vanka<double, FullForm>(make_prm(s), s->L[0], colour, s->omega, s->stream,
@@ -1417,6 +1759,30 @@ int qnsch_batch_step(qnsch_batch_t* B, const double* dt, int* status, int* n_vcy
     // qnsch_batch_create) would serialise their cycles and share their events
     for (int b = 0; b < a; ++b)
       if (B->inst[a]->stream == B->inst[b]->stream) return QNSCH_EINVAL;
+  }
+  // every member runs its step as one graph on its own stream: queue them
+  // all, then collect
+  bool all_device = true;
+  for (int a = 0; a < n; ++a) all_device = all_device && device_loop_on(B->inst[a]);
+  if (all_device) {
+    std::vector<char> queued(n, 0);
+    for (int a = 0; a < n; ++a) {
+      status[a] = launch_device_step(B->inst[a], dt[a]);
+      queued[a] = status[a] == QNSCH_OK;
+      if (n_vcycles) n_vcycles[a] = 0;
+    }
+    for (int a = 0; a < n; ++a) {
+      if (queued[a]) {
+        status[a] = finish_device_step(B->inst[a], n_vcycles ? &n_vcycles[a] : nullptr, nullptr);
+      } else if (status[a] == QNSCH_ECUDA && !device_loop_on(B->inst[a])) {
+        // that member's runtime refused the step graph: its host-driven step
+        int k = 0;
+        double r = 0.0;
+        status[a] = qnsch_step(B->inst[a], dt[a], &k, &r);
+        if (n_vcycles) n_vcycles[a] = k;
+      }
+    }
+    return QNSCH_OK;
   }
   std::vector<int> live(n, 1), cyc(n, 0), grew(n, 0);
   std::vector<char> wait(n, 0), late(n, 0);
@@ -1501,7 +1867,7 @@ int qnsch_batch_step(qnsch_batch_t* B, const double* dt, int* status, int* n_vcy
 int qnsch_smooth(qnsch_t* s, int sweeps) {
   if (s) s->res_valid = 0;
   if (!s || sweeps < 0) return QNSCH_EINVAL;
-  if (!s->pending) return QNSCH_ESTATE;
+  if (!s->pending || s->async) return QNSCH_ESTATE;
   Prm<double> P = make_prm(s);
   for (int k = 0; k < sweeps; ++k) {
     if (s->scheme) smooth<double, ProjForm>(s, s->L, P, 0);

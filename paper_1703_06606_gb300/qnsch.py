@@ -59,6 +59,9 @@ def lib():
                      "set_iterate", "get_iterate"):
             getattr(L, "qnsch_" + name).argtypes = [_VP, _VP, _VP, _VP, _VP, _VP]
         L.qnsch_step.argtypes = [_VP, d, ctypes.POINTER(i), p]
+        L.qnsch_step_launch.argtypes = [_VP, d]
+        L.qnsch_step_poll.argtypes = [_VP, ctypes.POINTER(i), ctypes.POINTER(i), p,
+                                      ctypes.POINTER(i), p]
         L.qnsch_begin_step.argtypes = [_VP, d]
         L.qnsch_vcycle.argtypes = [_VP, p]
         L.qnsch_commit_step.argtypes = [_VP]
@@ -74,6 +77,7 @@ def lib():
         L.qnsch_set_allocator.argtypes = [_VP, _VP, _VP]
         L.qnsch_profile.argtypes = [_VP, i]
         L.qnsch_profile_read.argtypes = [_VP, ctypes.POINTER(ctypes.c_longlong), p]
+        L.qnsch_profile_read_kind.argtypes = [_VP, i, ctypes.POINTER(ctypes.c_longlong), p, p]
         L.qnsch_kernel_launches.argtypes = [ctypes.POINTER(ctypes.c_longlong)]
         L.qnsch_set_budget.argtypes = [ctypes.c_size_t]
         L.qnsch_version.argtypes = [ctypes.POINTER(i)] * 3
@@ -283,6 +287,23 @@ class Solver:
                "qnsch_step")
         return n.value, r.value
 
+    def step_launch(self, dt):
+        """qnsch_step_launch: queue one whole step and return at once."""
+        _check(lib().qnsch_step_launch(self._h, float(dt)), "qnsch_step_launch")
+
+    def step_poll(self):
+        """qnsch_step_poll: None while the launched step runs, else
+        (n_vcycles, final_residual, status, device_ms); status is the code
+        qnsch_step would have returned (0 on success)."""
+        done, n, st = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        r, ms = ctypes.c_double(), ctypes.c_double()
+        _check(lib().qnsch_step_poll(self._h, ctypes.byref(done), ctypes.byref(n),
+                                     ctypes.byref(r), ctypes.byref(st), ctypes.byref(ms)),
+               "qnsch_step_poll")
+        if not done.value:
+            return None
+        return n.value, r.value, st.value, ms.value
+
     def begin_step(self, dt):
         _check(lib().qnsch_begin_step(self._h, float(dt)), "qnsch_begin_step")
 
@@ -312,8 +333,22 @@ class Solver:
         _check(lib().qnsch_smooth(self._h, int(sweeps)), "qnsch_smooth")
 
     # ---- measurement ----
+    # kinds of timed launches (qnsch_profile's bits)
+    PROFILE_KINDS = ("vanka_finest", "vanka_levels", "coarse_vcycle", "ch")
+
     def profile(self, enable=True):
-        _check(lib().qnsch_profile(self._h, int(bool(enable))), "qnsch_profile")
+        """enable: True (the finest-level Vanka launches), False, or a bit mask
+        over PROFILE_KINDS."""
+        mask = int(enable) if not isinstance(enable, bool) else int(enable)
+        _check(lib().qnsch_profile(self._h, mask), "qnsch_profile")
+
+    def profile_read_kind(self, kind):
+        """(launches, total ms, cell visits) of one kind of timed launch."""
+        k = self.PROFILE_KINDS.index(kind) if isinstance(kind, str) else int(kind)
+        n, ms, vis = ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double()
+        _check(lib().qnsch_profile_read_kind(self._h, k, ctypes.byref(n), ctypes.byref(ms),
+                                             ctypes.byref(vis)), "qnsch_profile_read_kind")
+        return n.value, ms.value, vis.value
 
     def profile_read(self):
         n, ms = ctypes.c_longlong(), ctypes.c_double()

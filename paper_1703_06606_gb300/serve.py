@@ -1,22 +1,30 @@
 """Continuous-batching server for independent q-NSCH simulations.
 
-Requests (a workload and a number of time steps) arrive over time.  The server
-keeps every admitted simulation's fields and multigrid hierarchy resident on
-the GPU, admits waiting requests in arrival order as soon as a slot is free and
-their device footprint (qnsch_footprint) fits the memory budget, and advances
-all resident simulations together, one time step per round, through
-qnsch_batch_step (their kernels overlap on the device).  A simulation leaves
-when it has done its steps (or failed).  Each simulation goes through exactly
-the arithmetic it would alone, so its result does not depend on the mix.
+Requests (a workload and a number of time steps) arrive over time.  An
+admission thread takes them in arrival order, and as soon as a slot is free and
+a request's device footprint (qnsch_footprint) fits the memory budget it
+creates the simulation (fields and multigrid hierarchy resident on the GPU,
+off the stepping loop's critical path).  The stepping loop advances every
+resident simulation independently: each one's next time step is queued
+(qnsch_step_launch, one graph on its own stream) the moment its previous step
+is seen finished (qnsch_step_poll), so the simulations' kernels overlap on the
+device and a small simulation never waits for a large one.  A simulation
+leaves when it has done its steps (or failed), which frees its memory for the
+next request.  Each simulation goes through exactly the arithmetic it would
+alone, so its result does not depend on the mix.  Per step the server records
+the wall time from launch to completion seen by the loop and the step's device
+time (CUDA events around it on the simulation's stream).
 
     python -m paper_1703_06606_gb300.serve --requests 40 --rate 50 --steps 20
 """
 from __future__ import annotations
 
 import argparse
+import collections
 import dataclasses
 import json
 import math
+import threading
 import time
 
 import numpy as np
@@ -35,6 +43,7 @@ class Request:
     done_steps: int = 0
     status: int = 0
     step_ms: list = dataclasses.field(default_factory=list)
+    device_ms: list = dataclasses.field(default_factory=list)
     vcycles: list = dataclasses.field(default_factory=list)
 
 
@@ -93,78 +102,153 @@ class Server:
     def footprint(self, P):
         return self.qn.footprint(P.m1, P.m2, P.periodic_x, P.levels, self.precision, P.Lx)
 
-    def run(self, requests, keep_fields=False):
+    def run(self, requests, keep_fields=False, device=None, poll_sleep_s=20e-6):
         """Serve `requests` (arrival times relative to now) to completion; returns
-        the requests (with timings) and, if keep_fields, their final fields."""
-        waiting = sorted(requests, key=lambda r: r.arrival)
-        resident = []  # (request, solver, footprint)
-        used = 0
+        the requests (with timings) and, if keep_fields, their final fields.
+        device: the CUDA device index the admission thread makes current before
+        it creates simulations (None: the thread's default)."""
+        waiting = collections.deque(sorted(requests, key=lambda r: r.arrival))
+        ready = collections.deque()  # admitted (request, solver, footprint)
+        cond = threading.Condition()
+        state = {"used": 0, "slots": 0, "admitting": True, "error": None, "max_wait": 0}
         t0 = time.perf_counter()
+        clock = lambda: time.perf_counter() - t0  # noqa: E731
+
+        def admit():
+            try:
+                if device is not None:
+                    import torch
+                    torch.cuda.set_device(device)
+                while waiting:
+                    r = waiting[0]
+                    delay = r.arrival - clock()
+                    if delay > 0:
+                        time.sleep(delay)
+                    fp = self.footprint(r.problem)
+                    if fp > self.budget:
+                        raise ValueError("request %d needs %d bytes, more than the budget"
+                                         % (r.rid, fp))
+                    with cond:
+                        # first in line waits for memory and a slot
+                        while (state["used"] + fp > self.budget or
+                               state["slots"] >= self.max_slots):
+                            cond.wait()
+                        state["used"] += fp
+                        state["slots"] += 1
+                    waiting.popleft()
+                    P = r.problem
+                    sv = self.qn.Solver(**P.create_kwargs(), tol=P.tol, precision=self.precision,
+                                        coupled=self.coupled, **self.options(P))
+                    sv.set_fields(P.fields())
+                    r.admitted = clock()
+                    with cond:
+                        ready.append((r, sv, fp))
+                        backlog = sum(1 for w in waiting if w.arrival <= clock())
+                        state["max_wait"] = max(state["max_wait"], backlog)
+            except BaseException as e:  # noqa: BLE001 - reported by the stepping loop
+                state["error"] = e
+            finally:
+                with cond:
+                    state["admitting"] = False
+
+        th = threading.Thread(target=admit, daemon=True)
+        th.start()
+        inflight = []  # [request, solver, footprint, launch time]
         fields = {}
         max_res = 0
-        while waiting or resident:
-            now = time.perf_counter() - t0
-            while (waiting and waiting[0].arrival <= now and len(resident) < self.max_slots):
-                r = waiting[0]
-                fp = self.footprint(r.problem)
-                if fp > self.budget:
-                    raise ValueError("request %d needs %d bytes, more than the budget"
-                                     % (r.rid, fp))
-                if used + fp > self.budget:
-                    break  # first in line waits for memory
-                waiting.pop(0)
-                P = r.problem
-                s = self.qn.Solver(**P.create_kwargs(), tol=P.tol, precision=self.precision,
-                                   coupled=self.coupled, **self.options(P))
-                s.set_fields(P.fields())
-                r.admitted = time.perf_counter() - t0
-                resident.append((r, s, fp))
-                used += fp
-            max_res = max(max_res, len(resident))
-            if not resident:
-                time.sleep(max(0.0, waiting[0].arrival - (time.perf_counter() - t0)))
-                continue
-            B = self.qn.Batch([s for _, s, _ in resident])
-            ts = time.perf_counter()
-            st, cyc = B.step([r.problem.dt for r, _, _ in resident])
-            dur = (time.perf_counter() - ts) * 1e3
-            B.close()
-            keep = []
-            for (r, s, fp), code, nc in zip(resident, st, cyc):
-                r.step_ms.append(dur)
-                r.vcycles.append(nc)
-                r.done_steps += 1
-                if code != 0:
-                    r.status = code
-                if code != 0 or r.done_steps >= r.steps:
-                    r.finished = time.perf_counter() - t0
-                    if keep_fields:
-                        fields[r.rid] = s.get_fields()
-                    s.close()
-                    used -= fp
-                else:
-                    keep.append((r, s, fp))
-            resident = keep
+        try:
+            while True:
+                with cond:
+                    new = list(ready)
+                    ready.clear()
+                    admitting = state["admitting"]
+                for r, sv, fp in new:
+                    sv.step_launch(r.problem.dt)
+                    inflight.append([r, sv, fp, clock()])
+                max_res = max(max_res, len(inflight))
+                if not inflight:
+                    if state["error"] is not None:
+                        raise state["error"]
+                    if not admitting:
+                        with cond:
+                            if not ready:
+                                break
+                        continue
+                    time.sleep(poll_sleep_s)
+                    continue
+                progressed = False
+                keep = []
+                for item in inflight:
+                    r, sv, fp, tl = item
+                    out = sv.step_poll()
+                    if out is None:
+                        keep.append(item)
+                        continue
+                    progressed = True
+                    now = clock()
+                    nc, _, code, dms = out
+                    r.step_ms.append(1e3 * (now - tl))
+                    r.device_ms.append(dms)
+                    r.vcycles.append(nc)
+                    r.done_steps += 1
+                    if code != 0:
+                        r.status = code
+                    if code != 0 or r.done_steps >= r.steps:
+                        r.finished = now
+                        if keep_fields:
+                            fields[r.rid] = sv.get_fields()
+                        sv.close()
+                        with cond:
+                            state["used"] -= fp
+                            state["slots"] -= 1
+                            cond.notify_all()
+                    else:
+                        sv.step_launch(r.problem.dt)
+                        item[3] = clock()
+                        keep.append(item)
+                inflight = keep
+                if not progressed:
+                    time.sleep(poll_sleep_s)
+        finally:
+            th.join(timeout=60)
+        if state["error"] is not None:
+            raise state["error"]
         self.max_resident = max_res
-        self.wall = time.perf_counter() - t0
+        self.max_backlog = state["max_wait"]
+        self.wall = clock()
         return requests, fields
 
 
-def summarize(reqs, wall, max_resident):
+def summarize(reqs, wall, max_resident, max_backlog=None):
+    """Throughput and latency of a served stream.  offered_cell_steps_per_s is
+    the work the arrivals asked for per second of the arrival span; when the
+    server delivers well below it the queue grows for the whole run
+    (saturated)."""
     steps = [ms for r in reqs for ms in r.step_ms]
+    dev = [ms for r in reqs for ms in r.device_ms if ms >= 0]
     lat = [1e3 * (r.finished - r.arrival) for r in reqs]
     wait = [1e3 * (r.admitted - r.arrival) for r in reqs]
     cell_steps = sum(r.problem.cells * r.done_steps for r in reqs)
-    return {"value": cell_steps / wall, "unit": "cell-updates/s", "requests": len(reqs),
-            "failed": sum(1 for r in reqs if r.status != 0), "wall_s": wall,
-            "cell_steps": cell_steps, "max_resident": max_resident,
-            "step_latency_ms": {"p50": float(np.percentile(steps, 50)),
-                                "p99": float(np.percentile(steps, 99))},
-            "request_latency_ms": {"p50": float(np.percentile(lat, 50)),
-                                   "p99": float(np.percentile(lat, 99))},
-            "queue_wait_ms": {"p50": float(np.percentile(wait, 50)),
-                              "p99": float(np.percentile(wait, 99))},
-            "mean_vcycles_per_step": float(np.mean([c for r in reqs for c in r.vcycles]))}
+    span = max(r.arrival for r in reqs) - min(r.arrival for r in reqs)
+    offered = sum(r.problem.cells * r.steps for r in reqs) / span if span > 0 else math.inf
+    value = cell_steps / wall
+    out = {"value": value, "unit": "cell-updates/s", "requests": len(reqs),
+           "failed": sum(1 for r in reqs if r.status != 0), "wall_s": wall,
+           "cell_steps": cell_steps, "max_resident": max_resident,
+           "offered_cell_steps_per_s": offered, "saturated": bool(value < 0.9 * offered),
+           "step_latency_ms": {"p50": float(np.percentile(steps, 50)),
+                               "p99": float(np.percentile(steps, 99))},
+           "request_latency_ms": {"p50": float(np.percentile(lat, 50)),
+                                  "p99": float(np.percentile(lat, 99))},
+           "queue_wait_ms": {"p50": float(np.percentile(wait, 50)),
+                             "p99": float(np.percentile(wait, 99))},
+           "mean_vcycles_per_step": float(np.mean([c for r in reqs for c in r.vcycles]))}
+    if dev:
+        out["step_device_ms"] = {"p50": float(np.percentile(dev, 50)),
+                                 "p99": float(np.percentile(dev, 99))}
+    if max_backlog is not None:
+        out["max_backlog"] = max_backlog
+    return out
 
 
 def request_record(r):
@@ -176,7 +260,8 @@ def request_record(r):
             "arrival_s": r.arrival, "admitted_s": r.admitted, "finished_s": r.finished,
             "queue_wait_ms": 1e3 * (r.admitted - r.arrival),
             "latency_ms": 1e3 * (r.finished - r.arrival),
-            "step_ms": list(r.step_ms), "vcycles": list(r.vcycles)}
+            "step_ms": list(r.step_ms), "device_ms": list(r.device_ms),
+            "vcycles": list(r.vcycles)}
 
 
 def main():
@@ -196,7 +281,7 @@ def main():
         with open(a.log, "w") as f:
             for r in reqs:
                 f.write(json.dumps(request_record(r)) + "\n")
-    print(json.dumps(summarize(reqs, srv.wall, srv.max_resident)))
+    print(json.dumps(summarize(reqs, srv.wall, srv.max_resident, srv.max_backlog)))
 
 
 if __name__ == "__main__":

@@ -1,8 +1,12 @@
 """The serving loop's host logic on CPU, with a stand-in backend in place of
 the qnsch binding: admission in arrival order under the memory budget and the
-slot limit, continuous batching (requests join while others are resident and
-leave when done), a failing request leaving without disturbing the others,
-and the refusal of a request larger than the budget."""
+slot limit, continuous batching at step granularity (every resident request's
+next step is queued as soon as its own previous step is seen finished, so
+requests join while others are resident, leave when done, and a small request
+never waits for a large one's steps), a failing request leaving without
+disturbing the others, and the refusal of a request larger than the budget."""
+import threading
+
 import pytest
 
 from paper_1703_06606_gb300 import serve
@@ -10,16 +14,20 @@ from paper_1703_06606_gb300 import workloads as W
 
 
 class FakeBackend:
-    """Solver / Batch / footprint with the binding's signatures.  A solver's
-    footprint is m1 * m2 bytes; the backend tracks the bytes and solvers alive
-    and every batch it is asked to step."""
+    """Solver / footprint with the binding's signatures.  A solver's footprint
+    is m1 * m2 bytes; a launched step finishes after `polls(m1, m2)` polls
+    (larger grids take longer).  The backend tracks the bytes and solvers
+    alive, the order of step launches and which solvers had a step in flight
+    at each launch."""
 
-    def __init__(self, fail_names=()):
+    def __init__(self, fail_names=(), polls=lambda m1, m2: 1):
         self.fail_names = set(fail_names)
+        self.polls = polls
         self.live_bytes = self.max_live_bytes = 0
         self.live = self.max_live = 0
         self.created = []
-        self.batches = []
+        self.launches = []      # (name, names of the other solvers with a step in flight)
+        self.lock = threading.Lock()
 
     def footprint(self, m1, m2, periodic_x=False, levels=0, precision=0, Lx=1.0):
         return m1 * m2
@@ -29,18 +37,18 @@ class FakeBackend:
         s.kw = kw
         return s
 
-    def Batch(self, solvers):
-        return FakeBatch(self, solvers)
-
 
 class FakeSolver:
     def __init__(self, be, m1, m2):
         self.be, self.fp, self.steps, self.name = be, m1 * m2, 0, None
-        be.live_bytes += self.fp
-        be.live += 1
-        be.max_live_bytes = max(be.max_live_bytes, be.live_bytes)
-        be.max_live = max(be.max_live, be.live)
-        be.created.append(self)
+        self.need = be.polls(m1, m2)
+        self.left = None  # polls until the launched step finishes
+        with be.lock:
+            be.live_bytes += self.fp
+            be.live += 1
+            be.max_live_bytes = max(be.max_live_bytes, be.live_bytes)
+            be.max_live = max(be.max_live, be.live)
+            be.created.append(self)
 
     def set_fields(self, f):
         self.name = f["name"]
@@ -48,26 +56,27 @@ class FakeSolver:
     def get_fields(self):
         return {"steps": self.steps}
 
+    def step_launch(self, dt):
+        assert self.left is None, "a step is already in flight"
+        with self.be.lock:
+            busy = [s.name for s in self.be.created if s.left is not None]
+            self.be.launches.append((self.name, busy))
+        self.left = self.need
+
+    def step_poll(self):
+        assert self.left is not None, "no step launched"
+        self.left -= 1
+        if self.left > 0:
+            return None
+        self.left = None
+        self.steps += 1
+        code = -4 if self.name in self.be.fail_names else 0
+        return 3, 1e-10, code, 0.5
+
     def close(self):
-        self.be.live_bytes -= self.fp
-        self.be.live -= 1
-
-
-class FakeBatch:
-    def __init__(self, be, solvers):
-        self.be, self.solvers = be, list(solvers)
-
-    def step(self, dts):
-        assert len(dts) == len(self.solvers)
-        self.be.batches.append([s.name for s in self.solvers])
-        st = []
-        for s in self.solvers:
-            s.steps += 1
-            st.append(-4 if s.name in self.be.fail_names else 0)
-        return st, [3] * len(self.solvers)
-
-    def close(self):
-        pass
+        with self.be.lock:
+            self.be.live_bytes -= self.fp
+            self.be.live -= 1
 
 
 def _requests(sizes, steps):
@@ -93,9 +102,31 @@ def test_admission_in_order_under_budget_and_slots():
         assert r.status == 0 and r.done_steps == r.steps
         assert fields[r.rid] == {"steps": r.steps}
         assert r.admitted <= r.finished
-    # continuous batching: some batch holds a request that joined after another left
-    joined = {n: i for i, b in reversed(list(enumerate(be.batches))) for n in b}
-    assert any(joined[b[-1]] > 0 and joined[b[0]] < joined[b[-1]] for b in be.batches)
+    # continuous batching: some request's first step was launched while an
+    # earlier request, admitted before it, still had steps in flight
+    first = {}
+    for k, (name, busy) in enumerate(be.launches):
+        first.setdefault(name, (k, busy))
+    assert any(busy and name != "r0" for name, (k, busy) in first.items())
+
+
+def test_a_small_request_does_not_wait_for_a_large_ones_steps():
+    """Steps at step granularity: a small request (one poll per step) does
+    all its steps while a large request (40 polls per step) is still in its
+    first one, and its recorded step latency is its own, not the large
+    request's."""
+    reqs = _requests([(128, 128), (16, 16)], [2, 6])
+    be = FakeBackend(polls=lambda m1, m2: 40 if m1 * m2 > 1000 else 1)
+    srv = serve.Server(budget_bytes=1e9, backend=be)
+    reqs, _ = srv.run(reqs, poll_sleep_s=0.0)
+    big, small = reqs
+    assert big.status == 0 and small.status == 0
+    assert small.done_steps == 6 and big.done_steps == 2
+    # all of the small request's launches came while the large one had a step in flight
+    small_launches = [busy for name, busy in be.launches if name == "r1"]
+    assert len(small_launches) == 6 and all("r0" in busy for busy in small_launches[1:])
+    assert small.finished < big.finished
+    assert max(small.step_ms) < min(big.step_ms)
 
 
 def test_a_failing_request_leaves_alone():
@@ -105,7 +136,7 @@ def test_a_failing_request_leaves_alone():
     reqs, _ = srv.run(reqs)
     assert [r.status for r in reqs] == [0, -4, 0, 0]
     assert [r.done_steps for r in reqs] == [3, 1, 3, 3]
-    assert be.batches[1] == ["r0", "r2", "r3"] and be.live == 0
+    assert [n for n, _ in be.launches].count("r1") == 1 and be.live == 0
 
 
 def test_a_request_larger_than_the_budget_is_refused():
@@ -124,7 +155,7 @@ def test_request_records():
     assert [(x["request"], x["status"], x["done_steps"]) for x in recs] == [
         (0, 0, 2), (1, -4, 1), (2, 0, 3)]
     for x in recs:
-        assert len(x["step_ms"]) == len(x["vcycles"]) == x["done_steps"]
+        assert len(x["step_ms"]) == len(x["vcycles"]) == len(x["device_ms"]) == x["done_steps"]
         assert x["arrival_s"] <= x["admitted_s"] <= x["finished_s"]
         assert x["latency_ms"] >= x["queue_wait_ms"] >= 0.0
 
