@@ -408,6 +408,7 @@ def run_ours(args, rank, world, local_rank):
     # FP64, tol 1e-10) and the Rayleigh-Taylor instability (1024x4096, mixed
     # precision, the paper's smoother)
     paper_workloads = None
+    roofline_fp32 = None
     if not args.no_workloads:
         paper_workloads = {}
         for Pw, prec, nsteps in ((workloads.capillary_64(), 0, 10),
@@ -432,7 +433,11 @@ def run_ours(args, rank, world, local_rank):
                 "value": world * Pw.cells * nsteps / wtot, "unit": UNIT,
                 "ms_per_step": float(np.mean(wms)), "vcycles_per_step": float(np.mean(wcyc)),
                 "precision": "mixed" if prec else "FP64", "steps": nsteps, "tol": Pw.tol,
-                "final_residual": res}
+                "final_residual": res,
+                "options": {k: sw.get_option(k) for k in ("wave_cells32", "wave_rows",
+                                                           "vanka_team_max32")}}
+            if prec:  # the FP32 smoothers of the mixed path against HBM
+                roofline_fp32 = fp32_smoother_roofline(sw, Pw, stream, flush)
             sw.close()
 
     # ---- per-step cost on the workload of Sec. 9 (the paper's Table 2: CPU
@@ -517,19 +522,28 @@ def run_ours(args, rank, world, local_rank):
         for sb in sols:
             sb.close()
 
-    # ---- serving: a bounded Poisson stream of capillary-wave and drop requests
+    # ---- serving: a Poisson stream of capillary-wave and drop requests at the
+    # serving workload's parameters (50 requests/s, N log-uniform in [128, 1024],
+    # 50 steps each at dt = 1e-4, mixed precision, 150 GB budget), bounded to
+    # --serve-requests requests so that the run ends within seconds; every
+    # resident request steps as soon as its own previous step is done
     serving = None
     if not args.no_serve:
         from paper_1703_06606_gb300 import serve
-        reqs = serve.poisson_requests(args.serve_requests, rate=50.0, n_min=128, n_max=512,
+        reqs = serve.poisson_requests(args.serve_requests, rate=50.0, n_min=128, n_max=1024,
                                       steps=args.serve_steps, dt=1e-4)
         srv = serve.Server(budget_bytes=150e9)
-        reqs, _ = srv.run(reqs)
-        serving = serve.summarize(reqs, srv.wall, srv.max_resident)
+        reqs, _ = srv.run(reqs, device=local_rank)
+        serving = serve.summarize(reqs, srv.wall, srv.max_resident, srv.max_backlog)
         serving.update({"arrivals": "Poisson, 50/s", "grid": "N x N, N log-uniform in "
-                        "[128, 512] (multiple of 64)", "steps_per_request": args.serve_steps,
+                        "[128, 1024] (multiple of 64)", "steps_per_request": args.serve_steps,
                         "dt": 1e-4, "budget_bytes": 150e9,
-                        "precision": "mixed", "smoother": "coupled 7x7 block"})
+                        "precision": "mixed", "smoother": "coupled 7x7 block",
+                        "stepping": "each request's next step is queued as soon as its own "
+                                    "previous step is seen finished (qnsch_step_launch / "
+                                    "qnsch_step_poll); step latency = launch to completion "
+                                    "seen by the server, step_device_ms = CUDA events around "
+                                    "the step on its stream"})
 
     # ---- end to end through the public API with host buffers (pinned)
     host_in = {k: torch.empty(v.shape, dtype=torch.float64, pin_memory=True).numpy()
@@ -589,6 +603,8 @@ def run_ours(args, rank, world, local_rank):
         line["stress"] = stress
     if paper_workloads is not None:
         line["workloads"] = paper_workloads
+    if roofline_fp32 is not None:
+        line["roofline_fp32"] = roofline_fp32
     if table2 is not None:
         line["table2"] = table2
     if batched is not None:
@@ -661,6 +677,50 @@ def prof_kinds(s, P, stream, flush, nsteps):
                               "share": tot / max(sum(ms), 1e-30), "visits": vis / nsteps,
                               "avg_launch_us": 1e3 * tot / max(n, 1),
                               "visits_per_launch": vis / max(n, 1)}
+    s.profile(False)
+    return out
+
+
+def hbm_peak_gbs():
+    """The measured HBM copy bandwidth of this machine's GPUs (MEASURED_PEAKS.json
+    beside this file), else the earlier measurement of 6800 GB/s."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback (6.8 TB/s, an earlier GB300 measurement)"
+
+
+def fp32_smoother_roofline(s, P, stream, flush, nsteps=2):
+    """The FP32 smoothers of the mixed path on a large workload, against HBM:
+    algorithmic bytes (one pass over the words a sweep needs, VANKA_WORDS_PER_CELL
+    and CH_WORDS_PER_CELL in FP32) over the event-timed duration of the finest
+    level's smoothing launches.  With the banded wavefront (wave_cells32) one
+    launch runs nu smoothing steps of both smoothers; without it the finest
+    level's Vanka colour launches and CH colour launches are timed apart."""
+    import torch
+    hbm, src = hbm_peak_gbs()
+    s.profile(1 | 8 | 16)
+    for k in range(nsteps):
+        flush.fill_(float(k))
+        s.step(P.dt)
+    torch.cuda.synchronize()
+    out = {"workload": P.name, "peak": hbm, "unit": "GB/s", "peak_source": src,
+           "bound": "hbm", "kernels": {}}
+    per_cell = {"wave": 4 * (VANKA_WORDS_PER_CELL + CH_WORDS_PER_CELL),
+                "vanka_finest": 4 * VANKA_WORDS_PER_CELL, "ch": 4 * CH_WORDS_PER_CELL}
+    for kind in ("wave", "vanka_finest", "ch"):
+        n, ms, vis = s.profile_read_kind(kind)
+        if n == 0:
+            continue
+        gbs = vis * per_cell[kind] / (ms * 1e-3) / 1e9
+        tr = TRAFFIC_BYTES.get(kind + "_fp32")
+        out["kernels"][kind] = {"launches": n, "avg_launch_us": 1e3 * ms / n,
+                                "visits_per_launch": vis / n,
+                                "algorithmic_bytes_per_launch": vis / n * per_cell[kind],
+                                "achieved": gbs, "frac": gbs / hbm,
+                                "traffic": tr[0] if tr else None,
+                                "traffic_source": tr[1] if tr else None}
     s.profile(False)
     return out
 
@@ -763,8 +823,8 @@ def main():
     ap.add_argument("--no-table2", action="store_true")
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=32)
-    ap.add_argument("--serve-steps", type=int, default=10)
+    ap.add_argument("--serve-requests", type=int, default=48)
+    ap.add_argument("--serve-steps", type=int, default=50)
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))

@@ -136,7 +136,9 @@ int qnsch_footprint(const qnsch_grid* grid, int precision, size_t* bytes);
    "eps_mob": Cn, "precision": 0, "graphs": 1, "fuse_cells": 128,
    "fuse_cells32": 512, "coupled": 0, "scheme": 0, "vanka_team_max": 8192,
    "ch_team_max": 4096, "vanka_team_max32": 65536, "ch_team_max32": 0,
-   "pdl": 1, "step_time_limit": 0, "diverge_cycles": 0, "device_loop": 1.
+   "pdl": 1, "step_time_limit": 0, "diverge_cycles": 0, "device_loop": 1,
+   "wave_cells32": 0, "wave_rows": 8, "wave_wait_cycles": 2147483648,
+   "wave_stall": 0.
    Unknown keys give QNSCH_EINVAL, and so do values out of range, which leave
    the option unchanged: NaN for any key; counts that are not integers in
    their range (nu1, nu2, nu_coarse: 0..1000; maxcyc, diverge_cycles:
@@ -150,6 +152,18 @@ int qnsch_footprint(const qnsch_grid* grid, int precision, size_t* bytes);
    exceeds the limit with the residual still above tol, stops and returns
    QNSCH_ETIMEOUT without committing the step.  A cycle already running goes
    to its end, so a step can overrun the limit by one outer cycle.
+   wave_cells32 (integer >= 0; 0: never): error-equation levels (precision 1
+   and 2) with at least this many cells and at least 2 wave_rows rows run
+   each block of nu smoothing steps as one banded wavefront launch instead of
+   one launch per colour: the passes (CH red and black, then the Vanka or
+   coupled colours) run band by band (bands of wave_rows >= 4 rows) in a
+   skewed order, each band's pass waiting only for the previous pass on the
+   band and its two neighbours, so a band stays in L2 across its passes.  The
+   results are bit-identical to the per-colour launches.  Its waits are
+   bounded by wave_wait_cycles SM clock cycles (integer >= 0); a wait that runs
+   out ends the step with QNSCH_ETIMEOUT, uncommitted.  wave_stall (0 or 1) is
+   a test hook for that path: with 1, one wait of every wavefront launch waits
+   for a count nothing reaches.
    device_loop: 1 (with graphs = 1 and profiling off) runs qnsch_step and
    qnsch_batch_step as one graph per step: the initial residual, a
    conditional WHILE node around the outer cycle whose last kernel applies the
@@ -308,11 +322,12 @@ int qnsch_iterate_energy(const qnsch_t* h, double* E, double* D);
 /* Measurement hooks (no counterpart in the paper).  qnsch_profile(h, mask)
    starts bracketing launches with pairs of CUDA events on the handle's stream
    (at most 4096 launches between reads) and resets the totals; mask 0 stops.
-   Bit k of mask (0..15, else QNSCH_EINVAL) times the launches of kind k:
+   Bit k of mask (0..31, else QNSCH_EINVAL) times the launches of kind k:
    0 the Vanka (or coupled, or projection 4x4) smoother on the finest level,
    1 the same smoother's per-level launches on the levels below it,
    2 the fused single-block V-cycle of the coarse levels, 3 the CH smoother on
-   the finest level.  Timing inserts event records into the replayed cycle
+   the finest level, 4 the banded wavefront launches on the finest level
+   (wave_cells32; visits: cells x smoothing steps).  Timing inserts event records into the replayed cycle
    graph, so while any bit is set qnsch_step drives its cycles from the host
    (device_loop is not used).  qnsch_profile_read synchronises the stream and
    returns the number of timed launches and their summed device time in
@@ -328,12 +343,16 @@ int qnsch_profile_read_kind(qnsch_t* h, int kind, long long* launches, double* t
 int qnsch_kernel_launches(long long* n);
 /* Asynchronous step (no counterpart in the paper; the interface a server
    uses to advance many instances without waiting for the slowest).
-   qnsch_step_launch queues one whole step of size dt on the handle's stream
-   and returns without waiting (with device_loop on: the step graph; without
-   it, the host-driven step runs inside the call).  Until qnsch_step_poll has
-   reported it done, the handle refuses other stepping calls with
-   QNSCH_ESTATE.  qnsch_step_poll does not wait: *done = 0 while the step is
-   on the GPU; once it has finished, *done = 1 and n_vcycles, final_residual,
+   qnsch_step_launch starts one step of size dt on the handle's stream and
+   returns without waiting.  With device_loop on it queues the whole step graph;
+   with device_loop = 0 it queues the step's start and initial residual, and
+   each qnsch_step_poll that finds the latest norms arrived applies the
+   stopping rules and queues the next outer cycle or the commit (the
+   host-driven loop of qnsch_step, one cycle per poll at most).  Until
+   qnsch_step_poll has reported the step done, the handle refuses other
+   stepping calls with QNSCH_ESTATE.  qnsch_step_poll does not wait for the
+   GPU: *done = 0 while the step runs; once it has ended, *done = 1 and
+   n_vcycles, final_residual,
    status (what qnsch_step would have returned: 0, QNSCH_ENOTCONV, QNSCH_ENAN,
    QNSCH_ETIMEOUT, ...) and device_ms (the step's device time between CUDA
    events recorded around it on the handle's stream) receive the outcome;
@@ -347,10 +366,11 @@ int qnsch_step_poll(qnsch_t* h, int* done, int* n_vcycles, double* final_residua
    GPU runs many small problems at once).  A batch refers to n existing
    handles, each with its own stream (handles created without qnsch_set_stream
    each have a private one; two handles sharing a stream are rejected).
-   qnsch_batch_step advances every instance by one step of size dt[a]: it
-   queues every instance's outer cycles, one cycle per instance per round, so
-   the instances' kernels run concurrently on the GPU, and stops each instance
-   at its own tolerance.  Every instance goes through exactly the arithmetic of
+   qnsch_batch_step advances every instance by one step of size dt[a] with the
+   host-driven loop: it polls the instances in turn and queues each one's next
+   outer cycle as soon as that instance's norms have arrived, so the
+   instances' kernels run concurrently on the GPU and none waits for another,
+   and stops each instance at its own tolerance.  Every instance goes through exactly the arithmetic of
    qnsch_step on that handle, so its result does not depend on the batch.
    status[a] receives that instance's qnsch_step status (0, QNSCH_ENOTCONV,
    QNSCH_ENAN, ...), n_vcycles[a] (may be NULL) its V-cycle count.  The call

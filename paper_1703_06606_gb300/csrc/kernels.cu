@@ -2057,6 +2057,137 @@ __global__ void __launch_bounds__(NT) k_coarse_vcycle(Prm<T> P, CoarseLevels<T> 
 }
 
 // --------------------------------------------------------------------------
+// banded wavefront of smoothing passes (one launch for nu smoothing steps on a
+// level).  A smoothing step is a sequence of passes: CH red, CH black, then the
+// Vanka colours (or the coupled block's colours).  Every visit reads and
+// writes rows within 2 of its own, so with bands of at least 4 rows pass k on
+// band b depends only on pass k - 1 on bands b - 1, b, b + 1.  Tickets are
+// handed out in the order of t = b + 2k (then k), a topological order: a
+// block takes a ticket, waits until each neighbouring band has finished pass
+// k - 1 (per-band counters of finished passes), runs the pass's visits on its
+// band and publishes the band's new count.  Each visit sees exactly the
+// values it sees when every pass is a launch over the whole level, so the
+// results are the same; what changes is that a band's arrays stay in L2
+// across its passes instead of every colour launch streaming the whole level.
+// A ticket's dependencies hold earlier tickets, taken by blocks that are
+// running or done, so the wavefront progresses whatever the number of
+// resident blocks.  Waits are bounded: past `budget` SM cycles a wait sets
+// *flag (the step then fails with QNSCH_ETIMEOUT) and every later wait
+// returns at once.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// the visits of pass `pass` on rows r0..r1 (1-based, inclusive)
+template <typename T, class Form>
+__device__ __forceinline__ void wave_pass(const Prm<T>& P, const Lv<T>& L, const WavePlan& W,
+                                          int pass, int r0, int r1, T omega) {
+  const int per = W.coupled ? L.kcol : L.kcol + 2;
+  const int q = pass % per;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (!W.coupled && q < 2) {  // CH colour q: packed as in k_ch
+    const int mpr = (L.m1 + 1) / 2;
+    const int t_lo = (r0 - 1) * mpr, t_hi = r1 * mpr;
+    if (mpr * L.m2 <= W.ch_team_max) {
+      for (int base = t_lo; base < t_hi; base += nt / 4) {
+        if (base + ((tid & ~31) >> 2) >= t_hi) continue;  // warp-uniform
+        int t = base + (tid >> 2), i = 1, j = 1;
+        bool ok = t < t_hi;
+        if (ok) {
+          j = t / mpr + 1;
+          i = (((q - j) & 1) ? 1 : 2) + 2 * (t % mpr);
+          ok = i <= L.m1;
+        }
+        if (!ok) i = j = 1;
+        ch_team<T, Form>(P, L, i, j, ok);
+      }
+    } else {
+      for (int t = t_lo + tid; t < t_hi; t += nt) {
+        int j = t / mpr + 1;
+        int i = (((q - j) & 1) ? 1 : 2) + 2 * (t % mpr);
+        if (i <= L.m1) ch_cell<T, Form>(P, L, i, j);
+      }
+    }
+    return;
+  }
+  const int col = W.coupled ? q : q - 2;
+  ColourSlots cs = vanka_slots(L, col);
+  // the slots whose row j0 + rstep * (t / mpr) lies in [r0, r1]
+  if (r1 < cs.j0) return;
+  const int qlo = r0 > cs.j0 ? (r0 - cs.j0 + cs.rstep - 1) / cs.rstep : 0;
+  const int qhi = (r1 - cs.j0) / cs.rstep;
+  const int t_lo = qlo * cs.mpr, t_hi = min((qhi + 1) * cs.mpr, cs.n);
+  if (cs.n <= W.vanka_team_max) {
+    for (int base = t_lo; base < t_hi; base += nt / 4) {
+      if (base + ((tid & ~31) >> 2) >= t_hi) continue;  // warp-uniform
+      int t = base + (tid >> 2), i = 1, j = 1;
+      bool ok = t < t_hi && vanka_slot_cell(L, col, cs, t, i, j);
+      if (!ok) i = j = 1;
+      if (W.coupled) coupled_team<T, Form>(P, L, i, j, ok, omega);
+      else vanka_team<T, Form>(P, L, i, j, ok, omega);
+    }
+  } else {
+    for (int t = t_lo + tid; t < t_hi; t += nt) {
+      int i, j;
+      if (!vanka_slot_cell(L, col, cs, t, i, j)) continue;
+      if (W.coupled) coupled_cell<T, Form>(P, L, i, j, omega);
+      else vanka_cell<T, Form>(P, L, i, j, omega);
+    }
+  }
+}
+
+constexpr int WAVE_NT = 256;
+
+template <typename T, class Form>
+__global__ void __launch_bounds__(WAVE_NT) k_wave(Prm<T> P, Lv<T> L, WavePlan W, T omega,
+                                                  unsigned* ctr, double* flag) {
+  pdl_enter();
+  __shared__ unsigned s_t;
+  unsigned* done = ctr + 1;
+  const int N = W.nbands, K = W.npass;
+  // tickets run over the (t = b + 2k, k) grid, t in [0, N + 2K - 2]
+  const unsigned tickets = (unsigned)(N + 2 * K - 1) * (unsigned)K;
+  for (;;) {
+    if (threadIdx.x == 0) s_t = atomicAdd(ctr, 1u);
+    __syncthreads();
+    const unsigned t = s_t;
+    __syncthreads();
+    if (t >= tickets) break;
+    const int tau = (int)(t / (unsigned)K), k = (int)(t % (unsigned)K), b = tau - 2 * k;
+    if (b < 0 || b >= N) continue;  // a ticket of the grid with no band
+    if (threadIdx.x == 0 && k > 0) {
+      // pass k - 1 done on this band and its neighbours (test hook: one
+      // wait for a count that nothing reaches)
+      const unsigned need = (W.stall && b == 0 && k == 1) ? 0xffffffffu : (unsigned)k;
+      const long long t0 = clock64();
+      for (int nb = max(b - 1, 0); nb <= min(b + 1, N - 1); ++nb) {
+        while (ld_acquire_u32(done + nb) < need) {
+          if (*(volatile double*)flag != 0.0) break;
+          if (clock64() - t0 > W.budget) {
+            *(volatile double*)flag = 1.0;
+            break;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    const int r0 = b * W.rows + 1, r1 = min((b + 1) * W.rows, L.m2);
+    wave_pass<T, Form>(P, L, W, k, r0, r1, omega);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      st_release_u32(done + b, (unsigned)(k + 1));
+    }
+  }
+}
+
+// --------------------------------------------------------------------------
 // defect correction (mixed precision): FP64 level <-> error-equation level
 // --------------------------------------------------------------------------
 // error-equation frozen data = rounded FP64 frozen data (whole padded arrays)
@@ -2363,7 +2494,8 @@ __global__ void k_dissipation(Prm<T> P, Lv<T> L, double w_visc, double w_div, do
 // if any family is not finite), [1] cycles done k, [2] consecutive cycles the
 // residual grew, [3] stopped by the time limit, [4] stopped by growth,
 // [5] commit, [6..10] l2 norms, [11..15] max norms, [16] (as a 64-bit
-// integer) the global timer in ns at the start of the step.
+// integer) the global timer in ns at the start of the step, [17] nonzero once
+// a bounded wait of the wavefront smoother has run out.
 // --------------------------------------------------------------------------
 __device__ __forceinline__ long long global_ns() {
   long long t;
@@ -2401,7 +2533,10 @@ __global__ void k_loop_ctl(const double* nrm, double* ctl, cudaGraphConditionalH
   }
   const bool div = !first && diverge > 0 && grew >= (double)diverge;
   bool cont = !div && r == r && r > tol && k < (double)maxcyc;
-  bool late = false;
+  // a bounded wait of the wavefront smoother ran out (ctl[17] set): the cycle's
+  // result is not to be trusted, the step ends as late
+  bool late = ctl[17] != 0.0;
+  if (late) cont = false;
   if (cont && limit_ns > 0.0 &&
       (double)(global_ns() - *reinterpret_cast<const long long*>(ctl + 16)) > limit_ns) {
     cont = false;
@@ -2716,6 +2851,29 @@ void launch_pack_out(const Lv<T>& L, double* dst, const T* src, int kind, cudaSt
   ++g_launches;
 }
 
+template <typename T, class Form>
+void launch_wave(const Prm<T>& P, const Lv<T>& L, const WavePlan& W, T omega, unsigned* ctr,
+                 double* flag, cudaStream_t s) {
+  static std::atomic<int> blocks_per_sm{0};
+  static std::atomic<int> sms{0};
+  if (!sms.load()) {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    sms = n > 0 ? n : 1;
+  }
+  if (!blocks_per_sm.load()) {
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_wave<T, Form>, WAVE_NT, 0);
+    blocks_per_sm = b > 0 ? b : 1;
+  }
+  const long long tasks = (long long)W.nbands * W.npass;
+  const int grid = (int)std::min<long long>((long long)sms.load() * blocks_per_sm.load(), tasks);
+  cudaMemsetAsync(ctr, 0, (size_t)(1 + W.nbands) * sizeof(unsigned), s);
+  qlaunch(&k_wave<T, Form>, grid, WAVE_NT, 0, s, P, L, W, omega, ctr, flag);
+  ++g_launches;
+}
+
 void launch_loop_clock(double* ctl, cudaStream_t s) {
   qlaunch(&k_loop_clock, 1, 1, 0, s, ctl);
   ++g_launches;
@@ -2769,6 +2927,10 @@ QN_INSTANTIATE(float)
 QN_INSTANTIATE_FORM(double, FullForm)
 QN_INSTANTIATE_FORM(double, ErrForm)
 QN_INSTANTIATE_FORM(float, ErrForm)
+template void launch_wave<float, ErrForm>(const Prm<float>&, const Lv<float>&, const WavePlan&,
+                                          float, unsigned*, double*, cudaStream_t);
+template void launch_wave<double, ErrForm>(const Prm<double>&, const Lv<double>&, const WavePlan&,
+                                           double, unsigned*, double*, cudaStream_t);
 // projection method (FP64, per-level launches)
 template void launch_residual<double, ProjForm>(const Prm<double>&, const Lv<double>&, double*,
                                                 cudaStream_t);

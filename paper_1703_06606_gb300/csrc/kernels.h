@@ -22,6 +22,22 @@ void launch_ch(const Prm<T>& P, const Lv<T>& L, int colour, cudaStream_t s, int 
 template <typename T, class Form>
 void launch_vanka(const Prm<T>& P, const Lv<T>& L, int colour, T omega, cudaStream_t s,
                   int team_max = 0);
+// a banded wavefront of smoothing passes on one level (kernels.cu, k_wave):
+// npass passes (per smoothing step: CH red, CH black and the kcol Vanka
+// colours, or the kcol coupled colours), bands of `rows` rows, the same team
+// thresholds as the per-colour launches, waits bounded by `budget` SM cycles;
+// stall: test hook, one wait that nothing satisfies
+struct WavePlan {
+  int npass, coupled, rows, nbands;
+  int ch_team_max, vanka_team_max;
+  long long budget;
+  int stall;
+};
+// ctr: 1 + nbands unsigned counters (zeroed by the launcher); flag: set to
+// nonzero when a wait runs out
+template <typename T, class Form>
+void launch_wave(const Prm<T>& P, const Lv<T>& L, const WavePlan& W, T omega, unsigned* ctr,
+                 double* flag, cudaStream_t s);
 // the V-cycle on levels[0..n-1] (levels[0] is its finest) in one thread block
 template <typename T, class Form>
 void launch_coarse_vcycle(const Prm<T>& P, const Lv<T>* levels, int n, int nu1, int nu2, int nuc,

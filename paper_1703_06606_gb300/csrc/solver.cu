@@ -88,10 +88,21 @@ double seconds_since(std::chrono::steady_clock::time_point t0) {
 
 constexpr int NFIELD = 45;  // arrays per level (see Lv)
 // doubles in s->scal and its pinned host mirror s->hbuf, and the offset of the
-// device-side step loop's control block in them (layout in kernels.cu)
+// device-side step loop's control block in them (layout in kernels.cu); its
+// entry WAIT_FLAG is set by a bounded wait of the wavefront smoother that ran
+// out of time
 constexpr int NSCAL = 128;
 constexpr int CTL = 64;
 constexpr int CTL_LEN = 18;
+constexpr int WAIT_FLAG = CTL + 17;
+// bands of the wavefront smoother have at least this many rows
+constexpr int WAVE_MIN_ROWS = 4;
+// bytes of the wavefront's counters: a ticket and one count per band of the
+// finest level at the smallest band height, rounded to 256 B
+size_t wave_ctr_bytes(int m2) {
+  size_t n = 2 + (size_t)(m2 + WAVE_MIN_ROWS - 1) / WAVE_MIN_ROWS;
+  return (n * sizeof(unsigned) + 255) / 256 * 256;
+}
 
 // option "pdl": programmatic dependent launch of every kernel (process-wide)
 static std::atomic<int> g_pdl_option{1};
@@ -163,6 +174,15 @@ struct qnsch_s {
   // the same on the error-equation levels of the defect correction (their
   // visits are latency-bound up to this size; larger levels stream from HBM)
   int team_max32 = 65536;
+  // error-equation levels with at least this many cells run nu smoothing steps
+  // as one banded wavefront launch (k_wave; 0: never), with bands of
+  // wave_rows rows, waits bounded by wave_budget SM cycles; wave_stall is a
+  // test hook that makes one wait run out
+  long long wave_cells = 0;
+  int wave_rows = 8;
+  long long wave_budget = 1LL << 31;
+  int wave_stall = 0;
+  unsigned* wave_ctr = nullptr;  // 1 + bands of level 0 counters
   // failure detection: a step stops once it has run this many seconds of wall
   // time (0: no limit), or once its residual has grown over this many
   // consecutive outer cycles (0: never)
@@ -220,6 +240,12 @@ struct qnsch_s {
   int a_status = 0, a_cycles = 0;
   double a_res = 0.0;
   cudaEvent_t ev_s0 = nullptr, ev_s1 = nullptr;
+  // the host-driven step as a state machine (async == 2; qnsch_batch_step):
+  // phase 1 waits for the norms of the initial residual, 2 for those of a
+  // cycle, 3 for the commit; the stopping rules are qnsch_step's
+  int hs_phase = 0, hs_k = 0, hs_grew = 0, hs_late = 0, hs_expired = 0;
+  double hs_res = 0.0, hs_prev = 0.0;
+  std::chrono::steady_clock::time_point hs_t0;
   // the FP64 residual arrays of level 0 hold r(x) of the current iterate
   int res_valid = 0;
   // optional CUDA-event timing of launches by kind (bit k of prof: kind k,
@@ -232,8 +258,8 @@ struct qnsch_s {
   int ev_used = 0;
   long long prof_launches = 0;
   double prof_ms = 0.0;
-  long long pk_n[4] = {0, 0, 0, 0};
-  double pk_ms[4] = {0, 0, 0, 0}, pk_visits[4] = {0, 0, 0, 0};
+  long long pk_n[5] = {0, 0, 0, 0, 0};
+  double pk_ms[5] = {0, 0, 0, 0, 0}, pk_visits[5] = {0, 0, 0, 0, 0};
   double dt = 0.0;
   double last_diss = 0.0;
 };
@@ -369,6 +395,10 @@ int alloc_all(qnsch_s* s) {
   s->scal = (double*)dev_alloc(s->mem, NSCAL * sizeof(double));
   if (!s->scal) return QNSCH_ENOMEM;
   s->blocks.push_back(s->scal);
+  s->wave_ctr = (unsigned*)dev_alloc(s->mem, wave_ctr_bytes(s->m2));
+  if (!s->wave_ctr) return QNSCH_ENOMEM;
+  s->blocks.push_back(s->wave_ctr);
+  cudaMemsetAsync(s->scal, 0, NSCAL * sizeof(double), s->stream);
   if (cudaMallocHost(&s->hbuf, NSCAL * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     return QNSCH_ENOMEM;
@@ -451,7 +481,7 @@ Prm<T> cast_prm(const Prm<double>& P) {
 
 constexpr int MAX_PROF_EVENTS = 8192;
 // kinds of timed launches (qnsch_profile's bit mask)
-enum { PK_VANKA0 = 0, PK_VANKA = 1, PK_COARSE = 2, PK_CH = 3, PK_N = 4 };
+enum { PK_VANKA0 = 0, PK_VANKA = 1, PK_COARSE = 2, PK_CH = 3, PK_WAVE = 4, PK_N = 5 };
 
 // cells of Vanka colour `colour` on an m1 x m2 level (the colourings of
 // colours_of: (2i + j) mod 8 when c8, else (i + 2j) mod kcol)
@@ -542,6 +572,33 @@ void smooth(qnsch_s* s, const std::vector<Lv<T>>& Ls, const Prm<T>& P, int l) {
   }
 }
 
+// n smoothing steps on level l: one banded wavefront launch on a large enough
+// error-equation level, else n times the per-colour launches of smooth()
+template <typename T, class Form>
+void smooth_steps(qnsch_s* s, const std::vector<Lv<T>>& Ls, const Prm<T>& P, int l, int n) {
+  if constexpr (std::is_same<Form, ErrForm>::value) {
+    const Lv<T>& L = Ls[l];
+    const int rows = std::max(s->wave_rows, WAVE_MIN_ROWS);
+    if (n > 0 && s->wave_cells > 0 && (long long)L.m1 * L.m2 >= s->wave_cells &&
+        L.m2 >= 2 * rows) {
+      qn::WavePlan W;
+      W.coupled = s->coupled;
+      W.rows = rows;
+      W.nbands = (L.m2 + rows - 1) / rows;
+      W.npass = n * (s->coupled ? L.kcol : L.kcol + 2);
+      W.ch_team_max = s->ch_team_max32;
+      W.vanka_team_max = s->team_max32;
+      W.budget = s->wave_budget;
+      W.stall = s->wave_stall;
+      int q = l == 0 ? prof_open(s, PK_WAVE, (double)L.m1 * L.m2 * n) : -1;
+      qn::launch_wave<T, Form>(P, L, W, (T)s->omega, s->wave_ctr, s->scal + WAIT_FLAG, s->stream);
+      prof_close(s, q);
+      return;
+    }
+  }
+  for (int k = 0; k < n; ++k) smooth<T, Form>(s, Ls, P, l);
+}
+
 // first level of Ls whose V-cycle runs fused in one thread block
 template <typename T>
 int fused_from(const qnsch_s* s, const std::vector<Lv<T>>& Ls) {
@@ -578,11 +635,10 @@ void vcycle(qnsch_s* s, const std::vector<Lv<T>>& Ls, const Prm<T>& P, int l) {
     return;
   }
   if (l == s->nlev - 1) {
-    int nc = coarse_sweeps(s);
-    for (int k = 0; k < nc; ++k) smooth<T, Form>(s, Ls, P, l);
+    smooth_steps<T, Form>(s, Ls, P, l, coarse_sweeps(s));
     return;
   }
-  for (int k = 0; k < s->nu1; ++k) smooth<T, Form>(s, Ls, P, l);
+  smooth_steps<T, Form>(s, Ls, P, l, s->nu1);
   const Lv<T>& F = Ls[l];
   const Lv<T>& C = Ls[l + 1];
   qn::launch_residual<T, Form>(P, F, (double*)nullptr, s->stream);
@@ -593,7 +649,7 @@ void vcycle(qnsch_s* s, const std::vector<Lv<T>>& Ls, const Prm<T>& P, int l) {
   vcycle<T, Form>(s, Ls, P, l + 1);
   qn::launch_prolong(P, F, C, s->stream);
   qn::launch_bc_unknowns(F, s->stream);
-  for (int k = 0; k < s->nu2; ++k) smooth<T, Form>(s, Ls, P, l);
+  smooth_steps<T, Form>(s, Ls, P, l, s->nu2);
 }
 
 // fold the recorded event pairs into the totals (stream must be idle)
@@ -631,7 +687,8 @@ void enqueue_norms(qnsch_s* s, const Prm<double>& P, bool to_host = true) {
   else qn::launch_residual<double, FullForm>(P, F, s->part, s->stream);
   qn::launch_norms_finalize(F, s->part, s->scal, s->stream);
   if (to_host)
-    cudaMemcpyAsync(s->hbuf, s->scal, 10 * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    cudaMemcpyAsync(s->hbuf, s->scal, (CTL + CTL_LEN) * sizeof(double), cudaMemcpyDeviceToHost,
+                    s->stream);
 }
 
 void norms_from_host(const qnsch_s* s, double* norms10) {
@@ -743,6 +800,7 @@ int alloc_err(qnsch_s* s) {
 void queue_begin(qnsch_s* s, double dt) {
   s->dt = dt;
   s->res_valid = 0;
+  cudaMemsetAsync(s->scal + WAIT_FLAG, 0, sizeof(double), s->stream);
   Prm<double> P = make_prm(s);
   Lv<double>& F = s->L[0];
   size_t bytes = s->level_elems0 * sizeof(double);
@@ -1098,11 +1156,88 @@ int finish_device_step(qnsch_s* s, int* n_vcycles, double* final_residual) {
   s->res_valid = 1;
   if (n_vcycles) *n_vcycles = k;
   if (final_residual) *final_residual = r;
+  if (c[17] != 0.0) return QNSCH_ETIMEOUT;  // a bounded wait of the smoother ran out
   if (!(r == r)) return QNSCH_ENAN;
   if (late) return QNSCH_ETIMEOUT;
   if (!committed) return QNSCH_ENOTCONV;
   s->last_diss = s->hbuf[25] + (s->scheme ? s->hbuf[26] : 0.0);
   return QNSCH_OK;
+}
+
+// Start a host-driven step: begin (A2), the initial residual with its norms
+// on their way to the host.  t0 is the time the step's clock starts from.
+int host_step_start(qnsch_s* s, double dt, std::chrono::steady_clock::time_point t0) {
+  int rc = begin(s, dt);
+  if (rc) return rc;
+  enqueue_norms(s, make_prm(s));
+  s->res_valid = 1;
+  cudaEventRecord(s->ev_norms, s->stream);
+  s->hs_phase = 1;
+  s->hs_k = s->hs_grew = s->hs_late = s->hs_expired = 0;
+  s->hs_res = HUGE_VAL;
+  s->hs_t0 = t0;
+  return QNSCH_OK;
+}
+
+// Advance a host-driven step without waiting: 0 while it runs (the next cycle
+// or the commit queued when the norms allowed), 1 once it has ended, with
+// *status as qnsch_step returns it and *k, *r its cycles and last residual.
+int host_step_advance(qnsch_s* s, int* status, int* k, double* r) {
+  if (s->hs_phase == 3) {  // the commit
+    cudaError_t e = cudaEventQuery(s->ev_norms);
+    if (e == cudaErrorNotReady) return 0;
+    s->hs_phase = 0;
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      s->pending = 0;
+      *status = QNSCH_ECUDA;
+    } else {
+      *status = finish_commit(s);
+    }
+    *k = s->hs_k;
+    *r = s->hs_res;
+    return 1;
+  }
+  double nrm[10];
+  int got = poll_norms(s, nrm);
+  if (got == 0) return 0;
+  auto end = [&](int st) {
+    s->hs_phase = 0;
+    s->pending = 0;
+    *status = st;
+    *k = s->hs_k;
+    *r = s->hs_res;
+    return 1;
+  };
+  if (got < 0) return end(got);
+  s->hs_res = maxfam(nrm);
+  if (s->hs_phase == 2) {  // a cycle has ended
+    ++s->hs_k;
+    if (s->hbuf[WAIT_FLAG] != 0.0) {  // a bounded wait of the smoother ran out
+      s->hs_expired = 1;
+      return end(QNSCH_ETIMEOUT);
+    }
+    s->hs_grew = s->hs_res > s->hs_prev ? s->hs_grew + 1 : 0;
+  }
+  const double rr = s->hs_res;
+  const bool div = s->hs_phase == 2 && s->diverge > 0 && s->hs_grew >= s->diverge;
+  if (!div && rr == rr && rr > s->tol && s->hs_k < s->maxcyc) {
+    if (s->time_limit > 0.0 && seconds_since(s->hs_t0) > s->time_limit) {
+      s->hs_late = 1;
+      return end(QNSCH_ETIMEOUT);
+    }
+    s->hs_prev = rr;
+    launch_cycle(s);
+    cudaEventRecord(s->ev_norms, s->stream);
+    s->hs_phase = 2;
+    return 0;
+  }
+  if (!(rr == rr)) return end(QNSCH_ENAN);
+  if (rr > s->tol) return end(QNSCH_ENOTCONV);
+  launch_commit(s);
+  cudaEventRecord(s->ev_norms, s->stream);
+  s->hs_phase = 3;
+  return 0;
 }
 
 }  // namespace
@@ -1215,6 +1350,7 @@ int qnsch_footprint(const qnsch_grid* grid, int precision, size_t* bytes) {
   total += (size_t)qn::partial_rows_needed(grid->m1, grid->m2) * 10 * sizeof(double);
   total += (size_t)(grid->m1 + 1) * (grid->m2 + 1) * sizeof(double);         // staging
   total += NSCAL * sizeof(double);
+  total += wave_ctr_bytes(grid->m2);
   *bytes = total;
   return QNSCH_OK;
 }
@@ -1282,6 +1418,17 @@ int set_option(qnsch_s* s, const std::string& k, double value) {
     s->use_graphs = value != 0.0;
   } else if (k == "device_loop") {
     s->device_loop = value != 0.0;
+  } else if (k == "wave_cells32") {
+    if (!(value >= 0.0 && value <= 9.0e15 && value == std::floor(value))) return QNSCH_EINVAL;
+    s->wave_cells = (long long)value;
+  } else if (k == "wave_rows") {
+    if (!count_of(value, WAVE_MIN_ROWS, 1 << 20, &n)) return QNSCH_EINVAL;
+    s->wave_rows = n;
+  } else if (k == "wave_wait_cycles") {
+    if (!(value >= 0.0) || !(value <= 9.0e15) || value != std::floor(value)) return QNSCH_EINVAL;
+    s->wave_budget = (long long)value;
+  } else if (k == "wave_stall") {
+    s->wave_stall = value != 0.0;
   } else if (k == "step_time_limit") {
     if (!(value >= 0.0) || !std::isfinite(value)) return QNSCH_EINVAL;
     s->time_limit = value;
@@ -1340,6 +1487,10 @@ int qnsch_get_option(const qnsch_t* s, const char* key, double* value) {
   else if (k == "precision") *value = s->precision;
   else if (k == "graphs") *value = s->use_graphs;
   else if (k == "device_loop") *value = s->device_loop;
+  else if (k == "wave_cells32") *value = (double)s->wave_cells;
+  else if (k == "wave_rows") *value = s->wave_rows;
+  else if (k == "wave_wait_cycles") *value = (double)s->wave_budget;
+  else if (k == "wave_stall") *value = s->wave_stall;
   else if (k == "step_time_limit") *value = s->time_limit;
   else if (k == "diverge_cycles") *value = s->diverge;
   else if (k == "fuse_cells") *value = s->fuse64;
@@ -1369,7 +1520,7 @@ int qnsch_profile(qnsch_t* s, int enable) {
     cudaStreamSynchronize(s->stream);
     prof_collect(s);
   }
-  if (enable < 0 || enable > 15) return QNSCH_EINVAL;
+  if (enable < 0 || enable > 31) return QNSCH_EINVAL;
   s->prof = enable;
   s->prof_launches = 0;
   s->prof_ms = 0.0;
@@ -1491,7 +1642,7 @@ int qnsch_step(qnsch_t* s, double dt, int* n_vcycles, double* final_residual) {
   double n[10];
   rc = residual_norms(s, P, n);
   if (rc) return rc;
-  int k = 0, grew = 0, late = 0;
+  int k = 0, grew = 0, late = 0, expired = 0;
   double r = maxfam(n);
   while (r == r && r > s->tol && k < s->maxcyc) {
     if (s->time_limit > 0.0 && seconds_since(t0) > s->time_limit) {
@@ -1503,11 +1654,19 @@ int qnsch_step(qnsch_t* s, double dt, int* n_vcycles, double* final_residual) {
     if (rc) return rc;
     r = maxfam(n);
     ++k;
+    if (s->hbuf[WAIT_FLAG] != 0.0) {  // a bounded wait of the smoother ran out
+      expired = 1;
+      break;
+    }
     grew = r > prev ? grew + 1 : 0;
     if (s->diverge > 0 && grew >= s->diverge) break;
   }
   if (n_vcycles) *n_vcycles = k;
   if (final_residual) *final_residual = r;
+  if (expired) {  // the cycle's result is not to be trusted, whatever its residual
+    s->pending = 0;
+    return QNSCH_ETIMEOUT;
+  }
   if (!(r == r)) {
     s->pending = 0;
     return QNSCH_ENAN;
@@ -1536,10 +1695,10 @@ int qnsch_step_launch(qnsch_t* s, double dt) {
     }
     if (rc != QNSCH_ECUDA || device_loop_on(s)) return rc;
   }
-  // no device-side loop: the step runs here and the poll reports its outcome
+  // no device-side loop: a host-driven step that each poll advances
   cudaEventRecord(s->ev_s0, s->stream);
-  s->a_status = qnsch_step(s, dt, &s->a_cycles, &s->a_res);
-  cudaEventRecord(s->ev_s1, s->stream);
+  int rc = host_step_start(s, dt, std::chrono::steady_clock::now());
+  if (rc) return rc;
   s->async = 2;
   return QNSCH_OK;
 }
@@ -1548,15 +1707,24 @@ int qnsch_step_poll(qnsch_t* s, int* done, int* n_vcycles, double* final_residua
                     double* device_ms) {
   if (!s || !done) return QNSCH_EINVAL;
   if (!s->async) return QNSCH_ESTATE;
-  cudaError_t e = cudaEventQuery(s->ev_s1);
-  if (e == cudaErrorNotReady) {
-    *done = 0;
-    return QNSCH_OK;
+  int st = 0, k = 0;
+  double r = 0.0;
+  if (s->async == 2) {
+    if (!host_step_advance(s, &st, &k, &r)) {
+      *done = 0;
+      return QNSCH_OK;
+    }
+    cudaEventRecord(s->ev_s1, s->stream);
+    cudaEventSynchronize(s->ev_s1);  // the step's work has ended: immediate
+  } else {
+    cudaError_t e = cudaEventQuery(s->ev_s1);
+    if (e == cudaErrorNotReady) {
+      *done = 0;
+      return QNSCH_OK;
+    }
+    if (e != cudaSuccess) cudaGetLastError();
+    st = finish_device_step(s, &k, &r);
   }
-  if (e != cudaSuccess) cudaGetLastError();
-  int st = s->a_status, k = s->a_cycles;
-  double r = s->a_res;
-  if (s->async == 1) st = finish_device_step(s, &k, &r);
   float ms = 0.f;
   if (cudaEventElapsedTime(&ms, s->ev_s0, s->ev_s1) != cudaSuccess) {
     cudaGetLastError();
@@ -1760,106 +1928,32 @@ int qnsch_batch_step(qnsch_batch_t* B, const double* dt, int* status, int* n_vcy
     for (int b = 0; b < a; ++b)
       if (B->inst[a]->stream == B->inst[b]->stream) return QNSCH_EINVAL;
   }
-  // every member runs its step as one graph on its own stream: queue them
-  // all, then collect
-  bool all_device = true;
-  for (int a = 0; a < n; ++a) all_device = all_device && device_loop_on(B->inst[a]);
-  if (all_device) {
-    std::vector<char> queued(n, 0);
-    for (int a = 0; a < n; ++a) {
-      status[a] = launch_device_step(B->inst[a], dt[a]);
-      queued[a] = status[a] == QNSCH_OK;
-      if (n_vcycles) n_vcycles[a] = 0;
-    }
-    for (int a = 0; a < n; ++a) {
-      if (queued[a]) {
-        status[a] = finish_device_step(B->inst[a], n_vcycles ? &n_vcycles[a] : nullptr, nullptr);
-      } else if (status[a] == QNSCH_ECUDA && !device_loop_on(B->inst[a])) {
-        // that member's runtime refused the step graph: its host-driven step
-        int k = 0;
-        double r = 0.0;
-        status[a] = qnsch_step(B->inst[a], dt[a], &k, &r);
-        if (n_vcycles) n_vcycles[a] = k;
-      }
-    }
-    return QNSCH_OK;
-  }
-  std::vector<int> live(n, 1), cyc(n, 0), grew(n, 0);
-  std::vector<char> wait(n, 0), late(n, 0);
-  std::vector<double> res(n, HUGE_VAL);
+  // Each member advances through its own host-driven step: its next cycle is
+  // queued as soon as its norms arrive, so instances of different sizes do
+  // not wait for one another.  (The members' whole-step graphs with the loop
+  // on the device measured slower here: 64 such graphs on 64 streams took
+  // 194 ms per batch step against 114 ms host-driven.)
   const auto t0 = std::chrono::steady_clock::now();
-  double nrm[10];
+  std::vector<char> running(n, 0);
   for (int a = 0; a < n; ++a) {
-    qnsch_s* s = B->inst[a];
-    status[a] = begin(s, dt[a]);
-    if (status[a]) {
-      live[a] = 0;
-      continue;
-    }
-    enqueue_norms(s, make_prm(s));
-    s->res_valid = 1;
-    cudaEventRecord(s->ev_norms, s->stream);
-    wait[a] = 1;
+    if (n_vcycles) n_vcycles[a] = 0;
+    status[a] = host_step_start(B->inst[a], dt[a], t0);
+    running[a] = status[a] == QNSCH_OK;
   }
-  // outer cycles: each instance queues its next cycle as soon as its norms
-  // arrive, so instances of different sizes do not wait for one another
-  for (int pending = 1; pending;) {
-    pending = 0;
+  for (int left = 1; left;) {
+    left = 0;
     for (int a = 0; a < n; ++a) {
-      if (!wait[a]) continue;
-      qnsch_s* s = B->inst[a];
-      int got = poll_norms(s, nrm);
-      if (got == 0) {
-        pending = 1;
-        continue;
-      }
-      wait[a] = 0;
-      if (got < 0) {
-        status[a] = got;
-        live[a] = 0;
-        continue;
-      }
-      const double prev = res[a];
-      res[a] = maxfam(nrm);
-      grew[a] = cyc[a] > 0 && res[a] > prev ? grew[a] + 1 : 0;
-      if (s->diverge > 0 && grew[a] >= s->diverge) continue;
-      if (res[a] == res[a] && res[a] > s->tol && s->time_limit > 0.0 &&
-          seconds_since(t0) > s->time_limit) {
-        late[a] = 1;
-        continue;
-      }
-      if (res[a] == res[a] && res[a] > s->tol && cyc[a] < s->maxcyc) {
-        launch_cycle(s);
-        cudaEventRecord(s->ev_norms, s->stream);
-        ++cyc[a];
-        wait[a] = 1;
-        pending = 1;
+      if (!running[a]) continue;
+      int st = 0, k = 0;
+      double r = 0.0;
+      if (host_step_advance(B->inst[a], &st, &k, &r)) {
+        running[a] = 0;
+        status[a] = st;
+        if (n_vcycles) n_vcycles[a] = k;
+      } else {
+        left = 1;
       }
     }
-  }
-  for (int a = 0; a < n; ++a) {
-    qnsch_s* s = B->inst[a];
-    if (n_vcycles) n_vcycles[a] = cyc[a];
-    if (!live[a]) {
-      s->pending = 0;
-      continue;
-    }
-    if (!(res[a] == res[a])) {
-      status[a] = QNSCH_ENAN;
-      s->pending = 0;
-    } else if (late[a]) {
-      status[a] = QNSCH_ETIMEOUT;
-      s->pending = 0;
-    } else if (res[a] > s->tol) {
-      status[a] = QNSCH_ENOTCONV;
-      s->pending = 0;
-    } else {
-      launch_commit(s);
-    }
-  }
-  for (int a = 0; a < n; ++a) {
-    qnsch_s* s = B->inst[a];
-    if (live[a] && s->pending) status[a] = finish_commit(s);
   }
   return QNSCH_OK;
 }

@@ -334,7 +334,7 @@ class Solver:
 
     # ---- measurement ----
     # kinds of timed launches (qnsch_profile's bits)
-    PROFILE_KINDS = ("vanka_finest", "vanka_levels", "coarse_vcycle", "ch")
+    PROFILE_KINDS = ("vanka_finest", "vanka_levels", "coarse_vcycle", "ch", "wave")
 
     def profile(self, enable=True):
         """enable: True (the finest-level Vanka launches), False, or a bit mask

@@ -7,8 +7,10 @@ creates the simulation (fields and multigrid hierarchy resident on the GPU,
 off the stepping loop's critical path).  The stepping loop advances every
 resident simulation independently: each one's next time step is queued
 (qnsch_step_launch, one graph on its own stream) the moment its previous step
-is seen finished (qnsch_step_poll), so the simulations' kernels overlap on the
-device and a small simulation never waits for a large one.  A simulation
+is seen finished, and each of its outer cycles as soon as the previous
+cycle's norms are seen (qnsch_step_poll drives the host-driven loop), so the
+simulations' kernels overlap on the device and a small simulation never waits
+for a large one.  A simulation
 leaves when it has done its steps (or failed), which frees its memory for the
 next request.  Each simulation goes through exactly the arithmetic it would
 alone, so its result does not depend on the mix.  Per step the server records
@@ -137,8 +139,12 @@ class Server:
                         state["slots"] += 1
                     waiting.popleft()
                     P = r.problem
+                    # host-driven steps: many resident simulations' whole-step
+                    # graphs (device_loop) measured slower than their cycles
+                    # queued from the host as each one's norms arrive
                     sv = self.qn.Solver(**P.create_kwargs(), tol=P.tol, precision=self.precision,
-                                        coupled=self.coupled, **self.options(P))
+                                        coupled=self.coupled, device_loop=0,
+                                        **self.options(P))
                     sv.set_fields(P.fields())
                     r.admitted = clock()
                     with cond:

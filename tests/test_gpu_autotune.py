@@ -30,9 +30,11 @@ def test_tuned_options_keep_the_step(qn):
         out.append((n, s.get_fields()))
         s.close()
     assert out[0][0] == out[1][0]
+    # two mixed-precision paths, each within the mixed bar of the FP64 solution
+    from mixed_tol import MIXED_TOL
     for k in out[0][1]:
         a, b = out[0][1][k], out[1][1][k]
-        assert np.max(np.abs(a - b)) <= 1e-7 * max(np.max(np.abs(a)), 1e-30), k
+        assert np.max(np.abs(a - b)) <= 2 * MIXED_TOL[k] * max(np.max(np.abs(a)), 1e-30), k
 
 
 def test_server_applies_the_table(qn):

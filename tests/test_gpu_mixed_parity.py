@@ -1,0 +1,103 @@
+"""Mixed precision against the FP64 oracle, field by field, at the bars of
+tests/mixed_tol.py (about ten times the measured differences), with V-cycle
+counts within one of the oracle's and mass conserved: small cases with either
+smoother, the batch's own option set (coupled block, one lane per block in
+the per-level launches, levels up to 2048 cells fused) on two draws of the
+64-drop batch workload at density ratios 83 and 57, the 256x512 rising drop
+with the per-colour smoother launches and with the banded wavefront, and a
+512^2 drop with the coupled block.  Also the FP64 path at full size over
+several steps: three steps of the 256x512 drop from the state the GPU reaches
+after five, against the oracle from that same state."""
+import numpy as np
+import pytest
+
+from mixed_tol import MIXED_MASS_TOL, check_mixed
+from oracle.ref import RefSolver
+from paper_1703_06606_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+BATCH_OPTS = {"precision": 1, "coupled": 1, "fuse_cells32": 2048, "vanka_team_max32": 0}
+
+
+@pytest.fixture(scope="module")
+def qn():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1703_06606_gb300 import qnsch
+    return qnsch
+
+
+def _drop512():
+    P = W.rising_drop_256x512()
+    P.m1, P.m2 = 512, 512
+    P.init_args = dict(x0=0.5, y0=0.3, R=0.2)
+    return P
+
+
+def _cases():
+    ds = W.batch_drops(n=64)
+    return [
+        ("small_walls", W.small_case(32, 48, False), 1, {"precision": 1}, {}),
+        ("small_periodic", W.small_case(32, 48, True), 1, {"precision": 1}, {}),
+        ("small_walls_coupled", W.small_case(32, 48, False), 2, {"precision": 1, "coupled": 1},
+         {"coupled": 1}),
+        ("batch_draw_1_ratio83", ds[1], 2, BATCH_OPTS, {"coupled": 1}),
+        ("batch_draw_9_ratio57", ds[9], 2, BATCH_OPTS, {"coupled": 1}),
+        ("drop_256x512", W.rising_drop_256x512(), 2, {"precision": 1}, {}),
+        ("drop_256x512_wavefront", W.rising_drop_256x512(), 2,
+         {"precision": 1, "wave_cells32": 1}, {}),
+        ("drop_256x512_coupled", W.rising_drop_256x512(), 2, {"precision": 1, "coupled": 1},
+         {"coupled": 1}),
+        ("drop_512_coupled", _drop512(), 1, {"precision": 1, "coupled": 1}, {"coupled": 1}),
+    ]
+
+
+CASES = _cases()
+
+
+@pytest.mark.parametrize("name,P,steps,gopts,ropts", CASES, ids=[c[0] for c in CASES])
+def test_mixed_step_against_the_oracle(qn, name, P, steps, gopts, ropts):
+    if name.startswith("batch_draw"):
+        ratio = max(P.rho1, P.rho2) / min(P.rho1, P.rho2)
+        assert ratio >= 50.0, ratio
+    g = qn.Solver(**P.create_kwargs(), tol=P.tol, **gopts)
+    r = RefSolver(**P.create_kwargs(), tol=P.tol, **ropts)
+    f = P.fields()
+    g.set_fields(f)
+    r.set_fields(f)
+    m0 = r.mass()
+    for _ in range(steps):
+        ng, resg = g.step(P.dt)
+        nr, resr = r.step(P.dt)
+        assert resg <= P.tol and resr <= P.tol
+        assert abs(ng - nr) <= 1, (ng, nr)
+    check_mixed(g.get_fields(), r.get_fields())
+    mg = g.mass()
+    assert abs(mg[0] - m0[0]) <= MIXED_MASS_TOL * m0[0]
+    assert abs(mg[1] - m0[1]) <= MIXED_MASS_TOL * m0[1]
+
+
+def test_fp64_full_size_three_steps_after_five(qn):
+    """The benchmark workload past its start: the GPU's state after five FP64
+    steps, then three more steps on the GPU and in the oracle from that state:
+    equal V-cycle counts and every field within 1e-10."""
+    P = W.rising_drop_256x512()
+    g = qn.Solver(**P.create_kwargs(), tol=P.tol)
+    g.set_fields(P.fields())
+    for _ in range(5):
+        g.step(P.dt)
+    start = g.get_fields()
+    r = RefSolver(**P.create_kwargs(), tol=P.tol)
+    r.set_fields(start)
+    for _ in range(3):
+        ng, resg = g.step(P.dt)
+        nr, resr = r.step(P.dt)
+        assert ng == nr and resg <= P.tol and resr <= P.tol
+    fg, fr = g.get_fields(), r.get_fields()
+    for k in fg:
+        e = np.max(np.abs(fg[k] - fr[k])) / max(np.max(np.abs(fr[k])), 1e-300)
+        assert e <= 1e-10, (k, e)
+    mg, mr = g.mass(), r.mass()
+    assert abs(mg[0] - mr[0]) <= 1e-13 * mr[0] and abs(mg[1] - mr[1]) <= 1e-13 * mr[1]

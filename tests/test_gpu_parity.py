@@ -6,13 +6,15 @@ V-cycle, and full time steps; conservation and energy checks on the GPU
 results; edge cases (smallest grids, ragged sizes, periodic seams) and error
 statuses.  FP64 tolerances: per-kernel results to 1e-11 relative (rounding
 order and FMA contraction differ between the two builds), converged steps to
-1e-10 relative in max norm per field.
+1e-10 relative in max norm per field.  Mixed precision: the per-field bars of
+tests/mixed_tol.py.
 """
 import math
 
 import numpy as np
 import pytest
 
+from mixed_tol import check_mixed
 from oracle.ref import RefSolver
 from paper_1703_06606_gb300 import workloads as W
 
@@ -277,10 +279,8 @@ def test_mixed_precision_step_meets_fp64_tolerance(qn, case):
     m0 = g.mass()
     ng, resg = g.step(P.dt)
     nr, resr = r.step(P.dt)
-    assert resg <= P.tol and ng <= nr + 6
-    fg, fr = g.get_fields(), r.get_fields()
-    errs = {k: relerr(fg[k], fr[k]) for k in fg}
-    assert max(errs.values()) <= 1e-7, errs
+    assert resg <= P.tol and abs(ng - nr) <= 1
+    check_mixed(g.get_fields(), r.get_fields())
     m1 = g.mass()
     assert abs(m1[0] - m0[0]) <= 1e-12 * m0[0] and abs(m1[1] - m0[1]) <= 1e-12 * m0[1]
 
@@ -354,9 +354,8 @@ def test_coupled_mixed_step_512(qn):
     r.set_fields(f)
     ng, resg = g.step(P.dt)
     nr, resr = r.step(P.dt)
-    assert resg <= P.tol and ng <= nr + 4
-    errs = {k: relerr(v, r.get_fields()[k]) for k, v in g.get_fields().items()}
-    assert max(errs.values()) <= 1e-7, errs
+    assert resg <= P.tol and abs(ng - nr) <= 1
+    check_mixed(g.get_fields(), r.get_fields())
 
 
 def _rt(m1, m2):
