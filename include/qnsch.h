@@ -159,7 +159,8 @@ int qnsch_footprint(const qnsch_grid* grid, int precision, size_t* bytes);
    coupled colours) run band by band (bands of wave_rows >= 4 rows) in a
    skewed order, each band's pass waiting only for the previous pass on the
    band and its two neighbours, so a band stays in L2 across its passes.  The
-   results are bit-identical to the per-colour launches.  Its waits are
+   results are the per-colour launches' up to rounding (the same arithmetic on
+   the same values).  Its waits are
    bounded by wave_wait_cycles SM clock cycles (integer >= 0); a wait that runs
    out ends the step with QNSCH_ETIMEOUT, uncommitted.  wave_stall (0 or 1) is
    a test hook for that path: with 1, one wait of every wavefront launch waits

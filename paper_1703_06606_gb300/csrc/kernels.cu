@@ -2066,9 +2066,11 @@ __global__ void __launch_bounds__(NT) k_coarse_vcycle(Prm<T> P, CoarseLevels<T> 
 // block takes a ticket, waits until each neighbouring band has finished pass
 // k - 1 (per-band counters of finished passes), runs the pass's visits on its
 // band and publishes the band's new count.  Each visit sees exactly the
-// values it sees when every pass is a launch over the whole level, so the
-// results are the same; what changes is that a band's arrays stay in L2
-// across its passes instead of every colour launch streaming the whole level.
+// values it sees when every pass is a launch over the whole level and runs the
+// same device code, so the results are those of the per-colour launches up to
+// the compiler's contraction of multiply-adds, which may differ between the
+// two kernels; what changes is that a band's arrays stay in L2 across its
+// passes instead of every colour launch streaming the whole level.
 // A ticket's dependencies hold earlier tickets, taken by blocks that are
 // running or done, so the wavefront progresses whatever the number of
 // resident blocks.  Waits are bounded: past `budget` SM cycles a wait sets
