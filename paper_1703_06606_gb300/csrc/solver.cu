@@ -520,13 +520,15 @@ int prof_open(qnsch_s* s, int kind, double visits) {
   }
   s->ev_kind[pair] = kind;
   s->ev_visits[pair] = visits;
-  cudaEventRecord(s->ev[s->ev_used], s->stream);
+  // an external record: inside a stream capture a plain record only orders the
+  // captured work and is not replayed as an event record node
+  cudaEventRecordWithFlags(s->ev[s->ev_used], s->stream, cudaEventRecordExternal);
   return s->ev_used;
 }
 
 void prof_close(qnsch_s* s, int q) {
   if (q < 0) return;
-  cudaEventRecord(s->ev[q + 1], s->stream);
+  cudaEventRecordWithFlags(s->ev[q + 1], s->stream, cudaEventRecordExternal);
   s->ev_used = q + 2;
 }
 
