@@ -502,6 +502,17 @@ long long colour_cells(int m1, int m2, int kcol, int c8, int colour) {
   return n;
 }
 
+// record a timing event on s->stream; inside a stream capture as an external
+// record (a plain record there only orders the captured work and is not
+// replayed as an event record node)
+void prof_record(qnsch_s* s, cudaEvent_t e) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s->stream, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+    cudaEventRecordWithFlags(e, s->stream, cudaEventRecordExternal);
+  else
+    cudaEventRecord(e, s->stream);
+}
+
 // open an event pair of `kind` around the launch queued next (-1: not timed)
 int prof_open(qnsch_s* s, int kind, double visits) {
   if (!((s->prof >> kind) & 1) || s->ev_used + 2 > MAX_PROF_EVENTS) return -1;
@@ -520,15 +531,13 @@ int prof_open(qnsch_s* s, int kind, double visits) {
   }
   s->ev_kind[pair] = kind;
   s->ev_visits[pair] = visits;
-  // an external record: inside a stream capture a plain record only orders the
-  // captured work and is not replayed as an event record node
-  cudaEventRecordWithFlags(s->ev[s->ev_used], s->stream, cudaEventRecordExternal);
+  prof_record(s, s->ev[s->ev_used]);
   return s->ev_used;
 }
 
 void prof_close(qnsch_s* s, int q) {
   if (q < 0) return;
-  cudaEventRecordWithFlags(s->ev[q + 1], s->stream, cudaEventRecordExternal);
+  prof_record(s, s->ev[q + 1]);
   s->ev_used = q + 2;
 }
 

@@ -112,7 +112,8 @@ class Server:
         waiting = collections.deque(sorted(requests, key=lambda r: r.arrival))
         ready = collections.deque()  # admitted (request, solver, footprint)
         cond = threading.Condition()
-        state = {"used": 0, "slots": 0, "admitting": True, "error": None, "max_wait": 0}
+        state = {"used": 0, "slots": 0, "admitting": True, "error": None, "max_wait": 0,
+                 "max_used": 0}
         t0 = time.perf_counter()
         clock = lambda: time.perf_counter() - t0  # noqa: E731
 
@@ -137,6 +138,7 @@ class Server:
                             cond.wait()
                         state["used"] += fp
                         state["slots"] += 1
+                        state["max_used"] = max(state["max_used"], state["used"])
                     waiting.popleft()
                     P = r.problem
                     # host-driven steps: many resident simulations' whole-step
@@ -221,6 +223,7 @@ class Server:
             raise state["error"]
         self.max_resident = max_res
         self.max_backlog = state["max_wait"]
+        self.max_used_bytes = state["max_used"]
         self.wall = clock()
         return requests, fields
 

@@ -97,6 +97,7 @@ def test_admission_in_order_under_budget_and_slots():
     reqs, fields = srv.run(reqs, keep_fields=True)
     assert [s.name for s in be.created] == ["r%d" % k for k in range(8)]  # FIFO
     assert be.max_live_bytes <= 3 * 1024 + 512 and be.max_live <= 3
+    assert srv.max_used_bytes <= 3 * 1024 + 512
     assert be.live == 0 and be.live_bytes == 0  # every solver closed
     for r in reqs:
         assert r.status == 0 and r.done_steps == r.steps
