@@ -3,8 +3,10 @@
 The kernels' launch shapes are chosen per level by thresholds (include/qnsch.h):
 how many cells per colour a level may have for its Vanka, coupled or CH blocks
 to run with four lanes per block (vanka_team_max, ch_team_max and their FP32
-counterparts), and from which size the coarse levels run as one single-block
-V-cycle (fuse_cells, fuse_cells32).  The best values depend on the grid, the
+counterparts), from which size the coarse levels run as one single-block
+V-cycle (fuse_cells, fuse_cells32), and from which size the error-equation
+levels smooth as one banded wavefront launch and with what band height, its
+tile shape (wave_cells32, wave_rows).  The best values depend on the grid, the
 precision and the smoother, and on how busy the GPU is.  This module picks
 them by measurement: coordinate descent over the thresholds of the workload's
 precision, timing whole time steps from the same initial state, and keeps the
@@ -32,6 +34,10 @@ CANDIDATES = {
     "vanka_team_max32": [65536, 0, 8192, 131072, 1 << 30],
     "ch_team_max32": [0, 4096],
     "fuse_cells32": [512, 128, 2048],
+    # the banded wavefront on the error-equation levels: from which level size
+    # (0: never) and with how many rows per band (its tile height)
+    "wave_cells32": [0, 1 << 20, 1 << 16],
+    "wave_rows": [8, 4, 16, 32],
 }
 # a candidate's steps are cut off at this multiple of the best time per step
 CUTOFF = 20.0
@@ -39,8 +45,8 @@ CUTOFF = 20.0
 # 2 FP64 error form: its error levels use the FP64 thresholds)
 KNOBS = {
     0: ["vanka_team_max", "ch_team_max", "fuse_cells"],
-    1: ["vanka_team_max32", "ch_team_max32", "fuse_cells32"],
-    2: ["vanka_team_max32", "ch_team_max32", "fuse_cells"],
+    1: ["vanka_team_max32", "ch_team_max32", "fuse_cells32", "wave_cells32", "wave_rows"],
+    2: ["vanka_team_max32", "ch_team_max32", "fuse_cells", "wave_cells32", "wave_rows"],
 }
 
 

@@ -44,7 +44,8 @@ def test_coordinate_descent_finds_the_separable_optimum():
     P = W.small_case(32, 32, False)
     best, t, hist = autotune.tune(P, precision=1, coupled=1, steps=3, warmup=1,
                                   solver_cls=make_solver(clock, cost, calls), clock=clock)
-    assert best == best_of
+    assert {k: best[k] for k in best_of} == best_of
+    assert all(best[k] == autotune.CANDIDATES[k][0] for k in best if k not in best_of)
     assert t == pytest.approx(1.0)
     assert all(c["precision"] == 1 and c["coupled"] == 1 and c["scheme"] == 0 for c in calls)
     # every distinct option set is measured once
