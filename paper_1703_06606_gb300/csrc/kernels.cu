@@ -299,7 +299,7 @@ template <typename T, class Form>
 __device__ __forceinline__ void ch_cell(const Prm<T>& P, const Lv<T>& L, int i, int j) {
   T J[2][2], R[2];
   ch_system<T, Form>(P, L, i, j, J, R);
-  T idet = qdiv(T(1), J[0][0] * J[1][1] - J[0][1] * J[1][0]);
+  T idet = qrcp(J[0][0] * J[1][1] - J[0][1] * J[1][0]);
   T dc = (J[1][1] * R[0] - J[0][1] * R[1]) * idet;
   T dm = (J[0][0] * R[1] - J[1][0] * R[0]) * idet;
   int k = L.at(i, j);
@@ -462,7 +462,7 @@ __device__ __forceinline__ void ch_team(const Prm<T>& P, const Lv<T>& L, int i, 
   const int q = threadIdx.x & 3;
   const bool open = q == 0 ? (L.px || i > 1) : q == 1 ? (L.px || i < L.m1) : q == 2 ? j > 1 : j < L.m2;
   ChRows<T> R = ch_team_rows<T, Form>(P, L, i, j, q, open);
-  T idet = qdiv(T(1), R.J11 * R.J22 - R.J12 * R.J21);
+  T idet = qrcp(R.J11 * R.J22 - R.J12 * R.J21);
   T dc = (R.J22 * R.Rc - R.J12 * R.Rm) * idet;
   T dm = (R.J11 * R.Rm - R.J21 * R.Rc) * idet;
   if (ok && q == 0) {
@@ -690,7 +690,7 @@ __device__ __forceinline__ void solve_vanka(const T (&A)[5][5], T (&b)[5], const
     T B11 = a1 ? A[p1][p1] - v3 : A[p1][p1];
     T B01 = (a0 && a1) ? A[p0][p1] + v3 : A[p0][p1];
     T B10 = (a0 && a1) ? A[p1][p0] + v3 : A[p1][p0];
-    T idet = qdiv(T(1), B00 * B11 - B01 * B10);
+    T idet = qrcp(B00 * B11 - B01 * B10);
     y[p0] = (B11 * b[p0] - B01 * b[p1]) * idet;
     y[p1] = (B00 * b[p1] - B10 * b[p0]) * idet;
     // z = B^-1 w with w_p0 = a0 ? 1 : 0, w_p1 = a1 ? -1 : 0
@@ -702,9 +702,9 @@ __device__ __forceinline__ void solve_vanka(const T (&A)[5][5], T (&b)[5], const
   // inactive entries of y and z are 0 (identity rows, b = 0, w = 0)
   T sdot = (z[0] - z[1]) + (z[2] - z[3]);
   T tdot = (y[0] - y[1]) + (y[2] - y[3]);
-  T g = qdiv(T(1), T(1) + v3 * sdot);
+  T g = qrcp(T(1) + v3 * sdot);
   T pr = T(0);
-  if constexpr (NP == 5) pr = qdiv(b[4] + ih * tdot * g, A[4][4] + ih * a * sdot * g);
+  if constexpr (NP == 5) pr = (b[4] + ih * tdot * g) * qrcp(A[4][4] + ih * a * sdot * g);
   T f = g * (v3 * tdot + a * pr);
 #pragma unroll
   for (int q = 0; q < 4; ++q) b[q] = y[q] - z[q] * f;
@@ -747,13 +747,13 @@ __device__ __forceinline__ void solve_coupled7(const T (&A)[7][7], T (&b)[7], co
     B11[blk] = a1 ? A[2 + p1][2 + p1] - v3 : A[2 + p1][2 + p1];
     B01[blk] = (a0 && a1) ? A[2 + p0][2 + p1] + v3 : A[2 + p0][2 + p1];
     B10[blk] = (a0 && a1) ? A[2 + p1][2 + p0] + v3 : A[2 + p1][2 + p0];
-    idet[blk] = qdiv(T(1), B00[blk] * B11[blk] - B01[blk] * B10[blk]);
+    idet[blk] = qrcp(B00[blk] * B11[blk] - B01[blk] * B10[blk]);
     z[p0] = ((a0 ? B11[blk] : T(0)) + (a1 ? B01[blk] : T(0))) * idet[blk];
     z[p1] = -((a1 ? B00[blk] : T(0)) + (a0 ? B10[blk] : T(0))) * idet[blk];
   }
   const T sdot = (z[0] - z[1]) + (z[2] - z[3]);
-  const T g = qdiv(T(1), T(1) + v3 * sdot);
-  const T iden = qdiv(T(1), A[6][6] + ih * a * sdot * g);
+  const T g = qrcp(T(1) + v3 * sdot);
+  const T iden = qrcp(A[6][6] + ih * a * sdot * g);
   // x = A_NS^-1 r for a right-hand side r over (u_W, u_E, v_S, v_N, p)
   auto apply = [&](const T (&r)[5], T (&x)[5]) {
     T y[4];
@@ -788,7 +788,7 @@ __device__ __forceinline__ void solve_coupled7(const T (&A)[7][7], T (&b)[7], co
     rhs0 -= A[0][2 + m] * X0[m];
   }
   const T S10 = A[1][0], S11 = A[1][1], rhs1 = b[1];
-  T id2 = qdiv(T(1), S00 * S11 - S01 * S10);
+  T id2 = qrcp(S00 * S11 - S01 * S10);
   T dc = (S11 * rhs0 - S01 * rhs1) * id2;
   T dm = (S00 * rhs1 - S10 * rhs0) * id2;
   b[0] = dc;
@@ -1667,14 +1667,14 @@ struct TeamSolve {
     B11 = ap1 ? D1 - v3 : T(1);
     B01 = (ap0 && ap1) ? T(0.5) * S * ih - vc * P.iRe * L.ih2 : T(0);
     B10 = (ap0 && ap1) ? -T(0.5) * S * ih - vc * P.iRe * L.ih2 : T(0);
-    idet = qdiv(T(1), B00 * B11 - B01 * B10);
+    idet = qrcp(B00 * B11 - B01 * B10);
     T zn = odd ? ((ap1 ? B00 : T(0)) + (ap0 ? B10 : T(0))) : ((ap0 ? B11 : T(0)) + (ap1 ? B01 : T(0)));
     z = (odd ? -zn : zn) * idet;
     T sdot = odd ? -z : z;
     sdot += __shfl_xor_sync(FULL, sdot, 1);
     sdot += __shfl_xor_sync(FULL, sdot, 2);
-    g = qdiv(T(1), T(1) + v3 * sdot);
-    iden = with_p ? qdiv(T(1), A44 + ih * a * sdot * g) : T(0);
+    g = qrcp(T(1) + v3 * sdot);
+    iden = with_p ? qrcp(A44 + ih * a * sdot * g) : T(0);
   }
   __device__ __forceinline__ T apply(T rq, T r4, T& pr) const {
     const unsigned FULL = 0xffffffffu;
@@ -1801,7 +1801,7 @@ __device__ __forceinline__ void coupled_team(const Prm<T>& P, const Lv<T>& L, in
   T S00 = J11 - (team_sum<T>(gm * x1) + diffc * p1);
   T S01 = J12 - (team_sum<T>(gm * x2) + diffc * p2);
   T rhs0 = Rc - (team_sum<T>(gm * x0) + diffc * p0);
-  T id2 = qdiv(T(1), S00 * J22 - S01 * J21);
+  T id2 = qrcp(S00 * J22 - S01 * J21);
   T dc = (J22 * rhs0 - S01 * Rm) * id2;
   T dm = (S00 * Rm - J21 * rhs0) * id2;
   T x = x0 - x1 * dc - x2 * dm;

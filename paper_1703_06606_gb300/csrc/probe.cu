@@ -42,9 +42,16 @@
 //     stages, in microseconds.  threads in {32, 64, ..., 1024}, nb in
 //     [1, SM count], K in [0, 4096], stages in [1, 4096]; a barrier wait that
 //     runs out of time gives -6 (QNSCH_ETIMEOUT).
+//
+//   int qnsch_rcp_check(int n, const double* x, double* y_fast, double* y_ieee);
+//     host arrays of n doubles: y_fast = the FP64 reciprocal the block solves
+//     use (qrcp of qnsch_dev.cuh: Newton-Raphson from rcp.approx.ftz.f64),
+//     y_ieee = 1.0 / x (IEEE division), both computed on the device.
+//     n in [1, 2^24]; allocates and frees 3 n doubles; synchronises.
 #include <cuda_runtime.h>
 
 #include "qnsch.h"
+#include "qnsch_dev.cuh"
 
 namespace {
 
@@ -322,7 +329,40 @@ int run_stage_probe(int mode, int threads, int nb, int K, int S, double* us) {
   return rc;
 }
 
+__global__ void k_rcp_check(const double* x, double* yf, double* yi, int n) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  yf[t] = qn::qrcp(x[t]);
+  yi[t] = 1.0 / x[t];
+}
+
 }  // namespace
+
+extern "C" int qnsch_rcp_check(int n, const double* x, double* y_fast, double* y_ieee) {
+  if (n < 1 || n > (1 << 24) || !x || !y_fast || !y_ieee) return QNSCH_EINVAL;
+  int nd = 0;
+  if (cudaGetDeviceCount(&nd) != cudaSuccess || nd == 0) {
+    cudaGetLastError();
+    return QNSCH_ENODEV;
+  }
+  double* d = nullptr;
+  const size_t bytes = (size_t)n * sizeof(double);
+  if (cudaMalloc(&d, 3 * bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return QNSCH_ENOMEM;
+  }
+  int rc = QNSCH_OK;
+  if (cudaMemcpy(d, x, bytes, cudaMemcpyHostToDevice) != cudaSuccess) rc = QNSCH_ECUDA;
+  if (rc == QNSCH_OK) {
+    k_rcp_check<<<(n + 255) / 256, 256>>>(d, d + n, d + 2 * (size_t)n, n);
+    if (cudaMemcpy(y_fast, d + n, bytes, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(y_ieee, d + 2 * (size_t)n, bytes, cudaMemcpyDeviceToHost) != cudaSuccess)
+      rc = QNSCH_ECUDA;
+  }
+  if (rc != QNSCH_OK) cudaGetLastError();
+  cudaFree(d);
+  return rc;
+}
 
 extern "C" int qnsch_stage_probe(int mode, int threads, int nb, int K, int stages,
                                  double* us_per_stage) {

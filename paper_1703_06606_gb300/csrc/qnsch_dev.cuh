@@ -76,6 +76,22 @@ template <typename T> __device__ __forceinline__ T rho_of(const Prm<T>& P, T c) 
 // ulp, whose rounding the FP64 defect correction absorbs; IEEE division in FP64
 template <typename T> __device__ __forceinline__ T qdiv(T a, T b) { return a / b; }
 template <> __device__ __forceinline__ float qdiv(float a, float b) { return __fdividef(a, b); }
+// 1/x for the pivots of the local block solves.  FP32: the fast division, as
+// qdiv.  FP64: the Newton-Raphson iteration r <- r + r (1 - x r) for the zero
+// of 1/r - x, which squares the relative error of r at every step, started
+// from the hardware's approximate reciprocal (rcp.approx.ftz.f64); after two
+// steps the result is within a few units in the last place of 1/x (tested
+// against IEEE division).  Normal-range x only: the pivots are determinants
+// and diagonal sums of the local systems, far from the subnormal range.
+template <typename T> __device__ __forceinline__ T qrcp(T x) { return qdiv(T(1), x); }
+template <> __device__ __forceinline__ double qrcp(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
 template <> __device__ __forceinline__ float rho_of(const Prm<float>& P, float c) {
   return qdiv(1.0f, P.ia * c + P.ib);
 }

@@ -24,6 +24,7 @@ def lib():
         L.qnsch_fma_probe.argtypes = [i, i, i, p]
         L.qnsch_fp64_issue_probe.argtypes = [i, i, i, i, p]
         L.qnsch_stage_probe.argtypes = [i, i, i, i, i, p]
+        L.qnsch_rcp_check.argtypes = [i, p, p, p]
         _lib = L
     return _lib
 
@@ -60,6 +61,19 @@ def stage_probe(mode, threads=128, nb=152, K=0, stages=200):
     _check(lib().qnsch_stage_probe(int(mode), int(threads), int(nb), int(K), int(stages),
                                    ctypes.byref(t)), "qnsch_stage_probe")
     return t.value
+
+
+def rcp_check(x):
+    """qnsch_rcp_check: (the block solves' FP64 reciprocal of x, IEEE 1/x),
+    both computed on the device, for a float64 numpy array x."""
+    import numpy as np
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    yf, yi = np.empty_like(x), np.empty_like(x)
+    _check(lib().qnsch_rcp_check(int(x.size), x.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                 yf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                 yi.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+           "qnsch_rcp_check")
+    return yf, yi
 
 
 def fp64_peak_tflops():

@@ -39,3 +39,22 @@ def test_stage_probe_both_forms_run():
         chain = probe.stage_probe(mode, 128, 8, 64, 50)
         assert math.isfinite(empty) and 0.0 < empty < 100.0, (mode, empty)
         assert chain > empty, (mode, chain, empty)
+
+
+def test_block_solve_reciprocal_is_within_two_ulp_of_ieee_division():
+    """The FP64 reciprocal of the local block solves (Newton-Raphson from the
+    hardware's approximate reciprocal) against IEEE 1/x on the device, over
+    magnitudes from 1e-200 to 1e200 of both signs: at most 2 units in the last
+    place apart, and exact on powers of two."""
+    import numpy as np
+    from paper_1703_06606_gb300 import probe
+    rng = np.random.default_rng(1703066)
+    x = np.exp(rng.uniform(np.log(1e-200), np.log(1e200), 200000))
+    x *= np.where(rng.random(x.size) < 0.5, -1.0, 1.0)
+    x = np.concatenate([x, 2.0 ** np.arange(-60, 61), [1.0, 3.0, 7.0, 0.1]])
+    yf, yi = probe.rcp_check(x)
+    ulp = np.abs(yf - yi) / np.spacing(np.abs(yi))
+    assert np.all(np.isfinite(yf)) and ulp.max() <= 2.0, ulp.max()
+    p2 = 2.0 ** np.arange(-60, 61)
+    yf2, _ = probe.rcp_check(p2)
+    assert np.array_equal(yf2, 1.0 / p2)
