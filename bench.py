@@ -328,9 +328,7 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- kernel timing by kind on the same workload, right after the timed
     # region: CUDA events around every launch of each kind inside the replayed
-    # cycle graphs (event records cannot sit inside the device-side loop's
-    # conditional body, so these steps drive their cycles from the host; the
-    # kernels and their launch shapes are the same)
+    # cycle graphs (the same kernels and launch shapes as the timed steps)
     kinds = prof_kinds(s, P, stream, flush, nsteps=max(2, min(args.steps, 5)))
     fp64_peak = probe.fp64_peak_tflops()
 
@@ -339,10 +337,12 @@ def run_ours(args, rank, world, local_rank):
     # coupled 7x7 smoother
     variants = {}
     if not args.no_variants:
-        for name, prec, coup, sch in (("mixed", 1, 0, 0), ("fp64_coupled", 0, 1, 0),
-                                      ("mixed_coupled", 1, 1, 0), ("projection_fp64", 0, 0, 1)):
+        for name, prec, coup, sch, extra in (
+                ("mixed", 1, 0, 0, {}), ("fp64_coupled", 0, 1, 0, {}),
+                ("mixed_coupled", 1, 1, 0, {}), ("projection_fp64", 0, 0, 1, {}),
+                ("fp64_device_loop", 0, 0, 0, {"device_loop": 1})):
             sv = qnsch.Solver(**P.create_kwargs(), tol=P.tol, stream=stream, precision=prec,
-                              coupled=coup, scheme=sch)
+                              coupled=coup, scheme=sch, **extra)
             sv.set_fields_device(dev_fields)
             for _ in range(args.warmup):
                 sv.step(P.dt)
@@ -367,6 +367,7 @@ def run_ours(args, rank, world, local_rank):
                 "vcycles_per_step": float(np.mean(vcyc)), "tol": P.tol,
                 "precision": ("FP32 FAS cycles on the error equation; FP64 residual, defect "
                               "correction, gauge, mass, energy") if prec else "FP64",
+                "options": extra,
                 "smoother": "coupled 7x7 block, 5 colours" if coup else
                             ("projection method (Sec. 6.2): CH 2x2 red-black, intermediate-"
                              "velocity Vanka 4x4 (5 colours), pressure Gauss-Seidel red-black"

@@ -29,12 +29,11 @@
  * the stream set by qnsch_set_stream; without one, on a private stream of the
  * handle that the device-array calls order after the caller's earlier work on
  * the legacy default stream.  Every call returns only after its work has
- * completed, unless stated.  qnsch_step runs the whole step as one CUDA
- * graph whose outer-cycle loop and convergence test run on the device
- * (option "device_loop", default 1); qnsch_vcycle, profiling and
- * device_loop = 0 capture each outer V-cycle as a graph instead, with the
- * host reading the norms between cycles (option "graphs", default 1).  Graphs
- * are recaptured when dt or an option changes.
+ * completed, unless stated.  Each outer V-cycle is captured once as a CUDA
+ * graph and replayed, the host reading the norms between cycles (option
+ * "graphs", default 1); with option "device_loop" = 1, qnsch_step instead runs
+ * the whole step as one CUDA graph whose outer-cycle loop and convergence test
+ * run on the device.  Graphs are recaptured when dt or an option changes.
  *
  * Every call returns an int status: 0 on success, a negative QNSCH_E* code on
  * failure.  On failure no output is written and, unless stated, the handle is
@@ -136,7 +135,7 @@ int qnsch_footprint(const qnsch_grid* grid, int precision, size_t* bytes);
    "eps_mob": Cn, "precision": 0, "graphs": 1, "fuse_cells": 128,
    "fuse_cells32": 512, "coupled": 0, "scheme": 0, "vanka_team_max": 8192,
    "ch_team_max": 4096, "vanka_team_max32": 65536, "ch_team_max32": 0,
-   "pdl": 1, "step_time_limit": 0, "diverge_cycles": 0, "device_loop": 1,
+   "pdl": 1, "step_time_limit": 0, "diverge_cycles": 0, "device_loop": 0,
    "wave_cells32": 0, "wave_rows": 8, "wave_wait_cycles": 2147483648,
    "wave_stall": 0.
    Unknown keys give QNSCH_EINVAL, and so do values out of range, which leave
@@ -166,12 +165,15 @@ int qnsch_footprint(const qnsch_grid* grid, int precision, size_t* bytes);
    a test hook for that path: with 1, one wait of every wavefront launch waits
    for a count nothing reaches.
    device_loop: 1 (with graphs = 1 and profiling off) runs qnsch_step and
-   qnsch_batch_step as one graph per step: the initial residual, a
+   qnsch_step_launch as one graph per step: the initial residual, a
    conditional WHILE node around the outer cycle whose last kernel applies the
    stopping rules above (tol, maxcyc, diverge_cycles, step_time_limit) on the
    device, a conditional IF node around the commit, and one copy of the
    outcome to the host; no host round trip per cycle.  Results, cycle counts
-   and statuses are those of the host-driven loop (0).  If the runtime refuses
+   and statuses are those of the host-driven loop (0, the default).  Measured:
+   no faster for one instance (the host keeps ahead of the GPU), slower for
+   many instances stepping at once, and a graph with conditional nodes cannot
+   be profiled kernel by kernel; hence off by default.  If the runtime refuses
    to build that graph the handle sets device_loop to 0 and steps with the
    host-driven loop.
    diverge_cycles (integer >= 0; 0: never): a step whose largest family

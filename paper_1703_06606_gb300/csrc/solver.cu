@@ -225,9 +225,11 @@ struct qnsch_s {
   // the whole step as one graph whose outer-cycle loop runs on the device:
   // the initial residual, a conditional WHILE node around the cycle, a
   // conditional IF node around the commit, one copy of the results to the
-  // host (option "device_loop"; with it off, or while profiling, the host
+  // host (option "device_loop", off by default: it measured no faster for one
+  // instance and slower for many at once, and kernels inside a graph with
+  // conditional nodes cannot be profiled; off, or while profiling, the host
   // reads the norms after every cycle and queues the next one)
-  int device_loop = 1;
+  int device_loop = 0;
   cudaGraphExec_t sexec = nullptr;
   double s_dt = -1.0;
   int s_precision = -1;

@@ -1,9 +1,10 @@
 """The outer-cycle loop on the device: one qnsch_step is one CUDA graph (the
 initial residual, a conditional WHILE node around the outer cycle, a
-conditional IF node around the commit, one copy of the results to the host).
+conditional IF node around the commit, one copy of the results to the host),
+option device_loop = 1.
 
-Against the host-driven loop (option device_loop = 0: the host reads the
-norms after every cycle and queues the next), on the same inputs: the same
+Against the host-driven loop (device_loop = 0, the default: the host reads
+the norms after every cycle and queues the next), on the same inputs: the same
 V-cycle counts, bit-identical fields and the same mass, for the FP64 path,
 mixed precision with either smoother, and the projection method.  The
 handle keeps device_loop = 1 after its steps, so the graph was built and ran.
@@ -38,7 +39,7 @@ CASES = [
 
 @pytest.mark.parametrize("name,P,opts", CASES, ids=[c[0] for c in CASES])
 def test_device_loop_equals_host_loop(qn, name, P, opts):
-    dev = qn.Solver(**P.create_kwargs(), tol=P.tol, **opts)
+    dev = qn.Solver(**P.create_kwargs(), tol=P.tol, device_loop=1, **opts)
     host = qn.Solver(**P.create_kwargs(), tol=P.tol, device_loop=0, **opts)
     f = P.fields()
     dev.set_fields(f)
@@ -87,13 +88,14 @@ def test_device_loop_step_that_does_not_converge_is_not_committed(qn):
 
 
 def test_batch_of_device_loops_equals_alone(qn):
-    """The batch queues every member's step graph on its own stream before
-    collecting any: each member's result equals its host-driven step alone."""
+    """Members whose device_loop is on step in a batch through the batch's
+    host-driven state machine: each member's result equals its host-driven
+    step alone."""
     probs = [W.small_case(32, 32, True), W.small_case(64, 48, False, rho_ratio=10.0),
              W.capillary_64()]
     batch, alone = [], []
     for P in probs:
-        b = qn.Solver(**P.create_kwargs(), tol=P.tol, precision=1, coupled=1)
+        b = qn.Solver(**P.create_kwargs(), tol=P.tol, precision=1, coupled=1, device_loop=1)
         a = qn.Solver(**P.create_kwargs(), tol=P.tol, precision=1, coupled=1, device_loop=0)
         b.set_fields(P.fields())
         a.set_fields(P.fields())
@@ -111,13 +113,16 @@ def test_batch_of_device_loops_equals_alone(qn):
         assert all(np.array_equal(fa[k], fb[k]) for k in fa)
 
 
-def test_async_step_equals_step(qn):
+@pytest.mark.parametrize("device_loop", [0, 1])
+def test_async_step_equals_step(qn, device_loop):
     """qnsch_step_launch + qnsch_step_poll give what qnsch_step gives: the same
-    cycles, residual, status and bit-identical fields; the handle refuses a
+    cycles, residual, status and bit-identical fields, with the host-driven
+    loop advanced by the polls and with the step graph; the handle refuses a
     second launch or a plain step while one is in flight, and a poll without
     a launch."""
     P = W.small_case(48, 64, False, rho_ratio=10.0)
-    a = qn.Solver(**P.create_kwargs(), tol=P.tol, precision=1, coupled=1)
+    a = qn.Solver(**P.create_kwargs(), tol=P.tol, precision=1, coupled=1,
+                  device_loop=device_loop)
     b = qn.Solver(**P.create_kwargs(), tol=P.tol, precision=1, coupled=1)
     a.set_fields(P.fields())
     b.set_fields(P.fields())
