@@ -386,6 +386,12 @@ typedef struct qnsch_batch_s qnsch_batch_t;
 int qnsch_batch_create(int n, qnsch_t* const* insts, qnsch_batch_t** out);
 int qnsch_batch_step(qnsch_batch_t* b, const double* dt, int* status, int* n_vcycles);
 int qnsch_batch_size(const qnsch_batch_t* b);
+/* Batch options: "max_inflight" (integer >= 0; 0, the default: all): at most
+   this many members step at once; the others start, in member order, as
+   running members finish their steps, so fewer instances share the L2 and
+   the SMs at a time.  Results do not change.  Unknown keys and values out of
+   range give QNSCH_EINVAL. */
+int qnsch_batch_set_option(qnsch_batch_t* b, const char* key, double value);
 int qnsch_batch_destroy(qnsch_batch_t* b);
 
 /* Mass reduction that allocates nothing (the paper has no counterpart: this is

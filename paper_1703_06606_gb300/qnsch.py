@@ -86,6 +86,7 @@ def lib():
         L.qnsch_batch_create.argtypes = [i, ctypes.POINTER(_VP), ctypes.POINTER(_VP)]
         L.qnsch_batch_step.argtypes = [_VP, p, ctypes.POINTER(i), ctypes.POINTER(i)]
         L.qnsch_batch_size.argtypes = [_VP]
+        L.qnsch_batch_set_option.argtypes = [_VP, ctypes.c_char_p, d]
         L.qnsch_batch_destroy.argtypes = [_VP]
         L.qnsch_footprint.argtypes = [ctypes.POINTER(_Grid), i, ctypes.POINTER(ctypes.c_size_t)]
         _lib = L
@@ -404,13 +405,20 @@ class Batch:
     """qnsch_batch_*: step several Solver instances together (their kernels run
     concurrently on the GPU); each instance keeps its own tolerance and result."""
 
-    def __init__(self, solvers):
+    def __init__(self, solvers, max_inflight=0):
         self.solvers = list(solvers)
         arr = (_VP * len(self.solvers))(*[sv._h.value for sv in self.solvers])
         h = _VP()
         _check(lib().qnsch_batch_create(len(self.solvers), arr, ctypes.byref(h)),
                "qnsch_batch_create")
         self._h = h
+        if max_inflight:
+            self.set_option("max_inflight", max_inflight)
+
+    def set_option(self, key, value):
+        """qnsch_batch_set_option ("max_inflight": members stepping at once, 0 = all)."""
+        _check(lib().qnsch_batch_set_option(self._h, key.encode(), float(value)),
+               "qnsch_batch_set_option " + key)
 
     def step(self, dt):
         n = len(self.solvers)

@@ -70,3 +70,30 @@ def test_batch_failure_is_isolated(qn):
     ref.set_fields(probs[2].fields())
     ref.step(probs[2].dt)
     assert np.array_equal(ref.get_fields()["c"], sol[2].get_fields()["c"])
+
+
+@pytest.mark.parametrize("max_inflight", [1, 2])
+def test_batch_with_a_window_equals_alone(qn, max_inflight):
+    """max_inflight: at most that many members step at once, the rest start as
+    they finish; each member's result is still the one it has alone."""
+    probs = mix(with_drops=False)
+    alone, batch = [], []
+    for P in probs:
+        kw = dict(P.create_kwargs(), tol=P.tol, precision=1, coupled=1)
+        a, b = qn.Solver(**kw), qn.Solver(**kw)
+        a.set_fields(P.fields())
+        b.set_fields(P.fields())
+        alone.append(a)
+        batch.append(b)
+    B = qn.Batch(batch, max_inflight=max_inflight)
+    st, cyc = B.step([P.dt for P in probs])
+    assert all(x == 0 for x in st), st
+    for a, b, P, n in zip(alone, batch, probs, cyc):
+        na, _ = a.step(P.dt)
+        assert na == n
+        fa, fb = a.get_fields(), b.get_fields()
+        assert all(np.array_equal(fa[k], fb[k]) for k in fa)
+    with pytest.raises(qn.QnschError):
+        B.set_option("max_inflight", -1)
+    with pytest.raises(qn.QnschError):
+        B.set_option("no_such_option", 1)
