@@ -29,6 +29,8 @@ import time
 # candidate values per option; the first is the library default
 CANDIDATES = {
     "vanka_team_max": [8192, 2048, 32768, 0],
+    # eight lanes per FP64 Vanka block up to this many cells per colour (0: never)
+    "vanka_team8_max": [0, 2048, 512],
     "ch_team_max": [4096, 0, 16384],
     "fuse_cells": [128, 32, 512, 4096],
     "vanka_team_max32": [65536, 0, 8192, 131072, 1 << 30],
@@ -44,7 +46,7 @@ CUTOFF = 20.0
 # the options that shape the launches of each precision (0 FP64, 1 mixed,
 # 2 FP64 error form: its error levels use the FP64 thresholds)
 KNOBS = {
-    0: ["vanka_team_max", "ch_team_max", "fuse_cells"],
+    0: ["vanka_team_max", "vanka_team8_max", "ch_team_max", "fuse_cells"],
     1: ["vanka_team_max32", "ch_team_max32", "fuse_cells32", "wave_cells32", "wave_rows"],
     2: ["vanka_team_max32", "ch_team_max32", "fuse_cells", "wave_cells32", "wave_rows"],
 }

@@ -30,7 +30,8 @@ PARAMS = ("m1", "m2", "Lx", "periodic_x", "levels", "rho1", "rho2", "eta1", "eta
 OPTIONS = ("scheme", "precision", "coupled", "nu1", "nu2", "nu_coarse", "maxcyc", "tol",
            "omega_vanka", "M", "eta_st", "eps_mob", "graphs", "fuse_cells", "fuse_cells32",
            "vanka_team_max", "ch_team_max", "vanka_team_max32", "ch_team_max32",
-           "step_time_limit", "diverge_cycles", "device_loop", "wave_cells32", "wave_rows")
+           "step_time_limit", "diverge_cycles", "device_loop", "wave_cells32", "wave_rows",
+           "vanka_team8_max")
 
 
 def field_shapes(m1, m2):

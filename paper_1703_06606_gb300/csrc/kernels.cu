@@ -1733,6 +1733,80 @@ __device__ __forceinline__ void vanka_team(const Prm<T>& P, const Lv<T>& L, int 
   if (q == 0) store_cell(L, L.p, i, j, L.p[k] - omega * pr);
 }
 
+// One half of mom_residual for a lane pair of an eight-lane team: half 0 the
+// time term, the convection, gravity and -f; half 1 the pressure gradient,
+// the surface tension and the viscous terms.  The two halves sum to the
+// momentum row's N - f (up to the order of the additions).  FullForm only.
+template <typename T>
+__device__ __forceinline__ T mom_residual_half(const Prm<T>& P, const Lv<T>& L, const MomRow<T>& R,
+                                               int k, T rl, T rr, int half) {
+  const int s = R.s, t = R.t;
+  const T *a = R.a, *b = R.b;
+  T ae = a[k];
+  T dl = (ae - a[k - s]) * L.ih, dr = (a[k + s] - ae) * L.ih;
+  T Dp = (a[k + t] - ae) * L.ih, Dm = (ae - a[k - t]) * L.ih;
+  if (half == 0) {
+    T Ar = T(0.5) * (rl + rr);
+    T conv = T(0.5) * (R.S[k + s] * dr + R.S[k] * dl + R.Q[k] * Dp + R.Q[k - t] * Dm);
+    T time = ae * R.T1[k] + R.T0[k] + T(0.5) * P.idt * Ar * ae;
+    return time + conv + R.grav * R.Arn[k] - R.f[k];
+  }
+  const T *vis = L.visn, *rn = L.rhon;
+  T dvl = dl + (b[k] - b[k - t]) * L.ih;
+  T dvr = dr + (b[k + s] - b[k + s - t]) * L.ih;
+  T press = (L.p[k + s] - L.p[k]) * L.ih * P.iM;
+  T st = -(rn[k + s] * L.mu[k] + rn[k] * L.mu[k + s]) * R.Tf[k] * P.iM;
+  T vl = vis[k], vr = vis[k + s];
+  T visc = -P.iRe * L.ih * ((vr * dr - vl * dl) + (L.Av[k] * Dp - L.Av[k - t] * Dm) +
+                            (vr * dvr - vl * dvl) * T(1.0 / 3.0));
+  return press + st + visc;
+}
+
+// Vanka block of cell (i,j) by a team of eight lanes (FP64 full iterate): as
+// vanka_team, with each momentum row's residual split over the lane pair
+// (q, q + 4) (mom_residual_half) and summed by one shuffle, so that each lane
+// evaluates half a row.  Both halves of the team then run the same solve;
+// the lower half stores.  For levels whose colour leaves most of the GPU idle:
+// the visit's chain of dependent instructions is what bounds them.
+template <typename T>
+__device__ __forceinline__ void vanka_team8(const Prm<T>& P, const Lv<T>& L, int i, int j, bool ok,
+                                            T omega) {
+  const int W = L.pitch;
+  const int q = threadIdx.x & 3, d = q >> 1, half = (threadIdx.x >> 2) & 1;
+  const T ih = L.ih, ih2 = L.ih2;
+  int k = L.at(i, j);
+  int eW = (L.px && i == 1) ? L.m1 : i - 1;
+  int kW = L.at(eW, j);
+  bool a0 = L.px || i > 1, a1 = L.px || i < L.m1, a2 = j > 1, a3 = j < L.m2;
+  bool mine = q == 0 ? a0 : q == 1 ? a1 : q == 2 ? a2 : a3;
+  int ke = q == 0 ? kW : (q == 2 ? k - W : k);
+  MomRow<T> R = mom_row<T, FullForm>(P, L, d);
+  T rl = L.rhoc[ke], rr = L.rhoc[ke + R.s];
+  T dq = R.Dg[ke] + T(0.5) * P.idt * (T(0.5) * (rl + rr));
+  T bq = mom_residual_half<T>(P, L, R, ke, rl, rr, half);
+  bq += __shfl_xor_sync(0xffffffffu, bq, 4);
+  if (!mine) bq = T(0);
+  const T* mob = L.mobn;
+  const int nq = k + (q == 0 ? -1 : q == 1 ? 1 : q == 2 ? -W : W);
+  T am = mob[nq] + mob[k];
+  T f0 = team_sum<T>((q & 1) ? (d ? L.v[k] : L.u[k]) : -(d ? L.v[k - W] : L.u[k - 1]));
+  T f1 = team_sum<T>(T(0.5) * am * ((L.mu[nq] - L.mu[k]) + P.alpha * (L.p[nq] - L.p[k])));
+  T f2 = team_sum<T>(mine ? am : T(0));
+  T A44 = T(0.5) * P.alpha * P.alpha * P.iPe * f2 * ih2;
+  T b4 = f0 * ih - P.alpha * P.iPe * ih2 * f1 - L.fp[k];
+  TeamSolve<T> ts(P, L, q, dq, d ? a2 : a0, d ? a3 : a1, d ? L.Sy[k] : L.Sx[k], L.visn[k], A44);
+  T pr;
+  T x = ts.apply(bq, b4, pr);
+  if (!ok || half) return;
+  if (mine) {
+    if (q == 0) store_u(L, eW, j, L.u[kW] - omega * x);
+    else if (q == 1) store_u(L, i, j, L.u[k] - omega * x);
+    else if (q == 2) store_v(L, i, j - 1, L.v[k - W] - omega * x);
+    else store_v(L, i, j, L.v[k] - omega * x);
+  }
+  if (q == 0) store_cell(L, L.p, i, j, L.p[k] - omega * pr);
+}
+
 // The projection method's 4x4 intermediate-velocity block (vanka4_cell) by a
 // team of four lanes: lane q builds row q (team_row without pressure, surface
 // tension and gravity) and the team solves the block (TeamSolve without the
@@ -1850,6 +1924,20 @@ __global__ void __launch_bounds__(SNT) k_coupled_team(Prm<T> P, Lv<T> L, int col
   coupled_team<T, Form>(P, L, i, j, ok, omega);
 }
 
+// per-level launch with eight lanes per Vanka block (vanka_team8; FP64 full
+// iterate)
+__global__ void __launch_bounds__(SNT) k_vanka_team8(Prm<double> P, Lv<double> L, int colour,
+                                                     double omega) {
+  pdl_enter();
+  ColourSlots cs = vanka_slots(L, colour);
+  int t = blockIdx.x * SNT + threadIdx.x;
+  if ((t & ~31) >= 8 * cs.n) return;  // warp-uniform
+  int i = 1, j = 1;
+  bool ok = (t >> 3) < cs.n && vanka_slot_cell(L, colour, cs, t >> 3, i, j);
+  if (!ok) i = j = 1;
+  vanka_team8<double>(P, L, i, j, ok, omega);
+}
+
 template <typename T, class Form>
 __global__ void __launch_bounds__(SNT) k_vanka_team(Prm<T> P, Lv<T> L, int colour, T omega) {
   pdl_enter();
@@ -1866,7 +1954,7 @@ __global__ void __launch_bounds__(SNT) k_vanka_team(Prm<T> P, Lv<T> L, int colou
 constexpr int QN_TEAM_MAX_SLOTS = 32;
 
 template <typename T, class Form>
-__device__ void smooth_block(const Prm<T>& P, const Lv<T>& L, T omega, int coupled) {
+__device__ void smooth_block(const Prm<T>& P, const Lv<T>& L, T omega, int coupled, int team8 = 0) {
   const int kcol = L.kcol;
   if constexpr (std::is_same<Form, ProjForm>::value) {
     // projection method (Sec. 7.2): CH red-black, intermediate-velocity blocks
@@ -1986,7 +2074,15 @@ __device__ void smooth_block(const Prm<T>& P, const Lv<T>& L, T omega, int coupl
     // FP64: while the colour fits four warps (one per sub-partition); the
     // latency-bound FP32 error levels: while it fits the block in one pass
     const int team_slots = team_ok ? QN_TEAM_MAX_SLOTS : (int)blockDim.x / 4;
-    if (vteam_ok && cs.n <= team_slots) {
+    if (team_ok && team8 && 8 * cs.n <= (int)blockDim.x) {  // eight lanes per block
+      int t = threadIdx.x;
+      if ((t & ~31) < 8 * cs.n) {  // warp-uniform: the warp holds at least one team
+        int i = 1, j = 1;
+        bool ok = (t >> 3) < cs.n && vanka_slot_cell(L, col, cs, t >> 3, i, j);
+        if (!ok) i = j = 1;
+        if constexpr (team_ok) vanka_team8<double>(P, L, i, j, ok, omega);
+      }
+    } else if (vteam_ok && cs.n <= team_slots) {
       int t = threadIdx.x;
       if ((t & ~31) < 4 * cs.n) {  // warp-uniform: the warp holds at least one team
         int i = 1, j = 1;
@@ -2007,7 +2103,8 @@ __device__ void smooth_block(const Prm<T>& P, const Lv<T>& L, T omega, int coupl
 
 template <typename T, class Form, int NT>
 __global__ void __launch_bounds__(NT) k_coarse_vcycle(Prm<T> P, CoarseLevels<T> C, int nu1, int nu2,
-                                                      int nuc, int kcol, T omega, int coupled) {
+                                                      int nuc, int kcol, T omega, int coupled,
+                                                      int team8) {
   pdl_enter();
   const int n = C.n;
   double dummy[10];
@@ -2029,7 +2126,7 @@ __global__ void __launch_bounds__(NT) k_coarse_vcycle(Prm<T> P, CoarseLevels<T> 
   for (int l = 0; l < n - 1; ++l) {
     const Lv<T>& F = C.L[l];
     const Lv<T>& G = C.L[l + 1];
-    for (int s = 0; s < nu1; ++s) smooth_block<T, Form>(P, F, omega, coupled);
+    for (int s = 0; s < nu1; ++s) smooth_block<T, Form>(P, F, omega, coupled, team8);
     for (int t = threadIdx.x; t < F.m1 * F.m2; t += NT)
       residual_cell<T, 0, Form>(P, F, t % F.m1 + 1, t / F.m1 + 1, dummy);
     __syncthreads();
@@ -2044,7 +2141,7 @@ __global__ void __launch_bounds__(NT) k_coarse_vcycle(Prm<T> P, CoarseLevels<T> 
       residual_cell<T, 1, Form>(P, G, t % G.m1 + 1, t / G.m1 + 1, dummy);
     __syncthreads();
   }
-  for (int s = 0; s < nuc; ++s) smooth_block<T, Form>(P, C.L[n - 1], omega, coupled);
+  for (int s = 0; s < nuc; ++s) smooth_block<T, Form>(P, C.L[n - 1], omega, coupled, team8);
   for (int l = n - 2; l >= 0; --l) {
     const Lv<T>& F = C.L[l];
     const Lv<T>& G = C.L[l + 1];
@@ -2052,7 +2149,7 @@ __global__ void __launch_bounds__(NT) k_coarse_vcycle(Prm<T> P, CoarseLevels<T> 
       prolong_cell(P, F, G, t % F.m1 + 1, t / F.m1 + 1);
     __syncthreads();
     bc_unknowns_block(F);
-    for (int s = 0; s < nu2; ++s) smooth_block<T, Form>(P, F, omega, coupled);
+    for (int s = 0; s < nu2; ++s) smooth_block<T, Form>(P, F, omega, coupled, team8);
   }
 }
 
@@ -2623,9 +2720,16 @@ void launch_ch(const Prm<T>& P, const Lv<T>& L, int colour, cudaStream_t s, int 
 }
 template <typename T, class Form>
 void launch_vanka(const Prm<T>& P, const Lv<T>& L, int colour, T omega, cudaStream_t s,
-                  int team_max) {
+                  int team_max, int team8_max) {
   int n = vanka_slots(L, colour).n;
   if (n <= 0) return;
+  if constexpr (std::is_same<Form, FullForm>::value && sizeof(T) == 8) {
+    if (n <= team8_max) {  // eight lanes per block: half a momentum row per lane
+      qlaunch(&k_vanka_team8, (8 * n + SNT - 1) / SNT, SNT, 0, s, P, L, colour, omega);
+      ++g_launches;
+      return;
+    }
+  }
   if constexpr ((std::is_same<Form, FullForm>::value && sizeof(T) == 8) ||
                 std::is_same<Form, ErrForm>::value) {
     if (n <= team_max) {  // four lanes per block: shorter critical path per visit
@@ -2639,13 +2743,14 @@ void launch_vanka(const Prm<T>& P, const Lv<T>& L, int colour, T omega, cudaStre
 }
 template <typename T, class Form>
 void launch_coarse_vcycle(const Prm<T>& P, const Lv<T>* levels, int n, int nu1, int nu2, int nuc,
-                          int kcol, T omega, int coupled, cudaStream_t s) {
+                          int kcol, T omega, int coupled, cudaStream_t s, int team8) {
   CoarseLevels<T> C;
   C.n = n;
   C.base = std::is_same<Form, ErrForm>::value;
   for (int l = 0; l < n; ++l) C.L[l] = levels[l];
   constexpr int NT = sizeof(T) == 8 ? 256 : 512;
-  qlaunch(&k_coarse_vcycle<T, Form, NT>, 1, NT, 0, s, P, C, nu1, nu2, nuc, kcol, omega, coupled);
+  qlaunch(&k_coarse_vcycle<T, Form, NT>, 1, NT, 0, s, P, C, nu1, nu2, nuc, kcol, omega, coupled,
+          team8);
   ++g_launches;
 }
 
@@ -2894,12 +2999,12 @@ int partial_rows_needed(int m1, int m2) {
 
 #define QN_INSTANTIATE_FORM(T, F)                                                                \
   template void launch_coarse_vcycle<T, F>(const Prm<T>&, const Lv<T>*, int, int, int, int, int,  \
-                                           T, int, cudaStream_t);                                \
+                                           T, int, cudaStream_t, int);                           \
   template void launch_coupled<T, F>(const Prm<T>&, const Lv<T>&, int, T, cudaStream_t, int);     \
   template void launch_residual<T, F>(const Prm<T>&, const Lv<T>&, double*, cudaStream_t);       \
   template void launch_add_op<T, F>(const Prm<T>&, const Lv<T>&, cudaStream_t);                  \
   template void launch_ch<T, F>(const Prm<T>&, const Lv<T>&, int, cudaStream_t, int);            \
-  template void launch_vanka<T, F>(const Prm<T>&, const Lv<T>&, int, T, cudaStream_t, int);
+  template void launch_vanka<T, F>(const Prm<T>&, const Lv<T>&, int, T, cudaStream_t, int, int);
 
 #define QN_INSTANTIATE(T)                                                                        \
   template void launch_cast_frozen<T>(const Lv<double>&, const Lv<T>&, cudaStream_t);            \
@@ -2937,7 +3042,7 @@ template void launch_wave<double, ErrForm>(const Prm<double>&, const Lv<double>&
 template void launch_residual<double, ProjForm>(const Prm<double>&, const Lv<double>&, double*,
                                                 cudaStream_t);
 template void launch_coarse_vcycle<double, ProjForm>(const Prm<double>&, const Lv<double>*, int, int,
-                                                     int, int, int, double, int, cudaStream_t);
+                                                     int, int, int, double, int, cudaStream_t, int);
 template void launch_add_op<double, ProjForm>(const Prm<double>&, const Lv<double>&, cudaStream_t);
 template void launch_ch<double, ProjForm>(const Prm<double>&, const Lv<double>&, int, cudaStream_t,
                                           int);

@@ -18,10 +18,11 @@ template <typename T, class Form> void launch_add_op(const Prm<T>& P, const Lv<T
 template <typename T, class Form>
 void launch_ch(const Prm<T>& P, const Lv<T>& L, int colour, cudaStream_t s, int team_max = 0);
 // team_max: FP64 full-iterate levels with at most this many cells per colour
-// use four lanes per Vanka block
+// use four lanes per Vanka block; team8_max: FP64 full-iterate levels with at
+// most this many cells per colour use eight (half a momentum row per lane)
 template <typename T, class Form>
 void launch_vanka(const Prm<T>& P, const Lv<T>& L, int colour, T omega, cudaStream_t s,
-                  int team_max = 0);
+                  int team_max = 0, int team8_max = 0);
 // a banded wavefront of smoothing passes on one level (kernels.cu, k_wave):
 // npass passes (per smoothing step: CH red, CH black and the kcol Vanka
 // colours, or the kcol coupled colours), bands of `rows` rows, the same team
@@ -39,9 +40,11 @@ template <typename T, class Form>
 void launch_wave(const Prm<T>& P, const Lv<T>& L, const WavePlan& W, T omega, unsigned* ctr,
                  double* flag, cudaStream_t s);
 // the V-cycle on levels[0..n-1] (levels[0] is its finest) in one thread block
+// (team8: the FP64 full-iterate Vanka blocks use eight lanes where a colour
+// fits the block in one pass)
 template <typename T, class Form>
 void launch_coarse_vcycle(const Prm<T>& P, const Lv<T>* levels, int n, int nu1, int nu2, int nuc,
-                          int kcol, T omega, int coupled, cudaStream_t s);
+                          int kcol, T omega, int coupled, cudaStream_t s, int team8 = 0);
 // one colour of the coupled 7x7 smoother (option "coupled")
 template <typename T, class Form>
 void launch_coupled(const Prm<T>& P, const Lv<T>& L, int colour, T omega, cudaStream_t s,

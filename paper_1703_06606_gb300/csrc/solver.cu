@@ -167,8 +167,11 @@ struct qnsch_s {
   // 0: the primitive method (Sec. 6.1); 1: the projection method (Sec. 6.2)
   int scheme = 0;
   // FP64 levels with at most this many cells per Vanka colour smooth with four
-  // lanes per block in the per-level launches
+  // lanes per block in the per-level launches, and with eight (half a
+  // momentum row per lane) up to team8_max; team8_max > 0 also turns on the
+  // eight-lane blocks of the single-block coarse V-cycle
   int team_max = 8192;
+  int team8_max = 0;
   // the same for the CH smoother's per-level launches (cells per red-black colour)
   int ch_team_max = 4096, ch_team_max32 = 0;
   // the same on the error-equation levels of the defect correction (their
@@ -580,7 +583,8 @@ void smooth(qnsch_s* s, const std::vector<Lv<T>>& Ls, const Prm<T>& P, int l) {
     if (s->coupled) qn::launch_coupled<T, Form>(P, L, c, (T)s->omega, s->stream,
                                                 std::is_same<Form, ErrForm>::value ? s->team_max32 : s->team_max);
     else qn::launch_vanka<T, Form>(P, L, c, (T)s->omega, s->stream,
-                                   std::is_same<Form, ErrForm>::value ? s->team_max32 : s->team_max);
+                                   std::is_same<Form, ErrForm>::value ? s->team_max32 : s->team_max,
+                                   std::is_same<Form, ErrForm>::value ? 0 : s->team8_max);
     prof_close(s, q);
   }
 }
@@ -643,7 +647,8 @@ void vcycle(qnsch_s* s, const std::vector<Lv<T>>& Ls, const Prm<T>& P, int l) {
                 (m == s->nlev - 1 ? coarse_sweeps(s) : s->nu1 + s->nu2);
     int q = prof_open(s, PK_COARSE, visits);
     qn::launch_coarse_vcycle<T, Form>(P, &Ls[l], s->nlev - l, s->nu1, s->nu2, coarse_sweeps(s),
-                                      s->kcol, (T)s->omega, s->coupled, s->stream);
+                                      s->kcol, (T)s->omega, s->coupled, s->stream,
+                                      s->team8_max > 0 ? 1 : 0);
     prof_close(s, q);
     return;
   }
@@ -1449,11 +1454,13 @@ int set_option(qnsch_s* s, const std::string& k, double value) {
     if (!count_of(value, 0, 1e6, &n)) return QNSCH_EINVAL;
     s->diverge = n;
   } else if (k == "fuse_cells" || k == "fuse_cells32" || k == "vanka_team_max" ||
-             k == "ch_team_max" || k == "ch_team_max32" || k == "vanka_team_max32") {
+             k == "ch_team_max" || k == "ch_team_max32" || k == "vanka_team_max32" ||
+             k == "vanka_team8_max") {
     if (!count_of(value, 0, imax, &n)) return QNSCH_EINVAL;
     (k == "fuse_cells" ? s->fuse64 : k == "fuse_cells32" ? s->fuse32
      : k == "vanka_team_max" ? s->team_max : k == "ch_team_max" ? s->ch_team_max
-     : k == "ch_team_max32" ? s->ch_team_max32 : s->team_max32) = n;
+     : k == "ch_team_max32" ? s->ch_team_max32 : k == "vanka_team8_max" ? s->team8_max
+     : s->team_max32) = n;
   } else if (k == "coupled") {
     if (value != 0.0 && s->scheme) return QNSCH_EINVAL;  // a primitive-method smoother
     s->coupled = value != 0.0;
@@ -1514,6 +1521,7 @@ int qnsch_get_option(const qnsch_t* s, const char* key, double* value) {
   else if (k == "ch_team_max") *value = s->ch_team_max;
   else if (k == "ch_team_max32") *value = s->ch_team_max32;
   else if (k == "vanka_team_max32") *value = s->team_max32;
+  else if (k == "vanka_team8_max") *value = s->team8_max;
   else if (k == "pdl") *value = g_pdl_option.load();
   else return QNSCH_EINVAL;
   return QNSCH_OK;
