@@ -498,16 +498,34 @@ def run_ours(args, rank, world, local_rank):
             st, _ = B.step(dts)
             bad += sum(1 for x in st if x != 0)
         torch.cuda.synchronize()
-        bms, bcyc = [], []
+        bms, bcyc, spans = [], [], []
         for k in range(args.steps):
             flush.fill_(float(k))
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             st, cy = B.step(dts)
             bms.append((time.perf_counter() - t0) * 1e3)
+            spans.append(B.step_times())
             bad += sum(1 for x in st if x != 0)
             bcyc.append(float(np.mean(cy)))
         bcells = sum(Pb.cells for Pb in probs)
+        # where the batch step goes: each member's span on its stream inside the
+        # batch, and each member's step alone (events on its own stream, one
+        # step after the timed ones, the others idle)
+        spans = np.concatenate(spans)
+        alone = []
+        for sb, Pb in zip(sols, probs):
+            ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            ea.record(stream)
+            sb.set_stream(stream)
+            sb.step(Pb.dt)
+            eb.record(stream)
+            torch.cuda.synchronize()
+            alone.append(ea.elapsed_time(eb))
+        by_grid = {}
+        for Pb, ms in zip(probs, alone):
+            by_grid.setdefault("%dx%d" % (Pb.m1, Pb.m2), []).append(ms)
         btot = replicas.slowest(sum(bms) / 1e3, dev)
         batched = {"value": world * bcells * args.steps / btot, "unit": UNIT,
                    "instances": len(probs), "cells": bcells,
@@ -518,7 +536,18 @@ def run_ours(args, rank, world, local_rank):
                    "precision": "FP32 FAS cycles on the error equation; FP64 residual, "
                                 "defect correction, gauge, mass, energy",
                    "smoother": "coupled 7x7 block", "tol": 1e-9, "options": bopts,
-                   "timing": "host wall clock per batch step (it synchronises every stream)"}
+                   "timing": "host wall clock per batch step (it synchronises every stream)",
+                   "breakdown": {
+                       "member_span_ms": {"p50": float(np.percentile(spans, 50)),
+                                          "p99": float(np.percentile(spans, 99)),
+                                          "max": float(np.max(spans))},
+                       "sum_of_steps_alone_ms": float(np.sum(alone)),
+                       "steps_alone_ms_by_grid": {g: {"instances": len(v),
+                                                      "mean": float(np.mean(v))}
+                                                  for g, v in sorted(by_grid.items())},
+                       "what": "member_span: from an event before a member's step to one "
+                               "after it on the member's stream, inside the batch; alone: "
+                               "each member's step by itself after the timed steps"}}
         B.close()
         for sb in sols:
             sb.close()

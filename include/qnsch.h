@@ -399,6 +399,12 @@ int qnsch_batch_size(const qnsch_batch_t* b);
    the SMs at a time.  Results do not change.  Unknown keys and values out of
    range give QNSCH_EINVAL. */
 int qnsch_batch_set_option(qnsch_batch_t* b, const char* key, double value);
+/* Each member's last qnsch_batch_step on the GPU: ms[a] receives the device
+   time from a CUDA event recorded on member a's stream before its step began
+   to one recorded after it ended (the member's span inside the batch,
+   including the time it shared the GPU with the others); -1 for a member
+   not timed.  ms holds qnsch_batch_size(b) doubles. */
+int qnsch_batch_step_times(const qnsch_batch_t* b, double* ms);
 int qnsch_batch_destroy(qnsch_batch_t* b);
 
 /* Mass reduction that allocates nothing (the paper has no counterpart: this is

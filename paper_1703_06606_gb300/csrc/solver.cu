@@ -1918,6 +1918,9 @@ struct qnsch_batch_s {
   // at most this many members step at once (0: all); the others start, in
   // member order, as running ones finish their steps
   int max_inflight = 0;
+  // each member's last batch step on its stream: from the event before its
+  // start to the event after its end (ms; -1 if not timed)
+  std::vector<double> step_ms;
 };
 
 int qnsch_batch_create(int n, qnsch_t* const* insts, qnsch_batch_t** out) {
@@ -1961,10 +1964,12 @@ int qnsch_batch_step(qnsch_batch_t* B, const double* dt, int* status, int* n_vcy
   const int cap = B->max_inflight > 0 ? std::min(B->max_inflight, n) : n;
   std::vector<char> running(n, 0);
   int next = 0, inflight = 0;
+  B->step_ms.assign(n, -1.0);
   auto start_more = [&]() {
     while (inflight < cap && next < n) {
       const int a = next++;
       if (n_vcycles) n_vcycles[a] = 0;
+      cudaEventRecord(B->inst[a]->ev_s0, B->inst[a]->stream);
       status[a] = host_step_start(B->inst[a], dt[a], t0);
       running[a] = status[a] == QNSCH_OK;
       inflight += running[a];
@@ -1981,10 +1986,26 @@ int qnsch_batch_step(qnsch_batch_t* B, const double* dt, int* status, int* n_vcy
         --inflight;
         status[a] = st;
         if (n_vcycles) n_vcycles[a] = k;
+        cudaEventRecord(B->inst[a]->ev_s1, B->inst[a]->stream);
         start_more();
       }
     }
   }
+  for (int a = 0; a < n; ++a) {  // every member's work has ended: the events are done
+    float ms = 0.f;
+    if (cudaEventSynchronize(B->inst[a]->ev_s1) == cudaSuccess &&
+        cudaEventElapsedTime(&ms, B->inst[a]->ev_s0, B->inst[a]->ev_s1) == cudaSuccess)
+      B->step_ms[a] = ms;
+    else
+      cudaGetLastError();
+  }
+  return QNSCH_OK;
+}
+
+int qnsch_batch_step_times(const qnsch_batch_t* B, double* ms) {
+  if (!B || !ms) return QNSCH_EINVAL;
+  for (size_t a = 0; a < B->inst.size(); ++a)
+    ms[a] = a < B->step_ms.size() ? B->step_ms[a] : -1.0;
   return QNSCH_OK;
 }
 

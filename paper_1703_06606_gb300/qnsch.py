@@ -87,6 +87,7 @@ def lib():
         L.qnsch_batch_step.argtypes = [_VP, p, ctypes.POINTER(i), ctypes.POINTER(i)]
         L.qnsch_batch_size.argtypes = [_VP]
         L.qnsch_batch_set_option.argtypes = [_VP, ctypes.c_char_p, d]
+        L.qnsch_batch_step_times.argtypes = [_VP, p]
         L.qnsch_batch_destroy.argtypes = [_VP]
         L.qnsch_footprint.argtypes = [ctypes.POINTER(_Grid), i, ctypes.POINTER(ctypes.c_size_t)]
         _lib = L
@@ -414,6 +415,13 @@ class Batch:
         self._h = h
         if max_inflight:
             self.set_option("max_inflight", max_inflight)
+
+    def step_times(self):
+        """qnsch_batch_step_times: each member's device span (ms) in the last step."""
+        out = np.zeros(len(self.solvers))
+        _check(lib().qnsch_batch_step_times(self._h, out.ctypes.data_as(_D)),
+               "qnsch_batch_step_times")
+        return out
 
     def set_option(self, key, value):
         """qnsch_batch_set_option ("max_inflight": members stepping at once, 0 = all)."""

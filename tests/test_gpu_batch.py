@@ -93,6 +93,8 @@ def test_batch_with_a_window_equals_alone(qn, max_inflight):
         assert na == n
         fa, fb = a.get_fields(), b.get_fields()
         assert all(np.array_equal(fa[k], fb[k]) for k in fa)
+    t = B.step_times()
+    assert t.shape == (len(probs),) and np.all(t > 0.0)
     with pytest.raises(qn.QnschError):
         B.set_option("max_inflight", -1)
     with pytest.raises(qn.QnschError):
