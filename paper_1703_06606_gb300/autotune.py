@@ -6,7 +6,9 @@ to run with four lanes per block (vanka_team_max, ch_team_max and their FP32
 counterparts), from which size the coarse levels run as one single-block
 V-cycle (fuse_cells, fuse_cells32), and from which size the error-equation
 levels smooth as one banded wavefront launch and with what band height, its
-tile shape (wave_cells32, wave_rows).  The best values depend on the grid, the
+tile shape (wave_cells32, wave_rows).  It also searches the smoothing counts
+(nu1, nu2, nu_coarse), which trade the cost of a V-cycle against the number
+of V-cycles a step needs.  The best values depend on the grid, the
 precision and the smoother, and on how busy the GPU is.  This module picks
 them by measurement: coordinate descent over the thresholds of the workload's
 precision, timing whole time steps from the same initial state, and keeps the
@@ -16,8 +18,9 @@ result in a JSON table keyed by GPU, grid, precision and smoother.
         --coupled 1 --table tuned.json
 
 serve.Server(tuned_table=...) applies a table's entries to the instances it
-admits.  Options never change the fixed point of a step, only the order in
-which per-lane sums are added and which kernels run.
+admits.  Options never change the fixed point of a step (the discrete
+solution at the tolerance), only the order in which per-lane sums are added,
+which kernels run and, for the smoothing counts, the path of the iteration.
 """
 from __future__ import annotations
 
@@ -40,15 +43,26 @@ CANDIDATES = {
     # (0: never) and with how many rows per band (its tile height)
     "wave_cells32": [0, 1 << 20, 1 << 16],
     "wave_rows": [8, 4, 16, 32],
+    # smoothing steps before and after the coarse-grid correction, and on the
+    # coarsest grid (more steps: fewer, dearer V-cycles)
+    "nu1": [2, 3, 1],
+    "nu2": [2, 3, 1],
+    "nu_coarse": [4, 2, 8],
 }
 # a candidate's steps are cut off at this multiple of the best time per step
 CUTOFF = 20.0
+# a candidate replaces the incumbent only if it is at least this much faster
+# (relative), so that timing noise does not move a knob
+MIN_GAIN = 0.005
 # the options that shape the launches of each precision (0 FP64, 1 mixed,
 # 2 FP64 error form: its error levels use the FP64 thresholds)
 KNOBS = {
-    0: ["vanka_team_max", "vanka_team8_max", "ch_team_max", "fuse_cells"],
-    1: ["vanka_team_max32", "ch_team_max32", "fuse_cells32", "wave_cells32", "wave_rows"],
-    2: ["vanka_team_max32", "ch_team_max32", "fuse_cells", "wave_cells32", "wave_rows"],
+    0: ["vanka_team_max", "vanka_team8_max", "ch_team_max", "fuse_cells", "nu1", "nu2",
+        "nu_coarse"],
+    1: ["vanka_team_max32", "ch_team_max32", "fuse_cells32", "wave_cells32", "wave_rows", "nu1",
+        "nu2", "nu_coarse"],
+    2: ["vanka_team_max32", "ch_team_max32", "fuse_cells", "wave_cells32", "wave_rows", "nu1",
+        "nu2", "nu_coarse"],
 }
 
 
@@ -120,7 +134,7 @@ def tune(P, precision=0, coupled=0, scheme=0, steps=4, warmup=2, solver_cls=None
                     continue
                 trial = dict(best, **{k: v})
                 t = measure(trial)
-                if t is not None and (best_t is None or t < best_t):
+                if t is not None and (best_t is None or t < best_t * (1.0 - MIN_GAIN)):
                     best, best_t, changed = trial, t, True
         if not changed:
             break
