@@ -671,10 +671,19 @@ VANKA_FP64_FLOPS_PER_VISIT = 391.0
 # them executed (add, mul = 1, fma = 2) on the FP64 kernels
 CH_FP64_FLOPS_PER_VISIT = 241.0
 RESIDUAL_FP64_FLOPS_PER_CELL = 327.0
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of a timed kind, from one
-# ncu capture of the same kernel build (profiles/ file named beside it); a kind
-# without a capture of the current build reports traffic null
-TRAFFIC_BYTES = {}
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of a timed kind (average
+# over its launches), from one ncu capture of the same kernel build (the
+# profiles/ file named beside it; cold-cache, serialised); a kind without a
+# capture of the current build reports traffic null.  Drop these entries when
+# the kernels change.
+TRAFFIC_BYTES = {
+    "vanka_levels": (2.51e6, "profiles/dram_per_kernel_fp64_step_rising_drop_256x512.md"),
+    "vanka_finest": (27.57e6, "profiles/dram_per_kernel_fp64_step_rising_drop_256x512.md"),
+    "coarse_vcycle": (0.37e6, "profiles/dram_per_kernel_fp64_step_rising_drop_256x512.md"),
+    "ch": (15.66e6, "profiles/dram_per_kernel_fp64_step_rising_drop_256x512.md"),
+    "vanka_finest_fp32": (431.99e6, "profiles/dram_per_kernel_rayleigh_taylor_1024x4096.md"),
+    "ch_fp32": (299.10e6, "profiles/dram_per_kernel_rayleigh_taylor_1024x4096.md"),
+}
 # words per cell a sweep moves at one pass over the arrays it needs (Sec. 7.1
 # smoothers; read c^n, u^n, v^n, c, mu, u, v, p and the three right-hand sides,
 # write u, v, p for the Vanka block; c^n, u, v, c, mu, p and two right-hand
