@@ -6,7 +6,8 @@ to run with four lanes per block (vanka_team_max, ch_team_max and their FP32
 counterparts), from which size the coarse levels run as one single-block
 V-cycle (fuse_cells, fuse_cells32), and from which size the error-equation
 levels smooth as one banded wavefront launch and with what band height, its
-tile shape (wave_cells32, wave_rows).  It also searches the smoothing counts
+tile shape (wave_cells32, wave_rows), or in the skewed-chunk schedule and with
+what chunk height (skew_cells32, skew_rows).  It also searches the smoothing counts
 (nu1, nu2, nu_coarse), which trade the cost of a V-cycle against the number
 of V-cycles a step needs.  The best values depend on the grid, the
 precision and the smoother, and on how busy the GPU is.  This module picks
@@ -43,6 +44,10 @@ CANDIDATES = {
     # (0: never) and with how many rows per band (its tile height)
     "wave_cells32": [0, 1 << 20, 1 << 16],
     "wave_rows": [8, 4, 16, 32],
+    # the skewed-chunk schedule on the error-equation levels: from which level
+    # size (0: never) and with chunks of how many rows
+    "skew_cells32": [0, 1 << 20, 1 << 17],
+    "skew_rows": [32, 64, 16],
     # smoothing steps before and after the coarse-grid correction, and on the
     # coarsest grid (more steps: fewer, dearer V-cycles)
     "nu1": [2, 3, 1],
@@ -59,10 +64,10 @@ MIN_GAIN = 0.005
 KNOBS = {
     0: ["vanka_team_max", "vanka_team8_max", "ch_team_max", "fuse_cells", "nu1", "nu2",
         "nu_coarse"],
-    1: ["vanka_team_max32", "ch_team_max32", "fuse_cells32", "wave_cells32", "wave_rows", "nu1",
-        "nu2", "nu_coarse"],
-    2: ["vanka_team_max32", "ch_team_max32", "fuse_cells", "wave_cells32", "wave_rows", "nu1",
-        "nu2", "nu_coarse"],
+    1: ["vanka_team_max32", "ch_team_max32", "fuse_cells32", "wave_cells32", "wave_rows",
+        "skew_cells32", "skew_rows", "nu1", "nu2", "nu_coarse"],
+    2: ["vanka_team_max32", "ch_team_max32", "fuse_cells", "wave_cells32", "wave_rows",
+        "skew_cells32", "skew_rows", "nu1", "nu2", "nu_coarse"],
 }
 
 

@@ -2287,6 +2287,49 @@ __global__ void __launch_bounds__(WAVE_NT) k_wave(Prm<T> P, Lv<T> L, WavePlan W,
 }
 
 // --------------------------------------------------------------------------
+// skewed-chunk schedule of the smoothing passes on a large error-equation
+// level.  A colour launch over the whole level touches every sector of every
+// array its visits read (the visits of one colour are spread over all rows
+// and columns), so a level larger than L2 streams from DRAM once per pass.
+// Here the passes of a smoothing block run together over chunks of H rows:
+// launch d runs pass p on the rows [1 + (d - p) H - 2p, 1 + (d - p + 1) H - 2p)
+// (clipped to the level), so each pass trails the one before it by a chunk
+// and two rows, and the rows the launch touches stay in L2 between the
+// passes.  A visit at row j reads rows j - 2 .. j + 1 and writes rows j - 1
+// and j (and the ghost row beside row 1 or row m2), so within one launch no
+// task reads or writes what another task writes, every row a task reads
+// already holds the results of the earlier passes (they ran in earlier
+// launches) and none holds a later pass's: each visit sees the values it sees
+// when every pass is a launch over the whole level, with the same device code.
+// No block waits for another; stream order orders the launches.
+// --------------------------------------------------------------------------
+template <typename T, class Form, bool COUPLED>
+__global__ void __launch_bounds__(SNT) k_skew(Prm<T> P, Lv<T> L, SkewTasks S, T omega) {
+  pdl_enter();
+  const int b = blockIdx.x;
+  int k = 0;
+  while (k + 1 < S.n && S.boff[k + 1] <= b) ++k;
+  const int t = S.t_lo[k] + (b - S.boff[k]) * SNT + threadIdx.x;
+  if (t >= S.t_hi[k]) return;
+  const int q = S.q[k];
+  if constexpr (!COUPLED) {
+    if (q < 2) {  // CH colour q, slots as in k_ch
+      const int mpr = (L.m1 + 1) / 2;
+      const int j = t / mpr + 1;
+      const int i = (((q - j) & 1) ? 1 : 2) + 2 * (t % mpr);
+      if (i <= L.m1) ch_cell<T, Form>(P, L, i, j);
+      return;
+    }
+  }
+  const int col = COUPLED ? q : q - 2;
+  ColourSlots cs = vanka_slots(L, col);
+  int i, j;
+  if (!vanka_slot_cell(L, col, cs, t, i, j)) return;
+  if constexpr (COUPLED) coupled_cell<T, Form>(P, L, i, j, omega);
+  else vanka_cell<T, Form>(P, L, i, j, omega);
+}
+
+// --------------------------------------------------------------------------
 // defect correction (mixed precision): FP64 level <-> error-equation level
 // --------------------------------------------------------------------------
 // error-equation frozen data = rounded FP64 frozen data (whole padded arrays)
@@ -2981,6 +3024,59 @@ void launch_wave(const Prm<T>& P, const Lv<T>& L, const WavePlan& W, T omega, un
   ++g_launches;
 }
 
+template <typename T, class Form>
+int launch_skew(const Prm<T>& P, const Lv<T>& L, int nsteps, int coupled, int rows, T omega,
+                cudaStream_t s) {
+  const int per = coupled ? L.kcol : L.kcol + 2;
+  const int H = std::max(rows, 1);
+  const int group = std::max(1, SKEW_MAX_TASKS / per);  // steps per schedule
+  int launches = 0;
+  for (int s0 = 0; s0 < nsteps; s0 += group) {
+    const int npass = std::min(group, nsteps - s0) * per;
+    // the last diagonal on which the last pass still has rows of the level
+    const int D = npass + (L.m2 - 1 + (npass - 1) * SKEW_LAG) / H;
+    for (int d = 0; d < D; ++d) {
+      SkewTasks S;
+      S.n = 0;
+      int nb = 0;
+      for (int p = 0; p < npass; ++p) {
+        const int lo = std::max(1 + (d - p) * H - p * SKEW_LAG, 1);
+        const int hi = std::min(1 + (d - p + 1) * H - p * SKEW_LAG, L.m2 + 1);
+        if (lo >= hi) continue;
+        const int q = p % per;
+        int t_lo, t_hi;
+        if (!coupled && q < 2) {
+          const int mpr = (L.m1 + 1) / 2;
+          t_lo = (lo - 1) * mpr;
+          t_hi = (hi - 1) * mpr;
+        } else {
+          const ColourSlots cs = vanka_slots(L, coupled ? q : q - 2);
+          const int r1 = hi - 1;  // rows lo .. r1
+          if (r1 < cs.j0) continue;
+          const int qlo = lo > cs.j0 ? (lo - cs.j0 + cs.rstep - 1) / cs.rstep : 0;
+          const int qhi = (r1 - cs.j0) / cs.rstep;
+          t_lo = qlo * cs.mpr;
+          t_hi = std::min((qhi + 1) * cs.mpr, cs.n);
+        }
+        if (t_lo >= t_hi) continue;
+        S.q[S.n] = q;
+        S.t_lo[S.n] = t_lo;
+        S.t_hi[S.n] = t_hi;
+        S.boff[S.n] = nb;
+        nb += (t_hi - t_lo + SNT - 1) / SNT;
+        ++S.n;
+      }
+      S.boff[S.n] = nb;
+      if (S.n == 0) continue;
+      if (coupled) qlaunch(&k_skew<T, Form, true>, nb, SNT, 0, s, P, L, S, omega);
+      else qlaunch(&k_skew<T, Form, false>, nb, SNT, 0, s, P, L, S, omega);
+      ++g_launches;
+      ++launches;
+    }
+  }
+  return launches;
+}
+
 void launch_loop_clock(double* ctl, cudaStream_t s) {
   qlaunch(&k_loop_clock, 1, 1, 0, s, ctl);
   ++g_launches;
@@ -3038,6 +3134,10 @@ template void launch_wave<float, ErrForm>(const Prm<float>&, const Lv<float>&, c
                                           float, unsigned*, double*, cudaStream_t);
 template void launch_wave<double, ErrForm>(const Prm<double>&, const Lv<double>&, const WavePlan&,
                                            double, unsigned*, double*, cudaStream_t);
+template int launch_skew<float, ErrForm>(const Prm<float>&, const Lv<float>&, int, int, int, float,
+                                         cudaStream_t);
+template int launch_skew<double, ErrForm>(const Prm<double>&, const Lv<double>&, int, int, int, double,
+                                          cudaStream_t);
 // projection method (FP64, per-level launches)
 template void launch_residual<double, ProjForm>(const Prm<double>&, const Lv<double>&, double*,
                                                 cudaStream_t);

@@ -39,6 +39,24 @@ struct WavePlan {
 template <typename T, class Form>
 void launch_wave(const Prm<T>& P, const Lv<T>& L, const WavePlan& W, T omega, unsigned* ctr,
                  double* flag, cudaStream_t s);
+// the skewed-chunk schedule of nsteps smoothing steps on one error-equation
+// level (kernels.cu, k_skew): the steps' passes (per step: CH red, CH black
+// and the kcol Vanka colours, or the kcol coupled colours) over chunks of
+// `rows` rows, pass p behind pass p - 1 by one chunk and SKEW_LAG rows; one
+// launch per diagonal, stream order the only dependency.  One lane per visit.
+// Returns the number of launches it queued.
+constexpr int SKEW_MAX_TASKS = 32;
+constexpr int SKEW_LAG = 2;
+struct SkewTasks {
+  int n;                         // tasks (pass on a row range) of one launch
+  int q[SKEW_MAX_TASKS];         // pass within its step: CH colour 0/1, then Vanka colours
+  int t_lo[SKEW_MAX_TASKS];      // the task's slots t_lo .. t_hi - 1
+  int t_hi[SKEW_MAX_TASKS];
+  int boff[SKEW_MAX_TASKS + 1];  // first block of each task; boff[n] = blocks
+};
+template <typename T, class Form>
+int launch_skew(const Prm<T>& P, const Lv<T>& L, int nsteps, int coupled, int rows, T omega,
+                cudaStream_t s);
 // the V-cycle on levels[0..n-1] (levels[0] is its finest) in one thread block
 // (team8: the FP64 full-iterate Vanka blocks use eight lanes where a colour
 // fits the block in one pass)

@@ -186,6 +186,10 @@ struct qnsch_s {
   long long wave_budget = 1LL << 31;
   int wave_stall = 0;
   unsigned* wave_ctr = nullptr;  // 1 + bands of level 0 counters
+  // error-equation levels with at least this many cells run nu smoothing steps
+  // in the skewed-chunk schedule (k_skew; 0: never), chunks of skew_rows rows
+  long long skew_cells = 0;
+  int skew_rows = 32;
   // failure detection: a step stops once it has run this many seconds of wall
   // time (0: no limit), or once its residual has grown over this many
   // consecutive outer cycles (0: never)
@@ -263,8 +267,8 @@ struct qnsch_s {
   int ev_used = 0;
   long long prof_launches = 0;
   double prof_ms = 0.0;
-  long long pk_n[5] = {0, 0, 0, 0, 0};
-  double pk_ms[5] = {0, 0, 0, 0, 0}, pk_visits[5] = {0, 0, 0, 0, 0};
+  long long pk_n[6] = {0, 0, 0, 0, 0, 0};
+  double pk_ms[6] = {0, 0, 0, 0, 0, 0}, pk_visits[6] = {0, 0, 0, 0, 0, 0};
   double dt = 0.0;
   double last_diss = 0.0;
 };
@@ -486,7 +490,8 @@ Prm<T> cast_prm(const Prm<double>& P) {
 
 constexpr int MAX_PROF_EVENTS = 8192;
 // kinds of timed launches (qnsch_profile's bit mask)
-enum { PK_VANKA0 = 0, PK_VANKA = 1, PK_COARSE = 2, PK_CH = 3, PK_WAVE = 4, PK_N = 5 };
+enum { PK_VANKA0 = 0, PK_VANKA = 1, PK_COARSE = 2, PK_CH = 3, PK_WAVE = 4, PK_SKEW = 5, PK_N = 6 };
+static_assert(PK_N == sizeof(qnsch_s::pk_n) / sizeof(long long), "one total per profiling kind");
 
 // cells of Vanka colour `colour` on an m1 x m2 level (the colourings of
 // colours_of: (2i + j) mod 8 when c8, else (i + 2j) mod kcol)
@@ -589,12 +594,19 @@ void smooth(qnsch_s* s, const std::vector<Lv<T>>& Ls, const Prm<T>& P, int l) {
   }
 }
 
-// n smoothing steps on level l: one banded wavefront launch on a large enough
-// error-equation level, else n times the per-colour launches of smooth()
+// n smoothing steps on level l: on a large enough error-equation level the
+// skewed-chunk schedule or one banded wavefront launch, else n times the
+// per-colour launches of smooth()
 template <typename T, class Form>
 void smooth_steps(qnsch_s* s, const std::vector<Lv<T>>& Ls, const Prm<T>& P, int l, int n) {
   if constexpr (std::is_same<Form, ErrForm>::value) {
     const Lv<T>& L = Ls[l];
+    if (n > 0 && s->skew_cells > 0 && (long long)L.m1 * L.m2 >= s->skew_cells) {
+      int q = l == 0 ? prof_open(s, PK_SKEW, (double)L.m1 * L.m2 * n) : -1;
+      qn::launch_skew<T, Form>(P, L, n, s->coupled, s->skew_rows, (T)s->omega, s->stream);
+      prof_close(s, q);
+      return;
+    }
     const int rows = std::max(s->wave_rows, WAVE_MIN_ROWS);
     if (n > 0 && s->wave_cells > 0 && (long long)L.m1 * L.m2 >= s->wave_cells &&
         L.m2 >= 2 * rows) {
@@ -1447,6 +1459,12 @@ int set_option(qnsch_s* s, const std::string& k, double value) {
     s->wave_budget = (long long)value;
   } else if (k == "wave_stall") {
     s->wave_stall = value != 0.0;
+  } else if (k == "skew_cells32") {
+    if (!(value >= 0.0 && value <= 9.0e15 && value == std::floor(value))) return QNSCH_EINVAL;
+    s->skew_cells = (long long)value;
+  } else if (k == "skew_rows") {
+    if (!count_of(value, 1, 1 << 20, &n)) return QNSCH_EINVAL;
+    s->skew_rows = n;
   } else if (k == "step_time_limit") {
     if (!(value >= 0.0) || !std::isfinite(value)) return QNSCH_EINVAL;
     s->time_limit = value;
@@ -1511,6 +1529,8 @@ int qnsch_get_option(const qnsch_t* s, const char* key, double* value) {
   else if (k == "wave_rows") *value = s->wave_rows;
   else if (k == "wave_wait_cycles") *value = (double)s->wave_budget;
   else if (k == "wave_stall") *value = s->wave_stall;
+  else if (k == "skew_cells32") *value = (double)s->skew_cells;
+  else if (k == "skew_rows") *value = s->skew_rows;
   else if (k == "step_time_limit") *value = s->time_limit;
   else if (k == "diverge_cycles") *value = s->diverge;
   else if (k == "fuse_cells") *value = s->fuse64;
@@ -1541,7 +1561,7 @@ int qnsch_profile(qnsch_t* s, int enable) {
     cudaStreamSynchronize(s->stream);
     prof_collect(s);
   }
-  if (enable < 0 || enable > 31) return QNSCH_EINVAL;
+  if (enable < 0 || enable >= (1 << PK_N)) return QNSCH_EINVAL;
   s->prof = enable;
   s->prof_launches = 0;
   s->prof_ms = 0.0;

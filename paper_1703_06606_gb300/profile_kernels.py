@@ -2,6 +2,8 @@
 
     python -m paper_1703_06606_gb300.profile_kernels --kernel vanka --m1 1024 --m2 1024 --reps 3
     python -m paper_1703_06606_gb300.profile_kernels --workload rt --kernel step --precision 1
+    python -m paper_1703_06606_gb300.profile_kernels --workload rt --kernel step --precision 1 \
+        --option skew_cells32=1048576 --option skew_rows=64
     python -m paper_1703_06606_gb300.profile_kernels --kernel fmapeak
     python -m paper_1703_06606_gb300.profile_kernels --kernel fp64issue
     python -m paper_1703_06606_gb300.profile_kernels --kernel stage
@@ -41,6 +43,8 @@ def main():
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2])
     ap.add_argument("--coupled", type=int, default=0, choices=[0, 1])
     ap.add_argument("--scheme", type=int, default=0, choices=[0, 1])
+    ap.add_argument("--option", action="append", default=[], metavar="KEY=VALUE",
+                    help="a solver option for the step (repeatable), e.g. skew_cells32=1048576")
     a = ap.parse_args()
     if a.kernel == "fmapeak":
         for fp64 in (True, False):
@@ -72,8 +76,12 @@ def main():
         P = workloads.rising_drop_256x512()
         P.m1, P.m2, P.Lx = a.m1, a.m2, 1.0
         P.init_args = dict(x0=0.5, y0=0.25 * a.m2 / a.m1, R=0.2)
+    opts = {}
+    for kv in a.option:
+        k, v = kv.split("=", 1)
+        opts[k] = float(v)
     s = qnsch.Solver(**P.create_kwargs(), tol=P.tol, precision=a.precision, coupled=a.coupled,
-                     scheme=a.scheme)
+                     scheme=a.scheme, **opts)
     s.set_fields(P.fields())
     if a.kernel == "step":
         for _ in range(a.reps):

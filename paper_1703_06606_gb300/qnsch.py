@@ -336,7 +336,7 @@ class Solver:
 
     # ---- measurement ----
     # kinds of timed launches (qnsch_profile's bits)
-    PROFILE_KINDS = ("vanka_finest", "vanka_levels", "coarse_vcycle", "ch", "wave")
+    PROFILE_KINDS = ("vanka_finest", "vanka_levels", "coarse_vcycle", "ch", "wave", "skew")
 
     def profile(self, enable=True):
         """enable: True (the finest-level Vanka launches), False, or a bit mask
