@@ -481,12 +481,11 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_batch:
         probs = workloads.batch_drops(n=args.batch)
         sols = []
-        # options for throughput: with 64 instances in flight the GPU is full, so
-        # one lane per coupled block in the per-level launches does less work
-        # than the four-lane teams, and larger levels fuse into each
-        # instance's single-block V-cycle (measured 5.2e7 against 4.4e7
-        # cell-updates/s with the single-instance defaults)
-        bopts = {"fuse_cells32": 2048, "vanka_team_max32": 0}
+        # options for throughput (serve.THROUGHPUT_OPTIONS): with 64 instances in
+        # flight the GPU is full, so one lane per coupled block, larger fused
+        # coarse levels and one pre-smoothing step do less work in all
+        from paper_1703_06606_gb300 import serve
+        bopts = dict(serve.THROUGHPUT_OPTIONS)
         for Pb in probs:
             sb = qnsch.Solver(**Pb.create_kwargs(), tol=Pb.tol, precision=1, coupled=1, **bopts)
             sb.set_fields(Pb.fields())
@@ -562,13 +561,14 @@ def run_ours(args, rank, world, local_rank):
         from paper_1703_06606_gb300 import serve
         reqs = serve.poisson_requests(args.serve_requests, rate=50.0, n_min=128, n_max=1024,
                                       steps=args.serve_steps, dt=1e-4)
-        srv = serve.Server(budget_bytes=150e9)
+        srv = serve.Server(budget_bytes=150e9, base_options=serve.THROUGHPUT_OPTIONS)
         reqs, _ = srv.run(reqs, device=local_rank)
         serving = serve.summarize(reqs, srv.wall, srv.max_resident, srv.max_backlog)
         serving.update({"arrivals": "Poisson, 50/s", "grid": "N x N, N log-uniform in "
                         "[128, 1024] (multiple of 64)", "steps_per_request": args.serve_steps,
                         "dt": 1e-4, "budget_bytes": 150e9,
                         "precision": "mixed", "smoother": "coupled 7x7 block",
+                        "options": dict(serve.THROUGHPUT_OPTIONS),
                         "stepping": "each request's next step is queued as soon as its own "
                                     "previous step is seen finished (qnsch_step_launch / "
                                     "qnsch_step_poll); step latency = launch to completion "

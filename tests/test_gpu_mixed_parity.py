@@ -1,8 +1,10 @@
 """Mixed precision against the FP64 oracle, field by field, at the bars of
 tests/mixed_tol.py (about ten times the measured differences), with V-cycle
 counts within one of the oracle's and mass conserved: small cases with either
-smoother, the batch's own option set (coupled block, one lane per block in
-the per-level launches, levels up to 2048 cells fused) on two draws of the
+smoother, the option set of the batch and the server (serve.THROUGHPUT_OPTIONS:
+coupled block, one lane per block in the per-level launches, levels up to
+2048 cells fused, one smoothing step before the coarse-grid correction and two
+after, the oracle running the same smoothing counts) on two draws of the
 64-drop batch workload at density ratios 83 and 57, the 256x512 rising drop
 with the per-colour smoother launches and with the banded wavefront, and a
 512^2 drop with the coupled block.  Also the FP64 path at full size over
@@ -14,10 +16,13 @@ import pytest
 from mixed_tol import MIXED_MASS_TOL, check_mixed
 from oracle.ref import RefSolver
 from paper_1703_06606_gb300 import workloads as W
+from paper_1703_06606_gb300.serve import THROUGHPUT_OPTIONS
 
 pytestmark = pytest.mark.gpu
 
-BATCH_OPTS = {"precision": 1, "coupled": 1, "fuse_cells32": 2048, "vanka_team_max32": 0}
+BATCH_OPTS = dict(precision=1, coupled=1, **THROUGHPUT_OPTIONS)
+# the oracle follows the same algorithm: the coupled block and the smoothing counts
+BATCH_REF = {"coupled": 1, "nu1": THROUGHPUT_OPTIONS["nu1"], "nu2": THROUGHPUT_OPTIONS["nu2"]}
 
 
 @pytest.fixture(scope="module")
@@ -43,8 +48,8 @@ def _cases():
         ("small_periodic", W.small_case(32, 48, True), 1, {"precision": 1}, {}),
         ("small_walls_coupled", W.small_case(32, 48, False), 2, {"precision": 1, "coupled": 1},
          {"coupled": 1}),
-        ("batch_draw_1_ratio83", ds[1], 2, BATCH_OPTS, {"coupled": 1}),
-        ("batch_draw_9_ratio57", ds[9], 2, BATCH_OPTS, {"coupled": 1}),
+        ("batch_draw_1_ratio83", ds[1], 2, BATCH_OPTS, BATCH_REF),
+        ("batch_draw_9_ratio57", ds[9], 2, BATCH_OPTS, BATCH_REF),
         ("drop_256x512", W.rising_drop_256x512(), 2, {"precision": 1}, {}),
         ("drop_256x512_wavefront", W.rising_drop_256x512(), 2,
          {"precision": 1, "wave_cells32": 1}, {}),

@@ -176,3 +176,35 @@ def test_tuned_options_reach_the_matching_requests():
     assert kws["r1"]["fuse_cells32"] == 2048 and kws["r1"]["vanka_team_max32"] == 0
     assert "fuse_cells32" not in kws["r0"] and "fuse_cells32" not in kws["r2"]
     assert all(kw["precision"] == 1 and kw["coupled"] == 1 for kw in kws.values())
+
+
+def test_base_options_reach_every_request_and_the_table_overrides_them():
+    """base_options (for example THROUGHPUT_OPTIONS) go to every simulation the
+    server creates; a matching tuned-table entry replaces the keys it names."""
+    from paper_1703_06606_gb300 import autotune
+    reqs = _requests([(32, 32), (64, 32)], [1, 1])
+    P = reqs[1].problem
+    table = {autotune.key_of(P, 1, 1, 0, autotune.device_name()):
+             {"options": {"fuse_cells32": 512}, "ms_per_step": 1.0}}
+    be = FakeBackend()
+    serve.Server(budget_bytes=1e9, backend=be, tuned_table=table,
+                 base_options=serve.THROUGHPUT_OPTIONS).run(reqs)
+    kws = {s.name: s.kw for s in be.created}
+    for k, v in serve.THROUGHPUT_OPTIONS.items():
+        assert kws["r0"][k] == v
+    assert kws["r1"]["fuse_cells32"] == 512
+    assert all(kws["r1"][k] == v for k, v in serve.THROUGHPUT_OPTIONS.items()
+               if k != "fuse_cells32")
+
+
+def test_throughput_options_are_library_options():
+    """Every key of THROUGHPUT_OPTIONS is an option the header documents and
+    the checkpoint keeps, so a served simulation can be saved and resumed with
+    its options."""
+    import os
+    from paper_1703_06606_gb300 import checkpoint
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    header = open(os.path.join(root, "include", "qnsch.h")).read()
+    for k in serve.THROUGHPUT_OPTIONS:
+        assert '"%s"' % k in header, k
+        assert k in checkpoint.OPTIONS, k
