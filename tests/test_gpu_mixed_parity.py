@@ -106,3 +106,51 @@ def test_fp64_full_size_three_steps_after_five(qn):
         assert e <= 1e-10, (k, e)
     mg, mr = g.mass(), r.mass()
     assert abs(mg[0] - mr[0]) <= 1e-13 * mr[0] and abs(mg[1] - mr[1]) <= 1e-13 * mr[1]
+
+
+def _bench():
+    import importlib.util
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "..", "bench.py")
+    spec = importlib.util.spec_from_file_location("bench_for_parity", path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+# the bench's paths on its workload at the smoothing counts it times them with
+# (bench.SMOOTHING), the oracle running the same counts and smoother
+BENCH_PATHS = [
+    ("fp64", {}, {}),
+    ("mixed", {"precision": 1}, {}),
+    ("fp64_coupled", {"coupled": 1}, {"coupled": 1}),
+    ("mixed_coupled", {"precision": 1, "coupled": 1}, {"coupled": 1}),
+    ("projection_fp64", {"scheme": 1}, {"scheme": 1}),
+]
+
+
+@pytest.mark.parametrize("name,gopts,ropts", BENCH_PATHS, ids=[c[0] for c in BENCH_PATHS])
+def test_bench_paths_at_their_smoothing_counts(qn, name, gopts, ropts):
+    """Two steps of the 256x512 drop per path: FP64 paths with equal V-cycle
+    counts and every field within 1e-10 of the oracle, mixed paths within the
+    mixed bars and one V-cycle."""
+    nu = _bench().SMOOTHING[name]
+    P = W.rising_drop_256x512()
+    g = qn.Solver(**P.create_kwargs(), tol=P.tol, **gopts, **nu)
+    r = RefSolver(**P.create_kwargs(), tol=P.tol, **ropts, **nu)
+    f = P.fields()
+    g.set_fields(f)
+    r.set_fields(f)
+    mixed = gopts.get("precision", 0) == 1
+    for _ in range(2):
+        ng, resg = g.step(P.dt)
+        nr, resr = r.step(P.dt)
+        assert resg <= P.tol and resr <= P.tol
+        assert (abs(ng - nr) <= 1) if mixed else (ng == nr), (ng, nr)
+    fg, fr = g.get_fields(), r.get_fields()
+    if mixed:
+        check_mixed(fg, fr)
+    else:
+        for k in fg:
+            e = np.max(np.abs(fg[k] - fr[k])) / max(np.max(np.abs(fr[k])), 1e-300)
+            assert e <= 1e-10, (k, e)
