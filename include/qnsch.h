@@ -138,7 +138,7 @@ int qnsch_footprint(const qnsch_grid* grid, int precision, size_t* bytes);
    "ch_team_max": 4096, "vanka_team_max32": 65536, "ch_team_max32": 0,
    "pdl": 1, "step_time_limit": 0, "diverge_cycles": 0, "device_loop": 0,
    "wave_cells32": 0, "wave_rows": 8, "wave_wait_cycles": 2147483648,
-   "wave_stall": 0, "skew_cells32": 0, "skew_rows": 32.
+   "wave_stall": 0, "skew_cells32": 0, "skew_rows": 32, "predictor": 0.
    Unknown keys give QNSCH_EINVAL, and so do values out of range, which leave
    the option unchanged: NaN for any key; counts that are not integers in
    their range (nu1, nu2, nu_coarse: 0..1000; maxcyc, diverge_cycles:
@@ -165,6 +165,15 @@ int qnsch_footprint(const qnsch_grid* grid, int precision, size_t* bytes);
    out ends the step with QNSCH_ETIMEOUT, uncommitted.  wave_stall (0 or 1) is
    a test hook for that path: with 1, one wait of every wavefront launch waits
    for a count nothing reaches.
+   predictor (0, 1 or 2): the initial iterate of a step.  0 (the default):
+   the committed state x^n.  1 or 2: the polynomial in time through x^n and
+   the last one or two states committed before it (qnsch_get_history),
+   evaluated at the new time t + dt, with the step sizes as they were
+   (Lagrange interpolation on unequal nodes); with fewer states held, the
+   highest order they allow.  The predicted iterate only moves the start of
+   the outer cycles: the step still stops at the same residual tolerance.
+   Setting the option clears the history; each committed step adds to it.
+   history (read-only; 0 clears it): the number of earlier states held.
    skew_cells32 (integer >= 0; 0: never; checked before wave_cells32):
    error-equation levels with at least this many cells run each block of nu
    smoothing steps in the skewed-chunk schedule: launch d runs pass p (the
@@ -259,6 +268,22 @@ int qnsch_set_fields_device(qnsch_t* h, const double* c, const double* mu, const
                             const double* v, const double* p);
 int qnsch_get_fields_device(const qnsch_t* h, double* c, double* mu, double* u, double* v,
                             double* p);
+/* The states committed before the current one, which the option "predictor"
+   extrapolates from (k = 0 the most recent; get_option "history" gives how
+   many are held, at most 2).  qnsch_get_history copies state k into host
+   arrays in the layouts above (NULL pointers skipped) and its step size dt
+   (the step that led from it to the next state); QNSCH_EINVAL if k is not
+   below the count or dt is NULL.  qnsch_set_history sets state k and its dt
+   (k at most the count, so k equal to the count appends; all five pointers;
+   dt > 0 and finite; else QNSCH_EINVAL), for example to resume a run so that
+   its next steps start from the same predicted iterates as the uninterrupted
+   run's.  Both need no pending step (QNSCH_ESTATE).  qnsch_set_fields and
+   qnsch_set_fields_device clear the history, and so do set_option
+   "predictor" and set_option "history" = 0. */
+int qnsch_get_history(const qnsch_t* h, int k, double* dt, double* c, double* mu, double* u,
+                      double* v, double* p);
+int qnsch_set_history(qnsch_t* h, int k, double dt, const double* c, const double* mu,
+                      const double* u, const double* v, const double* p);
 
 /* One time step of the scheme of Sec. 6.1 (primitive) or Sec. 6.2
    (projection, option scheme = 1), solved by the FAS V-cycles of Sec. 7.1 /

@@ -159,6 +159,12 @@ struct ref_solver {
   /* committed state (finest level, ghosted) */
   double *c, *mu, *p, *u, *v;
   double last_res;
+  /* option "predictor": the states committed 1 and 2 steps before the
+     current one (ghosted, finest level), the sizes of the steps that left
+     them, and how many are held */
+  int predictor, nhist;
+  double hdt[2];
+  double *hc[2], *hmu[2], *hp[2], *hu[2], *hv[2];
 };
 
 /* ------------------------------------------------------------------------ */
@@ -1408,6 +1414,13 @@ int qnsch_ref_create(int m1, int m2, double Lx, int periodic_x, int levels, doub
   s->p = zalloc(ncell(F));
   s->u = zalloc(nu_(F));
   s->v = zalloc(nv_(F));
+  for (int k = 0; k < 2; ++k) {
+    s->hc[k] = zalloc(ncell(F));
+    s->hmu[k] = zalloc(ncell(F));
+    s->hp[k] = zalloc(ncell(F));
+    s->hu[k] = zalloc(nu_(F));
+    s->hv[k] = zalloc(nv_(F));
+  }
   *out = s;
   return REF_OK;
 }
@@ -1422,6 +1435,13 @@ int qnsch_ref_destroy(ref_solver* s) {
   free(s->p);
   free(s->u);
   free(s->v);
+  for (int k = 0; k < 2; ++k) {
+    free(s->hc[k]);
+    free(s->hmu[k]);
+    free(s->hp[k]);
+    free(s->hu[k]);
+    free(s->hv[k]);
+  }
   free(s);
   return REF_OK;
 }
@@ -1445,6 +1465,15 @@ int qnsch_ref_set_option(ref_solver* s, const char* key, double value) {
     if (value != 0.0 && s->P.scheme) return REF_EINVAL; /* the 7x7 block is a primitive-method smoother */
     s->coupled = value != 0.0;
   }
+  else if (!strcmp(key, "predictor")) {
+    if (s->pending || !(value == 0.0 || value == 1.0 || value == 2.0)) return REF_EINVAL;
+    s->predictor = (int)value;
+    s->nhist = 0;
+  }
+  else if (!strcmp(key, "history")) {
+    if (s->pending || value != 0.0) return REF_EINVAL;
+    s->nhist = 0;
+  }
   else return REF_EINVAL;
   return REF_OK;
 }
@@ -1462,6 +1491,8 @@ int qnsch_ref_get_option(const ref_solver* s, const char* key, double* value) {
   else if (!strcmp(key, "eta_st")) *value = s->P.eta;
   else if (!strcmp(key, "eps_mob")) *value = s->P.eps_m;
   else if (!strcmp(key, "coupled")) *value = s->coupled;
+  else if (!strcmp(key, "predictor")) *value = s->predictor;
+  else if (!strcmp(key, "history")) *value = s->nhist;
   else return REF_EINVAL;
   return REF_OK;
 }
@@ -1581,7 +1612,52 @@ int qnsch_ref_set_fields(ref_solver* s, const double* c, const double* mu, const
   if (!s || !c || !mu || !u || !v || !p) return REF_EINVAL;
   if (s->pending) return REF_ESTATE;
   pack_in(&s->lev[0], s->c, s->mu, s->p, s->u, s->v, c, mu, p, u, v);
+  s->nhist = 0;
   return REF_OK;
+}
+
+/* the states the predictor extrapolates from (k = 0 the most recent) */
+int qnsch_ref_get_history(const ref_solver* s, int k, double* dt, double* c, double* mu,
+                          double* u, double* v, double* p) {
+  if (!s || !dt || k < 0 || k >= s->nhist) return REF_EINVAL;
+  pack_out(&s->lev[0], s->hc[k], s->hmu[k], s->hp[k], s->hu[k], s->hv[k], c, mu, p, u, v);
+  *dt = s->hdt[k];
+  return REF_OK;
+}
+
+int qnsch_ref_set_history(ref_solver* s, int k, double dt, const double* c, const double* mu,
+                          const double* u, const double* v, const double* p) {
+  if (!s || !c || !mu || !u || !v || !p || k < 0 || k > 1 || k > s->nhist || !(dt > 0))
+    return REF_EINVAL;
+  if (s->pending) return REF_ESTATE;
+  pack_in(&s->lev[0], s->hc[k], s->hmu[k], s->hp[k], s->hu[k], s->hv[k], c, mu, p, u, v);
+  s->hdt[k] = dt;
+  if (k == s->nhist) s->nhist = k + 1;
+  return REF_OK;
+}
+
+/* Lagrange basis at tau = dt for the nodes tau_0 = 0 (the committed state),
+   tau_1 = -hdt[0], tau_2 = -hdt[0] - hdt[1] (the earlier states), of the
+   degree the option and the history allow: l_i(dt) = prod over j != i of
+   (dt - tau_j) / (tau_i - tau_j); degree 0 gives the committed state. */
+static void predict_weights(const ref_solver* s, double dt, double w[3]) {
+  int m = s->predictor < s->nhist ? s->predictor : s->nhist;
+  double tau[3];
+  tau[0] = 0.0;
+  tau[1] = -s->hdt[0];
+  tau[2] = -s->hdt[0] - s->hdt[1];
+  for (int i = 0; i < 3; ++i) w[i] = 0.0;
+  for (int i = 0; i <= m; ++i) {
+    double l = 1.0;
+    for (int j = 0; j <= m; ++j)
+      if (j != i) l *= (dt - tau[j]) / (tau[i] - tau[j]);
+    w[i] = l;
+  }
+}
+
+static void combine(double* x, size_t n, const double w[3], const double* a, const double* b,
+                    const double* c) {
+  for (size_t i = 0; i < n; ++i) x[i] = w[0] * a[i] + w[1] * b[i] + w[2] * c[i];
 }
 
 int qnsch_ref_get_fields(const ref_solver* s, double* c, double* mu, double* u, double* v,
@@ -1600,6 +1676,18 @@ int qnsch_ref_begin_step(ref_solver* s, double dt) {
   memcpy(F->p, s->p, ncell(F) * sizeof(double));
   memcpy(F->u, s->u, nu_(F) * sizeof(double));
   memcpy(F->v, s->v, nv_(F) * sizeof(double));
+  {
+    /* the initial iterate: x^n, or its extrapolation in time (predictor) */
+    double w[3];
+    predict_weights(s, dt, w);
+    if (w[1] != 0.0 || w[2] != 0.0) {
+      combine(F->c, ncell(F), w, s->c, s->hc[0], s->hc[1]);
+      combine(F->mu, ncell(F), w, s->mu, s->hmu[0], s->hmu[1]);
+      combine(F->p, ncell(F), w, s->p, s->hp[0], s->hp[1]);
+      combine(F->u, nu_(F), w, s->u, s->hu[0], s->hu[1]);
+      combine(F->v, nv_(F), w, s->v, s->hv[0], s->hv[1]);
+    }
+  }
   memcpy(F->cn, s->c, ncell(F) * sizeof(double));
   memcpy(F->un, s->u, nu_(F) * sizeof(double));
   memcpy(F->vn, s->v, nv_(F) * sizeof(double));
@@ -1636,6 +1724,25 @@ int qnsch_ref_commit_step(ref_solver* s) {
   if (!s) return REF_EINVAL;
   if (!s->pending) return REF_ESTATE;
   ref_level* F = &s->lev[0];
+  if (s->predictor > 0) {
+    /* the state being replaced becomes the most recent earlier state */
+    double* t;
+#define ROTATE(h) (t = h[1], h[1] = h[0], h[0] = t)
+    ROTATE(s->hc);
+    ROTATE(s->hmu);
+    ROTATE(s->hp);
+    ROTATE(s->hu);
+    ROTATE(s->hv);
+#undef ROTATE
+    memcpy(s->hc[0], s->c, ncell(F) * sizeof(double));
+    memcpy(s->hmu[0], s->mu, ncell(F) * sizeof(double));
+    memcpy(s->hp[0], s->p, ncell(F) * sizeof(double));
+    memcpy(s->hu[0], s->u, nu_(F) * sizeof(double));
+    memcpy(s->hv[0], s->v, nv_(F) * sizeof(double));
+    s->hdt[1] = s->hdt[0];
+    s->hdt[0] = s->dt;
+    s->nhist = s->nhist < 2 ? s->nhist + 1 : 2;
+  }
   memcpy(s->c, F->c, ncell(F) * sizeof(double));
   memcpy(s->mu, F->mu, ncell(F) * sizeof(double));
   memcpy(s->p, F->p, ncell(F) * sizeof(double));

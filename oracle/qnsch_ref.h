@@ -48,6 +48,14 @@ int qnsch_ref_set_fields(ref_solver* s, const double* c, const double* mu,
                          const double* u, const double* v, const double* p);
 int qnsch_ref_get_fields(const ref_solver* s, double* c, double* mu, double* u,
                          double* v, double* p);
+/* option "predictor" (0, 1, 2): the initial iterate of a step extrapolated in
+   time from the committed state and the last one or two states committed
+   before it; these calls read and set those states (k = 0 the most recent)
+   and the step sizes that left them */
+int qnsch_ref_get_history(const ref_solver* s, int k, double* dt, double* c, double* mu,
+                          double* u, double* v, double* p);
+int qnsch_ref_set_history(ref_solver* s, int k, double dt, const double* c, const double* mu,
+                          const double* u, const double* v, const double* p);
 
 /* one time step = begin + outer V-cycles until tol + commit */
 int qnsch_ref_step(ref_solver* s, double dt, int* n_vcycles, double* final_res);

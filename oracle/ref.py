@@ -53,6 +53,8 @@ def lib():
             getattr(L, "qnsch_ref_" + name).argtypes = [vp, p, p, p, p, p]
         for name in ("get_fields", "get_iterate"):
             getattr(L, "qnsch_ref_" + name).argtypes = [vp, p, p, p, p, p]
+        L.qnsch_ref_get_history.argtypes = [vp, i, p, p, p, p, p, p]
+        L.qnsch_ref_set_history.argtypes = [vp, i, d, p, p, p, p, p]
         L.qnsch_ref_step.argtypes = [vp, d, ctypes.POINTER(i), p]
         L.qnsch_ref_begin_step.argtypes = [vp, d]
         L.qnsch_ref_vcycle.argtypes = [vp, p]
@@ -185,6 +187,21 @@ class RefSolver:
         _check(lib().qnsch_ref_get_fields(self._h, _ptr(a["c"]), _ptr(a["mu"]), _ptr(a["u"]),
                                           _ptr(a["v"]), _ptr(a["p"])), "get_fields")
         return a
+
+    def history(self, k):
+        """(fields, dt) of the k-th state committed before the current one."""
+        a = self.zeros()
+        dt = np.zeros(1)
+        _check(lib().qnsch_ref_get_history(self._h, int(k), _ptr(dt), _ptr(a["c"]), _ptr(a["mu"]),
+                                           _ptr(a["u"]), _ptr(a["v"]), _ptr(a["p"])),
+               "get_history")
+        return a, float(dt[0])
+
+    def set_history(self, k, f, dt):
+        a = self._in(f)
+        _check(lib().qnsch_ref_set_history(self._h, int(k), float(dt), _ptr(a["c"]), _ptr(a["mu"]),
+                                           _ptr(a["u"]), _ptr(a["v"]), _ptr(a["p"])),
+               "set_history")
 
     def set_iterate(self, f):
         a = self._in(f)

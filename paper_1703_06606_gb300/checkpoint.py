@@ -31,7 +31,7 @@ OPTIONS = ("scheme", "precision", "coupled", "nu1", "nu2", "nu_coarse", "maxcyc"
            "omega_vanka", "M", "eta_st", "eps_mob", "graphs", "fuse_cells", "fuse_cells32",
            "vanka_team_max", "ch_team_max", "vanka_team_max32", "ch_team_max32",
            "step_time_limit", "diverge_cycles", "device_loop", "wave_cells32", "wave_rows",
-           "vanka_team8_max", "skew_cells32", "skew_rows")
+           "vanka_team8_max", "skew_cells32", "skew_rows", "predictor")
 
 
 def field_shapes(m1, m2):
@@ -41,10 +41,12 @@ def field_shapes(m1, m2):
     return {"c": (m2, m1), "mu": (m2, m1), "p": (m2, m1), "u": (m2, m1 + 1), "v": (m2 + 1, m1)}
 
 
-def save(path, fields, params, options, t=0.0, n=0, library=None):
+def save(path, fields, params, options, t=0.0, n=0, library=None, history=()):
     """Write one checkpoint.  fields: the five arrays; params: the creation
     parameters (PARAMS); options: option key -> value; library: the version of
-    the library that computed the state (recorded, not checked on load)."""
+    the library that computed the state (recorded, not checked on load);
+    history: the earlier states the option "predictor" extrapolates from, as
+    (fields, dt) pairs, the most recent first (qnsch_get_history)."""
     missing = [k for k in PARAMS if k not in params]
     if missing:
         raise ValueError("checkpoint parameters missing: %s" % missing)
@@ -55,9 +57,18 @@ def save(path, fields, params, options, t=0.0, n=0, library=None):
         if a.shape != shapes[k]:
             raise ValueError("field %s has shape %s, expected %s" % (k, a.shape, shapes[k]))
         arrays[k] = a
+    hdt = []
+    for j, (hf, dt) in enumerate(history):
+        for k in FIELDS:
+            a = np.ascontiguousarray(hf[k], dtype=np.float64)
+            if a.shape != shapes[k]:
+                raise ValueError("history %d field %s has shape %s, expected %s"
+                                 % (j, k, a.shape, shapes[k]))
+            arrays["h%d_%s" % (j, k)] = a
+        hdt.append(float(dt))
     meta = {"format": FORMAT, "params": {k: params[k] for k in PARAMS},
             "options": {k: float(v) for k, v in options.items()}, "t": float(t), "n": int(n),
-            "library": None if library is None else list(library)}
+            "library": None if library is None else list(library), "history_dt": hdt}
     tmp = "%s.tmp%d" % (path, os.getpid())
     with open(tmp, "wb") as f:
         np.savez(f, meta=np.array(json.dumps(meta)), **arrays)
@@ -81,3 +92,21 @@ def load(path):
             fields[k] = a
     opts = {k: meta["options"][k] for k in OPTIONS if k in meta["options"]}
     return fields, params, opts, meta["t"], meta["n"]
+
+
+def load_history(path):
+    """The earlier states a checkpoint recorded, as (fields, dt) pairs, the
+    most recent first ([] for a checkpoint without them)."""
+    with np.load(path, allow_pickle=False) as z:
+        meta = json.loads(str(z["meta"]))
+        shapes = field_shapes(int(meta["params"]["m1"]), int(meta["params"]["m2"]))
+        out = []
+        for j, dt in enumerate(meta.get("history_dt", [])):
+            f = {}
+            for k in FIELDS:
+                a = np.array(z["h%d_%s" % (j, k)], dtype=np.float64)
+                if a.shape != shapes[k]:
+                    raise ValueError("history %d field %s has shape %s" % (j, k, a.shape))
+                f[k] = a
+            out.append((f, float(dt)))
+    return out

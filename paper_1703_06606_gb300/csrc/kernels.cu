@@ -2330,6 +2330,26 @@ __global__ void __launch_bounds__(SNT) k_skew(Prm<T> P, Lv<T> L, SkewTasks S, T 
 }
 
 // --------------------------------------------------------------------------
+// the predicted initial iterate of a step (option predictor): a Lagrange
+// extrapolation in time of the committed state and the states before it,
+// over the whole padded arrays (ghosts are linear in the values they copy,
+// so the combination keeps them consistent)
+// --------------------------------------------------------------------------
+struct FiveArrays {
+  double* p[5];
+};
+
+__global__ void k_predict(FiveArrays X, FiveArrays A, FiveArrays B, FiveArrays C, double w0,
+                          double w1, double w2, long long n, int off) {
+  pdl_enter();
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int q = blockIdx.y;
+  const long long i = t - off;
+  X.p[q][i] = w0 * A.p[q][i] + w1 * B.p[q][i] + w2 * C.p[q][i];
+}
+
+// --------------------------------------------------------------------------
 // defect correction (mixed precision): FP64 level <-> error-equation level
 // --------------------------------------------------------------------------
 // error-equation frozen data = rounded FP64 frozen data (whole padded arrays)
@@ -3075,6 +3095,21 @@ int launch_skew(const Prm<T>& P, const Lv<T>& L, int nsteps, int coupled, int ro
     }
   }
   return launches;
+}
+
+void launch_predict(double* const x[5], double* const a[5], double* const b[5],
+                    double* const c[5], const double w[3], size_t n, int off, cudaStream_t s) {
+  FiveArrays X, A, B, C;
+  for (int q = 0; q < 5; ++q) {
+    X.p[q] = x[q];
+    A.p[q] = a[q];
+    B.p[q] = b[q];
+    C.p[q] = c[q];
+  }
+  const int NT = 256;
+  dim3 grid((unsigned)((n + NT - 1) / NT), 5);
+  qlaunch(&k_predict, grid, NT, 0, s, X, A, B, C, w[0], w[1], w[2], (long long)n, off);
+  ++g_launches;
 }
 
 void launch_loop_clock(double* ctl, cudaStream_t s) {

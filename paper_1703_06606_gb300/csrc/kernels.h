@@ -57,6 +57,11 @@ struct SkewTasks {
 template <typename T, class Form>
 int launch_skew(const Prm<T>& P, const Lv<T>& L, int nsteps, int coupled, int rows, T omega,
                 cudaStream_t s);
+// the predicted initial iterate of a step: x[q] = w[0] a[q] + w[1] b[q] +
+// w[2] c[q] elementwise, q over the five unknowns (c, mu, p, u, v), each array
+// n padded elements starting `off` elements before its origin pointer
+void launch_predict(double* const x[5], double* const a[5], double* const b[5],
+                    double* const c[5], const double w[3], size_t n, int off, cudaStream_t s);
 // the V-cycle on levels[0..n-1] (levels[0] is its finest) in one thread block
 // (team8: the FP64 full-iterate Vanka blocks use eight lanes where a colour
 // fits the block in one pass)

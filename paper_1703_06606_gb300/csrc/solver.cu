@@ -190,6 +190,15 @@ struct qnsch_s {
   // in the skewed-chunk schedule (k_skew; 0: never), chunks of skew_rows rows
   long long skew_cells = 0;
   int skew_rows = 32;
+  // initial iterate of a step: 0 the committed state x^n; 1 or 2 its
+  // extrapolation in time (Lagrange, at the new time) through x^n and the one
+  // or two states committed before it.  hist[k] is the state committed k + 1
+  // steps before the current one (c, mu, p, u, v, padded level-0 layout) and
+  // hdt[k] the size of the step that left it; nhist of them are valid
+  int predictor = 0;
+  int nhist = 0;
+  double hdt[2] = {0.0, 0.0};
+  double* hist[2][5] = {};
   // failure detection: a step stops once it has run this many seconds of wall
   // time (0: no limit), or once its residual has grown over this many
   // consecutive outer cycles (0: never)
@@ -239,6 +248,7 @@ struct qnsch_s {
   int device_loop = 0;
   cudaGraphExec_t sexec = nullptr;
   double s_dt = -1.0;
+  double s_w[3] = {0.0, 0.0, 0.0};  // the predictor's weights the graph was built with
   int s_precision = -1;
   unsigned s_opt = ~0u;
   long long s_pro = 0, s_body = 0, s_commit = 0;  // kernels in the graph's three parts
@@ -393,6 +403,12 @@ int alloc_all(qnsch_s* s) {
   s->sp = st + 2 * n0 + pitch0 + 1;
   s->su = st + 3 * n0 + pitch0 + 1;
   s->sv = st + 4 * n0 + pitch0 + 1;
+  double* hs = (double*)dev_alloc(s->mem, n0 * 10 * sizeof(double));
+  if (!hs) return QNSCH_ENOMEM;
+  s->blocks.push_back(hs);
+  cudaMemsetAsync(hs, 0, n0 * 10 * sizeof(double), s->stream);
+  for (int k = 0; k < 2; ++k)
+    for (int q = 0; q < 5; ++q) s->hist[k][q] = hs + (size_t)(5 * k + q) * n0 + pitch0 + 1;
   int rows = qn::partial_rows_needed(s->m1, s->m2);
   s->part = (double*)dev_alloc(s->mem, (size_t)rows * 10 * sizeof(double));
   if (!s->part) return QNSCH_ENOMEM;
@@ -827,6 +843,35 @@ int alloc_err(qnsch_s* s) {
 
 // the queued part of a step's start: the committed state into the iterate and
 // the frozen level-n data, then the frozen data of every level (A2)
+// Weights of the step's initial iterate w[0] x^n + w[1] x^(n-1) + w[2] x^(n-2):
+// the Lagrange polynomial through the committed state (time t) and the
+// predictor's earlier states (t - hdt[0], t - hdt[0] - hdt[1]) evaluated at
+// t + dt; (1, 0, 0) without a predictor or without history.
+void predictor_weights(const qnsch_s* s, double dt, double w[3]) {
+  w[0] = 1.0;
+  w[1] = w[2] = 0.0;
+  const int n = std::min(s->predictor, s->nhist);
+  if (n == 1) {
+    const double a = s->hdt[0];
+    w[0] = (dt + a) / a;
+    w[1] = -dt / a;
+  } else if (n == 2) {
+    const double a = s->hdt[0], b = s->hdt[1];
+    w[0] = (dt + a) * (dt + a + b) / (a * (a + b));
+    w[1] = -dt * (dt + a + b) / (a * b);
+    w[2] = dt * (dt + a) / ((a + b) * b);
+  }
+}
+
+// after a committed step: the state it replaced becomes hist[0] (the copies
+// were queued by queue_commit)
+void note_commit(qnsch_s* s) {
+  if (s->predictor <= 0) return;
+  s->hdt[1] = s->hdt[0];
+  s->hdt[0] = s->dt;
+  s->nhist = std::min(s->nhist + 1, 2);
+}
+
 void queue_begin(qnsch_s* s, double dt) {
   s->dt = dt;
   s->res_valid = 0;
@@ -837,9 +882,16 @@ void queue_begin(qnsch_s* s, double dt) {
   double* src[5] = {s->sc, s->smu, s->sp, s->su, s->sv};
   double* dst[5] = {F.c, F.mu, F.p, F.u, F.v};
   int pitch = F.pitch;
-  for (int q = 0; q < 5; ++q)
-    cudaMemcpyAsync(dst[q] - pitch - 1, src[q] - pitch - 1, bytes, cudaMemcpyDeviceToDevice,
-                    s->stream);
+  double w[3];
+  predictor_weights(s, dt, w);
+  if (w[1] == 0.0 && w[2] == 0.0) {
+    for (int q = 0; q < 5; ++q)
+      cudaMemcpyAsync(dst[q] - pitch - 1, src[q] - pitch - 1, bytes, cudaMemcpyDeviceToDevice,
+                      s->stream);
+  } else {
+    qn::launch_predict(dst, src, s->hist[0], s->hist[1], w, s->level_elems0, pitch + 1,
+                       s->stream);
+  }
   cudaMemcpyAsync(F.cn - pitch - 1, s->sc - pitch - 1, bytes, cudaMemcpyDeviceToDevice, s->stream);
   cudaMemcpyAsync(F.un - pitch - 1, s->su - pitch - 1, bytes, cudaMemcpyDeviceToDevice, s->stream);
   cudaMemcpyAsync(F.vn - pitch - 1, s->sv - pitch - 1, bytes, cudaMemcpyDeviceToDevice, s->stream);
@@ -993,6 +1045,14 @@ void queue_commit(qnsch_s* s, bool to_host) {
   int pitch = F.pitch;
   double* src[5] = {F.c, F.mu, F.p, F.u, F.v};
   double* dst[5] = {s->sc, s->smu, s->sp, s->su, s->sv};
+  if (s->predictor > 0) {  // the state being replaced moves into the history
+    for (int q = 0; q < 5; ++q) {
+      cudaMemcpyAsync(s->hist[1][q] - pitch - 1, s->hist[0][q] - pitch - 1, bytes,
+                      cudaMemcpyDeviceToDevice, s->stream);
+      cudaMemcpyAsync(s->hist[0][q] - pitch - 1, dst[q] - pitch - 1, bytes,
+                      cudaMemcpyDeviceToDevice, s->stream);
+    }
+  }
   int nq = s->scheme ? 3 : 5;  // projection: the velocity is u^{n+1} of (pj-num-pjx)
   for (int q = 0; q < nq; ++q)
     cudaMemcpyAsync(dst[q] - pitch - 1, src[q] - pitch - 1, bytes, cudaMemcpyDeviceToDevice,
@@ -1021,6 +1081,7 @@ int finish_commit(qnsch_s* s) {
   if (rc) return rc;
   s->last_diss = s->hbuf[25] + (s->scheme ? s->hbuf[26] : 0.0);
   s->pending = 0;
+  note_commit(s);
   return QNSCH_OK;
 }
 
@@ -1143,6 +1204,7 @@ int build_step_graph(qnsch_s* s, double dt) {
   s->s_body = c2 - c1;
   s->s_commit = c3 - c2;
   s->s_dt = dt;
+  predictor_weights(s, dt, s->s_w);
   s->s_precision = s->precision;
   s->s_opt = s->opt_version;
   return QNSCH_OK;
@@ -1155,8 +1217,11 @@ bool device_loop_on(const qnsch_s* s) { return s->device_loop && s->use_graphs &
 // queue one whole step as a graph replay; QNSCH_ECUDA if the graph cannot be
 // built (the handle then falls back to the host-driven loop for good)
 int launch_device_step(qnsch_s* s, double dt) {
+  double w[3];
+  predictor_weights(s, dt, w);
   const bool fresh = s->sexec && s->s_dt == dt && s->s_precision == s->precision &&
-                     s->s_opt == s->opt_version;
+                     s->s_opt == s->opt_version && s->s_w[0] == w[0] && s->s_w[1] == w[1] &&
+                     s->s_w[2] == w[2];
   if (!fresh) {
     int rc = build_step_graph(s, dt);
     if (rc == QNSCH_ECUDA) s->device_loop = 0;
@@ -1191,6 +1256,7 @@ int finish_device_step(qnsch_s* s, int* n_vcycles, double* final_residual) {
   if (late) return QNSCH_ETIMEOUT;
   if (!committed) return QNSCH_ENOTCONV;
   s->last_diss = s->hbuf[25] + (s->scheme ? s->hbuf[26] : 0.0);
+  note_commit(s);
   return QNSCH_OK;
 }
 
@@ -1377,6 +1443,7 @@ int qnsch_footprint(const qnsch_grid* grid, int precision, size_t* bytes) {
     b /= 2;
   }
   total += n0 * 5 * sizeof(double);                                           // committed state
+  total += n0 * 10 * sizeof(double);                                          // two earlier states
   total += (size_t)qn::partial_rows_needed(grid->m1, grid->m2) * 10 * sizeof(double);
   total += (size_t)(grid->m1 + 1) * (grid->m2 + 1) * sizeof(double);         // staging
   total += NSCAL * sizeof(double);
@@ -1465,6 +1532,15 @@ int set_option(qnsch_s* s, const std::string& k, double value) {
   } else if (k == "skew_rows") {
     if (!count_of(value, 1, 1 << 20, &n)) return QNSCH_EINVAL;
     s->skew_rows = n;
+  } else if (k == "predictor") {
+    if (!count_of(value, 0, 2, &n)) return QNSCH_EINVAL;
+    if (s->pending) return QNSCH_ESTATE;
+    s->predictor = n;
+    s->nhist = 0;  // the history restarts with the next committed step
+  } else if (k == "history") {  // read-only but for 0, which clears it
+    if (value != 0.0) return QNSCH_EINVAL;
+    if (s->pending) return QNSCH_ESTATE;
+    s->nhist = 0;
   } else if (k == "step_time_limit") {
     if (!(value >= 0.0) || !std::isfinite(value)) return QNSCH_EINVAL;
     s->time_limit = value;
@@ -1531,6 +1607,8 @@ int qnsch_get_option(const qnsch_t* s, const char* key, double* value) {
   else if (k == "wave_stall") *value = s->wave_stall;
   else if (k == "skew_cells32") *value = (double)s->skew_cells;
   else if (k == "skew_rows") *value = s->skew_rows;
+  else if (k == "predictor") *value = s->predictor;
+  else if (k == "history") *value = s->nhist;
   else if (k == "step_time_limit") *value = s->time_limit;
   else if (k == "diverge_cycles") *value = s->diverge;
   else if (k == "fuse_cells") *value = s->fuse64;
@@ -1614,6 +1692,7 @@ int qnsch_set_fields(qnsch_t* s, const double* c, const double* mu, const double
   if (s->pending) return QNSCH_ESTATE;
   double* dst[5] = {s->sc, s->smu, s->su, s->sv, s->sp};
   const double* src[5] = {c, mu, u, v, p};
+  s->nhist = 0;  // a new state: no history behind it
   return copy_fields_in(s, dst, src, true);
 }
 
@@ -1623,8 +1702,33 @@ int qnsch_set_fields_device(qnsch_t* s, const double* c, const double* mu, const
   if (s->pending) return QNSCH_ESTATE;
   double* dst[5] = {s->sc, s->smu, s->su, s->sv, s->sp};
   const double* src[5] = {c, mu, u, v, p};
+  s->nhist = 0;
   enter(s);
   return copy_fields_in(s, dst, src, false);
+}
+
+int qnsch_get_history(const qnsch_t* s, int k, double* dt, double* c, double* mu, double* u,
+                      double* v, double* p) {
+  if (!s || !dt || k < 0 || k >= s->nhist) return QNSCH_EINVAL;
+  if (s->pending) return QNSCH_ESTATE;
+  double* src[5] = {s->hist[k][0], s->hist[k][1], s->hist[k][3], s->hist[k][4], s->hist[k][2]};
+  double* dst[5] = {c, mu, u, v, p};
+  *dt = s->hdt[k];
+  return copy_fields_out(s, src, dst, true);
+}
+
+int qnsch_set_history(qnsch_t* s, int k, double dt, const double* c, const double* mu,
+                      const double* u, const double* v, const double* p) {
+  if (!s || !c || !mu || !u || !v || !p || k < 0 || k > s->nhist || k > 1) return QNSCH_EINVAL;
+  if (!(dt > 0.0) || !std::isfinite(dt)) return QNSCH_EINVAL;
+  if (s->pending) return QNSCH_ESTATE;
+  double* dst[5] = {s->hist[k][0], s->hist[k][1], s->hist[k][3], s->hist[k][4], s->hist[k][2]};
+  const double* src[5] = {c, mu, u, v, p};
+  int rc = copy_fields_in(s, dst, src, true);
+  if (rc) return rc;
+  s->hdt[k] = dt;
+  if (k == s->nhist) s->nhist = k + 1;
+  return QNSCH_OK;
 }
 
 int qnsch_get_fields(const qnsch_t* s, double* c, double* mu, double* u, double* v, double* p) {

@@ -58,6 +58,8 @@ def lib():
         for name in ("set_fields", "get_fields", "set_fields_device", "get_fields_device",
                      "set_iterate", "get_iterate"):
             getattr(L, "qnsch_" + name).argtypes = [_VP, _VP, _VP, _VP, _VP, _VP]
+        L.qnsch_get_history.argtypes = [_VP, i, p, _VP, _VP, _VP, _VP, _VP]
+        L.qnsch_set_history.argtypes = [_VP, i, d, _VP, _VP, _VP, _VP, _VP]
         L.qnsch_step.argtypes = [_VP, d, ctypes.POINTER(i), p]
         L.qnsch_step_launch.argtypes = [_VP, d]
         L.qnsch_step_poll.argtypes = [_VP, ctypes.POINTER(i), ctypes.POINTER(i), p,
@@ -203,10 +205,12 @@ class Solver:
     # ---- checkpoint / resume ----
     def save_checkpoint(self, path, t=0.0, n=0):
         """Write the committed state, creation parameters and options (plus the
-        caller's time t and step count n) to the .npz file `path`."""
+        caller's time t and step count n) to the .npz file `path`, with the
+        earlier states the option "predictor" extrapolates from."""
         from . import checkpoint
+        hist = [self.history(k) for k in range(int(self.get_option("history")))]
         checkpoint.save(path, self.get_fields(), self.params, self.options(), t, n,
-                        library=version())
+                        library=version(), history=hist)
 
     @classmethod
     def from_checkpoint(cls, path, stream=None, **overrides):
@@ -218,6 +222,8 @@ class Solver:
         for k, v in dict(opts, **overrides).items():
             s.set_option(k, v)
         s.set_fields(fields)
+        for k, (hf, dt) in enumerate(checkpoint.load_history(path)):
+            s.set_history(k, hf, dt)
         return s, t, n
 
     @property
@@ -277,6 +283,23 @@ class Solver:
 
     def set_iterate(self, f):
         self._host_call(lib().qnsch_set_iterate, f, "qnsch_set_iterate")
+
+    def history(self, k):
+        """qnsch_get_history: (fields, dt) of the k-th state committed before the
+        current one (0 the most recent)."""
+        a = self.zeros()
+        dt = ctypes.c_double()
+        _check(lib().qnsch_get_history(self._h, int(k), ctypes.byref(dt),
+                                       *[_np_ptr(a[q]) for q in self.FIELDS]),
+               "qnsch_get_history")
+        return a, dt.value
+
+    def set_history(self, k, f, dt):
+        """qnsch_set_history: the k-th earlier state and the step size that left it."""
+        a = self._host_in(f)
+        _check(lib().qnsch_set_history(self._h, int(k), float(dt),
+                                       *[_np_ptr(a[q]) for q in self.FIELDS]),
+               "qnsch_set_history")
 
     def get_iterate(self):
         return self._host_get(lib().qnsch_get_iterate, "qnsch_get_iterate")

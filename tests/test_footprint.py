@@ -3,7 +3,8 @@ and the design notes describe, recomputed here: per level one FP64 block of 45
 arrays over the padded index space (row pitch m1 + 3 rounded up to 32
 elements, m2 + 3 rows), one more block of 43 arrays per level for the error
 equation (FP32 at precision 1, FP64 at precision 2), the committed state (5
-arrays of the finest level's size), the reduction partials (10 doubles per
+arrays of the finest level's size), the two earlier states the predictor
+extrapolates from (10 more), the reduction partials (10 doubles per
 32 x 8 tile of the (m1 + 1) x (m2 + 1) points), a host-I/O staging array of
 (m1 + 1)(m2 + 1) doubles, 128 scalars (norms, reductions and the
 control block of the device-side outer-cycle loop) and the banded wavefront's
@@ -31,7 +32,7 @@ def _bytes(m1, m2, px, levels, precision):
             n0 = n
         total += 45 * 8 * n + (43 * (4 if precision == 1 else 8) * n if precision else 0)
         a, b = a // 2, b // 2
-    total += 5 * 8 * n0
+    total += 5 * 8 * n0 + 10 * 8 * n0
     total += -(-(m1 + 1) // 32) * -(-(m2 + 1) // 8) * 10 * 8
     total += (m1 + 1) * (m2 + 1) * 8 + 128 * 8
     total += -(-(4 * (2 + -(-m2 // 4))) // 256) * 256
@@ -51,8 +52,8 @@ def test_footprint_of_the_bench_workloads():
     """The sizes quoted for the droplet and Rayleigh-Taylor workloads."""
     mb = [qnsch.footprint(256, 512, False, 0, p) / 1e6 for p in (0, 1, 2)]
     gb = [qnsch.footprint(1024, 4096, True, 0, p) / 1e9 for p in (0, 1, 2)]
-    assert [round(x, 1) for x in mb] == [82.3, 118.2, 154.1]
-    assert [round(x, 2) for x in gb] == [2.32, 3.33, 4.33]
+    assert [round(x, 1) for x in mb] == [94.1, 130.1, 166.0]
+    assert [round(x, 2) for x in gb] == [2.66, 3.67, 4.68]
 
 
 def test_footprint_rejects_what_create_rejects():
