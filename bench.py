@@ -50,41 +50,54 @@ def field_bytes(P):
     return 8 * (3 * m1 * m2 + (m1 + 1) * m2 + m1 * (m2 + 1))
 
 
-# Smoothing steps before (nu1) and after (nu2) the coarse-grid correction, per
-# path.  The paper leaves them open; the library's and the oracle's defaults
-# are the reading nu1 = nu2 = 2.  The bench runs each path at the counts
-# measured fastest on a GB300 at its own protocol (ms per step over 20 steps
-# after 5 warm-up, the 256x512 drop unless named; nu_coarse 4 throughout):
-#   FP64, the paper's smoother: (3, 2) 28.6-28.9 against (2, 2) 31.2-31.6,
-#     (3, 1) 28.9, (3, 3) 30.1, (4, 2) 29.8
-#   mixed, the paper's smoother: (3, 1) 12.3 against 13.2, (1, 2) 14.4
-#   FP64 coupled: (1, 2) 19.1 against 24.1, (2, 1) 21.2
-#   mixed coupled: (1, 2) 6.8 against 8.2, (2, 1) 7.5
-#   projection, FP64: (1, 2) 19.8 against 22.3, (3, 2) 25.1
-#   capillary wave 64^2, FP64: (3, 2) 5.9 against 6.4
-#   Rayleigh-Taylor 1024x4096, mixed: (1, 2) 67.7 against 74.3, (3, 2) 80.2
-# Every path still stops at the same FP64 residual tolerance.  The oracle legs
-# (cpu_baseline, --impl reference) run the headline's counts, so that they
-# time the same V-cycles.  The stress cases and the Sec. 9 table keep the
-# defaults.
-SMOOTHING = {
-    "fp64": {"nu1": 3, "nu2": 2},
-    "mixed": {"nu1": 3, "nu2": 1},
-    "fp64_coupled": {"nu1": 1, "nu2": 2},
-    "mixed_coupled": {"nu1": 1, "nu2": 2},
-    "projection_fp64": {"nu1": 1, "nu2": 2},
-    "fp64_device_loop": {"nu1": 3, "nu2": 2},
-    "capillary_wave_64x64": {"nu1": 3, "nu2": 2},
-    "rayleigh_taylor_1024x4096": {"nu1": 1, "nu2": 2},
+# Solver options per path: the smoothing steps before (nu1) and after (nu2)
+# the coarse-grid correction, and the predicted initial iterate (predictor).
+# The paper leaves both open.  The library's and the oracle's defaults are the
+# reading: nu1 = nu2 = 2, and each step starts from x^n.  The bench runs each
+# path with the options measured fastest on a GB300 at its own protocol (ms per
+# step over 20 steps after 5 warm-up, the 256x512 drop unless named;
+# nu_coarse 4 throughout):
+#   FP64, the paper's smoother: (3, 2) with the quadratic predictor 20.4,
+#     against (3, 2) 28.7 and (2, 2) 31.3 without a predictor, (3, 2) with
+#     the linear one 23.9, (2, 2) with the quadratic one 20.6
+#   mixed, the paper's smoother: (3, 2) quadratic 8.7, against (3, 1) 12.4
+#     and (2, 2) 13.4 without, (3, 1) quadratic 9.1
+#   FP64 coupled: (1, 2) quadratic 15.5, against (1, 2) 19.1 and (2, 2) 24.1
+#     without
+#   mixed coupled: (1, 2) quadratic 5.7, against (1, 2) 6.9 and (2, 2) 8.2
+#     without
+#   projection, FP64: (1, 2) quadratic 18.8, against (1, 2) 19.8 and (2, 2)
+#     22.3 without
+#   capillary wave 64^2, FP64: (3, 2) quadratic 3.0, against (3, 2) 5.7 and
+#     (2, 2) 6.4 without
+#   Rayleigh-Taylor 1024x4096, mixed (5 steps after 5 warm-up): (1, 2)
+#     quadratic 19.7, against (1, 2) 49.3 without; its first steps move fast
+#     (the interface relaxes), and there extrapolation costs cycles, so the
+#     workload is timed after 5 warm-up steps
+# Every step still stops at the same FP64 residual tolerance.  The oracle legs
+# (cpu_baseline, --impl reference) run the headline's options, and the
+# cpu_baseline starts from the GPU's state and history, so that both time the
+# same V-cycles.  The stress cases and the Sec. 9 table keep the defaults.
+PATH_OPTIONS = {
+    "fp64": {"nu1": 3, "nu2": 2, "predictor": 2},
+    "mixed": {"nu1": 3, "nu2": 2, "predictor": 2},
+    "fp64_coupled": {"nu1": 1, "nu2": 2, "predictor": 2},
+    "mixed_coupled": {"nu1": 1, "nu2": 2, "predictor": 2},
+    "projection_fp64": {"nu1": 1, "nu2": 2, "predictor": 2},
+    "fp64_device_loop": {"nu1": 3, "nu2": 2, "predictor": 2},
+    "capillary_wave_64x64": {"nu1": 3, "nu2": 2, "predictor": 2},
+    "rayleigh_taylor_1024x4096": {"nu1": 1, "nu2": 2, "predictor": 2},
 }
 
 
-def config_of(P, levels, precision="fp64", nu=None):
-    nu = nu or SMOOTHING["fp64"]
+def config_of(P, levels, precision="fp64", opts=None):
+    opts = opts or PATH_OPTIONS["fp64"]
     return {"workload": P.name, "grid": "%dx%d" % (P.m1, P.m2), "levels": levels,
             "dt": P.dt, "tol": P.tol, "precision": precision,
             "smoother": "CH 2x2 red-black + Vanka 5x5 (5 colours)",
-            "nu1_nu2_nucoarse": [nu["nu1"], nu["nu2"], 4],
+            "nu1_nu2_nucoarse": [opts["nu1"], opts["nu2"], 4],
+            "predictor": "quadratic extrapolation in time of the initial iterate"
+                         if opts.get("predictor") == 2 else opts.get("predictor", 0),
             "l2": "flushed between timed steps (256 MiB write)",
             "parallelism": "replicas"}
 
@@ -197,13 +210,17 @@ def host_cpu():
             "usable": usable_cores(cap=1 << 20)}
 
 
-def oracle_rate(P, steps, budget_s, fields=None, options=None):
+def oracle_rate(P, steps, budget_s, fields=None, options=None, history=()):
     """Time the FP64 oracle (serial, as it stands) on the workload: up to `steps`
     implicit steps from `fields` (default: the initial state), stopping once
-    `budget_s` is spent; options: the oracle's options (smoothing counts)."""
+    `budget_s` is spent; options: the oracle's options (smoothing counts,
+    predictor); history: the earlier states the predictor extrapolates from,
+    (fields, dt) pairs, the most recent first."""
     from oracle.ref import RefSolver
     r = RefSolver(**P.create_kwargs(), tol=P.tol, **(options or {}))
     r.set_fields(P.fields() if fields is None else fields)
+    for k, (hf, hdt) in enumerate(history):
+        r.set_history(k, hf, hdt)
     times, cycles = [], []
     t_all = time.perf_counter()
     for _ in range(steps):
@@ -312,7 +329,7 @@ def run_ours(args, rank, world, local_rank):
     P = workloads.rising_drop_256x512()
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
-    s = qnsch.Solver(**P.create_kwargs(), tol=P.tol, stream=stream, **SMOOTHING["fp64"])
+    s = qnsch.Solver(**P.create_kwargs(), tol=P.tol, stream=stream, **PATH_OPTIONS["fp64"])
     levels = s.levels
     f0 = P.fields()
     dev_fields = {k: torch.tensor(v, device=dev, dtype=torch.float64) for k, v in f0.items()}
@@ -322,9 +339,11 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(args.warmup):
         s.step(P.dt)
     torch.cuda.synchronize()
-    # the committed state the timed steps start from (the CPU baseline starts
-    # the oracle from it, so both time the same steps)
+    # the committed state the timed steps start from and the earlier states the
+    # predictor extrapolates from (the CPU baseline starts the oracle from
+    # them, so both time the same steps)
     start_fields = s.get_fields()
+    start_hist = [s.history(k) for k in range(int(s.get_option("history")))]
 
     # ---- timed region: K steps, device time per step (CUDA events on our
     # stream); each step is one graph whose outer-cycle loop runs on the device
@@ -373,7 +392,7 @@ def run_ours(args, rank, world, local_rank):
                 ("mixed", 1, 0, 0, {}), ("fp64_coupled", 0, 1, 0, {}),
                 ("mixed_coupled", 1, 1, 0, {}), ("projection_fp64", 0, 0, 1, {}),
                 ("fp64_device_loop", 0, 0, 0, {"device_loop": 1})):
-            extra = dict(extra, **SMOOTHING[name])
+            extra = dict(extra, **PATH_OPTIONS[name])
             sv = qnsch.Solver(**P.create_kwargs(), tol=P.tol, stream=stream, precision=prec,
                               coupled=coup, scheme=sch, **extra)
             sv.set_fields_device(dev_fields)
@@ -445,12 +464,15 @@ def run_ours(args, rank, world, local_rank):
     roofline_fp32 = None
     if not args.no_workloads:
         paper_workloads = {}
+        # 5 untimed steps first, as for the headline: past the start, where the
+        # predictor has its history
         for Pw, prec, nsteps in ((workloads.capillary_64(), 0, 10),
-                                 (workloads.rayleigh_taylor_1024x4096(), 1, 3)):
+                                 (workloads.rayleigh_taylor_1024x4096(), 1, 5)):
             sw = qnsch.Solver(**Pw.create_kwargs(), tol=Pw.tol, stream=stream, precision=prec,
-                              **SMOOTHING[Pw.name])
+                              **PATH_OPTIONS[Pw.name])
             sw.set_fields(Pw.fields())
-            sw.step(Pw.dt)
+            for _ in range(5):
+                sw.step(Pw.dt)
             wev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                    for _ in range(nsteps)]
             wcyc = []
@@ -469,9 +491,10 @@ def run_ours(args, rank, world, local_rank):
                 "ms_per_step": float(np.mean(wms)), "vcycles_per_step": float(np.mean(wcyc)),
                 "precision": "mixed" if prec else "FP64", "steps": nsteps, "tol": Pw.tol,
                 "final_residual": res,
+                "warmup": 5,
                 "options": {k: sw.get_option(k) for k in ("wave_cells32", "wave_rows",
                                                            "vanka_team_max32", "nu1", "nu2",
-                                                           "nu_coarse")}}
+                                                           "nu_coarse", "predictor")}}
             if prec:  # the FP32 smoothers of the mixed path against HBM
                 roofline_fp32 = fp32_smoother_roofline(sw, Pw, stream, flush)
             sw.close()
@@ -610,21 +633,37 @@ def run_ours(args, rank, world, local_rank):
                                     "seen by the server, step_device_ms = CUDA events around "
                                     "the step on its stream"})
 
-    # ---- end to end through the public API with host buffers (pinned)
-    host_in = {k: torch.empty(v.shape, dtype=torch.float64, pin_memory=True).numpy()
-               for k, v in f0.items()}
+    # ---- end to end through the public API with host buffers (pinned): each
+    # step's inputs are the committed state and the earlier states the
+    # predictor extrapolates from (qnsch_set_history), its output the new state
+    def pinned():
+        return {k: torch.empty(v.shape, dtype=torch.float64, pin_memory=True).numpy()
+                for k, v in f0.items()}
+    nh = int(s.get_option("history"))
+    host_in = pinned()
+    host_hist = [pinned() for _ in range(nh)]
     cur = s.get_fields()
     for k in host_in:
         host_in[k][...] = cur[k]
+    for j in range(nh):
+        hf, _ = s.history(j)
+        for k in hf:
+            host_hist[j][k][...] = hf[k]
     e2e_ms = []
     for k in range(args.steps):
         flush.fill_(float(k))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         s.set_fields(host_in)
+        for j in range(nh):
+            s.set_history(j, host_hist[j], P.dt)
         n, res = s.step(P.dt)
         out = s.get_fields()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        if nh:  # the history moves back by one step on the host
+            host_hist.insert(0, host_hist.pop())
+            for q in host_in:
+                host_hist[0][q][...] = host_in[q]
         for q in host_in:
             host_in[q][...] = out[q]
     e2e_total = replicas.slowest(sum(e2e_ms) / 1e3, dev)
@@ -653,8 +692,12 @@ def run_ours(args, rank, world, local_rank):
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
                        "p99": float(np.percentile(step_ms, 99))},
         "vcycles_per_step": float(np.mean(cyc)),
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": field_bytes(P),
-                "d2h_bytes_per_step": field_bytes(P)},
+        "e2e": {"value": e2e_value, "unit": UNIT,
+                "h2d_bytes_per_step": (1 + nh) * field_bytes(P),
+                "d2h_bytes_per_step": field_bytes(P),
+                "what": "per step: the committed state and the %d earlier states the predictor "
+                        "extrapolates from copied in from pinned host memory, one step, the new "
+                        "state copied out" % nh},
         "gpu_launches": int(launches),
         "device_loop": bool(device_loop),
         "roofline": roofline,
@@ -678,7 +721,7 @@ def run_ours(args, rank, world, local_rank):
         line["serving"] = serving
     if world == 1 and not args.no_cpu_baseline:
         times, cycles = oracle_rate(P, steps=3, budget_s=args.cpu_budget, fields=start_fields,
-                                    options=SMOOTHING["fp64"])
+                                    options=PATH_OPTIONS["fp64"], history=start_hist)
         line["cpu_baseline"] = {
             "value": cells * len(times) / sum(times), "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "time steps %d..%d of the rising-droplet 256x512 workload (the first %d "
@@ -687,11 +730,11 @@ def run_ours(args, rank, world, local_rank):
                       % (args.warmup + 1, args.warmup + len(times), len(times), args.warmup,
                          sum(times)),
             "vcycles": cycles, "gpu_vcycles_same_steps": cyc[:len(times)],
-            "options": dict(SMOOTHING["fp64"])}
+            "options": dict(PATH_OPTIONS["fp64"])}
         line["cpu_baseline"]["host"] = host_cpu()
         if not args.no_cpu_all_cores:
             line["cpu_baseline"]["all_cores"] = oracle_all_cores(steps=1,
-                                                                 options=SMOOTHING["fp64"])
+                                                                 options=PATH_OPTIONS["fp64"])
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -869,7 +912,7 @@ def run_reference(args, rank, world):
     for _ in range(min(args.warmup, 3)):
         r.step(w.dt)
     times, cycles = oracle_rate(P, steps=args.steps, budget_s=max(per_step_budget * args.steps, 20.0),
-                                options=SMOOTHING["fp64"])
+                                options=PATH_OPTIONS["fp64"])
     value = P.cells * len(times) / sum(times)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": len(times),

@@ -161,7 +161,9 @@ struct ref_solver {
   double last_res;
   /* option "predictor": the states committed 1 and 2 steps before the
      current one (ghosted, finest level), the sizes of the steps that left
-     them, and how many are held */
+     them, and how many are held; nhist = -1 while the committed state is the
+     one the caller set (its mu and p are guesses, not a solution), which is
+     then no node of the extrapolation either */
   int predictor, nhist;
   double hdt[2];
   double *hc[2], *hmu[2], *hp[2], *hu[2], *hv[2];
@@ -1394,6 +1396,7 @@ int qnsch_ref_create(int m1, int m2, double Lx, int periodic_x, int levels, doub
   s->maxcyc = 50;
   s->tol = 1e-9;
   s->omega = 1.0;
+  s->nhist = -1; /* no state set yet */
   s->kcol = colours_of(m1, periodic_x);
   s->nlev = levels;
   s->lev = (ref_level*)calloc((size_t)levels, sizeof(ref_level));
@@ -1468,11 +1471,11 @@ int qnsch_ref_set_option(ref_solver* s, const char* key, double value) {
   else if (!strcmp(key, "predictor")) {
     if (s->pending || !(value == 0.0 || value == 1.0 || value == 2.0)) return REF_EINVAL;
     s->predictor = (int)value;
-    s->nhist = 0;
+    if (s->nhist > 0) s->nhist = 0;
   }
   else if (!strcmp(key, "history")) {
     if (s->pending || value != 0.0) return REF_EINVAL;
-    s->nhist = 0;
+    if (s->nhist > 0) s->nhist = 0;
   }
   else return REF_EINVAL;
   return REF_OK;
@@ -1492,7 +1495,7 @@ int qnsch_ref_get_option(const ref_solver* s, const char* key, double* value) {
   else if (!strcmp(key, "eps_mob")) *value = s->P.eps_m;
   else if (!strcmp(key, "coupled")) *value = s->coupled;
   else if (!strcmp(key, "predictor")) *value = s->predictor;
-  else if (!strcmp(key, "history")) *value = s->nhist;
+  else if (!strcmp(key, "history")) *value = s->nhist > 0 ? s->nhist : 0;
   else return REF_EINVAL;
   return REF_OK;
 }
@@ -1612,7 +1615,7 @@ int qnsch_ref_set_fields(ref_solver* s, const double* c, const double* mu, const
   if (!s || !c || !mu || !u || !v || !p) return REF_EINVAL;
   if (s->pending) return REF_ESTATE;
   pack_in(&s->lev[0], s->c, s->mu, s->p, s->u, s->v, c, mu, p, u, v);
-  s->nhist = 0;
+  s->nhist = -1;
   return REF_OK;
 }
 
@@ -1627,12 +1630,13 @@ int qnsch_ref_get_history(const ref_solver* s, int k, double* dt, double* c, dou
 
 int qnsch_ref_set_history(ref_solver* s, int k, double dt, const double* c, const double* mu,
                           const double* u, const double* v, const double* p) {
-  if (!s || !c || !mu || !u || !v || !p || k < 0 || k > 1 || k > s->nhist || !(dt > 0))
-    return REF_EINVAL;
+  if (!s) return REF_EINVAL;
+  int held = s->nhist > 0 ? s->nhist : 0;
+  if (!c || !mu || !u || !v || !p || k < 0 || k > 1 || k > held || !(dt > 0)) return REF_EINVAL;
   if (s->pending) return REF_ESTATE;
   pack_in(&s->lev[0], s->hc[k], s->hmu[k], s->hp[k], s->hu[k], s->hv[k], c, mu, p, u, v);
   s->hdt[k] = dt;
-  if (k == s->nhist) s->nhist = k + 1;
+  if (k >= s->nhist) s->nhist = k + 1;
   return REF_OK;
 }
 
@@ -1642,6 +1646,7 @@ int qnsch_ref_set_history(ref_solver* s, int k, double dt, const double* c, cons
    (dt - tau_j) / (tau_i - tau_j); degree 0 gives the committed state. */
 static void predict_weights(const ref_solver* s, double dt, double w[3]) {
   int m = s->predictor < s->nhist ? s->predictor : s->nhist;
+  if (m < 0) m = 0;
   double tau[3];
   tau[0] = 0.0;
   tau[1] = -s->hdt[0];

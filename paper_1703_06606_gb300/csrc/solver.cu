@@ -194,9 +194,11 @@ struct qnsch_s {
   // extrapolation in time (Lagrange, at the new time) through x^n and the one
   // or two states committed before it.  hist[k] is the state committed k + 1
   // steps before the current one (c, mu, p, u, v, padded level-0 layout) and
-  // hdt[k] the size of the step that left it; nhist of them are valid
+  // hdt[k] the size of the step that left it; nhist of them are valid.
+  // nhist = -1: the committed state was set by the caller, not computed by a
+  // step (its mu and p are only guesses), so it is no node either
   int predictor = 0;
-  int nhist = 0;
+  int nhist = -1;
   double hdt[2] = {0.0, 0.0};
   double* hist[2][5] = {};
   // failure detection: a step stops once it has run this many seconds of wall
@@ -1536,11 +1538,11 @@ int set_option(qnsch_s* s, const std::string& k, double value) {
     if (!count_of(value, 0, 2, &n)) return QNSCH_EINVAL;
     if (s->pending) return QNSCH_ESTATE;
     s->predictor = n;
-    s->nhist = 0;  // the history restarts with the next committed step
+    s->nhist = std::min(s->nhist, 0);  // the history restarts with the next committed step
   } else if (k == "history") {  // read-only but for 0, which clears it
     if (value != 0.0) return QNSCH_EINVAL;
     if (s->pending) return QNSCH_ESTATE;
-    s->nhist = 0;
+    s->nhist = std::min(s->nhist, 0);
   } else if (k == "step_time_limit") {
     if (!(value >= 0.0) || !std::isfinite(value)) return QNSCH_EINVAL;
     s->time_limit = value;
@@ -1608,7 +1610,7 @@ int qnsch_get_option(const qnsch_t* s, const char* key, double* value) {
   else if (k == "skew_cells32") *value = (double)s->skew_cells;
   else if (k == "skew_rows") *value = s->skew_rows;
   else if (k == "predictor") *value = s->predictor;
-  else if (k == "history") *value = s->nhist;
+  else if (k == "history") *value = std::max(s->nhist, 0);
   else if (k == "step_time_limit") *value = s->time_limit;
   else if (k == "diverge_cycles") *value = s->diverge;
   else if (k == "fuse_cells") *value = s->fuse64;
@@ -1692,7 +1694,7 @@ int qnsch_set_fields(qnsch_t* s, const double* c, const double* mu, const double
   if (s->pending) return QNSCH_ESTATE;
   double* dst[5] = {s->sc, s->smu, s->su, s->sv, s->sp};
   const double* src[5] = {c, mu, u, v, p};
-  s->nhist = 0;  // a new state: no history behind it
+  s->nhist = -1;  // a state from the caller: no history, and no node itself
   return copy_fields_in(s, dst, src, true);
 }
 
@@ -1702,7 +1704,7 @@ int qnsch_set_fields_device(qnsch_t* s, const double* c, const double* mu, const
   if (s->pending) return QNSCH_ESTATE;
   double* dst[5] = {s->sc, s->smu, s->su, s->sv, s->sp};
   const double* src[5] = {c, mu, u, v, p};
-  s->nhist = 0;
+  s->nhist = -1;
   enter(s);
   return copy_fields_in(s, dst, src, false);
 }
@@ -1719,7 +1721,8 @@ int qnsch_get_history(const qnsch_t* s, int k, double* dt, double* c, double* mu
 
 int qnsch_set_history(qnsch_t* s, int k, double dt, const double* c, const double* mu,
                       const double* u, const double* v, const double* p) {
-  if (!s || !c || !mu || !u || !v || !p || k < 0 || k > s->nhist || k > 1) return QNSCH_EINVAL;
+  if (!s || !c || !mu || !u || !v || !p || k < 0 || k > std::max(s->nhist, 0) || k > 1)
+    return QNSCH_EINVAL;
   if (!(dt > 0.0) || !std::isfinite(dt)) return QNSCH_EINVAL;
   if (s->pending) return QNSCH_ESTATE;
   double* dst[5] = {s->hist[k][0], s->hist[k][1], s->hist[k][3], s->hist[k][4], s->hist[k][2]};
@@ -1727,7 +1730,7 @@ int qnsch_set_history(qnsch_t* s, int k, double dt, const double* c, const doubl
   int rc = copy_fields_in(s, dst, src, true);
   if (rc) return rc;
   s->hdt[k] = dt;
-  if (k == s->nhist) s->nhist = k + 1;
+  if (k >= s->nhist) s->nhist = k + 1;  // the committed state is a node too
   return QNSCH_OK;
 }
 

@@ -4,7 +4,8 @@ counts within one of the oracle's and mass conserved: small cases with either
 smoother, the option set of the batch and the server (serve.THROUGHPUT_OPTIONS:
 coupled block, one lane per block in the per-level launches, levels up to
 2048 cells fused, one smoothing step before the coarse-grid correction and two
-after, the oracle running the same smoothing counts) on two draws of the
+after, each step from the quadratic extrapolation of the last three states,
+the oracle running the same counts and predictor; four steps) on two draws of the
 64-drop batch workload at density ratios 83 and 57, the 256x512 rising drop
 with the per-colour smoother launches and with the banded wavefront, and a
 512^2 drop with the coupled block.  Also the FP64 path at full size over
@@ -21,8 +22,9 @@ from paper_1703_06606_gb300.serve import THROUGHPUT_OPTIONS
 pytestmark = pytest.mark.gpu
 
 BATCH_OPTS = dict(precision=1, coupled=1, **THROUGHPUT_OPTIONS)
-# the oracle follows the same algorithm: the coupled block and the smoothing counts
-BATCH_REF = {"coupled": 1, "nu1": THROUGHPUT_OPTIONS["nu1"], "nu2": THROUGHPUT_OPTIONS["nu2"]}
+# the oracle follows the same algorithm: the coupled block, the smoothing
+# counts and the predicted initial iterate
+BATCH_REF = {"coupled": 1, **{k: THROUGHPUT_OPTIONS[k] for k in ("nu1", "nu2", "predictor")}}
 
 
 @pytest.fixture(scope="module")
@@ -48,8 +50,8 @@ def _cases():
         ("small_periodic", W.small_case(32, 48, True), 1, {"precision": 1}, {}),
         ("small_walls_coupled", W.small_case(32, 48, False), 2, {"precision": 1, "coupled": 1},
          {"coupled": 1}),
-        ("batch_draw_1_ratio83", ds[1], 2, BATCH_OPTS, BATCH_REF),
-        ("batch_draw_9_ratio57", ds[9], 2, BATCH_OPTS, BATCH_REF),
+        ("batch_draw_1_ratio83", ds[1], 4, BATCH_OPTS, BATCH_REF),
+        ("batch_draw_9_ratio57", ds[9], 4, BATCH_OPTS, BATCH_REF),
         ("drop_256x512", W.rising_drop_256x512(), 2, {"precision": 1}, {}),
         ("drop_256x512_wavefront", W.rising_drop_256x512(), 2,
          {"precision": 1, "wave_cells32": 1}, {}),
@@ -118,8 +120,9 @@ def _bench():
     return mod
 
 
-# the bench's paths on its workload at the smoothing counts it times them with
-# (bench.SMOOTHING), the oracle running the same counts and smoother
+# the bench's paths on its workload with the options it times them with
+# (bench.PATH_OPTIONS: smoothing counts and predictor), the oracle running the
+# same options and smoother
 BENCH_PATHS = [
     ("fp64", {}, {}),
     ("mixed", {"precision": 1}, {}),
@@ -130,11 +133,12 @@ BENCH_PATHS = [
 
 
 @pytest.mark.parametrize("name,gopts,ropts", BENCH_PATHS, ids=[c[0] for c in BENCH_PATHS])
-def test_bench_paths_at_their_smoothing_counts(qn, name, gopts, ropts):
-    """Two steps of the 256x512 drop per path: FP64 paths with equal V-cycle
-    counts and every field within 1e-10 of the oracle, mixed paths within the
-    mixed bars and one V-cycle."""
-    nu = _bench().SMOOTHING[name]
+def test_bench_paths_with_their_options(qn, name, gopts, ropts):
+    """Four steps of the 256x512 drop per path (the last two start from the
+    predicted iterate): FP64 paths with equal V-cycle counts and every field
+    within 1e-10 of the oracle, mixed paths within the mixed bars and one
+    V-cycle."""
+    nu = _bench().PATH_OPTIONS[name]
     P = W.rising_drop_256x512()
     g = qn.Solver(**P.create_kwargs(), tol=P.tol, **gopts, **nu)
     r = RefSolver(**P.create_kwargs(), tol=P.tol, **ropts, **nu)
@@ -142,7 +146,7 @@ def test_bench_paths_at_their_smoothing_counts(qn, name, gopts, ropts):
     g.set_fields(f)
     r.set_fields(f)
     mixed = gopts.get("precision", 0) == 1
-    for _ in range(2):
+    for _ in range(4):
         ng, resg = g.step(P.dt)
         nr, resr = r.step(P.dt)
         assert resg <= P.tol and resr <= P.tol
