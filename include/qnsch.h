@@ -138,7 +138,8 @@ int qnsch_footprint(const qnsch_grid* grid, int precision, size_t* bytes);
    "ch_team_max": 4096, "vanka_team_max32": 65536, "ch_team_max32": 0,
    "pdl": 1, "step_time_limit": 0, "diverge_cycles": 0, "device_loop": 0,
    "wave_cells32": 0, "wave_rows": 8, "wave_wait_cycles": 2147483648,
-   "wave_stall": 0, "skew_cells32": 0, "skew_rows": 32, "predictor": 0.
+   "wave_stall": 0, "skew_cells32": 0, "skew_rows": 32, "predictor": 0,
+   "nu1_fine": -1, "nu2_fine": -1.
    Unknown keys give QNSCH_EINVAL, and so do values out of range, which leave
    the option unchanged: NaN for any key; counts that are not integers in
    their range (nu1, nu2, nu_coarse: 0..1000; maxcyc, diverge_cycles:
@@ -165,6 +166,11 @@ int qnsch_footprint(const qnsch_grid* grid, int precision, size_t* bytes);
    out ends the step with QNSCH_ETIMEOUT, uncommitted.  wave_stall (0 or 1) is
    a test hook for that path: with 1, one wait of every wavefront launch waits
    for a count nothing reaches.
+   nu1_fine, nu2_fine (integers -1..1000; -1: nu1, nu2): the smoothing
+   steps before and after the coarse-grid correction on the finest level
+   only, so that the levels below can run fewer (nu1, nu2).  A finest level
+   with counts of its own is never fused into the single-block coarse
+   V-cycle.
    predictor (0, 1 or 2): the initial iterate of a step.  0 (the default):
    the committed state x^n.  1 or 2: the polynomial in time through x^n and
    the last one or two states committed before it (qnsch_get_history),

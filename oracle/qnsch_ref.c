@@ -154,6 +154,7 @@ struct ref_solver {
   int nlev;
   ref_level* lev;
   int nu1, nu2, nuc, maxcyc, kcol, coupled;
+  int nu1f, nu2f; /* smoothing steps on the finest level (-1: nu1, nu2) */
   double tol, omega, dt;
   int pending; /* 1 between begin_step and commit_step */
   /* committed state (finest level, ghosted) */
@@ -1105,7 +1106,9 @@ static void vcycle(ref_solver* s, int l) {
     for (int k = 0; k < nc; ++k) smooth(s, L);
     return;
   }
-  for (int k = 0; k < s->nu1; ++k) smooth(s, L);
+  int pre = (l == 0 && s->nu1f >= 0) ? s->nu1f : s->nu1;
+  int post = (l == 0 && s->nu2f >= 0) ? s->nu2f : s->nu2;
+  for (int k = 0; k < pre; ++k) smooth(s, L);
   residual(&s->P, L, s->dt, NULL);
   ref_level* C = &s->lev[l + 1];
   restrict_cell(L, C, L->c, C->c);
@@ -1138,7 +1141,7 @@ static void vcycle(ref_solver* s, int l) {
     for (int I = 1; I <= C->m1; ++I) C->fv[VI(C, I, J)] += N_v(&s->P, C, s->dt, I, J);
   vcycle(s, l + 1);
   prolong_correct(L, C);
-  for (int k = 0; k < s->nu2; ++k) smooth(s, L);
+  for (int k = 0; k < post; ++k) smooth(s, L);
 }
 
 /* mean of p removed (reading R9) */
@@ -1393,6 +1396,8 @@ int qnsch_ref_create(int m1, int m2, double Lx, int periodic_x, int levels, doub
   s->nu1 = 2;
   s->nu2 = 2;
   s->nuc = 4;
+  s->nu1f = -1;
+  s->nu2f = -1;
   s->maxcyc = 50;
   s->tol = 1e-9;
   s->omega = 1.0;
@@ -1453,6 +1458,8 @@ int qnsch_ref_set_option(ref_solver* s, const char* key, double value) {
   if (!s || !key) return REF_EINVAL;
   if (!strcmp(key, "nu1")) s->nu1 = (int)value;
   else if (!strcmp(key, "nu2")) s->nu2 = (int)value;
+  else if (!strcmp(key, "nu1_fine")) s->nu1f = (int)value;
+  else if (!strcmp(key, "nu2_fine")) s->nu2f = (int)value;
   else if (!strcmp(key, "nu_coarse")) s->nuc = (int)value;
   else if (!strcmp(key, "scheme")) {
     if (s->pending || (value != 0.0 && value != 1.0) || (value == 1.0 && s->coupled)) return REF_EINVAL;
@@ -1485,6 +1492,8 @@ int qnsch_ref_get_option(const ref_solver* s, const char* key, double* value) {
   if (!s || !key || !value) return REF_EINVAL;
   if (!strcmp(key, "nu1")) *value = s->nu1;
   else if (!strcmp(key, "nu2")) *value = s->nu2;
+  else if (!strcmp(key, "nu1_fine")) *value = s->nu1f;
+  else if (!strcmp(key, "nu2_fine")) *value = s->nu2f;
   else if (!strcmp(key, "nu_coarse")) *value = s->nuc;
   else if (!strcmp(key, "scheme")) *value = s->P.scheme;
   else if (!strcmp(key, "maxcyc")) *value = s->maxcyc;

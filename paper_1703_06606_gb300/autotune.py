@@ -53,6 +53,9 @@ CANDIDATES = {
     "nu1": [2, 3, 1],
     "nu2": [2, 3, 1],
     "nu_coarse": [4, 2, 8],
+    # the finest level's own smoothing counts (-1: nu1, nu2)
+    "nu1_fine": [-1, 2, 3],
+    "nu2_fine": [-1, 3, 2],
 }
 # a candidate's steps are cut off at this multiple of the best time per step
 CUTOFF = 20.0
@@ -63,11 +66,11 @@ MIN_GAIN = 0.005
 # 2 FP64 error form: its error levels use the FP64 thresholds)
 KNOBS = {
     0: ["vanka_team_max", "vanka_team8_max", "ch_team_max", "fuse_cells", "nu1", "nu2",
-        "nu_coarse"],
+        "nu_coarse", "nu1_fine", "nu2_fine"],
     1: ["vanka_team_max32", "ch_team_max32", "fuse_cells32", "wave_cells32", "wave_rows",
-        "skew_cells32", "skew_rows", "nu1", "nu2", "nu_coarse"],
+        "skew_cells32", "skew_rows", "nu1", "nu2", "nu_coarse", "nu1_fine", "nu2_fine"],
     2: ["vanka_team_max32", "ch_team_max32", "fuse_cells", "wave_cells32", "wave_rows",
-        "skew_cells32", "skew_rows", "nu1", "nu2", "nu_coarse"],
+        "skew_cells32", "skew_rows", "nu1", "nu2", "nu_coarse", "nu1_fine", "nu2_fine"],
 }
 
 

@@ -155,6 +155,8 @@ struct qnsch_s {
   double M, eta, eps_m;
   // options
   int nu1 = 2, nu2 = 2, nuc = 4, maxcyc = 50;
+  // smoothing steps on the finest level of the V-cycle (-1: nu1, nu2)
+  int nu1f = -1, nu2f = -1;
   double tol = 1e-9, omega = 1.0;
   // 0: FP64 FAS on the scheme itself; 1: FP64 defect correction around FP32 FAS
   // cycles on the error equation; 2: the same with FP64 error cycles
@@ -647,10 +649,17 @@ void smooth_steps(qnsch_s* s, const std::vector<Lv<T>>& Ls, const Prm<T>& P, int
 }
 
 // first level of Ls whose V-cycle runs fused in one thread block
+// smoothing steps before (pre) and after the coarse-grid correction on level l
+int nu_pre(const qnsch_s* s, int l) { return l == 0 && s->nu1f >= 0 ? s->nu1f : s->nu1; }
+int nu_post(const qnsch_s* s, int l) { return l == 0 && s->nu2f >= 0 ? s->nu2f : s->nu2; }
+
 template <typename T>
 int fused_from(const qnsch_s* s, const std::vector<Lv<T>>& Ls) {
   long long thr = sizeof(T) == 8 ? s->fuse64 : s->fuse32;
-  for (int l = 0; l < s->nlev; ++l)
+  // the fused V-cycle runs one pair of counts on all its levels: a finest
+  // level with counts of its own stays out of it
+  const bool own = nu_pre(s, 0) != s->nu1 || nu_post(s, 0) != s->nu2;
+  for (int l = own ? 1 : 0; l < s->nlev; ++l)
     if ((long long)Ls[l].m1 * Ls[l].m2 <= thr && s->nlev - l <= QN_MAX_FUSED_LEVELS) return l;
   return s->nlev;
 }
@@ -686,7 +695,7 @@ void vcycle(qnsch_s* s, const std::vector<Lv<T>>& Ls, const Prm<T>& P, int l) {
     smooth_steps<T, Form>(s, Ls, P, l, coarse_sweeps(s));
     return;
   }
-  smooth_steps<T, Form>(s, Ls, P, l, s->nu1);
+  smooth_steps<T, Form>(s, Ls, P, l, nu_pre(s, l));
   const Lv<T>& F = Ls[l];
   const Lv<T>& C = Ls[l + 1];
   qn::launch_residual<T, Form>(P, F, (double*)nullptr, s->stream);
@@ -697,7 +706,7 @@ void vcycle(qnsch_s* s, const std::vector<Lv<T>>& Ls, const Prm<T>& P, int l) {
   vcycle<T, Form>(s, Ls, P, l + 1);
   qn::launch_prolong(P, F, C, s->stream);
   qn::launch_bc_unknowns(F, s->stream);
-  smooth_steps<T, Form>(s, Ls, P, l, s->nu2);
+  smooth_steps<T, Form>(s, Ls, P, l, nu_post(s, l));
 }
 
 // fold the recorded event pairs into the totals (stream must be idle)
@@ -965,7 +974,8 @@ int cycle_graph(qnsch_s* s, const Prm<double>& P) {
     if (s->prof) {  // create the timing events before capture begins
       int pairs = 1;
       for (int l = 0; l < s->nlev; ++l)
-        pairs += (s->L[l].kcol + 2) * (l == s->nlev - 1 ? coarse_sweeps(s) : s->nu1 + s->nu2);
+        pairs += (s->L[l].kcol + 2) *
+                 (l == s->nlev - 1 ? coarse_sweeps(s) : nu_pre(s, l) + nu_post(s, l));
       while ((int)s->ev.size() < 2 * pairs && (int)s->ev.size() < MAX_PROF_EVENTS) {
         cudaEvent_t e;
         if (cudaEventCreate(&e) != cudaSuccess) {
@@ -1501,6 +1511,9 @@ int set_option(qnsch_s* s, const std::string& k, double value) {
   if (k == "nu1" || k == "nu2" || k == "nu_coarse") {
     if (!count_of(value, 0, 1000, &n)) return QNSCH_EINVAL;
     (k == "nu1" ? s->nu1 : k == "nu2" ? s->nu2 : s->nuc) = n;
+  } else if (k == "nu1_fine" || k == "nu2_fine") {
+    if (!count_of(value, -1, 1000, &n)) return QNSCH_EINVAL;
+    (k == "nu1_fine" ? s->nu1f : s->nu2f) = n;
   } else if (k == "maxcyc") {
     if (!count_of(value, 0, 1e6, &n)) return QNSCH_EINVAL;
     s->maxcyc = n;
@@ -1593,6 +1606,8 @@ int qnsch_get_option(const qnsch_t* s, const char* key, double* value) {
   std::string k(key);
   if (k == "nu1") *value = s->nu1;
   else if (k == "nu2") *value = s->nu2;
+  else if (k == "nu1_fine") *value = s->nu1f;
+  else if (k == "nu2_fine") *value = s->nu2f;
   else if (k == "nu_coarse") *value = s->nuc;
   else if (k == "maxcyc") *value = s->maxcyc;
   else if (k == "tol") *value = s->tol;

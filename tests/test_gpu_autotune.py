@@ -23,7 +23,7 @@ def test_tuned_options_keep_the_step(qn):
     cand = {"vanka_team_max32": [131072, 0], "ch_team_max32": [0, 4096],
             "fuse_cells32": [512, 2048], "wave_cells32": [0, 1024], "wave_rows": [8, 4],
             "skew_cells32": [0, 1024], "skew_rows": [32, 4], "nu1": [2], "nu2": [2],
-            "nu_coarse": [4]}
+            "nu_coarse": [4], "nu1_fine": [-1], "nu2_fine": [-1]}
     best, t, hist = autotune.tune(P, precision=1, coupled=1, steps=2, warmup=1, candidates=cand)
     assert t is not None and t > 0 and len(hist) >= 4
     assert set(best) == set(autotune.KNOBS[1])

@@ -14,7 +14,8 @@ MEMBERS = {"fuse_cells": "fuse64", "fuse_cells32": "fuse32", "vanka_team_max": "
            "precision": "precision", "diverge_cycles": "diverge", "device_loop": "device_loop",
            "wave_cells32": "wave_cells", "wave_rows": "wave_rows", "wave_stall": "wave_stall",
            "vanka_team8_max": "team8_max", "nu1": "nu1", "nu2": "nu2", "nu_coarse": "nuc",
-           "skew_cells32": "skew_cells", "skew_rows": "skew_rows", "predictor": "predictor"}
+           "skew_cells32": "skew_cells", "skew_rows": "skew_rows", "predictor": "predictor",
+           "nu1_fine": "nu1f", "nu2_fine": "nu2f"}
 
 
 def _header_defaults():
@@ -27,7 +28,7 @@ def _solver_defaults():
     txt = open(os.path.join(ROOT, "paper_1703_06606_gb300", "csrc", "solver.cu")).read()
     out = {}
     for member in MEMBERS.values():
-        m = re.search(r"\b%s\s*=\s*([0-9]+)\s*[,;]" % member, txt)
+        m = re.search(r"\b%s\s*=\s*(-?[0-9]+)\s*[,;]" % member, txt)
         assert m, member
         out[member] = int(m.group(1))
     return out
