@@ -133,7 +133,7 @@ int qnsch_footprint(const qnsch_grid* grid, int precision, size_t* bytes);
    longest side n exceeds 4 cells gets nu_coarse * ceil(n/4)^2), "tol": 1e-9,
    "maxcyc": 50, "omega_vanka": 1, "M": Cn, "eta_st": eta(rho1, rho2),
    "eps_mob": Cn, "precision": 0, "graphs": 1, "fuse_cells": 128,
-   "fuse_cells32": 512, "coupled": 0, "scheme": 0, "vanka_team_max": 8192,
+   "fuse_cells32": 512, "fuse_ctas": 1, "coupled": 0, "scheme": 0, "vanka_team_max": 8192,
    "vanka_team8_max": 0,
    "ch_team_max": 4096, "vanka_team_max32": 65536, "ch_team_max32": 0,
    "pdl": 1, "step_time_limit": 0, "diverge_cycles": 0, "device_loop": 0,
@@ -143,7 +143,8 @@ int qnsch_footprint(const qnsch_grid* grid, int precision, size_t* bytes);
    Unknown keys give QNSCH_EINVAL, and so do values out of range, which leave
    the option unchanged: NaN for any key; counts that are not integers in
    their range (nu1, nu2, nu_coarse: 0..1000; maxcyc, diverge_cycles:
-   0..10^6; precision: 0..2; scheme: 0..1; fuse_cells, fuse_cells32 and the
+   0..10^6; precision: 0..2; scheme: 0..1; fuse_ctas: 1, 2, 4, 8 or 16;
+   fuse_cells, fuse_cells32 and the
    four team thresholds: 0..2^31 - 1); tol or step_time_limit negative or
    infinite; omega_vanka, M, eta_st or eps_mob not positive and finite.
    step_time_limit (seconds, >= 0; 0: none): before each outer cycle of a
@@ -237,8 +238,14 @@ int qnsch_footprint(const qnsch_grid* grid, int precision, size_t* bytes);
    separate sweeps stall (the CH/NS coupling through (alpha/Pe) div(m grad(mu +
    alpha p)) grows like 1/h^2).
    fuse_cells / fuse_cells32: the V-cycle on every FP64 / FP32 level with at
-   most this many cells runs in one thread block, one launch for all of them
-   (same arithmetic and order as the per-level launches; 0 disables).
+   most this many cells runs in one launch for all of them (same arithmetic
+   and order as the per-level launches; 0 disables).
+   fuse_ctas: that launch is one thread block (1) or one thread-block cluster
+   of fuse_ctas blocks on as many SMs, its colour steps separated by the
+   cluster barrier.  Sizes above 8 need the non-portable cluster size; the
+   handle keeps the largest size not above the one asked for that the current
+   device can launch (read it back with qnsch_get_option).  Set it outside
+   stream capture: it queries the runtime.
    precision 0: FAS V-cycles in FP64 on the scheme itself.
    precision 1: mixed.  Each outer cycle forms the FP64 residual r = -N(x),
      runs one FAS V-cycle in FP32 on the error equation N(x + e) - N(x) = r

@@ -1473,11 +1473,12 @@ __global__ void k_prolong(Prm<T> P, Lv<T> F, Lv<T> C) {
 }
 
 // --------------------------------------------------------------------------
-// the coarse end of a V-cycle in one thread block: levels small enough for one
-// SM run their smoothing colours, residuals, transfers and ghost fills as
-// block-stride loops separated by __syncthreads(), one launch instead of
-// dozens.  Per-cell work is the same device code as the grid kernels above,
-// in the same colour order, so the results are the same.
+// the coarse end of a V-cycle in one launch: levels small enough for one SM,
+// or for one thread-block cluster of up to 16 SMs, run their smoothing
+// colours, residuals, transfers and ghost fills as group-stride loops
+// separated by group barriers (__syncthreads(), or the cluster barrier), one
+// launch instead of dozens.  Per-cell work is the same device code as the grid
+// kernels above, in the same colour order, so the results are the same.
 // --------------------------------------------------------------------------
 // coarse base X_H = R X_h (cells: 4-mean; edges: 2 coincident fine edges), one entry
 template <typename T>
@@ -1509,6 +1510,29 @@ __device__ __forceinline__ void bc_base_cell(const Lv<T>& L, int I, int J) {
   fill_v_ghost(L, L.Bv, I, J);
 }
 
+// The fused V-cycle runs in one thread block or in one thread-block cluster of
+// gridDim.x blocks (the grid is the cluster).  Its loops and colour steps go
+// over a rank of the whole group.  Warps are interleaved across the blocks:
+// rank = ((warp * blocks + block) * 32 + lane), so the first 4 x blocks warps
+// of a colour step sit on distinct SM sub-partitions (warp w of a block runs on
+// sub-partition w mod 4), each of which owns one FP64 pipe.  The low five bits
+// of the rank are the hardware lane, so four-lane teams stay inside a warp.
+// One block: the rank is threadIdx.x and the step barrier is __syncthreads().
+// A cluster: the barrier is the hardware cluster barrier, whose release and
+// acquire order every block's global-memory writes before the next step's
+// reads; every thread of the cluster reaches every barrier.
+__device__ __forceinline__ int grp_rank() {
+  return (((threadIdx.x >> 5) * gridDim.x + blockIdx.x) << 5) | (threadIdx.x & 31);
+}
+__device__ __forceinline__ int grp_size() { return gridDim.x * blockDim.x; }
+__device__ __forceinline__ void grp_sync() {
+  if (gridDim.x == 1) {
+    __syncthreads();
+  } else {
+    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+  }
+}
+
 template <typename T>
 struct CoarseLevels {
   Lv<T> L[QN_MAX_FUSED_LEVELS];
@@ -1519,7 +1543,7 @@ struct CoarseLevels {
 template <typename T>
 __device__ __forceinline__ void bc_unknowns_block(const Lv<T>& L) {
   int n = 4 * (L.m1 + 3) + 4 * (L.m2 + 3);
-  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+  for (int t = grp_rank(); t < n; t += grp_size()) {
     int I, J;
     if (!frame_pos(t, L.m1, L.m2, I, J)) continue;
     fill_cell_ghost(L, L.c, I, J);
@@ -1529,7 +1553,7 @@ __device__ __forceinline__ void bc_unknowns_block(const Lv<T>& L) {
     fill_u_ghost(L, L.u, I, J);
     fill_v_ghost(L, L.v, I, J);
   }
-  __syncthreads();
+  grp_sync();
 }
 
 // --------------------------------------------------------------------------
@@ -1950,7 +1974,8 @@ __global__ void __launch_bounds__(SNT) k_vanka_team(Prm<T> P, Lv<T> L, int colou
   vanka_team<T, Form>(P, L, i, j, ok, omega);
 }
 
-// teams of four lanes while the colour fits in four warps (one per sub-partition)
+// teams of four lanes while the colour fits in four warps per block of the
+// fused group (one warp per sub-partition)
 constexpr int QN_TEAM_MAX_SLOTS = 32;
 
 template <typename T, class Form>
@@ -1961,10 +1986,10 @@ __device__ void smooth_block(const Prm<T>& P, const Lv<T>& L, T omega, int coupl
     // over the Vanka colours, pressure Gauss-Seidel red-black
     const int mpr = (L.m1 + 1) / 2;
     // four lanes per cell while a colour fits the block in one pass
-    const bool cteam = 4 * mpr * L.m2 <= (int)blockDim.x;
+    const bool cteam = 4 * mpr * L.m2 <= grp_size();
     for (int col = 0; col < 2; ++col) {
       if (cteam) {
-        int t = threadIdx.x, sl = t >> 2, j = 1, i = 1;
+        int t = grp_rank(), sl = t >> 2, j = 1, i = 1;
         bool ok = false;
         if (sl < mpr * L.m2) {
           j = sl / mpr + 1;
@@ -1974,18 +1999,18 @@ __device__ void smooth_block(const Prm<T>& P, const Lv<T>& L, T omega, int coupl
         if (!ok) i = j = 1;
         if ((t & ~31) < 4 * mpr * L.m2) ch_team<T, Form>(P, L, i, j, ok);  // warp-uniform
       } else {
-        for (int t = threadIdx.x; t < mpr * L.m2; t += blockDim.x) {
+        for (int t = grp_rank(); t < mpr * L.m2; t += grp_size()) {
           int j = t / mpr + 1;
           int i = (((col - j) & 1) ? 1 : 2) + 2 * (t % mpr);
           if (i <= L.m1) ch_cell<T, Form>(P, L, i, j);
         }
       }
-      __syncthreads();
+      grp_sync();
     }
     for (int col = 0; col < kcol; ++col) {
       ColourSlots cs = vanka_slots(L, col);
-      if (sizeof(T) == 8 && cs.n <= QN_TEAM_MAX_SLOTS) {  // one warp per sub-partition
-        int t = threadIdx.x;
+      if (sizeof(T) == 8 && cs.n <= QN_TEAM_MAX_SLOTS * (int)gridDim.x) {  // one warp per sub-partition
+        int t = grp_rank();
         if ((t & ~31) < 4 * cs.n) {  // warp-uniform: the warp holds at least one team
           int i = 1, j = 1;
           bool ok = (t >> 2) < cs.n && vanka_slot_cell(L, col, cs, t >> 2, i, j);
@@ -1993,16 +2018,16 @@ __device__ void smooth_block(const Prm<T>& P, const Lv<T>& L, T omega, int coupl
           vanka4_team<T>(P, L, i, j, ok, omega);
         }
       } else {
-        for (int t = threadIdx.x; t < cs.n; t += blockDim.x) {
+        for (int t = grp_rank(); t < cs.n; t += grp_size()) {
           int i, j;
           if (vanka_slot_cell(L, col, cs, t, i, j)) vanka4_cell<T, Form>(P, L, i, j, omega);
         }
       }
-      __syncthreads();
+      grp_sync();
     }
     for (int col = 0; col < 2; ++col) {
       if (cteam) {
-        int t = threadIdx.x, sl = t >> 2, j = 1, i = 1;
+        int t = grp_rank(), sl = t >> 2, j = 1, i = 1;
         bool ok = false;
         if (sl < mpr * L.m2) {
           j = sl / mpr + 1;
@@ -2012,21 +2037,21 @@ __device__ void smooth_block(const Prm<T>& P, const Lv<T>& L, T omega, int coupl
         if (!ok) i = j = 1;
         if ((t & ~31) < 4 * mpr * L.m2) pgs_team<T>(P, L, i, j, ok);  // warp-uniform
       } else {
-        for (int t = threadIdx.x; t < mpr * L.m2; t += blockDim.x) {
+        for (int t = grp_rank(); t < mpr * L.m2; t += grp_size()) {
           int j = t / mpr + 1;
           int i = (((col - j) & 1) ? 1 : 2) + 2 * (t % mpr);
           if (i <= L.m1) pgs_cell<T>(P, L, i, j);
         }
       }
-      __syncthreads();
+      grp_sync();
     }
   } else {  // primitive method (full iterate or error equation)
   if (coupled) {
     for (int col = 0; col < kcol; ++col) {
       ColourSlots cs = vanka_slots(L, col);
       // four lanes per block while the colour fits the block in one pass
-      if (4 * cs.n <= (int)blockDim.x) {
-        int t = threadIdx.x;
+      if (4 * cs.n <= grp_size()) {
+        int t = grp_rank();
         if ((t & ~31) < 4 * cs.n) {  // warp-uniform: the warp holds at least one team
           int i = 1, j = 1;
           bool ok = (t >> 2) < cs.n && vanka_slot_cell(L, col, cs, t >> 2, i, j);
@@ -2034,12 +2059,12 @@ __device__ void smooth_block(const Prm<T>& P, const Lv<T>& L, T omega, int coupl
           coupled_team<T, Form>(P, L, i, j, ok, omega);
         }
       } else {
-        for (int t = threadIdx.x; t < cs.n; t += blockDim.x) {
+        for (int t = grp_rank(); t < cs.n; t += grp_size()) {
           int i, j;
           if (vanka_slot_cell(L, col, cs, t, i, j)) coupled_cell<T, Form>(P, L, i, j, omega);
         }
       }
-      __syncthreads();
+      grp_sync();
     }
     return;
   }
@@ -2047,8 +2072,8 @@ __device__ void smooth_block(const Prm<T>& P, const Lv<T>& L, T omega, int coupl
   constexpr bool team_ok = std::is_same<Form, FullForm>::value && sizeof(T) == 8;
   constexpr bool vteam_ok = team_ok || std::is_same<Form, ErrForm>::value;
   for (int col = 0; col < 2; ++col) {
-    if (vteam_ok && 4 * mpr * L.m2 <= (int)blockDim.x) {
-      int t = threadIdx.x;
+    if (vteam_ok && 4 * mpr * L.m2 <= grp_size()) {
+      int t = grp_rank();
       if ((t & ~31) < 4 * mpr * L.m2) {  // warp-uniform
         int sl = t >> 2, j = 1, i = 1;
         bool ok = false;
@@ -2061,21 +2086,21 @@ __device__ void smooth_block(const Prm<T>& P, const Lv<T>& L, T omega, int coupl
         ch_team<T, Form>(P, L, i, j, ok);
       }
     } else {
-      for (int t = threadIdx.x; t < mpr * L.m2; t += blockDim.x) {
+      for (int t = grp_rank(); t < mpr * L.m2; t += grp_size()) {
         int j = t / mpr + 1;
         int i = (((col - j) & 1) ? 1 : 2) + 2 * (t % mpr);
         if (i <= L.m1) ch_cell<T, Form>(P, L, i, j);
       }
     }
-    __syncthreads();
+    grp_sync();
   }
   for (int col = 0; col < kcol; ++col) {
     ColourSlots cs = vanka_slots(L, col);
-    // FP64: while the colour fits four warps (one per sub-partition); the
-    // latency-bound FP32 error levels: while it fits the block in one pass
-    const int team_slots = team_ok ? QN_TEAM_MAX_SLOTS : (int)blockDim.x / 4;
-    if (team_ok && team8 && 8 * cs.n <= (int)blockDim.x) {  // eight lanes per block
-      int t = threadIdx.x;
+    // FP64: while the colour fits one warp per sub-partition of the group; the
+    // latency-bound FP32 error levels: while it fits the group in one pass
+    const int team_slots = team_ok ? QN_TEAM_MAX_SLOTS * (int)gridDim.x : grp_size() / 4;
+    if (team_ok && team8 && 8 * cs.n <= grp_size()) {  // eight lanes per block
+      int t = grp_rank();
       if ((t & ~31) < 8 * cs.n) {  // warp-uniform: the warp holds at least one team
         int i = 1, j = 1;
         bool ok = (t >> 3) < cs.n && vanka_slot_cell(L, col, cs, t >> 3, i, j);
@@ -2083,7 +2108,7 @@ __device__ void smooth_block(const Prm<T>& P, const Lv<T>& L, T omega, int coupl
         if constexpr (team_ok) vanka_team8<double>(P, L, i, j, ok, omega);
       }
     } else if (vteam_ok && cs.n <= team_slots) {
-      int t = threadIdx.x;
+      int t = grp_rank();
       if ((t & ~31) < 4 * cs.n) {  // warp-uniform: the warp holds at least one team
         int i = 1, j = 1;
         bool ok = (t >> 2) < cs.n && vanka_slot_cell(L, col, cs, t >> 2, i, j);
@@ -2091,12 +2116,12 @@ __device__ void smooth_block(const Prm<T>& P, const Lv<T>& L, T omega, int coupl
         vanka_team<T, Form>(P, L, i, j, ok, omega);
       }
     } else {
-      for (int t = threadIdx.x; t < cs.n; t += blockDim.x) {
+      for (int t = grp_rank(); t < cs.n; t += grp_size()) {
         int i, j;
         if (vanka_slot_cell(L, col, cs, t, i, j)) vanka_cell<T, Form>(P, L, i, j, omega);
       }
     }
-    __syncthreads();
+    grp_sync();
   }
   }  // primitive method
 }
@@ -2112,42 +2137,42 @@ __global__ void __launch_bounds__(NT) k_coarse_vcycle(Prm<T> P, CoarseLevels<T> 
     for (int l = 1; l < n; ++l) {
       const Lv<T>& F = C.L[l - 1];
       const Lv<T>& G = C.L[l];
-      for (int t = threadIdx.x; t < (G.m1 + 1) * (G.m2 + 1); t += NT)
+      for (int t = grp_rank(); t < (G.m1 + 1) * (G.m2 + 1); t += grp_size())
         restrict_base_cell(F, G, t % (G.m1 + 1), t / (G.m1 + 1));
-      __syncthreads();
+      grp_sync();
       const int nf = 4 * (G.m1 + 3) + 4 * (G.m2 + 3);
-      for (int t = threadIdx.x; t < nf; t += NT) {
+      for (int t = grp_rank(); t < nf; t += grp_size()) {
         int I, J;
         if (frame_pos(t, G.m1, G.m2, I, J)) bc_base_cell(G, I, J);
       }
-      __syncthreads();
+      grp_sync();
     }
   }
   for (int l = 0; l < n - 1; ++l) {
     const Lv<T>& F = C.L[l];
     const Lv<T>& G = C.L[l + 1];
     for (int s = 0; s < nu1; ++s) smooth_block<T, Form>(P, F, omega, coupled, team8);
-    for (int t = threadIdx.x; t < F.m1 * F.m2; t += NT)
+    for (int t = grp_rank(); t < F.m1 * F.m2; t += grp_size())
       residual_cell<T, 0, Form>(P, F, t % F.m1 + 1, t / F.m1 + 1, dummy);
-    __syncthreads();
-    for (int t = threadIdx.x; t < (G.m1 + 1) * (G.m2 + 1); t += NT)
+    grp_sync();
+    for (int t = grp_rank(); t < (G.m1 + 1) * (G.m2 + 1); t += grp_size())
       restrict_state_cell(P, F, G, t % (G.m1 + 1), t / (G.m1 + 1));
-    __syncthreads();
+    grp_sync();
     bc_unknowns_block(G);
-    for (int t = threadIdx.x; t < G.m1 * G.m2; t += NT)
+    for (int t = grp_rank(); t < G.m1 * G.m2; t += grp_size())
       restrict_res_cell(F, G, t % G.m1 + 1, t / G.m1 + 1);
-    __syncthreads();
-    for (int t = threadIdx.x; t < G.m1 * G.m2; t += NT)
+    grp_sync();
+    for (int t = grp_rank(); t < G.m1 * G.m2; t += grp_size())
       residual_cell<T, 1, Form>(P, G, t % G.m1 + 1, t / G.m1 + 1, dummy);
-    __syncthreads();
+    grp_sync();
   }
   for (int s = 0; s < nuc; ++s) smooth_block<T, Form>(P, C.L[n - 1], omega, coupled, team8);
   for (int l = n - 2; l >= 0; --l) {
     const Lv<T>& F = C.L[l];
     const Lv<T>& G = C.L[l + 1];
-    for (int t = threadIdx.x; t < F.m1 * F.m2; t += NT)
+    for (int t = grp_rank(); t < F.m1 * F.m2; t += grp_size())
       prolong_cell(P, F, G, t % F.m1 + 1, t / F.m1 + 1);
-    __syncthreads();
+    grp_sync();
     bc_unknowns_block(F);
     for (int s = 0; s < nu2; ++s) smooth_block<T, Form>(P, F, omega, coupled, team8);
   }
@@ -2806,15 +2831,76 @@ void launch_vanka(const Prm<T>& P, const Lv<T>& L, int colour, T omega, cudaStre
 }
 template <typename T, class Form>
 void launch_coarse_vcycle(const Prm<T>& P, const Lv<T>* levels, int n, int nu1, int nu2, int nuc,
-                          int kcol, T omega, int coupled, cudaStream_t s, int team8) {
+                          int kcol, T omega, int coupled, cudaStream_t s, int team8, int ctas) {
   CoarseLevels<T> C;
   C.n = n;
   C.base = std::is_same<Form, ErrForm>::value;
   for (int l = 0; l < n; ++l) C.L[l] = levels[l];
   constexpr int NT = sizeof(T) == 8 ? 256 : 512;
-  qlaunch(&k_coarse_vcycle<T, Form, NT>, 1, NT, 0, s, P, C, nu1, nu2, nuc, kcol, omega, coupled,
-          team8);
+  if (ctas <= 1) {
+    qlaunch(&k_coarse_vcycle<T, Form, NT>, 1, NT, 0, s, P, C, nu1, nu2, nuc, kcol, omega, coupled,
+            team8);
+  } else {  // one cluster of ctas blocks (a size coarse_cluster_blocks accepted)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ctas);
+    cfg.blockDim = dim3(NT);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = ctas;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = g_pdl ? 2 : 1;
+    cudaLaunchKernelEx(&cfg, &k_coarse_vcycle<T, Form, NT>, P, C, nu1, nu2, nuc, kcol, omega,
+                       coupled, team8);
+  }
   ++g_launches;
+}
+
+// largest cluster of at most `ctas` blocks (a power of two) in which the fused
+// V-cycle of this form can run on the current device: a cluster is placed on
+// the SMs of one GPC as a whole, and sizes above 8 need the non-portable
+// cluster attribute, which the function must accept
+template <typename T, class Form>
+static int cluster_fit(int ctas) {
+  constexpr int NT = sizeof(T) == 8 ? 256 : 512;
+  auto kern = &k_coarse_vcycle<T, Form, NT>;
+  if (ctas > 8 &&
+      cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+    cudaGetLastError();
+    ctas = 8;
+  }
+  for (; ctas > 1; ctas >>= 1) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ctas);
+    cfg.blockDim = dim3(NT);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = ctas;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) == cudaSuccess && nclusters > 0)
+      break;
+    cudaGetLastError();
+  }
+  return ctas < 1 ? 1 : ctas;
+}
+
+int coarse_cluster_blocks(int ctas) {
+  int c = 1;
+  while (c < 16 && 2 * c <= ctas) c *= 2;
+  if (c == 1) return 1;
+  c = cluster_fit<double, FullForm>(c);
+  c = cluster_fit<double, ErrForm>(c);
+  c = cluster_fit<float, ErrForm>(c);
+  c = cluster_fit<double, ProjForm>(c);
+  return c;
 }
 
 template <typename T, class Form>
@@ -3130,7 +3216,7 @@ int partial_rows_needed(int m1, int m2) {
 
 #define QN_INSTANTIATE_FORM(T, F)                                                                \
   template void launch_coarse_vcycle<T, F>(const Prm<T>&, const Lv<T>*, int, int, int, int, int,  \
-                                           T, int, cudaStream_t, int);                           \
+                                           T, int, cudaStream_t, int, int);                      \
   template void launch_coupled<T, F>(const Prm<T>&, const Lv<T>&, int, T, cudaStream_t, int);     \
   template void launch_residual<T, F>(const Prm<T>&, const Lv<T>&, double*, cudaStream_t);       \
   template void launch_add_op<T, F>(const Prm<T>&, const Lv<T>&, cudaStream_t);                  \
@@ -3177,7 +3263,8 @@ template int launch_skew<double, ErrForm>(const Prm<double>&, const Lv<double>&,
 template void launch_residual<double, ProjForm>(const Prm<double>&, const Lv<double>&, double*,
                                                 cudaStream_t);
 template void launch_coarse_vcycle<double, ProjForm>(const Prm<double>&, const Lv<double>*, int, int,
-                                                     int, int, int, double, int, cudaStream_t, int);
+                                                     int, int, int, double, int, cudaStream_t, int,
+                                                     int);
 template void launch_add_op<double, ProjForm>(const Prm<double>&, const Lv<double>&, cudaStream_t);
 template void launch_ch<double, ProjForm>(const Prm<double>&, const Lv<double>&, int, cudaStream_t,
                                           int);

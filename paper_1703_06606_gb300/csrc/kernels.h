@@ -62,12 +62,19 @@ int launch_skew(const Prm<T>& P, const Lv<T>& L, int nsteps, int coupled, int ro
 // n padded elements starting `off` elements before its origin pointer
 void launch_predict(double* const x[5], double* const a[5], double* const b[5],
                     double* const c[5], const double w[3], size_t n, int off, cudaStream_t s);
-// the V-cycle on levels[0..n-1] (levels[0] is its finest) in one thread block
-// (team8: the FP64 full-iterate Vanka blocks use eight lanes where a colour
-// fits the block in one pass)
+// the V-cycle on levels[0..n-1] (levels[0] is its finest) in one launch: one
+// thread block (ctas = 1) or one thread-block cluster of ctas blocks, a size
+// coarse_cluster_blocks returned (team8: the FP64 full-iterate Vanka blocks use
+// eight lanes where a colour fits the group in one pass)
 template <typename T, class Form>
 void launch_coarse_vcycle(const Prm<T>& P, const Lv<T>* levels, int n, int nu1, int nu2, int nuc,
-                          int kcol, T omega, int coupled, cudaStream_t s, int team8 = 0);
+                          int kcol, T omega, int coupled, cudaStream_t s, int team8 = 0,
+                          int ctas = 1);
+// the largest power of two not above ctas (and not above 16) at which every
+// form of the fused V-cycle launches as one cluster on the current device; 1
+// when ctas < 2 or no cluster fits.  Queries the runtime: call it outside
+// stream capture
+int coarse_cluster_blocks(int ctas);
 // one colour of the coupled 7x7 smoother (option "coupled")
 template <typename T, class Form>
 void launch_coupled(const Prm<T>& P, const Lv<T>& L, int colour, T omega, cudaStream_t s,

@@ -164,6 +164,9 @@ struct qnsch_s {
   // levels with at most this many cells run as one fused single-block V-cycle
   // (0: never); separate thresholds for FP64 and FP32 levels
   int fuse64 = 128, fuse32 = 512;
+  // blocks of the fused V-cycle's launch: 1, or a thread-block cluster of that
+  // many blocks (a power of two up to 16 that the device accepts)
+  int fuse_ctas = 1;
   // 0: the paper's separate CH and Vanka sweeps; 1: the coupled 7x7 block
   int coupled = 0;
   // 0: the primitive method (Sec. 6.1); 1: the projection method (Sec. 6.2)
@@ -687,7 +690,7 @@ void vcycle(qnsch_s* s, const std::vector<Lv<T>>& Ls, const Prm<T>& P, int l) {
     int q = prof_open(s, PK_COARSE, visits);
     qn::launch_coarse_vcycle<T, Form>(P, &Ls[l], s->nlev - l, s->nu1, s->nu2, coarse_sweeps(s),
                                       s->kcol, (T)s->omega, s->coupled, s->stream,
-                                      s->team8_max > 0 ? 1 : 0);
+                                      s->team8_max > 0 ? 1 : 0, s->fuse_ctas);
     prof_close(s, q);
     return;
   }
@@ -1570,6 +1573,10 @@ int set_option(qnsch_s* s, const std::string& k, double value) {
      : k == "vanka_team_max" ? s->team_max : k == "ch_team_max" ? s->ch_team_max
      : k == "ch_team_max32" ? s->ch_team_max32 : k == "vanka_team8_max" ? s->team8_max
      : s->team_max32) = n;
+  } else if (k == "fuse_ctas") {
+    if (!count_of(value, 1, 16, &n) || (n & (n - 1))) return QNSCH_EINVAL;
+    // the largest cluster at most n blocks wide that this device can launch
+    s->fuse_ctas = qn::coarse_cluster_blocks(n);
   } else if (k == "coupled") {
     if (value != 0.0 && s->scheme) return QNSCH_EINVAL;  // a primitive-method smoother
     s->coupled = value != 0.0;
@@ -1629,6 +1636,7 @@ int qnsch_get_option(const qnsch_t* s, const char* key, double* value) {
   else if (k == "step_time_limit") *value = s->time_limit;
   else if (k == "diverge_cycles") *value = s->diverge;
   else if (k == "fuse_cells") *value = s->fuse64;
+  else if (k == "fuse_ctas") *value = s->fuse_ctas;
   else if (k == "coupled") *value = s->coupled;
   else if (k == "fuse_cells32") *value = s->fuse32;
   else if (k == "scheme") *value = s->scheme;
