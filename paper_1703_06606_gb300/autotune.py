@@ -40,6 +40,8 @@ CANDIDATES = {
     "vanka_team_max32": [65536, 0, 8192, 131072, 1 << 30],
     "ch_team_max32": [0, 4096],
     "fuse_cells32": [512, 128, 2048],
+    # blocks of the fused V-cycle's launch (1, or one thread-block cluster)
+    "fuse_ctas": [1, 16, 4],
     # the banded wavefront on the error-equation levels: from which level size
     # (0: never) and with how many rows per band (its tile height)
     "wave_cells32": [0, 1 << 20, 1 << 16],
@@ -65,12 +67,12 @@ MIN_GAIN = 0.005
 # the options that shape the launches of each precision (0 FP64, 1 mixed,
 # 2 FP64 error form: its error levels use the FP64 thresholds)
 KNOBS = {
-    0: ["vanka_team_max", "vanka_team8_max", "ch_team_max", "fuse_cells", "nu1", "nu2",
-        "nu_coarse", "nu1_fine", "nu2_fine"],
-    1: ["vanka_team_max32", "ch_team_max32", "fuse_cells32", "wave_cells32", "wave_rows",
-        "skew_cells32", "skew_rows", "nu1", "nu2", "nu_coarse", "nu1_fine", "nu2_fine"],
-    2: ["vanka_team_max32", "ch_team_max32", "fuse_cells", "wave_cells32", "wave_rows",
-        "skew_cells32", "skew_rows", "nu1", "nu2", "nu_coarse", "nu1_fine", "nu2_fine"],
+    0: ["vanka_team_max", "vanka_team8_max", "ch_team_max", "fuse_cells", "fuse_ctas", "nu1",
+        "nu2", "nu_coarse", "nu1_fine", "nu2_fine"],
+    1: ["vanka_team_max32", "ch_team_max32", "fuse_cells32", "fuse_ctas", "wave_cells32",
+        "wave_rows", "skew_cells32", "skew_rows", "nu1", "nu2", "nu_coarse", "nu1_fine", "nu2_fine"],
+    2: ["vanka_team_max32", "ch_team_max32", "fuse_cells", "fuse_ctas", "wave_cells32",
+        "wave_rows", "skew_cells32", "skew_rows", "nu1", "nu2", "nu_coarse", "nu1_fine", "nu2_fine"],
 }
 
 
