@@ -1274,6 +1274,37 @@ __global__ void k_frozen_coef2(Lv<T> L) {
   if (i >= 1) L.Dvv[k] = T(0.5) * ((L.Qy[k] - L.Qy[k - 1]) + (L.Sy[k + W] - L.Sy[k])) * L.ih;
 }
 
+// The assembled stencil of one momentum row of (pm-num-mx) at edge k (mom_asm):
+// s the stride along the edge normal, t across it; S the cell-centred and Q the
+// vertex convection coefficients, Tf = D c^n / 2 on the edge, t1 the time
+// term's coefficient T1.  With the differences of the row written out,
+//   conv = 1/2 h^-1 (S[k+s] (a[k+s] - a) - S[k] (a - a[k-s]) ... )  and
+//   visc = -h^-2/Re ((4/3)(vis[k+s] (a[k+s] - a) - vis[k] (a - a[k-s]))
+//                    + Av[k] (a[k+t] - a) - Av[k-t] (a - a[k-t])) + cross terms,
+// each neighbour's coefficient is the sum of its convective and viscous
+// parts, and the edge's own coefficient is minus their sum plus t1.  Wall
+// edges keep the undoubled coefficients: the row reads the reflected ghosts.
+template <typename T>
+__device__ __forceinline__ void assemble_row(const Prm<T>& P, const Lv<T>& L, int k, int s, int t,
+                                             T t1, const T* S, const T* Q, const T* Tf, T* C,
+                                             T* aP, T* aM, T* tP, T* tM, T* M0, T* M1) {
+  const T* vis = L.visn;
+  const T hc = T(0.5) * L.ih, hv = P.iRe * L.ih2, f43 = T(4.0 / 3.0);
+  T vl = vis[k], vr = vis[k + s];
+  T ap = hc * S[k + s] - f43 * hv * vr;
+  T am = -hc * S[k] - f43 * hv * vl;
+  T tp = hc * Q[k] - hv * L.Av[k];
+  T tm = -hc * Q[k - t] - hv * L.Av[k - t];
+  aP[k] = ap;
+  aM[k] = am;
+  tP[k] = tp;
+  tM[k] = tm;
+  C[k] = t1 + hc * (-S[k + s] + S[k] - Q[k] + Q[k - t]) +
+         hv * (f43 * (vr + vl) + L.Av[k] + L.Av[k - t]);
+  M0[k] = -L.rhon[k + s] * Tf[k] * P.iM;
+  M1[k] = -L.rhon[k] * Tf[k] * P.iM;
+}
+
 // per-step row coefficients of the momentum rows (needs k_frozen_coef2): time =
 // x T1 + T0 + A rho(c) x/(2dt); Dg = the iterate-independent part of the
 // diagonal entry (the whole entry is Dg + A rho(c)/(2dt)), with the reflected
@@ -1296,6 +1327,8 @@ __global__ void k_frozen_coef3(Prm<T> P, Lv<T> L) {
     L.T0u[k] = -Arn * L.un[k] * P.idt;
     L.Dgu[k] = t1 + T(0.5) * L.ih * (-L.Sx[k + 1] + L.Sx[k] - L.Qx[k] * gt + L.Qx[k - W] * gb) +
                P.iRe * L.ih2 * ((vis[k + 1] + vis[k]) * (T(1) + third) + gt * L.Av[k] + gb * L.Av[k - W]);
+    assemble_row(P, L, k, 1, W, t1, L.Sx, L.Qx, L.Tx, L.Cu, L.aPu, L.aMu, L.tPu, L.tMu, L.M0u,
+                 L.M1u);
   }
   if (i >= 1) {  // y-edge (i, j+1/2)
     T Arn = L.Arv[k];
@@ -1305,6 +1338,8 @@ __global__ void k_frozen_coef3(Prm<T> P, Lv<T> L) {
     L.T0v[k] = -Arn * L.vn[k] * P.idt;
     L.Dgv[k] = t1 + T(0.5) * L.ih * (-L.Qy[k] * ge + L.Qy[k - 1] * gw - L.Sy[k + W] + L.Sy[k]) +
                P.iRe * L.ih2 * (ge * L.Av[k] + gw * L.Av[k - 1] + (vis[k + W] + vis[k]) * (T(1) + third));
+    assemble_row(P, L, k, W, 1, t1, L.Sy, L.Qy, L.Ty, L.Cv, L.aPv, L.aMv, L.tPv, L.tMv, L.M0v,
+                 L.M1v);
   }
 }
 
@@ -1571,7 +1606,7 @@ __device__ __forceinline__ void bc_unknowns_block(const Lv<T>& L) {
 template <typename T>
 struct MomRow {
   const T *a, *b, *S, *Q, *Tf, *Arn, *Dv, *T1, *T0, *Dg, *B, *f;
-  int s, t;
+  int s, t, d;
   T grav;
 };
 
@@ -1595,6 +1630,7 @@ __device__ __forceinline__ MomRow<T> mom_row(const Prm<T>& P, const Lv<T>& L, in
   R.f = d ? L.fv : L.fu;
   R.s = d ? L.pitch : 1;
   R.t = d ? 1 : L.pitch;
+  R.d = d;
   // gravity: the primitive momentum row only (the error equation cancels it,
   // the projection method puts it in the projection equation)
   R.grav = (d && std::is_same<Form, FullForm>::value) ? P.Fr_inv : T(0);
@@ -1607,6 +1643,9 @@ template <typename T, class Form>
 __device__ __forceinline__ T mom_residual(const Prm<T>& P, const Lv<T>& L, const MomRow<T>& R, int k,
                                           T rl, T rr) {
   T Ar = T(0.5) * (rl + rr);
+  // FP64 primitive rows: the per-step assembled stencil
+  if constexpr (std::is_same<Form, FullForm>::value && sizeof(T) == 8)
+    return mom_asm(P, L, R.d, k, Ar) - R.f[k];
   const int s = R.s, t = R.t;
   const T *a = R.a, *b = R.b, *vis = L.visn, *rn = L.rhon;
   T ae = a[k];

@@ -58,6 +58,18 @@ struct Lv {
   // the residual read the density instead of dividing for it; the values are
   // those rho_of gives.
   T* rhoc = nullptr;
+  // FP64 full-iterate levels only, built per step: the momentum rows of
+  // (pm-num-mx) assembled as stencils.  Apart from the density term A rho(c)
+  // u / (2dt), each row is linear in the iterate with coefficients that depend
+  // on frozen data only.  For the x row at edge k (y row: u <-> v, strides
+  // swapped): Cu multiplies u at the edge itself, aPu / aMu its neighbours
+  // along x (k + 1, k - 1), tPu / tMu across (k + W, k - W), M0u / M1u the mu of
+  // the cells k and k + 1.  Wall edges read their reflected ghosts, as the
+  // unassembled row does.
+  T *Cu = nullptr, *aPu = nullptr, *aMu = nullptr, *tPu = nullptr, *tMu = nullptr,
+    *M0u = nullptr, *M1u = nullptr;
+  T *Cv = nullptr, *aPv = nullptr, *aMv = nullptr, *tPv = nullptr, *tMv = nullptr,
+    *M0v = nullptr, *M1v = nullptr;
   // error-equation (defect-correction) levels only: base state X the iterate
   // e is a correction to, and X.c - c^n formed in FP64 before rounding
   T *Bc = nullptr, *Bmu = nullptr, *Bu = nullptr, *Bv = nullptr, *Bdc = nullptr;
@@ -205,6 +217,29 @@ __device__ __forceinline__ T op_p(const Prm<T>& P, const Lv<T>& L, int k) {
   return dv - P.alpha * P.iPe * L.ih2 * diff;
 }
 
+// Momentum row d (0: x row at x-edge k, unknown u; 1: y row at y-edge k,
+// unknown v) of (pm-num-mx) from the per-step assembled stencil (the arrays
+// Cu.. / Cv.. of Lv): the same sum as op_u / op_v, term by term, regrouped by
+// unknown.  Ar = A rho(c) on the edge.  s is the stride along the edge normal,
+// t across it; a the row's own velocity, b the other one.
+template <typename T>
+__device__ __forceinline__ T mom_asm(const Prm<T>& P, const Lv<T>& L, int d, int k, T Ar) {
+  const int s = d ? L.pitch : 1, t = d ? 1 : L.pitch;
+  const T *a = d ? L.v : L.u, *b = d ? L.u : L.v;
+  const T *C = d ? L.Cv : L.Cu, *aP = d ? L.aPv : L.aPu, *aM = d ? L.aMv : L.aMu;
+  const T *tP = d ? L.tPv : L.tPu, *tM = d ? L.tMv : L.tMu;
+  const T *M0 = d ? L.M0v : L.M0u, *M1 = d ? L.M1v : L.M1u;
+  T ae = a[k];
+  T r = (d ? L.T0v : L.T0u)[k] + (C[k] + T(0.5) * P.idt * Ar) * ae;
+  r += aP[k] * a[k + s] + aM[k] * a[k - s] + tP[k] * a[k + t] + tM[k] * a[k - t];
+  // the grad-div term's cross derivative of the other velocity
+  T vl = L.visn[k], vr = L.visn[k + s];
+  r -= (P.iRe * L.ih2 * T(1.0 / 3.0)) * (vr * (b[k + s] - b[k + s - t]) - vl * (b[k] - b[k - t]));
+  r += (L.p[k + s] - L.p[k]) * (L.ih * P.iM) + M0[k] * L.mu[k] + M1[k] * L.mu[k + s];
+  if (d) r += P.Fr_inv * L.Arv[k];
+  return r;
+}
+
 // x row of (pm-num-mx) at edge u_{i+1/2,j} (array index k = at(i,j)); cells k (left), k+1 (right),
 // vertices k (top, (i+1/2, j+1/2)) and k-W (bottom); (e1e1-1), (e1e1-2) and (e1e1)
 // (Ar = (rho(c_k) + rho(c_{k+1})) / 2, the density average on the edge).  PST =
@@ -212,6 +247,7 @@ __device__ __forceinline__ T op_p(const Prm<T>& P, const Lv<T>& L, int k) {
 // row of the projection method (pj-num-mx).
 template <typename T, bool PST = true>
 __device__ __forceinline__ T op_u(const Prm<T>& P, const Lv<T>& L, int k, T Ar) {
+  if constexpr (PST && sizeof(T) == 8) return mom_asm(P, L, 0, k, Ar);  // FP64 primitive row
   const int W = L.pitch;
   const T *u = L.u, *vis = L.visn, *rn = L.rhon;
   T ue = u[k];
@@ -243,6 +279,7 @@ __device__ __forceinline__ T op_u(const Prm<T>& P, const Lv<T>& L, int k) {
 // pressure, surface tension and gravity (those act in (pj-num-pjx))
 template <typename T, bool PST = true>
 __device__ __forceinline__ T op_v(const Prm<T>& P, const Lv<T>& L, int k, T Ar) {
+  if constexpr (PST && sizeof(T) == 8) return mom_asm(P, L, 1, k, Ar);  // FP64 primitive row
   const int W = L.pitch;
   const T *v = L.v, *vis = L.visn, *rn = L.rhon;
   T ve = v[k];

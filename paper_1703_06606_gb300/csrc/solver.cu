@@ -86,7 +86,7 @@ double seconds_since(std::chrono::steady_clock::time_point t0) {
   return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
 }
 
-constexpr int NFIELD = 45;  // arrays per level (see Lv)
+constexpr int NFIELD = 59;  // arrays per FP64 level (see Lv)
 // doubles in s->scal and its pinned host mirror s->hbuf, and the offset of the
 // device-side step loop's control block in them (layout in kernels.cu); its
 // entry WAIT_FLAG is set by a bounded wait of the wavefront smoother that ran
@@ -393,7 +393,9 @@ int alloc_all(qnsch_s* s) {
                           &L.smu, &L.sp, &L.su,   &L.sv,   &L.cn,   &L.un, &L.vn,  &L.rhon,
                           &L.mobn, &L.visn, &L.Gn, &L.Aru, &L.Arv,  &L.Sx, &L.Sy,  &L.Qx,
                           &L.Qy, &L.Av,  &L.Tx,   &L.Ty,   &L.Dvu,  &L.Dvv, &L.T1u, &L.T1v,
-                          &L.T0u, &L.T0v, &L.Dgu, &L.Dgv, &L.rhoc};
+                          &L.T0u, &L.T0v, &L.Dgu, &L.Dgv, &L.rhoc,
+                          &L.Cu, &L.aPu, &L.aMu, &L.tPu, &L.tMu, &L.M0u, &L.M1u,
+                          &L.Cv, &L.aPv, &L.aMv, &L.tPv, &L.tMv, &L.M0v, &L.M1v};
     for (int q = 0; q < NFIELD; ++q) *f[q] = base + (size_t)q * n + pitch + 1;  // origin (0,0)
     a /= 2;
     b /= 2;
@@ -439,9 +441,10 @@ int alloc_all(qnsch_s* s) {
 }
 
 // error-equation levels: the 38 arrays of a level without the per-step row
-// coefficients and rho(c) of the iterate (their operators do not use them),
-// plus the base Bc, Bmu, Bu, Bv, Bdc
-constexpr int NFIELD_ERR = NFIELD - 7 + 5;
+// coefficients, the assembled momentum stencils and rho(c) of the iterate
+// (their operators use none of them), plus the base Bc, Bmu, Bu, Bv, Bdc
+constexpr int NFIELD_ERR = NFIELD - 7 - 14 + 5;
+static_assert(NFIELD_ERR == 43, "error-level arrays");
 
 template <typename T>
 int alloc_err_levels(qnsch_s* s, std::vector<Lv<T>>& E) {

@@ -1,5 +1,5 @@
 """qnsch_footprint (host logic, no device) against the layout include/qnsch.h
-and the design notes describe, recomputed here: per level one FP64 block of 45
+and the design notes describe, recomputed here: per level one FP64 block of 59
 arrays over the padded index space (row pitch m1 + 3 rounded up to 32
 elements, m2 + 3 rows), one more block of 43 arrays per level for the error
 equation (FP32 at precision 1, FP64 at precision 2), the committed state (5
@@ -30,7 +30,7 @@ def _bytes(m1, m2, px, levels, precision):
         n = -(-(a + 3) // 32) * 32 * (b + 3)
         if l == 0:
             n0 = n
-        total += 45 * 8 * n + (43 * (4 if precision == 1 else 8) * n if precision else 0)
+        total += 59 * 8 * n + (43 * (4 if precision == 1 else 8) * n if precision else 0)
         a, b = a // 2, b // 2
     total += 5 * 8 * n0 + 10 * 8 * n0
     total += -(-(m1 + 1) // 32) * -(-(m2 + 1) // 8) * 10 * 8
@@ -52,8 +52,8 @@ def test_footprint_of_the_bench_workloads():
     """The sizes quoted for the droplet and Rayleigh-Taylor workloads."""
     mb = [qnsch.footprint(256, 512, False, 0, p) / 1e6 for p in (0, 1, 2)]
     gb = [qnsch.footprint(1024, 4096, True, 0, p) / 1e9 for p in (0, 1, 2)]
-    assert [round(x, 1) for x in mb] == [94.1, 130.1, 166.0]
-    assert [round(x, 2) for x in gb] == [2.66, 3.67, 4.68]
+    assert [round(x, 1) for x in mb] == [117.5, 153.5, 189.4]
+    assert [round(x, 2) for x in gb] == [3.32, 4.33, 5.34]
 
 
 def test_footprint_rejects_what_create_rejects():
