@@ -755,23 +755,24 @@ def run_ours(args, rank, world, local_rank):
 # multiply-add = 2), counted from the formulas of one 5x5 Vanka block (Sec. 7.1)
 # as the kernel evaluates it: 4 edge averages of the densities rho(c) (read from
 # the array the smoothers keep), 4 diagonals from the per-step row
-# coefficients, off-diagonals and the mass row, 4 momentum and 1 mass
-# residual, the structured block solve, 5 updates
-VANKA_FP64_FLOPS_PER_VISIT = 391.0
+# coefficients, off-diagonals and the mass row, 4 momentum residuals from the
+# per-step assembled stencils and 1 mass residual, the structured block solve,
+# 5 updates
+VANKA_FP64_FLOPS_PER_VISIT = 287.0
 # FP64 operations per CH cell visit (N_c, N_mu, the 2x2 Jacobian, its solve and
 # rho of the new c) and per residual cell (all five families), as ncu counts
 # them executed (add, mul = 1, fma = 2) on the FP64 kernels
 CH_FP64_FLOPS_PER_VISIT = 241.0
-RESIDUAL_FP64_FLOPS_PER_CELL = 327.0
+RESIDUAL_FP64_FLOPS_PER_CELL = 223.0
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of a timed kind (average
 # over its launches), from one ncu capture of the same kernel build (the
 # profiles/ file named beside it; cold-cache, serialised); a kind without a
 # capture of the current build reports traffic null.  Drop these entries when
 # the kernels change.
 TRAFFIC_BYTES = {
-    "vanka_levels": (2.51e6, "profiles/dram_per_kernel_fp64_step_rising_drop_256x512.md"),
-    "vanka_finest": (27.57e6, "profiles/dram_per_kernel_fp64_step_rising_drop_256x512.md"),
-    "coarse_vcycle": (0.37e6, "profiles/dram_per_kernel_fp64_step_rising_drop_256x512.md"),
+    "vanka_levels": (3.08e6, "profiles/dram_per_kernel_fp64_step_rising_drop_256x512.md"),
+    "vanka_finest": (33.99e6, "profiles/dram_per_kernel_fp64_step_rising_drop_256x512.md"),
+    "coarse_vcycle": (0.39e6, "profiles/dram_per_kernel_fp64_step_rising_drop_256x512.md"),
     "ch": (15.66e6, "profiles/dram_per_kernel_fp64_step_rising_drop_256x512.md"),
     "vanka_finest_fp32": (431.99e6, "profiles/dram_per_kernel_rayleigh_taylor_1024x4096.md"),
     "ch_fp32": (299.10e6, "profiles/dram_per_kernel_rayleigh_taylor_1024x4096.md"),

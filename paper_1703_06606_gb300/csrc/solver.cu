@@ -799,24 +799,40 @@ double maxfam(const double* n10) {
   return m;
 }
 
+// The host layout of a field (qnsch_get_fields) as a box of the padded level
+// layout: kind 0 cells (m1 x m2 from (1,1)), 1 x-edges (m1 + 1 x m2 from
+// (0,1)), 2 y-edges (m1 x m2 + 1 from (1,0)); rows of `width` bytes, `rows`
+// of them, `dpitch` bytes apart on the device, contiguous on the host.
+struct HostBox {
+  double* dev;
+  size_t dpitch, width, rows;
+};
+HostBox host_box(const Lv<double>& V, double* a, int kind) {
+  const int i0 = kind == 1 ? 0 : 1, j0 = kind == 2 ? 0 : 1;
+  HostBox b;
+  b.dev = a + (size_t)j0 * V.pitch + i0;
+  b.dpitch = (size_t)V.pitch * sizeof(double);
+  b.width = (size_t)(kind == 1 ? V.m1 + 1 : V.m1) * sizeof(double);
+  b.rows = (size_t)(kind == 2 ? V.m2 + 1 : V.m2);
+  return b;
+}
+
 int copy_fields_in(qnsch_s* s, double* const dst[5], const double* const src[5], bool host) {
   Lv<double> V = s->L[0];
   const int kinds[5] = {0, 0, 1, 2, 0};  // c, mu, u, v, p
-  size_t nel[3] = {(size_t)s->m1 * s->m2, (size_t)(s->m1 + 1) * s->m2,
-                   (size_t)s->m1 * (s->m2 + 1)};
-  double* tmp = host ? s->stage : nullptr;
   for (int q = 0; q < 5; ++q) {
-    const double* sp = src[q];
     if (host) {
-      if (cudaMemcpyAsync(tmp, src[q], nel[kinds[q]] * sizeof(double), cudaMemcpyHostToDevice,
-                          s->stream) != cudaSuccess)
+      // host rows straight into the padded layout (one strided copy per field;
+      // the sync below returns only once every copy has read the caller's arrays)
+      const HostBox b = host_box(V, dst[q], kinds[q]);
+      if (cudaMemcpy2DAsync(b.dev, b.dpitch, src[q], b.width, b.width, b.rows,
+                            cudaMemcpyHostToDevice, s->stream) != cudaSuccess) {
+        cudaGetLastError();
+        sync(s);
         return QNSCH_ECUDA;
-      sp = tmp;
-    }
-    qn::launch_pack_in(V, dst[q], sp, kinds[q], s->stream);
-    if (host) {
-      int rc = sync(s);  // the staging buffer is reused by the next field
-      if (rc) return rc;
+      }
+    } else {
+      qn::launch_pack_in(V, dst[q], src[q], kinds[q], s->stream);
     }
   }
   Lv<double> W = V;
@@ -834,21 +850,23 @@ int copy_fields_in(qnsch_s* s, double* const dst[5], const double* const src[5],
 int copy_fields_out(const qnsch_s* s, double* const src[5], double* const dst[5], bool host) {
   const Lv<double>& V = s->L[0];
   const int kinds[5] = {0, 0, 1, 2, 0};
-  size_t nel[3] = {(size_t)s->m1 * s->m2, (size_t)(s->m1 + 1) * s->m2,
-                   (size_t)s->m1 * (s->m2 + 1)};
-  double* tmp = host ? s->stage : nullptr;
+  int rc = QNSCH_OK;
   for (int q = 0; q < 5; ++q) {
     if (!dst[q]) continue;
-    double* dp = host ? tmp : dst[q];
-    qn::launch_pack_out(V, dp, src[q], kinds[q], s->stream);
     if (host) {
-      cudaMemcpyAsync(dst[q], tmp, nel[kinds[q]] * sizeof(double), cudaMemcpyDeviceToHost,
-                      s->stream);
-      int rc = sync(s);
-      if (rc) return rc;
+      const HostBox b = host_box(V, src[q], kinds[q]);
+      if (cudaMemcpy2DAsync(dst[q], b.width, b.dev, b.dpitch, b.width, b.rows,
+                            cudaMemcpyDeviceToHost, s->stream) != cudaSuccess) {
+        cudaGetLastError();
+        rc = QNSCH_ECUDA;
+        break;
+      }
+    } else {
+      qn::launch_pack_out(V, dst[q], src[q], kinds[q], s->stream);
     }
   }
-  return sync(s);
+  int rs = sync(s);
+  return rc ? rc : rs;
 }
 
 // the error-equation levels of the precision in use (allocated once)
