@@ -134,7 +134,7 @@ int qnsch_footprint(const qnsch_grid* grid, int precision, size_t* bytes);
    "maxcyc": 50, "omega_vanka": 1, "M": Cn, "eta_st": eta(rho1, rho2),
    "eps_mob": Cn, "precision": 0, "graphs": 1, "fuse_cells": 128,
    "fuse_cells32": 512, "fuse_ctas": 1, "coupled": 0, "scheme": 0, "vanka_team_max": 8192,
-   "vanka_team8_max": 0,
+   "vanka_team8_max": 0, "vanka_pair_max": 0,
    "ch_team_max": 4096, "vanka_team_max32": 65536, "ch_team_max32": 0,
    "pdl": 1, "step_time_limit": 0, "diverge_cycles": 0, "device_loop": 0,
    "wave_cells32": 0, "wave_rows": 8, "wave_wait_cycles": 2147483648,
@@ -226,6 +226,12 @@ int qnsch_footprint(const qnsch_grid* grid, int precision, size_t* bytes);
    instructions per lane; same arithmetic up to the order of two additions);
    a value > 0 also uses eight lanes in the single-block coarse V-cycle where
    a colour fits the block in one pass.  0 (the default): never.
+   vanka_pair_max: FP64 full-iterate levels above vanka_team_max with at most
+   this many cells per Vanka colour run the 5x5 blocks with a lane pair, the
+   x pair of rows (W, E) on one lane and the y pair (S, N) on the other, each
+   lane factoring its own 2x2 block of the structured solve (half the FP64
+   instructions per lane of one lane per block; the four-lane team's
+   arithmetic).  0 (the default): never.
    pdl: 1 launches every kernel with programmatic dependent launch, so that
    a kernel is scheduled as its predecessor's blocks exit and waits on the GPU
    for the predecessor's results before touching memory (same results); 0

@@ -2013,6 +2013,97 @@ __global__ void __launch_bounds__(SNT) k_vanka_team(Prm<T> P, Lv<T> L, int colou
   vanka_team<T, Form>(P, L, i, j, ok, omega);
 }
 
+// Vanka block of cell (i,j) by a lane pair (FP64 full iterate; lane & 1 = d):
+// lane 0 holds the x pair of the block (rows W, E), lane 1 the y pair (S, N).
+// Each lane builds its two momentum rows (team_row) and its two faces of the
+// mass row; one shuffle adds the faces.  The structured solve of solve_vanka
+// then runs with each lane factoring only its own pair's 2x2 block B: s = w.z
+// and t = w.y are the sums of the two pairs' shares, one shuffle each, and
+// g, p and the pressure pivot are formed on both lanes alike.  Every sum is
+// associated as in the four-lane team ((W + E) + (S + N)), so the arithmetic
+// is the team's.  Against one lane per visit this halves each lane's FP64
+// instructions, which is what bounds a launch whose colour fills the GPU
+// more than once: the busiest sub-partition issues three warps of half a
+// visit instead of two warps of a whole one.
+template <typename T, class Form>
+__device__ __forceinline__ void vanka_pair(const Prm<T>& P, const Lv<T>& L, int i, int j, bool ok,
+                                           T omega) {
+  const unsigned FULL = 0xffffffffu;
+  const int W = L.pitch;
+  const int d = threadIdx.x & 1;
+  const T ih = L.ih, ih2 = L.ih2;
+  int k = L.at(i, j);
+  int eW = (L.px && i == 1) ? L.m1 : i - 1;
+  int kW = L.at(eW, j);
+  bool a0 = L.px || i > 1, a1 = L.px || i < L.m1, a2 = j > 1, a3 = j < L.m2;
+  // this lane's edges: the low one (W or S) and the high one (E or N)
+  bool ap0 = d ? a2 : a0, ap1 = d ? a3 : a1;
+  int ke0 = d ? k - W : kW;
+  T dq0, bq0, dq1, bq1;
+  team_row<T, Form>(P, L, i, j, d, ke0, ap0, dq0, bq0);
+  team_row<T, Form>(P, L, i, j, d, k, ap1, dq1, bq1);
+  // the mass row by faces (as vanka_team): faces W, E on lane 0, S, N on lane 1
+  const T* mob = L.mobn;
+  const int off = d ? W : 1;
+  const int n0 = k - off, n1 = k + off;
+  T am0 = mob[n0] + mob[k], am1 = mob[n1] + mob[k];
+  T fs0 = -(d ? L.v[k - W] : L.u[k - 1]) + (d ? L.v[k] : L.u[k]);
+  T fs1 = T(0.5) * am0 * ((L.mu[n0] - L.mu[k]) + P.alpha * (L.p[n0] - L.p[k])) +
+          T(0.5) * am1 * ((L.mu[n1] - L.mu[k]) + P.alpha * (L.p[n1] - L.p[k]));
+  T fs2 = (ap0 ? am0 : T(0)) + (ap1 ? am1 : T(0));
+  fs0 += __shfl_xor_sync(FULL, fs0, 1);
+  fs1 += __shfl_xor_sync(FULL, fs1, 1);
+  fs2 += __shfl_xor_sync(FULL, fs2, 1);
+  T A44 = T(0.5) * P.alpha * P.alpha * P.iPe * fs2 * ih2;
+  T b4 = fs0 * ih - P.alpha * P.iPe * ih2 * fs1 - L.fp[k];
+  // this pair's block B = A_vv - v3 w w^T (TeamSolve, both rows on one lane)
+  T vc = L.visn[k];
+  T S = d ? L.Sy[k] : L.Sx[k];
+  T v3 = vc * P.iRe * L.ih2 * T(1.0 / 3.0);
+  T a = L.ih * P.iM;
+  T B00 = ap0 ? dq0 - v3 : T(1);
+  T B11 = ap1 ? dq1 - v3 : T(1);
+  T B01 = (ap0 && ap1) ? T(0.5) * S * ih - vc * P.iRe * L.ih2 : T(0);
+  T B10 = (ap0 && ap1) ? -T(0.5) * S * ih - vc * P.iRe * L.ih2 : T(0);
+  T idet = qrcp(B00 * B11 - B01 * B10);
+  T z0 = ((ap0 ? B11 : T(0)) + (ap1 ? B01 : T(0))) * idet;
+  T z1 = -((ap1 ? B00 : T(0)) + (ap0 ? B10 : T(0))) * idet;
+  T sdot = z0 + -z1;
+  sdot += __shfl_xor_sync(FULL, sdot, 1);
+  T g = qrcp(T(1) + v3 * sdot);
+  T iden = qrcp(A44 + ih * a * sdot * g);
+  T y0 = (B11 * bq0 - B01 * bq1) * idet;
+  T y1 = (B00 * bq1 - B10 * bq0) * idet;
+  T tdot = y0 + -y1;
+  tdot += __shfl_xor_sync(FULL, tdot, 1);
+  T pr = (b4 + ih * tdot * g) * iden;
+  T f = g * (v3 * tdot + a * pr);
+  T x0 = y0 - z0 * f, x1 = y1 - z1 * f;
+  if (!ok) return;
+  if (d == 0) {
+    if (ap0) store_u(L, eW, j, L.u[kW] - omega * x0);
+    if (ap1) store_u(L, i, j, L.u[k] - omega * x1);
+    store_cell(L, L.p, i, j, L.p[k] - omega * pr);
+  } else {
+    if (ap0) store_v(L, i, j - 1, L.v[k - W] - omega * x0);
+    if (ap1) store_v(L, i, j, L.v[k] - omega * x1);
+  }
+}
+
+// per-level launch with a lane pair per Vanka block (vanka_pair; FP64 full
+// iterate).  Whole warps past the last pair return together.
+template <typename T, class Form>
+__global__ void __launch_bounds__(SNT) k_vanka_pair(Prm<T> P, Lv<T> L, int colour, T omega) {
+  pdl_enter();
+  ColourSlots cs = vanka_slots(L, colour);
+  int t = blockIdx.x * SNT + threadIdx.x;
+  if ((t & ~31) >= 2 * cs.n) return;  // warp-uniform
+  int i = 1, j = 1;
+  bool ok = (t >> 1) < cs.n && vanka_slot_cell(L, colour, cs, t >> 1, i, j);
+  if (!ok) i = j = 1;
+  vanka_pair<T, Form>(P, L, i, j, ok, omega);
+}
+
 // teams of four lanes while the colour fits in four warps per block of the
 // fused group (one warp per sub-partition)
 constexpr int QN_TEAM_MAX_SLOTS = 32;
@@ -2847,7 +2938,7 @@ void launch_ch(const Prm<T>& P, const Lv<T>& L, int colour, cudaStream_t s, int 
 }
 template <typename T, class Form>
 void launch_vanka(const Prm<T>& P, const Lv<T>& L, int colour, T omega, cudaStream_t s,
-                  int team_max, int team8_max) {
+                  int team_max, int team8_max, int pair_max) {
   int n = vanka_slots(L, colour).n;
   if (n <= 0) return;
   if constexpr (std::is_same<Form, FullForm>::value && sizeof(T) == 8) {
@@ -2861,6 +2952,13 @@ void launch_vanka(const Prm<T>& P, const Lv<T>& L, int colour, T omega, cudaStre
                 std::is_same<Form, ErrForm>::value) {
     if (n <= team_max) {  // four lanes per block: shorter critical path per visit
       qlaunch(&k_vanka_team<T, Form>, (4 * n + SNT - 1) / SNT, SNT, 0, s, P, L, colour, omega);
+      ++g_launches;
+      return;
+    }
+  }
+  if constexpr (std::is_same<Form, FullForm>::value && sizeof(T) == 8) {
+    if (n <= pair_max) {  // a lane pair per block: half the FP64 instructions per lane
+      qlaunch(&k_vanka_pair<T, Form>, (2 * n + SNT - 1) / SNT, SNT, 0, s, P, L, colour, omega);
       ++g_launches;
       return;
     }
@@ -3260,7 +3358,7 @@ int partial_rows_needed(int m1, int m2) {
   template void launch_residual<T, F>(const Prm<T>&, const Lv<T>&, double*, cudaStream_t);       \
   template void launch_add_op<T, F>(const Prm<T>&, const Lv<T>&, cudaStream_t);                  \
   template void launch_ch<T, F>(const Prm<T>&, const Lv<T>&, int, cudaStream_t, int);            \
-  template void launch_vanka<T, F>(const Prm<T>&, const Lv<T>&, int, T, cudaStream_t, int, int);
+  template void launch_vanka<T, F>(const Prm<T>&, const Lv<T>&, int, T, cudaStream_t, int, int, int);
 
 #define QN_INSTANTIATE(T)                                                                        \
   template void launch_cast_frozen<T>(const Lv<double>&, const Lv<T>&, cudaStream_t);            \

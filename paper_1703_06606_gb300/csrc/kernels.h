@@ -19,10 +19,13 @@ template <typename T, class Form>
 void launch_ch(const Prm<T>& P, const Lv<T>& L, int colour, cudaStream_t s, int team_max = 0);
 // team_max: FP64 full-iterate levels with at most this many cells per colour
 // use four lanes per Vanka block; team8_max: FP64 full-iterate levels with at
-// most this many cells per colour use eight (half a momentum row per lane)
+// most this many cells per colour use eight (half a momentum row per lane);
+// pair_max: FP64 full-iterate levels above team_max with at most this many
+// cells per colour use two (the x pair of rows on one lane, the y pair on the
+// other)
 template <typename T, class Form>
 void launch_vanka(const Prm<T>& P, const Lv<T>& L, int colour, T omega, cudaStream_t s,
-                  int team_max = 0, int team8_max = 0);
+                  int team_max = 0, int team8_max = 0, int pair_max = 0);
 // a banded wavefront of smoothing passes on one level (kernels.cu, k_wave):
 // npass passes (per smoothing step: CH red, CH black and the kcol Vanka
 // colours, or the kcol coupled colours), bands of `rows` rows, the same team
