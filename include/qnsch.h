@@ -134,7 +134,7 @@ int qnsch_footprint(const qnsch_grid* grid, int precision, size_t* bytes);
    "maxcyc": 50, "omega_vanka": 1, "M": Cn, "eta_st": eta(rho1, rho2),
    "eps_mob": Cn, "precision": 0, "graphs": 1, "fuse_cells": 128,
    "fuse_cells32": 512, "fuse_ctas": 1, "coupled": 0, "scheme": 0, "vanka_team_max": 8192,
-   "vanka_team8_max": 0, "vanka_pair_max": 0,
+   "vanka_team8_max": 0, "vanka_pair_max": 0, "vanka_split": 0,
    "ch_team_max": 4096, "vanka_team_max32": 65536, "ch_team_max32": 0,
    "pdl": 1, "step_time_limit": 0, "diverge_cycles": 0, "device_loop": 0,
    "wave_cells32": 0, "wave_rows": 8, "wave_wait_cycles": 2147483648,
@@ -232,6 +232,15 @@ int qnsch_footprint(const qnsch_grid* grid, int precision, size_t* bytes);
    lane factoring its own 2x2 block of the structured solve (half the FP64
    instructions per lane of one lane per block; the four-lane team's
    arithmetic).  0 (the default): never.
+   vanka_split: FP64 full-iterate Vanka launches that would run one lane per
+   block split their colour instead: the first slots one lane each (a whole
+   number of warps, launched first), the rest as lane pairs.  1: where a cost
+   model of the busiest SM sub-partition finds it cheaper, for colours that
+   fill the sub-partitions more than once (the finest level of the 256x512
+   droplet: one round of single-lane warps and one round of pair warps in
+   place of two single-lane rounds, the second mostly empty); a value >= 2:
+   that many slots, rounded down to a multiple of 32, one lane each; 0 (the
+   default): never.  Each block is visited as vanka_cell or vanka_pair would.
    pdl: 1 launches every kernel with programmatic dependent launch, so that
    a kernel is scheduled as its predecessor's blocks exit and waits on the GPU
    for the predecessor's results before touching memory (same results); 0

@@ -7,6 +7,7 @@
 #include <math_constants.h>
 
 #include <atomic>
+#include <algorithm>
 #include <type_traits>
 
 #include "kernels.h"
@@ -2104,6 +2105,33 @@ __global__ void __launch_bounds__(SNT) k_vanka_pair(Prm<T> P, Lv<T> L, int colou
   vanka_pair<T, Form>(P, L, i, j, ok, omega);
 }
 
+// per-level launch that splits a colour between one lane per block and lane
+// pairs: slots [0, nsingle) one lane each (vanka_cell), the rest a lane pair
+// each (vanka_pair), the single-lane warps first.  nsingle is a multiple of
+// 32, so both branches are warp-uniform.  For a colour that fills the GPU's
+// sub-partitions once and a fraction more (the finest level of the 256x512
+// droplet: 820 warps on 608), a full round of single-lane warps followed by a
+// round of pair warps for the remainder issues fewer FP64 instructions on the
+// busiest sub-partition than a second, mostly empty single-lane round.
+template <typename T, class Form>
+__global__ void __launch_bounds__(SNT) k_vanka_split(Prm<T> P, Lv<T> L, int colour, T omega,
+                                                     int nsingle) {
+  pdl_enter();
+  ColourSlots cs = vanka_slots(L, colour);
+  int t = blockIdx.x * SNT + threadIdx.x;
+  if (t < nsingle) {
+    int i, j;
+    if (t < cs.n && vanka_slot_cell(L, colour, cs, t, i, j)) vanka_cell<T, Form>(P, L, i, j, omega);
+    return;
+  }
+  int u = t - nsingle;
+  if ((u & ~31) >= 2 * (cs.n - nsingle)) return;  // warp-uniform
+  int sl = nsingle + (u >> 1), i = 1, j = 1;
+  bool ok = sl < cs.n && vanka_slot_cell(L, colour, cs, sl, i, j);
+  if (!ok) i = j = 1;
+  vanka_pair<T, Form>(P, L, i, j, ok, omega);
+}
+
 // teams of four lanes while the colour fits in four warps per block of the
 // fused group (one warp per sub-partition)
 constexpr int QN_TEAM_MAX_SLOTS = 32;
@@ -2936,9 +2964,47 @@ void launch_ch(const Prm<T>& P, const Lv<T>& L, int colour, cudaStream_t s, int 
   qlaunch(&k_ch<T, Form>, (n + 63) / 64, 64, 0, s, P, L, colour);
   ++g_launches;
 }
+// SM sub-partitions of the current device (4 per SM)
+static int sub_partitions() {
+  static std::atomic<int> sms{0};
+  if (!sms.load()) {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    sms = n > 0 ? n : 1;
+  }
+  return 4 * sms.load();
+}
+
+// Slots of an n-slot FP64 Vanka colour that k_vanka_split runs one lane per
+// block (the rest run as lane pairs).  split >= 2 forces split rounded down to
+// a multiple of 32; split == 1 picks the count by a cost model of the busiest
+// sub-partition: ceil(warps / sub-partitions) rounds of single-lane warps cost
+// one unit each, rounds of pair warps VANKA_PAIR_ROUND each (the measured
+// ratio of a pair round to a single-lane round on the 256x512 droplet's finest
+// level, 7.5 us against 10.4 us), for colours that need two rounds or more.
+// Returns n when no split is cheaper.
+constexpr double VANKA_PAIR_ROUND = 0.72;
+int vanka_split_single(int n, int split) {
+  if (split >= 2) return std::min(n, split / 32 * 32);
+  const long long S = sub_partitions();
+  const long long ws = (n + 31) / 32, rounds = (ws + S - 1) / S;
+  // one round is bound by the latency of a visit's chain, which pairs do not shorten
+  if (rounds < 2) return n;
+  double best = (double)rounds;
+  int ns = n;
+  for (long long k = 0; k < rounds; ++k) {
+    const long long single = std::min<long long>(n, k * S * 32);
+    const long long pw = (2 * (n - single) + 31) / 32;
+    const double cost = (double)k + VANKA_PAIR_ROUND * (double)((pw + S - 1) / S);
+    if (cost < best) { best = cost; ns = (int)single; }
+  }
+  return ns;
+}
+
 template <typename T, class Form>
 void launch_vanka(const Prm<T>& P, const Lv<T>& L, int colour, T omega, cudaStream_t s,
-                  int team_max, int team8_max, int pair_max) {
+                  int team_max, int team8_max, int pair_max, int split) {
   int n = vanka_slots(L, colour).n;
   if (n <= 0) return;
   if constexpr (std::is_same<Form, FullForm>::value && sizeof(T) == 8) {
@@ -2959,6 +3025,14 @@ void launch_vanka(const Prm<T>& P, const Lv<T>& L, int colour, T omega, cudaStre
   if constexpr (std::is_same<Form, FullForm>::value && sizeof(T) == 8) {
     if (n <= pair_max) {  // a lane pair per block: half the FP64 instructions per lane
       qlaunch(&k_vanka_pair<T, Form>, (2 * n + SNT - 1) / SNT, SNT, 0, s, P, L, colour, omega);
+      ++g_launches;
+      return;
+    }
+    const int ns = split > 0 ? vanka_split_single(n, split) : n;
+    if (ns < n) {  // one lane per block for slots [0, ns), a lane pair for the rest
+      const long long threads = (long long)ns + 2LL * (n - ns);
+      qlaunch(&k_vanka_split<T, Form>, (int)((threads + SNT - 1) / SNT), SNT, 0, s, P, L, colour,
+              omega, ns);
       ++g_launches;
       return;
     }
@@ -3358,7 +3432,7 @@ int partial_rows_needed(int m1, int m2) {
   template void launch_residual<T, F>(const Prm<T>&, const Lv<T>&, double*, cudaStream_t);       \
   template void launch_add_op<T, F>(const Prm<T>&, const Lv<T>&, cudaStream_t);                  \
   template void launch_ch<T, F>(const Prm<T>&, const Lv<T>&, int, cudaStream_t, int);            \
-  template void launch_vanka<T, F>(const Prm<T>&, const Lv<T>&, int, T, cudaStream_t, int, int, int);
+  template void launch_vanka<T, F>(const Prm<T>&, const Lv<T>&, int, T, cudaStream_t, int, int, int, int);
 
 #define QN_INSTANTIATE(T)                                                                        \
   template void launch_cast_frozen<T>(const Lv<double>&, const Lv<T>&, cudaStream_t);            \

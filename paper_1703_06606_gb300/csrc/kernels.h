@@ -22,10 +22,15 @@ void launch_ch(const Prm<T>& P, const Lv<T>& L, int colour, cudaStream_t s, int 
 // most this many cells per colour use eight (half a momentum row per lane);
 // pair_max: FP64 full-iterate levels above team_max with at most this many
 // cells per colour use two (the x pair of rows on one lane, the y pair on the
-// other)
+// other); split (FP64 full-iterate single-lane launches): 0 never, 1 split a
+// colour between one lane per block and lane pairs where a cost model of the
+// busiest sub-partition says it is cheaper, >= 2 that many slots (rounded
+// down to a multiple of 32) one lane each and the rest as pairs
 template <typename T, class Form>
 void launch_vanka(const Prm<T>& P, const Lv<T>& L, int colour, T omega, cudaStream_t s,
-                  int team_max = 0, int team8_max = 0, int pair_max = 0);
+                  int team_max = 0, int team8_max = 0, int pair_max = 0, int split = 0);
+// slots of an n-slot colour that the split launch runs one lane each (n: no split)
+int vanka_split_single(int n, int split);
 // a banded wavefront of smoothing passes on one level (kernels.cu, k_wave):
 // npass passes (per smoothing step: CH red, CH black and the kcol Vanka
 // colours, or the kcol coupled colours), bands of `rows` rows, the same team

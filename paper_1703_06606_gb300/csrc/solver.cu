@@ -181,6 +181,10 @@ struct qnsch_s {
   // Vanka colour smooth with a lane pair per block (x rows on one lane, y rows
   // on the other) in the per-level launches
   int pair_max = 0;
+  // FP64 full-iterate single-lane Vanka launches: 0 as they are; 1 split a
+  // colour between one lane per block and lane pairs where a cost model says
+  // it is cheaper; >= 2 that many slots (a multiple of 32) one lane each
+  int vsplit = 0;
   // the same for the CH smoother's per-level launches (cells per red-black colour)
   int ch_team_max = 4096, ch_team_max32 = 0;
   // the same on the error-equation levels of the defect correction (their
@@ -620,7 +624,8 @@ void smooth(qnsch_s* s, const std::vector<Lv<T>>& Ls, const Prm<T>& P, int l) {
     else qn::launch_vanka<T, Form>(P, L, c, (T)s->omega, s->stream,
                                    std::is_same<Form, ErrForm>::value ? s->team_max32 : s->team_max,
                                    std::is_same<Form, ErrForm>::value ? 0 : s->team8_max,
-                                   std::is_same<Form, ErrForm>::value ? 0 : s->pair_max);
+                                   std::is_same<Form, ErrForm>::value ? 0 : s->pair_max,
+                                   std::is_same<Form, ErrForm>::value ? 0 : s->vsplit);
     prof_close(s, q);
   }
 }
@@ -1593,12 +1598,13 @@ int set_option(qnsch_s* s, const std::string& k, double value) {
     s->diverge = n;
   } else if (k == "fuse_cells" || k == "fuse_cells32" || k == "vanka_team_max" ||
              k == "ch_team_max" || k == "ch_team_max32" || k == "vanka_team_max32" ||
-             k == "vanka_team8_max" || k == "vanka_pair_max") {
+             k == "vanka_team8_max" || k == "vanka_pair_max" || k == "vanka_split") {
     if (!count_of(value, 0, imax, &n)) return QNSCH_EINVAL;
     (k == "fuse_cells" ? s->fuse64 : k == "fuse_cells32" ? s->fuse32
      : k == "vanka_team_max" ? s->team_max : k == "ch_team_max" ? s->ch_team_max
      : k == "ch_team_max32" ? s->ch_team_max32 : k == "vanka_team8_max" ? s->team8_max
-     : k == "vanka_pair_max" ? s->pair_max : s->team_max32) = n;
+     : k == "vanka_pair_max" ? s->pair_max : k == "vanka_split" ? s->vsplit
+     : s->team_max32) = n;
   } else if (k == "fuse_ctas") {
     if (!count_of(value, 1, 16, &n) || (n & (n - 1))) return QNSCH_EINVAL;
     // the largest cluster at most n blocks wide that this device can launch
@@ -1672,6 +1678,7 @@ int qnsch_get_option(const qnsch_t* s, const char* key, double* value) {
   else if (k == "vanka_team_max32") *value = s->team_max32;
   else if (k == "vanka_team8_max") *value = s->team8_max;
   else if (k == "vanka_pair_max") *value = s->pair_max;
+  else if (k == "vanka_split") *value = s->vsplit;
   else if (k == "pdl") *value = g_pdl_option.load();
   else return QNSCH_EINVAL;
   return QNSCH_OK;

@@ -55,7 +55,7 @@ def main():
         return
     if a.kernel == "fp64issue":
         print("warps/block  active lanes  chains  cycles per warp FMA")
-        for warps in (4, 16):
+        for warps in (1, 2, 3, 4, 8, 16):
             for active in (1, 32):
                 for chains in (1, 8):
                     c = probe.fp64_issue_probe(warps, active, chains, 1024)

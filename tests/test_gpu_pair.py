@@ -108,3 +108,61 @@ def test_pair_full_steps_rising_drop(qn):
     fg, fr = g.get_fields(), r.get_fields()
     for k in fg:
         assert relerr(fg[k], fr[k]) <= 1e-10, k
+
+
+# ---- the split launch (option vanka_split): one lane per block for the first
+# slots of a colour, lane pairs for the rest
+
+
+@pytest.mark.parametrize("m1,m2,px,split", [(37, 29, False, 64), (40, 24, True, 32),
+                                           (65, 33, False, 96), (16, 12, True, 2)])
+def test_split_sweep_parity(qn, m1, m2, px, split):
+    """A forced split (split slots one lane each, rounded down to a multiple
+    of 32; 2 rounds to none, so every block is a pair) against the oracle."""
+    g = qn.Solver(m1, m2, periodic_x=px, vanka_team_max=0, vanka_split=split, **KW)
+    r = RefSolver(m1, m2, periodic_x=px, **KW)
+    fn = W.random_state(m1, m2, px, seed=47)
+    fx = W.random_state(m1, m2, px, seed=48)
+    for s in (g, r):
+        _begin(s, fn, fx)
+    for colour in range(g.ncolours_vanka):
+        g.smooth_vanka(colour)
+        r.smooth_vanka(colour)
+        fg, fr = g.get_iterate(), r.get_iterate()
+        for k in fg:
+            assert relerr(fg[k], fr[k]) <= 1e-11, (colour, k)
+
+
+def test_split_vcycle_parity(qn):
+    P = W.small_case(64, 96, True)
+    g = qn.Solver(**P.create_kwargs(), vanka_team_max=0, vanka_split=64)
+    r = RefSolver(**P.create_kwargs())
+    for s in (g, r):
+        s.set_fields(P.fields())
+        s.begin_step(P.dt)
+    for _ in range(3):
+        g.vcycle()
+        r.vcycle()
+        fg, fr = g.get_iterate(), r.get_iterate()
+        for k in fg:
+            assert relerr(fg[k], fr[k]) <= 1e-10, k
+
+
+def test_split_full_steps_rising_drop(qn):
+    """The cost model's split (vanka_split = 1) on the 256x512 droplet, whose
+    finest colours (26,214 blocks) fill a GB300's 608 sub-partitions 1.35
+    times: three steps with the headline's options, equal V-cycle counts and
+    fields within 1e-10 of the oracle."""
+    P = W.rising_drop_256x512()
+    opts = dict(nu1=1, nu2=1, nu1_fine=2, nu2_fine=3, predictor=2)
+    g = qn.Solver(**P.create_kwargs(), tol=P.tol, vanka_split=1, **opts)
+    r = RefSolver(**P.create_kwargs(), tol=P.tol, **opts)
+    g.set_fields(P.fields())
+    r.set_fields(P.fields())
+    for _ in range(3):
+        ng, _ = g.step(P.dt)
+        nr, _ = r.step(P.dt)
+        assert ng == nr
+    fg, fr = g.get_fields(), r.get_fields()
+    for k in fg:
+        assert relerr(fg[k], fr[k]) <= 1e-10, k
