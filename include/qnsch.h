@@ -134,7 +134,7 @@ int qnsch_footprint(const qnsch_grid* grid, int precision, size_t* bytes);
    "maxcyc": 50, "omega_vanka": 1, "M": Cn, "eta_st": eta(rho1, rho2),
    "eps_mob": Cn, "precision": 0, "graphs": 1, "fuse_cells": 128,
    "fuse_cells32": 512, "fuse_ctas": 1, "coupled": 0, "scheme": 0, "vanka_team_max": 8192,
-   "vanka_team8_max": 0, "vanka_pair_max": 0, "vanka_split": 0,
+   "vanka_team8_max": 0, "vanka_pair_max": 0, "vanka_split": 0, "coarse_smem": 1,
    "ch_team_max": 4096, "vanka_team_max32": 65536, "ch_team_max32": 0,
    "pdl": 1, "step_time_limit": 0, "diverge_cycles": 0, "device_loop": 0,
    "wave_cells32": 0, "wave_rows": 8, "wave_wait_cycles": 2147483648,
@@ -241,6 +241,14 @@ int qnsch_footprint(const qnsch_grid* grid, int precision, size_t* bytes);
    place of two single-lane rounds, the second mostly empty); a value >= 2:
    that many slots, rounded down to a multiple of 32, one lane each; 0 (the
    default): never.  Each block is visited as vanka_cell or vanka_pair would.
+   coarse_smem: 1 (the default) runs the fused V-cycle of the coarse FP64
+   full-iterate levels (fuse_cells, in one thread block: fuse_ctas = 1) on a
+   copy of those levels in shared memory, made at the start of the launch and
+   written back at its end, wherever the copy fits the device's shared memory
+   per block (about 151 KB for the 8x16, 4x8 and 2x4 levels); 0 runs it from
+   global memory.  The same device code runs on the same values, so the
+   results are the same.  Reading the key "coarse_smem_used" (get only) gives
+   1 if the last fused launch ran on the shared-memory copy.
    pdl: 1 launches every kernel with programmatic dependent launch, so that
    a kernel is scheduled as its predecessor's blocks exit and waits on the GPU
    for the predecessor's results before touching memory (same results); 0

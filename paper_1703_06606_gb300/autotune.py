@@ -41,6 +41,9 @@ CANDIDATES = {
     # single-lane FP64 Vanka launches split between one lane per block and
     # lane pairs (0: never, 1: by the cost model)
     "vanka_split": [0, 1],
+    # the fused coarse V-cycle of the FP64 levels on a shared-memory copy (1) or
+    # from global memory (0)
+    "coarse_smem": [1, 0],
     "ch_team_max": [4096, 0, 16384],
     "fuse_cells": [128, 32, 512, 4096],
     "vanka_team_max32": [65536, 0, 8192, 131072, 1 << 30],
@@ -74,7 +77,8 @@ MIN_GAIN = 0.005
 # 2 FP64 error form: its error levels use the FP64 thresholds)
 KNOBS = {
     0: ["vanka_team_max", "vanka_team8_max", "vanka_pair_max", "vanka_split", "ch_team_max",
-        "fuse_cells", "fuse_ctas", "nu1", "nu2", "nu_coarse", "nu1_fine", "nu2_fine"],
+        "fuse_cells", "fuse_ctas", "coarse_smem", "nu1", "nu2", "nu_coarse", "nu1_fine",
+        "nu2_fine"],
     1: ["vanka_team_max32", "ch_team_max32", "fuse_cells32", "fuse_ctas", "wave_cells32",
         "wave_rows", "skew_cells32", "skew_rows", "nu1", "nu2", "nu_coarse", "nu1_fine", "nu2_fine"],
     2: ["vanka_team_max32", "ch_team_max32", "fuse_cells", "fuse_ctas", "wave_cells32",

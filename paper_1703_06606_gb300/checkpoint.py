@@ -31,7 +31,7 @@ OPTIONS = ("scheme", "precision", "coupled", "nu1", "nu2", "nu_coarse", "maxcyc"
            "omega_vanka", "M", "eta_st", "eps_mob", "graphs", "fuse_cells", "fuse_cells32",
            "vanka_team_max", "ch_team_max", "vanka_team_max32", "ch_team_max32",
            "step_time_limit", "diverge_cycles", "device_loop", "wave_cells32", "wave_rows",
-           "vanka_team8_max", "vanka_pair_max", "vanka_split", "skew_cells32", "skew_rows", "predictor", "nu1_fine", "nu2_fine",
+           "vanka_team8_max", "vanka_pair_max", "vanka_split", "coarse_smem", "skew_cells32", "skew_rows", "predictor", "nu1_fine", "nu2_fine",
            "fuse_ctas")
 
 

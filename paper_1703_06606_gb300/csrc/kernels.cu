@@ -2284,11 +2284,10 @@ __device__ void smooth_block(const Prm<T>& P, const Lv<T>& L, T omega, int coupl
   }  // primitive method
 }
 
-template <typename T, class Form, int NT>
-__global__ void __launch_bounds__(NT) k_coarse_vcycle(Prm<T> P, CoarseLevels<T> C, int nu1, int nu2,
-                                                      int nuc, int kcol, T omega, int coupled,
-                                                      int team8) {
-  pdl_enter();
+template <typename T, class Form>
+__device__ __forceinline__ void coarse_vcycle_body(const Prm<T>& P, const CoarseLevels<T>& C, int nu1,
+                                                   int nu2, int nuc, T omega, int coupled,
+                                                   int team8) {
   const int n = C.n;
   double dummy[10];
   if (C.base) {
@@ -2333,6 +2332,109 @@ __global__ void __launch_bounds__(NT) k_coarse_vcycle(Prm<T> P, CoarseLevels<T> 
     grp_sync();
     bc_unknowns_block(F);
     for (int s = 0; s < nu2; ++s) smooth_block<T, Form>(P, F, omega, coupled, team8);
+  }
+}
+
+template <typename T, class Form, int NT>
+__global__ void __launch_bounds__(NT) k_coarse_vcycle(Prm<T> P, CoarseLevels<T> C, int nu1, int nu2,
+                                                      int nuc, int kcol, T omega, int coupled,
+                                                      int team8) {
+  pdl_enter();
+  coarse_vcycle_body<T, Form>(P, C, nu1, nu2, nuc, omega, coupled, team8);
+}
+
+// --------------------------------------------------------------------------
+// The fused V-cycle of the FP64 full-iterate levels on a shared-memory copy.
+// Its colour steps are chains of dependent loads and FP64 instructions of one
+// visit each; from shared memory the loads take tens of cycles instead of an
+// L2 round trip.  The block copies every array of its levels (QN_LV_ARRAYS,
+// the padded frame [-1, m1+1] x [-1, m2+1] that the device code reads and
+// writes) into shared memory at the compact pitch m1 + 3, runs the V-cycle
+// body unchanged on level descriptors that point into the copy, and writes
+// back the arrays the V-cycle writes: the unknowns, sources, residuals and the
+// kept restricted iterate (the first 20 arrays) and rho(c).  Same device code
+// on the same values: the results are those of k_coarse_vcycle.
+// --------------------------------------------------------------------------
+constexpr int QN_LV_NARR = 59;     // arrays of QN_LV_ARRAYS
+constexpr int QN_LV_WRITTEN = 20;  // arrays 0..19 are written; and rho(c):
+constexpr int QN_LV_RHOC = 44;
+
+struct CoarseSmem {
+  int off[QN_MAX_FUSED_LEVELS];  // first element of level l's copy
+  long long ng[QN_MAX_FUSED_LEVELS];  // elements per array in the global block
+  int head;  // elements (doubles) before the first copy: the descriptors
+};
+
+// copy arrays [q0, q1) of one level between its global block (pitch pg, ng
+// elements per array) and its compact copy (pitch cc, rr rows).  Thread t
+// takes column t % cw (cw >= cc) of rows t / cw + k NT / cw.  IN: global to
+// shared by asynchronous copies (cp.async, 8 bytes each, all of a thread's in
+// flight at once; the caller waits for them with cp.async.wait_all); else
+// shared to global by plain stores.
+template <int NT, bool IN>
+__device__ __forceinline__ void coarse_copy(double* __restrict__ g, int pg, long long ng,
+                                            double* __restrict__ sh, int cc, int rr, int q0,
+                                            int q1) {
+  const int cw = cc <= 16 ? 16 : 32, tx = threadIdx.x % cw, rstep = NT / cw;
+  if (tx >= cc) return;
+  const int ns = cc * rr;
+  for (int r = threadIdx.x / cw; r < rr; r += rstep) {
+    double* __restrict__ gr = g + (long long)r * pg + tx;
+    double* __restrict__ sr = sh + r * cc + tx;
+#pragma unroll 8
+    for (int q = q0; q < q1; ++q) {
+      if (IN) {
+        const unsigned sa = (unsigned)__cvta_generic_to_shared(sr + q * ns);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gr + q * ng)
+                     : "memory");
+      } else {
+        gr[q * ng] = sr[q * ns];
+      }
+    }
+  }
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) k_coarse_vcycle_smem(Prm<double> P, CoarseLevels<double> C,
+                                                           CoarseSmem M, int nu1, int nu2, int nuc,
+                                                           double omega, int coupled, int team8) {
+  extern __shared__ __align__(16) double qn_coarse_smem[];
+  pdl_enter();
+  CoarseLevels<double>* S = reinterpret_cast<CoarseLevels<double>*>(qn_coarse_smem);
+  double* arr = qn_coarse_smem + M.head;
+  const int n = C.n;
+  for (int l = 0; l < n; ++l) {
+    const Lv<double>& G = C.L[l];
+    const int cc = G.m1 + 3, rr = G.m2 + 3;
+    coarse_copy<NT, true>(G.c - (G.pitch + 1), G.pitch, M.ng[l], arr + M.off[l], cc, rr, 0,
+                          QN_LV_NARR);
+  }
+  if (threadIdx.x < n) {  // the descriptor of level l, its arrays in the copy
+    const int l = threadIdx.x;
+    Lv<double> X = C.L[l];
+    const int cc = X.m1 + 3, ns = cc * (X.m2 + 3);
+    double* o = arr + M.off[l] + cc + 1;  // origin (0,0) of array 0
+    int q = 0;
+#define QN_REBASE(m) X.m = o + (q++) * ns;
+    QN_LV_ARRAYS(QN_REBASE)
+#undef QN_REBASE
+    X.pitch = cc;
+    S->L[l] = X;
+  }
+  if (threadIdx.x == 0) {
+    S->n = n;
+    S->base = 0;
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  __syncthreads();
+  coarse_vcycle_body<double, FullForm>(P, *S, nu1, nu2, nuc, omega, coupled, team8);
+  __syncthreads();
+  for (int l = 0; l < n; ++l) {
+    const Lv<double>& G = C.L[l];
+    const int cc = G.m1 + 3, rr = G.m2 + 3;
+    double* g = G.c - (G.pitch + 1);
+    coarse_copy<NT, false>(g, G.pitch, M.ng[l], arr + M.off[l], cc, rr, 0, QN_LV_WRITTEN);
+    coarse_copy<NT, false>(g, G.pitch, M.ng[l], arr + M.off[l], cc, rr, QN_LV_RHOC, QN_LV_RHOC + 1);
   }
 }
 
@@ -3040,14 +3142,72 @@ void launch_vanka(const Prm<T>& P, const Lv<T>& L, int colour, T omega, cudaStre
   qlaunch(&k_vanka<T, Form>, (n + SNT - 1) / SNT, SNT, 0, s, P, L, colour, omega);
   ++g_launches;
 }
+// Plan of the shared-memory copy of an FP64 full-iterate fused group: every
+// level's arrays at their block's stride in QN_LV_ARRAYS order (checked
+// pointer by pointer), columns within the copy kernel's 32-wide rows, and the
+// whole copy within the device's opt-in shared memory per block.  Returns the
+// dynamic shared-memory bytes, 0 if the group does not qualify.
+static size_t coarse_smem_plan(const Lv<double>* levels, int n, CoarseSmem& M) {
+  static std::atomic<int> optin{0};
+  if (!optin.load()) {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    optin = v > 0 ? v : 1;
+  }
+  const int head = (int)((sizeof(CoarseLevels<double>) + 15) / 16 * 2);
+  long long elems = head;
+  M.head = head;
+  for (int l = 0; l < n; ++l) {
+    const Lv<double>& L = levels[l];
+    const int cc = L.m1 + 3, rr = L.m2 + 3;
+    if (cc > 32 || !L.c) return 0;
+    const long long ng = (long long)L.pitch * rr;
+    int q = 0;
+    bool ok = true;
+#define QN_CHECK(m) ok = ok && L.m == L.c + (q++) * ng;
+    QN_LV_ARRAYS(QN_CHECK)
+#undef QN_CHECK
+    if (!ok) return 0;
+    M.ng[l] = ng;
+    M.off[l] = (int)(elems - head);
+    elems += (long long)QN_LV_NARR * cc * rr;
+    elems = (elems + 1) / 2 * 2;  // 16-byte aligned copies
+  }
+  const size_t bytes = (size_t)elems * sizeof(double);
+  return bytes <= (size_t)optin.load() ? bytes : 0;
+}
+
+void coarse_smem_prepare() {
+  int dev = 0, v = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
+      v > 0)
+    cudaFuncSetAttribute(&k_coarse_vcycle_smem<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, v);
+  cudaGetLastError();
+}
+
 template <typename T, class Form>
-void launch_coarse_vcycle(const Prm<T>& P, const Lv<T>* levels, int n, int nu1, int nu2, int nuc,
-                          int kcol, T omega, int coupled, cudaStream_t s, int team8, int ctas) {
+int launch_coarse_vcycle(const Prm<T>& P, const Lv<T>* levels, int n, int nu1, int nu2, int nuc,
+                         int kcol, T omega, int coupled, cudaStream_t s, int team8, int ctas,
+                         int smem) {
   CoarseLevels<T> C;
   C.n = n;
   C.base = std::is_same<Form, ErrForm>::value;
   for (int l = 0; l < n; ++l) C.L[l] = levels[l];
   constexpr int NT = sizeof(T) == 8 ? 256 : 512;
+  if constexpr (std::is_same<Form, FullForm>::value && sizeof(T) == 8) {
+    if (smem && ctas <= 1) {
+      CoarseSmem M = {};
+      const size_t bytes = coarse_smem_plan(levels, n, M);
+      if (bytes) {
+        qlaunch(&k_coarse_vcycle_smem<NT>, 1, NT, bytes, s, P, C, M, nu1, nu2, nuc, omega, coupled,
+                team8);
+        ++g_launches;
+        return 1;
+      }
+    }
+  }
   if (ctas <= 1) {
     qlaunch(&k_coarse_vcycle<T, Form, NT>, 1, NT, 0, s, P, C, nu1, nu2, nuc, kcol, omega, coupled,
             team8);
@@ -3069,6 +3229,7 @@ void launch_coarse_vcycle(const Prm<T>& P, const Lv<T>* levels, int n, int nu1, 
                        coupled, team8);
   }
   ++g_launches;
+  return 0;
 }
 
 // largest cluster of at most `ctas` blocks (a power of two) in which the fused
@@ -3426,8 +3587,8 @@ int partial_rows_needed(int m1, int m2) {
 }
 
 #define QN_INSTANTIATE_FORM(T, F)                                                                \
-  template void launch_coarse_vcycle<T, F>(const Prm<T>&, const Lv<T>*, int, int, int, int, int,  \
-                                           T, int, cudaStream_t, int, int);                      \
+  template int launch_coarse_vcycle<T, F>(const Prm<T>&, const Lv<T>*, int, int, int, int, int,   \
+                                          T, int, cudaStream_t, int, int, int);                  \
   template void launch_coupled<T, F>(const Prm<T>&, const Lv<T>&, int, T, cudaStream_t, int);     \
   template void launch_residual<T, F>(const Prm<T>&, const Lv<T>&, double*, cudaStream_t);       \
   template void launch_add_op<T, F>(const Prm<T>&, const Lv<T>&, cudaStream_t);                  \
@@ -3473,9 +3634,9 @@ template int launch_skew<double, ErrForm>(const Prm<double>&, const Lv<double>&,
 // projection method (FP64, per-level launches)
 template void launch_residual<double, ProjForm>(const Prm<double>&, const Lv<double>&, double*,
                                                 cudaStream_t);
-template void launch_coarse_vcycle<double, ProjForm>(const Prm<double>&, const Lv<double>*, int, int,
-                                                     int, int, int, double, int, cudaStream_t, int,
-                                                     int);
+template int launch_coarse_vcycle<double, ProjForm>(const Prm<double>&, const Lv<double>*, int, int,
+                                                    int, int, int, double, int, cudaStream_t, int,
+                                                    int, int);
 template void launch_add_op<double, ProjForm>(const Prm<double>&, const Lv<double>&, cudaStream_t);
 template void launch_ch<double, ProjForm>(const Prm<double>&, const Lv<double>&, int, cudaStream_t,
                                           int);

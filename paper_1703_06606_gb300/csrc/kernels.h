@@ -73,11 +73,17 @@ void launch_predict(double* const x[5], double* const a[5], double* const b[5],
 // the V-cycle on levels[0..n-1] (levels[0] is its finest) in one launch: one
 // thread block (ctas = 1) or one thread-block cluster of ctas blocks, a size
 // coarse_cluster_blocks returned (team8: the FP64 full-iterate Vanka blocks use
-// eight lanes where a colour fits the group in one pass)
+// eight lanes where a colour fits the group in one pass).  smem: an FP64
+// full-iterate group in one block runs on a shared-memory copy of its levels
+// where the copy fits (k_coarse_vcycle_smem, same results).  Returns 1 if it
+// ran on the shared-memory copy, else 0.
 template <typename T, class Form>
-void launch_coarse_vcycle(const Prm<T>& P, const Lv<T>* levels, int n, int nu1, int nu2, int nuc,
-                          int kcol, T omega, int coupled, cudaStream_t s, int team8 = 0,
-                          int ctas = 1);
+int launch_coarse_vcycle(const Prm<T>& P, const Lv<T>* levels, int n, int nu1, int nu2, int nuc,
+                         int kcol, T omega, int coupled, cudaStream_t s, int team8 = 0,
+                         int ctas = 1, int smem = 0);
+// lets the shared-memory fused V-cycle use the device's opt-in shared memory
+// per block (call with the device current, outside stream capture)
+void coarse_smem_prepare();
 // the largest power of two not above ctas (and not above 16) at which every
 // form of the fused V-cycle launches as one cluster on the current device; 1
 // when ctas < 2 or no cluster fits.  Queries the runtime: call it outside

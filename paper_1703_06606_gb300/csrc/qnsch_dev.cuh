@@ -78,6 +78,16 @@ struct Lv {
   __device__ __forceinline__ int uhi() const { return px ? m1 : m1 - 1; }
 };
 
+// The arrays of an FP64 full-iterate level in the order in which they sit in
+// the level's block (one allocation, NFIELD arrays of the same padded size):
+// X(member) for each.
+#define QN_LV_ARRAYS(X)                                                                        \
+  X(c) X(mu) X(p) X(u) X(v) X(fc) X(fmu) X(fp) X(fu) X(fv) X(rc) X(rmu) X(rp) X(ru) X(rv)     \
+  X(sc) X(smu) X(sp) X(su) X(sv) X(cn) X(un) X(vn) X(rhon) X(mobn) X(visn) X(Gn) X(Aru)       \
+  X(Arv) X(Sx) X(Sy) X(Qx) X(Qy) X(Av) X(Tx) X(Ty) X(Dvu) X(Dvv) X(T1u) X(T1v) X(T0u) X(T0v)  \
+  X(Dgu) X(Dgv) X(rhoc) X(Cu) X(aPu) X(aMu) X(tPu) X(tMu) X(M0u) X(M1u) X(Cv) X(aPv) X(aMv)   \
+  X(tPv) X(tMv) X(M0v) X(M1v)
+
 // ---------------------------------------------------------------------------
 // constitutive functions (Sec. 2.1) and secants (Sec. 4.1)
 // ---------------------------------------------------------------------------

@@ -185,6 +185,11 @@ struct qnsch_s {
   // colour between one lane per block and lane pairs where a cost model says
   // it is cheaper; >= 2 that many slots (a multiple of 32) one lane each
   int vsplit = 0;
+  // the fused V-cycle of FP64 full-iterate levels in one block runs on a
+  // shared-memory copy of its levels where it fits (1) or from global memory
+  // (0); coarse_smem_used: whether the last fused launch did
+  int coarse_smem = 1;
+  int coarse_smem_used = 0;
   // the same for the CH smoother's per-level launches (cells per red-black colour)
   int ch_team_max = 4096, ch_team_max32 = 0;
   // the same on the error-equation levels of the defect correction (their
@@ -374,6 +379,7 @@ int alloc_all(qnsch_s* s) {
     return QNSCH_ECUDA;
   }
   s->stream = s->own_stream;
+  qn::coarse_smem_prepare();
   int a = s->m1, b = s->m2;
   double h = s->h;
   s->L.resize(s->nlev);
@@ -701,9 +707,9 @@ void vcycle(qnsch_s* s, const std::vector<Lv<T>>& Ls, const Prm<T>& P, int l) {
       visits += (double)Ls[m].m1 * Ls[m].m2 *
                 (m == s->nlev - 1 ? coarse_sweeps(s) : s->nu1 + s->nu2);
     int q = prof_open(s, PK_COARSE, visits);
-    qn::launch_coarse_vcycle<T, Form>(P, &Ls[l], s->nlev - l, s->nu1, s->nu2, coarse_sweeps(s),
-                                      s->kcol, (T)s->omega, s->coupled, s->stream,
-                                      s->team8_max > 0 ? 1 : 0, s->fuse_ctas);
+    s->coarse_smem_used = qn::launch_coarse_vcycle<T, Form>(
+        P, &Ls[l], s->nlev - l, s->nu1, s->nu2, coarse_sweeps(s), s->kcol, (T)s->omega, s->coupled,
+        s->stream, s->team8_max > 0 ? 1 : 0, s->fuse_ctas, s->coarse_smem);
     prof_close(s, q);
     return;
   }
@@ -1598,13 +1604,14 @@ int set_option(qnsch_s* s, const std::string& k, double value) {
     s->diverge = n;
   } else if (k == "fuse_cells" || k == "fuse_cells32" || k == "vanka_team_max" ||
              k == "ch_team_max" || k == "ch_team_max32" || k == "vanka_team_max32" ||
-             k == "vanka_team8_max" || k == "vanka_pair_max" || k == "vanka_split") {
+             k == "vanka_team8_max" || k == "vanka_pair_max" || k == "vanka_split" ||
+             k == "coarse_smem") {
     if (!count_of(value, 0, imax, &n)) return QNSCH_EINVAL;
     (k == "fuse_cells" ? s->fuse64 : k == "fuse_cells32" ? s->fuse32
      : k == "vanka_team_max" ? s->team_max : k == "ch_team_max" ? s->ch_team_max
      : k == "ch_team_max32" ? s->ch_team_max32 : k == "vanka_team8_max" ? s->team8_max
      : k == "vanka_pair_max" ? s->pair_max : k == "vanka_split" ? s->vsplit
-     : s->team_max32) = n;
+     : k == "coarse_smem" ? s->coarse_smem : s->team_max32) = n;
   } else if (k == "fuse_ctas") {
     if (!count_of(value, 1, 16, &n) || (n & (n - 1))) return QNSCH_EINVAL;
     // the largest cluster at most n blocks wide that this device can launch
@@ -1679,6 +1686,8 @@ int qnsch_get_option(const qnsch_t* s, const char* key, double* value) {
   else if (k == "vanka_team8_max") *value = s->team8_max;
   else if (k == "vanka_pair_max") *value = s->pair_max;
   else if (k == "vanka_split") *value = s->vsplit;
+  else if (k == "coarse_smem") *value = s->coarse_smem;
+  else if (k == "coarse_smem_used") *value = s->coarse_smem_used;
   else if (k == "pdl") *value = g_pdl_option.load();
   else return QNSCH_EINVAL;
   return QNSCH_OK;

@@ -84,6 +84,7 @@ def test_every_knob_has_the_library_default_first():
     defaults = {"vanka_team_max": 8192, "ch_team_max": 4096, "fuse_cells": 128,
                 "vanka_team_max32": 65536, "ch_team_max32": 0, "fuse_cells32": 512,
                 "nu1": 2, "nu2": 2, "nu_coarse": 4, "vanka_team8_max": 0, "vanka_pair_max": 0, "vanka_split": 0,
+                "coarse_smem": 1,
                 "wave_cells32": 0,
                 "wave_rows": 8, "skew_cells32": 0, "skew_rows": 32, "nu1_fine": -1, "nu2_fine": -1}
     for k, v in defaults.items():

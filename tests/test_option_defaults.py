@@ -13,7 +13,7 @@ MEMBERS = {"fuse_cells": "fuse64", "fuse_cells32": "fuse32", "vanka_team_max": "
            "ch_team_max32": "ch_team_max32", "coupled": "coupled", "scheme": "scheme",
            "precision": "precision", "diverge_cycles": "diverge", "device_loop": "device_loop",
            "wave_cells32": "wave_cells", "wave_rows": "wave_rows", "wave_stall": "wave_stall",
-           "vanka_team8_max": "team8_max", "vanka_pair_max": "pair_max", "vanka_split": "vsplit", "nu1": "nu1", "nu2": "nu2", "nu_coarse": "nuc",
+           "vanka_team8_max": "team8_max", "vanka_pair_max": "pair_max", "vanka_split": "vsplit", "coarse_smem": "coarse_smem", "nu1": "nu1", "nu2": "nu2", "nu_coarse": "nuc",
            "skew_cells32": "skew_cells", "skew_rows": "skew_rows", "predictor": "predictor",
            "nu1_fine": "nu1f", "nu2_fine": "nu2f", "fuse_ctas": "fuse_ctas"}
 
