@@ -686,7 +686,7 @@ def run_ours(args, rank, world, local_rank):
     cells = P.cells
     value = world * cells * args.steps / total_s
     e2e_value = world * cells * args.steps / e2e_total
-    roofline = roofline_of(kinds, fp64_peak)
+    roofline = roofline_of(kinds, fp64_peak, coarse_smem=s.get_option("coarse_smem_used") == 1)
     step_flops = step_fp64_flops(s, P, float(np.mean(cyc)))
     roofline["step"] = {
         "achieved": step_flops / (float(np.mean(step_ms)) * 1e-3) / 1e12,
@@ -857,10 +857,11 @@ def fp32_smoother_roofline(s, P, stream, flush, nsteps=2):
     return out
 
 
-def roofline_of(kinds, fp64_peak):
+def roofline_of(kinds, fp64_peak, coarse_smem=False):
     """The roofline entry of the dominant kind of launch (largest share of the
     step's device time): algorithmic FP64 operations per launch over its
-    average event-timed duration, against the FP64 peak measured in this run."""
+    average event-timed duration, against the FP64 peak measured in this run.
+    coarse_smem: the fused coarse V-cycle ran on its shared-memory copy."""
     name, k = max(kinds["kinds"].items(), key=lambda kv: kv[1]["share"])
     per_visit = {"vanka_finest": VANKA_FP64_FLOPS_PER_VISIT,
                  "vanka_levels": VANKA_FP64_FLOPS_PER_VISIT,
@@ -870,7 +871,8 @@ def roofline_of(kinds, fp64_peak):
     achieved = flops / (k["avg_launch_us"] * 1e-6) / 1e12
     kernel = {"vanka_finest": "k_vanka<double> (finest level)",
               "vanka_levels": "k_vanka_team<double> (levels below the finest)",
-              "coarse_vcycle": "k_coarse_vcycle<double> (fused coarse levels)",
+              "coarse_vcycle": ("k_coarse_vcycle_smem (fused coarse levels, shared-memory copy)"
+                                if coarse_smem else "k_coarse_vcycle<double> (fused coarse levels)"),
               "ch": "k_ch<double> (finest level)"}[name]
     tr = TRAFFIC_BYTES.get(name)
     return {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
