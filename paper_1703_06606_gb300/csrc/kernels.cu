@@ -3085,7 +3085,10 @@ static int sub_partitions() {
 // one unit each, rounds of pair warps VANKA_PAIR_ROUND each (the measured
 // ratio of a pair round to a single-lane round on the 256x512 droplet's finest
 // level, 7.5 us against 10.4 us), for colours that need two rounds or more.
-// Returns n when no split is cheaper.
+// Returns n when no split is cheaper.  The model's premise, that the rounds of
+// a sub-partition add up, did not hold on that level: the split it picks
+// (19,456 single-lane blocks, the rest in pairs) took 22.8 us against 20.7 us
+// for one lane per block, whose time is set by one visit's chain per round.
 constexpr double VANKA_PAIR_ROUND = 0.72;
 int vanka_split_single(int n, int split) {
   if (split >= 2) return std::min(n, split / 32 * 32);
