@@ -3,8 +3,10 @@ on one lane, the y pair on the other, each lane factoring its own 2x2 block of
 the structured solve; sums associated as in the four-lane team.  Against the
 FP64 oracle: single colour sweeps at 1e-11 (walls, periodic, ragged, the
 smallest grids), V-cycles with the pairs on every per-level launch at 1e-10,
-and a full step of the 256x512 droplet with equal V-cycle counts at 1e-10;
-against the four-lane team on the same sweep, agreement to rounding."""
+and full steps of the 256x512 droplet with equal V-cycle counts at 1e-10;
+against the four-lane team on the same sweep, agreement to rounding.  The
+split launch (option vanka_split: one lane per block for the first slots of a
+colour, pairs for the rest) is held to the same bars."""
 import numpy as np
 import pytest
 
