@@ -31,10 +31,10 @@ def test_device_array_list_matches_the_allocation_order():
     assert macro == alloc
 
 
-def test_copy_back_covers_what_the_fused_v_cycle_writes():
-    """The copy writes back arrays 0..19 (unknowns, sources, residuals, kept
-    restricted iterate) and rho(c); those are the arrays the fused V-cycle's
-    device functions assign to."""
+def test_copy_back_indices_name_the_arrays_meant():
+    """The copy writes back arrays 0..QN_LV_WRITTEN-1 and QN_LV_RHOC by index;
+    those indices name the unknowns, the sources, the residuals, the kept
+    restricted iterate and rho(c) of the list."""
     macro = _macro_order()
     txt = open(os.path.join(CSRC, "kernels.cu")).read()
     written = int(re.search(r"QN_LV_WRITTEN = (\d+);", txt).group(1))
